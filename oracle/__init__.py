@@ -1,0 +1,248 @@
+"""CPU oracle for semi-analytical (Pollock 1988) particle tracking.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg import this package.  The product path (the
+CUDA library and its binding) never touches it, and this package imports
+nothing from the product.
+
+The arithmetic lives in ``mp_oracle.c`` (plain single-threaded IEEE double,
+compiled with ``-O2 -ffp-contract=off``); this file only compiles it and
+marshals numpy arrays.  A field is any object with the attributes
+``nlay, nrow, ncol, delr, delc, dz, origin, qx, qy, qz, porosity, ibound``.
+
+Pins: every function here is checked against closed forms, brute-force RK4
+integration and invariants in ``tests/test_oracle_*.py``; parity with
+MODPATH itself is unpinned (MODPATH is not available).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mp_oracle.c")
+_HDR = os.path.join(_HERE, "mp_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+ST_ACTIVE, ST_TIME, ST_SINK, ST_BOUNDARY, ST_EXIT_DOMAIN, ST_NO_EXIT, ST_STEP_CAP, ST_INVALID_RELEASE = range(8)
+FACE_NONE = 255
+DEFAULT_MAX_STEPS = 1_000_000
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, no FMA contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Field(ctypes.Structure):
+    _fields_ = [("nlay", ctypes.c_int32), ("nrow", ctypes.c_int32), ("ncol", ctypes.c_int32),
+                ("delr", ctypes.c_void_p), ("delc", ctypes.c_void_p), ("dz", ctypes.c_void_p),
+                ("origin", ctypes.c_double * 3),
+                ("qx", ctypes.c_void_p), ("qy", ctypes.c_void_p), ("qz", ctypes.c_void_p),
+                ("porosity", ctypes.c_void_p), ("ibound", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
+                ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64)]
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in
+                ("cell", "px", "py", "pz", "gx", "gy", "gz", "t", "status", "steps", "exit_face", "hash",
+                 "ts_x", "ts_y", "ts_z", "ts_cell", "ts_status")]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp = ctypes.c_void_p
+            lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_exit_time.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_int)]
+            lib.orc_exit_time.restype = ctypes.c_double
+            lib.orc_move.argtypes = [ctypes.c_double] * 5
+            lib.orc_move.restype = ctypes.c_double
+            lib.orc_release_box.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp,
+                                            ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp, vp]
+            lib.orc_release_box.restype = ctypes.c_int
+            lib.orc_release_explicit.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_release_explicit.restype = ctypes.c_int
+            lib.orc_track.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
+                                      ctypes.POINTER(_Opts), ctypes.POINTER(_Out)]
+            lib.orc_track.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleField:
+    """Keeps contiguous float64 / int8 copies of a field and its C view."""
+
+    def __init__(self, f):
+        self.nlay, self.nrow, self.ncol = int(f.nlay), int(f.nrow), int(f.ncol)
+        c = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt).reshape(-1))
+        self.delr, self.delc, self.dz = c(f.delr, np.float64), c(f.delc, np.float64), c(f.dz, np.float64)
+        self.qx, self.qy, self.qz = c(f.qx, np.float64), c(f.qy, np.float64), c(f.qz, np.float64)
+        self.porosity = c(f.porosity, np.float64)
+        self.ibound = c(f.ibound, np.int8)
+        assert self.qx.size == self.nlay * self.nrow * (self.ncol + 1)
+        assert self.qy.size == self.nlay * (self.nrow + 1) * self.ncol
+        assert self.qz.size == (self.nlay + 1) * self.nrow * self.ncol
+        assert self.porosity.size == self.ibound.size == self.nlay * self.nrow * self.ncol
+        self.origin = tuple(float(o) for o in f.origin)
+        self.c = _Field(self.nlay, self.nrow, self.ncol, _ptr(self.delr), _ptr(self.delc), _ptr(self.dz),
+                        (ctypes.c_double * 3)(*self.origin), _ptr(self.qx), _ptr(self.qy), _ptr(self.qz),
+                        _ptr(self.porosity), _ptr(self.ibound))
+
+
+def as_oracle_field(f) -> OracleField:
+    return f if isinstance(f, OracleField) else OracleField(f)
+
+
+def philox4x32_10(ctr, key):
+    lib = _load()
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    o = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def exit_time(v1, v2, A, D, p):
+    """(t_exit, face) for one axis of one cell (face +1, -1 or 0 = none)."""
+    lib = _load()
+    face = ctypes.c_int(0)
+    t = lib.orc_exit_time(float(v1), float(v2), float(A), float(D), float(p), ctypes.byref(face))
+    return t, face.value
+
+
+def move(v1, A, D, p, dt):
+    return _load().orc_move(float(v1), float(A), float(D), float(p), float(dt))
+
+
+def release_box(f, n, lo, hi, seed, id_offset=0):
+    """Particles uniform in the box [lo, hi] via Philox4x32-10; returns a state dict."""
+    lib = _load()
+    of = as_oracle_field(f)
+    st = dict(cell=np.zeros(n, np.int32), px=np.zeros(n), py=np.zeros(n), pz=np.zeros(n),
+              status=np.zeros(n, np.uint8))
+    lo_a = np.asarray(lo, dtype=np.float64).copy()
+    hi_a = np.asarray(hi, dtype=np.float64).copy()
+    rc = lib.orc_release_box(ctypes.byref(of.c), int(n), _ptr(lo_a), _ptr(hi_a), int(seed) & (2**64 - 1),
+                             int(id_offset), _ptr(st["cell"]), _ptr(st["px"]), _ptr(st["py"]), _ptr(st["pz"]),
+                             _ptr(st["status"]))
+    if rc != 0:
+        raise RuntimeError("orc_release_box failed")
+    st["t"] = np.zeros(n)
+    return st
+
+
+def release_explicit(f, cells, frac):
+    lib = _load()
+    of = as_oracle_field(f)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    frac = np.ascontiguousarray(frac, dtype=np.float64).reshape(-1, 3)
+    n = cells.size
+    st = dict(cell=np.zeros(n, np.int32), px=np.zeros(n), py=np.zeros(n), pz=np.zeros(n),
+              status=np.zeros(n, np.uint8))
+    lib.orc_release_explicit(ctypes.byref(of.c), n, _ptr(cells), _ptr(frac), _ptr(st["cell"]),
+                             _ptr(st["px"]), _ptr(st["py"]), _ptr(st["pz"]), _ptr(st["status"]))
+    st["t"] = np.zeros(n)
+    return st
+
+
+def subset(state, idx):
+    return {k: np.ascontiguousarray(v[idx]) for k, v in state.items()}
+
+
+def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None):
+    """Track every particle of ``state`` (dict of cell, px, py, pz, t, status).
+
+    Returns a dict with the endpoint arrays (cell, px, py, pz, gx, gy, gz, t,
+    status, steps, exit_face, hash) and, when ``times`` is given, timeseries
+    arrays ts_x/ts_y/ts_z/ts_cell/ts_status of shape [n_times, n].
+    """
+    lib = _load()
+    of = as_oracle_field(f)
+    n = int(np.asarray(state["cell"]).size)
+    cell0 = np.ascontiguousarray(state["cell"], dtype=np.int32)
+    px0 = np.ascontiguousarray(state["px"], dtype=np.float64)
+    py0 = np.ascontiguousarray(state["py"], dtype=np.float64)
+    pz0 = np.ascontiguousarray(state["pz"], dtype=np.float64)
+    t0 = np.ascontiguousarray(state.get("t", np.zeros(n)), dtype=np.float64)
+    s0 = np.ascontiguousarray(state.get("status", np.zeros(n, np.uint8)), dtype=np.uint8)
+    res = dict(cell=np.zeros(n, np.int32), px=np.zeros(n), py=np.zeros(n), pz=np.zeros(n),
+               gx=np.zeros(n), gy=np.zeros(n), gz=np.zeros(n), t=np.zeros(n),
+               status=np.zeros(n, np.uint8), steps=np.zeros(n, np.uint32),
+               exit_face=np.zeros(n, np.uint8), hash=np.zeros(n, np.uint64))
+    nt = 0
+    tarr = None
+    if times is not None and (timeseries is None or timeseries):
+        tarr = np.ascontiguousarray(times, dtype=np.float64)
+        nt = tarr.size
+        for k in ("ts_x", "ts_y", "ts_z"):
+            res[k] = np.zeros((nt, n))
+        res["ts_cell"] = np.zeros((nt, n), np.int32)
+        res["ts_status"] = np.zeros((nt, n), np.uint8)
+    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps))
+    out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_])
+    rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
+                       _ptr(s0), ctypes.byref(opts), ctypes.byref(out))
+    if rc != 0:
+        raise RuntimeError("orc_track failed")
+    return res
+
+
+def track_parallel(f, state, threads: int, chunk: int = 256, **kw):
+    """The oracle as it stands, run on ``threads`` host threads.
+
+    Particles are handed out in chunks from a shared counter (the "dynamic"
+    schedule); each chunk is one call of the single-threaded oracle (ctypes
+    releases the GIL during the call).  Results are identical to ``track``.
+    """
+    n = int(np.asarray(state["cell"]).size)
+    of = as_oracle_field(f)
+    parts = {}
+    nxt = [0]
+    lk = threading.Lock()
+
+    def worker():
+        while True:
+            with lk:
+                s = nxt[0]
+                nxt[0] += chunk
+            if s >= n:
+                return
+            idx = slice(s, min(n, s + chunk))
+            parts[s] = track(of, {k: v[idx] for k, v in state.items()}, **kw)
+
+    ths = [threading.Thread(target=worker) for _ in range(max(1, threads))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    keys = sorted(parts)
+    out = {}
+    for name in parts[keys[0]]:
+        ax = 1 if name.startswith("ts_") else 0
+        out[name] = np.concatenate([parts[s][name] for s in keys], axis=ax)
+    return out

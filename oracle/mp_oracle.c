@@ -1,0 +1,397 @@
+/*
+ * mp_oracle.c - CPU oracle for semi-analytical particle tracking.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code with the CUDA path and is deliberately plain: one particle at a time,
+ * one cell at a time, IEEE double precision, no FMA contraction
+ * (-ffp-contract=off), no vectorisation.
+ *
+ * What it computes.  The paper (Introduction; Methods, "MODPATH") moves each
+ * particle independently with the semi-analytical solution of Pollock (1988):
+ * one displacement takes the particle from its position to a face of the
+ * current cell, after which it is handed to the neighbour across that face,
+ * until a stopping condition holds (a boundary face, the maximum tracking time,
+ * a sink cell).  The Pollock solution inside one cell, per axis a:
+ *
+ *   face velocities   v1 = Q1 / (n * area_a),  v2 = Q2 / (n * area_a)
+ *   gradient          A  = (v2 - v1) / D_a            (D_a = cell size)
+ *   velocity at p     vp = v1 + A * p                 (p = offset from face 1)
+ *   motion            p(t) = p + vp * t * (e^{A t} - 1) / (A t)
+ *   exit time         t_a = ln(v_exit / vp) / A = (d / vp) * ln(1 + z) / z,
+ *                     d = signed distance to the exit face, z = A d / vp,
+ *                     and t_a = d / vp in the limit A -> 0 (z == 0).
+ *
+ * A face is reachable on an axis only if the particle velocity and the
+ * exit-face velocity point the same way (vp > 0 and v2 > 0 -> face 2;
+ * vp < 0 and v1 < 0 -> face 1).  The step time is the smallest reachable t_a
+ * (ties go to the lowest axis, x before y before z); the other axes move by
+ * the motion formula, the exit axis is set exactly on its face.
+ *
+ * Readings of points the paper leaves open (it defers the algorithm to
+ * Pollock 1988/2016):
+ *   - velocities use the cell's own porosity and the cell's own face area;
+ *   - z == 0 (and w == 0 in the motion factor) takes the exact limit 1;
+ *   - stop at t_stop if t + t_min >= t_stop: every axis moves by t_stop - t;
+ *   - no reachable face and t_stop infinite: status NO_EXIT;
+ *   - entering an inactive (ibound 0) or constant-head (ibound -1) cell ends
+ *     the path (BOUNDARY), entering a sink cell (ibound 2) ends it (SINK,
+ *     strong sink), leaving the grid ends it (EXIT_DOMAIN); in all three the
+ *     particle stays in its last cell, on the face it left through;
+ *   - a cell-step is one exit-time evaluation, including zero-length steps
+ *     and the final partial step; max_steps caps them (STEP_CAP);
+ *   - output times t_k are recorded in the step whose interval (t, t + dt]
+ *     holds them, with the motion formula at tau = t_k - t on every axis;
+ *     t_k at or before the start time records the release position, t_k
+ *     after termination records the final position with the final status.
+ *
+ * Axes: x along column j, y along row i, z along layer k (z grows with k).
+ * Offsets p are metres from the cell's low face on each axis.
+ */
+#include "mp_oracle.h"
+
+#include <math.h>
+#include <string.h>
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------- */
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo)
+{
+    uint64_t prod = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(prod >> 32);
+    *lo = (uint32_t)prod;
+}
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; round++) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(M0, c0, &hi0, &lo0);
+        mulhilo32(M1, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 53-bit uniform in [0, 1) from two 32-bit words */
+static double unit53(uint32_t a, uint32_t b)
+{
+    uint64_t v = (((uint64_t)a << 32) | (uint64_t)b) >> 11;
+    return (double)v * (1.0 / 9007199254740992.0);
+}
+
+/* ---- grid helpers ------------------------------------------------------ */
+
+static void face_coords(const double* sizes, int n, double origin, double* out /* n+1 */)
+{
+    out[0] = origin;
+    for (int a = 0; a < n; a++) out[a + 1] = out[a] + sizes[a];
+}
+
+/* largest index a in [0, n-1] with f[a] <= x (f has n+1 entries); -1 if x
+ * lies outside [f[0], f[n]] */
+static int locate(const double* f, int n, double x)
+{
+    if (!(x >= f[0]) || !(x <= f[n])) return -1;
+    int a = 0;
+    while (a + 1 < n && f[a + 1] <= x) a++;
+    return a;
+}
+
+static uint64_t fnv_step(uint64_t h, int32_t c)
+{
+    h ^= (uint64_t)(uint32_t)c;
+    h *= 0x100000001b3ULL;
+    return h;
+}
+
+/* ---- the Pollock pieces ---------------------------------------------- */
+
+double orc_exit_time(double v1, double v2, double A, double D, double p, int* face)
+{
+    double vp = v1 + A * p;
+    double d;
+    if (vp > 0.0 && v2 > 0.0) { *face = 1; d = D - p; }
+    else if (vp < 0.0 && v1 < 0.0) { *face = -1; d = -p; }
+    else { *face = 0; return INFINITY; }
+    double t1 = d / vp;
+    double z = A * t1;
+    if (z == 0.0) return t1;
+    return t1 * (log1p(z) / z);
+}
+
+double orc_move(double v1, double A, double D, double p, double dt)
+{
+    double vp = v1 + A * p;
+    double s = vp * dt;
+    if (s == 0.0) return p;
+    double w = A * dt;
+    double f = (w == 0.0) ? 1.0 : expm1(w) / w;
+    double pn = p + s * f;
+    if (pn < 0.0) pn = 0.0;
+    if (pn > D) pn = D;
+    return pn;
+}
+
+/* ---- cell data gathered at cell entry (the per-cell "initialisation") -- */
+
+typedef struct {
+    double v1[3], v2[3], A[3], D[3];
+} cellvel;
+
+static void cell_velocities(const orc_field* f, int k, int i, int j, cellvel* cv)
+{
+    const int nrow = f->nrow, ncol = f->ncol, nlay = f->nlay;
+    size_t c = ((size_t)k * nrow + i) * ncol + j;
+    double n = f->porosity[c];
+    double dx = f->delr[j], dy = f->delc[i], dzz = f->dz[k];
+    double ax = dy * dzz, ay = dx * dzz, az = dx * dy;
+    double qx1 = f->qx[((size_t)k * nrow + i) * (ncol + 1) + j];
+    double qx2 = f->qx[((size_t)k * nrow + i) * (ncol + 1) + j + 1];
+    double qy1 = f->qy[((size_t)k * (nrow + 1) + i) * ncol + j];
+    double qy2 = f->qy[((size_t)k * (nrow + 1) + i + 1) * ncol + j];
+    double qz1 = f->qz[((size_t)k * nrow + i) * ncol + j];
+    double qz2 = f->qz[((size_t)(k + 1) * nrow + i) * ncol + j];
+    (void)nlay;
+    cv->v1[0] = qx1 / (n * ax); cv->v2[0] = qx2 / (n * ax);
+    cv->v1[1] = qy1 / (n * ay); cv->v2[1] = qy2 / (n * ay);
+    cv->v1[2] = qz1 / (n * az); cv->v2[2] = qz2 / (n * az);
+    cv->D[0] = dx; cv->D[1] = dy; cv->D[2] = dzz;
+    for (int a = 0; a < 3; a++) cv->A[a] = (cv->v2[a] - cv->v1[a]) / cv->D[a];
+}
+
+/* ---- release ----------------------------------------------------------- */
+
+int orc_release_box(const orc_field* f, int64_t n, const double lo[3], const double hi[3],
+                    uint64_t seed, uint64_t id_offset,
+                    int32_t* cell, double* px, double* py, double* pz, uint8_t* status)
+{
+    const int nlay = f->nlay, nrow = f->nrow, ncol = f->ncol;
+    double xf[ORC_MAX_AXIS + 1], yf[ORC_MAX_AXIS + 1], zf[ORC_MAX_AXIS + 1];
+    if (ncol > ORC_MAX_AXIS || nrow > ORC_MAX_AXIS || nlay > ORC_MAX_AXIS) return -1;
+    face_coords(f->delr, ncol, f->origin[0], xf);
+    face_coords(f->delc, nrow, f->origin[1], yf);
+    face_coords(f->dz, nlay, f->origin[2], zf);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t q = 0; q < n; q++) {
+        uint64_t id = (uint64_t)q + id_offset;
+        uint32_t c0[4] = {(uint32_t)id, (uint32_t)(id >> 32), 0u, 0u};
+        uint32_t c1[4] = {(uint32_t)id, (uint32_t)(id >> 32), 1u, 0u};
+        uint32_t r[4], s[4];
+        orc_philox4x32_10(c0, key, r);
+        orc_philox4x32_10(c1, key, s);
+        double ux = unit53(r[0], r[1]), uy = unit53(r[2], r[3]), uz = unit53(s[0], s[1]);
+        double gx = lo[0] + ux * (hi[0] - lo[0]);
+        double gy = lo[1] + uy * (hi[1] - lo[1]);
+        double gz = lo[2] + uz * (hi[2] - lo[2]);
+        int j = locate(xf, ncol, gx), i = locate(yf, nrow, gy), k = locate(zf, nlay, gz);
+        if (j < 0 || i < 0 || k < 0) {
+            cell[q] = -1; px[q] = 0.0; py[q] = 0.0; pz[q] = 0.0;
+            status[q] = ORC_ST_INVALID_RELEASE;
+            continue;
+        }
+        double ox = gx - xf[j], oy = gy - yf[i], oz = gz - zf[k];
+        if (ox < 0.0) ox = 0.0;
+        if (ox > f->delr[j]) ox = f->delr[j];
+        if (oy < 0.0) oy = 0.0;
+        if (oy > f->delc[i]) oy = f->delc[i];
+        if (oz < 0.0) oz = 0.0;
+        if (oz > f->dz[k]) oz = f->dz[k];
+        int32_t c = (int32_t)(((int64_t)k * nrow + i) * ncol + j);
+        cell[q] = c; px[q] = ox; py[q] = oy; pz[q] = oz;
+        int8_t ib = f->ibound[c];
+        status[q] = (ib == 1) ? ORC_ST_ACTIVE : (ib == 2) ? ORC_ST_SINK : ORC_ST_INVALID_RELEASE;
+    }
+    return 0;
+}
+
+int orc_release_explicit(const orc_field* f, int64_t n, const int32_t* cell_in, const double* frac,
+                         int32_t* cell, double* px, double* py, double* pz, uint8_t* status)
+{
+    const int nlay = f->nlay, nrow = f->nrow, ncol = f->ncol;
+    const int64_t ncell = (int64_t)nlay * nrow * ncol;
+    for (int64_t q = 0; q < n; q++) {
+        int32_t c = cell_in[q];
+        if (c < 0 || c >= ncell) {
+            cell[q] = -1; px[q] = py[q] = pz[q] = 0.0; status[q] = ORC_ST_INVALID_RELEASE;
+            continue;
+        }
+        int j = c % ncol, i = (c / ncol) % nrow, k = c / (ncol * nrow);
+        double fx = frac[3 * q], fy = frac[3 * q + 1], fz = frac[3 * q + 2];
+        if (fx < 0.0) fx = 0.0;
+        if (fx > 1.0) fx = 1.0;
+        if (fy < 0.0) fy = 0.0;
+        if (fy > 1.0) fy = 1.0;
+        if (fz < 0.0) fz = 0.0;
+        if (fz > 1.0) fz = 1.0;
+        cell[q] = c;
+        px[q] = fx * f->delr[j]; py[q] = fy * f->delc[i]; pz[q] = fz * f->dz[k];
+        int8_t ib = f->ibound[c];
+        status[q] = (ib == 1) ? ORC_ST_ACTIVE : (ib == 2) ? ORC_ST_SINK : ORC_ST_INVALID_RELEASE;
+    }
+    return 0;
+}
+
+/* ---- tracking ------------------------------------------------------------ */
+
+static void write_record(const orc_track_out* o, int64_t n, int kk, int64_t q,
+                         double gx, double gy, double gz, int32_t cell, uint8_t st)
+{
+    size_t r = (size_t)kk * (size_t)n + (size_t)q;
+    o->ts_x[r] = gx; o->ts_y[r] = gy; o->ts_z[r] = gz;
+    o->ts_cell[r] = cell; o->ts_status[r] = st;
+}
+
+int orc_track(const orc_field* f, int64_t n,
+              const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+              const double* t0, const uint8_t* status0,
+              const orc_track_opts* opt, const orc_track_out* out)
+{
+    const int nlay = f->nlay, nrow = f->nrow, ncol = f->ncol;
+    double xf[ORC_MAX_AXIS + 1], yf[ORC_MAX_AXIS + 1], zf[ORC_MAX_AXIS + 1];
+    if (ncol > ORC_MAX_AXIS || nrow > ORC_MAX_AXIS || nlay > ORC_MAX_AXIS) return -1;
+    face_coords(f->delr, ncol, f->origin[0], xf);
+    face_coords(f->delc, nrow, f->origin[1], yf);
+    face_coords(f->dz, nlay, f->origin[2], zf);
+    const double t_stop = opt->t_stop;
+    const int nt = (opt->times && out->ts_x) ? opt->n_times : 0;
+    const int64_t max_steps = opt->max_steps > 0 ? opt->max_steps : ORC_DEFAULT_MAX_STEPS;
+
+    for (int64_t q = 0; q < n; q++) {
+        int32_t c = cell0[q];
+        uint8_t st = status0 ? status0[q] : ORC_ST_ACTIVE;
+        double p[3] = {px0[q], py0[q], pz0[q]};
+        double t = t0 ? t0[q] : 0.0;
+        int64_t steps = 0;
+        uint8_t exit_face = ORC_FACE_NONE;
+        uint64_t h = 0xcbf29ce484222325ULL;
+        int kn = 0;
+        int j = 0, i = 0, k = 0;
+        if (c >= 0) {
+            j = c % ncol; i = (c / ncol) % nrow; k = c / (ncol * nrow);
+            h = fnv_step(h, c);
+        } else {
+            st = ORC_ST_INVALID_RELEASE;
+        }
+        /* output times at or before the start: the release position */
+        while (kn < nt && opt->times[kn] <= t) {
+            if (c >= 0)
+                write_record(out, n, kn, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], c, st);
+            else
+                write_record(out, n, kn, q, NAN, NAN, NAN, -1, st);
+            kn++;
+        }
+        while (st == ORC_ST_ACTIVE) {
+            if (t >= t_stop) { st = ORC_ST_TIME; break; }
+            if (steps >= max_steps) { st = ORC_ST_STEP_CAP; break; }
+            cellvel cv;
+            cell_velocities(f, k, i, j, &cv);
+            int face[3];
+            double te[3];
+            for (int a = 0; a < 3; a++)
+                te[a] = orc_exit_time(cv.v1[a], cv.v2[a], cv.A[a], cv.D[a], p[a], &face[a]);
+            int ax = -1;
+            double tmin = INFINITY;
+            for (int a = 0; a < 3; a++)
+                if (face[a] != 0 && te[a] < tmin) { tmin = te[a]; ax = a; }
+            steps++;
+            if (ax < 0 && !(t_stop < INFINITY)) {
+                /* no reachable face and no stop time: the particle stays in
+                 * this cell; later output times still see it move inside */
+                while (kn < nt) {
+                    double tau = opt->times[kn] - t;
+                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
+                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
+                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                    write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_NO_EXIT);
+                    kn++;
+                }
+                st = ORC_ST_NO_EXIT;
+                break;
+            }
+            if (ax < 0 || t + tmin >= t_stop) {
+                double dt = t_stop - t;
+                while (kn < nt && opt->times[kn] <= t_stop) {
+                    double tau = opt->times[kn] - t;
+                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
+                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
+                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                    write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
+                    kn++;
+                }
+                for (int a = 0; a < 3; a++) p[a] = orc_move(cv.v1[a], cv.A[a], cv.D[a], p[a], dt);
+                t = t_stop;
+                st = ORC_ST_TIME;
+                break;
+            }
+            /* displacement to the exit face of axis ax */
+            double dt = tmin;
+            double t_end = t + dt;
+            while (kn < nt && opt->times[kn] <= t_end) {
+                double tau = opt->times[kn] - t;
+                double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
+                double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
+                double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
+                kn++;
+            }
+            for (int a = 0; a < 3; a++) {
+                if (a == ax) p[a] = (face[a] > 0) ? cv.D[a] : 0.0;
+                else p[a] = orc_move(cv.v1[a], cv.A[a], cv.D[a], p[a], dt);
+            }
+            t = t_end;
+            exit_face = (uint8_t)(2 * ax + (face[ax] > 0 ? 1 : 0));
+            /* hand over to the neighbour across the exit face */
+            int nj = j, ni = i, nk = k;
+            if (ax == 0) nj += face[0];
+            else if (ax == 1) ni += face[1];
+            else nk += face[2];
+            if (nj < 0 || nj >= ncol || ni < 0 || ni >= nrow || nk < 0 || nk >= nlay) {
+                st = ORC_ST_EXIT_DOMAIN;
+                break;
+            }
+            int32_t nc = (int32_t)(((int64_t)nk * nrow + ni) * ncol + nj);
+            int8_t ib = f->ibound[nc];
+            if (ib == 0 || ib == -1) { st = ORC_ST_BOUNDARY; break; }
+            if (ib == 2) { st = ORC_ST_SINK; break; }
+            j = nj; i = ni; k = nk; c = nc;
+            if (face[ax] > 0) p[ax] = 0.0;
+            else p[ax] = (ax == 0) ? f->delr[j] : (ax == 1) ? f->delc[i] : f->dz[k];
+            h = fnv_step(h, c);
+        }
+        /* output times after termination: the final position */
+        while (kn < nt) {
+            if (c >= 0)
+                write_record(out, n, kn, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], c, st);
+            else
+                write_record(out, n, kn, q, NAN, NAN, NAN, -1, st);
+            kn++;
+        }
+        if (out->cell) out->cell[q] = c;
+        if (out->px) {
+            out->px[q] = p[0]; out->py[q] = p[1]; out->pz[q] = p[2];
+        }
+        if (out->gx) {
+            if (c >= 0) {
+                out->gx[q] = xf[j] + p[0]; out->gy[q] = yf[i] + p[1]; out->gz[q] = zf[k] + p[2];
+            } else {
+                out->gx[q] = NAN; out->gy[q] = NAN; out->gz[q] = NAN;
+            }
+        }
+        if (out->t) out->t[q] = t;
+        if (out->status) out->status[q] = st;
+        if (out->steps) out->steps[q] = (uint32_t)steps;
+        if (out->exit_face) out->exit_face[q] = exit_face;
+        if (out->hash) out->hash[q] = h;
+    }
+    return 0;
+}

@@ -1,0 +1,66 @@
+/*
+ * mp_oracle.h - CPU oracle for semi-analytical (Pollock 1988) particle
+ * tracking on structured grids.  TEST INFRASTRUCTURE ONLY: used by the tests,
+ * the smoke check and the benchmark's CPU-baseline leg, never by the product
+ * path.  Plain single-threaded IEEE double precision.
+ */
+#ifndef MP_ORACLE_H
+#define MP_ORACLE_H
+#include <stdint.h>
+#include <stddef.h>
+
+#define ORC_MAX_AXIS 8192
+#define ORC_DEFAULT_MAX_STEPS 1000000
+
+/* particle status */
+#define ORC_ST_ACTIVE 0
+#define ORC_ST_TIME 1
+#define ORC_ST_SINK 2
+#define ORC_ST_BOUNDARY 3
+#define ORC_ST_EXIT_DOMAIN 4
+#define ORC_ST_NO_EXIT 5
+#define ORC_ST_STEP_CAP 6
+#define ORC_ST_INVALID_RELEASE 7
+
+#define ORC_FACE_NONE 255
+
+typedef struct {
+    int32_t nlay, nrow, ncol;
+    const double* delr;   /* [ncol] */
+    const double* delc;   /* [nrow] */
+    const double* dz;     /* [nlay] */
+    double origin[3];
+    const double* qx;     /* [nlay][nrow][ncol+1] */
+    const double* qy;     /* [nlay][nrow+1][ncol] */
+    const double* qz;     /* [nlay+1][nrow][ncol] */
+    const double* porosity; /* [nlay][nrow][ncol] */
+    const int8_t* ibound;   /* [nlay][nrow][ncol] */
+} orc_field;
+
+typedef struct {
+    double t_stop;        /* +inf allowed */
+    int32_t n_times;
+    const double* times;  /* ascending */
+    int64_t max_steps;    /* <= 0: default */
+} orc_track_opts;
+
+typedef struct {
+    int32_t* cell; double *px, *py, *pz; double *gx, *gy, *gz; double* t;
+    uint8_t* status; uint32_t* steps; uint8_t* exit_face; uint64_t* hash;
+    /* timeseries [n_times][n]; ts_x == NULL disables */
+    double *ts_x, *ts_y, *ts_z; int32_t* ts_cell; uint8_t* ts_status;
+} orc_track_out;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_exit_time(double v1, double v2, double A, double D, double p, int* face);
+double orc_move(double v1, double A, double D, double p, double dt);
+int orc_release_box(const orc_field* f, int64_t n, const double lo[3], const double hi[3],
+                    uint64_t seed, uint64_t id_offset,
+                    int32_t* cell, double* px, double* py, double* pz, uint8_t* status);
+int orc_release_explicit(const orc_field* f, int64_t n, const int32_t* cell_in, const double* frac,
+                         int32_t* cell, double* px, double* py, double* pz, uint8_t* status);
+int orc_track(const orc_field* f, int64_t n,
+              const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+              const double* t0, const uint8_t* status0,
+              const orc_track_opts* opt, const orc_track_out* out);
+#endif
