@@ -73,7 +73,6 @@ def test_uniform_flow_stop_time_position():
     f = H.uniform_x_field(1, 1, 6, seed=3)
     st = O.release_explicit(f, np.array([0], np.int32), np.array([[0.0, 0.5, 0.5]]))
     v = [f.qx[0, 0, 0] / (f.porosity[0, 0, j] * f.delc[0] * f.dz[0]) for j in range(6)]
-    T = 0.5 * f.delr[0] / v[0] + 0.25 * f.delr[1] / v[1] + f.delr[0] / v[0] * 0.5
     # time T: cell 0 fully (delr0/v0), then 0.25 of cell 1
     T = f.delr[0] / v[0] + 0.25 * f.delr[1] / v[1]
     r = O.track(f, st, t_stop=T)
@@ -214,3 +213,18 @@ def test_release_box_locates_cells():
     # the stream is keyed by (seed, particle index): an offset shifts it
     st2 = O.release_box(f, 100, (0.0, 0.0, 0.0), (Lx, Ly, Lz), seed=1234, id_offset=400)
     assert np.array_equal(st2["cell"], st["cell"][400:]) and np.array_equal(st2["px"], st["px"][400:])
+
+
+def test_exact_tie_goes_to_lowest_axis():
+    """Equal exit times on x and y (a reading: the lowest axis wins, and only
+    that face is crossed); the y coordinate lands on its face by the motion
+    formula and leaves on the next step with a zero-length step."""
+    por, D = 0.5, (2.0, 2.0, 1.0)
+    qx = 1.0 * por * D[1] * D[2]
+    qy = 1.0 * por * D[0] * D[2]
+    f = H.single_cell_field(qx, qx, qy, qy, d=D, por=por)
+    st = O.release_explicit(f, np.array([0], np.int32), np.array([[0.25, 0.25, 0.5]]))
+    r = O.track(f, st)
+    assert r["exit_face"][0] == 1          # +x, not +y
+    assert r["t"][0] == 1.5
+    assert r["px"][0] == 2.0 and r["py"][0] == 2.0
