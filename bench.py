@@ -1,0 +1,366 @@
+"""Benchmark: Pollock cell-steps/s on the 200x200x20 heterogeneous field.
+
+Workload (one "step"): release 1e6 particles uniformly on the west face of
+column 1 (Philox, on the device) and track every one of them to termination
+with endpoint records plus timeseries records at 50 log-spaced times, on the
+200x200x20 field of 5x5x1 m cells with ln K ~ N(-9.2, 1), exponential
+covariance (10, 10, 2) cells, porosity 0.3, constant heads west/east.  The
+headline value is the FP64 path; the mixed-precision path (FP32 in-cell,
+FP64 time and position) is timed beside it on the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank tracks its own 1e6
+particles (disjoint Philox counters) against its own copy of the field:
+weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Pollock cell-steps/s (FP32+FP64-time vs FP64) at 1 GB300; request p50/p99 ms"
+UNIT = "cell-steps/s"
+WORKLOAD = ("200x200x20 cells (5x5x1 m), lnK N(-9.2,1) exp. cov. (10,10,2) cells, porosity 0.3, CH west/east, "
+            "PCG head solve; 1e6 particles on the west face of column 1; endpoint + timeseries at 50 log times")
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, seconds: float = 10.0, threads: int = 0):
+    """The oracle as it stands on the host cores: particles handed out in
+    chunks to `threads` threads until `seconds` have passed."""
+    import oracle as O
+    threads = threads or os.cpu_count() or 1
+    n = w.release.n
+    state = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
+    of = O.as_oracle_field(w.field)
+    perm = np.random.default_rng(0).permutation(n)
+    chunk = 512
+    lock = threading.Lock()
+    nxt = [0]
+    done = {"steps": 0, "particles": 0}
+    t_end = time.perf_counter() + seconds
+
+    def worker():
+        while time.perf_counter() < t_end:
+            with lock:
+                s = nxt[0]
+                nxt[0] += chunk
+            if s >= n:
+                return
+            idx = perm[s:s + chunk]
+            r = O.track(of, O.subset(state, idx), times=w.times)
+            with lock:
+                done["steps"] += int(r["steps"].astype(np.int64).sum())
+                done["particles"] += idx.size
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    el = time.perf_counter() - t0
+    return {"value": done["steps"] / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done['particles']} of the 1e6 particles (random subset), endpoint + 50 output times, "
+                      f"{el:.1f} s wall on {threads} host threads",
+            "particles_per_s": done["particles"] / el}
+
+
+def run_reference(args):
+    """The oracle (plain single-threaded C per call) on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2302_13590_gb300 import inputs as I
+    w = I.workload("cfg2")
+    for _ in range(args.warmup):
+        cpu_baseline(w, seconds=1.0)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, seconds=args.ref_seconds))
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": args.ref_seconds * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {**vals[-1], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_13590_gb300 import inputs as I
+    from paper_2302_13590_gb300 import mp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = I.workload("cfg2")
+    rel = I.Release(w.release.n, w.release.lo, w.release.hi, w.release.seed, id_offset=rank * w.release.n)
+    n = rel.n
+    nt = len(w.times)
+    ctx = mp.Context(local)
+    fh = ctx.field(w.field)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def maxed(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def summed(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def one_step(prec, sched):
+        gh = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset,
+                                 stream=stream)
+        opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=prec, schedule=sched,
+                            times=w.times, block=args.block, steps_per_fetch=args.spf)
+        rid = mp.mp_track(ctx.h, gh, opts, stream)
+        return gh, rid
+
+    def timed(prec, sched, steps, warmup):
+        for _ in range(warmup):
+            gh, rid = one_step(prec, sched)
+            mp.mp_wait(ctx.h, rid)
+            mp.mp_req_free(ctx.h, rid)
+            mp.mp_group_free(gh)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        live = []
+        clk = ClockSampler(local)
+        clk.start()
+        t_wall = time.perf_counter()
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            evs[k][0].record(stream)
+            live.append(one_step(prec, sched))
+            evs[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t_wall
+        clocks = clk.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        cell_steps = 0
+        kern_ms = []
+        counts = np.zeros(8, np.int64)
+        for gh, rid in live:
+            st = mp.mp_get_stats(ctx.h, rid)
+            assert st["device_error"] == 0
+            cell_steps += st["cell_steps"]
+            kern_ms.append(st["kernel_ms"])
+            counts += np.array(st["n_status"])
+            mp.mp_req_free(ctx.h, rid)
+            mp.mp_group_free(gh)
+        return {"ms": ms, "wall_s": wall, "cell_steps": cell_steps, "kernel_ms": kern_ms, "clocks": clocks,
+                "status_counts": counts.tolist()}
+
+    results = {}
+    for name, prec in (("fp64", mp.PREC_FP64), ("mixed", mp.PREC_MIXED)):
+        r = timed(prec, args.schedule, args.steps, args.warmup)
+        ms_max = maxed(r["ms"])
+        steps_all = summed(r["cell_steps"])
+        results[name] = dict(r, ms_max=ms_max, cell_steps_all=steps_all,
+                             value=steps_all / (ms_max / 1e3),
+                             particles_per_s=summed(n * args.steps) / (ms_max / 1e3))
+
+    # end to end through the C ABI with host buffers: pinned host release
+    # arrays in, endpoint and timeseries records out, every step
+    e2e = None
+    if not args.no_e2e:
+        rng = np.random.default_rng(7)
+        s0 = results  # noqa: F841
+        ep_host = {k: torch.empty(n, dtype=getattr(torch, np.dtype(dt).name), pin_memory=True).numpy()
+                   for k, dt in mp.ENDPOINT_DTYPES.items() if k != "hash"}
+        ep_host["hash"] = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        ts_host = torch.empty(nt * n * 32, dtype=torch.uint8, pin_memory=True).numpy().view(mp.TS_RECORD).reshape(nt, n)
+        # explicit release arrays = the device release of this step's particles
+        gh0 = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset)
+        r0 = ctx.track(gh0, t_stop=0.0, schedule=mp.SCHED_STATIC)
+        ep0 = r0.endpoints()
+        r0.free()
+        mp.mp_group_free(gh0)
+        cells_h = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+        local_h = torch.empty(3 * n, dtype=torch.float64, pin_memory=True).numpy()
+        cells_h[:] = ep0["cell"]
+        c = ep0["cell"]
+        j, i, k = c % w.field.ncol, (c // w.field.ncol) % w.field.nrow, c // (w.field.ncol * w.field.nrow)
+        local_h[0::3] = ep0["px"] / w.field.delr[j]
+        local_h[1::3] = ep0["py"] / w.field.delc[i]
+        local_h[2::3] = ep0["pz"] / w.field.dz[k]
+        h2d = cells_h.nbytes + local_h.nbytes
+        d2h = sum(a.nbytes for a in ep_host.values()) + ts_host.nbytes
+        e2e_vals = {}
+        for name, prec in (("fp64", mp.PREC_FP64), ("mixed", mp.PREC_MIXED)):
+            tot_steps = 0
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                gh = mp.mp_release_group(ctx.h, fh, cell=cells_h, local=local_h, stream=stream)
+                opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=prec,
+                                    schedule=args.schedule, times=w.times)
+                rid = mp.mp_track(ctx.h, gh, opts, stream)
+                mp.mp_get_endpoints(ctx.h, rid, n, out=ep_host)
+                mp.mp_get_timeseries(ctx.h, rid, n, nt, out=ts_host)
+                tot_steps += mp.mp_get_stats(ctx.h, rid)["cell_steps"]
+                mp.mp_req_free(ctx.h, rid)
+                mp.mp_group_free(gh)
+            barrier()
+            el = maxed(time.perf_counter() - t0)
+            e2e_vals[name] = summed(tot_steps) / el
+        e2e = {"value": e2e_vals["fp64"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "mixed": e2e_vals["mixed"]}
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, src = _peaks()
+    rf = {}
+    for name in ("fp64", "mixed"):
+        r = results[name]
+        kms = float(np.mean(r["kernel_ms"]))
+        steps_per_launch = r["cell_steps"] / len(r["kernel_ms"])
+        bpu = 57.0 if name == "fp64" else 29.0
+        achieved = bpu * steps_per_launch / (kms / 1e3) / 1e9
+        rf[name] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "peak_source": f"{src} hbm_gbs", "kernel_ms": kms,
+                    "bytes_per_cell_step": bpu, "cell_steps_per_launch": steps_per_launch}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(w, seconds=args.cpu_seconds)
+    f64 = results["fp64"]
+    line = {
+        "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": f64["ms_max"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "output_times": nt,
+                   "schedule": "dynamic" if args.schedule == mp.SCHED_DYNAMIC else "static",
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "particles_per_s": f64["particles_per_s"],
+        "roofline": rf["fp64"],
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps * 2,
+        "clocks": f64["clocks"],
+        "mixed": {"value": results["mixed"]["value"], "ms_per_step": results["mixed"]["ms_max"] / args.steps,
+                  "particles_per_s": results["mixed"]["particles_per_s"], "dtype": "f32+f64",
+                  "roofline": rf["mixed"], "clocks": results["mixed"]["clocks"]},
+        "status_counts": f64["status_counts"],
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schedule", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--spf", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * mp.h - C ABI of libmp: semi-analytical particle tracking (Pollock 1988)
+ * through a steady, structured, MODFLOW-style flow field on one GPU.
+ *
+ * The operation is the particle loop of the paper (Methods, "MODPATH" and
+ * Fig. 1): every particle is moved independently, one displacement per cell,
+ * from its position to a face of the current cell and across it into the
+ * neighbour, until a stopping condition holds (a boundary face, the maximum
+ * tracking time, a sink cell; Methods, "MODPATH").  Endpoint and timeseries
+ * outputs follow the paper's simulation types (Methods, "MODPATH").
+ *
+ * Conventions used by every call:
+ *   - grid nlay x nrow x ncol, cell (k, i, j), linear index
+ *     c = (k * nrow + i) * ncol + j;
+ *   - x runs along column j, y along row i, z along layer k (z grows with k);
+ *   - face flows are signed positive in the +axis direction:
+ *     qx[k][i][j] (j = 0..ncol) is the flow through the west face of column j,
+ *     qy[k][i][j] (i = 0..nrow), qz[k][i][j] (k = 0..nlay); units m^3/s;
+ *   - ibound: 0 inactive, 1 active, -1 constant head, 2 strong sink;
+ *   - global positions are metres from origin + cumulative cell sizes.
+ *
+ * Ownership: the library owns every device buffer it allocates (fields,
+ * groups, request outputs) and frees it in the matching *_free call.  Callers
+ * own every host buffer they pass; inputs are copied during the call unless
+ * MP_DEVICE_PTR says they are device pointers, which are then read during the
+ * call only (field load, release) and never retained.
+ *
+ * Errors: every call returns MP_OK (0) or a negative MP_ERR_* code and leaves
+ * its out-parameters untouched on error; mp_last_error() returns a message for
+ * the calling thread's last failure.  No call aborts the process and no
+ * device wait is unbounded.
+ *
+ * Threads: calls on one context are serialised internally; handles may be
+ * used from any thread.
+ */
+#ifndef MP_H
+#define MP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define MP_OK 0
+#define MP_ERR_INVALID_ARG -1  /* null pointer, bad enum, bad size            */
+#define MP_ERR_SHAPE -2        /* grid dimensions / array sizes inconsistent  */
+#define MP_ERR_NONFINITE -3    /* NaN/Inf flow, porosity <= 0 in active cell */
+#define MP_ERR_OOM -4          /* device allocation failed                    */
+#define MP_ERR_BUSY -5         /* request still running (try again)          */
+#define MP_ERR_TIMEOUT -6      /* mp_wait timed out; the request continues    */
+#define MP_ERR_CUDA -7         /* a CUDA runtime call failed                  */
+#define MP_ERR_NOT_READY -8    /* unknown or freed request id                 */
+#define MP_ERR_DEVICE -9       /* a kernel raised its error flag (bad index)  */
+
+/* ---- particle status (endpoint and timeseries records) -------------------- */
+#define MP_ST_ACTIVE 0          /* still moving (timeseries rows only)        */
+#define MP_ST_TIME 1            /* reached t_stop inside a cell               */
+#define MP_ST_SINK 2            /* entered (or released in) a strong sink     */
+#define MP_ST_BOUNDARY 3        /* next cell inactive or constant head        */
+#define MP_ST_EXIT_DOMAIN 4     /* left the grid through an outer face        */
+#define MP_ST_NO_EXIT 5         /* no reachable face and t_stop infinite      */
+#define MP_ST_STEP_CAP 6        /* max_steps cell-steps taken                 */
+#define MP_ST_INVALID_RELEASE 7 /* released outside the grid / in CH/inactive */
+#define MP_N_STATUS 8
+
+#define MP_FACE_NONE 255 /* exit_face: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+ */
+
+/* ---- enums and flags ------------------------------------------------------ */
+#define MP_DEVICE_PTR 1u        /* array arguments are device pointers       */
+
+#define MP_PREC_FP64 0          /* IEEE double throughout                     */
+#define MP_PREC_MIXED 1         /* FP32 in-cell coordinates and velocities,
+                                   FP64 travel time and global position      */
+
+#define MP_MODE_ENDPOINT 1      /* bit: endpoint record per particle          */
+#define MP_MODE_TIMESERIES 2    /* bit: a record per output time per particle */
+
+#define MP_SCHED_STATIC 0       /* one thread per particle, plain grid        */
+#define MP_SCHED_DYNAMIC 1      /* persistent warps refilled from a queue     */
+
+#define MP_TRACK_UPDATE_GROUP 1u /* write final state back into the group     */
+
+#define MP_RELEASE_EXPLICIT 0
+#define MP_RELEASE_BOX 1
+
+typedef struct mp_ctx mp_ctx;
+typedef struct mp_field mp_field;
+typedef struct mp_group mp_group;
+typedef int64_t mp_req;
+
+/* Flow field.  delr/delc/dz are always host arrays; qx..ibound are host
+ * arrays unless flags has MP_DEVICE_PTR.  Sizes: qx nlay*nrow*(ncol+1),
+ * qy nlay*(nrow+1)*ncol, qz (nlay+1)*nrow*ncol, porosity and ibound
+ * nlay*nrow*ncol (row-major as in the linear cell index). */
+typedef struct {
+    int32_t nlay, nrow, ncol;
+    const double* delr;      /* [ncol] cell widths along x (m), > 0   */
+    const double* delc;      /* [nrow] cell widths along y (m), > 0   */
+    const double* dz;        /* [nlay] cell thickness along z (m), > 0 */
+    double origin[3];        /* global coordinates of face (0,0,0)    */
+    const double* qx;
+    const double* qy;
+    const double* qz;
+    const double* porosity;  /* (0, 1] in active and sink cells       */
+    const int8_t* ibound;
+    uint32_t flags;          /* MP_DEVICE_PTR                          */
+} mp_field_desc;
+
+/* Particle release.  kind MP_RELEASE_EXPLICIT: cell[n] linear indices and
+ * local[n][3] fractions in [0,1] of the cell size per axis (clamped), t0[n]
+ * start times or NULL for 0.  kind MP_RELEASE_BOX: n positions uniform in the
+ * box [lo, hi] (global m; lo == hi on an axis gives a plane), drawn with
+ * Philox4x32-10 keyed by seed, particle q using counter (q + id_offset, 0|1);
+ * start time 0.  A particle released outside the grid or in an inactive or
+ * constant-head cell gets status MP_ST_INVALID_RELEASE, one released in a
+ * sink cell MP_ST_SINK; both take no steps. */
+typedef struct {
+    int64_t n;
+    int32_t kind;
+    uint32_t flags;          /* MP_DEVICE_PTR for cell/local/t0 */
+    const int32_t* cell;
+    const double* local;
+    const double* t0;
+    double lo[3], hi[3];
+    uint64_t seed, id_offset;
+} mp_release_desc;
+
+/* Tracking options.  times[n_times] ascending (host); t_stop may be +inf
+ * (endpoint mode then runs until every particle terminates or hits
+ * max_steps).  block / steps_per_fetch: 0 picks the tuned default. */
+typedef struct {
+    int32_t mode;            /* MP_MODE_* bits                  */
+    int32_t precision;       /* MP_PREC_*                       */
+    int32_t schedule;        /* MP_SCHED_*                      */
+    int32_t n_times;
+    const double* times;
+    double t_stop;
+    int64_t max_steps;       /* <= 0: 1,000,000                 */
+    int32_t block;           /* threads per block, 0 = auto     */
+    int32_t steps_per_fetch; /* dynamic schedule, 0 = auto      */
+    uint32_t flags;          /* MP_TRACK_UPDATE_GROUP           */
+} mp_track_opts;
+
+/* Endpoint arrays (SoA, particle order).  Any pointer may be NULL to skip
+ * that array.  cell is the last cell the particle was tracked in; for
+ * SINK/BOUNDARY/EXIT_DOMAIN it sits on the face exit_face of that cell.
+ * px/py/pz are offsets (m) from the cell's low faces; x/y/z global (m).
+ * hash is FNV-1a (64-bit, over the 32-bit cell indices) of the sequence of
+ * cells tracked in, release cell first. */
+typedef struct {
+    int32_t* cell;
+    double *x, *y, *z;
+    double *px, *py, *pz;
+    double* t;
+    uint8_t* status;
+    uint32_t* steps;
+    uint8_t* exit_face;
+    uint64_t* hash;
+} mp_endpoints;
+
+/* One timeseries record; the output is [n_times][n] records, 32 bytes each.
+ * status MP_ST_ACTIVE while moving; after termination the record holds the
+ * final position and the final status. */
+typedef struct {
+    double x, y, z;
+    int32_t cell;
+    uint8_t status;
+    uint8_t pad[3];
+} mp_ts_record;
+
+typedef struct {
+    uint64_t cell_steps;             /* sum of per-particle cell-steps   */
+    uint64_t n_status[MP_N_STATUS];  /* particles per final status       */
+    float kernel_ms;                 /* device time of the tracking kernel */
+    int32_t device_error;            /* kernel error flag (0 = none)     */
+} mp_stats;
+
+/* Context on one CUDA device.  The device is made current on the calling
+ * thread.  Errors: MP_ERR_INVALID_ARG, MP_ERR_CUDA. */
+int mp_ctx_create(int device, mp_ctx** out);
+/* Frees every field, group and request still owned by the context. */
+int mp_ctx_destroy(mp_ctx* ctx);
+
+/* Message for this thread's last failed call ("" if none). */
+const char* mp_last_error(void);
+
+/* Copy (or read, MP_DEVICE_PTR) a flow field and build its device form:
+ * per-cell velocity records in FP64 and FP32 (the paper's central flow-data
+ * object, Methods, "Multiprocessing"), neighbour classes and face
+ * coordinates.  Validates shapes, finiteness and porosity.  Synchronous.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_NONFINITE, MP_ERR_OOM,
+ * MP_ERR_CUDA. */
+int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out);
+int mp_field_free(mp_field* f);
+/* Device bytes held by a loaded field. */
+int mp_field_bytes(const mp_field* f, size_t* bytes);
+
+/* Create a particle group on the field (state resident on the device).
+ * Runs on `stream` (a cudaStream_t, NULL = legacy default) and returns when
+ * the release is enqueued; the state is ready in stream order.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, void* stream,
+                     mp_group** out);
+int mp_group_free(mp_group* g);
+int mp_group_size(const mp_group* g, int64_t* n);
+
+/* Track a group (Methods, "MODPATH": the particle loop) asynchronously on
+ * `stream`.  Allocates the request's outputs (stream-ordered) and enqueues
+ * the tracking kernel; returns the request id at once.  The group is read,
+ * not changed, unless o->flags has MP_TRACK_UPDATE_GROUP (resume: the
+ * group's state becomes the final state, terminated particles keep their
+ * status).  Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out);
+
+/* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
+ * wait is always bounded, and a negative value means 60 s) for a request.
+ * Errors: MP_ERR_TIMEOUT (still running), MP_ERR_NOT_READY (unknown id),
+ * MP_ERR_DEVICE (kernel error flag), MP_ERR_CUDA. */
+int mp_wait(mp_ctx* ctx, mp_req r, int64_t timeout_us);
+
+/* 1 if the request's work has finished, 0 if not; negative on error. */
+int mp_query(mp_ctx* ctx, mp_req r);
+
+/* Copy endpoint arrays out.  flags & MP_DEVICE_PTR: destinations are device
+ * pointers, copies are enqueued on `stream` after the request and the call
+ * returns at once; otherwise destinations are host memory and the call
+ * waits (bounded, 60 s) for the request and the copies.
+ * Errors: MP_ERR_NOT_READY, MP_ERR_TIMEOUT, MP_ERR_CUDA. */
+int mp_get_endpoints(mp_ctx* ctx, mp_req r, const mp_endpoints* out, uint32_t flags, void* stream);
+
+/* Copy the [n_times][n] timeseries records out (same rules as endpoints).
+ * Errors: MP_ERR_INVALID_ARG (request has no timeseries), as above. */
+int mp_get_timeseries(mp_ctx* ctx, mp_req r, mp_ts_record* out, uint32_t flags, void* stream);
+
+/* Device views of the request's own output buffers (valid until
+ * mp_req_free); any out-pointer may be NULL. */
+int mp_endpoints_device(mp_ctx* ctx, mp_req r, mp_endpoints* out, mp_ts_record** ts);
+
+/* Counters of a finished request (waits, bounded, like mp_get_endpoints). */
+int mp_get_stats(mp_ctx* ctx, mp_req r, mp_stats* out);
+
+/* Release a request's outputs (stream-ordered after its work). */
+int mp_req_free(mp_ctx* ctx, mp_req r);
+
+/* Device bytes mp_track allocates for n particles under options o. */
+int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes);
+
+/* Number of CUDA kernel launches mp_track issues for these options. */
+int mp_track_launches(const mp_track_opts* o, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MP_H */

@@ -1,0 +1,732 @@
+// mp_api.cu - host side of the libmp C ABI (declared in include/mp.h).
+//
+// The library holds the flow field once on the device (the paper's central
+// flow-data object reached through a pointer instead of per-thread copies;
+// Methods, "Multiprocessing") and runs the particle loop as CUDA kernels.
+// Request outputs come from the stream-ordered allocator so that many
+// requests can be admitted, run and released without device-wide syncs.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mp_internal.h"
+
+using namespace mp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return MP_ERR_CUDA;
+}
+
+#define MP_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Wait for an event with a bound; returns MP_OK, MP_ERR_TIMEOUT or MP_ERR_CUDA.
+int wait_event(cudaEvent_t ev, int64_t timeout_us)
+{
+    if (timeout_us < 0) timeout_us = 60LL * 1000 * 1000;
+    const auto t0 = std::chrono::steady_clock::now();
+    int64_t sleep_us = 2;
+    while (true) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return MP_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+        const int64_t el = std::chrono::duration_cast<std::chrono::microseconds>(
+                               std::chrono::steady_clock::now() - t0).count();
+        if (el >= timeout_us) return fail(MP_ERR_TIMEOUT, "request still running after the wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(std::min<int64_t>(sleep_us, timeout_us - el)));
+        sleep_us = std::min<int64_t>(sleep_us * 2, 200);
+    }
+}
+
+}  // namespace
+
+struct mp_field {
+    mp_ctx* ctx = nullptr;
+    DevField d{};
+    void* buf = nullptr;   // one allocation for all device arrays
+    size_t bytes = 0;
+};
+
+struct mp_group {
+    mp_ctx* ctx = nullptr;
+    const mp_field* field = nullptr;
+    DevState d{};
+    void* buf = nullptr;
+    long long n = 0;
+    cudaStream_t stream = nullptr;
+};
+
+struct Request {
+    mp_group* group = nullptr;
+    long long n = 0;
+    int n_times = 0;
+    int precision = 0;
+    DevOut d{};
+    void* buf = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;
+};
+
+struct mp_ctx {
+    int device = 0;
+    std::mutex mu;
+    std::map<int64_t, Request*> reqs;
+    std::set<mp_field*> fields;
+    std::set<mp_group*> groups;
+    int64_t next_id = 1;
+};
+
+namespace {
+
+// Wait (bounded) until no request of ctx still reads the given group/field.
+int drain_users(mp_ctx* ctx, const mp_group* g, const mp_field* f)
+{
+    std::vector<cudaEvent_t> evs;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto& kv : ctx->reqs) {
+            Request* r = kv.second;
+            if ((g && r->group == g) || (f && r->group && r->group->field == f)) evs.push_back(r->k1);
+        }
+    }
+    for (cudaEvent_t e : evs) {
+        int rc = wait_event(e, -1);
+        if (rc != MP_OK) return rc;
+    }
+    return MP_OK;
+}
+
+Request* find_req(mp_ctx* ctx, mp_req id)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->reqs.find(id);
+    return it == ctx->reqs.end() ? nullptr : it->second;
+}
+
+int read_counters(Request* r, unsigned long long* h)
+{
+    MP_CUDA(cudaMemcpy(h, r->d.counters, sizeof(unsigned long long) * N_COUNTERS, cudaMemcpyDeviceToHost),
+            "copy counters");
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mp_last_error(void) { return g_err.c_str(); }
+
+int mp_ctx_create(int device, mp_ctx** out)
+{
+    if (!out) return fail(MP_ERR_INVALID_ARG, "mp_ctx_create: out is NULL");
+    int ndev = 0;
+    MP_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(MP_ERR_INVALID_ARG, "mp_ctx_create: no such device");
+    MP_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    MP_CUDA(cudaFree(nullptr), "context init");
+    // keep freed request buffers in the stream-ordered pool for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    mp_ctx* c = new mp_ctx();
+    c->device = device;
+    *out = c;
+    return MP_OK;
+}
+
+int mp_ctx_destroy(mp_ctx* ctx)
+{
+    if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_ctx_destroy: NULL");
+    cudaSetDevice(ctx->device);
+    std::vector<mp_req> ids;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto& kv : ctx->reqs) ids.push_back(kv.first);
+    }
+    for (mp_req id : ids) mp_req_free(ctx, id);
+    std::vector<mp_group*> gs(ctx->groups.begin(), ctx->groups.end());
+    for (mp_group* g : gs) mp_group_free(g);
+    std::vector<mp_field*> fs(ctx->fields.begin(), ctx->fields.end());
+    for (mp_field* f : fs) mp_field_free(f);
+    cudaDeviceSynchronize();
+    delete ctx;
+    return MP_OK;
+}
+
+int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
+{
+    if (!ctx || !d || !out) return fail(MP_ERR_INVALID_ARG, "mp_field_load: NULL argument");
+    if (d->nlay <= 0 || d->nrow <= 0 || d->ncol <= 0) return fail(MP_ERR_SHAPE, "mp_field_load: dims must be > 0");
+    const long long nl = d->nlay, nr = d->nrow, nc = d->ncol;
+    const long long ncell = nl * nr * nc;
+    if (ncell > 0x7fffffffLL) return fail(MP_ERR_SHAPE, "mp_field_load: more than 2^31-1 cells");
+    if (!d->delr || !d->delc || !d->dz || !d->qx || !d->qy || !d->qz || !d->porosity || !d->ibound)
+        return fail(MP_ERR_INVALID_ARG, "mp_field_load: NULL array");
+    for (long long a = 0; a < nc; ++a)
+        if (!(d->delr[a] > 0.0) || !std::isfinite(d->delr[a])) return fail(MP_ERR_NONFINITE, "delr must be finite and > 0");
+    for (long long a = 0; a < nr; ++a)
+        if (!(d->delc[a] > 0.0) || !std::isfinite(d->delc[a])) return fail(MP_ERR_NONFINITE, "delc must be finite and > 0");
+    for (long long a = 0; a < nl; ++a)
+        if (!(d->dz[a] > 0.0) || !std::isfinite(d->dz[a])) return fail(MP_ERR_NONFINITE, "dz must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->origin[a])) return fail(MP_ERR_NONFINITE, "origin must be finite");
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+
+    const long long nqx = nl * nr * (nc + 1), nqy = nl * (nr + 1) * nc, nqz = (nl + 1) * nr * nc;
+    // persistent layout
+    size_t off = 0;
+    const size_t o_r64 = off; off = align256(off + sizeof(CellF64) * ncell);
+    const size_t o_r32 = off; off = align256(off + sizeof(CellF32) * ncell);
+    const size_t o_delr = off; off = align256(off + sizeof(double) * nc);
+    const size_t o_delc = off; off = align256(off + sizeof(double) * nr);
+    const size_t o_dz = off; off = align256(off + sizeof(double) * nl);
+    const size_t o_xf = off; off = align256(off + sizeof(double) * (nc + 1));
+    const size_t o_yf = off; off = align256(off + sizeof(double) * (nr + 1));
+    const size_t o_zf = off; off = align256(off + sizeof(double) * (nl + 1));
+    const size_t o_ib = off; off = align256(off + ncell);
+    const size_t o_flag = off; off = align256(off + sizeof(unsigned));
+    const size_t persistent = off;
+    const bool dev_in = (d->flags & MP_DEVICE_PTR) != 0;
+    // staging for host inputs (freed once the records are built)
+    size_t soff = 0;
+    const size_t o_qx = soff; soff = align256(soff + (dev_in ? 0 : sizeof(double) * nqx));
+    const size_t o_qy = soff; soff = align256(soff + (dev_in ? 0 : sizeof(double) * nqy));
+    const size_t o_qz = soff; soff = align256(soff + (dev_in ? 0 : sizeof(double) * nqz));
+    const size_t o_por = soff; soff = align256(soff + (dev_in ? 0 : sizeof(double) * ncell));
+
+    char* buf = nullptr;
+    char* stage = nullptr;
+    if (cudaMalloc(&buf, persistent) != cudaSuccess || (!dev_in && cudaMalloc(&stage, soff) != cudaSuccess)) {
+        cudaGetLastError();
+        if (buf) cudaFree(buf);
+        return fail(MP_ERR_OOM, "mp_field_load: device allocation failed");
+    }
+    auto cleanup = [&](int rc) { cudaFree(buf); if (stage) cudaFree(stage); return rc; };
+    std::vector<double> xf(nc + 1), yf(nr + 1), zf(nl + 1);
+    xf[0] = d->origin[0];
+    for (long long a = 0; a < nc; ++a) xf[a + 1] = xf[a] + d->delr[a];
+    yf[0] = d->origin[1];
+    for (long long a = 0; a < nr; ++a) yf[a + 1] = yf[a] + d->delc[a];
+    zf[0] = d->origin[2];
+    for (long long a = 0; a < nl; ++a) zf[a + 1] = zf[a] + d->dz[a];
+
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    auto fin = [&](int rc) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        return cleanup(rc);
+    };
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+    const cudaMemcpyKind in_kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* qx = dev_in ? d->qx : reinterpret_cast<double*>(stage + o_qx);
+    const double* qy = dev_in ? d->qy : reinterpret_cast<double*>(stage + o_qy);
+    const double* qz = dev_in ? d->qz : reinterpret_cast<double*>(stage + o_qz);
+    const double* por = dev_in ? d->porosity : reinterpret_cast<double*>(stage + o_por);
+    if (!dev_in) {
+        if ((e = cudaMemcpyAsync(stage + o_qx, d->qx, sizeof(double) * nqx, h2d, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(stage + o_qy, d->qy, sizeof(double) * nqy, h2d, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(stage + o_qz, d->qz, sizeof(double) * nqz, h2d, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(stage + o_por, d->porosity, sizeof(double) * ncell, h2d, s)) != cudaSuccess)
+            return fin(cuda_fail(e, "mp_field_load: upload"));
+    }
+    if ((e = cudaMemcpyAsync(buf + o_ib, d->ibound, ncell, in_kind, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_delr, d->delr, sizeof(double) * nc, h2d, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_delc, d->delc, sizeof(double) * nr, h2d, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_dz, d->dz, sizeof(double) * nl, h2d, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_xf, xf.data(), sizeof(double) * (nc + 1), h2d, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_yf, yf.data(), sizeof(double) * (nr + 1), h2d, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_zf, zf.data(), sizeof(double) * (nl + 1), h2d, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(buf + o_flag, 0, sizeof(unsigned), s)) != cudaSuccess)
+        return fin(cuda_fail(e, "mp_field_load: upload"));
+    unsigned* dflag = reinterpret_cast<unsigned*>(buf + o_flag);
+    if ((e = launch_validate(qx, nqx, qy, nqy, qz, nqz, por, reinterpret_cast<int8_t*>(buf + o_ib), ncell, dflag,
+                             s)) != cudaSuccess)
+        return fin(cuda_fail(e, "mp_field_load: validate"));
+    unsigned hflag = 0;
+    if ((e = cudaMemcpyAsync(&hflag, dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fin(cuda_fail(e, "mp_field_load: validate"));
+    if (hflag & 1u) return fin(fail(MP_ERR_NONFINITE, "mp_field_load: non-finite face flow"));
+    if (hflag & 2u) return fin(fail(MP_ERR_NONFINITE, "mp_field_load: porosity outside (0, 1] in an active cell"));
+    if (hflag & 4u) return fin(fail(MP_ERR_INVALID_ARG, "mp_field_load: ibound outside {-1, 0, 1, 2}"));
+
+    mp_field* f = new mp_field();
+    f->ctx = ctx;
+    f->d.nlay = (int)nl; f->d.nrow = (int)nr; f->d.ncol = (int)nc;
+    f->d.ncell = ncell;
+    f->d.rec64 = reinterpret_cast<CellF64*>(buf + o_r64);
+    f->d.rec32 = reinterpret_cast<CellF32*>(buf + o_r32);
+    f->d.delr = reinterpret_cast<double*>(buf + o_delr);
+    f->d.delc = reinterpret_cast<double*>(buf + o_delc);
+    f->d.dz = reinterpret_cast<double*>(buf + o_dz);
+    f->d.xf = reinterpret_cast<double*>(buf + o_xf);
+    f->d.yf = reinterpret_cast<double*>(buf + o_yf);
+    f->d.zf = reinterpret_cast<double*>(buf + o_zf);
+    f->d.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
+    e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32), qx, qy, qz,
+                             por, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (stage) cudaFree(stage);
+    if (e != cudaSuccess) {
+        delete f;
+        cudaFree(buf);
+        return cuda_fail(e, "mp_field_load: build records");
+    }
+    f->buf = buf;
+    f->bytes = persistent;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->fields.insert(f);
+    }
+    *out = f;
+    return MP_OK;
+}
+
+int mp_field_free(mp_field* f)
+{
+    if (!f) return fail(MP_ERR_INVALID_ARG, "mp_field_free: NULL");
+    mp_ctx* ctx = f->ctx;
+    int rc = drain_users(ctx, nullptr, f);
+    if (rc != MP_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->fields.erase(f);
+    }
+    cudaSetDevice(ctx->device);
+    cudaFree(f->buf);
+    delete f;
+    return MP_OK;
+}
+
+int mp_field_bytes(const mp_field* f, size_t* bytes)
+{
+    if (!f || !bytes) return fail(MP_ERR_INVALID_ARG, "mp_field_bytes: NULL");
+    *bytes = f->bytes;
+    return MP_OK;
+}
+
+int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, void* stream, mp_group** out)
+{
+    if (!ctx || !f || !r || !out) return fail(MP_ERR_INVALID_ARG, "mp_release_group: NULL argument");
+    if (r->n < 0) return fail(MP_ERR_INVALID_ARG, "mp_release_group: n < 0");
+    if (r->kind != MP_RELEASE_EXPLICIT && r->kind != MP_RELEASE_BOX)
+        return fail(MP_ERR_INVALID_ARG, "mp_release_group: unknown kind");
+    const long long n = r->n;
+    const bool dev_in = (r->flags & MP_DEVICE_PTR) != 0;
+    if (r->kind == MP_RELEASE_EXPLICIT) {
+        if (n > 0 && (!r->cell || !r->local)) return fail(MP_ERR_INVALID_ARG, "mp_release_group: NULL cell/local");
+        if (!dev_in) {
+            for (long long q = 0; q < 3 * n; ++q)
+                if (!std::isfinite(r->local[q])) return fail(MP_ERR_NONFINITE, "mp_release_group: non-finite local");
+            if (r->t0)
+                for (long long q = 0; q < n; ++q)
+                    if (!std::isfinite(r->t0[q])) return fail(MP_ERR_NONFINITE, "mp_release_group: non-finite t0");
+        }
+    } else {
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(r->lo[a]) || !std::isfinite(r->hi[a]) || r->hi[a] < r->lo[a])
+                return fail(MP_ERR_INVALID_ARG, "mp_release_group: box must be finite with lo <= hi");
+    }
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t off = 0;
+    const size_t o_cell = off; off = align256(off + 4 * (size_t)n);
+    const size_t o_px = off; off = align256(off + 8 * (size_t)n);
+    const size_t o_py = off; off = align256(off + 8 * (size_t)n);
+    const size_t o_pz = off; off = align256(off + 8 * (size_t)n);
+    const size_t o_t = off; off = align256(off + 8 * (size_t)n);
+    const size_t o_st = off; off = align256(off + (size_t)n);
+    const size_t bytes = std::max<size_t>(off, 256);
+    char* buf = nullptr;
+    if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_ERR_OOM, "mp_release_group: device allocation failed");
+    }
+    mp_group* g = new mp_group();
+    g->ctx = ctx;
+    g->field = f;
+    g->n = n;
+    g->buf = buf;
+    g->stream = s;
+    g->d.cell = reinterpret_cast<int32_t*>(buf + o_cell);
+    g->d.px = reinterpret_cast<double*>(buf + o_px);
+    g->d.py = reinterpret_cast<double*>(buf + o_py);
+    g->d.pz = reinterpret_cast<double*>(buf + o_pz);
+    g->d.t = reinterpret_cast<double*>(buf + o_t);
+    g->d.status = reinterpret_cast<uint8_t*>(buf + o_st);
+    cudaError_t e = cudaSuccess;
+    if (r->kind == MP_RELEASE_BOX) {
+        e = launch_release_box(f->d, g->d, n, r->lo, r->hi, r->seed, r->id_offset, s);
+    } else if (n > 0) {
+        const int32_t* cell = r->cell;
+        const double* local = r->local;
+        const double* t0 = r->t0;
+        char* tmp = nullptr;
+        if (!dev_in) {
+            size_t toff = 0;
+            const size_t o_c = toff; toff = align256(toff + 4 * (size_t)n);
+            const size_t o_l = toff; toff = align256(toff + 24 * (size_t)n);
+            const size_t o_t0 = toff; toff = align256(toff + (r->t0 ? 8 * (size_t)n : 0));
+            e = cudaMallocAsync(&tmp, toff, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + o_c, r->cell, 4 * (size_t)n, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + o_l, r->local, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && r->t0)
+                e = cudaMemcpyAsync(tmp + o_t0, r->t0, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+            cell = reinterpret_cast<int32_t*>(tmp + o_c);
+            local = reinterpret_cast<double*>(tmp + o_l);
+            t0 = r->t0 ? reinterpret_cast<double*>(tmp + o_t0) : nullptr;
+        }
+        if (e == cudaSuccess) e = launch_release_explicit(f->d, g->d, n, cell, local, t0, s);
+        if (tmp) cudaFreeAsync(tmp, s);
+    }
+    if (e != cudaSuccess) {
+        cudaFreeAsync(buf, s);
+        delete g;
+        return cuda_fail(e, "mp_release_group");
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->groups.insert(g);
+    }
+    *out = g;
+    return MP_OK;
+}
+
+int mp_group_free(mp_group* g)
+{
+    if (!g) return fail(MP_ERR_INVALID_ARG, "mp_group_free: NULL");
+    mp_ctx* ctx = g->ctx;
+    int rc = drain_users(ctx, g, nullptr);
+    if (rc != MP_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->groups.erase(g);
+    }
+    cudaSetDevice(ctx->device);
+    cudaFreeAsync(g->buf, g->stream);
+    delete g;
+    return MP_OK;
+}
+
+int mp_group_size(const mp_group* g, int64_t* n)
+{
+    if (!g || !n) return fail(MP_ERR_INVALID_ARG, "mp_group_size: NULL");
+    *n = g->n;
+    return MP_OK;
+}
+
+int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes)
+{
+    if (!o || !bytes || n < 0) return fail(MP_ERR_INVALID_ARG, "mp_query_bytes: bad argument");
+    const bool ts = (o->mode & MP_MODE_TIMESERIES) && o->n_times > 0;
+    size_t b = 0;
+    b += align256(4 * (size_t)n);           // cell
+    b += 7 * align256(8 * (size_t)n);       // x y z px py pz t
+    b += align256((size_t)n);               // status
+    b += align256(4 * (size_t)n);           // steps
+    b += align256((size_t)n);               // exit_face
+    b += align256(8 * (size_t)n);           // hash
+    b += align256(sizeof(unsigned long long) * N_COUNTERS);
+    b += align256(sizeof(unsigned long long));
+    if (ts) {
+        b += align256(sizeof(mp_ts_record) * (size_t)o->n_times * (size_t)n);
+        b += align256(sizeof(double) * (size_t)o->n_times);
+    }
+    *bytes = b;
+    return MP_OK;
+}
+
+int mp_track_launches(const mp_track_opts* o, int32_t* launches)
+{
+    if (!o || !launches) return fail(MP_ERR_INVALID_ARG, "mp_track_launches: NULL");
+    *launches = 1;
+    return MP_OK;
+}
+
+int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out)
+{
+    if (!ctx || !g || !o || !out) return fail(MP_ERR_INVALID_ARG, "mp_track: NULL argument");
+    if (g->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_track: group belongs to another context");
+    if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))
+        return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
+    if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
+        return fail(MP_ERR_INVALID_ARG, "mp_track: unknown precision");
+    if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC)
+        return fail(MP_ERR_INVALID_ARG, "mp_track: unknown schedule");
+    if (o->block < 0 || o->block > 1024) return fail(MP_ERR_INVALID_ARG, "mp_track: block outside [0, 1024]");
+    if (std::isnan(o->t_stop)) return fail(MP_ERR_INVALID_ARG, "mp_track: t_stop is NaN");
+    const bool want_ts = (o->mode & MP_MODE_TIMESERIES) != 0;
+    if (want_ts && (o->n_times <= 0 || !o->times))
+        return fail(MP_ERR_INVALID_ARG, "mp_track: timeseries mode needs output times");
+    if (o->n_times < 0) return fail(MP_ERR_INVALID_ARG, "mp_track: n_times < 0");
+    const int nt = want_ts ? o->n_times : 0;
+    for (int k = 0; k < nt; ++k) {
+        if (!std::isfinite(o->times[k])) return fail(MP_ERR_NONFINITE, "mp_track: non-finite output time");
+        if (k > 0 && o->times[k] < o->times[k - 1]) return fail(MP_ERR_INVALID_ARG, "mp_track: times not ascending");
+    }
+    double t_stop = o->t_stop;
+    if (want_ts && !(o->mode & MP_MODE_ENDPOINT) && !(t_stop < INFINITY)) t_stop = o->times[nt - 1];
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const long long n = g->n;
+    size_t bytes = 0;
+    mp_track_opts oo = *o;
+    oo.n_times = nt;
+    mp_query_bytes(&oo, n, &bytes);
+    char* buf = nullptr;
+    if (cudaMallocAsync(&buf, std::max<size_t>(bytes, 256), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_ERR_OOM, "mp_track: device allocation failed");
+    }
+    Request* r = new Request();
+    r->group = g;
+    r->n = n;
+    r->n_times = nt;
+    r->precision = o->precision;
+    r->buf = buf;
+    r->bytes = bytes;
+    r->stream = s;
+    size_t off = 0;
+    auto take = [&](size_t sz) { char* p = buf + off; off += align256(sz); return p; };
+    r->d.cell = reinterpret_cast<int32_t*>(take(4 * (size_t)n));
+    r->d.x = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.y = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.z = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.px = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.py = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.pz = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.t = reinterpret_cast<double*>(take(8 * (size_t)n));
+    r->d.status = reinterpret_cast<uint8_t*>(take((size_t)n));
+    r->d.steps = reinterpret_cast<uint32_t*>(take(4 * (size_t)n));
+    r->d.exit_face = reinterpret_cast<uint8_t*>(take((size_t)n));
+    r->d.hash = reinterpret_cast<unsigned long long*>(take(8 * (size_t)n));
+    r->d.counters = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * N_COUNTERS));
+    r->d.queue = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
+    r->d.ts = nullptr;
+    r->d.times = nullptr;
+    if (nt > 0) {
+        r->d.ts = reinterpret_cast<mp_ts_record*>(take(sizeof(mp_ts_record) * (size_t)nt * (size_t)n));
+        r->d.times = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nt));
+    }
+    cudaError_t e = cudaSuccess;
+    if (nt > 0) e = cudaMemcpyAsync(const_cast<double*>(r->d.times), o->times, sizeof(double) * nt,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(r->d.counters, 0, sizeof(unsigned long long) * (N_COUNTERS + 0), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d.queue, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->k0);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->k1);
+    if (e == cudaSuccess) e = cudaEventRecord(r->k0, s);
+    TrackParams p{};
+    p.n = n;
+    p.t_stop = t_stop;
+    p.max_steps = o->max_steps > 0 ? o->max_steps : 1000000LL;
+    p.n_times = nt;
+    p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
+    p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    const int block = o->block > 0 ? o->block : 128;
+    if (e == cudaSuccess) {
+        if (o->precision == MP_PREC_FP64) e = launch_track_fp64(g->field->d, g->d, r->d, p, o->schedule, block, 0, s);
+        else e = launch_track_mixed(g->field->d, g->d, r->d, p, o->schedule, block, 0, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(r->k1, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        cudaFreeAsync(buf, s);
+        if (r->k0) cudaEventDestroy(r->k0);
+        if (r->k1) cudaEventDestroy(r->k1);
+        delete r;
+        return cuda_fail(e, "mp_track");
+    }
+    int64_t id;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        id = ctx->next_id++;
+        ctx->reqs[id] = r;
+    }
+    *out = id;
+    return MP_OK;
+}
+
+int mp_query(mp_ctx* ctx, mp_req id)
+{
+    if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_query: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_query: unknown request");
+    cudaError_t e = cudaEventQuery(r->k1);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return cuda_fail(e, "mp_query");
+}
+
+int mp_wait(mp_ctx* ctx, mp_req id, int64_t timeout_us)
+{
+    if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_wait: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_wait: unknown request");
+    return wait_event(r->k1, timeout_us);
+}
+
+namespace {
+
+int copy_out(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s)
+{
+    if (!dst || bytes == 0) return MP_OK;
+    if (dev) {
+        MP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s), "copy out");
+    } else {
+        MP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost), "copy out");
+    }
+    return MP_OK;
+}
+
+int prepare_read(mp_ctx* ctx, Request* r, uint32_t flags, cudaStream_t s)
+{
+    if (flags & MP_DEVICE_PTR) {
+        MP_CUDA(cudaStreamWaitEvent(s, r->k1, 0), "cudaStreamWaitEvent");
+        return MP_OK;
+    }
+    int rc = wait_event(r->k1, -1);
+    if (rc != MP_OK) return rc;
+    unsigned long long h[N_COUNTERS];
+    rc = read_counters(r, h);
+    if (rc != MP_OK) return rc;
+    if (h[COUNTER_ERR]) return fail(MP_ERR_DEVICE, "tracking kernel raised its error flag");
+    (void)ctx;
+    return MP_OK;
+}
+
+}  // namespace
+
+int mp_get_endpoints(mp_ctx* ctx, mp_req id, const mp_endpoints* out, uint32_t flags, void* stream)
+{
+    if (!ctx || !out) return fail(MP_ERR_INVALID_ARG, "mp_get_endpoints: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_get_endpoints: unknown request");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = prepare_read(ctx, r, flags, s);
+    if (rc != MP_OK) return rc;
+    const bool dev = (flags & MP_DEVICE_PTR) != 0;
+    const size_t n = (size_t)r->n;
+    if ((rc = copy_out(out->cell, r->d.cell, 4 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->x, r->d.x, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->y, r->d.y, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->z, r->d.z, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->px, r->d.px, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->py, r->d.py, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->pz, r->d.pz, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->t, r->d.t, 8 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->status, r->d.status, n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->steps, r->d.steps, 4 * n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->exit_face, r->d.exit_face, n, dev, s)) != MP_OK) return rc;
+    if ((rc = copy_out(out->hash, r->d.hash, 8 * n, dev, s)) != MP_OK) return rc;
+    return MP_OK;
+}
+
+int mp_get_timeseries(mp_ctx* ctx, mp_req id, mp_ts_record* out, uint32_t flags, void* stream)
+{
+    if (!ctx || !out) return fail(MP_ERR_INVALID_ARG, "mp_get_timeseries: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_get_timeseries: unknown request");
+    if (!r->d.ts) return fail(MP_ERR_INVALID_ARG, "mp_get_timeseries: request has no timeseries");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = prepare_read(ctx, r, flags, s);
+    if (rc != MP_OK) return rc;
+    return copy_out(out, r->d.ts, sizeof(mp_ts_record) * (size_t)r->n_times * (size_t)r->n,
+                    (flags & MP_DEVICE_PTR) != 0, s);
+}
+
+int mp_endpoints_device(mp_ctx* ctx, mp_req id, mp_endpoints* out, mp_ts_record** ts)
+{
+    if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_endpoints_device: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_endpoints_device: unknown request");
+    if (out) {
+        out->cell = r->d.cell;
+        out->x = r->d.x; out->y = r->d.y; out->z = r->d.z;
+        out->px = r->d.px; out->py = r->d.py; out->pz = r->d.pz;
+        out->t = r->d.t;
+        out->status = r->d.status;
+        out->steps = r->d.steps;
+        out->exit_face = r->d.exit_face;
+        out->hash = reinterpret_cast<uint64_t*>(r->d.hash);
+    }
+    if (ts) *ts = r->d.ts;
+    return MP_OK;
+}
+
+int mp_get_stats(mp_ctx* ctx, mp_req id, mp_stats* out)
+{
+    if (!ctx || !out) return fail(MP_ERR_INVALID_ARG, "mp_get_stats: NULL");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_get_stats: unknown request");
+    cudaSetDevice(ctx->device);
+    int rc = wait_event(r->k1, -1);
+    if (rc != MP_OK) return rc;
+    unsigned long long h[N_COUNTERS];
+    rc = read_counters(r, h);
+    if (rc != MP_OK) return rc;
+    mp_stats st{};
+    st.cell_steps = h[COUNTER_STEPS];
+    for (int k = 0; k < MP_N_STATUS; ++k) st.n_status[k] = h[COUNTER_STATUS + k];
+    float ms = 0.f;
+    MP_CUDA(cudaEventElapsedTime(&ms, r->k0, r->k1), "cudaEventElapsedTime");
+    st.kernel_ms = ms;
+    st.device_error = h[COUNTER_ERR] ? 1 : 0;
+    *out = st;
+    return MP_OK;
+}
+
+int mp_req_free(mp_ctx* ctx, mp_req id)
+{
+    if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_req_free: NULL");
+    Request* r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->reqs.find(id);
+        if (it == ctx->reqs.end()) return fail(MP_ERR_NOT_READY, "mp_req_free: unknown request");
+        r = it->second;
+        ctx->reqs.erase(it);
+    }
+    cudaSetDevice(ctx->device);
+    cudaFreeAsync(r->buf, r->stream);
+    cudaEventDestroy(r->k0);
+    cudaEventDestroy(r->k1);
+    delete r;
+    return MP_OK;
+}
+
+}  // extern "C"

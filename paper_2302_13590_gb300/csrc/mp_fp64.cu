@@ -1,0 +1,479 @@
+// mp_fp64.cu - field records, particle release and FP64 tracking kernels.
+//
+// Compiled with -fmad=false: every multiply and add below rounds on its own,
+// in the order written, so that the FP64 path evaluates the same IEEE
+// operations as a plain double-precision statement of the method.
+//
+// Method (Pollock 1988, the displacement scheme the paper keeps unchanged;
+// Methods, "MODPATH"): inside a cell each velocity component varies linearly
+// between its two faces, v(p) = v1 + A p with A = (v2 - v1) / D, so the
+// motion along each axis is p(t) = p + v_p t (e^{A t} - 1) / (A t) and the
+// time to reach the exit face is t_a = (d / v_p) ln(1 + z) / z with
+// z = A d / v_p (t_a = d / v_p when z == 0).  The particle leaves through the
+// face with the smallest t_a (lowest axis on ties) and is handed to the
+// neighbour across it, until a stopping condition holds (Methods, "MODPATH").
+#include <cfloat>
+#include <cmath>
+
+#include "mp_internal.h"
+#include "mp_sched.cuh"
+
+namespace mp {
+
+// ---------------------------------------------------------------------------
+// field records
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int nb_class(const DevField& f, int k, int i, int j)
+{
+    if (k < 0 || k >= f.nlay || i < 0 || i >= f.nrow || j < 0 || j >= f.ncol) return NB_OUTSIDE;
+    const int8_t ib = f.ibound[((long long)k * f.nrow + i) * f.ncol + j];
+    if (ib == 1) return NB_ACTIVE;
+    if (ib == 2) return NB_SINK;
+    return NB_BOUNDARY;
+}
+
+__global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const double* qx, const double* qy,
+                                const double* qz, const double* por)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= f.ncell) return;
+    const int ncol = f.ncol, nrow = f.nrow;
+    const int j = (int)(c % ncol), i = (int)((c / ncol) % nrow), k = (int)(c / ((long long)ncol * nrow));
+    unsigned long long nb = 0;
+    nb |= (unsigned long long)nb_class(f, k, i, j - 1) << 0;
+    nb |= (unsigned long long)nb_class(f, k, i, j + 1) << 2;
+    nb |= (unsigned long long)nb_class(f, k, i - 1, j) << 4;
+    nb |= (unsigned long long)nb_class(f, k, i + 1, j) << 6;
+    nb |= (unsigned long long)nb_class(f, k - 1, i, j) << 8;
+    nb |= (unsigned long long)nb_class(f, k + 1, i, j) << 10;
+    CellF64 r{};
+    CellF32 s{};
+    const int8_t ib = f.ibound[c];
+    if (ib == 1 || ib == 2) {
+        const double n = por[c];
+        const double dx = f.delr[j], dy = f.delc[i], dzz = f.dz[k];
+        const double ax = dy * dzz, ay = dx * dzz, az = dx * dy;
+        const double qx1 = qx[((long long)k * nrow + i) * (ncol + 1) + j];
+        const double qx2 = qx[((long long)k * nrow + i) * (ncol + 1) + j + 1];
+        const double qy1 = qy[((long long)k * (nrow + 1) + i) * ncol + j];
+        const double qy2 = qy[((long long)k * (nrow + 1) + i + 1) * ncol + j];
+        const double qz1 = qz[((long long)k * nrow + i) * ncol + j];
+        const double qz2 = qz[((long long)(k + 1) * nrow + i) * ncol + j];
+        r.v1x = qx1 / (n * ax); r.v2x = qx2 / (n * ax);
+        r.v1y = qy1 / (n * ay); r.v2y = qy2 / (n * ay);
+        r.v1z = qz1 / (n * az); r.v2z = qz2 / (n * az);
+        r.Ax = (r.v2x - r.v1x) / dx;
+        r.Ay = (r.v2y - r.v1y) / dy;
+        r.Az = (r.v2z - r.v1z) / dzz;
+        s.u1x = (float)(r.v1x / dx); s.u2x = (float)(r.v2x / dx);
+        s.u1y = (float)(r.v1y / dy); s.u2y = (float)(r.v2y / dy);
+        s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(r.v2z / dzz);
+    }
+    r.nb = nb;
+    s.nb = (uint32_t)nb;
+    r64[c] = r;
+    r32[c] = s;
+}
+
+cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, const double* qx,
+                                 const double* qy, const double* qz, const double* por, cudaStream_t s)
+{
+    if (f.ncell <= 0) return cudaSuccess;
+    const int b = 256;
+    const long long g = (f.ncell + b - 1) / b;
+    k_build_records<<<(unsigned)g, b, 0, s>>>(f, rec64, rec32, qx, qy, qz, por);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// release: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    #pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ double unit53(unsigned a, unsigned b)
+{
+    const unsigned long long v = ((((unsigned long long)a) << 32) | (unsigned long long)b) >> 11;
+    return (double)v * (1.0 / 9007199254740992.0);
+}
+
+// largest a in [0, n-1] with f[a] <= x; -1 if x is outside [f[0], f[n]]
+__device__ __forceinline__ int locate(const double* fc, int n, double x)
+{
+    if (!(x >= fc[0]) || !(x <= fc[n])) return -1;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fc[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint8_t release_status(const DevField& f, long long c)
+{
+    const int8_t ib = f.ibound[c];
+    return ib == 1 ? MP_ST_ACTIVE : (ib == 2 ? MP_ST_SINK : MP_ST_INVALID_RELEASE);
+}
+
+struct Box { double lo[3], hi[3]; };
+
+__global__ void k_release_box(DevField f, DevState st, long long n, Box b, unsigned long long seed,
+                              unsigned long long off)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const unsigned long long id = (unsigned long long)q + off;
+    const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    const uint4 r = philox4x32_10(make_uint4((unsigned)id, (unsigned)(id >> 32), 0u, 0u), key);
+    const uint4 s = philox4x32_10(make_uint4((unsigned)id, (unsigned)(id >> 32), 1u, 0u), key);
+    const double ux = unit53(r.x, r.y), uy = unit53(r.z, r.w), uz = unit53(s.x, s.y);
+    const double gx = b.lo[0] + ux * (b.hi[0] - b.lo[0]);
+    const double gy = b.lo[1] + uy * (b.hi[1] - b.lo[1]);
+    const double gz = b.lo[2] + uz * (b.hi[2] - b.lo[2]);
+    const int j = locate(f.xf, f.ncol, gx), i = locate(f.yf, f.nrow, gy), k = locate(f.zf, f.nlay, gz);
+    st.t[q] = 0.0;
+    if (j < 0 || i < 0 || k < 0) {
+        st.cell[q] = -1; st.px[q] = 0.0; st.py[q] = 0.0; st.pz[q] = 0.0;
+        st.status[q] = MP_ST_INVALID_RELEASE;
+        return;
+    }
+    double ox = gx - f.xf[j], oy = gy - f.yf[i], oz = gz - f.zf[k];
+    ox = fmin(fmax(ox, 0.0), f.delr[j]);
+    oy = fmin(fmax(oy, 0.0), f.delc[i]);
+    oz = fmin(fmax(oz, 0.0), f.dz[k]);
+    const long long c = ((long long)k * f.nrow + i) * f.ncol + j;
+    st.cell[q] = (int32_t)c;
+    st.px[q] = ox; st.py[q] = oy; st.pz[q] = oz;
+    st.status[q] = release_status(f, c);
+}
+
+__global__ void k_release_explicit(DevField f, DevState st, long long n, const int32_t* cell,
+                                   const double* local, const double* t0)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const long long c = cell[q];
+    st.t[q] = t0 ? t0[q] : 0.0;
+    if (c < 0 || c >= f.ncell) {
+        st.cell[q] = -1; st.px[q] = 0.0; st.py[q] = 0.0; st.pz[q] = 0.0;
+        st.status[q] = MP_ST_INVALID_RELEASE;
+        return;
+    }
+    const int j = (int)(c % f.ncol), i = (int)((c / f.ncol) % f.nrow), k = (int)(c / ((long long)f.ncol * f.nrow));
+    const double fx = fmin(fmax(local[3 * q], 0.0), 1.0);
+    const double fy = fmin(fmax(local[3 * q + 1], 0.0), 1.0);
+    const double fz = fmin(fmax(local[3 * q + 2], 0.0), 1.0);
+    st.cell[q] = (int32_t)c;
+    st.px[q] = fx * f.delr[j]; st.py[q] = fy * f.delc[i]; st.pz[q] = fz * f.dz[k];
+    st.status[q] = release_status(f, c);
+}
+
+cudaError_t launch_release_box(const DevField& f, const DevState& st, long long n, const double lo[3],
+                               const double hi[3], unsigned long long seed, unsigned long long id_offset,
+                               cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    Box b;
+    for (int a = 0; a < 3; ++a) { b.lo[a] = lo[a]; b.hi[a] = hi[a]; }
+    k_release_box<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, st, n, b, seed, id_offset);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long long n, const int32_t* cell,
+                                    const double* local, const double* t0, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_release_explicit<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, st, n, cell, local, t0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tracking engine
+// ---------------------------------------------------------------------------
+
+struct F64Engine {
+    DevField f;
+    DevState in;
+    DevOut o;
+    TrackParams p;
+
+    struct State {
+        int c, i, j, k;
+        double x0, x1, x2;   // offsets (m) from the cell's low faces
+        double t;
+        unsigned steps;
+        unsigned long long h;
+        int kn;
+        int st;
+        int ef;
+    };
+
+    // exit time along one axis (face = +1, -1, or 0 when no face is reachable)
+    __device__ __forceinline__ static double exit_time(double v1, double v2, double A, double D, double vp,
+                                                       double pp, int& face)
+    {
+        double d;
+        if (vp > 0.0 && v2 > 0.0) { face = 1; d = D - pp; }
+        else if (vp < 0.0 && v1 < 0.0) { face = -1; d = -pp; }
+        else { face = 0; return CUDART_INF; }
+        const double t1 = d / vp;
+        const double z = A * t1;
+        if (z == 0.0) return t1;
+        return t1 * (log1p(z) / z);
+    }
+
+    // analytic motion along one axis for a time dt, clamped to the cell
+    __device__ __forceinline__ static double move(double A, double D, double vp, double pp, double dt)
+    {
+        const double s = vp * dt;
+        if (s == 0.0) return pp;
+        const double w = A * dt;
+        const double fct = (w == 0.0) ? 1.0 : expm1(w) / w;
+        double pn = pp + s * fct;
+        if (pn < 0.0) pn = 0.0;
+        if (pn > D) pn = D;
+        return pn;
+    }
+
+    __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
+                                           int st) const
+    {
+        store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
+    }
+
+    __device__ __forceinline__ double gx(const State& s) const { return __ldg(f.xf + s.j) + s.x0; }
+    __device__ __forceinline__ double gy(const State& s) const { return __ldg(f.yf + s.i) + s.x1; }
+    __device__ __forceinline__ double gz(const State& s) const { return __ldg(f.zf + s.k) + s.x2; }
+
+    template <bool TS>
+    __device__ __forceinline__ void load(long long q, State& s) const
+    {
+        s.c = in.cell[q];
+        s.st = in.status[q];
+        s.x0 = in.px[q]; s.x1 = in.py[q]; s.x2 = in.pz[q];
+        s.t = in.t[q];
+        s.steps = 0;
+        s.h = FNV_INIT;
+        s.kn = 0;
+        s.ef = MP_FACE_NONE;
+        if (s.c >= 0 && (long long)s.c < f.ncell) {
+            s.j = s.c % f.ncol;
+            s.i = (s.c / f.ncol) % f.nrow;
+            s.k = s.c / (f.ncol * f.nrow);
+            s.h = fnv_step(s.h, s.c);
+        } else {
+            s.c = -1; s.i = s.j = s.k = 0;
+            s.st = MP_ST_INVALID_RELEASE;
+        }
+        if (TS) {
+            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
+                if (s.c >= 0) record(q, s.kn, s, gx(s), gy(s), gz(s), s.st);
+                else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
+                s.kn++;
+            }
+        }
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void step(long long q, State& s) const
+    {
+        if (s.t >= p.t_stop) { s.st = MP_ST_TIME; return; }
+        if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
+        if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
+            atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
+            s.st = MP_ST_INVALID_RELEASE;
+            return;
+        }
+        const double2* rp = reinterpret_cast<const double2*>(f.rec64 + s.c);
+        const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
+                      r4 = __ldg(rp + 4);
+        const double v1x = r0.x, v2x = r0.y, Ax = r1.x, v1y = r1.y, v2y = r2.x, Ay = r2.y, v1z = r3.x,
+                     v2z = r3.y, Az = r4.x;
+        const unsigned long long nb = (unsigned long long)__double_as_longlong(r4.y);
+        const double D0 = __ldg(f.delr + s.j), D1 = __ldg(f.delc + s.i), D2 = __ldg(f.dz + s.k);
+        const double vp0 = v1x + Ax * s.x0;
+        const double vp1 = v1y + Ay * s.x1;
+        const double vp2 = v1z + Az * s.x2;
+        int f0, f1, f2;
+        const double te0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, f0);
+        const double te1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, f1);
+        const double te2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, f2);
+        int ax = -1;
+        double tmin = CUDART_INF;
+        if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
+        if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
+        if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
+        s.steps++;
+        if (ax < 0 && !(p.t_stop < CUDART_INF)) {
+            if (TS) {
+                while (s.kn < p.n_times) {
+                    const double tau = __ldg(o.times + s.kn) - s.t;
+                    record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
+                           __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
+                           __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_NO_EXIT);
+                    s.kn++;
+                }
+            }
+            s.st = MP_ST_NO_EXIT;
+            return;
+        }
+        if (ax < 0 || s.t + tmin >= p.t_stop) {
+            const double dt = p.t_stop - s.t;
+            if (TS) {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                    const double tau = __ldg(o.times + s.kn) - s.t;
+                    record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
+                           __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
+                           __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
+                    s.kn++;
+                }
+            }
+            s.x0 = move(Ax, D0, vp0, s.x0, dt);
+            s.x1 = move(Ay, D1, vp1, s.x1, dt);
+            s.x2 = move(Az, D2, vp2, s.x2, dt);
+            s.t = p.t_stop;
+            s.st = MP_ST_TIME;
+            return;
+        }
+        const double dt = tmin;
+        const double t_end = s.t + dt;
+        if (TS) {
+            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
+                const double tau = __ldg(o.times + s.kn) - s.t;
+                record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
+                       __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
+                       __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
+                s.kn++;
+            }
+        }
+        int face;
+        if (ax == 0) {
+            face = f0;
+            s.x0 = face > 0 ? D0 : 0.0;
+            s.x1 = move(Ay, D1, vp1, s.x1, dt);
+            s.x2 = move(Az, D2, vp2, s.x2, dt);
+        } else if (ax == 1) {
+            face = f1;
+            s.x0 = move(Ax, D0, vp0, s.x0, dt);
+            s.x1 = face > 0 ? D1 : 0.0;
+            s.x2 = move(Az, D2, vp2, s.x2, dt);
+        } else {
+            face = f2;
+            s.x0 = move(Ax, D0, vp0, s.x0, dt);
+            s.x1 = move(Ay, D1, vp1, s.x1, dt);
+            s.x2 = face > 0 ? D2 : 0.0;
+        }
+        s.t = t_end;
+        const int fidx = 2 * ax + (face > 0 ? 1 : 0);
+        s.ef = fidx;
+        const int cls = (int)((nb >> (2 * fidx)) & 3ULL);
+        if (cls == NB_OUTSIDE) { s.st = MP_ST_EXIT_DOMAIN; return; }
+        if (cls == NB_BOUNDARY) { s.st = MP_ST_BOUNDARY; return; }
+        if (cls == NB_SINK) { s.st = MP_ST_SINK; return; }
+        if (ax == 0) {
+            s.j += face;
+            s.c += face;
+            s.x0 = face > 0 ? 0.0 : __ldg(f.delr + s.j);
+        } else if (ax == 1) {
+            s.i += face;
+            s.c += face * f.ncol;
+            s.x1 = face > 0 ? 0.0 : __ldg(f.delc + s.i);
+        } else {
+            s.k += face;
+            s.c += face * f.ncol * f.nrow;
+            s.x2 = face > 0 ? 0.0 : __ldg(f.dz + s.k);
+        }
+        s.h = fnv_step(s.h, s.c);
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
+    {
+        const bool ok = s.c >= 0;
+        const double x = ok ? gx(s) : CUDART_NAN, y = ok ? gy(s) : CUDART_NAN, z = ok ? gz(s) : CUDART_NAN;
+        if (TS) {
+            for (int kk = s.kn; kk < p.n_times; ++kk) record(q, kk, s, x, y, z, s.st);
+        }
+        o.cell[q] = s.c;
+        o.x[q] = x; o.y[q] = y; o.z[q] = z;
+        o.px[q] = s.x0; o.py[q] = s.x1; o.pz[q] = s.x2;
+        o.t[q] = s.t;
+        o.status[q] = (uint8_t)s.st;
+        o.steps[q] = s.steps;
+        o.exit_face[q] = (uint8_t)s.ef;
+        o.hash[q] = s.h;
+        if (p.update_group && ok) {
+            in.cell[q] = s.c;
+            in.px[q] = s.x0; in.py[q] = s.x1; in.pz[q] = s.x2;
+            in.t[q] = s.t;
+            in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
+        }
+        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);
+        atomicAdd(s_cnt + COUNTER_STATUS + (s.st & 7), 1ULL);
+    }
+};
+
+cudaError_t launch_track_fp64(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
+                              int schedule, int block, int blocks_per_sm_cap, cudaStream_t s)
+{
+    F64Engine e{f, st, o, p};
+    return launch_tracking(e, o.ts != nullptr && p.n_times > 0, schedule, block, blocks_per_sm_cap, s);
+}
+
+}  // namespace mp
+
+namespace mp {
+
+// ---------------------------------------------------------------------------
+// field validation: bit 1 non-finite flow, bit 2 porosity outside (0, 1] in
+// an active or sink cell, bit 4 ibound outside {-1, 0, 1, 2}
+// ---------------------------------------------------------------------------
+
+__global__ void k_validate(const double* qx, long long nqx, const double* qy, long long nqy, const double* qz,
+                           long long nqz, const double* por, const int8_t* ib, long long ncell, unsigned* flags)
+{
+    const long long total = nqx + nqy + nqz + ncell;
+    unsigned bad = 0;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+         u += (long long)gridDim.x * blockDim.x) {
+        if (u < nqx) {
+            if (!isfinite(qx[u])) bad |= 1u;
+        } else if (u < nqx + nqy) {
+            if (!isfinite(qy[u - nqx])) bad |= 1u;
+        } else if (u < nqx + nqy + nqz) {
+            if (!isfinite(qz[u - nqx - nqy])) bad |= 1u;
+        } else {
+            const long long c = u - nqx - nqy - nqz;
+            const int8_t b = ib[c];
+            if (b < -1 || b > 2) bad |= 4u;
+            if (b == 1 || b == 2) {
+                const double n = por[c];
+                if (!(n > 0.0 && n <= 1.0)) bad |= 2u;
+            }
+        }
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+cudaError_t launch_validate(const double* qx, long long nqx, const double* qy, long long nqy, const double* qz,
+                            long long nqz, const double* por, const int8_t* ib, long long ncell, unsigned* flags,
+                            cudaStream_t s)
+{
+    k_validate<<<1024, 256, 0, s>>>(qx, nqx, qy, nqy, qz, nqz, por, ib, ncell, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace mp

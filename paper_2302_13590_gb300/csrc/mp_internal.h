@@ -1,0 +1,111 @@
+// mp_internal.h - device-side layouts and kernel launchers of libmp.
+//
+// Field layout in HBM (built once by mp_field_load):
+//   rec64[c]  80 B  {v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az, nb}: the FP64
+//             face velocities v = Q / (n * area) and gradients
+//             A = (v2 - v1) / D of Pollock (1988), one gather per cell-step.
+//   rec32[c]  32 B  {u1x, u2x, u1y, u2y, u1z, u2z, nb, pad}: the same
+//             velocities divided by the cell size (units 1/s) in FP32 for
+//             the mixed-precision path, which works in local fractions
+//             xi in [0, 1]; one 32-byte sector per cell-step.
+//   nb        2 bits per face (x-, x+, y-, y+, z-, z+): the class of the
+//             neighbour across it (0 active, 1 sink, 2 inactive or constant
+//             head, 3 outside the grid), so crossing needs no second gather.
+//   delr/delc/dz and face coordinates xf/yf/zf (n+1 entries each, FP64).
+// Particle state (group) in SoA: cell int32, px/py/pz/t FP64, status u8.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp.h"
+
+namespace mp {
+
+enum : int { NB_ACTIVE = 0, NB_SINK = 1, NB_BOUNDARY = 2, NB_OUTSIDE = 3 };
+
+struct __align__(16) CellF64 {
+    double v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az;
+    unsigned long long nb;
+};
+static_assert(sizeof(CellF64) == 80, "CellF64 is 80 bytes");
+
+struct __align__(32) CellF32 {
+    float u1x, u2x, u1y, u2y, u1z, u2z;
+    uint32_t nb;
+    float pad;
+};
+static_assert(sizeof(CellF32) == 32, "CellF32 is one 32-byte sector");
+
+struct DevField {
+    int nlay, nrow, ncol;
+    long long ncell;
+    const CellF64* rec64;
+    const CellF32* rec32;
+    const double* delr;
+    const double* delc;
+    const double* dz;
+    const double* xf;  // [ncol+1]
+    const double* yf;  // [nrow+1]
+    const double* zf;  // [nlay+1]
+    const int8_t* ibound;
+};
+
+struct DevState {
+    int32_t* cell;
+    double* px;
+    double* py;
+    double* pz;
+    double* t;
+    uint8_t* status;
+};
+
+// counters[0] = cell-steps, [1 + s] = particles with final status s,
+// [COUNTER_ERR] = device error flag (index of the first bad access + 1)
+enum : int { COUNTER_STEPS = 0, COUNTER_STATUS = 1, COUNTER_ERR = 1 + MP_N_STATUS, N_COUNTERS = 2 + MP_N_STATUS };
+
+struct DevOut {
+    int32_t* cell;
+    double* x;
+    double* y;
+    double* z;
+    double* px;
+    double* py;
+    double* pz;
+    double* t;
+    uint8_t* status;
+    uint32_t* steps;
+    uint8_t* exit_face;
+    unsigned long long* hash;
+    mp_ts_record* ts;            // [n_times][n] or nullptr
+    const double* times;         // device copy, [n_times]
+    unsigned long long* counters;  // [N_COUNTERS]
+    unsigned long long* queue;     // dynamic schedule head
+};
+
+struct TrackParams {
+    long long n;
+    double t_stop;
+    long long max_steps;
+    int n_times;
+    int steps_per_fetch;
+    int update_group;
+};
+
+// Kernel launchers (each enqueues one kernel on `s`).
+cudaError_t launch_validate(const double* qx, long long nqx, const double* qy, long long nqy, const double* qz,
+                            long long nqz, const double* por, const int8_t* ib, long long ncell, unsigned* flags,
+                            cudaStream_t s);
+cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, const double* qx,
+                                 const double* qy, const double* qz, const double* por, cudaStream_t s);
+cudaError_t launch_release_box(const DevField& f, const DevState& st, long long n, const double lo[3],
+                               const double hi[3], unsigned long long seed, unsigned long long id_offset,
+                               cudaStream_t s);
+cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long long n, const int32_t* cell,
+                                    const double* local, const double* t0, cudaStream_t s);
+cudaError_t launch_track_fp64(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
+                              int schedule, int block, int blocks_per_sm_cap, cudaStream_t s);
+cudaError_t launch_track_mixed(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
+                               int schedule, int block, int blocks_per_sm_cap, cudaStream_t s);
+
+}  // namespace mp

@@ -1,0 +1,269 @@
+// mp_mixed.cu - mixed-precision tracking kernels.
+//
+// Same method as the FP64 path (Pollock 1988: per-axis linear velocity,
+// exit time (d / v_p) ln(1 + z) / z, analytic motion, smallest exit time
+// wins, hand-over to the neighbour), evaluated in local fractions
+// xi in [0, 1] of the cell with velocities u = v / D (1/s) in FP32:
+//   u_p = u1 + A xi, A = u2 - u1, exit distance d = 1 - xi or -xi,
+//   t_a = (d / u_p) g(z), z = A d / u_p, g(z) = ln(1 + z) / z,
+//   xi(t) = xi + u_p t h(A t), h(w) = (e^w - 1) / w.
+// g and h use their Taylor series for |z|, |w| < 2^-7 (exact to below FP32
+// rounding there, and free of the 0/0 at z = 0).  The cumulative travel time,
+// the stop-time and output-time comparisons, and every global position are
+// FP64.  Compiled with FMA contraction on (FP32 results are compared with the
+// FP64 oracle within tolerances, not bit for bit).
+#include <cfloat>
+#include <cmath>
+
+#include "mp_internal.h"
+#include "mp_sched.cuh"
+
+namespace mp {
+
+struct MixEngine {
+    DevField f;
+    DevState in;
+    DevOut o;
+    TrackParams p;
+
+    struct State {
+        int c, i, j, k;
+        float x0, x1, x2;  // local fractions in [0, 1]
+        double t;
+        unsigned steps;
+        unsigned long long h;
+        int kn;
+        int st;
+        int ef;
+    };
+
+    static constexpr float SMALL = 0.0078125f;  // 2^-7
+
+    __device__ __forceinline__ static float g_log1p_over(float z)
+    {
+        if (fabsf(z) < SMALL) return 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
+        return log1pf(z) / z;
+    }
+    __device__ __forceinline__ static float h_expm1_over(float w)
+    {
+        if (fabsf(w) < SMALL) return 1.0f + w * (0.5f + w * (1.0f / 6.0f + w * (1.0f / 24.0f + w * (1.0f / 120.0f))));
+        return expm1f(w) / w;
+    }
+
+    __device__ __forceinline__ static float exit_time(float u1, float u2, float A, float up, float xi, int& face)
+    {
+        float d;
+        if (up > 0.0f && u2 > 0.0f) { face = 1; d = 1.0f - xi; }
+        else if (up < 0.0f && u1 < 0.0f) { face = -1; d = -xi; }
+        else { face = 0; return CUDART_INF_F; }
+        const float t1 = d / up;
+        return t1 * g_log1p_over(A * t1);
+    }
+
+    __device__ __forceinline__ static float move(float A, float up, float xi, float dt)
+    {
+        const float s = up * dt;
+        if (s == 0.0f) return xi;
+        const float xn = xi + s * h_expm1_over(A * dt);
+        return fminf(fmaxf(xn, 0.0f), 1.0f);
+    }
+
+    __device__ __forceinline__ double gx(const State& s, float xi) const
+    {
+        return __ldg(f.xf + s.j) + (double)xi * __ldg(f.delr + s.j);
+    }
+    __device__ __forceinline__ double gy(const State& s, float xi) const
+    {
+        return __ldg(f.yf + s.i) + (double)xi * __ldg(f.delc + s.i);
+    }
+    __device__ __forceinline__ double gz(const State& s, float xi) const
+    {
+        return __ldg(f.zf + s.k) + (double)xi * __ldg(f.dz + s.k);
+    }
+
+    __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
+                                           int st) const
+    {
+        store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void load(long long q, State& s) const
+    {
+        s.c = in.cell[q];
+        s.st = in.status[q];
+        s.t = in.t[q];
+        s.steps = 0;
+        s.h = FNV_INIT;
+        s.kn = 0;
+        s.ef = MP_FACE_NONE;
+        if (s.c >= 0 && (long long)s.c < f.ncell) {
+            s.j = s.c % f.ncol;
+            s.i = (s.c / f.ncol) % f.nrow;
+            s.k = s.c / (f.ncol * f.nrow);
+            s.x0 = (float)(in.px[q] / __ldg(f.delr + s.j));
+            s.x1 = (float)(in.py[q] / __ldg(f.delc + s.i));
+            s.x2 = (float)(in.pz[q] / __ldg(f.dz + s.k));
+            s.h = fnv_step(s.h, s.c);
+        } else {
+            s.c = -1; s.i = s.j = s.k = 0;
+            s.x0 = s.x1 = s.x2 = 0.0f;
+            s.st = MP_ST_INVALID_RELEASE;
+        }
+        if (TS) {
+            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
+                if (s.c >= 0) record(q, s.kn, s, gx(s, s.x0), gy(s, s.x1), gz(s, s.x2), s.st);
+                else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
+                s.kn++;
+            }
+        }
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void step(long long q, State& s) const
+    {
+        if (s.t >= p.t_stop) { s.st = MP_ST_TIME; return; }
+        if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
+        if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
+            atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
+            s.st = MP_ST_INVALID_RELEASE;
+            return;
+        }
+        const float4* rp = reinterpret_cast<const float4*>(f.rec32 + s.c);
+        const float4 ra = __ldg(rp), rb = __ldg(rp + 1);
+        const float u1x = ra.x, u2x = ra.y, u1y = ra.z, u2y = ra.w, u1z = rb.x, u2z = rb.y;
+        const unsigned nb = __float_as_uint(rb.z);
+        const float Ax = u2x - u1x, Ay = u2y - u1y, Az = u2z - u1z;
+        const float up0 = u1x + Ax * s.x0, up1 = u1y + Ay * s.x1, up2 = u1z + Az * s.x2;
+        int f0, f1, f2;
+        const float te0 = exit_time(u1x, u2x, Ax, up0, s.x0, f0);
+        const float te1 = exit_time(u1y, u2y, Ay, up1, s.x1, f1);
+        const float te2 = exit_time(u1z, u2z, Az, up2, s.x2, f2);
+        int ax = -1;
+        float tmin = CUDART_INF_F;
+        if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
+        if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
+        if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
+        s.steps++;
+        if (ax < 0 && !(p.t_stop < CUDART_INF)) {
+            if (TS) {
+                while (s.kn < p.n_times) {
+                    const float tau = (float)(__ldg(o.times + s.kn) - s.t);
+                    record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
+                           gz(s, move(Az, up2, s.x2, tau)), MP_ST_NO_EXIT);
+                    s.kn++;
+                }
+            }
+            s.st = MP_ST_NO_EXIT;
+            return;
+        }
+        const double t_end = s.t + (double)tmin;
+        if (ax < 0 || t_end >= p.t_stop) {
+            const float dt = (float)(p.t_stop - s.t);
+            if (TS) {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                    const float tau = (float)(__ldg(o.times + s.kn) - s.t);
+                    record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
+                           gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
+                    s.kn++;
+                }
+            }
+            s.x0 = move(Ax, up0, s.x0, dt);
+            s.x1 = move(Ay, up1, s.x1, dt);
+            s.x2 = move(Az, up2, s.x2, dt);
+            s.t = p.t_stop;
+            s.st = MP_ST_TIME;
+            return;
+        }
+        const float dt = tmin;
+        if (TS) {
+            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
+                const float tau = (float)(__ldg(o.times + s.kn) - s.t);
+                record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
+                       gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
+                s.kn++;
+            }
+        }
+        int face;
+        if (ax == 0) {
+            face = f0;
+            s.x0 = face > 0 ? 1.0f : 0.0f;
+            s.x1 = move(Ay, up1, s.x1, dt);
+            s.x2 = move(Az, up2, s.x2, dt);
+        } else if (ax == 1) {
+            face = f1;
+            s.x0 = move(Ax, up0, s.x0, dt);
+            s.x1 = face > 0 ? 1.0f : 0.0f;
+            s.x2 = move(Az, up2, s.x2, dt);
+        } else {
+            face = f2;
+            s.x0 = move(Ax, up0, s.x0, dt);
+            s.x1 = move(Ay, up1, s.x1, dt);
+            s.x2 = face > 0 ? 1.0f : 0.0f;
+        }
+        s.t = t_end;
+        const int fidx = 2 * ax + (face > 0 ? 1 : 0);
+        s.ef = fidx;
+        const int cls = (int)((nb >> (2 * fidx)) & 3u);
+        if (cls == NB_OUTSIDE) { s.st = MP_ST_EXIT_DOMAIN; return; }
+        if (cls == NB_BOUNDARY) { s.st = MP_ST_BOUNDARY; return; }
+        if (cls == NB_SINK) { s.st = MP_ST_SINK; return; }
+        if (ax == 0) {
+            s.j += face;
+            s.c += face;
+            s.x0 = face > 0 ? 0.0f : 1.0f;
+        } else if (ax == 1) {
+            s.i += face;
+            s.c += face * f.ncol;
+            s.x1 = face > 0 ? 0.0f : 1.0f;
+        } else {
+            s.k += face;
+            s.c += face * f.ncol * f.nrow;
+            s.x2 = face > 0 ? 0.0f : 1.0f;
+        }
+        s.h = fnv_step(s.h, s.c);
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
+    {
+        const bool ok = s.c >= 0;
+        double px = 0.0, py = 0.0, pz = 0.0, x = CUDART_NAN, y = CUDART_NAN, z = CUDART_NAN;
+        if (ok) {
+            px = (double)s.x0 * __ldg(f.delr + s.j);
+            py = (double)s.x1 * __ldg(f.delc + s.i);
+            pz = (double)s.x2 * __ldg(f.dz + s.k);
+            x = __ldg(f.xf + s.j) + px;
+            y = __ldg(f.yf + s.i) + py;
+            z = __ldg(f.zf + s.k) + pz;
+        }
+        if (TS) {
+            for (int kk = s.kn; kk < p.n_times; ++kk) record(q, kk, s, x, y, z, s.st);
+        }
+        o.cell[q] = s.c;
+        o.x[q] = x; o.y[q] = y; o.z[q] = z;
+        o.px[q] = px; o.py[q] = py; o.pz[q] = pz;
+        o.t[q] = s.t;
+        o.status[q] = (uint8_t)s.st;
+        o.steps[q] = s.steps;
+        o.exit_face[q] = (uint8_t)s.ef;
+        o.hash[q] = s.h;
+        if (p.update_group && ok) {
+            in.cell[q] = s.c;
+            in.px[q] = px; in.py[q] = py; in.pz[q] = pz;
+            in.t[q] = s.t;
+            in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
+        }
+        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);
+        atomicAdd(s_cnt + COUNTER_STATUS + (s.st & 7), 1ULL);
+    }
+};
+
+cudaError_t launch_track_mixed(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
+                               int schedule, int block, int blocks_per_sm_cap, cudaStream_t s)
+{
+    MixEngine e{f, st, o, p};
+    return launch_tracking(e, o.ts != nullptr && p.n_times > 0, schedule, block, blocks_per_sm_cap, s);
+}
+
+}  // namespace mp

@@ -151,11 +151,11 @@ def solve_flow(nlay, nrow, ncol, delr, delc, dz, K, ibound, head_bc, q_src=None,
 
 
 def _fast_len(n: int) -> int:
-    """Smallest length >= n whose prime factors are 2, 3 and 5 (fast FFT sizes)."""
+    """Smallest length >= n whose prime factors are 2 and 5 (fast FFT sizes)."""
     m = max(1, n)
     while True:
         r = m
-        for p in (2, 3, 5):
+        for p in (2, 5):
             while r % p == 0:
                 r //= p
         if r == 1:

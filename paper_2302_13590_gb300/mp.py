@@ -1,0 +1,374 @@
+"""Thin Python binding of libmp (the C ABI in include/mp.h).
+
+Argument marshalling only: every step of the tracking runs in the CUDA
+kernels of ``libmp.so``.  The module-level functions carry the C names
+(``mp_field_load``, ``mp_release_group``, ``mp_track``, ``mp_get_endpoints``,
+``mp_get_timeseries`` ...); ``Context`` / ``Request`` are small conveniences
+on top of them.  Arrays are numpy (host) or anything exposing
+``data_ptr()`` (torch CUDA tensors, passed with ``device=True``).  Streams are
+``cudaStream_t`` handles as integers (e.g. ``torch.cuda.current_stream()
+.cuda_stream``) or None for the legacy default stream.
+
+There is no CPU fallback: if ``libmp.so`` cannot be built or loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+# ---- constants mirrored from mp.h --------------------------------------------
+MP_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NONFINITE", -4: "OOM", -5: "BUSY", -6: "TIMEOUT",
+          -7: "CUDA", -8: "NOT_READY", -9: "DEVICE"}
+MP_ERR_TIMEOUT = -6
+ST_ACTIVE, ST_TIME, ST_SINK, ST_BOUNDARY, ST_EXIT_DOMAIN, ST_NO_EXIT, ST_STEP_CAP, ST_INVALID_RELEASE = range(8)
+STATUS_NAMES = ["ACTIVE", "TIME", "SINK", "BOUNDARY", "EXIT_DOMAIN", "NO_EXIT", "STEP_CAP", "INVALID_RELEASE"]
+FACE_NONE = 255
+MP_DEVICE_PTR = 1
+PREC_FP64, PREC_MIXED = 0, 1
+MODE_ENDPOINT, MODE_TIMESERIES = 1, 2
+SCHED_STATIC, SCHED_DYNAMIC = 0, 1
+TRACK_UPDATE_GROUP = 1
+RELEASE_EXPLICIT, RELEASE_BOX = 0, 1
+
+TS_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("cell", "<i4"), ("status", "u1"),
+                      ("pad", "u1", (3,))])
+assert TS_RECORD.itemsize == 32
+
+_vp = ctypes.c_void_p
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [("nlay", ctypes.c_int32), ("nrow", ctypes.c_int32), ("ncol", ctypes.c_int32),
+                ("delr", _vp), ("delc", _vp), ("dz", _vp), ("origin", ctypes.c_double * 3),
+                ("qx", _vp), ("qy", _vp), ("qz", _vp), ("porosity", _vp), ("ibound", _vp),
+                ("flags", ctypes.c_uint32)]
+
+
+class ReleaseDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("cell", _vp), ("local", _vp), ("t0", _vp),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("seed", ctypes.c_uint64), ("id_offset", ctypes.c_uint64)]
+
+
+class TrackOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("n_times", ctypes.c_int32), ("times", _vp), ("t_stop", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("block", ctypes.c_int32), ("steps_per_fetch", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class Endpoints(ctypes.Structure):
+    _fields_ = [(n, _vp) for n in ("cell", "x", "y", "z", "px", "py", "pz", "t", "status", "steps",
+                                   "exit_face", "hash")]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cell_steps", ctypes.c_uint64), ("n_status", ctypes.c_uint64 * 8),
+                ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32)]
+
+
+ENDPOINT_DTYPES = {"cell": np.int32, "x": np.float64, "y": np.float64, "z": np.float64, "px": np.float64,
+                   "py": np.float64, "pz": np.float64, "t": np.float64, "status": np.uint8,
+                   "steps": np.uint32, "exit_face": np.uint8, "hash": np.uint64}
+
+# every exported entry point with (restype, argtypes)
+_P = ctypes.POINTER
+SIGNATURES = {
+    "mp_ctx_create": (ctypes.c_int, [ctypes.c_int, _P(_vp)]),
+    "mp_ctx_destroy": (ctypes.c_int, [_vp]),
+    "mp_last_error": (ctypes.c_char_p, []),
+    "mp_field_load": (ctypes.c_int, [_vp, _P(FieldDesc), _P(_vp)]),
+    "mp_field_free": (ctypes.c_int, [_vp]),
+    "mp_field_bytes": (ctypes.c_int, [_vp, _P(ctypes.c_size_t)]),
+    "mp_release_group": (ctypes.c_int, [_vp, _vp, _P(ReleaseDesc), _vp, _P(_vp)]),
+    "mp_group_free": (ctypes.c_int, [_vp]),
+    "mp_group_size": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
+    "mp_track": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), _vp, _P(ctypes.c_int64)]),
+    "mp_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
+    "mp_query": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "mp_get_endpoints": (ctypes.c_int, [_vp, ctypes.c_int64, _P(Endpoints), ctypes.c_uint32, _vp]),
+    "mp_get_timeseries": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, ctypes.c_uint32, _vp]),
+    "mp_endpoints_device": (ctypes.c_int, [_vp, ctypes.c_int64, _P(Endpoints), _P(_vp)]),
+    "mp_get_stats": (ctypes.c_int, [_vp, ctypes.c_int64, _P(Stats)]),
+    "mp_req_free": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "mp_query_bytes": (ctypes.c_int, [_P(TrackOpts), ctypes.c_int64, _P(ctypes.c_size_t)]),
+    "mp_track_launches": (ctypes.c_int, [_P(TrackOpts), _P(ctypes.c_int32)]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class MPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmp error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build: bool = True):
+    """Load libmp.so (building it with nvcc first if needed); raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build_lib() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmp.so not found at {path}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MP_OK:
+        raise MPError(rc, load_library().mp_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a tensor (data_ptr); None stays NULL."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype).reshape(-1))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+# ---- C-named functions ----------------------------------------------------------
+
+def mp_ctx_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(load_library().mp_ctx_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def mp_ctx_destroy(ctx):
+    _check(load_library().mp_ctx_destroy(ctx))
+
+
+def mp_field_load(ctx, field, device_arrays: bool = False):
+    """Load a field (an object with nlay, nrow, ncol, delr, delc, dz, origin,
+    qx, qy, qz, porosity, ibound).  With device_arrays=True the flow arrays are
+    CUDA tensors (float64 / int8, contiguous) read in place."""
+    keep = []
+    delr, delc, dz = (_host(field.delr, np.float64), _host(field.delc, np.float64), _host(field.dz, np.float64))
+    keep += [delr, delc, dz]
+    if device_arrays:
+        arrs = [field.qx, field.qy, field.qz, field.porosity, field.ibound]
+    else:
+        arrs = [_host(field.qx, np.float64), _host(field.qy, np.float64), _host(field.qz, np.float64),
+                _host(field.porosity, np.float64), _host(field.ibound, np.int8)]
+        keep += arrs
+    d = FieldDesc(int(field.nlay), int(field.nrow), int(field.ncol), _ptr(delr), _ptr(delc), _ptr(dz),
+                  (ctypes.c_double * 3)(*[float(o) for o in field.origin]), *[_ptr(a) for a in arrs],
+                  MP_DEVICE_PTR if device_arrays else 0)
+    h = ctypes.c_void_p()
+    _check(load_library().mp_field_load(ctx, ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def mp_field_free(fh):
+    _check(load_library().mp_field_free(fh))
+
+
+def mp_field_bytes(fh) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().mp_field_bytes(fh, ctypes.byref(b)))
+    return b.value
+
+
+def mp_release_group(ctx, fh, *, n=None, lo=None, hi=None, seed=0, id_offset=0, cell=None, local=None,
+                     t0=None, stream=None, device_arrays: bool = False):
+    """Box release (lo, hi, seed) or explicit release (cell, local[, t0])."""
+    keep = []
+    if cell is not None:
+        if device_arrays:
+            c, l, t = cell, local, t0
+            nn = int(cell.numel())
+        else:
+            c, l = _host(cell, np.int32), _host(local, np.float64)
+            t = None if t0 is None else _host(t0, np.float64)
+            keep += [c, l, t]
+            nn = c.size
+        d = ReleaseDesc(nn, RELEASE_EXPLICIT, MP_DEVICE_PTR if device_arrays else 0, _ptr(c), _ptr(l), _ptr(t),
+                        (ctypes.c_double * 3)(0, 0, 0), (ctypes.c_double * 3)(0, 0, 0), 0, 0)
+    else:
+        d = ReleaseDesc(int(n), RELEASE_BOX, 0, None, None, None, (ctypes.c_double * 3)(*map(float, lo)),
+                        (ctypes.c_double * 3)(*map(float, hi)), int(seed) & (2 ** 64 - 1), int(id_offset))
+    h = ctypes.c_void_p()
+    _check(load_library().mp_release_group(ctx, fh, ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def mp_group_free(gh):
+    _check(load_library().mp_group_free(gh))
+
+
+def mp_group_size(gh) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().mp_group_size(gh, ctypes.byref(n)))
+    return n.value
+
+
+def make_opts(mode=MODE_ENDPOINT, precision=PREC_FP64, schedule=SCHED_DYNAMIC, times=None, t_stop=math.inf,
+              max_steps=0, block=0, steps_per_fetch=0, flags=0):
+    tarr = None if times is None else _host(times, np.float64)
+    o = TrackOpts(int(mode), int(precision), int(schedule), 0 if tarr is None else int(tarr.size), _ptr(tarr),
+                  float(t_stop), int(max_steps), int(block), int(steps_per_fetch), int(flags))
+    o._keep = tarr
+    return o
+
+
+def mp_track(ctx, gh, opts: TrackOpts, stream=None) -> int:
+    r = ctypes.c_int64()
+    _check(load_library().mp_track(ctx, gh, ctypes.byref(opts), _stream(stream), ctypes.byref(r)))
+    return r.value
+
+
+def mp_wait(ctx, req: int, timeout_us: int = -1):
+    _check(load_library().mp_wait(ctx, int(req), int(timeout_us)))
+
+
+def mp_query(ctx, req: int) -> bool:
+    rc = load_library().mp_query(ctx, int(req))
+    if rc < 0:
+        _check(rc)
+    return rc == 1
+
+
+def mp_get_endpoints(ctx, req: int, n: int, out: Optional[dict] = None, device: bool = False, stream=None):
+    """Endpoint arrays; host numpy by default, or into given tensors (device=True)."""
+    if out is None:
+        out = {k: np.empty(n, dt) for k, dt in ENDPOINT_DTYPES.items()}
+    e = Endpoints(*[_ptr(out.get(k)) for k, _ in Endpoints._fields_])
+    _check(load_library().mp_get_endpoints(ctx, int(req), ctypes.byref(e), MP_DEVICE_PTR if device else 0,
+                                           _stream(stream)))
+    return out
+
+
+def mp_get_timeseries(ctx, req: int, n: int, n_times: int, out=None, device: bool = False, stream=None):
+    """[n_times, n] records (numpy structured array TS_RECORD, or a given buffer)."""
+    if out is None:
+        out = np.empty((n_times, n), TS_RECORD)
+    _check(load_library().mp_get_timeseries(ctx, int(req), _ptr(out), MP_DEVICE_PTR if device else 0,
+                                            _stream(stream)))
+    return out
+
+
+def mp_endpoints_device(ctx, req: int):
+    """(dict of device pointers, timeseries device pointer) of the request's own buffers."""
+    e = Endpoints()
+    ts = ctypes.c_void_p()
+    _check(load_library().mp_endpoints_device(ctx, int(req), ctypes.byref(e), ctypes.byref(ts)))
+    return {k: getattr(e, k) for k, _ in Endpoints._fields_}, ts.value
+
+
+def mp_get_stats(ctx, req: int) -> dict:
+    s = Stats()
+    _check(load_library().mp_get_stats(ctx, int(req), ctypes.byref(s)))
+    return {"cell_steps": int(s.cell_steps), "n_status": [int(v) for v in s.n_status],
+            "kernel_ms": float(s.kernel_ms), "device_error": int(s.device_error)}
+
+
+def mp_req_free(ctx, req: int):
+    _check(load_library().mp_req_free(ctx, int(req)))
+
+
+def mp_query_bytes(opts: TrackOpts, n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().mp_query_bytes(ctypes.byref(opts), int(n), ctypes.byref(b)))
+    return b.value
+
+
+def mp_track_launches(opts: TrackOpts) -> int:
+    v = ctypes.c_int32()
+    _check(load_library().mp_track_launches(ctypes.byref(opts), ctypes.byref(v)))
+    return v.value
+
+
+# ---- conveniences -------------------------------------------------------------------
+
+class Context:
+    """Owns an mp_ctx; fields, groups and requests are freed with it."""
+
+    def __init__(self, device: int = 0):
+        self.h = mp_ctx_create(device)
+
+    def close(self):
+        if self.h is not None:
+            mp_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def field(self, f, device_arrays=False):
+        return mp_field_load(self.h, f, device_arrays=device_arrays)
+
+    def release_box(self, fh, n, lo, hi, seed, id_offset=0, stream=None):
+        return mp_release_group(self.h, fh, n=n, lo=lo, hi=hi, seed=seed, id_offset=id_offset, stream=stream)
+
+    def release_explicit(self, fh, cell, local, t0=None, stream=None, device_arrays=False):
+        return mp_release_group(self.h, fh, cell=cell, local=local, t0=t0, stream=stream,
+                                device_arrays=device_arrays)
+
+    def track(self, gh, stream=None, **kw) -> "Request":
+        opts = make_opts(**kw)
+        n = mp_group_size(gh)
+        rid = mp_track(self.h, gh, opts, stream)
+        nt = opts.n_times if (opts.mode & MODE_TIMESERIES) else 0
+        return Request(self, rid, n, nt)
+
+
+class Request:
+    def __init__(self, ctx: Context, rid: int, n: int, n_times: int):
+        self.ctx, self.id, self.n, self.n_times = ctx, rid, n, n_times
+
+    def wait(self, timeout_us=-1):
+        mp_wait(self.ctx.h, self.id, timeout_us)
+
+    def done(self) -> bool:
+        return mp_query(self.ctx.h, self.id)
+
+    def endpoints(self):
+        return mp_get_endpoints(self.ctx.h, self.id, self.n)
+
+    def timeseries(self):
+        return mp_get_timeseries(self.ctx.h, self.id, self.n, self.n_times)
+
+    def stats(self):
+        return mp_get_stats(self.ctx.h, self.id)
+
+    def free(self):
+        mp_req_free(self.ctx.h, self.id)

@@ -1,0 +1,74 @@
+"""Shared GPU-test helpers: run the CUDA path through the C ABI and compare
+it with the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2302_13590_gb300 import mp
+
+KEYS_EXACT = ("status", "cell", "steps", "exit_face", "hash")
+
+
+def gpu_run(ctx, fh, *, release=None, cells=None, frac=None, t0=None, times=None, t_stop=np.inf,
+            precision=mp.PREC_FP64, schedule=mp.SCHED_DYNAMIC, max_steps=0, block=0, steps_per_fetch=0,
+            mode=None):
+    """Release + track through the C ABI; returns (endpoints dict, timeseries or None, stats)."""
+    if release is not None:
+        gh = mp.mp_release_group(ctx.h, fh, n=release.n, lo=release.lo, hi=release.hi, seed=release.seed,
+                                 id_offset=release.id_offset)
+    else:
+        gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac, t0=t0)
+    if mode is None:
+        mode = mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if times is not None else 0)
+    req = ctx.track(gh, mode=mode, precision=precision, schedule=schedule, times=times, t_stop=t_stop,
+                    max_steps=max_steps, block=block, steps_per_fetch=steps_per_fetch)
+    req.wait()
+    ep = req.endpoints()
+    ts = req.timeseries() if req.n_times else None
+    st = req.stats()
+    req.free()
+    mp.mp_group_free(gh)
+    return ep, ts, st
+
+
+def release_state(ctx, fh, release):
+    """The device release as a state dict (a zero-time run reports the release)."""
+    ep, _, _ = gpu_run(ctx, fh, release=release, t_stop=0.0, schedule=mp.SCHED_STATIC)
+    st = np.where(ep["status"] == mp.ST_TIME, mp.ST_ACTIVE, ep["status"]).astype(np.uint8)
+    return dict(cell=ep["cell"], px=ep["px"], py=ep["py"], pz=ep["pz"], t=np.zeros(ep["cell"].size), status=st)
+
+
+def rel_err(a, b, scale=None):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    d = np.abs(a - b)
+    s = np.abs(b) if scale is None else scale
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(d == 0, 0.0, d / np.maximum(s, 1e-300))
+
+
+def compare_fp64(ep, ref, idx=None, rtol=1e-10):
+    """FP64 parity: exact cell sequences and statuses, 1e-10 relative values."""
+    sel = slice(None) if idx is None else idx
+    for k in KEYS_EXACT:
+        a, b = ep[k][sel], ref[k]
+        bad = np.nonzero(a != b)[0]
+        assert bad.size == 0, f"{k}: {bad.size} mismatches, first {bad[:5]}: gpu {a[bad[:5]]} oracle {b[bad[:5]]}"
+    for gk, ok in (("x", "gx"), ("y", "gy"), ("z", "gz"), ("t", "t")):
+        a, b = ep[gk][sel], ref[ok]
+        fin = np.isfinite(b)
+        assert np.array_equal(np.isfinite(a), fin), gk
+        e = rel_err(a[fin], b[fin])
+        assert e.max(initial=0.0) <= rtol, f"{gk}: max rel err {e.max()}"
+
+
+def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10):
+    sel = slice(None) if idx is None else idx
+    assert np.array_equal(ts["cell"][:, sel], ref["ts_cell"])
+    assert np.array_equal(ts["status"][:, sel], ref["ts_status"])
+    for gk, ok in (("x", "ts_x"), ("y", "ts_y"), ("z", "ts_z")):
+        a, b = ts[gk][:, sel], ref[ok]
+        fin = np.isfinite(b)
+        assert np.array_equal(np.isfinite(a), fin)
+        e = rel_err(a[fin], b[fin])
+        assert e.max(initial=0.0) <= rtol, f"ts {gk}: max rel err {e.max()}"

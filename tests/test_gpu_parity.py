@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+FP64: exit-cell sequences (FNV hash), statuses, cells, step counts and exit
+faces bit-exact; positions and travel times within 1e-10 relative.  Mixed
+precision: travel time within 1e-5 relative and endpoint within 1e-4 cell
+widths for particles whose cell sequence matches; the fraction of particles
+whose sequence diverges at near-ties is reported and bounded.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_13590_gb300 import inputs as I
+from paper_2302_13590_gb300 import mp
+from tests import gpu_common as G
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch  # noqa: F401  (same CUDA runtime as the rest of the process)
+    c = mp.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def cfg1(ctx):
+    w = I.workload("cfg1")
+    return w, ctx.field(w.field)
+
+
+@pytest.fixture(scope="module")
+def cfg2(ctx):
+    w = I.workload("cfg2")
+    return w, ctx.field(w.field)
+
+
+def test_release_box_bit_exact(ctx, cfg1):
+    w, fh = cfg1
+    g = G.release_state(ctx, fh, w.release)
+    r = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+    for k in ("cell", "px", "py", "pz", "status"):
+        assert np.array_equal(g[k], r[k]), k
+
+
+def test_release_box_ragged_and_outside(ctx):
+    f = I.random_box_field(3, 5, 7, seed=17, n_inactive=2, n_wells=1)
+    fh = ctx.field(f)
+    Lx, Ly, Lz = f.extent
+    for n in (1, 31, 33, 1000):
+        rel = I.Release(n, (-1.0, 0.0, 0.0), (Lx + 1.0, Ly, Lz), seed=99, id_offset=5)
+        g = G.release_state(ctx, fh, rel)
+        r = O.release_box(f, n, rel.lo, rel.hi, rel.seed, rel.id_offset)
+        for k in ("cell", "px", "py", "pz", "status"):
+            assert np.array_equal(g[k], r[k]), (n, k)
+    mp.mp_field_free(fh)
+
+
+@pytest.mark.parametrize("schedule", [mp.SCHED_STATIC, mp.SCHED_DYNAMIC])
+def test_fp64_cfg1_full(ctx, cfg1, schedule):
+    w, fh = cfg1
+    ep, ts, st = G.gpu_run(ctx, fh, release=w.release, times=w.times, schedule=schedule)
+    ostate = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+    ref = O.track(w.field, ostate, times=w.times)
+    G.compare_fp64(ep, ref)
+    G.compare_timeseries_fp64(ts, ref)
+    assert st["cell_steps"] == int(ref["steps"].sum())
+    assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
+    assert st["device_error"] == 0
+
+
+@pytest.mark.parametrize("seed,n,schedule,t_frac", [(1, 1, mp.SCHED_STATIC, None), (2, 37, mp.SCHED_DYNAMIC, None),
+                                                    (3, 1000, mp.SCHED_DYNAMIC, 0.5), (4, 257, mp.SCHED_STATIC, 0.3),
+                                                    (5, 4099, mp.SCHED_DYNAMIC, None)])
+def test_fp64_random_fields(ctx, seed, n, schedule, t_frac):
+    f = I.random_box_field(4, 9, 12, seed=300 + seed, lnk_var=2.0, n_wells=2, n_inactive=3)
+    fh = ctx.field(f)
+    cells, frac = I.explicit_particles(f, n, seed=seed, cols=(1, 6))
+    st0 = O.release_explicit(f, cells, frac)
+    full = O.track(f, st0)
+    t_stop = np.inf if t_frac is None else float(np.quantile(full["t"], t_frac))
+    times = np.quantile(full["t"], [0.0, 0.05, 0.2, 0.5, 0.8, 0.99]) * 1.01
+    ref = O.track(f, st0, t_stop=t_stop, times=times)
+    ep, ts, stats = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, t_stop=t_stop, schedule=schedule)
+    G.compare_fp64(ep, ref)
+    G.compare_timeseries_fp64(ts, ref)
+    for k in ("px", "py", "pz"):
+        assert np.max(G.rel_err(ep[k], ref[k], scale=1.0)) <= 1e-10
+    mp.mp_field_free(fh)
+
+
+def test_fp64_edge_cases(ctx):
+    f = I.random_box_field(2, 4, 6, seed=77, n_wells=1, n_inactive=1)
+    fh = ctx.field(f)
+    ib = f.ibound.reshape(-1)
+    sink = int(np.nonzero(ib == 2)[0][0])
+    ch = int(np.nonzero(ib == -1)[0][0])
+    inact = int(np.nonzero(ib == 0)[0][0])
+    act = int(np.nonzero(ib == 1)[0][0])
+    cells = np.array([sink, ch, inact, act, -5, f.ncell + 3, act, act], np.int32)
+    frac = np.array([[0.5] * 3, [0.5] * 3, [0.5] * 3, [0.0, 0.0, 0.0], [0.5] * 3, [0.5] * 3, [1.0, 1.0, 1.0],
+                     [0.3, 0.7, 0.2]])
+    st0 = O.release_explicit(f, cells, frac)
+    for t_stop, max_steps in ((np.inf, 0), (0.0, 0), (np.inf, 2), (1e3, 0)):
+        ref = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, times=[0.0, 10.0, 1e4])
+        for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+            ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, max_steps=max_steps,
+                                  times=[0.0, 10.0, 1e4], schedule=sch)
+            G.compare_fp64(ep, ref)
+            G.compare_timeseries_fp64(ts, ref)
+    # an empty group
+    ep, ts, st = G.gpu_run(ctx, fh, cells=np.zeros(0, np.int32), frac=np.zeros((0, 3)))
+    assert ep["cell"].size == 0 and st["cell_steps"] == 0
+    mp.mp_field_free(fh)
+
+
+def test_fp64_no_exit_divide(ctx):
+    """Flow diverging inside a cell: no face reachable (NO_EXIT), and with a
+    stop time the particle keeps moving inside the cell."""
+    f = H.single_cell_field(-2e-4, 3e-4, d=(2.0, 3.0, 1.5), por=0.25)
+    fh = ctx.field(f)
+    cells = np.zeros(3, np.int32)
+    frac = np.array([[0.5, 0.5, 0.5], [0.2, 0.1, 0.9], [0.9, 0.5, 0.5]])
+    st0 = O.release_explicit(f, cells, frac)
+    for t_stop in (np.inf, 5e3):
+        ref = O.track(f, st0, t_stop=t_stop, times=[1.0, 1e3, 4e3])
+        ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, times=[1.0, 1e3, 4e3])
+        G.compare_fp64(ep, ref)
+        G.compare_timeseries_fp64(ts, ref)
+    mp.mp_field_free(fh)
+
+
+def test_fp64_cfg2_full_size_sampled(ctx, cfg2):
+    """The benchmark's workload and launch configuration at full size
+    (1e6 particles, endpoint + 50 output times, dynamic schedule), checked on
+    a random sample of particles that the oracle tracks one by one."""
+    w, fh = cfg2
+    ep, ts, st = G.gpu_run(ctx, fh, release=w.release, times=w.times, schedule=mp.SCHED_DYNAMIC)
+    n = w.release.n
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.choice(n, 20000, replace=False), np.arange(64), np.arange(n - 64, n)]))
+    full_state = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
+    ref = O.track(w.field, O.subset(full_state, idx), times=w.times)
+    G.compare_fp64(ep, ref, idx=idx)
+    G.compare_timeseries_fp64(ts, ref, idx=idx)
+    # whole-run invariants at full size
+    assert st["cell_steps"] == int(ep["steps"].astype(np.uint64).sum())
+    assert st["n_status"] == np.bincount(ep["status"], minlength=8).tolist()
+    assert st["device_error"] == 0
+    assert np.all(ep["status"] != mp.ST_ACTIVE)
+
+
+def test_static_equals_dynamic(ctx, cfg2):
+    w, fh = cfg2
+    rel = I.Release(100_003, w.release.lo, w.release.hi, w.release.seed)
+    a, ta, _ = G.gpu_run(ctx, fh, release=rel, times=w.times[:10], schedule=mp.SCHED_STATIC)
+    for S in (1, 4, 16):
+        b, tb, _ = G.gpu_run(ctx, fh, release=rel, times=w.times[:10], schedule=mp.SCHED_DYNAMIC, steps_per_fetch=S)
+        for k in a:
+            assert np.array_equal(a[k], b[k], equal_nan=True), k
+        assert np.array_equal(ta.view(np.uint8), tb.view(np.uint8))
+
+
+def test_update_group_resume(ctx, cfg1):
+    """Resume == continue: the group's state after a stop at T1 continues to T2
+    exactly as the oracle continues its own state."""
+    w, fh = cfg1
+    gh = mp.mp_release_group(ctx.h, fh, n=w.release.n, lo=w.release.lo, hi=w.release.hi, seed=w.release.seed)
+    T1, T2 = 0.2 * w.t_adv, 0.7 * w.t_adv
+    r1 = ctx.track(gh, t_stop=T1, flags=mp.TRACK_UPDATE_GROUP)
+    r1.wait()
+    r2 = ctx.track(gh, t_stop=T2, flags=mp.TRACK_UPDATE_GROUP)
+    ep = r2.endpoints()
+    s0 = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+    a = O.track(w.field, s0, t_stop=T1)
+    mid = dict(cell=a["cell"], px=a["px"], py=a["py"], pz=a["pz"], t=a["t"],
+               status=np.where(a["status"] == O.ST_TIME, O.ST_ACTIVE, a["status"]).astype(np.uint8))
+    b = O.track(w.field, mid, t_stop=T2)
+    for k in ("status", "cell", "steps", "exit_face"):
+        assert np.array_equal(ep[k], b[k]), k
+    assert np.max(G.rel_err(ep["t"], b["t"])) <= 1e-10
+    assert np.max(G.rel_err(ep["x"], b["gx"])) <= 1e-10
+    r1.free()
+    r2.free()
+    mp.mp_group_free(gh)
+
+
+def _mixed_report(ep, ref, field):
+    same = ep["hash"] == ref["hash"]
+    frac_div = 1.0 - same.mean()
+    fin = same & np.isfinite(ref["t"]) & (ref["t"] > 0)
+    t_err = G.rel_err(ep["t"][fin], ref["t"][fin])
+    c = ref["cell"][same]
+    j, i, k = c % field.ncol, (c // field.ncol) % field.nrow, c // (field.ncol * field.nrow)
+    ex = np.abs(ep["x"][same] - ref["gx"][same]) / field.delr[j]
+    ey = np.abs(ep["y"][same] - ref["gy"][same]) / field.delc[i]
+    ez = np.abs(ep["z"][same] - ref["gz"][same]) / field.dz[k]
+    pos_err = np.maximum(ex, np.maximum(ey, ez))
+    return frac_div, t_err.max(initial=0.0), pos_err.max(initial=0.0)
+
+
+def test_mixed_cfg1(ctx, cfg1):
+    w, fh = cfg1
+    ep, ts, _ = G.gpu_run(ctx, fh, release=w.release, times=w.times, precision=mp.PREC_MIXED)
+    s0 = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+    ref = O.track(w.field, s0, times=w.times)
+    frac_div, t_err, pos_err = _mixed_report(ep, ref, w.field)
+    print(f"mixed cfg1: divergent {frac_div:.2e} t_err {t_err:.2e} pos_err {pos_err:.2e}")
+    assert frac_div <= 0.01
+    assert t_err <= 1e-5
+    assert pos_err <= 1e-4
+    assert np.mean(ep["status"] == ref["status"]) >= 0.99
+
+
+def test_mixed_cfg2_sampled(ctx, cfg2):
+    w, fh = cfg2
+    ep, ts, st = G.gpu_run(ctx, fh, release=w.release, times=w.times, precision=mp.PREC_MIXED)
+    n = w.release.n
+    idx = np.sort(np.random.default_rng(2).choice(n, 10000, replace=False))
+    s0 = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
+    ref = O.track(w.field, O.subset(s0, idx), times=w.times)
+    sub = {k: v[idx] for k, v in ep.items()}
+    frac_div, t_err, pos_err = _mixed_report(sub, ref, w.field)
+    print(f"mixed cfg2: divergent {frac_div:.2e} t_err {t_err:.2e} pos_err {pos_err:.2e}")
+    assert frac_div <= 0.01
+    assert t_err <= 1e-5
+    assert pos_err <= 1e-4
+    assert st["device_error"] == 0
+
+
+def test_field_validation_errors(ctx):
+    f = I.random_box_field(2, 3, 4, seed=5)
+    bad = H.SimpleField(f.nlay, f.nrow, f.ncol, f.delr, f.delc, f.dz, f.origin, f.qx.copy(), f.qy, f.qz,
+                        f.porosity.copy(), f.ibound.copy())
+    bad.qx[0, 0, 1] = np.nan
+    with pytest.raises(mp.MPError) as e:
+        ctx.field(bad)
+    assert e.value.code == -3
+    bad.qx[0, 0, 1] = 0.0
+    bad.porosity[0, 1, 1] = 0.0
+    with pytest.raises(mp.MPError) as e:
+        ctx.field(bad)
+    assert e.value.code == -3
+    bad.porosity[0, 1, 1] = 0.3
+    bad.ibound[0, 1, 1] = 5
+    with pytest.raises(mp.MPError) as e:
+        ctx.field(bad)
+    assert e.value.code == -1
+
+
+def test_wait_is_bounded(ctx, cfg2):
+    """mp_wait returns MP_ERR_TIMEOUT instead of blocking; the request then
+    finishes normally."""
+    w, fh = cfg2
+    gh = ctx.release_box(fh, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+    r = ctx.track(gh, precision=mp.PREC_FP64, schedule=mp.SCHED_STATIC)
+    with pytest.raises(mp.MPError) as e:
+        r.wait(timeout_us=0)
+    assert e.value.code == mp.MP_ERR_TIMEOUT
+    r.wait()
+    assert r.stats()["device_error"] == 0
+    r.free()
+    mp.mp_group_free(gh)
