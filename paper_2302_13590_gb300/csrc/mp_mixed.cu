@@ -8,7 +8,8 @@
 //   t_a = (d / u_p) g(z), z = A d / u_p, g(z) = ln(1 + z) / z,
 //   xi(t) = xi + u_p t h(A t), h(w) = (e^w - 1) / w.
 // g and h use their Taylor series for |z|, |w| < 2^-7 (exact to below FP32
-// rounding there, and free of the 0/0 at z = 0).  The cumulative travel time,
+// rounding there, and free of the 0/0 at z = 0); for z < -1/2 g takes
+// ln(u_exit / u_p) / z, which keeps full FP32 accuracy as u_exit -> 0.  The cumulative travel time,
 // the stop-time and output-time comparisons, and every global position are
 // FP64.  Compiled with FMA contraction on (FP32 results are compared with the
 // FP64 oracle within tolerances, not bit for bit).
@@ -39,9 +40,13 @@ struct MixEngine {
 
     static constexpr float SMALL = 0.0078125f;  // 2^-7
 
-    __device__ __forceinline__ static float g_log1p_over(float z)
+    // g(z) = ln(1 + z) / z, with 1 + z = u_exit / u_p.  Near z = -1 (exit
+    // face almost stagnant) 1 + z cancels in FP32, so the ratio of the two
+    // stored velocities is logged directly there.
+    __device__ __forceinline__ static float g_log1p_over(float z, float ratio)
     {
         if (fabsf(z) < SMALL) return 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
+        if (z < -0.5f) return logf(ratio) / z;
         return log1pf(z) / z;
     }
     __device__ __forceinline__ static float h_expm1_over(float w)
@@ -52,12 +57,12 @@ struct MixEngine {
 
     __device__ __forceinline__ static float exit_time(float u1, float u2, float A, float up, float xi, int& face)
     {
-        float d;
-        if (up > 0.0f && u2 > 0.0f) { face = 1; d = 1.0f - xi; }
-        else if (up < 0.0f && u1 < 0.0f) { face = -1; d = -xi; }
+        float d, ue;
+        if (up > 0.0f && u2 > 0.0f) { face = 1; d = 1.0f - xi; ue = u2; }
+        else if (up < 0.0f && u1 < 0.0f) { face = -1; d = -xi; ue = u1; }
         else { face = 0; return CUDART_INF_F; }
         const float t1 = d / up;
-        return t1 * g_log1p_over(A * t1);
+        return t1 * g_log1p_over(A * t1, ue / up);
     }
 
     __device__ __forceinline__ static float move(float A, float up, float xi, float dt)

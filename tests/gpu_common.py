@@ -47,28 +47,42 @@ def rel_err(a, b, scale=None):
         return np.where(d == 0, 0.0, d / np.maximum(s, 1e-300))
 
 
-def compare_fp64(ep, ref, idx=None, rtol=1e-10):
-    """FP64 parity: exact cell sequences and statuses, 1e-10 relative values."""
+def dmin(f):
+    """Smallest cell size per axis of a field."""
+    return (float(np.min(f.delr)), float(np.min(f.delc)), float(np.min(f.dz)))
+
+
+def pos_scale(field, b):
+    """Scale for position errors along one axis: the larger of |coordinate|
+    and the smallest cell size of that axis (a relative error of a coordinate
+    near the origin says nothing)."""
+    return np.maximum(np.abs(b), b * 0 + field)
+
+
+def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
+    """FP64 parity: exact cell sequences and statuses; travel times within
+    rtol relative; positions within rtol relative to max(|x|, min cell size)."""
     sel = slice(None) if idx is None else idx
     for k in KEYS_EXACT:
         a, b = ep[k][sel], ref[k]
         bad = np.nonzero(a != b)[0]
         assert bad.size == 0, f"{k}: {bad.size} mismatches, first {bad[:5]}: gpu {a[bad[:5]]} oracle {b[bad[:5]]}"
-    for gk, ok in (("x", "gx"), ("y", "gy"), ("z", "gz"), ("t", "t")):
+    for ax, (gk, ok) in enumerate((("x", "gx"), ("y", "gy"), ("z", "gz"), ("t", "t"))):
         a, b = ep[gk][sel], ref[ok]
         fin = np.isfinite(b)
         assert np.array_equal(np.isfinite(a), fin), gk
-        e = rel_err(a[fin], b[fin])
+        scale = None if gk == "t" else pos_scale(dmin[ax], b[fin])
+        e = rel_err(a[fin], b[fin], scale=scale)
         assert e.max(initial=0.0) <= rtol, f"{gk}: max rel err {e.max()}"
 
 
-def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10):
+def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
     sel = slice(None) if idx is None else idx
     assert np.array_equal(ts["cell"][:, sel], ref["ts_cell"])
     assert np.array_equal(ts["status"][:, sel], ref["ts_status"])
-    for gk, ok in (("x", "ts_x"), ("y", "ts_y"), ("z", "ts_z")):
+    for ax, (gk, ok) in enumerate((("x", "ts_x"), ("y", "ts_y"), ("z", "ts_z"))):
         a, b = ts[gk][:, sel], ref[ok]
         fin = np.isfinite(b)
         assert np.array_equal(np.isfinite(a), fin)
-        e = rel_err(a[fin], b[fin])
+        e = rel_err(a[fin], b[fin], scale=pos_scale(dmin[ax], b[fin]))
         assert e.max(initial=0.0) <= rtol, f"ts {gk}: max rel err {e.max()}"

@@ -67,8 +67,8 @@ def test_fp64_cfg1_full(ctx, cfg1, schedule):
     ep, ts, st = G.gpu_run(ctx, fh, release=w.release, times=w.times, schedule=schedule)
     ostate = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
     ref = O.track(w.field, ostate, times=w.times)
-    G.compare_fp64(ep, ref)
-    G.compare_timeseries_fp64(ts, ref)
+    G.compare_fp64(ep, ref, dmin=G.dmin(w.field))
+    G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(w.field))
     assert st["cell_steps"] == int(ref["steps"].sum())
     assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
     assert st["device_error"] == 0
@@ -87,8 +87,8 @@ def test_fp64_random_fields(ctx, seed, n, schedule, t_frac):
     times = np.quantile(full["t"], [0.0, 0.05, 0.2, 0.5, 0.8, 0.99]) * 1.01
     ref = O.track(f, st0, t_stop=t_stop, times=times)
     ep, ts, stats = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, t_stop=t_stop, schedule=schedule)
-    G.compare_fp64(ep, ref)
-    G.compare_timeseries_fp64(ts, ref)
+    G.compare_fp64(ep, ref, dmin=G.dmin(f))
+    G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
     for k in ("px", "py", "pz"):
         assert np.max(G.rel_err(ep[k], ref[k], scale=1.0)) <= 1e-10
     mp.mp_field_free(fh)
@@ -111,8 +111,8 @@ def test_fp64_edge_cases(ctx):
         for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
             ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, max_steps=max_steps,
                                   times=[0.0, 10.0, 1e4], schedule=sch)
-            G.compare_fp64(ep, ref)
-            G.compare_timeseries_fp64(ts, ref)
+            G.compare_fp64(ep, ref, dmin=G.dmin(f))
+            G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
     # an empty group
     ep, ts, st = G.gpu_run(ctx, fh, cells=np.zeros(0, np.int32), frac=np.zeros((0, 3)))
     assert ep["cell"].size == 0 and st["cell_steps"] == 0
@@ -130,8 +130,8 @@ def test_fp64_no_exit_divide(ctx):
     for t_stop in (np.inf, 5e3):
         ref = O.track(f, st0, t_stop=t_stop, times=[1.0, 1e3, 4e3])
         ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, times=[1.0, 1e3, 4e3])
-        G.compare_fp64(ep, ref)
-        G.compare_timeseries_fp64(ts, ref)
+        G.compare_fp64(ep, ref, dmin=G.dmin(f))
+        G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
     mp.mp_field_free(fh)
 
 
@@ -146,8 +146,8 @@ def test_fp64_cfg2_full_size_sampled(ctx, cfg2):
     idx = np.unique(np.concatenate([rng.choice(n, 20000, replace=False), np.arange(64), np.arange(n - 64, n)]))
     full_state = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
     ref = O.track(w.field, O.subset(full_state, idx), times=w.times)
-    G.compare_fp64(ep, ref, idx=idx)
-    G.compare_timeseries_fp64(ts, ref, idx=idx)
+    G.compare_fp64(ep, ref, idx=idx, dmin=G.dmin(w.field))
+    G.compare_timeseries_fp64(ts, ref, idx=idx, dmin=G.dmin(w.field))
     # whole-run invariants at full size
     assert st["cell_steps"] == int(ep["steps"].astype(np.uint64).sum())
     assert st["n_status"] == np.bincount(ep["status"], minlength=8).tolist()
@@ -201,6 +201,11 @@ def _mixed_report(ep, ref, field):
     ey = np.abs(ep["y"][same] - ref["gy"][same]) / field.delc[i]
     ez = np.abs(ep["z"][same] - ref["gz"][same]) / field.dz[k]
     pos_err = np.maximum(ex, np.maximum(ey, ez))
+    if t_err.size:
+        w = np.argsort(t_err)[-3:]
+        ids = np.nonzero(fin)[0][w]
+        print("worst t:", [(int(q), float(ref["t"][q]), float(ep["t"][q]), int(ref["steps"][q]), int(ref["status"][q]))
+                           for q in ids])
     return frac_div, t_err.max(initial=0.0), pos_err.max(initial=0.0)
 
 
