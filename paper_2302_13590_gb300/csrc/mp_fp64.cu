@@ -219,33 +219,45 @@ struct F64Engine {
         int kn;
         int st;
         int ef;
+        double tev;  // next output time or the stop time, whichever is first
     };
 
-    // exit time along one axis (face = +1, -1, or 0 when no face is reachable)
+    // Exit time along one axis (face = +1, -1, or 0 when no face is reachable).
+    // Written without branches around the divisions and log1p so that the
+    // lanes of a warp stay converged; lanes with no reachable face compute on
+    // harmless operands and select +inf.  The values equal those of the
+    // branchy form (t1 = d / vp, z = A t1, t1 when z == 0 else
+    // t1 * (log1p(z) / z)).
     __device__ __forceinline__ static double exit_time(double v1, double v2, double A, double D, double vp,
                                                        double pp, int& face)
     {
-        double d;
-        if (vp > 0.0 && v2 > 0.0) { face = 1; d = D - pp; }
-        else if (vp < 0.0 && v1 < 0.0) { face = -1; d = -pp; }
-        else { face = 0; return CUDART_INF; }
-        const double t1 = d / vp;
+        const bool up = vp > 0.0 && v2 > 0.0;
+        const bool dn = vp < 0.0 && v1 < 0.0;
+        face = up ? 1 : (dn ? -1 : 0);
+        const double d = up ? D - pp : -pp;
+        const double t1 = d / (face ? vp : 1.0);
         const double z = A * t1;
-        if (z == 0.0) return t1;
-        return t1 * (log1p(z) / z);
+        const bool lin = (z == 0.0) || !face;
+        const double zs = lin ? 1.0 : z;
+        const double g = log1p(zs) / zs;
+        const double te = (z == 0.0) ? t1 : t1 * g;
+        return face ? te : CUDART_INF;
     }
 
     // analytic motion along one axis for a time dt, clamped to the cell
+    // (the same values as: s == 0 -> pp; w == 0 -> factor 1)
     __device__ __forceinline__ static double move(double A, double D, double vp, double pp, double dt)
     {
         const double s = vp * dt;
-        if (s == 0.0) return pp;
         const double w = A * dt;
-        const double fct = (w == 0.0) ? 1.0 : expm1(w) / w;
+        const bool lin = (w == 0.0);
+        const double ws = lin ? 1.0 : w;
+        const double e = expm1(ws) / ws;
+        const double fct = lin ? 1.0 : e;
         double pn = pp + s * fct;
         if (pn < 0.0) pn = 0.0;
         if (pn > D) pn = D;
-        return pn;
+        return (s == 0.0) ? pp : pn;
     }
 
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
@@ -257,6 +269,13 @@ struct F64Engine {
     __device__ __forceinline__ double gx(const State& s) const { return __ldg(f.xf + s.j) + s.x0; }
     __device__ __forceinline__ double gy(const State& s) const { return __ldg(f.yf + s.i) + s.x1; }
     __device__ __forceinline__ double gz(const State& s) const { return __ldg(f.zf + s.k) + s.x2; }
+
+    // next time at which the step loop must leave its fast path
+    __device__ __forceinline__ double next_event(const State& s) const
+    {
+        const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
+        return fmin(tk, p.t_stop);
+    }
 
     template <bool TS>
     __device__ __forceinline__ void load(long long q, State& s) const
@@ -285,12 +304,14 @@ struct F64Engine {
                 s.kn++;
             }
         }
+        // a particle that starts at or after the stop time takes no step
+        if (s.st == MP_ST_ACTIVE && s.t >= p.t_stop) s.st = MP_ST_TIME;
+        s.tev = TS ? next_event(s) : p.t_stop;
     }
 
     template <bool TS>
     __device__ __forceinline__ void step(long long q, State& s) const
     {
-        if (s.t >= p.t_stop) { s.st = MP_ST_TIME; return; }
         if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
         if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
             atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
@@ -317,84 +338,86 @@ struct F64Engine {
         if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
         if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
         s.steps++;
-        if (ax < 0 && !(p.t_stop < CUDART_INF)) {
-            if (TS) {
-                while (s.kn < p.n_times) {
-                    const double tau = __ldg(o.times + s.kn) - s.t;
-                    record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
-                           __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
-                           __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_NO_EXIT);
-                    s.kn++;
+        const double t_end = s.t + tmin;
+        if (ax < 0 || t_end >= s.tev) {
+            // slow path: no exit, the stop time, or an output time in this step
+            if (ax < 0 && !(p.t_stop < CUDART_INF)) {
+                if (TS) {
+                    while (s.kn < p.n_times) {
+                        const double tau = __ldg(o.times + s.kn) - s.t;
+                        record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
+                               __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
+                               __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_NO_EXIT);
+                        s.kn++;
+                    }
                 }
+                s.st = MP_ST_NO_EXIT;
+                return;
             }
-            s.st = MP_ST_NO_EXIT;
-            return;
-        }
-        if (ax < 0 || s.t + tmin >= p.t_stop) {
-            const double dt = p.t_stop - s.t;
+            if (ax < 0 || t_end >= p.t_stop) {
+                const double dt = p.t_stop - s.t;
+                if (TS) {
+                    while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                        const double tau = __ldg(o.times + s.kn) - s.t;
+                        record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
+                               __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
+                               __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
+                        s.kn++;
+                    }
+                }
+                s.x0 = move(Ax, D0, vp0, s.x0, dt);
+                s.x1 = move(Ay, D1, vp1, s.x1, dt);
+                s.x2 = move(Az, D2, vp2, s.x2, dt);
+                s.t = p.t_stop;
+                s.st = MP_ST_TIME;
+                return;
+            }
             if (TS) {
-                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
                     const double tau = __ldg(o.times + s.kn) - s.t;
                     record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
                            __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
                            __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
                     s.kn++;
                 }
+                s.tev = next_event(s);
             }
-            s.x0 = move(Ax, D0, vp0, s.x0, dt);
-            s.x1 = move(Ay, D1, vp1, s.x1, dt);
-            s.x2 = move(Az, D2, vp2, s.x2, dt);
-            s.t = p.t_stop;
-            s.st = MP_ST_TIME;
-            return;
         }
+        // displacement to the exit face: every axis moves by the analytic
+        // formula (uniform across lanes), then the exit axis is put on its face
         const double dt = tmin;
-        const double t_end = s.t + dt;
-        if (TS) {
-            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
-                const double tau = __ldg(o.times + s.kn) - s.t;
-                record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
-                       __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
-                       __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
-                s.kn++;
-            }
-        }
-        int face;
-        if (ax == 0) {
-            face = f0;
-            s.x0 = face > 0 ? D0 : 0.0;
-            s.x1 = move(Ay, D1, vp1, s.x1, dt);
-            s.x2 = move(Az, D2, vp2, s.x2, dt);
-        } else if (ax == 1) {
-            face = f1;
-            s.x0 = move(Ax, D0, vp0, s.x0, dt);
-            s.x1 = face > 0 ? D1 : 0.0;
-            s.x2 = move(Az, D2, vp2, s.x2, dt);
-        } else {
-            face = f2;
-            s.x0 = move(Ax, D0, vp0, s.x0, dt);
-            s.x1 = move(Ay, D1, vp1, s.x1, dt);
-            s.x2 = face > 0 ? D2 : 0.0;
-        }
+        const double n0 = move(Ax, D0, vp0, s.x0, dt);
+        const double n1 = move(Ay, D1, vp1, s.x1, dt);
+        const double n2 = move(Az, D2, vp2, s.x2, dt);
+        const int face = ax == 0 ? f0 : (ax == 1 ? f1 : f2);
+        const double Dax = ax == 0 ? D0 : (ax == 1 ? D1 : D2);
+        const double onface = face > 0 ? Dax : 0.0;
+        s.x0 = ax == 0 ? onface : n0;
+        s.x1 = ax == 1 ? onface : n1;
+        s.x2 = ax == 2 ? onface : n2;
         s.t = t_end;
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3ULL);
-        if (cls == NB_OUTSIDE) { s.st = MP_ST_EXIT_DOMAIN; return; }
-        if (cls == NB_BOUNDARY) { s.st = MP_ST_BOUNDARY; return; }
-        if (cls == NB_SINK) { s.st = MP_ST_SINK; return; }
-        if (ax == 0) {
-            s.j += face;
-            s.c += face;
-            s.x0 = face > 0 ? 0.0 : __ldg(f.delr + s.j);
-        } else if (ax == 1) {
-            s.i += face;
-            s.c += face * f.ncol;
-            s.x1 = face > 0 ? 0.0 : __ldg(f.delc + s.i);
+        if (cls != NB_ACTIVE) {
+            s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
+            return;
+        }
+        // hand over to the neighbour; the exit coordinate enters on the shared face
+        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
+        s.j += dj;
+        s.i += di;
+        s.k += dk;
+        s.c += dj + di * f.ncol + dk * f.ncol * f.nrow;
+        if (face < 0) {
+            const double Dn = ax == 0 ? __ldg(f.delr + s.j) : (ax == 1 ? __ldg(f.delc + s.i) : __ldg(f.dz + s.k));
+            if (ax == 0) s.x0 = Dn;
+            else if (ax == 1) s.x1 = Dn;
+            else s.x2 = Dn;
         } else {
-            s.k += face;
-            s.c += face * f.ncol * f.nrow;
-            s.x2 = face > 0 ? 0.0 : __ldg(f.dz + s.k);
+            if (ax == 0) s.x0 = 0.0;
+            else if (ax == 1) s.x1 = 0.0;
+            else s.x2 = 0.0;
         }
         s.h = fnv_step(s.h, s.c);
     }

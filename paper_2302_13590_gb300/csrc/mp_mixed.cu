@@ -36,6 +36,7 @@ struct MixEngine {
         int kn;
         int st;
         int ef;
+        double tev;  // next output time or the stop time, whichever is first
     };
 
     static constexpr float SMALL = 0.0078125f;  // 2^-7
@@ -46,31 +47,36 @@ struct MixEngine {
     __device__ __forceinline__ static float g_log1p_over(float z, float ratio)
     {
         if (fabsf(z) < SMALL) return 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
-        if (z < -0.5f) return logf(ratio) / z;
-        return log1pf(z) / z;
+        if (z < -0.5f) return __fdividef(logf(ratio), z);
+        return __fdividef(log1pf(z), z);
     }
     __device__ __forceinline__ static float h_expm1_over(float w)
     {
         if (fabsf(w) < SMALL) return 1.0f + w * (0.5f + w * (1.0f / 6.0f + w * (1.0f / 24.0f + w * (1.0f / 120.0f))));
-        return expm1f(w) / w;
+        return __fdividef(expm1f(w), w);
     }
 
+    // exit time along one axis in local units; branch-free around the
+    // transcendental so that a warp's lanes stay converged (no-exit lanes
+    // compute on harmless operands and select +inf)
     __device__ __forceinline__ static float exit_time(float u1, float u2, float A, float up, float xi, int& face)
     {
-        float d, ue;
-        if (up > 0.0f && u2 > 0.0f) { face = 1; d = 1.0f - xi; ue = u2; }
-        else if (up < 0.0f && u1 < 0.0f) { face = -1; d = -xi; ue = u1; }
-        else { face = 0; return CUDART_INF_F; }
-        const float t1 = d / up;
-        return t1 * g_log1p_over(A * t1, ue / up);
+        const bool fw = up > 0.0f && u2 > 0.0f;
+        const bool bw = up < 0.0f && u1 < 0.0f;
+        face = fw ? 1 : (bw ? -1 : 0);
+        const float d = fw ? 1.0f - xi : -xi;
+        const float ue = fw ? u2 : u1;
+        const float ups = face ? up : 1.0f;
+        const float t1 = __fdividef(d, ups);
+        const float g = g_log1p_over(A * t1, __fdividef(ue, ups));
+        return face ? t1 * g : CUDART_INF_F;
     }
 
     __device__ __forceinline__ static float move(float A, float up, float xi, float dt)
     {
         const float s = up * dt;
-        if (s == 0.0f) return xi;
-        const float xn = xi + s * h_expm1_over(A * dt);
-        return fminf(fmaxf(xn, 0.0f), 1.0f);
+        const float xn = fminf(fmaxf(xi + s * h_expm1_over(A * dt), 0.0f), 1.0f);
+        return s == 0.0f ? xi : xn;
     }
 
     __device__ __forceinline__ double gx(const State& s, float xi) const
@@ -90,6 +96,12 @@ struct MixEngine {
                                            int st) const
     {
         store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
+    }
+
+    __device__ __forceinline__ double next_event(const State& s) const
+    {
+        const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
+        return fmin(tk, p.t_stop);
     }
 
     template <bool TS>
@@ -122,12 +134,13 @@ struct MixEngine {
                 s.kn++;
             }
         }
+        if (s.st == MP_ST_ACTIVE && s.t >= p.t_stop) s.st = MP_ST_TIME;
+        s.tev = TS ? next_event(s) : p.t_stop;
     }
 
     template <bool TS>
     __device__ __forceinline__ void step(long long q, State& s) const
     {
-        if (s.t >= p.t_stop) { s.st = MP_ST_TIME; return; }
         if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
         if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
             atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
@@ -150,82 +163,73 @@ struct MixEngine {
         if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
         if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
         s.steps++;
-        if (ax < 0 && !(p.t_stop < CUDART_INF)) {
-            if (TS) {
-                while (s.kn < p.n_times) {
-                    const float tau = (float)(__ldg(o.times + s.kn) - s.t);
-                    record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
-                           gz(s, move(Az, up2, s.x2, tau)), MP_ST_NO_EXIT);
-                    s.kn++;
-                }
-            }
-            s.st = MP_ST_NO_EXIT;
-            return;
-        }
         const double t_end = s.t + (double)tmin;
-        if (ax < 0 || t_end >= p.t_stop) {
-            const float dt = (float)(p.t_stop - s.t);
+        if (ax < 0 || t_end >= s.tev) {
+            if (ax < 0 && !(p.t_stop < CUDART_INF)) {
+                if (TS) {
+                    while (s.kn < p.n_times) {
+                        const float tau = (float)(__ldg(o.times + s.kn) - s.t);
+                        record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
+                               gz(s, move(Az, up2, s.x2, tau)), MP_ST_NO_EXIT);
+                        s.kn++;
+                    }
+                }
+                s.st = MP_ST_NO_EXIT;
+                return;
+            }
+            if (ax < 0 || t_end >= p.t_stop) {
+                const float dt = (float)(p.t_stop - s.t);
+                if (TS) {
+                    while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                        const float tau = (float)(__ldg(o.times + s.kn) - s.t);
+                        record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
+                               gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
+                        s.kn++;
+                    }
+                }
+                s.x0 = move(Ax, up0, s.x0, dt);
+                s.x1 = move(Ay, up1, s.x1, dt);
+                s.x2 = move(Az, up2, s.x2, dt);
+                s.t = p.t_stop;
+                s.st = MP_ST_TIME;
+                return;
+            }
             if (TS) {
-                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
                     const float tau = (float)(__ldg(o.times + s.kn) - s.t);
                     record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
                            gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
                     s.kn++;
                 }
+                s.tev = next_event(s);
             }
-            s.x0 = move(Ax, up0, s.x0, dt);
-            s.x1 = move(Ay, up1, s.x1, dt);
-            s.x2 = move(Az, up2, s.x2, dt);
-            s.t = p.t_stop;
-            s.st = MP_ST_TIME;
-            return;
         }
         const float dt = tmin;
-        if (TS) {
-            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
-                const float tau = (float)(__ldg(o.times + s.kn) - s.t);
-                record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
-                       gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
-                s.kn++;
-            }
-        }
-        int face;
-        if (ax == 0) {
-            face = f0;
-            s.x0 = face > 0 ? 1.0f : 0.0f;
-            s.x1 = move(Ay, up1, s.x1, dt);
-            s.x2 = move(Az, up2, s.x2, dt);
-        } else if (ax == 1) {
-            face = f1;
-            s.x0 = move(Ax, up0, s.x0, dt);
-            s.x1 = face > 0 ? 1.0f : 0.0f;
-            s.x2 = move(Az, up2, s.x2, dt);
-        } else {
-            face = f2;
-            s.x0 = move(Ax, up0, s.x0, dt);
-            s.x1 = move(Ay, up1, s.x1, dt);
-            s.x2 = face > 0 ? 1.0f : 0.0f;
-        }
+        const float n0 = move(Ax, up0, s.x0, dt);
+        const float n1 = move(Ay, up1, s.x1, dt);
+        const float n2 = move(Az, up2, s.x2, dt);
+        const int face = ax == 0 ? f0 : (ax == 1 ? f1 : f2);
+        const float onface = face > 0 ? 1.0f : 0.0f;
+        s.x0 = ax == 0 ? onface : n0;
+        s.x1 = ax == 1 ? onface : n1;
+        s.x2 = ax == 2 ? onface : n2;
         s.t = t_end;
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3u);
-        if (cls == NB_OUTSIDE) { s.st = MP_ST_EXIT_DOMAIN; return; }
-        if (cls == NB_BOUNDARY) { s.st = MP_ST_BOUNDARY; return; }
-        if (cls == NB_SINK) { s.st = MP_ST_SINK; return; }
-        if (ax == 0) {
-            s.j += face;
-            s.c += face;
-            s.x0 = face > 0 ? 0.0f : 1.0f;
-        } else if (ax == 1) {
-            s.i += face;
-            s.c += face * f.ncol;
-            s.x1 = face > 0 ? 0.0f : 1.0f;
-        } else {
-            s.k += face;
-            s.c += face * f.ncol * f.nrow;
-            s.x2 = face > 0 ? 0.0f : 1.0f;
+        if (cls != NB_ACTIVE) {
+            s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
+            return;
         }
+        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
+        s.j += dj;
+        s.i += di;
+        s.k += dk;
+        s.c += dj + di * f.ncol + dk * f.ncol * f.nrow;
+        const float entry = face > 0 ? 0.0f : 1.0f;
+        s.x0 = ax == 0 ? entry : s.x0;
+        s.x1 = ax == 1 ? entry : s.x1;
+        s.x2 = ax == 2 ? entry : s.x2;
         s.h = fnv_step(s.h, s.c);
     }
 
