@@ -309,79 +309,108 @@ struct F64Engine {
         s.tev = TS ? next_event(s) : p.t_stop;
     }
 
-    template <bool TS>
-    __device__ __forceinline__ void step(long long q, State& s) const
+    // per-warp queue of deferred timeseries records (structure of arrays)
+    struct RecQ {
+        double p0[RQ_CAP], p1[RQ_CAP], p2[RQ_CAP], tau[RQ_CAP];
+        long long q[RQ_CAP];
+        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP];
+    };
+
+    __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
-        if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
-        if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
-            atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
-            s.st = MP_ST_INVALID_RELEASE;
-            return;
+        Q.p0[slot] = s.x0; Q.p1[slot] = s.x1; Q.p2[slot] = s.x2;
+        Q.tau[slot] = __ldg(o.times + kk) - s.t;
+        Q.q[slot] = q;
+        Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
+        Q.kk[slot] = kk; Q.st[slot] = st;
+    }
+
+    // the position at tau after the step's start, by the motion formula on
+    // every axis (the same operations as an endpoint stop at that time)
+    __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
+    {
+        const int c = Q.c[slot], i = Q.i[slot], j = Q.j[slot], k = Q.k[slot];
+        const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
+        const double2* rp = reinterpret_cast<const double2*>(f.rec64 + c);
+        const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r3 = __ldg(rp + 3), r4 = __ldg(rp + 4);
+        const double2 r2 = __ldg(rp + 2);
+        const double v1x = r0.x, Ax = r1.x, v1y = r1.y, Ay = r2.y, v1z = r3.x, Az = r4.x;
+        const double D0 = __ldg(f.delr + j), D1 = __ldg(f.delc + i), D2 = __ldg(f.dz + k);
+        const double x = __ldg(f.xf + j) + move(Ax, D0, v1x + Ax * p0, p0, tau);
+        const double y = __ldg(f.yf + i) + move(Ay, D1, v1y + Ay * p1, p1, tau);
+        const double z = __ldg(f.zf + k) + move(Az, D2, v1z + Az * p2, p2, tau);
+        store_record(o.ts + (long long)Q.kk[slot] * p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
+    }
+
+    // One cell-step for every lane of the warp (warp-uniform call; lanes with
+    // live == false only take part in the record queue).
+    template <bool TS>
+    __device__ __forceinline__ void step(long long q, State& s, bool live, RecQ& Q, int& qcount) const
+    {
+        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
+        int path = P_NONE;
+        int m = 0;
+        double v1x = 0, Ax = 0, v1y = 0, Ay = 0, v1z = 0, Az = 0, D0 = 1, D1 = 1, D2 = 1;
+        double vp0 = 0, vp1 = 0, vp2 = 0, tmin = 0, t_end = 0;
+        int f0 = 0, f1 = 0, f2 = 0, ax = -1;
+        unsigned long long nb = 0;
+        if (live) {
+            if ((long long)s.steps >= p.max_steps) {
+                s.st = MP_ST_STEP_CAP;
+            } else if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
+                atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
+                s.st = MP_ST_INVALID_RELEASE;
+            } else {
+                const double2* rp = reinterpret_cast<const double2*>(f.rec64 + s.c);
+                const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
+                              r4 = __ldg(rp + 4);
+                v1x = r0.x; Ax = r1.x; v1y = r1.y; Ay = r2.y; v1z = r3.x; Az = r4.x;
+                const double v2x = r0.y, v2y = r2.x, v2z = r3.y;
+                nb = (unsigned long long)__double_as_longlong(r4.y);
+                D0 = __ldg(f.delr + s.j); D1 = __ldg(f.delc + s.i); D2 = __ldg(f.dz + s.k);
+                vp0 = v1x + Ax * s.x0;
+                vp1 = v1y + Ay * s.x1;
+                vp2 = v1z + Az * s.x2;
+                const double te0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, f0);
+                const double te1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, f1);
+                const double te2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, f2);
+                tmin = CUDART_INF;
+                if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
+                if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
+                if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
+                s.steps++;
+                t_end = s.t + tmin;
+                if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                else path = P_CROSS;
+                if (TS && (ax < 0 || t_end >= s.tev)) {
+                    const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
+                    int kk = s.kn;
+                    while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                    m = kk - s.kn;
+                }
+            }
         }
-        const double2* rp = reinterpret_cast<const double2*>(f.rec64 + s.c);
-        const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
-                      r4 = __ldg(rp + 4);
-        const double v1x = r0.x, v2x = r0.y, Ax = r1.x, v1y = r1.y, v2y = r2.x, Ay = r2.y, v1z = r3.x,
-                     v2z = r3.y, Az = r4.x;
-        const unsigned long long nb = (unsigned long long)__double_as_longlong(r4.y);
-        const double D0 = __ldg(f.delr + s.j), D1 = __ldg(f.delc + s.i), D2 = __ldg(f.dz + s.k);
-        const double vp0 = v1x + Ax * s.x0;
-        const double vp1 = v1y + Ay * s.x1;
-        const double vp2 = v1z + Az * s.x2;
-        int f0, f1, f2;
-        const double te0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, f0);
-        const double te1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, f1);
-        const double te2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, f2);
-        int ax = -1;
-        double tmin = CUDART_INF;
-        if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
-        if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
-        if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
-        s.steps++;
-        const double t_end = s.t + tmin;
-        if (ax < 0 || t_end >= s.tev) {
-            // slow path: no exit, the stop time, or an output time in this step
-            if (ax < 0 && !(p.t_stop < CUDART_INF)) {
-                if (TS) {
-                    while (s.kn < p.n_times) {
-                        const double tau = __ldg(o.times + s.kn) - s.t;
-                        record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
-                               __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
-                               __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_NO_EXIT);
-                        s.kn++;
-                    }
-                }
-                s.st = MP_ST_NO_EXIT;
-                return;
-            }
-            if (ax < 0 || t_end >= p.t_stop) {
-                const double dt = p.t_stop - s.t;
-                if (TS) {
-                    while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
-                        const double tau = __ldg(o.times + s.kn) - s.t;
-                        record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
-                               __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
-                               __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
-                        s.kn++;
-                    }
-                }
-                s.x0 = move(Ax, D0, vp0, s.x0, dt);
-                s.x1 = move(Ay, D1, vp1, s.x1, dt);
-                s.x2 = move(Az, D2, vp2, s.x2, dt);
-                s.t = p.t_stop;
-                s.st = MP_ST_TIME;
-                return;
-            }
-            if (TS) {
-                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
-                    const double tau = __ldg(o.times + s.kn) - s.t;
-                    record(q, s.kn, s, __ldg(f.xf + s.j) + move(Ax, D0, vp0, s.x0, tau),
-                           __ldg(f.yf + s.i) + move(Ay, D1, vp1, s.x1, tau),
-                           __ldg(f.zf + s.k) + move(Az, D2, vp2, s.x2, tau), MP_ST_ACTIVE);
-                    s.kn++;
-                }
+        if (TS) {
+            rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
+            if (m) {
+                s.kn += m;
                 s.tev = next_event(s);
             }
+        }
+        if (path == P_NONE) return;
+        if (path == P_NOEXIT) {
+            s.st = MP_ST_NO_EXIT;
+            return;
+        }
+        if (path == P_TIME) {
+            const double dt = p.t_stop - s.t;
+            s.x0 = move(Ax, D0, vp0, s.x0, dt);
+            s.x1 = move(Ay, D1, vp1, s.x1, dt);
+            s.x2 = move(Az, D2, vp2, s.x2, dt);
+            s.t = p.t_stop;
+            s.st = MP_ST_TIME;
+            return;
         }
         // displacement to the exit face: every axis moves by the analytic
         // formula (uniform across lanes), then the exit axis is put on its face

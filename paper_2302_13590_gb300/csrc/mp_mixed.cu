@@ -138,71 +138,100 @@ struct MixEngine {
         s.tev = TS ? next_event(s) : p.t_stop;
     }
 
-    template <bool TS>
-    __device__ __forceinline__ void step(long long q, State& s) const
+    // per-warp queue of deferred timeseries records (structure of arrays)
+    struct RecQ {
+        float x0[RQ_CAP], x1[RQ_CAP], x2[RQ_CAP], tau[RQ_CAP];
+        long long q[RQ_CAP];
+        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP];
+    };
+
+    __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
-        if ((long long)s.steps >= p.max_steps) { s.st = MP_ST_STEP_CAP; return; }
-        if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
-            atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
-            s.st = MP_ST_INVALID_RELEASE;
-            return;
-        }
-        const float4* rp = reinterpret_cast<const float4*>(f.rec32 + s.c);
+        Q.x0[slot] = s.x0; Q.x1[slot] = s.x1; Q.x2[slot] = s.x2;
+        Q.tau[slot] = (float)(__ldg(o.times + kk) - s.t);
+        Q.q[slot] = q;
+        Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
+        Q.kk[slot] = kk; Q.st[slot] = st;
+    }
+
+    __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
+    {
+        State r;
+        r.c = Q.c[slot]; r.i = Q.i[slot]; r.j = Q.j[slot]; r.k = Q.k[slot];
+        const float tau = Q.tau[slot];
+        const float4* rp = reinterpret_cast<const float4*>(f.rec32 + r.c);
         const float4 ra = __ldg(rp), rb = __ldg(rp + 1);
-        const float u1x = ra.x, u2x = ra.y, u1y = ra.z, u2y = ra.w, u1z = rb.x, u2z = rb.y;
-        const unsigned nb = __float_as_uint(rb.z);
-        const float Ax = u2x - u1x, Ay = u2y - u1y, Az = u2z - u1z;
-        const float up0 = u1x + Ax * s.x0, up1 = u1y + Ay * s.x1, up2 = u1z + Az * s.x2;
-        int f0, f1, f2;
-        const float te0 = exit_time(u1x, u2x, Ax, up0, s.x0, f0);
-        const float te1 = exit_time(u1y, u2y, Ay, up1, s.x1, f1);
-        const float te2 = exit_time(u1z, u2z, Az, up2, s.x2, f2);
-        int ax = -1;
-        float tmin = CUDART_INF_F;
-        if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
-        if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
-        if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
-        s.steps++;
-        const double t_end = s.t + (double)tmin;
-        if (ax < 0 || t_end >= s.tev) {
-            if (ax < 0 && !(p.t_stop < CUDART_INF)) {
-                if (TS) {
-                    while (s.kn < p.n_times) {
-                        const float tau = (float)(__ldg(o.times + s.kn) - s.t);
-                        record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
-                               gz(s, move(Az, up2, s.x2, tau)), MP_ST_NO_EXIT);
-                        s.kn++;
-                    }
+        const float Ax = ra.y - ra.x, Ay = ra.w - ra.z, Az = rb.y - rb.x;
+        const float a0 = Q.x0[slot], a1 = Q.x1[slot], a2 = Q.x2[slot];
+        const double x = gx(r, move(Ax, ra.x + Ax * a0, a0, tau));
+        const double y = gy(r, move(Ay, ra.z + Ay * a1, a1, tau));
+        const double z = gz(r, move(Az, rb.x + Az * a2, a2, tau));
+        store_record(o.ts + (long long)Q.kk[slot] * p.n + Q.q[slot], x, y, z, r.c, Q.st[slot]);
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void step(long long q, State& s, bool live, RecQ& Q, int& qcount) const
+    {
+        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
+        int path = P_NONE;
+        int m = 0;
+        float Ax = 0, Ay = 0, Az = 0, up0 = 0, up1 = 0, up2 = 0, tmin = 0;
+        double t_end = 0;
+        int f0 = 0, f1 = 0, f2 = 0, ax = -1;
+        unsigned nb = 0;
+        if (live) {
+            if ((long long)s.steps >= p.max_steps) {
+                s.st = MP_ST_STEP_CAP;
+            } else if ((unsigned long long)s.c >= (unsigned long long)f.ncell) {
+                atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
+                s.st = MP_ST_INVALID_RELEASE;
+            } else {
+                const float4* rp = reinterpret_cast<const float4*>(f.rec32 + s.c);
+                const float4 ra = __ldg(rp), rb = __ldg(rp + 1);
+                const float u1x = ra.x, u2x = ra.y, u1y = ra.z, u2y = ra.w, u1z = rb.x, u2z = rb.y;
+                nb = __float_as_uint(rb.z);
+                Ax = u2x - u1x; Ay = u2y - u1y; Az = u2z - u1z;
+                up0 = u1x + Ax * s.x0; up1 = u1y + Ay * s.x1; up2 = u1z + Az * s.x2;
+                const float te0 = exit_time(u1x, u2x, Ax, up0, s.x0, f0);
+                const float te1 = exit_time(u1y, u2y, Ay, up1, s.x1, f1);
+                const float te2 = exit_time(u1z, u2z, Az, up2, s.x2, f2);
+                tmin = CUDART_INF_F;
+                if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
+                if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
+                if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
+                s.steps++;
+                t_end = s.t + (double)tmin;
+                if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                else path = P_CROSS;
+                if (TS && (ax < 0 || t_end >= s.tev)) {
+                    const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
+                    int kk = s.kn;
+                    while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                    m = kk - s.kn;
                 }
-                s.st = MP_ST_NO_EXIT;
-                return;
             }
-            if (ax < 0 || t_end >= p.t_stop) {
-                const float dt = (float)(p.t_stop - s.t);
-                if (TS) {
-                    while (s.kn < p.n_times && __ldg(o.times + s.kn) <= p.t_stop) {
-                        const float tau = (float)(__ldg(o.times + s.kn) - s.t);
-                        record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
-                               gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
-                        s.kn++;
-                    }
-                }
-                s.x0 = move(Ax, up0, s.x0, dt);
-                s.x1 = move(Ay, up1, s.x1, dt);
-                s.x2 = move(Az, up2, s.x2, dt);
-                s.t = p.t_stop;
-                s.st = MP_ST_TIME;
-                return;
-            }
-            if (TS) {
-                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t_end) {
-                    const float tau = (float)(__ldg(o.times + s.kn) - s.t);
-                    record(q, s.kn, s, gx(s, move(Ax, up0, s.x0, tau)), gy(s, move(Ay, up1, s.x1, tau)),
-                           gz(s, move(Az, up2, s.x2, tau)), MP_ST_ACTIVE);
-                    s.kn++;
-                }
+        }
+        if (TS) {
+            rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
+            if (m) {
+                s.kn += m;
                 s.tev = next_event(s);
             }
+        }
+        if (path == P_NONE) return;
+        if (path == P_NOEXIT) {
+            s.st = MP_ST_NO_EXIT;
+            return;
+        }
+        if (path == P_TIME) {
+            const float dt = (float)(p.t_stop - s.t);
+            s.x0 = move(Ax, up0, s.x0, dt);
+            s.x1 = move(Ay, up1, s.x1, dt);
+            s.x2 = move(Az, up2, s.x2, dt);
+            s.t = p.t_stop;
+            s.st = MP_ST_TIME;
+            return;
         }
         const float dt = tmin;
         const float n0 = move(Ax, up0, s.x0, dt);

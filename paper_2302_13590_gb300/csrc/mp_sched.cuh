@@ -47,19 +47,88 @@ __device__ __forceinline__ void flush_counters(const E& e, unsigned long long* s
         if (s_cnt[i]) atomicAdd(e.o.counters + i, s_cnt[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Deferred timeseries records (the GPU form of the paper's thread-exclusive
+// output units, Methods, "Multiprocessing").  A lane whose step passes output
+// times does not evaluate them on the spot - that would run the record
+// branch for the whole warp with one or two lanes active in almost every
+// step.  It pushes (pre-step position, cell, tau, slot) into its warp's
+// shared-memory queue; whenever 32 requests are queued, the warp evaluates
+// them together, one per lane, and writes 32 full-sector records.
+// ---------------------------------------------------------------------------
+
+constexpr int RQ_CAP = 64;   // requests per warp (>= 2 x 32)
+
+template <class E>
+__device__ __forceinline__ void rq_drain(const E& e, typename E::RecQ& Q, int& qcount, bool all)
+{
+    const int lane = threadIdx.x & 31;
+    while (qcount >= 32 || (all && qcount > 0)) {
+        const int nb = qcount < 32 ? qcount : 32;
+        const int base = qcount - nb;
+        if (lane < nb) e.rec_eval(Q, base + lane);
+        qcount = base;
+        __syncwarp();
+    }
+}
+
+// Queue m records per lane (output indices kn0 .. kn0+m-1 of the particle in
+// this lane, evaluated from its pre-step state); warp-uniform call.
+template <class E>
+__device__ __forceinline__ void rq_push(const E& e, typename E::RecQ& Q, int& qcount,
+                                        const typename E::State& s, long long q, int kn0, int m, int st)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int done = 0;
+    while (true) {
+        const int want = m - done;
+        int incl = want;
+        #pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int excl = incl - want;
+        const int room = RQ_CAP - qcount;
+        int take = room - excl;
+        take = take < 0 ? 0 : (take > want ? want : take);
+        for (int r = 0; r < take; ++r) e.rec_put(Q, qcount + excl + r, s, q, kn0 + done + r, st);
+        const int total = __shfl_sync(FULL, incl, 31);
+        qcount += total < room ? total : room;
+        done += take;
+        __syncwarp();
+        rq_drain(e, Q, qcount, false);
+        if (!__any_sync(FULL, done < m)) break;
+    }
+}
+
 template <class E, bool TS>
 __global__ void __launch_bounds__(256) k_track_static(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
+    __shared__ typename E::RecQ s_q[TS ? 8 : 1];
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
     __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
+    int qcount = 0;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    typename E::State s;
+    bool live = false;
     if (q < e.p.n) {
-        typename E::State s;
         e.template load<TS>(q, s);
-        while (s.st == MP_ST_ACTIVE) e.template step<TS>(q, s);
-        e.template finish<TS>(q, s, s_cnt);
+        live = s.st == MP_ST_ACTIVE;
+        if (!live) e.template finish<TS>(q, s, s_cnt);
     }
+    while (__any_sync(FULL, live)) {
+        e.template step<TS>(q, s, live, Q, qcount);
+        if (live && s.st != MP_ST_ACTIVE) {
+            e.template finish<TS>(q, s, s_cnt);
+            live = false;
+        }
+    }
+    if (TS) rq_drain(e, Q, qcount, true);
     flush_counters(e, s_cnt);
 }
 
@@ -67,8 +136,11 @@ template <class E, bool TS>
 __global__ void __launch_bounds__(256) k_track_dynamic(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
+    __shared__ typename E::RecQ s_q[TS ? 8 : 1];
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
     __syncthreads();
+    typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
+    int qcount = 0;
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -101,15 +173,14 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
             continue;
         }
         for (int it = 0; it < S; ++it) {
-            if (live) {
-                e.template step<TS>(q, s);
-                if (s.st != MP_ST_ACTIVE) {
-                    e.template finish<TS>(q, s, s_cnt);
-                    live = false;
-                }
+            e.template step<TS>(q, s, live, Q, qcount);
+            if (live && s.st != MP_ST_ACTIVE) {
+                e.template finish<TS>(q, s, s_cnt);
+                live = false;
             }
         }
     }
+    if (TS) rq_drain(e, Q, qcount, true);
     flush_counters(e, s_cnt);
 }
 
