@@ -251,6 +251,44 @@ int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes);
 /* Number of CUDA kernel launches mp_track issues for these options. */
 int mp_track_launches(const mp_track_opts* o, int32_t* launches);
 
+/* ---- tracking without device allocation ----------------------------------
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory where they track: code that runs inside a
+ * caller-owned memory budget or arena, inside a CUDA stream capture (where
+ * cudaMalloc is not allowed), or on a path that must not synchronise the
+ * device.  The caller passes every buffer: the particle state (device arrays
+ * in the layout of a group: cell int32, px/py/pz offsets in m from the cell's
+ * low faces and t as FP64, status u8), the endpoint arrays (device, all
+ * required) and, in timeseries mode, the [n_times][n] record buffer (device).
+ * times stays a host array.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  Its only other device memory is a
+ * fixed file-scope array of 8 + 10 + MP_NOALLOC_MAX_TIMES 64-bit words
+ * (queue head, counters, a copy of the output times; about 33 KB) that every
+ * GPU that loads the library holds until the process exits.
+ *   - The first call on each device takes the array's device address; make
+ *     that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents; the
+ *     call clears the queue head and counters itself.  Calls that overlap on
+ *     the GPU (different streams, or a second call before the first has run)
+ *     race on it: run them one after another on one stream.
+ *   - n_times > MP_NOALLOC_MAX_TIMES is rejected with MP_ERR_INVALID_ARG.
+ *   - stats == NULL: the call only enqueues work on `stream`.  Otherwise it
+ *     waits for the stream and fills *stats (kernel_ms is 0).
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NONFINITE, MP_ERR_CUDA, MP_ERR_DEVICE. */
+#define MP_NOALLOC_MAX_TIMES 4096
+
+typedef struct {
+    int64_t n;
+    int32_t* cell;
+    double *px, *py, *pz, *t;
+    uint8_t* status;
+    mp_endpoints out;
+    mp_ts_record* ts;
+    mp_track_opts opts;
+} mp_noalloc_args;
+
+int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

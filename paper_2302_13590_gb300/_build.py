@@ -5,6 +5,7 @@ Three translation units, compiled in parallel:
   mp_fp64.cu   field records, release, FP64 tracking (-fmad=false: no FMA
                contraction, so FP64 results round exactly as written)
   mp_mixed.cu  mixed-precision tracking (contraction allowed)
+  mp_noalloc.cu  the entry point that allocates no device memory
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ UNITS = {
     "mp_api.cu": [],
     "mp_fp64.cu": ["-fmad=false"],
     "mp_mixed.cu": [],
+    "mp_noalloc.cu": [],
 }
 
 

@@ -730,3 +730,11 @@ int mp_req_free(mp_ctx* ctx, mp_req id)
 }
 
 }  // extern "C"
+
+namespace mp {
+
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+const DevField* field_device_view(const mp_field* f) { return &f->d; }
+
+}  // namespace mp

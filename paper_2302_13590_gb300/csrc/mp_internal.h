@@ -108,4 +108,9 @@ cudaError_t launch_track_fp64(const DevField& f, const DevState& st, const DevOu
 cudaError_t launch_track_mixed(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
                                int schedule, int block, int blocks_per_sm_cap, cudaStream_t s);
 
+// Host helpers shared by the entry points: the calling thread's error
+// message (what mp_last_error returns) and a loaded field's device view.
+void set_last_error(const char* msg);
+const DevField* field_device_view(const mp_field* f);
+
 }  // namespace mp

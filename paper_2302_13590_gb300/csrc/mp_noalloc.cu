@@ -1,0 +1,135 @@
+// mp_noalloc.cu - tracking entry point that allocates no device memory.
+//
+// Some callers cannot allocate device memory at the point where they track
+// particles: code running under a caller-owned memory budget (an embedding
+// application that hands out a fixed arena), inside a stream capture where
+// cudaMalloc is not permitted, or on a path that must not synchronise the
+// device.  mp_track_noalloc serves them: the caller passes every input and
+// output buffer, and the only other device memory the call uses is the small
+// file-scope array below, which every GPU that loads this library holds
+// until the process exits.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "mp_internal.h"
+
+using namespace mp;
+
+namespace {
+
+// queue head, reduction counters and a copy of the output times
+constexpr int kScratchWords = 8 + N_COUNTERS + MP_NOALLOC_MAX_TIMES;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned long long* g_ptr[kMaxDevices] = {};
+
+int na_fail(int code, const std::string& m)
+{
+    mp::set_last_error(m.c_str());
+    return code;
+}
+
+// Device address of the scratch array for the current device; taken once per
+// device (the first call on a device does it, so that call should come
+// before any stream capture).
+int scratch_ptr(unsigned long long** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: device index too large");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return na_fail(MP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_ptr[dev] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_ptr[dev];
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats)
+{
+    if (!f || !a) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: NULL argument");
+    if (a->n < 0) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: n < 0");
+    const mp_track_opts* o = &a->opts;
+    if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: bad mode");
+    if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: unknown precision");
+    if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC)
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: unknown schedule");
+    if (std::isnan(o->t_stop)) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: t_stop is NaN");
+    const bool want_ts = (o->mode & MP_MODE_TIMESERIES) != 0;
+    const int nt = want_ts ? o->n_times : 0;
+    if (want_ts && (nt <= 0 || !o->times || !a->ts))
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: timeseries mode needs times and a record buffer");
+    if (nt > MP_NOALLOC_MAX_TIMES)
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: more than MP_NOALLOC_MAX_TIMES output times (" +
+                                               std::to_string(MP_NOALLOC_MAX_TIMES) + ")");
+    for (int k = 0; k < nt; ++k) {
+        if (!std::isfinite(o->times[k])) return na_fail(MP_ERR_NONFINITE, "mp_track_noalloc: non-finite time");
+        if (k > 0 && o->times[k] < o->times[k - 1]) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: times not ascending");
+    }
+    const mp_endpoints& ep = a->out;
+    if (a->n > 0 && (!a->cell || !a->px || !a->py || !a->pz || !a->t || !a->status || !ep.cell || !ep.x || !ep.y ||
+                     !ep.z || !ep.px || !ep.py || !ep.pz || !ep.t || !ep.status || !ep.steps || !ep.exit_face ||
+                     !ep.hash))
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: every state and endpoint array is required");
+    unsigned long long* scratch = nullptr;
+    int rc = scratch_ptr(&scratch);
+    if (rc != MP_OK) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* queue = scratch;
+    unsigned long long* counters = scratch + 8;
+    double* times = reinterpret_cast<double*>(scratch + 8 + N_COUNTERS);
+    // the array keeps the last call's contents: the queue head and counters
+    // must start from zero
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (8 + N_COUNTERS), s);
+    if (e == cudaSuccess && nt > 0)
+        e = cudaMemcpyAsync(times, o->times, sizeof(double) * nt, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: ") + cudaGetErrorString(e));
+    DevState st{a->cell, a->px, a->py, a->pz, a->t, a->status};
+    DevOut d{};
+    d.cell = ep.cell; d.x = ep.x; d.y = ep.y; d.z = ep.z; d.px = ep.px; d.py = ep.py; d.pz = ep.pz; d.t = ep.t;
+    d.status = ep.status; d.steps = ep.steps; d.exit_face = ep.exit_face;
+    d.hash = reinterpret_cast<unsigned long long*>(ep.hash);
+    d.ts = nt > 0 ? a->ts : nullptr;
+    d.times = times;
+    d.counters = counters;
+    d.queue = queue;
+    TrackParams p{};
+    p.n = a->n;
+    p.t_stop = (want_ts && !(o->mode & MP_MODE_ENDPOINT) && !(o->t_stop < INFINITY)) ? o->times[nt - 1] : o->t_stop;
+    p.max_steps = o->max_steps > 0 ? o->max_steps : 1000000LL;
+    p.n_times = nt;
+    p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
+    p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    const int block = o->block > 0 ? o->block : 128;
+    const DevField& fd = *mp::field_device_view(f);
+    e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, st, d, p, o->schedule, block, 0, s)
+                                       : launch_track_mixed(fd, st, d, p, o->schedule, block, 0, s);
+    if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: launch: ") + cudaGetErrorString(e));
+    if (stats) {
+        unsigned long long h[N_COUNTERS];
+        e = cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: stats: ") + cudaGetErrorString(e));
+        mp_stats out{};
+        out.cell_steps = h[COUNTER_STEPS];
+        for (int k = 0; k < MP_N_STATUS; ++k) out.n_status[k] = h[COUNTER_STATUS + k];
+        out.kernel_ms = 0.0f;
+        out.device_error = h[COUNTER_ERR] ? 1 : 0;
+        *stats = out;
+        if (h[COUNTER_ERR]) return na_fail(MP_ERR_DEVICE, "mp_track_noalloc: kernel raised its error flag");
+    }
+    return MP_OK;
+}

@@ -72,6 +72,14 @@ class Endpoints(ctypes.Structure):
                                    "exit_face", "hash")]
 
 
+class NoallocArgs(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("cell", _vp), ("px", _vp), ("py", _vp), ("pz", _vp), ("t", _vp),
+                ("status", _vp), ("out", Endpoints), ("ts", _vp), ("opts", TrackOpts)]
+
+
+NOALLOC_MAX_TIMES = 4096
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("cell_steps", ctypes.c_uint64), ("n_status", ctypes.c_uint64 * 8),
                 ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32)]
@@ -103,6 +111,7 @@ SIGNATURES = {
     "mp_req_free": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "mp_query_bytes": (ctypes.c_int, [_P(TrackOpts), ctypes.c_int64, _P(ctypes.c_size_t)]),
     "mp_track_launches": (ctypes.c_int, [_P(TrackOpts), _P(ctypes.c_int32)]),
+    "mp_track_noalloc": (ctypes.c_int, [_vp, _P(NoallocArgs), _vp, _P(Stats)]),
 }
 
 _lib = None
@@ -312,6 +321,27 @@ def mp_track_launches(opts: TrackOpts) -> int:
     v = ctypes.c_int32()
     _check(load_library().mp_track_launches(ctypes.byref(opts), ctypes.byref(v)))
     return v.value
+
+
+def mp_track_noalloc(fh, state: dict, out: dict, ts=None, opts: TrackOpts = None, stream=None,
+                     want_stats: bool = True):
+    """Track with caller-owned device buffers only (no device allocation).
+
+    ``state``: cell/px/py/pz/t/status device tensors; ``out``: every endpoint
+    array as a device tensor; ``ts``: device record buffer ([n_times, n] x 32
+    bytes) in timeseries mode.  Returns the stats dict when ``want_stats``
+    (the call then waits for the stream), else None."""
+    n = int(state["cell"].numel())
+    e = Endpoints(*[_ptr(out[k]) for k, _ in Endpoints._fields_])
+    a = NoallocArgs(n, _ptr(state["cell"]), _ptr(state["px"]), _ptr(state["py"]), _ptr(state["pz"]),
+                    _ptr(state["t"]), _ptr(state["status"]), e, _ptr(ts), opts)
+    st = Stats()
+    _check(load_library().mp_track_noalloc(fh, ctypes.byref(a), _stream(stream),
+                                           ctypes.byref(st) if want_stats else None))
+    if not want_stats:
+        return None
+    return {"cell_steps": int(st.cell_steps), "n_status": [int(v) for v in st.n_status],
+            "kernel_ms": float(st.kernel_ms), "device_error": int(st.device_error)}
 
 
 # ---- conveniences -------------------------------------------------------------------
