@@ -270,6 +270,14 @@ struct F64Engine {
     __device__ __forceinline__ double gy(const State& s) const { return __ldg(f.yf + s.i) + s.x1; }
     __device__ __forceinline__ double gz(const State& s) const { return __ldg(f.zf + s.k) + s.x2; }
 
+    __device__ __forceinline__ void final_pos(const State& s, double& x, double& y, double& z) const
+    {
+        const bool ok = s.c >= 0;
+        x = ok ? gx(s) : CUDART_NAN;
+        y = ok ? gy(s) : CUDART_NAN;
+        z = ok ? gz(s) : CUDART_NAN;
+    }
+
     // next time at which the step loop must leave its fast path
     __device__ __forceinline__ double next_event(const State& s) const
     {
@@ -391,7 +399,7 @@ struct F64Engine {
                 }
             }
         }
-        if (TS) {
+        if (TS && __any_sync(0xffffffffu, m > 0)) {
             rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
             if (m) {
                 s.kn += m;
@@ -456,9 +464,6 @@ struct F64Engine {
     {
         const bool ok = s.c >= 0;
         const double x = ok ? gx(s) : CUDART_NAN, y = ok ? gy(s) : CUDART_NAN, z = ok ? gz(s) : CUDART_NAN;
-        if (TS) {
-            for (int kk = s.kn; kk < p.n_times; ++kk) record(q, kk, s, x, y, z, s.st);
-        }
         o.cell[q] = s.c;
         o.x[q] = x; o.y[q] = y; o.z[q] = z;
         o.px[q] = s.x0; o.py[q] = s.x1; o.pz[q] = s.x2;

@@ -79,23 +79,36 @@ struct MixEngine {
         return s == 0.0f ? xi : xn;
     }
 
+    // global coordinate = face coordinate + fraction * cell size, rounded
+    // step by step (no contraction) so endpoints and records agree exactly
     __device__ __forceinline__ double gx(const State& s, float xi) const
     {
-        return __ldg(f.xf + s.j) + (double)xi * __ldg(f.delr + s.j);
+        return __dadd_rn(__ldg(f.xf + s.j), __dmul_rn((double)xi, __ldg(f.delr + s.j)));
     }
     __device__ __forceinline__ double gy(const State& s, float xi) const
     {
-        return __ldg(f.yf + s.i) + (double)xi * __ldg(f.delc + s.i);
+        return __dadd_rn(__ldg(f.yf + s.i), __dmul_rn((double)xi, __ldg(f.delc + s.i)));
     }
     __device__ __forceinline__ double gz(const State& s, float xi) const
     {
-        return __ldg(f.zf + s.k) + (double)xi * __ldg(f.dz + s.k);
+        return __dadd_rn(__ldg(f.zf + s.k), __dmul_rn((double)xi, __ldg(f.dz + s.k)));
     }
 
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
                                            int st) const
     {
         store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
+    }
+
+    __device__ __forceinline__ void final_pos(const State& s, double& x, double& y, double& z) const
+    {
+        if (s.c < 0) {
+            x = y = z = CUDART_NAN;
+            return;
+        }
+        x = gx(s, s.x0);
+        y = gy(s, s.x1);
+        z = gz(s, s.x2);
     }
 
     __device__ __forceinline__ double next_event(const State& s) const
@@ -212,7 +225,7 @@ struct MixEngine {
                 }
             }
         }
-        if (TS) {
+        if (TS && __any_sync(0xffffffffu, m > 0)) {
             rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
             if (m) {
                 s.kn += m;
@@ -268,15 +281,12 @@ struct MixEngine {
         const bool ok = s.c >= 0;
         double px = 0.0, py = 0.0, pz = 0.0, x = CUDART_NAN, y = CUDART_NAN, z = CUDART_NAN;
         if (ok) {
-            px = (double)s.x0 * __ldg(f.delr + s.j);
-            py = (double)s.x1 * __ldg(f.delc + s.i);
-            pz = (double)s.x2 * __ldg(f.dz + s.k);
-            x = __ldg(f.xf + s.j) + px;
-            y = __ldg(f.yf + s.i) + py;
-            z = __ldg(f.zf + s.k) + pz;
-        }
-        if (TS) {
-            for (int kk = s.kn; kk < p.n_times; ++kk) record(q, kk, s, x, y, z, s.st);
+            px = __dmul_rn((double)s.x0, __ldg(f.delr + s.j));
+            py = __dmul_rn((double)s.x1, __ldg(f.delc + s.i));
+            pz = __dmul_rn((double)s.x2, __ldg(f.dz + s.k));
+            x = gx(s, s.x0);
+            y = gy(s, s.x1);
+            z = gz(s, s.x2);
         }
         o.cell[q] = s.c;
         o.x[q] = x; o.y[q] = y; o.z[q] = z;

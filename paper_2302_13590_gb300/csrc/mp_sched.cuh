@@ -103,6 +103,29 @@ __device__ __forceinline__ void rq_push(const E& e, typename E::RecQ& Q, int& qc
     }
 }
 
+// After a particle ends, its remaining output times all hold the final
+// position and status.  The lanes of the warp write them together: the final
+// record of each ending lane is broadcast and the 32 lanes store its slots.
+template <class E>
+__device__ __forceinline__ void tail_fill(const E& e, const typename E::State& s, long long q, bool ended)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned mask = __ballot_sync(FULL, ended);
+    if (!mask) return;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (ended) e.final_pos(s, x, y, z);
+    while (mask) {
+        const int L = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const double bx = __shfl_sync(FULL, x, L), by = __shfl_sync(FULL, y, L), bz = __shfl_sync(FULL, z, L);
+        const int c = __shfl_sync(FULL, s.c, L), st = __shfl_sync(FULL, s.st, L), kn = __shfl_sync(FULL, s.kn, L);
+        const long long qq = __shfl_sync(FULL, q, L);
+        for (int kk = kn + lane; kk < e.p.n_times; kk += 32)
+            store_record(e.o.ts + (long long)kk * e.p.n + qq, bx, by, bz, c, st);
+    }
+}
+
 template <class E, bool TS>
 __global__ void __launch_bounds__(256) k_track_static(E e)
 {
@@ -115,15 +138,19 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
     int qcount = 0;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     typename E::State s;
-    bool live = false;
+    bool live = false, ended = false;
     if (q < e.p.n) {
         e.template load<TS>(q, s);
         live = s.st == MP_ST_ACTIVE;
-        if (!live) e.template finish<TS>(q, s, s_cnt);
+        ended = !live;
     }
+    if (TS) tail_fill(e, s, q, ended);
+    if (ended) e.template finish<TS>(q, s, s_cnt);
     while (__any_sync(FULL, live)) {
         e.template step<TS>(q, s, live, Q, qcount);
-        if (live && s.st != MP_ST_ACTIVE) {
+        ended = live && s.st != MP_ST_ACTIVE;
+        if (TS) tail_fill(e, s, q, ended);
+        if (ended) {
             e.template finish<TS>(q, s, s_cnt);
             live = false;
         }
@@ -152,6 +179,7 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     typename E::State s;
     while (true) {
         const unsigned idle = __ballot_sync(FULL, !live);
+        bool ended = false;
         if (idle && !drained) {
             const unsigned cnt = __popc(idle);
             unsigned long long base = 0;
@@ -163,18 +191,22 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
                 if (qq < n) {
                     q = (long long)qq;
                     e.template load<TS>(q, s);
-                    if (s.st == MP_ST_ACTIVE) live = true;
-                    else e.template finish<TS>(q, s, s_cnt);
+                    live = s.st == MP_ST_ACTIVE;
+                    ended = !live;
                 }
             }
         }
+        if (TS) tail_fill(e, s, q, ended);
+        if (ended) e.template finish<TS>(q, s, s_cnt);
         if (!__any_sync(FULL, live)) {
             if (drained) break;
             continue;
         }
         for (int it = 0; it < S; ++it) {
             e.template step<TS>(q, s, live, Q, qcount);
-            if (live && s.st != MP_ST_ACTIVE) {
+            ended = live && s.st != MP_ST_ACTIVE;
+            if (TS) tail_fill(e, s, q, ended);
+            if (ended) {
                 e.template finish<TS>(q, s, s_cnt);
                 live = false;
             }
