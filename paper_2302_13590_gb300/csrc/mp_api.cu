@@ -293,6 +293,8 @@ int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
     f->d.yf = reinterpret_cast<double*>(buf + o_yf);
     f->d.zf = reinterpret_cast<double*>(buf + o_zf);
     f->d.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
+    f->d.m_ncol = div_magic((unsigned)nc);
+    f->d.m_nrow = div_magic((unsigned)nr);
     e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32), qx, qy, qz,
                              por, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -297,9 +297,7 @@ struct F64Engine {
         s.kn = 0;
         s.ef = MP_FACE_NONE;
         if (s.c >= 0 && (long long)s.c < f.ncell) {
-            s.j = s.c % f.ncol;
-            s.i = (s.c / f.ncol) % f.nrow;
-            s.k = s.c / (f.ncol * f.nrow);
+            split_cell(f, s.c, s.k, s.i, s.j);
             s.h = fnv_step(s.h, s.c);
         } else {
             s.c = -1; s.i = s.j = s.k = 0;

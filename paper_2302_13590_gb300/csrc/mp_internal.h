@@ -49,7 +49,31 @@ struct DevField {
     const double* yf;  // [nrow+1]
     const double* zf;  // [nlay+1]
     const int8_t* ibound;
+    // x / ncol and x / nrow as a 64-bit multiply-high (x < 2^32):
+    // floor(x / d) == umul64hi(x, floor((2^64 - 1) / d) + 1) for 1 < d < 2^32
+    unsigned long long m_ncol, m_nrow;
 };
+
+__host__ __device__ inline unsigned long long div_magic(unsigned d)
+{
+    return d <= 1 ? 0ULL : (~0ULL) / d + 1ULL;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fast_div(unsigned x, unsigned d, unsigned long long m)
+{
+    return d <= 1 ? x : (unsigned)__umul64hi((unsigned long long)x, m);
+}
+
+// (k, i, j) of a linear cell index without integer division instructions
+__device__ __forceinline__ void split_cell(const DevField& f, int c, int& k, int& i, int& j)
+{
+    const unsigned r = fast_div((unsigned)c, (unsigned)f.ncol, f.m_ncol);   // k * nrow + i
+    j = c - (int)(r * (unsigned)f.ncol);
+    k = (int)fast_div(r, (unsigned)f.nrow, f.m_nrow);
+    i = (int)r - k * f.nrow;
+}
+#endif
 
 struct DevState {
     int32_t* cell;

@@ -30,7 +30,11 @@ struct MixEngine {
     struct State {
         int c, i, j, k;
         float x0, x1, x2;  // local fractions in [0, 1]
-        double t;
+        // travel time: FP64 base at the last output / stop event plus the
+        // time since then as an unevaluated FP32 pair (ah + al, error-free
+        // two-sum per step); (rh + rl) = FP32 pair of tev - tb
+        double tb;
+        float ah, al, rh, rl;
         unsigned steps;
         unsigned long long h;
         int kn;
@@ -111,6 +115,27 @@ struct MixEngine {
         z = gz(s, s.x2);
     }
 
+    __device__ __forceinline__ static double time_of(const State& s)
+    {
+        return s.tb + (double)s.ah + (double)s.al;
+    }
+
+    // restart the FP32 accumulator at FP64 time t
+    __device__ __forceinline__ static void flush(State& s, double t)
+    {
+        s.tb = t;
+        s.ah = 0.0f;
+        s.al = 0.0f;
+        const double rem = s.tev - t;
+        if (rem < 3.0e38) {
+            s.rh = (float)rem;
+            s.rl = (float)(rem - (double)s.rh);
+        } else {
+            s.rh = CUDART_INF_F;
+            s.rl = 0.0f;
+        }
+    }
+
     __device__ __forceinline__ double next_event(const State& s) const
     {
         const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
@@ -122,18 +147,16 @@ struct MixEngine {
     {
         s.c = in.cell[q];
         s.st = in.status[q];
-        s.t = in.t[q];
+        const double t0 = in.t[q];
         s.steps = 0;
         s.h = FNV_INIT;
         s.kn = 0;
         s.ef = MP_FACE_NONE;
         if (s.c >= 0 && (long long)s.c < f.ncell) {
-            s.j = s.c % f.ncol;
-            s.i = (s.c / f.ncol) % f.nrow;
-            s.k = s.c / (f.ncol * f.nrow);
-            s.x0 = (float)(in.px[q] / __ldg(f.delr + s.j));
-            s.x1 = (float)(in.py[q] / __ldg(f.delc + s.i));
-            s.x2 = (float)(in.pz[q] / __ldg(f.dz + s.k));
+            split_cell(f, s.c, s.k, s.i, s.j);
+            s.x0 = __fdiv_rn((float)in.px[q], (float)__ldg(f.delr + s.j));
+            s.x1 = __fdiv_rn((float)in.py[q], (float)__ldg(f.delc + s.i));
+            s.x2 = __fdiv_rn((float)in.pz[q], (float)__ldg(f.dz + s.k));
             s.h = fnv_step(s.h, s.c);
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
@@ -141,14 +164,15 @@ struct MixEngine {
             s.st = MP_ST_INVALID_RELEASE;
         }
         if (TS) {
-            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
+            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= t0) {
                 if (s.c >= 0) record(q, s.kn, s, gx(s, s.x0), gy(s, s.x1), gz(s, s.x2), s.st);
                 else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
                 s.kn++;
             }
         }
-        if (s.st == MP_ST_ACTIVE && s.t >= p.t_stop) s.st = MP_ST_TIME;
+        if (s.st == MP_ST_ACTIVE && t0 >= p.t_stop) s.st = MP_ST_TIME;
         s.tev = TS ? next_event(s) : p.t_stop;
+        flush(s, t0);
     }
 
     // per-warp queue of deferred timeseries records (structure of arrays)
@@ -161,7 +185,7 @@ struct MixEngine {
     __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
         Q.x0[slot] = s.x0; Q.x1[slot] = s.x1; Q.x2[slot] = s.x2;
-        Q.tau[slot] = (float)(__ldg(o.times + kk) - s.t);
+        Q.tau[slot] = (float)(__ldg(o.times + kk) - time_of(s));
         Q.q[slot] = q;
         Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
         Q.kk[slot] = kk; Q.st[slot] = st;
@@ -188,8 +212,9 @@ struct MixEngine {
         enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
         int path = P_NONE;
         int m = 0;
-        float Ax = 0, Ay = 0, Az = 0, up0 = 0, up1 = 0, up2 = 0, tmin = 0;
+        float Ax = 0, Ay = 0, Az = 0, up0 = 0, up1 = 0, up2 = 0, tmin = 0, nh = 0, nl = 0;
         double t_end = 0;
+        bool ev = false;
         int f0 = 0, f1 = 0, f2 = 0, ax = -1;
         unsigned nb = 0;
         if (live) {
@@ -213,15 +238,26 @@ struct MixEngine {
                 if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
                 if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
                 s.steps++;
-                t_end = s.t + (double)tmin;
-                if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
-                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
-                else path = P_CROSS;
-                if (TS && (ax < 0 || t_end >= s.tev)) {
-                    const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
-                    int kk = s.kn;
-                    while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
-                    m = kk - s.kn;
+                // error-free FP32 two-sum of the accumulated time and tmin
+                const float sh = s.ah + tmin;
+                const float bb = sh - s.ah;
+                const float lo = s.al + ((s.ah - (sh - bb)) + (tmin - bb));
+                nh = sh + lo;
+                nl = lo - (nh - sh);
+                ev = ax < 0 || nh > s.rh || (nh == s.rh && nl >= s.rl);
+                if (ev) {
+                    t_end = time_of(s) + (double)tmin;
+                    if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                    else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                    else path = P_CROSS;
+                    if (TS) {
+                        const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
+                        int kk = s.kn;
+                        while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                        m = kk - s.kn;
+                    }
+                } else {
+                    path = P_CROSS;
                 }
             }
         }
@@ -238,11 +274,11 @@ struct MixEngine {
             return;
         }
         if (path == P_TIME) {
-            const float dt = (float)(p.t_stop - s.t);
+            const float dt = (float)(p.t_stop - time_of(s));
             s.x0 = move(Ax, up0, s.x0, dt);
             s.x1 = move(Ay, up1, s.x1, dt);
             s.x2 = move(Az, up2, s.x2, dt);
-            s.t = p.t_stop;
+            flush(s, p.t_stop);
             s.st = MP_ST_TIME;
             return;
         }
@@ -255,7 +291,12 @@ struct MixEngine {
         s.x0 = ax == 0 ? onface : n0;
         s.x1 = ax == 1 ? onface : n1;
         s.x2 = ax == 2 ? onface : n2;
-        s.t = t_end;
+        if (ev) {
+            flush(s, t_end);
+        } else {
+            s.ah = nh;
+            s.al = nl;
+        }
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3u);
@@ -291,7 +332,7 @@ struct MixEngine {
         o.cell[q] = s.c;
         o.x[q] = x; o.y[q] = y; o.z[q] = z;
         o.px[q] = px; o.py[q] = py; o.pz[q] = pz;
-        o.t[q] = s.t;
+        o.t[q] = time_of(s);
         o.status[q] = (uint8_t)s.st;
         o.steps[q] = s.steps;
         o.exit_face[q] = (uint8_t)s.ef;
@@ -299,7 +340,7 @@ struct MixEngine {
         if (p.update_group && ok) {
             in.cell[q] = s.c;
             in.px[q] = px; in.py[q] = py; in.pz[q] = pz;
-            in.t[q] = s.t;
+            in.t[q] = time_of(s);
             in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
         }
         atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);

@@ -65,6 +65,8 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         lib.fg_solve.restype = ctypes.c_int
         lib.fg_solve.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7 + [ctypes.c_double, ctypes.c_int] + [ctypes.c_void_p] * 5
+        lib.fg_solve_mg.restype = ctypes.c_int
+        lib.fg_solve_mg.argtypes = lib.fg_solve.argtypes
         lib.fg_balance.restype = ctypes.c_double
         lib.fg_balance.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 6
         _lib = lib
@@ -127,8 +129,10 @@ class Field:
 
 
 def solve_flow(nlay, nrow, ncol, delr, delc, dz, K, ibound, head_bc, q_src=None,
-               tol_abs=1e-13, max_iter=20000):
-    """Finite-volume head solve (IC(0)-PCG in C); returns (head, qx, qy, qz, iters, maxres)."""
+               tol_abs=1e-13, max_iter=20000, method="mg"):
+    """Finite-volume head solve in C: conjugate gradients preconditioned by a
+    multigrid V-cycle ("mg", default) or by IC(0) ("ic"); returns
+    (head, qx, qy, qz, iters, maxres)."""
     lib = _load()
     delr = np.ascontiguousarray(delr, dtype=np.float64)
     delc = np.ascontiguousarray(delc, dtype=np.float64)
@@ -142,7 +146,8 @@ def solve_flow(nlay, nrow, ncol, delr, delc, dz, K, ibound, head_bc, q_src=None,
     qz = np.zeros((nlay + 1, nrow, ncol))
     maxres = ctypes.c_double(0.0)
     iters = ctypes.c_int(0)
-    rc = lib.fg_solve(nlay, nrow, ncol, _p(delr), _p(delc), _p(dz), _p(K), _p(ib), _p(q), _p(head),
+    fn = lib.fg_solve_mg if method == "mg" else lib.fg_solve
+    rc = fn(nlay, nrow, ncol, _p(delr), _p(delc), _p(dz), _p(K), _p(ib), _p(q), _p(head),
                       float(tol_abs), int(max_iter), _p(qx), _p(qy), _p(qz),
                       ctypes.byref(maxres), ctypes.byref(iters))
     if rc not in (0, -3):

@@ -300,3 +300,342 @@ double fg_balance(int nlay, int nrow, int ncol, const double* qx, const double* 
             }
     return mx;
 }
+
+/* ======================================================================
+ * Multigrid-preconditioned CG (used for the large, strongly heterogeneous
+ * fields).  Levels store the operator in column order o = (i*nc + j)*nl + k
+ * (layer index fastest), so that z-lines are contiguous:
+ *   cx[o]: coupling to (i, j-1, k), cy[o]: to (i-1, j, k), cz[o]: to (i, j, k-1)
+ * Coarse levels aggregate 2x2x2 cells (Galerkin product with piecewise
+ * constant prolongation: coarse couplings are sums of fine couplings across
+ * the aggregate faces).  The smoother is z-line Gauss-Seidel over columns in
+ * red-black order (forward before, reverse after the coarse correction, so
+ * the V-cycle is symmetric and serves as a CG preconditioner); each line is
+ * solved exactly with the Thomas algorithm, which takes care of the strong
+ * vertical coupling of thin layers.
+ * ====================================================================== */
+
+typedef struct {
+    int nl, nr, nc;
+    size_t n;
+    double *diag, *cx, *cy, *cz;
+    uint8_t* unk;
+    double *x, *b, *r;
+} mg_level;
+
+#define MG_MAX_LEVELS 24
+
+static void mg_free_level(mg_level* L)
+{
+    free(L->diag); free(L->cx); free(L->cy); free(L->cz); free(L->unk);
+    free(L->x); free(L->b); free(L->r);
+}
+
+static int mg_alloc_level(mg_level* L, int nl, int nr, int nc)
+{
+    L->nl = nl; L->nr = nr; L->nc = nc;
+    L->n = (size_t)nl * nr * nc;
+    L->diag = calloc(L->n, sizeof(double)); L->cx = calloc(L->n, sizeof(double));
+    L->cy = calloc(L->n, sizeof(double)); L->cz = calloc(L->n, sizeof(double));
+    L->unk = calloc(L->n, 1);
+    L->x = calloc(L->n, sizeof(double)); L->b = calloc(L->n, sizeof(double)); L->r = calloc(L->n, sizeof(double));
+    return (L->diag && L->cx && L->cy && L->cz && L->unk && L->x && L->b && L->r) ? 0 : -1;
+}
+
+/* y = A x on one level */
+static void mg_apply(const mg_level* L, const double* x, double* y)
+{
+    const size_t sj = (size_t)L->nl, si = (size_t)L->nc * L->nl, n = L->n;
+    for (size_t o = 0; o < n; o++) {
+        if (!L->unk[o]) { y[o] = 0.0; continue; }
+        double s = L->diag[o] * x[o];
+        s -= L->cz[o] * (L->cz[o] != 0.0 ? x[o - 1] : 0.0);
+        if (o + 1 < n) s -= L->cz[o + 1] * (L->cz[o + 1] != 0.0 ? x[o + 1] : 0.0);
+        s -= L->cx[o] * (L->cx[o] != 0.0 ? x[o - sj] : 0.0);
+        if (o + sj < n) s -= L->cx[o + sj] * (L->cx[o + sj] != 0.0 ? x[o + sj] : 0.0);
+        s -= L->cy[o] * (L->cy[o] != 0.0 ? x[o - si] : 0.0);
+        if (o + si < n) s -= L->cy[o + si] * (L->cy[o + si] != 0.0 ? x[o + si] : 0.0);
+        y[o] = s;
+    }
+}
+
+/* exact solve along the z-line of column (i, j) with the horizontal
+ * neighbours held fixed */
+static void mg_line(mg_level* L, int i, int j, double* cp, double* dp)
+{
+    const int nl = L->nl;
+    const size_t sj = (size_t)nl, si = (size_t)L->nc * nl, n = L->n;
+    const size_t o0 = ((size_t)i * L->nc + j) * nl;
+    for (int k = 0; k < nl; k++) {
+        size_t o = o0 + k;
+        if (!L->unk[o]) { cp[k] = 0.0; dp[k] = 0.0; continue; }
+        double rhs = L->b[o];
+        if (L->cx[o] != 0.0) rhs += L->cx[o] * L->x[o - sj];
+        if (o + sj < n && L->cx[o + sj] != 0.0) rhs += L->cx[o + sj] * L->x[o + sj];
+        if (L->cy[o] != 0.0) rhs += L->cy[o] * L->x[o - si];
+        if (o + si < n && L->cy[o + si] != 0.0) rhs += L->cy[o + si] * L->x[o + si];
+        /* tridiagonal row: -cz[o] x[k-1] + diag x[k] - cz[o+1] x[k+1] = rhs */
+        double a = (k > 0) ? -L->cz[o] : 0.0;
+        double c = (k + 1 < nl) ? -L->cz[o + 1] : 0.0;
+        double den = L->diag[o] - (k > 0 ? a * cp[k - 1] : 0.0);
+        cp[k] = c / den;
+        dp[k] = (rhs - (k > 0 ? a * dp[k - 1] : 0.0)) / den;
+    }
+    for (int k = nl - 1; k >= 0; k--) {
+        size_t o = o0 + k;
+        if (!L->unk[o]) { L->x[o] = 0.0; continue; }
+        double v = dp[k] - (k + 1 < nl ? cp[k] * L->x[o + 1] : 0.0);
+        L->x[o] = v;
+    }
+}
+
+static void mg_smooth(mg_level* L, int reverse, double* cp, double* dp)
+{
+    for (int pass = 0; pass < 2; pass++) {
+        int color = reverse ? 1 - pass : pass;
+        for (int i = 0; i < L->nr; i++)
+            for (int j = 0; j < L->nc; j++)
+                if (((i + j) & 1) == color) mg_line(L, i, j, cp, dp);
+    }
+}
+
+/* build the Galerkin coarse level of F by 2x2x2 aggregation */
+static int mg_coarsen(const mg_level* F, mg_level* C)
+{
+    int cl = F->nl > 1 ? (F->nl + 1) / 2 : 1;
+    int cr = F->nr > 1 ? (F->nr + 1) / 2 : 1;
+    int cc = F->nc > 1 ? (F->nc + 1) / 2 : 1;
+    if (mg_alloc_level(C, cl, cr, cc)) return -1;
+    const int nl = F->nl, nc = F->nc;
+    for (int i = 0; i < F->nr; i++)
+        for (int j = 0; j < F->nc; j++)
+            for (int k = 0; k < F->nl; k++) {
+                size_t o = ((size_t)i * nc + j) * nl + k;
+                if (!F->unk[o]) continue;
+                int I = i / 2, J = j / 2, K = k / 2;
+                size_t O = ((size_t)I * cc + J) * cl + K;
+                C->unk[O] = 1;
+                C->diag[O] += F->diag[o];
+                if (j > 0 && F->cx[o] != 0.0) {
+                    if ((j - 1) / 2 == J) C->diag[O] -= 2.0 * F->cx[o];
+                    else C->cx[O] += F->cx[o];
+                }
+                if (i > 0 && F->cy[o] != 0.0) {
+                    if ((i - 1) / 2 == I) C->diag[O] -= 2.0 * F->cy[o];
+                    else C->cy[O] += F->cy[o];
+                }
+                if (k > 0 && F->cz[o] != 0.0) {
+                    if ((k - 1) / 2 == K) C->diag[O] -= 2.0 * F->cz[o];
+                    else C->cz[O] += F->cz[o];
+                }
+            }
+    for (size_t O = 0; O < C->n; O++)
+        if (!C->unk[O]) C->diag[O] = 1.0;
+    return 0;
+}
+
+static void mg_vcycle(mg_level* lv, int nlev, int l, double* cp, double* dp)
+{
+    mg_level* L = &lv[l];
+    if (l == nlev - 1) {
+        for (int s = 0; s < 60; s++) mg_smooth(L, s & 1, cp, dp);
+        return;
+    }
+    mg_smooth(L, 0, cp, dp);
+    mg_apply(L, L->x, L->r);
+    for (size_t o = 0; o < L->n; o++) L->r[o] = L->unk[o] ? L->b[o] - L->r[o] : 0.0;
+    mg_level* C = &lv[l + 1];
+    memset(C->b, 0, sizeof(double) * C->n);
+    memset(C->x, 0, sizeof(double) * C->n);
+    const int cl = C->nl, cc = C->nc;
+    for (int i = 0; i < L->nr; i++)
+        for (int j = 0; j < L->nc; j++)
+            for (int k = 0; k < L->nl; k++) {
+                size_t o = ((size_t)i * L->nc + j) * L->nl + k;
+                C->b[((size_t)(i / 2) * cc + j / 2) * cl + k / 2] += L->r[o];
+            }
+    mg_vcycle(lv, nlev, l + 1, cp, dp);
+    for (int i = 0; i < L->nr; i++)
+        for (int j = 0; j < L->nc; j++)
+            for (int k = 0; k < L->nl; k++) {
+                size_t o = ((size_t)i * L->nc + j) * L->nl + k;
+                if (L->unk[o]) L->x[o] += C->x[((size_t)(i / 2) * cc + j / 2) * cl + k / 2];
+            }
+    mg_smooth(L, 1, cp, dp);
+}
+
+int fg_solve_mg(int nlay, int nrow, int ncol,
+                const double* delr, const double* delc, const double* dz,
+                const double* K, const int8_t* ibound, const double* q_src,
+                double* head, double tol_abs, int max_iter,
+                double* qx, double* qy, double* qz,
+                double* out_maxres, int* out_iters)
+{
+    if (nlay <= 0 || nrow <= 0 || ncol <= 0) return FG_ERR_ARG;
+    mg_level lv[MG_MAX_LEVELS];
+    memset(lv, 0, sizeof(lv));
+    int nlev = 0, rc = FG_OK;
+    double *xs = NULL, *rs = NULL, *zs = NULL, *ps = NULL, *aps = NULL, *cp = NULL, *dp = NULL;
+    if (mg_alloc_level(&lv[0], nlay, nrow, ncol)) { rc = FG_ERR_OOM; goto done; }
+    nlev = 1;
+    mg_level* L0 = &lv[0];
+    const size_t n = L0->n;
+    const size_t sj = (size_t)nlay;
+    /* assemble the finest level (column order) */
+    for (int i = 0; i < nrow; i++)
+        for (int j = 0; j < ncol; j++)
+            for (int k = 0; k < nlay; k++) {
+                size_t o = ((size_t)i * ncol + j) * nlay + k;
+                L0->unk[o] = ibound[nat(k, i, j, nrow, ncol)] > 0;
+            }
+    double* rhs = L0->r;   /* temporarily the right-hand side */
+    for (int i = 0; i < nrow; i++)
+        for (int j = 0; j < ncol; j++)
+            for (int k = 0; k < nlay; k++) {
+                size_t o = ((size_t)i * ncol + j) * nlay + k;
+                size_t c = nat(k, i, j, nrow, ncol);
+                if (ibound[c] == 0) continue;
+                if (j > 0) {
+                    size_t cn = nat(k, i, j - 1, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delc[i] * dz[k], delr[j - 1], K[cn], delr[j], K[c]);
+                        size_t on = o - sj;
+                        if (L0->unk[o]) L0->diag[o] += C;
+                        if (L0->unk[on]) L0->diag[on] += C;
+                        if (L0->unk[o] && L0->unk[on]) L0->cx[o] = C;
+                        else if (L0->unk[o]) rhs[o] += C * head[cn];
+                        else if (L0->unk[on]) rhs[on] += C * head[c];
+                    }
+                }
+                if (i > 0) {
+                    size_t cn = nat(k, i - 1, j, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delr[j] * dz[k], delc[i - 1], K[cn], delc[i], K[c]);
+                        size_t on = o - (size_t)ncol * nlay;
+                        if (L0->unk[o]) L0->diag[o] += C;
+                        if (L0->unk[on]) L0->diag[on] += C;
+                        if (L0->unk[o] && L0->unk[on]) L0->cy[o] = C;
+                        else if (L0->unk[o]) rhs[o] += C * head[cn];
+                        else if (L0->unk[on]) rhs[on] += C * head[c];
+                    }
+                }
+                if (k > 0) {
+                    size_t cn = nat(k - 1, i, j, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delr[j] * delc[i], dz[k - 1], K[cn], dz[k], K[c]);
+                        size_t on = o - 1;
+                        if (L0->unk[o]) L0->diag[o] += C;
+                        if (L0->unk[on]) L0->diag[on] += C;
+                        if (L0->unk[o] && L0->unk[on]) L0->cz[o] = C;
+                        else if (L0->unk[o]) rhs[o] += C * head[cn];
+                        else if (L0->unk[on]) rhs[on] += C * head[c];
+                    }
+                }
+                if (L0->unk[o] && q_src) rhs[o] += q_src[c];
+            }
+    for (size_t o = 0; o < n; o++) {
+        if (L0->unk[o] && L0->diag[o] == 0.0) L0->unk[o] = 0;
+        if (!L0->unk[o]) L0->diag[o] = 1.0;
+    }
+    while (nlev < MG_MAX_LEVELS) {
+        mg_level* F = &lv[nlev - 1];
+        if (F->n <= 64 || (F->nl == 1 && F->nr == 1 && F->nc == 1)) break;
+        if (mg_coarsen(F, &lv[nlev])) { rc = FG_ERR_OOM; goto done; }
+        nlev++;
+    }
+    xs = calloc(n, sizeof(double)); rs = calloc(n, sizeof(double)); zs = calloc(n, sizeof(double));
+    ps = calloc(n, sizeof(double)); aps = calloc(n, sizeof(double));
+    cp = calloc((size_t)nlay + 1, sizeof(double)); dp = calloc((size_t)nlay + 1, sizeof(double));
+    if (!xs || !rs || !zs || !ps || !aps || !cp || !dp) { rc = FG_ERR_OOM; goto done; }
+    double* b0 = calloc(n, sizeof(double));
+    if (!b0) { rc = FG_ERR_OOM; goto done; }
+    memcpy(b0, rhs, sizeof(double) * n);
+    {
+        double hs = 0.0; size_t nh = 0;
+        for (size_t c = 0; c < n; c++) if (ibound[c] < 0) { hs += head[c]; nh++; }
+        double h0 = nh ? hs / (double)nh : 0.0;
+        for (size_t o = 0; o < n; o++) xs[o] = L0->unk[o] ? h0 : 0.0;
+    }
+    mg_apply(L0, xs, aps);
+    double maxres = 0.0;
+    for (size_t o = 0; o < n; o++) {
+        rs[o] = L0->unk[o] ? b0[o] - aps[o] : 0.0;
+        if (fabs(rs[o]) > maxres) maxres = fabs(rs[o]);
+    }
+    int it = 0;
+    double rz_old = 0.0;
+    while (maxres > tol_abs && it < max_iter) {
+        memcpy(L0->b, rs, sizeof(double) * n);
+        memset(L0->x, 0, sizeof(double) * n);
+        mg_vcycle(lv, nlev, 0, cp, dp);
+        memcpy(zs, L0->x, sizeof(double) * n);
+        double rz = 0.0;
+        for (size_t o = 0; o < n; o++) rz += rs[o] * zs[o];
+        if (it == 0) memcpy(ps, zs, sizeof(double) * n);
+        else {
+            double beta = rz / rz_old;
+            for (size_t o = 0; o < n; o++) ps[o] = zs[o] + beta * ps[o];
+        }
+        rz_old = rz;
+        mg_apply(L0, ps, aps);
+        double pap = 0.0;
+        for (size_t o = 0; o < n; o++) pap += ps[o] * aps[o];
+        if (!(pap > 0.0)) break;
+        double alpha = rz / pap;
+        for (size_t o = 0; o < n; o++) { xs[o] += alpha * ps[o]; rs[o] -= alpha * aps[o]; }
+        it++;
+        if (it % 20 == 0) {
+            mg_apply(L0, xs, aps);
+            for (size_t o = 0; o < n; o++) rs[o] = L0->unk[o] ? b0[o] - aps[o] : 0.0;
+        }
+        maxres = 0.0;
+        for (size_t o = 0; o < n; o++) if (fabs(rs[o]) > maxres) maxres = fabs(rs[o]);
+    }
+    free(b0);
+    /* heads back to natural order, then face flows */
+    for (int i = 0; i < nrow; i++)
+        for (int j = 0; j < ncol; j++)
+            for (int k = 0; k < nlay; k++) {
+                size_t o = ((size_t)i * ncol + j) * nlay + k;
+                size_t c = nat(k, i, j, nrow, ncol);
+                if (ibound[c] > 0) head[c] = L0->unk[o] ? xs[o] : 0.0;
+                else if (ibound[c] == 0) head[c] = 0.0;
+            }
+    memset(qx, 0, sizeof(double) * (size_t)nlay * nrow * (ncol + 1));
+    memset(qy, 0, sizeof(double) * (size_t)nlay * (nrow + 1) * ncol);
+    memset(qz, 0, sizeof(double) * (size_t)(nlay + 1) * nrow * ncol);
+    for (int k = 0; k < nlay; k++)
+        for (int i = 0; i < nrow; i++)
+            for (int j = 0; j < ncol; j++) {
+                size_t c = nat(k, i, j, nrow, ncol);
+                if (ibound[c] == 0) continue;
+                if (j > 0) {
+                    size_t cn = nat(k, i, j - 1, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delc[i] * dz[k], delr[j - 1], K[cn], delr[j], K[c]);
+                        qx[((size_t)k * nrow + i) * (ncol + 1) + j] = C * (head[cn] - head[c]);
+                    }
+                }
+                if (i > 0) {
+                    size_t cn = nat(k, i - 1, j, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delr[j] * dz[k], delc[i - 1], K[cn], delc[i], K[c]);
+                        qy[((size_t)k * (nrow + 1) + i) * ncol + j] = C * (head[cn] - head[c]);
+                    }
+                }
+                if (k > 0) {
+                    size_t cn = nat(k - 1, i, j, nrow, ncol);
+                    if (ibound[cn] != 0) {
+                        double C = cond(delr[j] * delc[i], dz[k - 1], K[cn], dz[k], K[c]);
+                        qz[((size_t)k * nrow + i) * ncol + j] = C * (head[cn] - head[c]);
+                    }
+                }
+            }
+    if (out_maxres) *out_maxres = maxres;
+    if (out_iters) *out_iters = it;
+    if (maxres > tol_abs) rc = FG_ERR_NOCONV;
+done:
+    for (int l = 0; l < nlev; l++) mg_free_level(&lv[l]);
+    free(xs); free(rs); free(zs); free(ps); free(aps); free(cp); free(dp);
+    return rc;
+}
