@@ -203,8 +203,10 @@ def run_ours(args):
     def one_step(prec, sched):
         gh = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset,
                                  stream=stream)
-        opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=prec, schedule=sched,
-                            times=w.times, block=args.block, steps_per_fetch=args.spf)
+        ts_mode = args.mode != "endpoint"
+        opts = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if ts_mode else 0), precision=prec,
+                            schedule=sched, times=w.times if ts_mode else None, block=args.block,
+                            steps_per_fetch=args.spf)
         rid = mp.mp_track(ctx.h, gh, opts, stream)
         return gh, rid
 
@@ -306,7 +308,7 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    if args.precisions != "fp64,mixed":
+    if args.precisions != "fp64,mixed" or args.mode != "endpoint+timeseries":
         # a partial run (profiling cases): report the timings only
         print(json.dumps({k: {"value": v["value"], "ms": v["ms_max"], "kernel_ms": v["kernel_ms"]}
                           for k, v in results.items()}), flush=True)
@@ -361,6 +363,8 @@ def main():
     ap.add_argument("--spf", type=int, default=0)
     ap.add_argument("--particles", type=int, default=0, help="override the particle count (profiling cases)")
     ap.add_argument("--precisions", default="fp64,mixed")
+    ap.add_argument("--mode", default="endpoint+timeseries", choices=["endpoint+timeseries", "endpoint"],
+                    help="profiling cases only; the benchmark line uses endpoint+timeseries")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

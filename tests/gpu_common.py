@@ -48,20 +48,20 @@ def rel_err(a, b, scale=None):
 
 
 def dmin(f):
-    """Smallest cell size per axis of a field."""
-    return (float(np.min(f.delr)), float(np.min(f.delc)), float(np.min(f.dz)))
+    """Position scale per axis: the extent of the grid along that axis."""
+    return (float(np.sum(f.delr)), float(np.sum(f.delc)), float(np.sum(f.dz)))
 
 
 def pos_scale(field, b):
     """Scale for position errors along one axis: the larger of |coordinate|
-    and the smallest cell size of that axis (a relative error of a coordinate
+    and the grid extent along that axis (a relative error of a coordinate
     near the origin says nothing)."""
     return np.maximum(np.abs(b), b * 0 + field)
 
 
 def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
     """FP64 parity: exact cell sequences and statuses; travel times within
-    rtol relative; positions within rtol relative to max(|x|, min cell size)."""
+    rtol relative; positions within rtol relative to max(|x|, grid extent)."""
     sel = slice(None) if idx is None else idx
     for k in KEYS_EXACT:
         a, b = ep[k][sel], ref[k]
