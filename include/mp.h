@@ -262,8 +262,9 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches);
  * required) and, in timeseries mode, the [n_times][n] record buffer (device).
  * times stays a host array.  The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.  Its only other device memory is a
- * fixed file-scope array of 8 + 10 + MP_NOALLOC_MAX_TIMES 64-bit words
- * (queue head, counters, a copy of the output times; about 33 KB) that every
+ * fixed file-scope array of 8 + 10 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words
+ * (queue head, counters, the output times in FP64 and as FP32 pairs; about
+ * 66 KB) that every
  * GPU that loads the library holds until the process exits.
  *   - The first call on each device takes the array's device address; make
  *     that first call before any stream capture.

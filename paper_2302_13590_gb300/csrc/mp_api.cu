@@ -464,6 +464,7 @@ int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes)
     if (ts) {
         b += align256(sizeof(mp_ts_record) * (size_t)o->n_times * (size_t)n);
         b += align256(sizeof(double) * (size_t)o->n_times);
+        b += align256(sizeof(float2) * (size_t)o->n_times);
     }
     *bytes = b;
     return MP_OK;
@@ -537,13 +538,21 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
     r->d.queue = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
     r->d.ts = nullptr;
     r->d.times = nullptr;
+    r->d.times_ff = nullptr;
     if (nt > 0) {
         r->d.ts = reinterpret_cast<mp_ts_record*>(take(sizeof(mp_ts_record) * (size_t)nt * (size_t)n));
         r->d.times = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nt));
+        r->d.times_ff = reinterpret_cast<float2*>(take(sizeof(float2) * (size_t)nt));
     }
     cudaError_t e = cudaSuccess;
     if (nt > 0) e = cudaMemcpyAsync(const_cast<double*>(r->d.times), o->times, sizeof(double) * nt,
                                     cudaMemcpyHostToDevice, s);
+    if (nt > 0 && e == cudaSuccess) {
+        std::vector<float2> ff((size_t)nt);
+        for (int k = 0; k < nt; ++k) split_ff(o->times[k], ff[k].x, ff[k].y);
+        e = cudaMemcpyAsync(const_cast<float2*>(r->d.times_ff), ff.data(), sizeof(float2) * nt,
+                            cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(r->d.counters, 0, sizeof(unsigned long long) * (N_COUNTERS + 0), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d.queue, 0, sizeof(unsigned long long), s);
@@ -557,6 +566,7 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
     p.n_times = nt;
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    split_ff(t_stop, p.tstop_hi, p.tstop_lo);
     const int block = o->block > 0 ? o->block : 128;
     if (e == cudaSuccess) {
         if (o->precision == MP_PREC_FP64) e = launch_track_fp64(g->field->d, g->d, r->d, p, o->schedule, block, 0, s);

@@ -103,6 +103,7 @@ struct DevOut {
     unsigned long long* hash;
     mp_ts_record* ts;            // [n_times][n] or nullptr
     const double* times;         // device copy, [n_times]
+    const float2* times_ff;      // the same times as FP32 pairs (hi, lo)
     unsigned long long* counters;  // [N_COUNTERS]
     unsigned long long* queue;     // dynamic schedule head
 };
@@ -114,7 +115,15 @@ struct TrackParams {
     int n_times;
     int steps_per_fetch;
     int update_group;
+    float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
 };
+
+// split an FP64 value into an FP32 pair hi + lo (hi = round(v), lo = round(v - hi))
+inline void split_ff(double v, float& hi, float& lo)
+{
+    hi = (float)v;
+    lo = (v - (double)hi < 3.0e38 && v - (double)hi > -3.0e38) ? (float)(v - (double)hi) : 0.0f;
+}
 
 // Kernel launchers (each enqueues one kernel on `s`).
 cudaError_t launch_validate(const double* qx, long long nqx, const double* qy, long long nqy, const double* qz,

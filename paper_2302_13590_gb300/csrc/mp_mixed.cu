@@ -9,10 +9,18 @@
 //   xi(t) = xi + u_p t h(A t), h(w) = (e^w - 1) / w.
 // g and h use their Taylor series for |z|, |w| < 2^-7 (exact to below FP32
 // rounding there, and free of the 0/0 at z = 0); for z < -1/2 g takes
-// ln(u_exit / u_p) / z, which keeps full FP32 accuracy as u_exit -> 0.  The cumulative travel time,
-// the stop-time and output-time comparisons, and every global position are
-// FP64.  Compiled with FMA contraction on (FP32 results are compared with the
-// FP64 oracle within tolerances, not bit for bit).
+// ln(u_exit / u_p) / z, which keeps full FP32 accuracy as u_exit -> 0.
+//
+// The cumulative travel time is carried as an unevaluated pair of FP32
+// values (a double-float number, 48-bit significand): each step adds its
+// FP32 step time with Knuth's error-free two-sum, and output times and the
+// stop time are compared as pairs (the host splits them once per request).
+// GB300 executes FP64 at 1/64 of the FP32 rate and output events occur in a
+// different step on every lane, so FP64 arithmetic there would run in
+// divergent branches; the pair keeps the time to ~1e-14 relative at FP32
+// cost.  FP64 is used for the values written out: travel times and global
+// positions.  Compiled with FMA contraction on (results are compared with the
+// FP64 oracle within stated tolerances, not bit for bit).
 #include <cfloat>
 #include <cmath>
 
@@ -30,18 +38,38 @@ struct MixEngine {
     struct State {
         int c, i, j, k;
         float x0, x1, x2;  // local fractions in [0, 1]
-        // travel time: FP64 base at the last output / stop event plus the
-        // time since then as an unevaluated FP32 pair (ah + al, error-free
-        // two-sum per step); (rh + rl) = FP32 pair of tev - tb
-        double tb;
-        float ah, al, rh, rl;
+        float th, tl;  // travel time as an FP32 pair th + tl
+        float eh, el;  // next output time or the stop time, whichever is first
         unsigned steps;
         unsigned long long h;
         int kn;
         int st;
         int ef;
-        double tev;  // next output time or the stop time, whichever is first
     };
+
+    // ---- double-float helpers (pairs with |lo| <= ulp(hi) / 2) ----
+    // (nh, nl) = (th, tl) + dt, exact up to the final rounding of the low part
+    __device__ __forceinline__ static void ff_add(float th, float tl, float dt, float& nh, float& nl)
+    {
+        const float sh = th + dt;
+        const float bb = sh - th;
+        const float lo = tl + ((th - (sh - bb)) + (dt - bb));
+        nh = sh + lo;
+        nl = lo - (nh - sh);
+    }
+    __device__ __forceinline__ static bool ff_ge(float ah, float al, float bh, float bl)
+    {
+        return ah > bh || (ah == bh && al >= bl);
+    }
+    // (a - b) as one FP32 value; a and b close, so the high parts cancel exactly
+    __device__ __forceinline__ static float ff_diff(float ah, float al, float bh, float bl)
+    {
+        return (ah - bh) + (al - bl);
+    }
+    __device__ __forceinline__ float2 time_pair(int kk) const
+    {
+        return __ldg(o.times_ff + kk);
+    }
 
     static constexpr float SMALL = 0.0078125f;  // 2^-7
 
@@ -115,31 +143,16 @@ struct MixEngine {
         z = gz(s, s.x2);
     }
 
-    __device__ __forceinline__ static double time_of(const State& s)
+    // next event as a pair: the next output time or the stop time
+    __device__ __forceinline__ void next_event(State& s) const
     {
-        return s.tb + (double)s.ah + (double)s.al;
-    }
-
-    // restart the FP32 accumulator at FP64 time t
-    __device__ __forceinline__ static void flush(State& s, double t)
-    {
-        s.tb = t;
-        s.ah = 0.0f;
-        s.al = 0.0f;
-        const double rem = s.tev - t;
-        if (rem < 3.0e38) {
-            s.rh = (float)rem;
-            s.rl = (float)(rem - (double)s.rh);
-        } else {
-            s.rh = CUDART_INF_F;
-            s.rl = 0.0f;
+        float eh = p.tstop_hi, el = p.tstop_lo;
+        if (s.kn < p.n_times) {
+            const float2 tk = time_pair(s.kn);
+            if (!ff_ge(tk.x, tk.y, eh, el)) { eh = tk.x; el = tk.y; }
         }
-    }
-
-    __device__ __forceinline__ double next_event(const State& s) const
-    {
-        const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
-        return fmin(tk, p.t_stop);
+        s.eh = eh;
+        s.el = el;
     }
 
     template <bool TS>
@@ -171,8 +184,9 @@ struct MixEngine {
             }
         }
         if (s.st == MP_ST_ACTIVE && t0 >= p.t_stop) s.st = MP_ST_TIME;
-        s.tev = TS ? next_event(s) : p.t_stop;
-        flush(s, t0);
+        s.th = (float)t0;
+        s.tl = (float)(t0 - (double)s.th);
+        next_event(s);
     }
 
     // per-warp queue of deferred timeseries records (structure of arrays)
@@ -185,7 +199,8 @@ struct MixEngine {
     __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
         Q.x0[slot] = s.x0; Q.x1[slot] = s.x1; Q.x2[slot] = s.x2;
-        Q.tau[slot] = (float)(__ldg(o.times + kk) - time_of(s));
+        const float2 tk = time_pair(kk);
+        Q.tau[slot] = ff_diff(tk.x, tk.y, s.th, s.tl);
         Q.q[slot] = q;
         Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
         Q.kk[slot] = kk; Q.st[slot] = st;
@@ -213,7 +228,6 @@ struct MixEngine {
         int path = P_NONE;
         int m = 0;
         float Ax = 0, Ay = 0, Az = 0, up0 = 0, up1 = 0, up2 = 0, tmin = 0, nh = 0, nl = 0;
-        double t_end = 0;
         bool ev = false;
         int f0 = 0, f1 = 0, f2 = 0, ax = -1;
         unsigned nb = 0;
@@ -238,22 +252,22 @@ struct MixEngine {
                 if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
                 if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
                 s.steps++;
-                // error-free FP32 two-sum of the accumulated time and tmin
-                const float sh = s.ah + tmin;
-                const float bb = sh - s.ah;
-                const float lo = s.al + ((s.ah - (sh - bb)) + (tmin - bb));
-                nh = sh + lo;
-                nl = lo - (nh - sh);
-                ev = ax < 0 || nh > s.rh || (nh == s.rh && nl >= s.rl);
+                ff_add(s.th, s.tl, tmin, nh, nl);
+                ev = ax < 0 || ff_ge(nh, nl, s.eh, s.el);
                 if (ev) {
-                    t_end = time_of(s) + (double)tmin;
                     if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
-                    else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                    else if (ax < 0 || ff_ge(nh, nl, p.tstop_hi, p.tstop_lo)) path = P_TIME;
                     else path = P_CROSS;
                     if (TS) {
-                        const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
+                        // output times inside this step: t_k <= end of step
+                        const float rh = path == P_NOEXIT ? CUDART_INF_F : (path == P_TIME ? p.tstop_hi : nh);
+                        const float rl = path == P_NOEXIT ? 0.0f : (path == P_TIME ? p.tstop_lo : nl);
                         int kk = s.kn;
-                        while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                        while (kk < p.n_times) {
+                            const float2 tk = time_pair(kk);
+                            if (!ff_ge(rh, rl, tk.x, tk.y)) break;
+                            kk++;
+                        }
                         m = kk - s.kn;
                     }
                 } else {
@@ -263,10 +277,6 @@ struct MixEngine {
         }
         if (TS && __any_sync(0xffffffffu, m > 0)) {
             rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
-            if (m) {
-                s.kn += m;
-                s.tev = next_event(s);
-            }
         }
         if (path == P_NONE) return;
         if (path == P_NOEXIT) {
@@ -274,11 +284,12 @@ struct MixEngine {
             return;
         }
         if (path == P_TIME) {
-            const float dt = (float)(p.t_stop - time_of(s));
+            const float dt = ff_diff(p.tstop_hi, p.tstop_lo, s.th, s.tl);
             s.x0 = move(Ax, up0, s.x0, dt);
             s.x1 = move(Ay, up1, s.x1, dt);
             s.x2 = move(Az, up2, s.x2, dt);
-            flush(s, p.t_stop);
+            s.th = p.tstop_hi;
+            s.tl = p.tstop_lo;
             s.st = MP_ST_TIME;
             return;
         }
@@ -291,11 +302,11 @@ struct MixEngine {
         s.x0 = ax == 0 ? onface : n0;
         s.x1 = ax == 1 ? onface : n1;
         s.x2 = ax == 2 ? onface : n2;
-        if (ev) {
-            flush(s, t_end);
-        } else {
-            s.ah = nh;
-            s.al = nl;
+        s.th = nh;
+        s.tl = nl;
+        if (TS && m) {
+            s.kn += m;
+            next_event(s);
         }
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
@@ -332,7 +343,7 @@ struct MixEngine {
         o.cell[q] = s.c;
         o.x[q] = x; o.y[q] = y; o.z[q] = z;
         o.px[q] = px; o.py[q] = py; o.pz[q] = pz;
-        o.t[q] = time_of(s);
+        o.t[q] = (double)s.th + (double)s.tl;
         o.status[q] = (uint8_t)s.st;
         o.steps[q] = s.steps;
         o.exit_face[q] = (uint8_t)s.ef;
@@ -340,7 +351,7 @@ struct MixEngine {
         if (p.update_group && ok) {
             in.cell[q] = s.c;
             in.px[q] = px; in.py[q] = py; in.pz[q] = pz;
-            in.t[q] = time_of(s);
+            in.t[q] = (double)s.th + (double)s.tl;
             in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
         }
         atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);

@@ -19,8 +19,9 @@ using namespace mp;
 
 namespace {
 
-// queue head, reduction counters and a copy of the output times
-constexpr int kScratchWords = 8 + N_COUNTERS + MP_NOALLOC_MAX_TIMES;
+// queue head, reduction counters, a copy of the output times and the same
+// times as FP32 pairs
+constexpr int kScratchWords = 8 + N_COUNTERS + 2 * MP_NOALLOC_MAX_TIMES;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
@@ -91,11 +92,20 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     unsigned long long* queue = scratch;
     unsigned long long* counters = scratch + 8;
     double* times = reinterpret_cast<double*>(scratch + 8 + N_COUNTERS);
+    float2* times_ff = reinterpret_cast<float2*>(scratch + 8 + N_COUNTERS + MP_NOALLOC_MAX_TIMES);
     // the array keeps the last call's contents: the queue head and counters
     // must start from zero
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (8 + N_COUNTERS), s);
     if (e == cudaSuccess && nt > 0)
         e = cudaMemcpyAsync(times, o->times, sizeof(double) * nt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nt > 0) {
+        float2 ff[256];
+        for (int k0 = 0; k0 < nt && e == cudaSuccess; k0 += 256) {
+            const int cnt = nt - k0 < 256 ? nt - k0 : 256;
+            for (int k = 0; k < cnt; ++k) split_ff(o->times[k0 + k], ff[k].x, ff[k].y);
+            e = cudaMemcpyAsync(times_ff + k0, ff, sizeof(float2) * cnt, cudaMemcpyHostToDevice, s);
+        }
+    }
     if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: ") + cudaGetErrorString(e));
     DevState st{a->cell, a->px, a->py, a->pz, a->t, a->status};
     DevOut d{};
@@ -104,6 +114,7 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     d.hash = reinterpret_cast<unsigned long long*>(ep.hash);
     d.ts = nt > 0 ? a->ts : nullptr;
     d.times = times;
+    d.times_ff = times_ff;
     d.counters = counters;
     d.queue = queue;
     TrackParams p{};
@@ -113,6 +124,7 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     p.n_times = nt;
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    split_ff(p.t_stop, p.tstop_hi, p.tstop_lo);
     const int block = o->block > 0 ? o->block : 128;
     const DevField& fd = *mp::field_device_view(f);
     e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, st, d, p, o->schedule, block, 0, s)
