@@ -39,12 +39,42 @@ WORKLOAD = ("200x200x20 cells (5x5x1 m), lnK N(-9.2,1) exp. cov. (10,10,2) cells
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
+# Algorithmic work per cell-step (one exit-time evaluation, rows a1-a5):
+# FP64 form: 28 add/mul/compare + 8 IEEE divisions + 3 log1p + 2 expm1, with
+# a division counted as 10 flops (reciprocal seed, two Newton steps and a
+# remainder correction in FMAs) and log1p / expm1 as 40 flops each (argument
+# reduction, ~13-term polynomial by Horner FMAs, reconstruction):
+# 28 + 80 + 120 + 80 = 308 flops.
+FP64_FLOPS_PER_STEP = 308.0
+# Bytes per cell-step an ideal gather needs: FP64 field 6 x 8 (face flows) +
+# 8 (porosity) + 1 (neighbour ibound) = 57 B; FP32 field copy 6 x 4 + 4 + 1.
+BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
+# GB300 FP64 rate (no measured figure exists for it): 152 SMs x 2.07 GHz x
+# 4 flop/clk/SM = 1.26 TFLOP/s, the nominal 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def l2_read_gbs(torch, dev) -> float:
+    """L2-resident read bandwidth (64 MB buffer summed repeatedly)."""
+    x = torch.ones(16 << 20, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        x.sum()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(50):
+        x.sum()
+    b.record()
+    torch.cuda.synchronize(dev)
+    return 50 * x.numel() * 4 / (a.elapsed_time(b) / 1e3) / 1e9
 
 
 class ClockSampler:
@@ -316,16 +346,31 @@ def run_ours(args):
         return
 
     hbm, src = _peaks()
+    l2 = l2_read_gbs(torch, dev)
     rf = {}
     for name in ("fp64", "mixed"):
         r = results[name]
         kms = float(np.mean(r["kernel_ms"]))
         steps_per_launch = r["cell_steps"] / len(r["kernel_ms"])
-        bpu = 57.0 if name == "fp64" else 29.0
-        achieved = bpu * steps_per_launch / (kms / 1e3) / 1e9
-        rf[name] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "peak_source": f"{src} hbm_gbs", "kernel_ms": kms,
-                    "bytes_per_cell_step": bpu, "cell_steps_per_launch": steps_per_launch}
+        rate = steps_per_launch / (kms / 1e3)
+        gbs = BYTES_PER_STEP[name] * rate / 1e9
+        traffic = args.traffic_fp64 if name == "fp64" else args.traffic_mixed
+        if name == "fp64":
+            achieved = FP64_FLOPS_PER_STEP * rate / 1e12
+            rf[name] = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                        "peak_source": "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 flop/clk); no measured FP64 peak",
+                        "flops_per_cell_step": FP64_FLOPS_PER_STEP, "kernel_ms": kms,
+                        "cell_steps_per_launch": steps_per_launch,
+                        "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                     "bytes_per_cell_step": BYTES_PER_STEP[name]}}
+        else:
+            rf[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                        "traffic": traffic, "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                        "bytes_per_cell_step": BYTES_PER_STEP[name], "kernel_ms": kms,
+                        "cell_steps_per_launch": steps_per_launch,
+                        "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
+                                    "peak_source": "measured in this run: L2-resident 64 MB read"}}
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, seconds=args.cpu_seconds)
     f64 = results["fp64"]
     line = {
@@ -369,6 +414,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--traffic-fp64", type=float, default=None,
+                    help="ncu dram bytes per full launch of the FP64 kernel (from profiles/)")
+    ap.add_argument("--traffic-mixed", type=float, default=None,
+                    help="ncu dram bytes per full launch of the mixed kernel (from profiles/)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
