@@ -215,6 +215,18 @@ int mp_group_size(const mp_group* g, int64_t* n);
  * status).  Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
 int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out);
 
+/* Track several groups in one launch per precision: the particles of all
+ * groups form one index space handed out by the persistent work queue (or
+ * one thread each), the GPU form of the paper's dynamic schedule over one
+ * particle loop (Methods, "Multiprocessing"; Results, "Thread scheduling").
+ * groups[n] must share one field; opts[n] are per request (mode, times,
+ * t_stop, max_steps, flags); schedule, block and steps_per_fetch of a launch
+ * come from the first request of that precision.  out[n] receives request
+ * ids that behave as mp_track's (own outputs and counters; kernel_ms is the
+ * shared launch's time).  Errors: as mp_track; on error no request exists. */
+int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_opts* opts, void* stream,
+                   mp_req* out);
+
 /* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
  * wait is always bounded, and a negative value means 60 s) for a request.
  * Errors: MP_ERR_TIMEOUT (still running), MP_ERR_NOT_READY (unknown id),

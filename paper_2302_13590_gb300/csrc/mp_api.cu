@@ -477,9 +477,16 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches)
     return MP_OK;
 }
 
-int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out)
+}  // extern "C"
+
+namespace {
+
+// Check options and allocate one request's outputs (stream-ordered); fills
+// the request's device descriptor on the host side.
+int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream_t s, Request** out,
+                    mp::Req* hreq, bool* has_ts)
 {
-    if (!ctx || !g || !o || !out) return fail(MP_ERR_INVALID_ARG, "mp_track: NULL argument");
+    if (!g || !o) return fail(MP_ERR_INVALID_ARG, "mp_track: NULL argument");
     if (g->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_track: group belongs to another context");
     if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))
         return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
@@ -500,8 +507,6 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
     }
     double t_stop = o->t_stop;
     if (want_ts && !(o->mode & MP_MODE_ENDPOINT) && !(t_stop < INFINITY)) t_stop = o->times[nt - 1];
-    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const long long n = g->n;
     size_t bytes = 0;
     mp_track_opts oo = *o;
@@ -535,7 +540,7 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
     r->d.exit_face = reinterpret_cast<uint8_t*>(take((size_t)n));
     r->d.hash = reinterpret_cast<unsigned long long*>(take(8 * (size_t)n));
     r->d.counters = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * N_COUNTERS));
-    r->d.queue = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
+    take(sizeof(unsigned long long));   // spare word (queue head of a single-request launch)
     r->d.ts = nullptr;
     r->d.times = nullptr;
     r->d.times_ff = nullptr;
@@ -553,13 +558,17 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
         e = cudaMemcpyAsync(const_cast<float2*>(r->d.times_ff), ff.data(), sizeof(float2) * nt,
                             cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(r->d.counters, 0, sizeof(unsigned long long) * (N_COUNTERS + 0), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d.queue, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d.counters, 0, sizeof(unsigned long long) * N_COUNTERS, s);
     if (e == cudaSuccess) e = cudaEventCreate(&r->k0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->k1);
-    if (e == cudaSuccess) e = cudaEventRecord(r->k0, s);
-    TrackParams p{};
+    if (e != cudaSuccess) {
+        cudaFreeAsync(buf, s);
+        if (r->k0) cudaEventDestroy(r->k0);
+        if (r->k1) cudaEventDestroy(r->k1);
+        delete r;
+        return cuda_fail(e, "mp_track");
+    }
+    mp::TrackParams p{};
     p.n = n;
     p.t_stop = t_stop;
     p.max_steps = o->max_steps > 0 ? o->max_steps : 1000000LL;
@@ -567,27 +576,127 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
     split_ff(t_stop, p.tstop_hi, p.tstop_lo);
-    const int block = o->block > 0 ? o->block : 128;
+    hreq->in = g->d;
+    hreq->o = r->d;
+    hreq->p = p;
+    *has_ts = nt > 0;
+    *out = r;
+    return MP_OK;
+}
+
+void drop_request(Request* r)
+{
+    cudaFreeAsync(r->buf, r->stream);
+    cudaEventDestroy(r->k0);
+    cudaEventDestroy(r->k1);
+    delete r;
+}
+
+// One launch over prepared requests of one precision (Methods,
+// "Multiprocessing": a single particle loop over every particle).
+int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n, int precision, int schedule,
+                    int block, int spf, bool ts, cudaStream_t s)
+{
+    size_t off = 0;
+    const size_t o_req = off; off = align256(off + sizeof(mp::Req) * (size_t)n);
+    const size_t o_st = off; off = align256(off + sizeof(long long) * ((size_t)n + 1));
+    const size_t o_q = off; off = align256(off + sizeof(unsigned long long));
+    char* tbl = nullptr;
+    if (cudaMallocAsync(&tbl, off, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_ERR_OOM, "mp_track: device allocation failed");
+    }
+    std::vector<long long> starts((size_t)n + 1, 0);
+    for (int i = 0; i < n; ++i) starts[i + 1] = starts[i] + hreqs[i].p.n;
+    cudaError_t e = cudaMemcpyAsync(tbl + o_req, hreqs, sizeof(mp::Req) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tbl + o_st, starts.data(), sizeof(long long) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tbl + o_q, 0, sizeof(unsigned long long), s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(rs[i]->k0, s);
+    mp::Batch b{};
+    b.reqs = reinterpret_cast<const mp::Req*>(tbl + o_req);
+    b.starts = reinterpret_cast<const long long*>(tbl + o_st);
+    b.n_reqs = n;
+    b.n_total = starts[n];
+    b.steps_per_fetch = spf > 0 ? spf : 4;
+    b.queue = reinterpret_cast<unsigned long long*>(tbl + o_q);
+    const int blk = block > 0 ? block : 128;
     if (e == cudaSuccess) {
-        if (o->precision == MP_PREC_FP64) e = launch_track_fp64(g->field->d, g->d, r->d, p, o->schedule, block, 0, s);
-        else e = launch_track_mixed(g->field->d, g->d, r->d, p, o->schedule, block, 0, s);
+        const mp::DevField& fd = *mp::field_device_view(f);
+        e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, ts, schedule, blk, 0, s)
+                                        : launch_track_mixed(fd, b, ts, schedule, blk, 0, s);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(r->k1, s);
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(s);
-        cudaFreeAsync(buf, s);
-        if (r->k0) cudaEventDestroy(r->k0);
-        if (r->k1) cudaEventDestroy(r->k1);
-        delete r;
-        return cuda_fail(e, "mp_track");
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(rs[i]->k1, s);
+    cudaFreeAsync(tbl, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_track: launch");
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out)
+{
+    if (!ctx || !g || !o || !out) return fail(MP_ERR_INVALID_ARG, "mp_track: NULL argument");
+    return mp_track_batch(ctx, 1, &g, o, stream, out);
+}
+
+int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_opts* opts, void* stream,
+                   mp_req* out)
+{
+    if (!ctx || !groups || !opts || !out || n < 0) return fail(MP_ERR_INVALID_ARG, "mp_track_batch: bad argument");
+    if (n == 0) return MP_OK;
+    for (int i = 0; i < n; ++i) {
+        if (!groups[i]) return fail(MP_ERR_INVALID_ARG, "mp_track_batch: NULL group");
+        if (groups[i]->field != groups[0]->field)
+            return fail(MP_ERR_INVALID_ARG, "mp_track_batch: all groups must be released on the same field");
     }
-    int64_t id;
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<Request*> rs((size_t)n, nullptr);
+    std::vector<mp::Req> hr((size_t)n);
+    std::vector<char> ts((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        bool has_ts = false;
+        const int rc = prepare_request(ctx, groups[i], &opts[i], s, &rs[i], &hr[i], &has_ts);
+        if (rc != MP_OK) {
+            for (int k = 0; k < i; ++k) drop_request(rs[k]);
+            return rc;
+        }
+        ts[i] = has_ts;
+    }
+    // one launch per precision; launch options of the first request of each
+    for (int prec = 0; prec < 2; ++prec) {
+        std::vector<Request*> sel;
+        std::vector<mp::Req> sreq;
+        bool any_ts = false;
+        int first = -1;
+        for (int i = 0; i < n; ++i)
+            if (opts[i].precision == prec) {
+                if (first < 0) first = i;
+                sel.push_back(rs[i]);
+                sreq.push_back(hr[i]);
+                any_ts = any_ts || ts[i];
+            }
+        if (sel.empty()) continue;
+        const mp_track_opts& o0 = opts[first];
+        const int rc = launch_requests(groups[0]->field, sel.data(), sreq.data(), (int)sel.size(), prec,
+                                       o0.schedule, o0.block, o0.steps_per_fetch, any_ts, s);
+        if (rc != MP_OK) {
+            cudaStreamSynchronize(s);
+            for (int k = 0; k < n; ++k) drop_request(rs[k]);
+            return rc;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        id = ctx->next_id++;
-        ctx->reqs[id] = r;
+        for (int i = 0; i < n; ++i) {
+            const int64_t id = ctx->next_id++;
+            ctx->reqs[id] = rs[i];
+            out[i] = id;
+        }
     }
-    *out = id;
     return MP_OK;
 }
 

@@ -206,11 +206,10 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 
 struct F64Engine {
     DevField f;
-    DevState in;
-    DevOut o;
-    TrackParams p;
+    Batch b;
 
     struct State {
+        int r;            // request of the particle within the launch
         int c, i, j, k;
         double x0, x1, x2;   // offsets (m) from the cell's low faces
         double t;
@@ -263,6 +262,11 @@ struct F64Engine {
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
                                            int st) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
     }
 
@@ -281,13 +285,24 @@ struct F64Engine {
     // next time at which the step loop must leave its fast path
     __device__ __forceinline__ double next_event(const State& s) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
         return fmin(tk, p.t_stop);
     }
 
     template <bool TS>
-    __device__ __forceinline__ void load(long long q, State& s) const
+    __device__ __forceinline__ void load(int r, long long q, State& s) const
     {
+        s.r = r;
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         s.c = in.cell[q];
         s.st = in.status[q];
         s.x0 = in.px[q]; s.x1 = in.py[q]; s.x2 = in.pz[q];
@@ -319,11 +334,17 @@ struct F64Engine {
     struct RecQ {
         double p0[RQ_CAP], p1[RQ_CAP], p2[RQ_CAP], tau[RQ_CAP];
         long long q[RQ_CAP];
-        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP];
+        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP], r[RQ_CAP];
     };
 
     __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
+        Q.r[slot] = s.r;
         Q.p0[slot] = s.x0; Q.p1[slot] = s.x1; Q.p2[slot] = s.x2;
         Q.tau[slot] = __ldg(o.times + kk) - s.t;
         Q.q[slot] = q;
@@ -335,6 +356,9 @@ struct F64Engine {
     // every axis (the same operations as an endpoint stop at that time)
     __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
     {
+        const Req& R = b.reqs[Q.r[slot]];
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
         const int c = Q.c[slot], i = Q.i[slot], j = Q.j[slot], k = Q.k[slot];
         const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
         const double2* rp = reinterpret_cast<const double2*>(f.rec64 + c);
@@ -353,6 +377,11 @@ struct F64Engine {
     template <bool TS>
     __device__ __forceinline__ void step(long long q, State& s, bool live, RecQ& Q, int& qcount) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
         int path = P_NONE;
         int m = 0;
@@ -460,6 +489,11 @@ struct F64Engine {
     template <bool TS>
     __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         const bool ok = s.c >= 0;
         const double x = ok ? gx(s) : CUDART_NAN, y = ok ? gy(s) : CUDART_NAN, z = ok ? gz(s) : CUDART_NAN;
         o.cell[q] = s.c;
@@ -476,16 +510,15 @@ struct F64Engine {
             in.t[q] = s.t;
             in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
         }
-        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);
-        atomicAdd(s_cnt + COUNTER_STATUS + (s.st & 7), 1ULL);
+        count_ended(b, s.r, s.steps, s.st, s_cnt);
     }
 };
 
-cudaError_t launch_track_fp64(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
-                              int schedule, int block, int blocks_per_sm_cap, cudaStream_t s)
+cudaError_t launch_track_fp64(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+                              int blocks_per_sm_cap, cudaStream_t s)
 {
-    F64Engine e{f, st, o, p};
-    return launch_tracking(e, o.ts != nullptr && p.n_times > 0, schedule, block, blocks_per_sm_cap, s);
+    F64Engine e{f, b};
+    return launch_tracking(e, ts, schedule, block, blocks_per_sm_cap, s);
 }
 
 }  // namespace mp

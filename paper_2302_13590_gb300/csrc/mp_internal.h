@@ -105,7 +105,6 @@ struct DevOut {
     const double* times;         // device copy, [n_times]
     const float2* times_ff;      // the same times as FP32 pairs (hi, lo)
     unsigned long long* counters;  // [N_COUNTERS]
-    unsigned long long* queue;     // dynamic schedule head
 };
 
 struct TrackParams {
@@ -116,6 +115,24 @@ struct TrackParams {
     int steps_per_fetch;
     int update_group;
     float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
+};
+
+// One tracking request of a launch: its particle state, outputs and options.
+struct Req {
+    DevState in;
+    DevOut o;
+    TrackParams p;
+};
+
+// A launch tracks the particles of one or more requests as one index space:
+// global particle g belongs to request r with starts[r] <= g < starts[r+1].
+struct Batch {
+    const Req* reqs;             // [n_reqs], device
+    const long long* starts;     // [n_reqs + 1], device
+    int n_reqs;
+    long long n_total;
+    int steps_per_fetch;
+    unsigned long long* queue;   // dynamic schedule head (zeroed before launch)
 };
 
 // split an FP64 value into an FP32 pair hi + lo (hi = round(v), lo = round(v - hi))
@@ -136,10 +153,11 @@ cudaError_t launch_release_box(const DevField& f, const DevState& st, long long 
                                cudaStream_t s);
 cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long long n, const int32_t* cell,
                                     const double* local, const double* t0, cudaStream_t s);
-cudaError_t launch_track_fp64(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
-                              int schedule, int block, int blocks_per_sm_cap, cudaStream_t s);
-cudaError_t launch_track_mixed(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
-                               int schedule, int block, int blocks_per_sm_cap, cudaStream_t s);
+// ts: true if any request of the batch writes timeseries records
+cudaError_t launch_track_fp64(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+                              int blocks_per_sm_cap, cudaStream_t s);
+cudaError_t launch_track_mixed(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+                               int blocks_per_sm_cap, cudaStream_t s);
 
 // Host helpers shared by the entry points: the calling thread's error
 // message (what mp_last_error returns) and a loaded field's device view.

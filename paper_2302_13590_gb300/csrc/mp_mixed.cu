@@ -31,11 +31,10 @@ namespace mp {
 
 struct MixEngine {
     DevField f;
-    DevState in;
-    DevOut o;
-    TrackParams p;
+    Batch b;
 
     struct State {
+        int r;            // request of the particle within the launch
         int c, i, j, k;
         float x0, x1, x2;  // local fractions in [0, 1]
         float th, tl;  // travel time as an FP32 pair th + tl
@@ -66,7 +65,7 @@ struct MixEngine {
     {
         return (ah - bh) + (al - bl);
     }
-    __device__ __forceinline__ float2 time_pair(int kk) const
+    __device__ __forceinline__ static float2 time_pair(const DevOut& o, int kk)
     {
         return __ldg(o.times_ff + kk);
     }
@@ -129,6 +128,11 @@ struct MixEngine {
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
                                            int st) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         store_record(o.ts + (long long)kk * p.n + q, x, y, z, s.c, st);
     }
 
@@ -146,9 +150,14 @@ struct MixEngine {
     // next event as a pair: the next output time or the stop time
     __device__ __forceinline__ void next_event(State& s) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         float eh = p.tstop_hi, el = p.tstop_lo;
         if (s.kn < p.n_times) {
-            const float2 tk = time_pair(s.kn);
+            const float2 tk = time_pair(o, s.kn);
             if (!ff_ge(tk.x, tk.y, eh, el)) { eh = tk.x; el = tk.y; }
         }
         s.eh = eh;
@@ -156,8 +165,14 @@ struct MixEngine {
     }
 
     template <bool TS>
-    __device__ __forceinline__ void load(long long q, State& s) const
+    __device__ __forceinline__ void load(int r, long long q, State& s) const
     {
+        s.r = r;
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         s.c = in.cell[q];
         s.st = in.status[q];
         const double t0 = in.t[q];
@@ -193,13 +208,19 @@ struct MixEngine {
     struct RecQ {
         float x0[RQ_CAP], x1[RQ_CAP], x2[RQ_CAP], tau[RQ_CAP];
         long long q[RQ_CAP];
-        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP];
+        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP], r[RQ_CAP];
     };
 
     __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
+        Q.r[slot] = s.r;
         Q.x0[slot] = s.x0; Q.x1[slot] = s.x1; Q.x2[slot] = s.x2;
-        const float2 tk = time_pair(kk);
+        const float2 tk = time_pair(o, kk);
         Q.tau[slot] = ff_diff(tk.x, tk.y, s.th, s.tl);
         Q.q[slot] = q;
         Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
@@ -208,6 +229,9 @@ struct MixEngine {
 
     __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
     {
+        const Req& R = b.reqs[Q.r[slot]];
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
         State r;
         r.c = Q.c[slot]; r.i = Q.i[slot]; r.j = Q.j[slot]; r.k = Q.k[slot];
         const float tau = Q.tau[slot];
@@ -224,6 +248,11 @@ struct MixEngine {
     template <bool TS>
     __device__ __forceinline__ void step(long long q, State& s, bool live, RecQ& Q, int& qcount) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
         int path = P_NONE;
         int m = 0;
@@ -264,7 +293,7 @@ struct MixEngine {
                         const float rl = path == P_NOEXIT ? 0.0f : (path == P_TIME ? p.tstop_lo : nl);
                         int kk = s.kn;
                         while (kk < p.n_times) {
-                            const float2 tk = time_pair(kk);
+                            const float2 tk = time_pair(o, kk);
                             if (!ff_ge(rh, rl, tk.x, tk.y)) break;
                             kk++;
                         }
@@ -330,6 +359,11 @@ struct MixEngine {
     template <bool TS>
     __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
     {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
         const bool ok = s.c >= 0;
         double px = 0.0, py = 0.0, pz = 0.0, x = CUDART_NAN, y = CUDART_NAN, z = CUDART_NAN;
         if (ok) {
@@ -354,16 +388,15 @@ struct MixEngine {
             in.t[q] = (double)s.th + (double)s.tl;
             in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
         }
-        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)s.steps);
-        atomicAdd(s_cnt + COUNTER_STATUS + (s.st & 7), 1ULL);
+        count_ended(b, s.r, s.steps, s.st, s_cnt);
     }
 };
 
-cudaError_t launch_track_mixed(const DevField& f, const DevState& st, const DevOut& o, const TrackParams& p,
-                               int schedule, int block, int blocks_per_sm_cap, cudaStream_t s)
+cudaError_t launch_track_mixed(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+                               int blocks_per_sm_cap, cudaStream_t s)
 {
-    MixEngine e{f, st, o, p};
-    return launch_tracking(e, o.ts != nullptr && p.n_times > 0, schedule, block, blocks_per_sm_cap, s);
+    MixEngine e{f, b};
+    return launch_tracking(e, ts, schedule, block, blocks_per_sm_cap, s);
 }
 
 }  // namespace mp

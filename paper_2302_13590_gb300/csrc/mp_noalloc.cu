@@ -20,8 +20,9 @@ using namespace mp;
 namespace {
 
 // queue head, reduction counters, a copy of the output times and the same
-// times as FP32 pairs
-constexpr int kScratchWords = 8 + N_COUNTERS + 2 * MP_NOALLOC_MAX_TIMES;
+// times as FP32 pairs, and the launch's one-entry request table
+constexpr int kReqWords = (int)((sizeof(Req) + 2 * sizeof(long long) + 7) / 8);
+constexpr int kScratchWords = 8 + N_COUNTERS + 2 * MP_NOALLOC_MAX_TIMES + kReqWords;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
@@ -107,6 +108,8 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
         }
     }
     if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: ") + cudaGetErrorString(e));
+    Req* dreq = reinterpret_cast<Req*>(scratch + 8 + N_COUNTERS + 2 * MP_NOALLOC_MAX_TIMES);
+    long long* dstarts = reinterpret_cast<long long*>(reinterpret_cast<char*>(dreq) + sizeof(Req));
     DevState st{a->cell, a->px, a->py, a->pz, a->t, a->status};
     DevOut d{};
     d.cell = ep.cell; d.x = ep.x; d.y = ep.y; d.z = ep.z; d.px = ep.px; d.py = ep.py; d.pz = ep.pz; d.t = ep.t;
@@ -116,7 +119,6 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     d.times = times;
     d.times_ff = times_ff;
     d.counters = counters;
-    d.queue = queue;
     TrackParams p{};
     p.n = a->n;
     p.t_stop = (want_ts && !(o->mode & MP_MODE_ENDPOINT) && !(o->t_stop < INFINITY)) ? o->times[nt - 1] : o->t_stop;
@@ -127,8 +129,23 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     split_ff(p.t_stop, p.tstop_hi, p.tstop_lo);
     const int block = o->block > 0 ? o->block : 128;
     const DevField& fd = *mp::field_device_view(f);
-    e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, st, d, p, o->schedule, block, 0, s)
-                                       : launch_track_mixed(fd, st, d, p, o->schedule, block, 0, s);
+    Req hreq;
+    hreq.in = st;
+    hreq.o = d;
+    hreq.p = p;
+    const long long hstarts[2] = {0, a->n};
+    e = cudaMemcpyAsync(dreq, &hreq, sizeof(Req), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dstarts, hstarts, sizeof(hstarts), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: ") + cudaGetErrorString(e));
+    Batch b{};
+    b.reqs = dreq;
+    b.starts = dstarts;
+    b.n_reqs = 1;
+    b.n_total = a->n;
+    b.steps_per_fetch = p.steps_per_fetch;
+    b.queue = queue;
+    e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, nt > 0, o->schedule, block, 0, s)
+                                       : launch_track_mixed(fd, b, nt > 0, o->schedule, block, 0, s);
     if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: launch: ") + cudaGetErrorString(e));
     if (stats) {
         unsigned long long h[N_COUNTERS];

@@ -39,12 +39,42 @@ __device__ __forceinline__ void store_record(mp_ts_record* dst, double x, double
     __stcs(reinterpret_cast<int4*>(dst) + 1, b);
 }
 
+// Per-status counts and cell-step totals.  A launch of one request sums them
+// in shared memory and adds them once per block; a batch adds each ended
+// particle's counts to its own request's counters directly.
 template <class E>
 __device__ __forceinline__ void flush_counters(const E& e, unsigned long long* s_cnt)
 {
     __syncthreads();
+    if (e.b.n_reqs != 1) return;
+    unsigned long long* dst = e.b.reqs[0].o.counters;
     for (int i = threadIdx.x; i < N_COUNTERS - 1; i += blockDim.x)
-        if (s_cnt[i]) atomicAdd(e.o.counters + i, s_cnt[i]);
+        if (s_cnt[i]) atomicAdd(dst + i, s_cnt[i]);
+}
+
+__device__ __forceinline__ void count_ended(const Batch& b, int r, unsigned steps, int st,
+                                            unsigned long long* s_cnt)
+{
+    if (b.n_reqs == 1) {
+        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)steps);
+        atomicAdd(s_cnt + COUNTER_STATUS + (st & 7), 1ULL);
+    } else {
+        unsigned long long* c = b.reqs[r].o.counters;
+        atomicAdd(c + COUNTER_STEPS, (unsigned long long)steps);
+        atomicAdd(c + COUNTER_STATUS + (st & 7), 1ULL);
+    }
+}
+
+// request of global particle index g (starts ascending, starts[0] = 0)
+__device__ __forceinline__ int request_of(const Batch& b, long long g)
+{
+    int lo = 0, hi = b.n_reqs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(b.starts + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -120,9 +150,14 @@ __device__ __forceinline__ void tail_fill(const E& e, const typename E::State& s
         mask &= mask - 1;
         const double bx = __shfl_sync(FULL, x, L), by = __shfl_sync(FULL, y, L), bz = __shfl_sync(FULL, z, L);
         const int c = __shfl_sync(FULL, s.c, L), st = __shfl_sync(FULL, s.st, L), kn = __shfl_sync(FULL, s.kn, L);
+        const int r = __shfl_sync(FULL, s.r, L);
         const long long qq = __shfl_sync(FULL, q, L);
-        for (int kk = kn + lane; kk < e.p.n_times; kk += 32)
-            store_record(e.o.ts + (long long)kk * e.p.n + qq, bx, by, bz, c, st);
+        const Req& R = e.b.reqs[r];
+        const int nt = R.p.n_times;
+        mp_ts_record* ts = R.o.ts;
+        const long long n = R.p.n;
+        for (int kk = kn + lane; kk < nt; kk += 32)
+            store_record(ts + (long long)kk * n + qq, bx, by, bz, c, st);
     }
 }
 
@@ -136,11 +171,15 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
     const unsigned FULL = 0xffffffffu;
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
     int qcount = 0;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long q = 0;
     typename E::State s;
+    s.r = 0;
     bool live = false, ended = false;
-    if (q < e.p.n) {
-        e.template load<TS>(q, s);
+    if (g < e.b.n_total) {
+        const int r = request_of(e.b, g);
+        q = g - __ldg(e.b.starts + r);
+        e.template load<TS>(r, q, s);
         live = s.st == MP_ST_ACTIVE;
         ended = !live;
     }
@@ -171,26 +210,28 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const unsigned long long n = (unsigned long long)e.p.n;
-    const int S = e.p.steps_per_fetch > 0 ? e.p.steps_per_fetch : 1;
+    const unsigned long long n = (unsigned long long)e.b.n_total;
+    const int S = e.b.steps_per_fetch > 0 ? e.b.steps_per_fetch : 1;
     long long q = -1;
     bool live = false;
     bool drained = false;
     typename E::State s;
+    s.r = 0;
     while (true) {
         const unsigned idle = __ballot_sync(FULL, !live);
         bool ended = false;
         if (idle && !drained) {
             const unsigned cnt = __popc(idle);
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(e.o.queue, (unsigned long long)cnt);
+            if (lane == 0) base = atomicAdd(e.b.queue, (unsigned long long)cnt);
             base = __shfl_sync(FULL, base, 0);
             if (base + cnt >= n) drained = true;
             if (!live) {
                 const unsigned long long qq = base + __popc(idle & lt_mask);
                 if (qq < n) {
-                    q = (long long)qq;
-                    e.template load<TS>(q, s);
+                    const int r = request_of(e.b, (long long)qq);
+                    q = (long long)qq - __ldg(e.b.starts + r);
+                    e.template load<TS>(r, q, s);
                     live = s.st == MP_ST_ACTIVE;
                     ended = !live;
                 }
@@ -219,12 +260,12 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
 template <class E>
 cudaError_t launch_tracking(const E& e, bool ts, int schedule, int block, int blocks_per_sm_cap, cudaStream_t st)
 {
-    if (e.p.n <= 0) return cudaSuccess;
+    if (e.b.n_total <= 0) return cudaSuccess;
     if (block <= 0) block = 128;
     if (block > 256) block = 256;
     block = (block + 31) / 32 * 32;
     if (schedule == MP_SCHED_STATIC) {
-        const long long grid = (e.p.n + block - 1) / block;
+        const long long grid = (e.b.n_total + block - 1) / block;
         if (ts) k_track_static<E, true><<<(unsigned)grid, block, 0, st>>>(e);
         else k_track_static<E, false><<<(unsigned)grid, block, 0, st>>>(e);
         return cudaGetLastError();
@@ -240,7 +281,7 @@ cudaError_t launch_tracking(const E& e, bool ts, int schedule, int block, int bl
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
     long long grid = (long long)sms * per_sm;
-    const long long need = (e.p.n + block - 1) / block;
+    const long long need = (e.b.n_total + block - 1) / block;
     if (grid > need) grid = need;
     if (ts) k_track_dynamic<E, true><<<(unsigned)grid, block, 0, st>>>(e);
     else k_track_dynamic<E, false><<<(unsigned)grid, block, 0, st>>>(e);

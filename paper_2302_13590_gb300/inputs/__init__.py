@@ -424,3 +424,71 @@ def explicit_particles(f: Field, n: int, seed: int, cols: Optional[Tuple[int, in
     cells = np.asarray(cells[:n], dtype=np.int32)
     frac = rng.random((n, 3))
     return cells, frac
+
+
+# ---------------------------------------------------------------------------
+# Many-request workloads (batched launches and serving)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class RequestSpec:
+    """One tracking request: a box release on a field, a mode and its times."""
+    field_name: str
+    release: Release
+    timeseries: bool
+    times: Optional[np.ndarray]
+    arrival_s: float = 0.0
+
+
+def _box_in(f: Field, rng, edge_lo=0.05, edge_hi=0.5):
+    """Random axis-aligned box inside the active columns (1 .. ncol-2)."""
+    x0, x1 = f.face_x(1), f.face_x(f.ncol - 1)
+    Ly, Lz = float(f.delc.sum()), float(f.dz.sum())
+    ext = [x1 - x0, Ly, Lz]
+    org = [x0, f.origin[1], f.origin[2]]
+    lo, hi = [], []
+    for a in range(3):
+        e = rng.uniform(edge_lo, edge_hi) * ext[a]
+        s = org[a] + rng.uniform(0.0, ext[a] - e)
+        lo.append(s)
+        hi.append(s + e)
+    return tuple(lo), tuple(hi)
+
+
+def batch_workload(n_req: int = 256, seed: int = SEED_BASE + 4, n_min=1e2, n_max=1e6, n_times=20):
+    """Independent requests on the 200x200x20 field: particle counts
+    log-uniform in [n_min, n_max], random boxes (edge fraction U(0.05, 0.5)),
+    half endpoint-only and half with timeseries at n_times log-spaced times."""
+    f = cfg2_field()
+    rng = np.random.default_rng(seed)
+    ta = t_adv_of(f, math.exp(-9.2), 0.3)
+    times = log_times(ta, n_times)
+    specs = []
+    for r in range(n_req):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        lo, hi = _box_in(f, rng)
+        rel = Release(n, lo, hi, seed=int(rng.integers(1, 2**62)), id_offset=0)
+        ts = (r % 2) == 1
+        specs.append(RequestSpec("cfg2", rel, ts, times if ts else None))
+    return specs
+
+
+def serving_workload(n_req: int = 5000, rate_hz: float = 200.0, seed: int = SEED_BASE + 5, n_min=1e3, n_max=1e6,
+                     n_times=20):
+    """Poisson arrivals at rate_hz against the 50x50x1 and 200x200x20 fields
+    (each with probability 1/2), group sizes log-uniform in [n_min, n_max],
+    endpoint or timeseries (n_times log-spaced times) at random."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    specs = []
+    for _ in range(n_req):
+        t += rng.exponential(1.0 / rate_hz)
+        name = "cfg1" if rng.random() < 0.5 else "cfg2"
+        f = cfg1_field() if name == "cfg1" else cfg2_field()
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        lo, hi = _box_in(f, rng)
+        ts = bool(rng.random() < 0.5)
+        kg, por = (1e-4, 0.3) if name == "cfg1" else (math.exp(-9.2), 0.3)
+        times = log_times(t_adv_of(f, kg, por), n_times) if ts else None
+        specs.append(RequestSpec(name, Release(n, lo, hi, seed=int(rng.integers(1, 2**62))), ts, times, t))
+    return specs

@@ -102,6 +102,7 @@ SIGNATURES = {
     "mp_group_free": (ctypes.c_int, [_vp]),
     "mp_group_size": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
     "mp_track": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), _vp, _P(ctypes.c_int64)]),
+    "mp_track_batch": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp), _P(TrackOpts), _vp, _P(ctypes.c_int64)]),
     "mp_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
     "mp_query": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "mp_get_endpoints": (ctypes.c_int, [_vp, ctypes.c_int64, _P(Endpoints), ctypes.c_uint32, _vp]),
@@ -260,6 +261,16 @@ def mp_track(ctx, gh, opts: TrackOpts, stream=None) -> int:
     r = ctypes.c_int64()
     _check(load_library().mp_track(ctx, gh, ctypes.byref(opts), _stream(stream), ctypes.byref(r)))
     return r.value
+
+
+def mp_track_batch(ctx, groups, opts_list, stream=None):
+    """Several groups (one field) in one launch per precision; returns request ids."""
+    n = len(groups)
+    garr = (_vp * n)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in groups])
+    oarr = (TrackOpts * n)(*opts_list)
+    ids = (ctypes.c_int64 * n)()
+    _check(load_library().mp_track_batch(ctx, n, garr, oarr, _stream(stream), ids))
+    return [int(v) for v in ids]
 
 
 def mp_wait(ctx, req: int, timeout_us: int = -1):
