@@ -338,7 +338,7 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    if args.precisions != "fp64,mixed" or args.mode != "endpoint+timeseries":
+    if args.precisions != "fp64,mixed" or args.mode != "endpoint+timeseries" or args.particles:
         # a partial run (profiling cases): report the timings only
         print(json.dumps({k: {"value": v["value"], "ms": v["ms_max"], "kernel_ms": v["kernel_ms"]}
                           for k, v in results.items()}), flush=True)
@@ -371,6 +371,22 @@ def run_ours(args):
                         "cell_steps_per_launch": steps_per_launch,
                         "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
                                     "peak_source": "measured in this run: L2-resident 64 MB read"}}
+    serving = None
+    if not args.no_serve:
+        from paper_2302_13590_gb300 import serve as SV
+        fields = {"cfg1": ctx.field(I.cfg1_field()), "cfg2": fh}
+        serving = {}
+        for name, prec, nreq in (("mixed", mp.PREC_MIXED, args.serve_requests),
+                                 ("fp64", mp.PREC_FP64, max(1, args.serve_requests // 5))):
+            specs = I.serving_workload(n_req=nreq, rate_hz=200.0)
+            srv = SV.Server(ctx, fields, precision=prec, schedule=mp.SCHED_STATIC)
+            rep = srv.run(specs, realtime=True)
+            sm = rep.summary()
+            sm["offered_requests_per_s"] = 200.0
+            sm["offered_particles_per_s"] = float(sum(x.release.n for x in specs)) / specs[-1].arrival_s
+            serving[name] = sm
+        serving["workload"] = ("Poisson arrivals at 200 requests/s on the 50x50x1 and 200x200x20 fields (p = 1/2), "
+                               "group sizes log-uniform in 1e3..1e6, endpoint or 20-time timeseries at random")
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, seconds=args.cpu_seconds)
     f64 = results["fp64"]
     line = {
@@ -390,6 +406,7 @@ def run_ours(args):
                   "particles_per_s": results["mixed"]["particles_per_s"], "dtype": "f32+f64",
                   "roofline": rf["mixed"], "clocks": results["mixed"]["clocks"]},
         "status_counts": f64["status_counts"],
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -412,6 +429,8 @@ def main():
                     help="profiling cases only; the benchmark line uses endpoint+timeseries")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--traffic-fp64", type=float, default=None,

@@ -89,6 +89,9 @@ __device__ __forceinline__ int request_of(const Batch& b, long long g)
 
 constexpr int RQ_CAP = 64;   // requests per warp (>= 2 x 32)
 
+// dynamic shared memory: one record queue per warp of the block
+extern __shared__ __align__(16) unsigned char s_dyn[];
+
 template <class E>
 __device__ __forceinline__ void rq_drain(const E& e, typename E::RecQ& Q, int& qcount, bool all)
 {
@@ -165,7 +168,7 @@ template <class E, bool TS>
 __global__ void __launch_bounds__(256) k_track_static(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
-    __shared__ typename E::RecQ s_q[TS ? 8 : 1];
+    typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
@@ -202,7 +205,7 @@ template <class E, bool TS>
 __global__ void __launch_bounds__(256) k_track_dynamic(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
-    __shared__ typename E::RecQ s_q[TS ? 8 : 1];
+    typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
     __syncthreads();
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
@@ -264,10 +267,11 @@ cudaError_t launch_tracking(const E& e, bool ts, int schedule, int block, int bl
     if (block <= 0) block = 128;
     if (block > 256) block = 256;
     block = (block + 31) / 32 * 32;
+    const size_t smem = ts ? sizeof(typename E::RecQ) * (size_t)(block / 32) : 0;
     if (schedule == MP_SCHED_STATIC) {
         const long long grid = (e.b.n_total + block - 1) / block;
-        if (ts) k_track_static<E, true><<<(unsigned)grid, block, 0, st>>>(e);
-        else k_track_static<E, false><<<(unsigned)grid, block, 0, st>>>(e);
+        if (ts) k_track_static<E, true><<<(unsigned)grid, block, smem, st>>>(e);
+        else k_track_static<E, false><<<(unsigned)grid, block, smem, st>>>(e);
         return cudaGetLastError();
     }
     int dev = 0, sms = 0, per_sm = 0;
@@ -275,16 +279,16 @@ cudaError_t launch_tracking(const E& e, bool ts, int schedule, int block, int bl
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    if (ts) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, true>, block, 0);
-    else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, false>, block, 0);
+    if (ts) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, true>, block, smem);
+    else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, false>, block, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
     long long grid = (long long)sms * per_sm;
     const long long need = (e.b.n_total + block - 1) / block;
     if (grid > need) grid = need;
-    if (ts) k_track_dynamic<E, true><<<(unsigned)grid, block, 0, st>>>(e);
-    else k_track_dynamic<E, false><<<(unsigned)grid, block, 0, st>>>(e);
+    if (ts) k_track_dynamic<E, true><<<(unsigned)grid, block, smem, st>>>(e);
+    else k_track_dynamic<E, false><<<(unsigned)grid, block, smem, st>>>(e);
     return cudaGetLastError();
 }
 

@@ -240,7 +240,9 @@ def make_field(nlay, nrow, ncol, dx, dy, dz, *, lnk_mean=math.log(1e-4), lnk_var
         ib[k, i, j] = IB_SINK
         q_src[k, i, j] += q
     if tol_abs is None:
-        # flows scale with K * face area * gradient; ask for ~1e-9 of that per cell
+        # flows scale with K * face area * gradient; ask for ~1e-9 of that per
+        # cell, relative to the geometric-mean K (the solver also stops at its
+        # rounding floor, which grows with the conductance contrast)
         qscale = float(np.exp(lnk_mean)) * dy * dz * abs(h_west - h_east) / max(Lx, 1e-30)
         tol_abs = min(1e-12, qscale * 1e-9)
     h, qx, qy, qz, iters, maxres = solve_flow(nlay, nrow, ncol, delr, delc, dzv, K, ib, head, q_src,

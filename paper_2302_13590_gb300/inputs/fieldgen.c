@@ -564,7 +564,12 @@ int fg_solve_mg(int nlay, int nrow, int ncol,
     }
     int it = 0;
     double rz_old = 0.0;
+    double best = maxres;
+    int since_best = 0;
     while (maxres > tol_abs && it < max_iter) {
+        /* stop at the rounding floor: no halving of the best residual in 60 iterations */
+        if (maxres < 0.5 * best) { best = maxres; since_best = 0; }
+        else if (++since_best > 60) break;
         memcpy(L0->b, rs, sizeof(double) * n);
         memset(L0->x, 0, sizeof(double) * n);
         mg_vcycle(lv, nlev, 0, cp, dp);
