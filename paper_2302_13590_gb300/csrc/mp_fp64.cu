@@ -71,6 +71,9 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const do
         s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(r.v2z / dzz);
     }
     r.nb = nb;
+    r.fv1x = (float)r.v1x; r.fv2x = (float)r.v2x; r.fAx = (float)r.Ax;
+    r.fv1y = (float)r.v1y; r.fv2y = (float)r.v2y; r.fAy = (float)r.Ay;
+    r.fv1z = (float)r.v1z; r.fv2z = (float)r.v2z; r.fAz = (float)r.Az;
     s.nb = (uint32_t)nb;
     r64[c] = r;
     r32[c] = s;
@@ -243,6 +246,40 @@ struct F64Engine {
         return face ? te : CUDART_INF;
     }
 
+    __device__ __forceinline__ static int face_of(double v1, double v2, double vp)
+    {
+        return (vp > 0.0 && v2 > 0.0) ? 1 : ((vp < 0.0 && v1 < 0.0) ? -1 : 0);
+    }
+
+    template <class T>
+    __device__ __forceinline__ static T sel3(int a, T x, T y, T z)
+    {
+        return a == 0 ? x : (a == 1 ? y : z);
+    }
+
+    // FP32 estimate of an exit time from the exact FP64 distance d and
+    // particle velocity vp.  Relative error: the two conversions and the
+    // approximate division give ~5e-7 on t1 = d / vp and on z = A t1;
+    // g(z) = ln(1 + z) / z is evaluated by its series (|z| < 2^-7), by
+    // log1pf, or for z < -1/2 by ln(u_exit / vp) (the ratio, not 1 + z,
+    // carries the information there), which keeps its error below ~1.5e-6;
+    // in all, below ~3e-6.  Velocities too small for FP32 (|vp| < 1e-30) or
+    // a NaN mark the estimate as untrusted.
+    __device__ __forceinline__ static float estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
+    {
+        const float vf = (float)vp;
+        const float vs = face ? vf : 1.0f;
+        const float t1 = __fdividef((float)d, vs);
+        const float z = fA * t1;
+        float g;
+        if (fabsf(z) < 0.0078125f) g = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
+        else if (z < -0.5f) g = __fdividef(logf(__fdividef(fue, vs)), z);
+        else g = __fdividef(log1pf(z), z);
+        const float e = t1 * g;
+        unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(e == e));
+        return face ? e : CUDART_INF_F;
+    }
+
     // analytic motion along one axis for a time dt, clamped to the cell
     // (the same values as: s == 0 -> pp; w == 0 -> factor 1)
     __device__ __forceinline__ static double move(double A, double D, double vp, double pp, double dt)
@@ -399,6 +436,8 @@ struct F64Engine {
                 const double2* rp = reinterpret_cast<const double2*>(f.rec64 + s.c);
                 const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
                               r4 = __ldg(rp + 4);
+                const float4* rf = reinterpret_cast<const float4*>(rp + 5);
+                const float4 g0 = __ldg(rf + 0), g1 = __ldg(rf + 1), g2 = __ldg(rf + 2);
                 v1x = r0.x; Ax = r1.x; v1y = r1.y; Ay = r2.y; v1z = r3.x; Az = r4.x;
                 const double v2x = r0.y, v2y = r2.x, v2z = r3.y;
                 nb = (unsigned long long)__double_as_longlong(r4.y);
@@ -406,13 +445,51 @@ struct F64Engine {
                 vp0 = v1x + Ax * s.x0;
                 vp1 = v1y + Ay * s.x1;
                 vp2 = v1z + Az * s.x2;
-                const double te0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, f0);
-                const double te1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, f1);
-                const double te2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, f2);
+                // reachable faces (the same tests as exit_time) and FP32
+                // estimates of the three exit times
+                f0 = face_of(v1x, v2x, vp0);
+                f1 = face_of(v1y, v2y, vp1);
+                f2 = face_of(v1z, v2z, vp2);
+                bool u0, u1, u2;
+                const float e0 = estimate(f0, f0 > 0 ? D0 - s.x0 : -s.x0, vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
+                const float e1 = estimate(f1, f1 > 0 ? D1 - s.x1 : -s.x1, vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
+                const float e2 = estimate(f2, f2 > 0 ? D2 - s.x2 : -s.x2, vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
+                // candidates: every axis whose estimate is within 2^-10 of the
+                // smallest (the estimates are within ~3e-6 of the exact times),
+                // and every axis whose estimate cannot be trusted
+                float em = CUDART_INF_F;
+                int a0 = -1;
+                if (f0 && !u0 && e0 < em) { em = e0; a0 = 0; }
+                if (f1 && !u1 && e1 < em) { em = e1; a0 = 1; }
+                if (f2 && !u2 && e2 < em) { em = e2; a0 = 2; }
+                const float thr = em * (1.0f + 0.0009765625f);
+                const unsigned cand = ((f0 && (u0 || e0 <= thr)) ? 1u : 0u) | ((f1 && (u1 || e1 <= thr)) ? 2u : 0u) |
+                                      ((f2 && (u2 || e2 <= thr)) ? 4u : 0u);
+                if (a0 < 0 && cand) a0 = __ffs(cand) - 1;
                 tmin = CUDART_INF;
-                if (f0 != 0 && te0 < tmin) { tmin = te0; ax = 0; }
-                if (f1 != 0 && te1 < tmin) { tmin = te1; ax = 1; }
-                if (f2 != 0 && te2 < tmin) { tmin = te2; ax = 2; }
+                if (a0 >= 0) {
+                    // the exact FP64 exit time of the leading candidate (one
+                    // evaluation per lane, uniform across the warp)
+                    int fa;
+                    const double te = exit_time(sel3(a0, v1x, v1y, v1z), sel3(a0, v2x, v2y, v2z), sel3(a0, Ax, Ay, Az),
+                                                sel3(a0, D0, D1, D2), sel3(a0, vp0, vp1, vp2),
+                                                sel3(a0, s.x0, s.x1, s.x2), fa);
+                    tmin = te;
+                    ax = a0;
+                    if ((cand & ~(1u << a0)) || !(te == te)) {
+                        // close call (or an unusable value): every reachable
+                        // axis exactly, in axis order, smallest wins
+                        int fx;
+                        const double t0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, fx);
+                        const double t1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, fx);
+                        const double t2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, fx);
+                        tmin = CUDART_INF;
+                        ax = -1;
+                        if (f0 != 0 && t0 < tmin) { tmin = t0; ax = 0; }
+                        if (f1 != 0 && t1 < tmin) { tmin = t1; ax = 1; }
+                        if (f2 != 0 && t2 < tmin) { tmin = t2; ax = 2; }
+                    }
+                }
                 s.steps++;
                 t_end = s.t + tmin;
                 if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
@@ -447,17 +524,20 @@ struct F64Engine {
             s.st = MP_ST_TIME;
             return;
         }
-        // displacement to the exit face: every axis moves by the analytic
-        // formula (uniform across lanes), then the exit axis is put on its face
+        // displacement to the exit face: the two other axes move by the
+        // analytic formula (selected into two slots, uniform across lanes),
+        // the exit axis is put on its face
         const double dt = tmin;
-        const double n0 = move(Ax, D0, vp0, s.x0, dt);
-        const double n1 = move(Ay, D1, vp1, s.x1, dt);
-        const double n2 = move(Az, D2, vp2, s.x2, dt);
+        const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+        const double n1 = move(sel3(a1, Ax, Ay, Az), sel3(a1, D0, D1, D2), sel3(a1, vp0, vp1, vp2),
+                               sel3(a1, s.x0, s.x1, s.x2), dt);
+        const double n2 = move(sel3(a2, Ax, Ay, Az), sel3(a2, D0, D1, D2), sel3(a2, vp0, vp1, vp2),
+                               sel3(a2, s.x0, s.x1, s.x2), dt);
         const int face = ax == 0 ? f0 : (ax == 1 ? f1 : f2);
         const double Dax = ax == 0 ? D0 : (ax == 1 ? D1 : D2);
         const double onface = face > 0 ? Dax : 0.0;
-        s.x0 = ax == 0 ? onface : n0;
-        s.x1 = ax == 1 ? onface : n1;
+        s.x0 = ax == 0 ? onface : n1;
+        s.x1 = ax == 1 ? onface : (ax == 0 ? n1 : n2);
         s.x2 = ax == 2 ? onface : n2;
         s.t = t_end;
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);

@@ -1,9 +1,9 @@
 // mp_internal.h - device-side layouts and kernel launchers of libmp.
 //
 // Field layout in HBM (built once by mp_field_load):
-//   rec64[c]  80 B  {v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az, nb}: the FP64
-//             face velocities v = Q / (n * area) and gradients
-//             A = (v2 - v1) / D of Pollock (1988), one gather per cell-step.
+//   rec64[c]  128 B {v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az, nb, FP32 copies}:
+//             the FP64 face velocities v = Q / (n * area) and gradients
+//             A = (v2 - v1) / D of Pollock (1988), one line per cell-step.
 //   rec32[c]  32 B  {u1x, u2x, u1y, u2y, u1z, u2z, nb, pad}: the same
 //             velocities divided by the cell size (units 1/s) in FP32 for
 //             the mixed-precision path, which works in local fractions
@@ -27,8 +27,11 @@ enum : int { NB_ACTIVE = 0, NB_SINK = 1, NB_BOUNDARY = 2, NB_OUTSIDE = 3 };
 struct __align__(16) CellF64 {
     double v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az;
     unsigned long long nb;
+    // FP32 copies of the same values, for screening the exit axis
+    float fv1x, fv2x, fAx, fv1y, fv2y, fAy, fv1z, fv2z, fAz;
+    float pad[3];
 };
-static_assert(sizeof(CellF64) == 80, "CellF64 is 80 bytes");
+static_assert(sizeof(CellF64) == 128, "CellF64 is one 128-byte line");
 
 struct __align__(32) CellF32 {
     float u1x, u2x, u1y, u2y, u1z, u2z;

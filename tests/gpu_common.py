@@ -59,10 +59,22 @@ def pos_scale(field, b):
     return np.maximum(np.abs(b), b * 0 + field)
 
 
-def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
+def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), allow_divergent=0.0):
     """FP64 parity: exact cell sequences and statuses; travel times within
-    rtol relative; positions within rtol relative to max(|x|, grid extent)."""
+    rtol relative; positions within rtol relative to max(|x|, grid extent).
+
+    allow_divergent: fraction of particles whose cell sequence may differ
+    (for strongly ill-conditioned fields, where a 1-ulp difference between
+    the platforms' log1p/expm1 can flip a near-tie); the other particles
+    are held to the full check.  Returns the number of divergent particles."""
     sel = slice(None) if idx is None else idx
+    hsame = ep["hash"][sel] == ref["hash"]
+    ndiv = int((~hsame).sum())
+    assert ndiv <= allow_divergent * hsame.size, f"{ndiv} divergent cell sequences of {hsame.size}"
+    keep = np.nonzero(hsame)[0]
+    ep = {k: (np.asarray(v)[sel][keep]) for k, v in ep.items()}
+    ref = {k: (np.asarray(v)[keep] if np.ndim(v) == 1 else v) for k, v in ref.items()}
+    sel = slice(None)
     for k in KEYS_EXACT:
         a, b = ep[k][sel], ref[k]
         bad = np.nonzero(a != b)[0]
@@ -74,10 +86,17 @@ def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
         scale = None if gk == "t" else pos_scale(dmin[ax], b[fin])
         e = rel_err(a[fin], b[fin], scale=scale)
         assert e.max(initial=0.0) <= rtol, f"{gk}: max rel err {e.max()}"
+    return ndiv
 
 
-def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0)):
+def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), keep=None):
+    """Timeseries parity; keep = boolean mask of particles (of the sample) to
+    check (those whose cell sequence matches)."""
     sel = slice(None) if idx is None else idx
+    if keep is not None:
+        base = np.arange(ts.shape[1])[sel]
+        sel = base[keep]
+        ref = {k: (v[:, keep] if np.ndim(v) == 2 else v) for k, v in ref.items()}
     assert np.array_equal(ts["cell"][:, sel], ref["ts_cell"])
     assert np.array_equal(ts["status"][:, sel], ref["ts_status"])
     for ax, (gk, ok) in enumerate((("x", "ts_x"), ("y", "ts_y"), ("z", "ts_z"))):
