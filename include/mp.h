@@ -80,6 +80,9 @@ extern "C" {
 
 #define MP_SCHED_STATIC 0       /* one thread per particle, plain grid        */
 #define MP_SCHED_DYNAMIC 1      /* persistent warps refilled from a queue     */
+#define MP_SCHED_AUTO 2         /* the context's tuned launch (mp_autotune)
+                                   for this field, precision and mode, else
+                                   dynamic, 128 threads, 4 steps per fetch   */
 
 #define MP_TRACK_UPDATE_GROUP 1u /* write final state back into the group     */
 
@@ -226,6 +229,29 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
  * shared launch's time).  Errors: as mp_track; on error no request exists. */
 int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_opts* opts, void* stream,
                    mp_req* out);
+
+/* Launch configuration chosen by the autotuner. */
+typedef struct {
+    int32_t schedule;         /* MP_SCHED_STATIC or MP_SCHED_DYNAMIC */
+    int32_t block;
+    int32_t steps_per_fetch;
+    int32_t tried;            /* configurations timed */
+    float ms;                 /* best time of the timed sample */
+} mp_tuning;
+
+/* Time candidate launch configurations (static and dynamic schedule x block
+ * 64/128/256 x steps per fetch 1/4/16 for dynamic) on the first
+ * min(n, sample) particles of the group with options o (the group is not
+ * changed), keep the fastest in the context for (field, o->precision,
+ * timeseries or not) and return it; later requests with MP_SCHED_AUTO use
+ * it.  Synchronous (bounded waits).  The paper's scheduling study (Results,
+ * "Thread scheduling") is this choice made by measurement.
+ * Errors: as mp_track, MP_ERR_TIMEOUT. */
+int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample, void* stream, mp_tuning* out);
+
+/* Install a launch configuration (e.g. one cached from an earlier run) for
+ * (field, precision, timeseries). */
+int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t timeseries, const mp_tuning* t);
 
 /* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
  * wait is always bounded, and a negative value means 60 s) for a request.

@@ -76,6 +76,10 @@ def _load():
             lib.orc_philox4x32_10.restype = None
             lib.orc_exit_time.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_int)]
             lib.orc_exit_time.restype = ctypes.c_double
+            lib.orc_log1p.argtypes = [ctypes.c_double]
+            lib.orc_log1p.restype = ctypes.c_double
+            lib.orc_expm1.argtypes = [ctypes.c_double]
+            lib.orc_expm1.restype = ctypes.c_double
             lib.orc_move.argtypes = [ctypes.c_double] * 5
             lib.orc_move.restype = ctypes.c_double
             lib.orc_release_box.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp,
@@ -133,6 +137,14 @@ def exit_time(v1, v2, A, D, p):
     face = ctypes.c_int(0)
     t = lib.orc_exit_time(float(v1), float(v2), float(A), float(D), float(p), ctypes.byref(face))
     return t, face.value
+
+
+def log1p(x):
+    return _load().orc_log1p(float(x))
+
+
+def expm1(w):
+    return _load().orc_expm1(float(w))
 
 
 def move(v1, A, D, p, dt):

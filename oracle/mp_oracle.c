@@ -114,6 +114,59 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
     return h;
 }
 
+/* ---- log1p and expm1 from their series --------------------------------
+ * Both are evaluated with IEEE additions, multiplications and divisions
+ * only (plus the exact frexp/ldexp/rint), in a fixed order, so that any
+ * other implementation of the same steps produces the same bits.  Accuracy
+ * (pinned against the C library in the tests): within 2 ulp.
+ *
+ * log1p(x): u = 1 + x rounded, c = the rounding error of that sum (exact by
+ * the two-sum argument), u = m 2^e with m in [1/sqrt2, sqrt2), f = m - 1
+ * (exact), log(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716:
+ * 2 s (1 + s^2/3 + s^4/5 + ... + s^24/25); log1p(x) = e ln2 + log(1 + f)
+ * + c / u, ln 2 split in a high part exact in products with e and a low
+ * part.
+ *
+ * expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
+ * r = w - k ln2 (split as above), expm1(r) = r + r^2/2! + ... + r^14/14!
+ * (|r| <= 0.347), expm1(w) = (2^k - 1) + 2^k expm1(r).
+ */
+static const double ORC_LN2_HI = 6.93147180369123816490e-01;
+static const double ORC_LN2_LO = 1.90821492927058770002e-10;
+
+double orc_log1p(double x)
+{
+    double u = 1.0 + x;
+    double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
+    int e;
+    double m = frexp(u, &e);
+    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
+    double f = m - 1.0;
+    double s = f / (2.0 + f);
+    double z2 = s * s;
+    double p = 1.0 / 25.0;
+    for (int j = 11; j >= 0; j--) p = p * z2 + 1.0 / (double)(2 * j + 1);
+    double logm = 2.0 * s * p;
+    double de = (double)e;
+    return de * ORC_LN2_HI + ((logm + c / u) + de * ORC_LN2_LO);
+}
+
+double orc_expm1(double w)
+{
+    double k = (fabs(w) < 0.5 * ORC_LN2_HI) ? 0.0 : rint(w * 1.44269504088896338700e+00);
+    double r = (w - k * ORC_LN2_HI) - k * ORC_LN2_LO;
+    double p = 1.0 / 87178291200.0;   /* 1/14! */
+    double fact = 87178291200.0;
+    for (int j = 13; j >= 1; j--) {
+        fact = fact / (double)(j + 1);
+        p = p * r + 1.0 / fact;
+    }
+    double em = r * p;
+    if (k == 0.0) return em;
+    double t = ldexp(1.0, (int)k);
+    return (t - 1.0) + t * em;
+}
+
 /* ---- the Pollock pieces ---------------------------------------------- */
 
 double orc_exit_time(double v1, double v2, double A, double D, double p, int* face)
@@ -126,7 +179,7 @@ double orc_exit_time(double v1, double v2, double A, double D, double p, int* fa
     double t1 = d / vp;
     double z = A * t1;
     if (z == 0.0) return t1;
-    return t1 * (log1p(z) / z);
+    return t1 * (orc_log1p(z) / z);
 }
 
 double orc_move(double v1, double A, double D, double p, double dt)
@@ -135,7 +188,7 @@ double orc_move(double v1, double A, double D, double p, double dt)
     double s = vp * dt;
     if (s == 0.0) return p;
     double w = A * dt;
-    double f = (w == 0.0) ? 1.0 : expm1(w) / w;
+    double f = (w == 0.0) ? 1.0 : orc_expm1(w) / w;
     double pn = p + s * f;
     if (pn < 0.0) pn = 0.0;
     if (pn > D) pn = D;

@@ -93,9 +93,22 @@ struct Request {
     cudaEvent_t k0 = nullptr, k1 = nullptr;
 };
 
+struct TuneKey {
+    const mp_field* f;
+    int precision;
+    int ts;
+    bool operator<(const TuneKey& o) const
+    {
+        if (f != o.f) return f < o.f;
+        if (precision != o.precision) return precision < o.precision;
+        return ts < o.ts;
+    }
+};
+
 struct mp_ctx {
     int device = 0;
     std::mutex mu;
+    std::map<TuneKey, mp_tuning> tuned;
     std::map<int64_t, Request*> reqs;
     std::set<mp_field*> fields;
     std::set<mp_group*> groups;
@@ -492,7 +505,7 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
         return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
     if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown precision");
-    if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC)
+    if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC && o->schedule != MP_SCHED_AUTO)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown schedule");
     if (o->block < 0 || o->block > 1024) return fail(MP_ERR_INVALID_ARG, "mp_track: block outside [0, 1024]");
     if (std::isnan(o->t_stop)) return fail(MP_ERR_INVALID_ARG, "mp_track: t_stop is NaN");
@@ -681,8 +694,21 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
             }
         if (sel.empty()) continue;
         const mp_track_opts& o0 = opts[first];
+        int sched = o0.schedule, blk = o0.block, spf = o0.steps_per_fetch;
+        if (sched == MP_SCHED_AUTO) {
+            sched = MP_SCHED_DYNAMIC;
+            blk = 128;
+            spf = 4;
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            auto it = ctx->tuned.find(TuneKey{groups[0]->field, prec, any_ts ? 1 : 0});
+            if (it != ctx->tuned.end()) {
+                sched = it->second.schedule;
+                blk = it->second.block;
+                spf = it->second.steps_per_fetch;
+            }
+        }
         const int rc = launch_requests(groups[0]->field, sel.data(), sreq.data(), (int)sel.size(), prec,
-                                       o0.schedule, o0.block, o0.steps_per_fetch, any_ts, s);
+                                       sched, blk, spf, any_ts, s);
         if (rc != MP_OK) {
             cudaStreamSynchronize(s);
             for (int k = 0; k < n; ++k) drop_request(rs[k]);
@@ -859,3 +885,64 @@ void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 const DevField* field_device_view(const mp_field* f) { return &f->d; }
 
 }  // namespace mp
+
+extern "C" {
+
+int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t timeseries, const mp_tuning* t)
+{
+    if (!ctx || !f || !t) return fail(MP_ERR_INVALID_ARG, "mp_set_tuning: NULL");
+    if ((t->schedule != MP_SCHED_STATIC && t->schedule != MP_SCHED_DYNAMIC) || t->block < 32 || t->block > 256 ||
+        t->steps_per_fetch < 0)
+        return fail(MP_ERR_INVALID_ARG, "mp_set_tuning: bad configuration");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned[TuneKey{f, precision, timeseries ? 1 : 0}] = *t;
+    return MP_OK;
+}
+
+int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample, void* stream, mp_tuning* out)
+{
+    if (!ctx || !g || !o || !out) return fail(MP_ERR_INVALID_ARG, "mp_autotune: NULL argument");
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    struct Cand { int sched, block, spf; };
+    std::vector<Cand> cands;
+    for (int b : {64, 128, 256}) cands.push_back({MP_SCHED_STATIC, b, 0});
+    for (int b : {64, 128, 256})
+        for (int spf : {1, 4, 16}) cands.push_back({MP_SCHED_DYNAMIC, b, spf});
+    mp_track_opts oo = *o;
+    oo.flags &= ~MP_TRACK_UPDATE_GROUP;
+    oo.schedule = MP_SCHED_DYNAMIC;
+    mp_tuning best{};
+    best.ms = INFINITY;
+    bool ts = false;
+    for (size_t ci = 0; ci <= cands.size(); ++ci) {
+        // the first pass warms the field and the allocator and is not counted
+        const Cand c = ci == 0 ? cands[0] : cands[ci - 1];
+        Request* r = nullptr;
+        mp::Req hr;
+        int rc = prepare_request(ctx, g, &oo, s, &r, &hr, &ts);
+        if (rc != MP_OK) return rc;
+        if (sample > 0 && hr.p.n > sample) hr.p.n = sample;
+        rc = launch_requests(g->field, &r, &hr, 1, o->precision, c.sched, c.block, c.spf, ts, s);
+        if (rc == MP_OK) rc = wait_event(r->k1, -1);
+        float ms = 0.f;
+        if (rc == MP_OK && cudaEventElapsedTime(&ms, r->k0, r->k1) != cudaSuccess) rc = fail(MP_ERR_CUDA, "timing");
+        drop_request(r);
+        if (rc != MP_OK) return rc;
+        if (ci > 0 && ms < best.ms) {
+            best.ms = ms;
+            best.schedule = c.sched;
+            best.block = c.block;
+            best.steps_per_fetch = c.spf;
+        }
+    }
+    best.tried = (int32_t)cands.size();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned[TuneKey{g->field, o->precision, ts ? 1 : 0}] = best;
+    }
+    *out = best;
+    return MP_OK;
+}
+
+}  // extern "C"

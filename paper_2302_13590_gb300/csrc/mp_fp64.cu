@@ -204,6 +204,78 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 }
 
 // ---------------------------------------------------------------------------
+// log1p and expm1 by argument reduction and series, with IEEE additions,
+// multiplications and divisions in a fixed order (no FMA: this file is built
+// with -fmad=false), so that the FP64 path produces the same bits as any
+// other evaluation of the same steps on the host.  Exit-axis choices near a
+// tie then agree exactly, which library functions with different last-bit
+// rounding cannot guarantee on ill-conditioned fields.
+//   log1p(x): u = 1 + x, c = its rounding error (two-sum), u = m 2^e with
+//     m in [1/sqrt2, sqrt2), f = m - 1, log(1 + f) = 2 atanh(f / (2 + f))
+//     by its odd series to the 25th power, + e ln2 (split) + c / u.
+//   expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
+//     r = w - k ln2 (split), expm1(r) by its Taylor series to r^14 / 14!,
+//     expm1(w) = (2^k - 1) + 2^k expm1(r).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double series_log1p(double x)
+{
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double u = 1.0 + x;
+    const double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
+    int e;
+    double m = frexp(u, &e);
+    if (m < 0.70710678118654752440) {
+        m = m * 2.0;
+        e = e - 1;
+    }
+    const double f = m - 1.0;
+    const double s = f / (2.0 + f);
+    const double z2 = s * s;
+    double p = 1.0 / 25.0;
+    p = p * z2 + 1.0 / 23.0;
+    p = p * z2 + 1.0 / 21.0;
+    p = p * z2 + 1.0 / 19.0;
+    p = p * z2 + 1.0 / 17.0;
+    p = p * z2 + 1.0 / 15.0;
+    p = p * z2 + 1.0 / 13.0;
+    p = p * z2 + 1.0 / 11.0;
+    p = p * z2 + 1.0 / 9.0;
+    p = p * z2 + 1.0 / 7.0;
+    p = p * z2 + 1.0 / 5.0;
+    p = p * z2 + 1.0 / 3.0;
+    p = p * z2 + 1.0;
+    const double logm = 2.0 * s * p;
+    const double de = (double)e;
+    return de * ln2_hi + ((logm + c / u) + de * ln2_lo);
+}
+
+__device__ __forceinline__ double series_expm1(double w)
+{
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double k = (fabs(w) < 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
+    const double r = (w - k * ln2_hi) - k * ln2_lo;
+    double p = 1.0 / 87178291200.0;           // 1/14!
+    p = p * r + 1.0 / 6227020800.0;           // 1/13!
+    p = p * r + 1.0 / 479001600.0;
+    p = p * r + 1.0 / 39916800.0;
+    p = p * r + 1.0 / 3628800.0;
+    p = p * r + 1.0 / 362880.0;
+    p = p * r + 1.0 / 40320.0;
+    p = p * r + 1.0 / 5040.0;
+    p = p * r + 1.0 / 720.0;
+    p = p * r + 1.0 / 120.0;
+    p = p * r + 1.0 / 24.0;
+    p = p * r + 1.0 / 6.0;
+    p = p * r + 1.0 / 2.0;
+    p = p * r + 1.0;
+    const double em = r * p;
+    if (k == 0.0) return em;
+    const double t = ldexp(1.0, (int)k);
+    return (t - 1.0) + t * em;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 tracking engine
 // ---------------------------------------------------------------------------
 
@@ -241,7 +313,7 @@ struct F64Engine {
         const double z = A * t1;
         const bool lin = (z == 0.0) || !face;
         const double zs = lin ? 1.0 : z;
-        const double g = log1p(zs) / zs;
+        const double g = series_log1p(zs) / zs;
         const double te = (z == 0.0) ? t1 : t1 * g;
         return face ? te : CUDART_INF;
     }
@@ -288,7 +360,7 @@ struct F64Engine {
         const double w = A * dt;
         const bool lin = (w == 0.0);
         const double ws = lin ? 1.0 : w;
-        const double e = expm1(ws) / ws;
+        const double e = series_expm1(ws) / ws;
         const double fct = lin ? 1.0 : e;
         double pn = pp + s * fct;
         if (pn < 0.0) pn = 0.0;

@@ -35,7 +35,7 @@ FACE_NONE = 255
 MP_DEVICE_PTR = 1
 PREC_FP64, PREC_MIXED = 0, 1
 MODE_ENDPOINT, MODE_TIMESERIES = 1, 2
-SCHED_STATIC, SCHED_DYNAMIC = 0, 1
+SCHED_STATIC, SCHED_DYNAMIC, SCHED_AUTO = 0, 1, 2
 TRACK_UPDATE_GROUP = 1
 RELEASE_EXPLICIT, RELEASE_BOX = 0, 1
 
@@ -80,6 +80,11 @@ class NoallocArgs(ctypes.Structure):
 NOALLOC_MAX_TIMES = 4096
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("block", ctypes.c_int32), ("steps_per_fetch", ctypes.c_int32),
+                ("tried", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("cell_steps", ctypes.c_uint64), ("n_status", ctypes.c_uint64 * 8),
                 ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32)]
@@ -113,6 +118,8 @@ SIGNATURES = {
     "mp_query_bytes": (ctypes.c_int, [_P(TrackOpts), ctypes.c_int64, _P(ctypes.c_size_t)]),
     "mp_track_launches": (ctypes.c_int, [_P(TrackOpts), _P(ctypes.c_int32)]),
     "mp_track_noalloc": (ctypes.c_int, [_vp, _P(NoallocArgs), _vp, _P(Stats)]),
+    "mp_autotune": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), ctypes.c_int64, _vp, _P(Tuning)]),
+    "mp_set_tuning": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning)]),
 }
 
 _lib = None
@@ -353,6 +360,40 @@ def mp_track_noalloc(fh, state: dict, out: dict, ts=None, opts: TrackOpts = None
         return None
     return {"cell_steps": int(st.cell_steps), "n_status": [int(v) for v in st.n_status],
             "kernel_ms": float(st.kernel_ms), "device_error": int(st.device_error)}
+
+
+def mp_autotune(ctx, gh, opts: TrackOpts, sample: int = 0, stream=None) -> dict:
+    """Time the candidate launch configurations; returns the fastest (also
+    kept in the context for MP_SCHED_AUTO)."""
+    t = Tuning()
+    _check(load_library().mp_autotune(ctx, gh, ctypes.byref(opts), int(sample), _stream(stream), ctypes.byref(t)))
+    return {"schedule": t.schedule, "block": t.block, "steps_per_fetch": t.steps_per_fetch, "tried": t.tried,
+            "ms": float(t.ms)}
+
+
+def mp_set_tuning(ctx, fh, precision: int, timeseries: bool, tuning: dict):
+    t = Tuning(int(tuning["schedule"]), int(tuning["block"]), int(tuning["steps_per_fetch"]),
+               int(tuning.get("tried", 0)), float(tuning.get("ms", 0.0)))
+    _check(load_library().mp_set_tuning(ctx, fh, int(precision), int(bool(timeseries)), ctypes.byref(t)))
+
+
+def load_tuning_cache(path: str) -> dict:
+    """Tuning results cached as JSON: {"<workload>/<precision>/<ts>": tuning}."""
+    import json
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_tuning_cache(path: str, cache: dict):
+    import json
+    import os as _os
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    _os.replace(tmp, path)
 
 
 # ---- conveniences -------------------------------------------------------------------

@@ -228,3 +228,22 @@ def test_exact_tie_goes_to_lowest_axis():
     assert r["exit_face"][0] == 1          # +x, not +y
     assert r["t"][0] == 1.5
     assert r["px"][0] == 2.0 and r["py"][0] == 2.0
+
+
+def test_series_log1p_expm1_against_libm():
+    """The oracle's own log1p/expm1 (argument reduction + series, IEEE basic
+    operations only) stay within a few ulp of the C library across the
+    ranges the tracker meets, and keep the limits exact."""
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([-np.exp(-rng.uniform(0, 40, 4000)), np.exp(rng.uniform(-60, 15, 4000)),
+                         -rng.uniform(0, 1, 4000) * (1 - 1e-12), rng.uniform(-1e-3, 1e-3, 4000)])
+    xs = xs[xs > -1]
+    worst = max(abs(O.log1p(x) - math.log1p(x)) / np.spacing(abs(math.log1p(x))) for x in xs if x != 0)
+    assert worst <= 4
+    ws = np.concatenate([rng.uniform(-40, 40, 4000), rng.uniform(-0.4, 0.4, 4000), rng.uniform(-1e-5, 1e-5, 4000),
+                         rng.uniform(-700, 700, 4000)])
+    worst = max(abs(O.expm1(w) - math.expm1(w)) / np.spacing(abs(math.expm1(w))) for w in ws if w != 0)
+    assert worst <= 4
+    assert O.log1p(0.0) == 0.0 and O.expm1(0.0) == 0.0
+    assert O.log1p(1e-300) == 1e-300 and O.expm1(-1e-300) == -1e-300
+    assert O.expm1(800.0) == math.inf and O.expm1(-800.0) == -1.0
