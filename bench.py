@@ -201,9 +201,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    from paper_2302_13590_gb300 import replicas
     w = I.workload("cfg2")
     n_part = args.particles or w.release.n
-    rel = I.Release(n_part, w.release.lo, w.release.hi, w.release.seed, id_offset=rank * n_part)
+    rel = replicas.shard_release(I.Release(n_part, w.release.lo, w.release.hi, w.release.seed), rank)
     n = rel.n
     nt = len(w.times)
     ctx = mp.Context(local)
@@ -276,14 +277,26 @@ def run_ours(args):
         return {"ms": ms, "wall_s": wall, "cell_steps": cell_steps, "kernel_ms": kern_ms, "clocks": clocks,
                 "status_counts": counts.tolist()}
 
+    # autotune the launch (block, schedule, steps per fetch) per precision on
+    # a 2e5-particle prefix, outside the timed region
+    tuning = {}
+    if args.schedule == mp.SCHED_AUTO:
+        for name, prec in (("fp64", mp.PREC_FP64), ("mixed", mp.PREC_MIXED)):
+            if name not in args.precisions:
+                continue
+            gh = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset,
+                                     stream=stream)
+            o = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if args.mode != "endpoint" else 0),
+                             precision=prec, times=w.times if args.mode != "endpoint" else None)
+            tuning[name] = mp.mp_autotune(ctx.h, gh, o, sample=min(n, 200_000), stream=stream)
+            mp.mp_group_free(gh)
+
     results = {}
     precs = [(nm, pr) for nm, pr in (("fp64", mp.PREC_FP64), ("mixed", mp.PREC_MIXED)) if nm in args.precisions]
     for name, prec in precs:
         r = timed(prec, args.schedule, args.steps, args.warmup)
-        ms_max = maxed(r["ms"])
-        steps_all = summed(r["cell_steps"])
-        results[name] = dict(r, ms_max=ms_max, cell_steps_all=steps_all,
-                             value=steps_all / (ms_max / 1e3),
+        steps_all, ms_max, value = replicas.job_rate(r["cell_steps"], r["ms"], world, dev)
+        results[name] = dict(r, ms_max=ms_max, cell_steps_all=steps_all, value=value,
                              particles_per_s=summed(n * args.steps) / (ms_max / 1e3))
 
     # end to end through the C ABI with host buffers: pinned host release
@@ -371,6 +384,31 @@ def run_ours(args):
                         "cell_steps_per_launch": steps_per_launch,
                         "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
                                     "peak_source": "measured in this run: L2-resident 64 MB read"}}
+    batch = None
+    if not args.no_batch:
+        specs = I.batch_workload()
+        batch = {"workload": "256 requests on the 200x200x20 field, sizes log-uniform in 1e2..1e6 (3.0e7 particles), "
+                             "random boxes, half with 20 output times; one launch per precision"}
+        for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
+            best = None
+            for rep in range(2):
+                groups = [mp.mp_release_group(ctx.h, fh, n=x.release.n, lo=x.release.lo, hi=x.release.hi,
+                                              seed=x.release.seed, stream=stream) for x in specs]
+                opts = [mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
+                                     precision=prec, schedule=mp.SCHED_DYNAMIC, times=x.times) for x in specs]
+                ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
+                sts = [mp.mp_get_stats(ctx.h, i) for i in ids]
+                steps_b = sum(x["cell_steps"] for x in sts)
+                kms = sts[0]["kernel_ms"]
+                for i in ids:
+                    mp.mp_req_free(ctx.h, i)
+                for g in groups:
+                    mp.mp_group_free(g)
+                if rep == 1:
+                    best = {"cell_steps_per_s": steps_b / (kms / 1e3), "kernel_ms": kms, "cell_steps": steps_b,
+                            "particles": int(sum(x.release.n for x in specs))}
+            batch[name] = best
+
     serving = None
     if not args.no_serve:
         from paper_2302_13590_gb300 import serve as SV
@@ -394,7 +432,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": f64["ms_max"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_gpu": n, "output_times": nt,
-                   "schedule": "dynamic" if args.schedule == mp.SCHED_DYNAMIC else "static",
+                   "schedule": {0: "static", 1: "dynamic", 2: "autotuned"}[args.schedule],
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
         "particles_per_s": f64["particles_per_s"],
         "roofline": rf["fp64"],
@@ -407,6 +445,8 @@ def run_ours(args):
                   "roofline": rf["mixed"], "clocks": results["mixed"]["clocks"]},
         "status_counts": f64["status_counts"],
         "serving": serving,
+        "batch": batch,
+        "tuning": tuning or None,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -420,7 +460,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--schedule", type=int, default=1)
+    ap.add_argument("--schedule", type=int, default=2, help="0 static, 1 dynamic, 2 autotuned (default)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spf", type=int, default=0)
     ap.add_argument("--particles", type=int, default=0, help="override the particle count (profiling cases)")
@@ -430,6 +470,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

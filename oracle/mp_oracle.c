@@ -115,17 +115,19 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
 }
 
 /* ---- log1p and expm1 from their series --------------------------------
- * Both are evaluated with IEEE additions, multiplications and divisions
- * only (plus the exact frexp/ldexp/rint), in a fixed order, so that any
+ * Both are evaluated with IEEE additions, multiplications, divisions and
+ * fused multiply-adds (C99 fma, one rounding) only, plus the exact
+ * frexp/ldexp/rint and one FP32 reciprocal, in a fixed order, so that any
  * other implementation of the same steps produces the same bits.  Accuracy
- * (pinned against the C library in the tests): within 2 ulp.
+ * (pinned against the C library in the tests): within a few ulp.
  *
  * log1p(x): u = 1 + x rounded, c = the rounding error of that sum (exact by
  * the two-sum argument), u = m 2^e with m in [1/sqrt2, sqrt2), f = m - 1
  * (exact), log(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716:
- * 2 s (1 + s^2/3 + s^4/5 + ... + s^24/25); log1p(x) = e ln2 + log(1 + f)
- * + c / u, ln 2 split in a high part exact in products with e and a low
- * part.
+ * 2 s (1 + s^2/3 + s^4/5 + ... + s^24/25) by Horner's rule with fma;
+ * log1p(x) = e ln2 + log(1 + f) + c / u, ln 2 split in a high part exact in
+ * products with e and a low part; c is below half an ulp of u, so c / u is
+ * taken as c times the FP32 reciprocal of u.
  *
  * expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
  * r = w - k ln2 (split as above), expm1(r) = r + r^2/2! + ... + r^14/14!
@@ -145,10 +147,11 @@ double orc_log1p(double x)
     double s = f / (2.0 + f);
     double z2 = s * s;
     double p = 1.0 / 25.0;
-    for (int j = 11; j >= 0; j--) p = p * z2 + 1.0 / (double)(2 * j + 1);
+    for (int j = 11; j >= 0; j--) p = fma(p, z2, 1.0 / (double)(2 * j + 1));
     double logm = 2.0 * s * p;
     double de = (double)e;
-    return de * ORC_LN2_HI + ((logm + c / u) + de * ORC_LN2_LO);
+    double ru = (double)(1.0f / (float)u);
+    return de * ORC_LN2_HI + ((logm + c * ru) + de * ORC_LN2_LO);
 }
 
 double orc_expm1(double w)
@@ -159,7 +162,7 @@ double orc_expm1(double w)
     double fact = 87178291200.0;
     for (int j = 13; j >= 1; j--) {
         fact = fact / (double)(j + 1);
-        p = p * r + 1.0 / fact;
+        p = fma(p, r, 1.0 / fact);
     }
     double em = r * p;
     if (k == 0.0) return em;

@@ -205,14 +205,16 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 
 // ---------------------------------------------------------------------------
 // log1p and expm1 by argument reduction and series, with IEEE additions,
-// multiplications and divisions in a fixed order (no FMA: this file is built
-// with -fmad=false), so that the FP64 path produces the same bits as any
-// other evaluation of the same steps on the host.  Exit-axis choices near a
+// multiplications, divisions and explicit fused multiply-adds in a fixed
+// order (no implicit contraction: this file is built with -fmad=false), so
+// that the FP64 path produces the same bits as any other evaluation of the
+// same steps on the host.  Exit-axis choices near a
 // tie then agree exactly, which library functions with different last-bit
 // rounding cannot guarantee on ill-conditioned fields.
 //   log1p(x): u = 1 + x, c = its rounding error (two-sum), u = m 2^e with
 //     m in [1/sqrt2, sqrt2), f = m - 1, log(1 + f) = 2 atanh(f / (2 + f))
-//     by its odd series to the 25th power, + e ln2 (split) + c / u.
+//     by its odd series to the 25th power (Horner, fma), + e ln2 (split)
+//     + c / u, with c (below half an ulp of u) times the FP32 reciprocal.
 //   expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
 //     r = w - k ln2 (split), expm1(r) by its Taylor series to r^14 / 14!,
 //     expm1(w) = (2^k - 1) + 2^k expm1(r).
@@ -233,21 +235,22 @@ __device__ __forceinline__ double series_log1p(double x)
     const double s = f / (2.0 + f);
     const double z2 = s * s;
     double p = 1.0 / 25.0;
-    p = p * z2 + 1.0 / 23.0;
-    p = p * z2 + 1.0 / 21.0;
-    p = p * z2 + 1.0 / 19.0;
-    p = p * z2 + 1.0 / 17.0;
-    p = p * z2 + 1.0 / 15.0;
-    p = p * z2 + 1.0 / 13.0;
-    p = p * z2 + 1.0 / 11.0;
-    p = p * z2 + 1.0 / 9.0;
-    p = p * z2 + 1.0 / 7.0;
-    p = p * z2 + 1.0 / 5.0;
-    p = p * z2 + 1.0 / 3.0;
-    p = p * z2 + 1.0;
+    p = fma(p, z2, 1.0 / 23.0);
+    p = fma(p, z2, 1.0 / 21.0);
+    p = fma(p, z2, 1.0 / 19.0);
+    p = fma(p, z2, 1.0 / 17.0);
+    p = fma(p, z2, 1.0 / 15.0);
+    p = fma(p, z2, 1.0 / 13.0);
+    p = fma(p, z2, 1.0 / 11.0);
+    p = fma(p, z2, 1.0 / 9.0);
+    p = fma(p, z2, 1.0 / 7.0);
+    p = fma(p, z2, 1.0 / 5.0);
+    p = fma(p, z2, 1.0 / 3.0);
+    p = fma(p, z2, 1.0);
     const double logm = 2.0 * s * p;
     const double de = (double)e;
-    return de * ln2_hi + ((logm + c / u) + de * ln2_lo);
+    const double ru = (double)__frcp_rn((float)u);
+    return de * ln2_hi + ((logm + c * ru) + de * ln2_lo);
 }
 
 __device__ __forceinline__ double series_expm1(double w)
@@ -256,19 +259,19 @@ __device__ __forceinline__ double series_expm1(double w)
     const double k = (fabs(w) < 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
     const double r = (w - k * ln2_hi) - k * ln2_lo;
     double p = 1.0 / 87178291200.0;           // 1/14!
-    p = p * r + 1.0 / 6227020800.0;           // 1/13!
-    p = p * r + 1.0 / 479001600.0;
-    p = p * r + 1.0 / 39916800.0;
-    p = p * r + 1.0 / 3628800.0;
-    p = p * r + 1.0 / 362880.0;
-    p = p * r + 1.0 / 40320.0;
-    p = p * r + 1.0 / 5040.0;
-    p = p * r + 1.0 / 720.0;
-    p = p * r + 1.0 / 120.0;
-    p = p * r + 1.0 / 24.0;
-    p = p * r + 1.0 / 6.0;
-    p = p * r + 1.0 / 2.0;
-    p = p * r + 1.0;
+    p = fma(p, r, 1.0 / 6227020800.0);           // 1/13!
+    p = fma(p, r, 1.0 / 479001600.0);
+    p = fma(p, r, 1.0 / 39916800.0);
+    p = fma(p, r, 1.0 / 3628800.0);
+    p = fma(p, r, 1.0 / 362880.0);
+    p = fma(p, r, 1.0 / 40320.0);
+    p = fma(p, r, 1.0 / 5040.0);
+    p = fma(p, r, 1.0 / 720.0);
+    p = fma(p, r, 1.0 / 120.0);
+    p = fma(p, r, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 1.0 / 2.0);
+    p = fma(p, r, 1.0);
     const double em = r * p;
     if (k == 0.0) return em;
     const double t = ldexp(1.0, (int)k);

@@ -109,6 +109,7 @@ class Server:
         inflight: List[Served] = []
         finished: List[Served] = []
         held = 0
+        peak_bytes = 0
         batches = 0
         peak = 0
         nxt = 0
@@ -168,6 +169,7 @@ class Server:
                     batches += 1
                 inflight.extend(admit)
                 peak = max(peak, len(inflight))
+                peak_bytes = max(peak_bytes, held)
             elif not inflight and realtime and nxt < n:
                 time.sleep(max(0.0, min(0.002, specs[nxt].arrival_s * time_scale - (time.perf_counter() - t0))))
             else:
@@ -177,4 +179,5 @@ class Server:
         qms = np.array([(s.admitted - s.arrival) * 1e3 for s in finished])
         self.results = {id(s.spec): s.result for s in finished if s.result is not None}
         return ServeReport(n, wall, int(sum(s.spec.release.n for s in finished)),
-                           int(sum(s.cell_steps for s in finished)), lat, qms, batches, peak)
+                           int(sum(s.cell_steps for s in finished)), lat, qms, batches, peak,
+                           extra={"peak_bytes": peak_bytes, "budget_bytes": self.budget})

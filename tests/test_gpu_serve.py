@@ -43,5 +43,12 @@ def test_memory_budget_limits_inflight(setup):
     one = max(S.Server(ctx, fields)._bytes(s) for s in specs)
     srv = S.Server(ctx, fields, memory_budget=int(2.5 * one))
     rep = srv.run(specs, realtime=False)
+    summ = rep.summary()
+    assert summ["peak_bytes"] <= summ["budget_bytes"]
+    assert summ["requests"] == 12
+    # with equal requests the budget admits two at a time
+    for s in specs:
+        s.timeseries, s.times = False, None
+    one = S.Server(ctx, fields)._bytes(specs[0])
+    rep = S.Server(ctx, fields, memory_budget=int(2.5 * one)).run(specs, realtime=False)
     assert rep.max_inflight <= 2
-    assert rep.summary()["requests"] == 12
