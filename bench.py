@@ -278,7 +278,8 @@ def run_ours(args):
                 "status_counts": counts.tolist()}
 
     # autotune the launch (block, schedule, steps per fetch) per precision on
-    # a 2e5-particle prefix, outside the timed region
+    # the whole group, outside the timed region: tail and queue costs depend
+    # on the particle count, so a smaller sample can rank the candidates wrongly
     tuning = {}
     if args.schedule == mp.SCHED_AUTO:
         for name, prec in (("fp64", mp.PREC_FP64), ("mixed", mp.PREC_MIXED)):
@@ -288,7 +289,7 @@ def run_ours(args):
                                      stream=stream)
             o = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if args.mode != "endpoint" else 0),
                              precision=prec, times=w.times if args.mode != "endpoint" else None)
-            tuning[name] = mp.mp_autotune(ctx.h, gh, o, sample=min(n, 200_000), stream=stream)
+            tuning[name] = mp.mp_autotune(ctx.h, gh, o, sample=0, stream=stream)
             mp.mp_group_free(gh)
 
     results = {}

@@ -85,6 +85,11 @@ extern "C" {
                                    dynamic, 128 threads, 4 steps per fetch   */
 
 #define MP_TRACK_UPDATE_GROUP 1u /* write final state back into the group     */
+#define MP_TRACK_PASS_WEAK_SINKS 2u /* enter sink cells and leave them through
+                                   a reachable face; a particle that has none
+                                   inside a sink cell is captured (SINK)
+                                   (the paper's second test case lets
+                                   particles pass through weak sinks) */
 
 #define MP_RELEASE_EXPLICIT 0
 #define MP_RELEASE_BOX 1
@@ -241,8 +246,8 @@ typedef struct {
 
 /* Time candidate launch configurations (static and dynamic schedule x block
  * 64/128/256 x steps per fetch 1/4/16 for dynamic) on the first
- * min(n, sample) particles of the group with options o (the group is not
- * changed), keep the fastest in the context for (field, o->precision,
+ * min(n, sample) particles of the group (sample <= 0: all of them) with
+ * options o (the group is not changed), keep the fastest in the context for (field, o->precision,
  * timeseries or not) and return it; later requests with MP_SCHED_AUTO use
  * it.  Synchronous (bounded waits).  The paper's scheduling study (Results,
  * "Thread scheduling") is this choice made by measurement.

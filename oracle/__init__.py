@@ -57,7 +57,7 @@ class _Field(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
-                ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64)]
+                ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32)]
 
 
 class _Out(ctypes.Structure):
@@ -186,7 +186,7 @@ def subset(state, idx):
     return {k: np.ascontiguousarray(v[idx]) for k, v in state.items()}
 
 
-def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None):
+def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False):
     """Track every particle of ``state`` (dict of cell, px, py, pz, t, status).
 
     Returns a dict with the endpoint arrays (cell, px, py, pz, gx, gy, gz, t,
@@ -215,7 +215,7 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None):
             res[k] = np.zeros((nt, n))
         res["ts_cell"] = np.zeros((nt, n), np.int32)
         res["ts_status"] = np.zeros((nt, n), np.uint8)
-    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps))
+    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)))
     out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_])
     rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
                        _ptr(s0), ctypes.byref(opts), ctypes.byref(out))

@@ -38,6 +38,11 @@
  *     the path (BOUNDARY), entering a sink cell (ibound 2) ends it (SINK,
  *     strong sink), leaving the grid ends it (EXIT_DOMAIN); in all three the
  *     particle stays in its last cell, on the face it left through;
+ *   - weak sinks (the paper's default for its second test case: particles
+ *     "pass through weak sink cells"): with pass_weak_sinks the particle
+ *     enters a sink cell like any other and leaves through a face it can
+ *     reach; when no face is reachable inside a sink cell the sink captures
+ *     it (SINK) where it is; a particle released in a sink cell stays SINK;
  *   - a cell-step is one exit-time evaluation, including zero-length steps
  *     and the final partial step; max_steps caps them (STEP_CAP);
  *   - output times t_k are recorded in the step whose interval (t, t + dt]
@@ -360,6 +365,11 @@ int orc_track(const orc_field* f, int64_t n,
             for (int a = 0; a < 3; a++)
                 if (face[a] != 0 && te[a] < tmin) { tmin = te[a]; ax = a; }
             steps++;
+            if (ax < 0 && f->ibound[c] == 2) {
+                /* inside a sink cell with no reachable face: captured */
+                st = ORC_ST_SINK;
+                break;
+            }
             if (ax < 0 && !(t_stop < INFINITY)) {
                 /* no reachable face and no stop time: the particle stays in
                  * this cell; later output times still see it move inside */
@@ -418,7 +428,7 @@ int orc_track(const orc_field* f, int64_t n,
             int32_t nc = (int32_t)(((int64_t)nk * nrow + ni) * ncol + nj);
             int8_t ib = f->ibound[nc];
             if (ib == 0 || ib == -1) { st = ORC_ST_BOUNDARY; break; }
-            if (ib == 2) { st = ORC_ST_SINK; break; }
+            if (ib == 2 && !opt->pass_weak_sinks) { st = ORC_ST_SINK; break; }
             j = nj; i = ni; k = nk; c = nc;
             if (face[ax] > 0) p[ax] = 0.0;
             else p[ax] = (ax == 0) ? f->delr[j] : (ax == 1) ? f->delc[i] : f->dz[k];

@@ -42,6 +42,7 @@ typedef struct {
     int32_t n_times;
     const double* times;  /* ascending */
     int64_t max_steps;    /* <= 0: default */
+    int32_t pass_weak_sinks; /* 1: enter sink cells, leave through outflow faces */
 } orc_track_opts;
 
 typedef struct {

@@ -588,6 +588,7 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     p.n_times = nt;
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
     split_ff(t_stop, p.tstop_hi, p.tstop_lo);
     hreq->in = g->d;
     hreq->o = r->d;

@@ -296,6 +296,7 @@ struct F64Engine {
         int kn;
         int st;
         int ef;
+        int in_sink;      // the current cell is a sink entered with pass-through
         double tev;  // next output time or the stop time, whichever is first
     };
 
@@ -423,9 +424,12 @@ struct F64Engine {
         s.h = FNV_INIT;
         s.kn = 0;
         s.ef = MP_FACE_NONE;
+        s.in_sink = 0;
         if (s.c >= 0 && (long long)s.c < f.ncell) {
             split_cell(f, s.c, s.k, s.i, s.j);
             s.h = fnv_step(s.h, s.c);
+            // a resumed particle may sit inside a sink cell it entered with pass-through
+            s.in_sink = __ldg(f.ibound + s.c) == 2;
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
             s.st = MP_ST_INVALID_RELEASE;
@@ -494,7 +498,7 @@ struct F64Engine {
         const DevOut& o = R.o;
         const TrackParams& p = R.p;
         (void)in; (void)o; (void)p;
-        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
+        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT, P_CAPTURE };
         int path = P_NONE;
         int m = 0;
         double v1x = 0, Ax = 0, v1y = 0, Ay = 0, v1z = 0, Az = 0, D0 = 1, D1 = 1, D2 = 1;
@@ -567,10 +571,11 @@ struct F64Engine {
                 }
                 s.steps++;
                 t_end = s.t + tmin;
-                if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                if (ax < 0 && s.in_sink) path = P_CAPTURE;
+                else if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
                 else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
                 else path = P_CROSS;
-                if (TS && (ax < 0 || t_end >= s.tev)) {
+                if (TS && path != P_CAPTURE && (ax < 0 || t_end >= s.tev)) {
                     const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
                     int kk = s.kn;
                     while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
@@ -586,6 +591,10 @@ struct F64Engine {
             }
         }
         if (path == P_NONE) return;
+        if (path == P_CAPTURE) {
+            s.st = MP_ST_SINK;
+            return;
+        }
         if (path == P_NOEXIT) {
             s.st = MP_ST_NO_EXIT;
             return;
@@ -618,10 +627,11 @@ struct F64Engine {
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3ULL);
-        if (cls != NB_ACTIVE) {
+        if (cls != NB_ACTIVE && !(cls == NB_SINK && p.pass_sinks)) {
             s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
             return;
         }
+        s.in_sink = cls == NB_SINK;
         // hand over to the neighbour; the exit coordinate enters on the shared face
         const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
         s.j += dj;

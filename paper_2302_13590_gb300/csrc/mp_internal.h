@@ -117,6 +117,7 @@ struct TrackParams {
     int n_times;
     int steps_per_fetch;
     int update_group;
+    int pass_sinks;              // enter sink cells, leave through outflow faces
     float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
 };
 

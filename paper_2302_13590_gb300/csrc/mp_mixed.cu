@@ -44,6 +44,7 @@ struct MixEngine {
         int kn;
         int st;
         int ef;
+        int in_sink;      // the current cell is a sink entered with pass-through
     };
 
     // ---- double-float helpers (pairs with |lo| <= ulp(hi) / 2) ----
@@ -180,12 +181,15 @@ struct MixEngine {
         s.h = FNV_INIT;
         s.kn = 0;
         s.ef = MP_FACE_NONE;
+        s.in_sink = 0;
         if (s.c >= 0 && (long long)s.c < f.ncell) {
             split_cell(f, s.c, s.k, s.i, s.j);
             s.x0 = __fdiv_rn((float)in.px[q], (float)__ldg(f.delr + s.j));
             s.x1 = __fdiv_rn((float)in.py[q], (float)__ldg(f.delc + s.i));
             s.x2 = __fdiv_rn((float)in.pz[q], (float)__ldg(f.dz + s.k));
             s.h = fnv_step(s.h, s.c);
+            // a resumed particle may sit inside a sink cell it entered with pass-through
+            s.in_sink = __ldg(f.ibound + s.c) == 2;
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
             s.x0 = s.x1 = s.x2 = 0.0f;
@@ -253,7 +257,7 @@ struct MixEngine {
         const DevOut& o = R.o;
         const TrackParams& p = R.p;
         (void)in; (void)o; (void)p;
-        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT };
+        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT, P_CAPTURE };
         int path = P_NONE;
         int m = 0;
         float Ax = 0, Ay = 0, Az = 0, up0 = 0, up1 = 0, up2 = 0, tmin = 0, nh = 0, nl = 0;
@@ -284,10 +288,11 @@ struct MixEngine {
                 ff_add(s.th, s.tl, tmin, nh, nl);
                 ev = ax < 0 || ff_ge(nh, nl, s.eh, s.el);
                 if (ev) {
-                    if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                    if (ax < 0 && s.in_sink) path = P_CAPTURE;
+                    else if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
                     else if (ax < 0 || ff_ge(nh, nl, p.tstop_hi, p.tstop_lo)) path = P_TIME;
                     else path = P_CROSS;
-                    if (TS) {
+                    if (TS && path != P_CAPTURE) {
                         // output times inside this step: t_k <= end of step
                         const float rh = path == P_NOEXIT ? CUDART_INF_F : (path == P_TIME ? p.tstop_hi : nh);
                         const float rl = path == P_NOEXIT ? 0.0f : (path == P_TIME ? p.tstop_lo : nl);
@@ -308,6 +313,10 @@ struct MixEngine {
             rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
         }
         if (path == P_NONE) return;
+        if (path == P_CAPTURE) {
+            s.st = MP_ST_SINK;
+            return;
+        }
         if (path == P_NOEXIT) {
             s.st = MP_ST_NO_EXIT;
             return;
@@ -340,10 +349,11 @@ struct MixEngine {
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3u);
-        if (cls != NB_ACTIVE) {
+        if (cls != NB_ACTIVE && !(cls == NB_SINK && p.pass_sinks)) {
             s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
             return;
         }
+        s.in_sink = cls == NB_SINK;
         const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
         s.j += dj;
         s.i += di;

@@ -126,6 +126,7 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     p.n_times = nt;
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
+    p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
     split_ff(p.t_stop, p.tstop_hi, p.tstop_lo);
     const int block = o->block > 0 ? o->block : 128;
     const DevField& fd = *mp::field_device_view(f);

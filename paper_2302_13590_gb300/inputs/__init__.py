@@ -365,12 +365,13 @@ def workload(name: str, n_particles: Optional[int] = None) -> Workload:
 
 def random_box_field(nlay, nrow, ncol, seed, lnk_var=1.0, corr=(2.0, 2.0, 1.0), dx=(1.0, 3.0),
                      dy=(1.0, 3.0), dz=(0.5, 2.0), porosity=(0.2, 0.4), n_wells=0,
-                     n_inactive=0) -> Field:
+                     n_inactive=0, well_scale=1.0) -> Field:
     """Small random test field with irregular rectilinear spacing.
 
     Cell sizes are drawn per column/row/layer, porosity per cell, optional
-    wells (strong sinks) and inactive cells; the head solve makes the flows
-    mass-conserving.
+    wells and inactive cells; the head solve makes the flows mass-conserving.
+    well_scale multiplies the well rates: a large one makes wells strong
+    (every face flows in), a small one weak (flow passes through).
     """
     rng = np.random.default_rng(seed)
     delr = rng.uniform(*dx, size=ncol)
@@ -392,7 +393,7 @@ def random_box_field(nlay, nrow, ncol, seed, lnk_var=1.0, corr=(2.0, 2.0, 1.0), 
     for _ in range(n_wells):
         k, i, j = int(rng.integers(0, nlay)), int(rng.integers(0, nrow)), int(rng.integers(1, ncol - 1))
         ib[k, i, j] = IB_SINK
-        q_src[k, i, j] = -float(rng.uniform(0.02, 0.1)) * 1e-4 * float(delc.sum() * dzv.sum()) / max(nrow * nlay, 1)
+        q_src[k, i, j] = -well_scale * float(rng.uniform(0.02, 0.1)) * 1e-4 * float(delc.sum() * dzv.sum()) / max(nrow * nlay, 1)
     for _ in range(n_inactive):
         k, i, j = int(rng.integers(0, nlay)), int(rng.integers(0, nrow)), int(rng.integers(1, ncol - 1))
         if ib[k, i, j] == IB_ACTIVE:

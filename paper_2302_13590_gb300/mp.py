@@ -37,6 +37,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 MODE_ENDPOINT, MODE_TIMESERIES = 1, 2
 SCHED_STATIC, SCHED_DYNAMIC, SCHED_AUTO = 0, 1, 2
 TRACK_UPDATE_GROUP = 1
+TRACK_PASS_WEAK_SINKS = 2
 RELEASE_EXPLICIT, RELEASE_BOX = 0, 1
 
 TS_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("cell", "<i4"), ("status", "u1"),

@@ -11,7 +11,7 @@ KEYS_EXACT = ("status", "cell", "steps", "exit_face", "hash")
 
 def gpu_run(ctx, fh, *, release=None, cells=None, frac=None, t0=None, times=None, t_stop=np.inf,
             precision=mp.PREC_FP64, schedule=mp.SCHED_DYNAMIC, max_steps=0, block=0, steps_per_fetch=0,
-            mode=None):
+            mode=None, flags=0):
     """Release + track through the C ABI; returns (endpoints dict, timeseries or None, stats)."""
     if release is not None:
         gh = mp.mp_release_group(ctx.h, fh, n=release.n, lo=release.lo, hi=release.hi, seed=release.seed,
@@ -21,7 +21,7 @@ def gpu_run(ctx, fh, *, release=None, cells=None, frac=None, t0=None, times=None
     if mode is None:
         mode = mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if times is not None else 0)
     req = ctx.track(gh, mode=mode, precision=precision, schedule=schedule, times=times, t_stop=t_stop,
-                    max_steps=max_steps, block=block, steps_per_fetch=steps_per_fetch)
+                    max_steps=max_steps, block=block, steps_per_fetch=steps_per_fetch, flags=flags)
     req.wait()
     ep = req.endpoints()
     ts = req.timeseries() if req.n_times else None

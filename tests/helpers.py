@@ -105,10 +105,13 @@ def _rk4(lin, p, h):
     return [pa + h / 6.0 * (a + 2 * b + 2 * c + d) for pa, a, b, c, d in zip(p, k1, k2, k3, k4)]
 
 
-def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3):
+def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_sinks=False,
+              capture_time=None):
     """Integrate one particle; returns (status, cells visited, final (k,i,j), final p, t).
 
     Status codes follow the oracle's: 1 TIME, 2 SINK, 3 BOUNDARY, 4 EXIT_DOMAIN.
+    pass_sinks: sink cells are entered; a particle that stays in a sink cell
+    longer than capture_time without reaching a face counts as captured.
     """
     p = [float(x) for x in p]
     t = 0.0
@@ -119,7 +122,10 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3):
         if vmax == 0.0:
             return 5, seq, (k, i, j), p, t
         h = frac * min(d for _, _, d in lin) / vmax
+        t_in = t
         while True:
+            if pass_sinks and capture_time is not None and f.ibound[k, i, j] == 2 and t - t_in > capture_time:
+                return 2, seq, (k, i, j), p, t
             hh = h
             if t + hh >= t_stop:
                 hh = t_stop - t
@@ -161,7 +167,7 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3):
             ib = int(f.ibound[nk, ni, nj])
             if ib in (0, -1):
                 return 3, seq, (k, i, j), p, t
-            if ib == 2:
+            if ib == 2 and not pass_sinks:
                 return 2, seq, (k, i, j), p, t
             k, i, j = nk, ni, nj
             p[ax] = 0.0 if side > 0 else (f.delr[j], f.delc[i], f.dz[k])[ax]

@@ -135,6 +135,56 @@ def test_fp64_no_exit_divide(ctx):
     mp.mp_field_free(fh)
 
 
+@pytest.mark.parametrize("scale,seed", [(30.0, 40), (1.0, 40), (30.0, 45)])
+def test_weak_sinks_pass_through(ctx, scale, seed):
+    """Weak sinks: particles enter well cells and leave through reachable
+    faces, or are captured there; FP64 bit-exact against the oracle with the
+    same option, mixed precision on the same cells and statuses."""
+    f = I.random_box_field(2, 5, 8, seed=seed, lnk_var=0.5, n_wells=3, well_scale=scale)
+    fh = ctx.field(f)
+    cells, frac = I.explicit_particles(f, 3000, seed=11, cols=(1, 3))
+    sink = int(np.nonzero(f.ibound.reshape(-1) == 2)[0][0])
+    cells[:3] = sink  # released inside a sink cell: SINK at release
+    st0 = O.release_explicit(f, cells, frac)
+    full = O.track(f, st0, pass_weak_sinks=True)
+    times = np.quantile(full["t"], [0.1, 0.5, 0.9])
+    ref = O.track(f, st0, times=times, pass_weak_sinks=True)
+    strong = O.track(f, st0)
+    assert not np.array_equal(ref["hash"], strong["hash"])
+    for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+        ep, ts, stats = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, schedule=sch,
+                                  flags=mp.TRACK_PASS_WEAK_SINKS)
+        G.compare_fp64(ep, ref, dmin=G.dmin(f))
+        G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+        assert stats["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
+    epm, _, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, precision=mp.PREC_MIXED,
+                          flags=mp.TRACK_PASS_WEAK_SINKS)
+    same = epm["hash"] == ref["hash"]
+    assert same.mean() >= 0.99
+    assert np.array_equal(epm["status"][same], ref["status"][same])
+    # without the flag the same run stops at the first well face
+    ep0, _, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac)
+    G.compare_fp64(ep0, strong, dmin=G.dmin(f))
+    # stop and resume: particles stopped inside a well cell continue from there
+    T1 = float(np.quantile(full["t"][full["t"] > 0], 0.3))
+    a = O.track(f, st0, t_stop=T1, pass_weak_sinks=True)
+    in_well = (a["status"] == O.ST_TIME) & (f.ibound.reshape(-1)[np.maximum(a["cell"], 0)] == 2)
+    mid = dict(cell=a["cell"], px=a["px"], py=a["py"], pz=a["pz"], t=a["t"],
+               status=np.where(a["status"] == O.ST_TIME, O.ST_ACTIVE, a["status"]).astype(np.uint8))
+    b = O.track(f, mid, pass_weak_sinks=True)
+    gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
+    flags = mp.TRACK_PASS_WEAK_SINKS | mp.TRACK_UPDATE_GROUP
+    r1 = ctx.track(gh, t_stop=T1, flags=flags)
+    r1.wait()
+    r2 = ctx.track(gh, flags=flags)
+    G.compare_fp64(r2.endpoints(), b, dmin=G.dmin(f))
+    print(f"weak sinks: {int(in_well.sum())} particles resumed inside a well cell")
+    r1.free()
+    r2.free()
+    mp.mp_group_free(gh)
+    mp.mp_field_free(fh)
+
+
 def test_fp64_cfg2_full_size_sampled(ctx, cfg2):
     """The benchmark's workload and launch configuration at full size
     (1e6 particles, endpoint + 50 output times, dynamic schedule), checked on

@@ -247,3 +247,37 @@ def test_series_log1p_expm1_against_libm():
     assert O.log1p(0.0) == 0.0 and O.expm1(0.0) == 0.0
     assert O.log1p(1e-300) == 1e-300 and O.expm1(-1e-300) == -1e-300
     assert O.expm1(800.0) == math.inf and O.expm1(-800.0) == -1.0
+
+
+def test_weak_sinks_pass_through_against_rk4():
+    """Pass-through of weak sinks: particles enter well cells and leave
+    through faces they can reach (checked by RK4 integration); those that
+    cannot are captured inside the well cell."""
+    f = I.random_box_field(2, 5, 8, seed=40, lnk_var=0.5, n_wells=3, well_scale=30.0)
+    wells = np.nonzero(f.ibound.reshape(-1) == 2)[0]
+    cells, frac = I.explicit_particles(f, 60, seed=9, cols=(1, 3))
+    st = O.release_explicit(f, cells, frac)
+    strong = O.track(f, st)
+    weak = O.track(f, st, pass_weak_sinks=True)
+    passed = captured = 0
+    for q in range(len(cells)):
+        c = int(cells[q])
+        j, i, k = c % f.ncol, (c // f.ncol) % f.nrow, c // (f.ncol * f.nrow)
+        p0 = [st["px"][q], st["py"][q], st["pz"][q]]
+        # the capture horizon: far longer than any cell crossing
+        status, seq, (kk, ii, jj), p, t = H.rk4_track(f, k, i, j, p0, pass_sinks=True,
+                                                      capture_time=50 * float(np.max(strong["t"])))
+        assert status == weak["status"][q]
+        assert H.fnv_hash(seq) == int(weak["hash"][q])
+        if status != O.ST_SINK:
+            assert weak["t"][q] == pytest.approx(t, rel=1e-7)
+        entered = np.isin(seq, wells)
+        if entered.any() and status != O.ST_SINK:
+            passed += 1
+        if status == O.ST_SINK:
+            captured += 1
+            assert int(weak["cell"][q]) in wells
+        # without the option every particle that reaches a well stops at its face
+        if strong["status"][q] == O.ST_SINK:
+            assert int(strong["cell"][q]) not in wells
+    assert passed > 0 and captured > 0
