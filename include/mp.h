@@ -146,10 +146,10 @@ typedef struct {
     int32_t n_times;
     const double* times;
     double t_stop;
-    int64_t max_steps;       /* <= 0: 1,000,000                 */
+    int64_t max_steps;       /* <= 0: 1,000,000; counted since release */
     int32_t block;           /* threads per block, 0 = auto     */
     int32_t steps_per_fetch; /* dynamic schedule, 0 = auto      */
-    uint32_t flags;          /* MP_TRACK_UPDATE_GROUP           */
+    uint32_t flags;          /* MP_TRACK_* bits                 */
 } mp_track_opts;
 
 /* Endpoint arrays (SoA, particle order).  Any pointer may be NULL to skip
@@ -157,7 +157,10 @@ typedef struct {
  * SINK/BOUNDARY/EXIT_DOMAIN it sits on the face exit_face of that cell.
  * px/py/pz are offsets (m) from the cell's low faces; x/y/z global (m).
  * hash is FNV-1a (64-bit, over the 32-bit cell indices) of the sequence of
- * cells tracked in, release cell first. */
+ * cells tracked in, release cell first.  steps, hash and exit_face count
+ * from the release: a group resumed with MP_TRACK_UPDATE_GROUP carries
+ * them, so a resumed run reports what one continued run would (plus one
+ * partial step per pause). */
 typedef struct {
     int32_t* cell;
     double *x, *y, *z;
@@ -220,8 +223,37 @@ int mp_group_size(const mp_group* g, int64_t* n);
  * the tracking kernel; returns the request id at once.  The group is read,
  * not changed, unless o->flags has MP_TRACK_UPDATE_GROUP (resume: the
  * group's state becomes the final state, terminated particles keep their
- * status).  Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+ * status).  A moving particle whose cell is inactive or constant-head under
+ * the group's field ends there (BOUNDARY, no step), in a sink cell (SINK)
+ * unless MP_TRACK_PASS_WEAK_SINKS.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
 int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out);
+
+/* Rebind a group to another field on the same grid (same dims, cell sizes
+ * and origin; flows, porosity and ibound may differ): the next flow period
+ * of a piecewise-steady model.  Requests already enqueued keep the field
+ * they were launched with.  Not concurrent with mp_track on the same group.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE (another grid). */
+int mp_group_set_field(mp_group* g, const mp_field* f);
+
+/* Piecewise-steady (transient) flow (Methods, "MODPATH": the outermost loop
+ * runs over the flow model's time steps and updates the flow arrays when a
+ * step's end time is reached; TC2 runs three stress periods).
+ * fields[p] (n_periods of them, all on the group's grid) holds from
+ * t_end[p-1] to t_end[p]; t_end has n_periods - 1 ascending finite entries
+ * (NULL when n_periods == 1) and the last field has no end.  One request:
+ * one kernel launch per period on `stream`, each resuming from the state
+ * the previous one left (particles stopped at a period end continue in the
+ * next field, in the same cell; see mp_track for cells that change class).
+ * Outputs as mp_track's: endpoints of every particle (from the period it
+ * ended in), timeseries over o->times across the periods, stats summed
+ * (cell_steps of all launches, each particle counted once by its final
+ * status; kernel_ms from the first launch to the last).  The group changes
+ * only with MP_TRACK_UPDATE_GROUP, which also rebinds it to the last field.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_NONFINITE, MP_ERR_OOM,
+ * MP_ERR_CUDA. */
+int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* const* fields, const double* t_end,
+                     const mp_track_opts* o, void* stream, mp_req* out);
 
 /* Track several groups in one launch per precision: the particles of all
  * groups form one index space handed out by the persistent work queue (or

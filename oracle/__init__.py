@@ -87,7 +87,7 @@ def _load():
             lib.orc_release_box.restype = ctypes.c_int
             lib.orc_release_explicit.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_release_explicit.restype = ctypes.c_int
-            lib.orc_track.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
+            lib.orc_track.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                       ctypes.POINTER(_Opts), ctypes.POINTER(_Out)]
             lib.orc_track.restype = ctypes.c_int
             _lib = lib
@@ -187,7 +187,8 @@ def subset(state, idx):
 
 
 def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False):
-    """Track every particle of ``state`` (dict of cell, px, py, pz, t, status).
+    """Track every particle of ``state`` (dict of cell, px, py, pz, t, status,
+    and optionally steps, hash and exit_face carried by a resumed particle).
 
     Returns a dict with the endpoint arrays (cell, px, py, pz, gx, gy, gz, t,
     status, steps, exit_face, hash) and, when ``times`` is given, timeseries
@@ -202,6 +203,9 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
     pz0 = np.ascontiguousarray(state["pz"], dtype=np.float64)
     t0 = np.ascontiguousarray(state.get("t", np.zeros(n)), dtype=np.float64)
     s0 = np.ascontiguousarray(state.get("status", np.zeros(n, np.uint8)), dtype=np.uint8)
+    k0 = None if state.get("steps") is None else np.ascontiguousarray(state["steps"], dtype=np.uint32)
+    h0 = None if state.get("hash") is None else np.ascontiguousarray(state["hash"], dtype=np.uint64)
+    e0 = None if state.get("exit_face") is None else np.ascontiguousarray(state["exit_face"], dtype=np.uint8)
     res = dict(cell=np.zeros(n, np.int32), px=np.zeros(n), py=np.zeros(n), pz=np.zeros(n),
                gx=np.zeros(n), gy=np.zeros(n), gz=np.zeros(n), t=np.zeros(n),
                status=np.zeros(n, np.uint8), steps=np.zeros(n, np.uint32),
@@ -218,9 +222,75 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
     opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)))
     out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_])
     rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
-                       _ptr(s0), ctypes.byref(opts), ctypes.byref(out))
+                       _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
     if rc != 0:
         raise RuntimeError("orc_track failed")
+    return res
+
+
+RESUME_KEYS = ("cell", "px", "py", "pz", "t", "status", "steps", "hash", "exit_face")
+
+
+def resume_state(out):
+    """The state a tracking result leaves for the next call: position, time,
+    carried counts, and TIME / STEP_CAP turned back into ACTIVE."""
+    st = {k: np.array(out[k]) for k in RESUME_KEYS}
+    st["status"] = np.where((st["status"] == ST_TIME) | (st["status"] == ST_STEP_CAP), ST_ACTIVE,
+                            st["status"]).astype(np.uint8)
+    return st
+
+
+def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False):
+    """Piecewise-steady flow (Methods, "MODPATH": the outer loop runs over the
+    flow model's time steps and updates the flow arrays at each step's end).
+
+    fields[p] holds from t_end[p-1] to t_end[p] (len(t_end) == len(fields) - 1;
+    the last field has no end).  Every period is one ``track`` call with the
+    stop time at the period's end, resumed from the state the previous period
+    left (steps, hash and exit face carried); output times are split over the
+    periods, (t_end[p-1], t_end[p]] to period p.  A particle's endpoint is
+    the one from the last period it moved in.  All fields share one grid.
+    """
+    P = len(fields)
+    t_end = [float(v) for v in t_end]
+    if len(t_end) != P - 1 or any(b < a for a, b in zip(t_end, t_end[1:])):
+        raise ValueError("track_periods: need len(fields) - 1 ascending period ends")
+    n = int(np.asarray(state["cell"]).size)
+    cur = {k: np.array(state[k]) for k in ("cell", "px", "py", "pz")}
+    cur["t"] = np.array(state.get("t", np.zeros(n)), dtype=np.float64)
+    cur["status"] = np.array(state.get("status", np.zeros(n, np.uint8)), dtype=np.uint8)
+    cur["steps"] = np.array(state.get("steps", np.zeros(n, np.uint32)), dtype=np.uint32)
+    cur["hash"] = np.array(state.get("hash", np.zeros(n, np.uint64)), dtype=np.uint64)
+    cur["exit_face"] = np.array(state.get("exit_face", np.zeros(n, np.uint8)), dtype=np.uint8)
+    tarr = None if times is None else np.asarray(times, dtype=np.float64)
+    res = None
+    lo = -np.inf
+    for p, f in enumerate(fields):
+        last = p == P - 1
+        hi = np.inf if last else t_end[p]
+        tp = float(t_stop) if last else min(float(t_stop), hi)
+        window = None if tarr is None else np.nonzero((tarr > lo) & (tarr <= hi))[0]
+        wt = None if window is None or window.size == 0 else tarr[window]
+        moved = (cur["status"] == ST_ACTIVE) | (p == 0)
+        out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks)
+        if res is None:
+            res = {k: np.array(v) for k, v in out.items() if not k.startswith("ts_")}
+            if tarr is not None:
+                for k in ("ts_x", "ts_y", "ts_z"):
+                    res[k] = np.full((tarr.size, n), np.nan)
+                res["ts_cell"] = np.full((tarr.size, n), -1, np.int32)
+                res["ts_status"] = np.zeros((tarr.size, n), np.uint8)
+        else:
+            for k in res:
+                if not k.startswith("ts_"):
+                    res[k][moved] = out[k][moved]
+        if wt is not None:
+            for k in ("ts_x", "ts_y", "ts_z", "ts_cell", "ts_status"):
+                res[k][window] = out[k]
+        nxt = resume_state(out)
+        for k in RESUME_KEYS:
+            cur[k] = np.where(moved, nxt[k], cur[k])
+        lo = hi
     return res
 
 

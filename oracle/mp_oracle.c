@@ -44,7 +44,15 @@
  *     reach; when no face is reachable inside a sink cell the sink captures
  *     it (SINK) where it is; a particle released in a sink cell stays SINK;
  *   - a cell-step is one exit-time evaluation, including zero-length steps
- *     and the final partial step; max_steps caps them (STEP_CAP);
+ *     and the final partial step; max_steps caps them (STEP_CAP), counted
+ *     from the release (a resumed particle carries its count and its hash);
+ *   - piecewise-steady flow (Methods, "MODPATH": the outer loop runs over
+ *     the flow model's time steps and updates the flow arrays when a step's
+ *     end time is reached): each period is one call with t_stop at the
+ *     period's end on the period's field, resumed from the previous state;
+ *     a moving particle that finds its cell inactive or constant-head under
+ *     the new field ends there (BOUNDARY), in a sink cell (SINK) unless weak
+ *     sinks are passed;
  *   - output times t_k are recorded in the step whose interval (t, t + dt]
  *     holds them, with the motion formula at tau = t_k - t on every axis;
  *     t_k at or before the start time records the release position, t_k
@@ -314,8 +322,8 @@ static void write_record(const orc_track_out* o, int64_t n, int kk, int64_t q,
 
 int orc_track(const orc_field* f, int64_t n,
               const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
-              const double* t0, const uint8_t* status0,
-              const orc_track_opts* opt, const orc_track_out* out)
+              const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+              const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
 {
     const int nlay = f->nlay, nrow = f->nrow, ncol = f->ncol;
     double xf[ORC_MAX_AXIS + 1], yf[ORC_MAX_AXIS + 1], zf[ORC_MAX_AXIS + 1];
@@ -332,14 +340,21 @@ int orc_track(const orc_field* f, int64_t n,
         uint8_t st = status0 ? status0[q] : ORC_ST_ACTIVE;
         double p[3] = {px0[q], py0[q], pz0[q]};
         double t = t0 ? t0[q] : 0.0;
-        int64_t steps = 0;
-        uint8_t exit_face = ORC_FACE_NONE;
+        int64_t steps = steps0 ? (int64_t)steps0[q] : 0;
+        uint8_t exit_face = (steps > 0 && face0) ? face0[q] : ORC_FACE_NONE;
         uint64_t h = 0xcbf29ce484222325ULL;
         int kn = 0;
         int j = 0, i = 0, k = 0;
         if (c >= 0) {
             j = c % ncol; i = (c / ncol) % nrow; k = c / (ncol * nrow);
-            h = fnv_step(h, c);
+            h = (steps > 0 && hash0) ? hash0[q] : fnv_step(h, c);
+            /* a moving particle in a cell that is not active under this
+             * field (a later flow period can change ibound) stops there */
+            if (st == ORC_ST_ACTIVE) {
+                int8_t ib0 = f->ibound[c];
+                if (ib0 == 0 || ib0 == -1) st = ORC_ST_BOUNDARY;
+                else if (ib0 == 2 && !opt->pass_weak_sinks) st = ORC_ST_SINK;
+            }
         } else {
             st = ORC_ST_INVALID_RELEASE;
         }

@@ -62,8 +62,12 @@ int orc_release_box(const orc_field* f, int64_t n, const double lo[3], const dou
                     int32_t* cell, double* px, double* py, double* pz, uint8_t* status);
 int orc_release_explicit(const orc_field* f, int64_t n, const int32_t* cell_in, const double* frac,
                          int32_t* cell, double* px, double* py, double* pz, uint8_t* status);
+/* steps0/hash0/face0 (each may be NULL): cell-steps already taken, the FNV
+ * hash of the cells visited so far and the last face crossed, carried by a
+ * resumed particle; the run continues them (a particle with steps0 == 0
+ * starts a new hash). */
 int orc_track(const orc_field* f, int64_t n,
               const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
-              const double* t0, const uint8_t* status0,
-              const orc_track_opts* opt, const orc_track_out* out);
+              const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+              const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out);
 #endif

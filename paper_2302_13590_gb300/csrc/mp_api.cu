@@ -15,6 +15,8 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <type_traits>
+#include <vector>
 #include <vector>
 
 #include "mp_internal.h"
@@ -70,19 +72,22 @@ struct mp_field {
     DevField d{};
     void* buf = nullptr;   // one allocation for all device arrays
     size_t bytes = 0;
+    std::vector<double> geom;   // dims, delr, delc, dz, origin: fields with equal geom share a grid
 };
 
 struct mp_group {
     mp_ctx* ctx = nullptr;
     const mp_field* field = nullptr;
     DevState d{};
-    void* buf = nullptr;
+    void* buf = nullptr;   // one allocation for all state arrays
+    size_t bytes = 0;
     long long n = 0;
     cudaStream_t stream = nullptr;
 };
 
 struct Request {
     mp_group* group = nullptr;
+    std::vector<const mp_field*> fields;   // every field its launches read
     long long n = 0;
     int n_times = 0;
     int precision = 0;
@@ -125,7 +130,9 @@ int drain_users(mp_ctx* ctx, const mp_group* g, const mp_field* f)
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (auto& kv : ctx->reqs) {
             Request* r = kv.second;
-            if ((g && r->group == g) || (f && r->group && r->group->field == f)) evs.push_back(r->k1);
+            bool uses = g && r->group == g;
+            for (const mp_field* rf : r->fields) uses = uses || (f && rf == f);
+            if (uses) evs.push_back(r->k1);
         }
     }
     for (cudaEvent_t e : evs) {
@@ -320,6 +327,14 @@ int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
     }
     f->buf = buf;
     f->bytes = persistent;
+    f->geom.reserve(6 + nc + nr + nl);
+    f->geom.push_back((double)nl);
+    f->geom.push_back((double)nr);
+    f->geom.push_back((double)nc);
+    f->geom.insert(f->geom.end(), d->delr, d->delr + nc);
+    f->geom.insert(f->geom.end(), d->delc, d->delc + nr);
+    f->geom.insert(f->geom.end(), d->dz, d->dz + nl);
+    f->geom.insert(f->geom.end(), d->origin, d->origin + 3);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->fields.insert(f);
@@ -382,6 +397,9 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     const size_t o_pz = off; off = align256(off + 8 * (size_t)n);
     const size_t o_t = off; off = align256(off + 8 * (size_t)n);
     const size_t o_st = off; off = align256(off + (size_t)n);
+    const size_t o_steps = off; off = align256(off + 4 * (size_t)n);
+    const size_t o_hash = off; off = align256(off + 8 * (size_t)n);
+    const size_t o_face = off; off = align256(off + (size_t)n);
     const size_t bytes = std::max<size_t>(off, 256);
     char* buf = nullptr;
     if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
@@ -393,6 +411,7 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     g->field = f;
     g->n = n;
     g->buf = buf;
+    g->bytes = bytes;
     g->stream = s;
     g->d.cell = reinterpret_cast<int32_t*>(buf + o_cell);
     g->d.px = reinterpret_cast<double*>(buf + o_px);
@@ -400,7 +419,16 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     g->d.pz = reinterpret_cast<double*>(buf + o_pz);
     g->d.t = reinterpret_cast<double*>(buf + o_t);
     g->d.status = reinterpret_cast<uint8_t*>(buf + o_st);
-    cudaError_t e = cudaSuccess;
+    g->d.steps = reinterpret_cast<uint32_t*>(buf + o_steps);
+    g->d.hash = reinterpret_cast<unsigned long long*>(buf + o_hash);
+    g->d.exit_face = reinterpret_cast<uint8_t*>(buf + o_face);
+    // a fresh particle: no steps yet (hash and exit face are read only after one)
+    cudaError_t e = cudaMemsetAsync(g->d.steps, 0, 4 * (size_t)n, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(buf, s);
+        delete g;
+        return cuda_fail(e, "mp_release_group");
+    }
     if (r->kind == MP_RELEASE_BOX) {
         e = launch_release_box(f->d, g->d, n, r->lo, r->hi, r->seed, r->id_offset, s);
     } else if (n > 0) {
@@ -532,6 +560,7 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     }
     Request* r = new Request();
     r->group = g;
+    r->fields.push_back(g->field);
     r->n = n;
     r->n_times = nt;
     r->precision = o->precision;
@@ -589,6 +618,8 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
     p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
+    p.cont = 0;
+    p.last = 1;
     split_ff(t_stop, p.tstop_hi, p.tstop_lo);
     hreq->in = g->d;
     hreq->o = r->d;
@@ -608,8 +639,10 @@ void drop_request(Request* r)
 
 // One launch over prepared requests of one precision (Methods,
 // "Multiprocessing": a single particle loop over every particle).
+// ev: 1 records the requests' start events before the launch, 2 their end
+// events after it (a request made of several launches records each once).
 int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n, int precision, int schedule,
-                    int block, int spf, bool ts, cudaStream_t s)
+                    int block, int spf, bool ts, cudaStream_t s, unsigned ev = 3)
 {
     size_t off = 0;
     const size_t o_req = off; off = align256(off + sizeof(mp::Req) * (size_t)n);
@@ -626,7 +659,7 @@ int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tbl + o_st, starts.data(), sizeof(long long) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(tbl + o_q, 0, sizeof(unsigned long long), s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(rs[i]->k0, s);
+    for (int i = 0; i < n && e == cudaSuccess && (ev & 1u); ++i) e = cudaEventRecord(rs[i]->k0, s);
     mp::Batch b{};
     b.reqs = reinterpret_cast<const mp::Req*>(tbl + o_req);
     b.starts = reinterpret_cast<const long long*>(tbl + o_st);
@@ -640,10 +673,60 @@ int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n
         e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, ts, schedule, blk, 0, s)
                                         : launch_track_mixed(fd, b, ts, schedule, blk, 0, s);
     }
-    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(rs[i]->k1, s);
+    for (int i = 0; i < n && e == cudaSuccess && (ev & 2u); ++i) e = cudaEventRecord(rs[i]->k1, s);
     cudaFreeAsync(tbl, s);
     if (e != cudaSuccess) return cuda_fail(e, "mp_track: launch");
     return MP_OK;
+}
+
+// Launch configuration of a request: as given, or for MP_SCHED_AUTO the
+// tuned one for (field, precision, timeseries) if there is one.
+void resolve_launch(mp_ctx* ctx, const mp_field* f, int precision, bool ts, const mp_track_opts& o, int* sched,
+                    int* blk, int* spf)
+{
+    *sched = o.schedule;
+    *blk = o.block;
+    *spf = o.steps_per_fetch;
+    if (*sched != MP_SCHED_AUTO) return;
+    *sched = MP_SCHED_DYNAMIC;
+    *blk = 128;
+    *spf = 4;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->tuned.find(TuneKey{f, precision, ts ? 1 : 0});
+    if (it != ctx->tuned.end()) {
+        *sched = it->second.schedule;
+        *blk = it->second.block;
+        *spf = it->second.steps_per_fetch;
+    }
+}
+
+// The same state arrays at another base address (a copy of the group's buffer).
+DevState rebase(const DevState& d, const void* from, void* to)
+{
+    auto mv = [&](auto* ptr) {
+        using T = std::remove_pointer_t<decltype(ptr)>;
+        return reinterpret_cast<T*>(static_cast<char*>(to) +
+                                    (reinterpret_cast<const char*>(ptr) - static_cast<const char*>(from)));
+    };
+    DevState r{};
+    r.cell = mv(d.cell);
+    r.px = mv(d.px);
+    r.py = mv(d.py);
+    r.pz = mv(d.pz);
+    r.t = mv(d.t);
+    r.status = mv(d.status);
+    r.steps = mv(d.steps);
+    r.hash = mv(d.hash);
+    r.exit_face = mv(d.exit_face);
+    return r;
+}
+
+mp_req register_request(mp_ctx* ctx, Request* r)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const int64_t id = ctx->next_id++;
+    ctx->reqs[id] = r;
+    return id;
 }
 
 }  // namespace
@@ -694,20 +777,8 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
                 any_ts = any_ts || ts[i];
             }
         if (sel.empty()) continue;
-        const mp_track_opts& o0 = opts[first];
-        int sched = o0.schedule, blk = o0.block, spf = o0.steps_per_fetch;
-        if (sched == MP_SCHED_AUTO) {
-            sched = MP_SCHED_DYNAMIC;
-            blk = 128;
-            spf = 4;
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            auto it = ctx->tuned.find(TuneKey{groups[0]->field, prec, any_ts ? 1 : 0});
-            if (it != ctx->tuned.end()) {
-                sched = it->second.schedule;
-                blk = it->second.block;
-                spf = it->second.steps_per_fetch;
-            }
-        }
+        int sched = 0, blk = 0, spf = 0;
+        resolve_launch(ctx, groups[0]->field, prec, any_ts, opts[first], &sched, &blk, &spf);
         const int rc = launch_requests(groups[0]->field, sel.data(), sreq.data(), (int)sel.size(), prec,
                                        sched, blk, spf, any_ts, s);
         if (rc != MP_OK) {
@@ -724,6 +795,89 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
             out[i] = id;
         }
     }
+    return MP_OK;
+}
+
+int mp_group_set_field(mp_group* g, const mp_field* f)
+{
+    if (!g || !f) return fail(MP_ERR_INVALID_ARG, "mp_group_set_field: NULL argument");
+    if (f->ctx != g->ctx) return fail(MP_ERR_INVALID_ARG, "mp_group_set_field: field belongs to another context");
+    if (f->geom != g->field->geom)
+        return fail(MP_ERR_SHAPE, "mp_group_set_field: the field's grid differs from the group's");
+    g->field = f;
+    return MP_OK;
+}
+
+int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* const* fields, const double* t_end,
+                     const mp_track_opts* o, void* stream, mp_req* out)
+{
+    if (!ctx || !g || !o || !out || !fields || n_periods < 1)
+        return fail(MP_ERR_INVALID_ARG, "mp_track_periods: bad argument");
+    if (n_periods > 1 && !t_end) return fail(MP_ERR_INVALID_ARG, "mp_track_periods: NULL t_end");
+    for (int p = 0; p < n_periods; ++p) {
+        if (!fields[p]) return fail(MP_ERR_INVALID_ARG, "mp_track_periods: NULL field");
+        if (fields[p]->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_track_periods: field of another context");
+        if (fields[p]->geom != g->field->geom)
+            return fail(MP_ERR_SHAPE, "mp_track_periods: a period's grid differs from the group's");
+    }
+    for (int p = 0; p + 1 < n_periods; ++p) {
+        if (!std::isfinite(t_end[p])) return fail(MP_ERR_NONFINITE, "mp_track_periods: non-finite period end");
+        if (p > 0 && t_end[p] < t_end[p - 1]) return fail(MP_ERR_INVALID_ARG, "mp_track_periods: ends not ascending");
+    }
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Request* r = nullptr;
+    mp::Req hr;
+    bool ts = false;
+    int rc = prepare_request(ctx, g, o, s, &r, &hr, &ts);
+    if (rc != MP_OK) return rc;
+    r->fields.assign(fields, fields + n_periods);
+    // the periods advance a request-owned copy of the group's state
+    char* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, g->bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        drop_request(r);
+        return fail(MP_ERR_OOM, "mp_track_periods: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(scratch, g->buf, g->bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scratch, s);
+        drop_request(r);
+        return cuda_fail(e, "mp_track_periods: state copy");
+    }
+    const DevState sd = rebase(g->d, g->buf, scratch);
+    const double t_stop = hr.p.t_stop;
+    for (int p = 0; p < n_periods; ++p) {
+        const bool last = p == n_periods - 1;
+        mp::Req h = hr;
+        h.in = sd;
+        h.p.t_stop = last ? t_stop : std::min(t_stop, t_end[p]);
+        split_ff(h.p.t_stop, h.p.tstop_hi, h.p.tstop_lo);
+        h.p.update_group = 1;
+        h.p.cont = p > 0;
+        h.p.last = last ? 1 : 0;
+        int sched = 0, blk = 0, spf = 0;
+        resolve_launch(ctx, fields[p], o->precision, ts, *o, &sched, &blk, &spf);
+        rc = launch_requests(fields[p], &r, &h, 1, o->precision, sched, blk, spf, ts, s,
+                             (p == 0 ? 1u : 0u) | (last ? 2u : 0u));
+        if (rc != MP_OK) {
+            cudaStreamSynchronize(s);
+            cudaFreeAsync(scratch, s);
+            drop_request(r);
+            return rc;
+        }
+    }
+    if (o->flags & MP_TRACK_UPDATE_GROUP) {
+        e = cudaMemcpyAsync(g->buf, scratch, g->bytes, cudaMemcpyDeviceToDevice, s);
+        g->field = fields[n_periods - 1];
+    }
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        drop_request(r);
+        return cuda_fail(e, "mp_track_periods: state copy");
+    }
+    *out = register_request(ctx, r);
     return MP_OK;
 }
 

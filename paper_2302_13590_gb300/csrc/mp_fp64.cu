@@ -418,27 +418,46 @@ struct F64Engine {
         (void)in; (void)o; (void)p;
         s.c = in.cell[q];
         s.st = in.status[q];
+        // a later flow period leaves particles that ended before it untouched
+        // (decided on the stored status, before this field's cell classes)
+        if (p.cont && s.st != MP_ST_ACTIVE) {
+            s.st = ST_SKIP;
+            return;
+        }
         s.x0 = in.px[q]; s.x1 = in.py[q]; s.x2 = in.pz[q];
         s.t = in.t[q];
-        s.steps = 0;
+        // cell-steps, hash and last face carried by a resumed particle
+        s.steps = in.steps ? in.steps[q] : 0u;
         s.h = FNV_INIT;
         s.kn = 0;
-        s.ef = MP_FACE_NONE;
+        s.ef = (s.steps && in.exit_face) ? (int)in.exit_face[q] : MP_FACE_NONE;
         s.in_sink = 0;
         if (s.c >= 0 && (long long)s.c < f.ncell) {
             split_cell(f, s.c, s.k, s.i, s.j);
-            s.h = fnv_step(s.h, s.c);
-            // a resumed particle may sit inside a sink cell it entered with pass-through
-            s.in_sink = __ldg(f.ibound + s.c) == 2;
+            s.h = (s.steps && in.hash) ? in.hash[q] : fnv_step(s.h, s.c);
+            // a resumed particle may sit inside a sink cell it entered with
+            // pass-through; a moving particle whose cell is not active under
+            // this field (another flow period) stops there
+            const int ib = __ldg(f.ibound + s.c);
+            s.in_sink = ib == 2;
+            if (s.st == MP_ST_ACTIVE) {
+                if (ib == 0 || ib == -1) s.st = MP_ST_BOUNDARY;
+                else if (ib == 2 && !p.pass_sinks) s.st = MP_ST_SINK;
+            }
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
             s.st = MP_ST_INVALID_RELEASE;
         }
         if (TS) {
-            while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
-                if (s.c >= 0) record(q, s.kn, s, gx(s), gy(s), gz(s), s.st);
-                else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
-                s.kn++;
+            if (p.cont) {
+                // output times up to the period start were written by the previous period
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) s.kn++;
+            } else {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
+                    if (s.c >= 0) record(q, s.kn, s, gx(s), gy(s), gz(s), s.st);
+                    else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
+                    s.kn++;
+                }
             }
         }
         // a particle that starts at or after the stop time takes no step
@@ -660,6 +679,7 @@ struct F64Engine {
         const TrackParams& p = R.p;
         (void)in; (void)o; (void)p;
         const bool ok = s.c >= 0;
+        const unsigned base = in.steps ? in.steps[q] : 0u;   // read before the group update
         const double x = ok ? gx(s) : CUDART_NAN, y = ok ? gy(s) : CUDART_NAN, z = ok ? gz(s) : CUDART_NAN;
         o.cell[q] = s.c;
         o.x[q] = x; o.y[q] = y; o.z[q] = z;
@@ -674,8 +694,15 @@ struct F64Engine {
             in.px[q] = s.x0; in.py[q] = s.x1; in.pz[q] = s.x2;
             in.t[q] = s.t;
             in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
+            if (in.steps) {
+                in.steps[q] = s.steps;
+                in.hash[q] = s.h;
+                in.exit_face[q] = (uint8_t)s.ef;
+            }
         }
-        count_ended(b, s.r, s.steps, s.st, s_cnt);
+        // steps taken in this launch; a particle paused at the end of a flow
+        // period is counted by the period it ends in
+        count_ended(b, s.r, s.steps - base, s.st, s_cnt, p.last || !(s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP));
     }
 };
 

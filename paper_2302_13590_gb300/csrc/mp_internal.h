@@ -85,7 +85,15 @@ struct DevState {
     double* pz;
     double* t;
     uint8_t* status;
+    // carried by a resumed particle (each may be NULL: a fresh start)
+    uint32_t* steps;             // cell-steps since release
+    unsigned long long* hash;    // FNV hash of the cells visited (read when steps > 0)
+    uint8_t* exit_face;          // last face crossed (read when steps > 0)
 };
+
+// status a later flow period gives a particle that had already ended: the
+// launch neither writes nor counts it
+enum : int { ST_SKIP = 0xFF };
 
 // counters[0] = cell-steps, [1 + s] = particles with final status s,
 // [COUNTER_ERR] = device error flag (index of the first bad access + 1)
@@ -118,6 +126,9 @@ struct TrackParams {
     int steps_per_fetch;
     int update_group;
     int pass_sinks;              // enter sink cells, leave through outflow faces
+    int cont;                    // a later flow period of one request: skip ended particles and
+                                 // output times already written
+    int last;                    // the request's last launch: count particles paused at its stop time
     float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
 };
 

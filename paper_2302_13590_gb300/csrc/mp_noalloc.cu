@@ -110,7 +110,7 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: ") + cudaGetErrorString(e));
     Req* dreq = reinterpret_cast<Req*>(scratch + 8 + N_COUNTERS + 2 * MP_NOALLOC_MAX_TIMES);
     long long* dstarts = reinterpret_cast<long long*>(reinterpret_cast<char*>(dreq) + sizeof(Req));
-    DevState st{a->cell, a->px, a->py, a->pz, a->t, a->status};
+    DevState st{a->cell, a->px, a->py, a->pz, a->t, a->status, nullptr, nullptr, nullptr};
     DevOut d{};
     d.cell = ep.cell; d.x = ep.x; d.y = ep.y; d.z = ep.z; d.px = ep.px; d.py = ep.py; d.pz = ep.pz; d.t = ep.t;
     d.status = ep.status; d.steps = ep.steps; d.exit_face = ep.exit_face;
@@ -127,6 +127,8 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
     p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
+    p.cont = 0;
+    p.last = 1;
     split_ff(p.t_stop, p.tstop_hi, p.tstop_lo);
     const int block = o->block > 0 ? o->block : 128;
     const DevField& fd = *mp::field_device_view(f);

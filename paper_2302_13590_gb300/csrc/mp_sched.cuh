@@ -53,16 +53,19 @@ __device__ __forceinline__ void flush_counters(const E& e, unsigned long long* s
 }
 
 __device__ __forceinline__ void count_ended(const Batch& b, int r, unsigned steps, int st,
-                                            unsigned long long* s_cnt)
+                                            unsigned long long* s_cnt, bool count_status)
 {
-    if (b.n_reqs == 1) {
-        atomicAdd(s_cnt + COUNTER_STEPS, (unsigned long long)steps);
-        atomicAdd(s_cnt + COUNTER_STATUS + (st & 7), 1ULL);
-    } else {
-        unsigned long long* c = b.reqs[r].o.counters;
-        atomicAdd(c + COUNTER_STEPS, (unsigned long long)steps);
-        atomicAdd(c + COUNTER_STATUS + (st & 7), 1ULL);
-    }
+    unsigned long long* c = b.n_reqs == 1 ? s_cnt : b.reqs[r].o.counters;
+    atomicAdd(c + COUNTER_STEPS, (unsigned long long)steps);
+    if (count_status) atomicAdd(c + COUNTER_STATUS + (st & 7), 1ULL);
+}
+
+// A particle stopped at a non-final flow period's end: its later output
+// times are written by the next period, not filled with this position.
+template <class E, class S>
+__device__ __forceinline__ bool paused(const E& e, const S& s)
+{
+    return (s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) && !e.b.reqs[s.r].p.last;
 }
 
 // request of global particle index g (starts ascending, starts[0] = 0)
@@ -184,14 +187,14 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
         q = g - __ldg(e.b.starts + r);
         e.template load<TS>(r, q, s);
         live = s.st == MP_ST_ACTIVE;
-        ended = !live;
+        ended = !live && s.st != ST_SKIP;
     }
-    if (TS) tail_fill(e, s, q, ended);
+    if (TS) tail_fill(e, s, q, ended && !paused(e, s));
     if (ended) e.template finish<TS>(q, s, s_cnt);
     while (__any_sync(FULL, live)) {
         e.template step<TS>(q, s, live, Q, qcount);
         ended = live && s.st != MP_ST_ACTIVE;
-        if (TS) tail_fill(e, s, q, ended);
+        if (TS) tail_fill(e, s, q, ended && !paused(e, s));
         if (ended) {
             e.template finish<TS>(q, s, s_cnt);
             live = false;
@@ -236,11 +239,11 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
                     q = (long long)qq - __ldg(e.b.starts + r);
                     e.template load<TS>(r, q, s);
                     live = s.st == MP_ST_ACTIVE;
-                    ended = !live;
+                    ended = !live && s.st != ST_SKIP;
                 }
             }
         }
-        if (TS) tail_fill(e, s, q, ended);
+        if (TS) tail_fill(e, s, q, ended && !paused(e, s));
         if (ended) e.template finish<TS>(q, s, s_cnt);
         if (!__any_sync(FULL, live)) {
             if (drained) break;
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
         for (int it = 0; it < S; ++it) {
             e.template step<TS>(q, s, live, Q, qcount);
             ended = live && s.st != MP_ST_ACTIVE;
-            if (TS) tail_fill(e, s, q, ended);
+            if (TS) tail_fill(e, s, q, ended && !paused(e, s));
             if (ended) {
                 e.template finish<TS>(q, s, s_cnt);
                 live = false;

@@ -406,6 +406,46 @@ def random_box_field(nlay, nrow, ncol, seed, lnk_var=1.0, corr=(2.0, 2.0, 1.0), 
                  name=f"random{nlay}x{nrow}x{ncol}s{seed}")
 
 
+def period_fields(f: Field, seed: int, head_scale=(1.0, 0.5, -0.6), new_wells=(0, 2, 0),
+                  well_scale: float = 1.0, tol_abs: float = 1e-17) -> List[Field]:
+    """Stress periods of a piecewise-steady flow on the grid of f.
+
+    Period p keeps f's cells, K and porosity; the constant-head contrast is
+    scaled by head_scale[p] (a negative scale reverses the mean gradient) and
+    new_wells[p] more sink cells are switched on (seeded); each period's face
+    flows come from its own head solve, so every period conserves volume.
+    A scale of 1 with no new wells reproduces f's flows.
+    """
+    if f.K is None or f.head is None:
+        raise ValueError("period_fields: the field needs its K and heads")
+    rng = np.random.default_rng(seed)
+    ch = f.ibound == IB_CONST_HEAD
+    h_lo = float(f.head[ch].min())
+    ib = f.ibound.copy()
+    q_src = np.zeros(f.ibound.shape) if f.q_src is None else f.q_src.copy()
+    tot = abs(float(f.qx[:, :, 1].sum()))  # through-flow out of the west constant-head column
+    out = []
+    for p, (sc, nw) in enumerate(zip(head_scale, new_wells)):
+        ib = ib.copy()
+        q_src = q_src.copy()
+        for _ in range(nw):
+            act = np.argwhere(ib == IB_ACTIVE)
+            k, i, j = (int(v) for v in act[int(rng.integers(0, len(act)))])
+            ib[k, i, j] = IB_SINK
+            q_src[k, i, j] = -well_scale * float(rng.uniform(0.005, 0.02)) * max(tot, 1e-12)
+        head = f.head.copy()
+        head[ch] = h_lo + sc * (f.head[ch] - h_lo)
+        if sc == 1.0 and nw == 0 and p == 0:
+            out.append(f)
+            continue
+        h, qx, qy, qz, iters, maxres = solve_flow(f.nlay, f.nrow, f.ncol, f.delr, f.delc, f.dz, f.K, ib, head,
+                                                  q_src, tol_abs=tol_abs)
+        out.append(Field(f.nlay, f.nrow, f.ncol, f.delr, f.delc, f.dz, f.origin, qx, qy, qz, f.porosity, ib.copy(),
+                         head=h, K=f.K, q_src=q_src.copy(), solve_iters=iters, solve_maxres=maxres,
+                         name=f"{f.name}.period{p}"))
+    return out
+
+
 def explicit_particles(f: Field, n: int, seed: int, cols: Optional[Tuple[int, int]] = None,
                        active_only: bool = True):
     """n particles as (cell index int32, local fractions float64 [n,3]) in active cells.

@@ -29,6 +29,7 @@ MP_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NONFINITE", -4: "OOM", -5: "BUSY", -6: "TIMEOUT",
           -7: "CUDA", -8: "NOT_READY", -9: "DEVICE"}
 MP_ERR_TIMEOUT = -6
+ERR_INVALID_ARG, ERR_SHAPE, ERR_NONFINITE, ERR_OOM = -1, -2, -3, -4
 ST_ACTIVE, ST_TIME, ST_SINK, ST_BOUNDARY, ST_EXIT_DOMAIN, ST_NO_EXIT, ST_STEP_CAP, ST_INVALID_RELEASE = range(8)
 STATUS_NAMES = ["ACTIVE", "TIME", "SINK", "BOUNDARY", "EXIT_DOMAIN", "NO_EXIT", "STEP_CAP", "INVALID_RELEASE"]
 FACE_NONE = 255
@@ -121,6 +122,9 @@ SIGNATURES = {
     "mp_track_noalloc": (ctypes.c_int, [_vp, _P(NoallocArgs), _vp, _P(Stats)]),
     "mp_autotune": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), ctypes.c_int64, _vp, _P(Tuning)]),
     "mp_set_tuning": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning)]),
+    "mp_group_set_field": (ctypes.c_int, [_vp, _vp]),
+    "mp_track_periods": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(_vp), _vp, _P(TrackOpts), _vp,
+                                        _P(ctypes.c_int64)]),
 }
 
 _lib = None
@@ -254,6 +258,23 @@ def mp_group_size(gh) -> int:
     n = ctypes.c_int64()
     _check(load_library().mp_group_size(gh, ctypes.byref(n)))
     return n.value
+
+
+def mp_group_set_field(gh, fh):
+    """Rebind a group to another field on the same grid (the next flow period)."""
+    _check(load_library().mp_group_set_field(gh, fh))
+
+
+def mp_track_periods(ctx, gh, fields, t_end, opts: "TrackOpts", stream=None) -> int:
+    """Piecewise-steady flow: fields[p] holds until t_end[p] (len(fields) - 1
+    ends); one request, one launch per period."""
+    n = len(fields)
+    farr = (_vp * n)(*[f.value if isinstance(f, ctypes.c_void_p) else f for f in fields])
+    tarr = _host(t_end, np.float64) if n > 1 else None
+    r = ctypes.c_int64()
+    _check(load_library().mp_track_periods(ctx, gh, n, farr, _ptr(tarr), ctypes.byref(opts), _stream(stream),
+                                           ctypes.byref(r)))
+    return r.value
 
 
 def make_opts(mode=MODE_ENDPOINT, precision=PREC_FP64, schedule=SCHED_DYNAMIC, times=None, t_stop=math.inf,
@@ -430,6 +451,13 @@ class Context:
         opts = make_opts(**kw)
         n = mp_group_size(gh)
         rid = mp_track(self.h, gh, opts, stream)
+        nt = opts.n_times if (opts.mode & MODE_TIMESERIES) else 0
+        return Request(self, rid, n, nt)
+
+    def track_periods(self, gh, fields, t_end, stream=None, **kw) -> "Request":
+        opts = make_opts(**kw)
+        n = mp_group_size(gh)
+        rid = mp_track_periods(self.h, gh, fields, t_end, opts, stream)
         nt = opts.n_times if (opts.mode & MODE_TIMESERIES) else 0
         return Request(self, rid, n, nt)
 

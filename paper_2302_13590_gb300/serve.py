@@ -31,6 +31,10 @@ import numpy as np
 
 from . import mp
 
+# device bytes of a group's state per particle: cell, px/py/pz, t, status,
+# steps, hash, exit face (+ alignment slack in the 4096 per request)
+GROUP_BYTES_PER_PARTICLE = 4 + 24 + 8 + 1 + 4 + 8 + 1
+
 
 @dataclass
 class Served:
@@ -99,7 +103,7 @@ class Server:
 
     def _bytes(self, spec) -> int:
         n = spec.release.n
-        return mp.mp_query_bytes(self._opts(spec), n) + 41 * n + 4096
+        return mp.mp_query_bytes(self._opts(spec), n) + GROUP_BYTES_PER_PARTICLE * n + 4096
 
     def run(self, specs: List, realtime: bool = True, time_scale: float = 1.0) -> ServeReport:
         """Serve the requests; arrival times are honoured on the wall clock

@@ -106,17 +106,24 @@ def _rk4(lin, p, h):
 
 
 def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_sinks=False,
-              capture_time=None):
+              capture_time=None, periods=None):
     """Integrate one particle; returns (status, cells visited, final (k,i,j), final p, t).
 
     Status codes follow the oracle's: 1 TIME, 2 SINK, 3 BOUNDARY, 4 EXIT_DOMAIN.
     pass_sinks: sink cells are entered; a particle that stays in a sink cell
     longer than capture_time without reaching a face counts as captured.
+    periods: (fields, t_end) for piecewise-steady flow: fields[p] holds from
+    t_end[p-1] to t_end[p]; at a period end the integration restarts in the
+    same cell with the next field's velocities.
     """
+    fields, t_end = ([f], []) if periods is None else (list(periods[0]), list(periods[1]))
+    per = 0
     p = [float(x) for x in p]
     t = 0.0
-    seq = [(k * f.nrow + i) * f.ncol + j]
+    seq = [(k * fields[0].nrow + i) * fields[0].ncol + j]
     for _ in range(max_cells):
+        f = fields[per]
+        t_next = t_end[per] if per < len(t_end) else math.inf
         lin = _cell_lin(f, k, i, j)
         vmax = max(max(abs(a), abs(b)) for a, b, _ in lin)
         if vmax == 0.0:
@@ -126,7 +133,7 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
         while True:
             if pass_sinks and capture_time is not None and f.ibound[k, i, j] == 2 and t - t_in > capture_time:
                 return 2, seq, (k, i, j), p, t
-            hh = h
+            hh = min(h, t_next - t)
             if t + hh >= t_stop:
                 hh = t_stop - t
             q = _rk4(lin, p, hh)
@@ -135,6 +142,16 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
                 p, t = q, t + hh
                 if t >= t_stop:
                     return 1, seq, (k, i, j), p, t
+                if t >= t_next:
+                    # the next flow period: same cell, new velocities
+                    t = t_next
+                    per += 1
+                    ib = int(fields[per].ibound[k, i, j])
+                    if ib in (0, -1):
+                        return 3, seq, (k, i, j), p, t
+                    if ib == 2 and not pass_sinks:
+                        return 2, seq, (k, i, j), p, t
+                    break
                 continue
             # bisection for the first face crossing inside this RK4 step
             lo, hi = 0.0, hh

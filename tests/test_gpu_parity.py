@@ -169,9 +169,7 @@ def test_weak_sinks_pass_through(ctx, scale, seed):
     T1 = float(np.quantile(full["t"][full["t"] > 0], 0.3))
     a = O.track(f, st0, t_stop=T1, pass_weak_sinks=True)
     in_well = (a["status"] == O.ST_TIME) & (f.ibound.reshape(-1)[np.maximum(a["cell"], 0)] == 2)
-    mid = dict(cell=a["cell"], px=a["px"], py=a["py"], pz=a["pz"], t=a["t"],
-               status=np.where(a["status"] == O.ST_TIME, O.ST_ACTIVE, a["status"]).astype(np.uint8))
-    b = O.track(f, mid, pass_weak_sinks=True)
+    b = O.track(f, O.resume_state(a), pass_weak_sinks=True)
     gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
     flags = mp.TRACK_PASS_WEAK_SINKS | mp.TRACK_UPDATE_GROUP
     r1 = ctx.track(gh, t_stop=T1, flags=flags)
@@ -228,11 +226,11 @@ def test_update_group_resume(ctx, cfg1):
     ep = r2.endpoints()
     s0 = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
     a = O.track(w.field, s0, t_stop=T1)
-    mid = dict(cell=a["cell"], px=a["px"], py=a["py"], pz=a["pz"], t=a["t"],
-               status=np.where(a["status"] == O.ST_TIME, O.ST_ACTIVE, a["status"]).astype(np.uint8))
-    b = O.track(w.field, mid, t_stop=T2)
-    for k in ("status", "cell", "steps", "exit_face"):
+    b = O.track(w.field, O.resume_state(a), t_stop=T2)
+    # steps, hash and exit face are carried through the pause
+    for k in ("status", "cell", "steps", "exit_face", "hash"):
         assert np.array_equal(ep[k], b[k]), k
+    assert np.all(ep["steps"] >= a["steps"])
     assert np.max(G.rel_err(ep["t"], b["t"])) <= 1e-10
     assert np.max(G.rel_err(ep["x"], b["gx"])) <= 1e-10
     r1.free()

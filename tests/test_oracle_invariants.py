@@ -42,6 +42,15 @@ def test_time_additivity(fld, rel):
     for k in ("gx", "gy", "gz"):
         np.testing.assert_allclose(b[k], d[k], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(b["t"], d["t"], rtol=1e-13)
+    # carrying the step count, hash and exit face makes resume == continue
+    # for those too: the pause adds one partial step, the hash does not
+    # repeat the cell the particle paused in
+    c = O.track(fld, O.resume_state(a), t_stop=T2)
+    assert np.array_equal(c["hash"], d["hash"])
+    assert np.array_equal(c["exit_face"], d["exit_face"])
+    assert np.array_equal(c["steps"], d["steps"] + (a["status"] == O.ST_TIME))
+    for k in ("gx", "gy", "gz", "t", "status", "cell"):
+        assert np.array_equal(c[k], b[k]), k
 
 
 def test_timeseries_equals_endpoint_at_tk(fld, rel):
