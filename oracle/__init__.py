@@ -57,13 +57,20 @@ class _Field(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
-                ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32)]
+                ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32),
+                ("path_start", ctypes.c_int32)]
+
+
+# one pathline point (orc_path_rec)
+PATH_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("t", "<f8"), ("particle", "<i4"),
+                        ("cell", "<i4"), ("seq", "<u4"), ("status", "u1"), ("pad", "u1", (3,))])
 
 
 class _Out(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("cell", "px", "py", "pz", "gx", "gy", "gz", "t", "status", "steps", "exit_face", "hash",
-                 "ts_x", "ts_y", "ts_z", "ts_cell", "ts_status")]
+                 "ts_x", "ts_y", "ts_z", "ts_cell", "ts_status", "path")] + \
+        [("path_cap", ctypes.c_int64), ("path_n", ctypes.c_void_p)]
 
 
 def _load():
@@ -186,13 +193,17 @@ def subset(state, idx):
     return {k: np.ascontiguousarray(v[idx]) for k, v in state.items()}
 
 
-def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False):
+def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False,
+          pathline=False, path_start=True):
     """Track every particle of ``state`` (dict of cell, px, py, pz, t, status,
     and optionally steps, hash and exit_face carried by a resumed particle).
 
     Returns a dict with the endpoint arrays (cell, px, py, pz, gx, gy, gz, t,
     status, steps, exit_face, hash) and, when ``times`` is given, timeseries
-    arrays ts_x/ts_y/ts_z/ts_cell/ts_status of shape [n_times, n].
+    arrays ts_x/ts_y/ts_z/ts_cell/ts_status of shape [n_times, n].  With
+    ``pathline``, ``path`` holds the pathline points (PATH_RECORD) in the
+    order produced: per particle its start point (if ``path_start``) and the
+    point every cell-step ends at.
     """
     lib = _load()
     of = as_oracle_field(f)
@@ -219,12 +230,22 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
             res[k] = np.zeros((nt, n))
         res["ts_cell"] = np.zeros((nt, n), np.int32)
         res["ts_status"] = np.zeros((nt, n), np.uint8)
-    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)))
-    out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_])
-    rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
-                       _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
-    if rc != 0:
-        raise RuntimeError("orc_track failed")
+    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)), int(bool(path_start)))
+    cap = 64 * n + 16
+    while True:
+        path = np.zeros(cap if pathline else 0, PATH_RECORD)
+        path_n = np.zeros(1, np.int64)
+        out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_[:17]], _ptr(path) if pathline else None, cap,
+                   _ptr(path_n))
+        rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
+                           _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
+        if rc != 0:
+            raise RuntimeError("orc_track failed")
+        if not pathline or path_n[0] <= cap:
+            break
+        cap = int(path_n[0])   # the run is deterministic: repeat with room for every point
+    if pathline:
+        res["path"] = path[:int(path_n[0])]
     return res
 
 
@@ -240,7 +261,8 @@ def resume_state(out):
     return st
 
 
-def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False):
+def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False,
+                  pathline=False):
     """Piecewise-steady flow (Methods, "MODPATH": the outer loop runs over the
     flow model's time steps and updates the flow arrays at each step's end).
 
@@ -250,6 +272,8 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
     left (steps, hash and exit face carried); output times are split over the
     periods, (t_end[p-1], t_end[p]] to period p.  A particle's endpoint is
     the one from the last period it moved in.  All fields share one grid.
+    Pathline points of all periods are concatenated (start points from the
+    first period only: later periods continue the same lines).
     """
     P = len(fields)
     t_end = [float(v) for v in t_end]
@@ -264,6 +288,7 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
     cur["exit_face"] = np.array(state.get("exit_face", np.zeros(n, np.uint8)), dtype=np.uint8)
     tarr = None if times is None else np.asarray(times, dtype=np.float64)
     res = None
+    paths = []
     lo = -np.inf
     for p, f in enumerate(fields):
         last = p == P - 1
@@ -272,7 +297,10 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
         window = None if tarr is None else np.nonzero((tarr > lo) & (tarr <= hi))[0]
         wt = None if window is None or window.size == 0 else tarr[window]
         moved = (cur["status"] == ST_ACTIVE) | (p == 0)
-        out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks)
+        out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks,
+                    pathline=pathline, path_start=p == 0)
+        if pathline:
+            paths.append(out.pop("path"))
         if res is None:
             res = {k: np.array(v) for k, v in out.items() if not k.startswith("ts_")}
             if tarr is not None:
@@ -291,6 +319,8 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
         for k in RESUME_KEYS:
             cur[k] = np.where(moved, nxt[k], cur[k])
         lo = hi
+    if pathline:
+        res["path"] = np.concatenate(paths)
     return res
 
 

@@ -53,6 +53,10 @@
  *     a moving particle that finds its cell inactive or constant-head under
  *     the new field ends there (BOUNDARY), in a sink cell (SINK) unless weak
  *     sinks are passed;
+ *   - pathlines (Methods, "MODPATH": endpoint, timeseries and pathline
+ *     simulations): a point at the start and one at the end of every
+ *     cell-step (the entry point of the next cell, or where the path ends),
+ *     each with its cell, time, step count and status;
  *   - output times t_k are recorded in the step whose interval (t, t + dt]
  *     holds them, with the motion formula at tau = t_k - t on every axis;
  *     t_k at or before the start time records the release position, t_k
@@ -320,6 +324,18 @@ static void write_record(const orc_track_out* o, int64_t n, int kk, int64_t q,
     o->ts_cell[r] = cell; o->ts_status[r] = st;
 }
 
+static void path_point(const orc_track_out* o, int64_t q, double x, double y, double z, double t,
+                       int32_t cell, int64_t seq, uint8_t st)
+{
+    if (!o->path) return;
+    int64_t r = (*o->path_n)++;
+    if (r >= o->path_cap) return;
+    orc_path_rec* e = &o->path[r];
+    e->x = x; e->y = y; e->z = z; e->t = t;
+    e->particle = (int32_t)q; e->cell = cell; e->seq = (uint32_t)seq; e->status = st;
+    e->pad[0] = e->pad[1] = e->pad[2] = 0;
+}
+
 int orc_track(const orc_field* f, int64_t n,
               const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
               const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
@@ -366,7 +382,12 @@ int orc_track(const orc_field* f, int64_t n,
                 write_record(out, n, kn, q, NAN, NAN, NAN, -1, st);
             kn++;
         }
+        /* pathline: the start point, with the status it starts with */
+        if (opt->path_start && c >= 0)
+            path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, st);
+        int took = 0;   /* the last loop pass took a cell-step */
         while (st == ORC_ST_ACTIVE) {
+            took = 0;
             if (t >= t_stop) { st = ORC_ST_TIME; break; }
             if (steps >= max_steps) { st = ORC_ST_STEP_CAP; break; }
             cellvel cv;
@@ -380,6 +401,7 @@ int orc_track(const orc_field* f, int64_t n,
             for (int a = 0; a < 3; a++)
                 if (face[a] != 0 && te[a] < tmin) { tmin = te[a]; ax = a; }
             steps++;
+            took = 1;
             if (ax < 0 && f->ibound[c] == 2) {
                 /* inside a sink cell with no reachable face: captured */
                 st = ORC_ST_SINK;
@@ -448,7 +470,11 @@ int orc_track(const orc_field* f, int64_t n,
             if (face[ax] > 0) p[ax] = 0.0;
             else p[ax] = (ax == 0) ? f->delr[j] : (ax == 1) ? f->delc[i] : f->dz[k];
             h = fnv_step(h, c);
+            /* pathline: the entry point in the new cell */
+            path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, ORC_ST_ACTIVE);
         }
+        /* pathline: where the last step ended (stop time, sink, boundary, ...) */
+        if (took) path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, st);
         /* output times after termination: the final position */
         while (kn < nt) {
             if (c >= 0)

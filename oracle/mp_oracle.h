@@ -43,13 +43,28 @@ typedef struct {
     const double* times;  /* ascending */
     int64_t max_steps;    /* <= 0: default */
     int32_t pass_weak_sinks; /* 1: enter sink cells, leave through outflow faces */
+    int32_t path_start;   /* pathlines: 1 = a record at the start of every particle */
 } orc_track_opts;
+
+/* One pathline point (Methods, "MODPATH": pathline simulations record the
+ * path): the release point and the point reached by every cell-step. */
+typedef struct {
+    double x, y, z, t;    /* global position (m), time (s) */
+    int32_t particle;     /* index in the tracked state */
+    int32_t cell;         /* cell the point belongs to after the step */
+    uint32_t seq;         /* cell-steps taken since release when the point is reached */
+    uint8_t status;       /* status after the step (ACTIVE while moving on) */
+    uint8_t pad[3];
+} orc_path_rec;
 
 typedef struct {
     int32_t* cell; double *px, *py, *pz; double *gx, *gy, *gz; double* t;
     uint8_t* status; uint32_t* steps; uint8_t* exit_face; uint64_t* hash;
     /* timeseries [n_times][n]; ts_x == NULL disables */
     double *ts_x, *ts_y, *ts_z; int32_t* ts_cell; uint8_t* ts_status;
+    /* pathline points, appended in the order produced; path == NULL disables;
+     * *path_n counts every point, also those beyond path_cap */
+    orc_path_rec* path; int64_t path_cap; int64_t* path_n;
 } orc_track_out;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

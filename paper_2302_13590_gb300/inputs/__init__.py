@@ -446,6 +446,25 @@ def period_fields(f: Field, seed: int, head_scale=(1.0, 0.5, -0.6), new_wells=(0
     return out
 
 
+def staged_release(f: Field, cells, n_per_stage: int, n_stages: int, interval: float, seed: int,
+                   face_z: float = 0.0):
+    """Staged injection (TC2: particles released from the upper face of a
+    few cells, injected in stages at a fixed interval): n_per_stage particles
+    per cell and stage, uniform over the cell's face z = face_z (a fraction of
+    the cell height), stage s released at t0 = s * interval.  Returns (cell,
+    local fractions [n, 3], t0), stage-major."""
+    rng = np.random.default_rng(seed)
+    cells = np.asarray(cells, dtype=np.int32)
+    n = len(cells) * n_per_stage * n_stages
+    cell = np.tile(np.repeat(cells, n_per_stage), n_stages).astype(np.int32)
+    frac = np.empty((n, 3))
+    frac[:, 0] = rng.uniform(0.0, 1.0, n)
+    frac[:, 1] = rng.uniform(0.0, 1.0, n)
+    frac[:, 2] = face_z
+    t0 = np.repeat(np.arange(n_stages, dtype=np.float64) * interval, len(cells) * n_per_stage)
+    return cell, frac, t0
+
+
 def explicit_particles(f: Field, n: int, seed: int, cols: Optional[Tuple[int, int]] = None,
                        active_only: bool = True):
     """n particles as (cell index int32, local fractions float64 [n,3]) in active cells.

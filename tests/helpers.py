@@ -106,7 +106,7 @@ def _rk4(lin, p, h):
 
 
 def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_sinks=False,
-              capture_time=None, periods=None):
+              capture_time=None, periods=None, t0=0.0, trace=None):
     """Integrate one particle; returns (status, cells visited, final (k,i,j), final p, t).
 
     Status codes follow the oracle's: 1 TIME, 2 SINK, 3 BOUNDARY, 4 EXIT_DOMAIN.
@@ -114,12 +114,25 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
     longer than capture_time without reaching a face counts as captured.
     periods: (fields, t_end) for piecewise-steady flow: fields[p] holds from
     t_end[p-1] to t_end[p]; at a period end the integration restarts in the
-    same cell with the next field's velocities.
+    same cell with the next field's velocities.  t0: the release time (the
+    particle starts in the period that holds it).  trace: a list that
+    receives (t, cell, global point) at every face crossing and at the end.
     """
     fields, t_end = ([f], []) if periods is None else (list(periods[0]), list(periods[1]))
-    per = 0
+    g0 = fields[0]
+    xf = np.concatenate([[0.0], np.cumsum(g0.delr)]) + g0.origin[0]
+    yf = np.concatenate([[0.0], np.cumsum(g0.delc)]) + g0.origin[1]
+    zf = np.concatenate([[0.0], np.cumsum(g0.dz)]) + g0.origin[2]
+
+    def mark(t, k, i, j, p):
+        if trace is not None:
+            trace.append((t, (k * g0.nrow + i) * g0.ncol + j, (xf[j] + p[0], yf[i] + p[1], zf[k] + p[2])))
+
+    per = sum(1 for te in t_end if te <= t0)
     p = [float(x) for x in p]
-    t = 0.0
+    t = float(t0)
+    if t >= t_stop:
+        return 1, [(k * fields[0].nrow + i) * fields[0].ncol + j], (k, i, j), p, t
     seq = [(k * fields[0].nrow + i) * fields[0].ncol + j]
     for _ in range(max_cells):
         f = fields[per]
@@ -132,6 +145,7 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
         t_in = t
         while True:
             if pass_sinks and capture_time is not None and f.ibound[k, i, j] == 2 and t - t_in > capture_time:
+                mark(t, k, i, j, p)
                 return 2, seq, (k, i, j), p, t
             hh = min(h, t_next - t)
             if t + hh >= t_stop:
@@ -141,11 +155,13 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
             if not any(out):
                 p, t = q, t + hh
                 if t >= t_stop:
+                    mark(t, k, i, j, p)
                     return 1, seq, (k, i, j), p, t
                 if t >= t_next:
                     # the next flow period: same cell, new velocities
                     t = t_next
                     per += 1
+                    mark(t, k, i, j, p)
                     ib = int(fields[per].ibound[k, i, j])
                     if ib in (0, -1):
                         return 3, seq, (k, i, j), p, t
@@ -180,14 +196,18 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
             else:
                 nk += side
             if not (0 <= nj < f.ncol and 0 <= ni < f.nrow and 0 <= nk < f.nlay):
+                mark(t, k, i, j, p)
                 return 4, seq, (k, i, j), p, t
             ib = int(f.ibound[nk, ni, nj])
             if ib in (0, -1):
+                mark(t, k, i, j, p)
                 return 3, seq, (k, i, j), p, t
             if ib == 2 and not pass_sinks:
+                mark(t, k, i, j, p)
                 return 2, seq, (k, i, j), p, t
             k, i, j = nk, ni, nj
             p[ax] = 0.0 if side > 0 else (f.delr[j], f.delc[i], f.dz[k])[ax]
             seq.append((k * f.nrow + i) * f.ncol + j)
+            mark(t, k, i, j, p)
             break
     raise RuntimeError("rk4_track: too many cells")

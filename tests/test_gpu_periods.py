@@ -36,10 +36,10 @@ def small(ctx):
         mp.mp_field_free(fh)
 
 
-def _run(ctx, fhs, T, cells, frac, **kw):
+def _run(ctx, fhs, T, cells, frac, t0=None, **kw):
     if kw.get("times") is not None:
         kw.setdefault("mode", mp.MODE_ENDPOINT | mp.MODE_TIMESERIES)
-    gh = mp.mp_release_group(ctx.h, fhs[0], cell=cells, local=frac)
+    gh = mp.mp_release_group(ctx.h, fhs[0], cell=cells, local=frac, t0=t0)
     req = ctx.track_periods(gh, fhs, T, **kw)
     req.wait()
     ep = req.endpoints()
@@ -165,3 +165,25 @@ def test_periods_cfg2_sampled(ctx):
     mp.mp_group_free(gh)
     for fh in fhs:
         mp.mp_field_free(fh)
+
+
+@pytest.mark.parametrize("with_periods", [False, True])
+def test_staged_release_fp64(ctx, small, with_periods):
+    """Staged injection (TC2: particles released from the top face of a few
+    cells in stages at a fixed interval), steady or through the periods."""
+    f, fs, fhs, cells, frac, st0, full, T = small
+    top = np.nonzero(f.ibound.reshape(-1)[:f.nrow * f.ncol] == 1)[0]
+    src = [c for c in top if (c % f.ncol) in (1, 2, 3) and all(g.ibound.reshape(-1)[c] == 1 for g in fs)][:4]
+    cell, fr, t0 = I.staged_release(f, src, 50, 10, interval=float(T[1]) / 6, seed=7)
+    st = O.release_explicit(f, cell, fr)
+    st["t"] = t0
+    times = np.linspace(0.0, 2.0 * T[1], 9)
+    if with_periods:
+        ref = O.track_periods(fs, T, st, times=times)
+        ep, ts, stats = _run(ctx, fhs, T, cell, fr, times=times, t0=t0)
+    else:
+        ref = O.track(f, st, times=times)
+        ep, ts, stats = G.gpu_run(ctx, fhs[0], cells=cell, frac=fr, t0=t0, times=times)
+    G.compare_fp64(ep, ref, dmin=G.dmin(f))
+    G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+    assert stats["n_status"] == np.bincount(ref["status"], minlength=8).tolist()

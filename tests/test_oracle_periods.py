@@ -116,3 +116,53 @@ def test_period_driver_rejects_bad_ends(base):
         O.track_periods([f, f], [], st0)
     with pytest.raises(ValueError):
         O.track_periods([f, f, f], [2.0, 1.0], st0)
+
+
+def test_staged_release_is_a_time_translation(base):
+    """Staged injection (TC2) in steady flow: a particle released at t0
+    follows the path of the same particle released at 0, shifted by t0;
+    output times before t0 see the release position."""
+    f, cells, frac, st0, full = base
+    t0 = np.linspace(0.0, 3.0, cells.size) * float(np.median(full["t"]))
+    st = dict(st0, t=t0)
+    r = O.track(f, st)
+    for k in ("hash", "steps", "status", "cell", "exit_face", "px", "py", "pz"):
+        assert np.array_equal(r[k], full[k]), k
+    np.testing.assert_allclose(r["t"] - t0, full["t"], rtol=1e-12)
+    tau = np.quantile(full["t"], [0.1, 0.5])
+    q = int(np.argmax(t0))
+    times = np.sort(np.concatenate([tau, t0[q] + tau, [0.5 * t0[q]]]))
+    rs = O.track(f, {k: v[q:q + 1] for k, v in st.items()}, times=times)
+    r0 = O.track(f, {k: v[q:q + 1] for k, v in st0.items()}, times=tau)
+    before = times < t0[q]
+    assert np.all(rs["ts_status"][before, 0] == O.ST_ACTIVE)
+    c = int(st0["cell"][q])
+    k0, i0, j0 = _kij(f, c)
+    x0 = float(np.sum(f.delr[:j0]) + f.origin[0] + st0["px"][q])
+    assert np.all(rs["ts_x"][before, 0] == x0)
+    after = np.nonzero(~before)[0][-2:]
+    for k in ("ts_x", "ts_y", "ts_z"):
+        np.testing.assert_allclose(rs[k][after, 0], r0[k][:, 0], rtol=1e-11)
+
+
+def test_staged_release_through_periods_against_rk4(base):
+    f, cells, frac, st0, full = base
+    fs = I.period_fields(f, seed=5, head_scale=(1.0, 0.5, -0.6), new_wells=(0, 2, 0))
+    T = np.quantile(full["t"], [0.2, 0.5])
+    top = np.nonzero(f.ibound.reshape(-1)[:f.nrow * f.ncol] == 1)[0]
+    src = [c for c in top if (c % f.ncol) in (1, 2) and all(g.ibound.reshape(-1)[c] == 1 for g in fs)][:4]
+    cell, fr, t0 = I.staged_release(f, src, 3, 5, interval=float(T[1]) / 3, seed=4)
+    st = O.release_explicit(f, cell, fr)
+    st["t"] = t0
+    r = O.track_periods(fs, T, st)
+    for q in range(cell.size):
+        k, i, j = _kij(f, int(cell[q]))
+        status, seq, _, p, t = H.rk4_track(f, k, i, j, [st["px"][q], st["py"][q], st["pz"][q]],
+                                           periods=(fs, T), t0=float(t0[q]))
+        assert status == r["status"][q], q
+        assert H.fnv_hash(seq) == int(r["hash"][q]), q
+        assert r["t"][q] == pytest.approx(t, rel=1e-7)
+    # stages released into the reversed last period leave west, the first stage east
+    col = r["cell"] % f.ncol
+    assert np.all(col[t0 > T[1]] < f.ncol // 2)
+    assert np.any(col[t0 < T[0]] >= f.ncol // 2)
