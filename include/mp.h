@@ -77,6 +77,7 @@ extern "C" {
 
 #define MP_MODE_ENDPOINT 1      /* bit: endpoint record per particle          */
 #define MP_MODE_TIMESERIES 2    /* bit: a record per output time per particle */
+#define MP_MODE_PATHLINE 4      /* bit: a point at release and one per cell-step */
 
 #define MP_SCHED_STATIC 0       /* one thread per particle, plain grid        */
 #define MP_SCHED_DYNAMIC 1      /* persistent warps refilled from a queue     */
@@ -150,6 +151,7 @@ typedef struct {
     int32_t block;           /* threads per block, 0 = auto     */
     int32_t steps_per_fetch; /* dynamic schedule, 0 = auto      */
     uint32_t flags;          /* MP_TRACK_* bits                 */
+    int64_t path_capacity;   /* pathline points the request keeps; <= 0: 64 per particle */
 } mp_track_opts;
 
 /* Endpoint arrays (SoA, particle order).  Any pointer may be NULL to skip
@@ -182,11 +184,30 @@ typedef struct {
     uint8_t pad[3];
 } mp_ts_record;
 
+/* One pathline point (Methods, "MODPATH": pathline simulations record the
+ * path of every particle), 48 bytes: the release point (seq = steps taken
+ * before this request, status as released) and the point every cell-step
+ * ends at: the entry point of the next cell (status ACTIVE), or where the
+ * path stops (TIME on the stop time, or the final status).  Points are
+ * stored in the order the GPU produces them (the points of one particle in
+ * increasing seq, particles interleaved), as the paper's threads append to
+ * their output units. */
+typedef struct {
+    double x, y, z, t;       /* global position (m), time (s)              */
+    int32_t particle;        /* index in the group                         */
+    int32_t cell;            /* cell after the step                        */
+    uint32_t seq;            /* cell-steps since release                   */
+    uint8_t status;          /* MP_ST_*                                    */
+    uint8_t pad[3];
+} mp_path_record;
+
 typedef struct {
     uint64_t cell_steps;             /* sum of per-particle cell-steps   */
     uint64_t n_status[MP_N_STATUS];  /* particles per final status       */
     float kernel_ms;                 /* device time of the tracking kernel */
     int32_t device_error;            /* kernel error flag (0 = none)     */
+    uint64_t path_points;            /* pathline points produced (also beyond
+                                        the capacity: rerun with more room)  */
 } mp_stats;
 
 /* Context on one CUDA device.  The device is made current on the calling
@@ -310,6 +331,16 @@ int mp_get_endpoints(mp_ctx* ctx, mp_req r, const mp_endpoints* out, uint32_t fl
  * Errors: MP_ERR_INVALID_ARG (request has no timeseries), as above. */
 int mp_get_timeseries(mp_ctx* ctx, mp_req r, mp_ts_record* out, uint32_t flags, void* stream);
 
+/* Copy a pathline request's points (MP_MODE_PATHLINE) to host memory, or
+ * to device memory with MP_DEVICE_PTR (then enqueued on `stream`): at most
+ * max_points of them, in the order they were produced; *n_points gets the
+ * number copied.  Points beyond the request's path_capacity are counted
+ * (mp_stats.path_points) but not kept.  Waits (bounded) for the request.
+ * Errors: MP_ERR_INVALID_ARG (no pathlines), MP_ERR_NOT_READY (unknown id),
+ * MP_ERR_TIMEOUT, MP_ERR_DEVICE, MP_ERR_CUDA. */
+int mp_get_pathlines(mp_ctx* ctx, mp_req id, mp_path_record* out, int64_t max_points, int64_t* n_points,
+                     uint32_t flags, void* stream);
+
 /* Device views of the request's own output buffers (valid until
  * mp_req_free); any out-pointer may be NULL. */
 int mp_endpoints_device(mp_ctx* ctx, mp_req r, mp_endpoints* out, mp_ts_record** ts);
@@ -337,9 +368,9 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches);
  * required) and, in timeseries mode, the [n_times][n] record buffer (device).
  * times stays a host array.  The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.  Its only other device memory is a
- * fixed file-scope array of 8 + 10 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words
- * (queue head, counters, the output times in FP64 and as FP32 pairs; about
- * 66 KB) that every
+ * fixed file-scope array of 8 + 11 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words
+ * plus the launch's request descriptor (queue head, counters, the output
+ * times in FP64 and as FP32 pairs; about 66 KB) that every
  * GPU that loads the library holds until the process exits.
  *   - The first call on each device takes the array's device address; make
  *     that first call before any stream capture.

@@ -489,6 +489,20 @@ int mp_group_size(const mp_group* g, int64_t* n)
     return MP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// pathline points a request keeps (the caller's capacity, else 64 per particle)
+long long path_capacity(const mp_track_opts* o, long long n)
+{
+    return o->path_capacity > 0 ? (long long)o->path_capacity : 64LL * n;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes)
 {
     if (!o || !bytes || n < 0) return fail(MP_ERR_INVALID_ARG, "mp_query_bytes: bad argument");
@@ -507,6 +521,7 @@ int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes)
         b += align256(sizeof(double) * (size_t)o->n_times);
         b += align256(sizeof(float2) * (size_t)o->n_times);
     }
+    if (o->mode & MP_MODE_PATHLINE) b += align256(sizeof(mp_path_record) * (size_t)path_capacity(o, n));
     *bytes = b;
     return MP_OK;
 }
@@ -525,11 +540,11 @@ namespace {
 // Check options and allocate one request's outputs (stream-ordered); fills
 // the request's device descriptor on the host side.
 int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream_t s, Request** out,
-                    mp::Req* hreq, bool* has_ts)
+                    mp::Req* hreq, unsigned* modes)
 {
     if (!g || !o) return fail(MP_ERR_INVALID_ARG, "mp_track: NULL argument");
     if (g->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_track: group belongs to another context");
-    if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))
+    if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES | MP_MODE_PATHLINE)) == 0 || (o->mode & ~7))
         return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
     if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown precision");
@@ -591,6 +606,13 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
         r->d.times = reinterpret_cast<double*>(take(sizeof(double) * (size_t)nt));
         r->d.times_ff = reinterpret_cast<float2*>(take(sizeof(float2) * (size_t)nt));
     }
+    const bool want_pl = (o->mode & MP_MODE_PATHLINE) != 0;
+    r->d.path = nullptr;
+    r->d.path_cap = 0;
+    if (want_pl) {
+        r->d.path_cap = path_capacity(o, n);
+        r->d.path = reinterpret_cast<mp_path_record*>(take(sizeof(mp_path_record) * (size_t)r->d.path_cap));
+    }
     cudaError_t e = cudaSuccess;
     if (nt > 0) e = cudaMemcpyAsync(const_cast<double*>(r->d.times), o->times, sizeof(double) * nt,
                                     cudaMemcpyHostToDevice, s);
@@ -621,10 +643,11 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     p.cont = 0;
     p.last = 1;
     split_ff(t_stop, p.tstop_hi, p.tstop_lo);
+    p.pathline = want_pl ? 1 : 0;
     hreq->in = g->d;
     hreq->o = r->d;
     hreq->p = p;
-    *has_ts = nt > 0;
+    *modes = (nt > 0 ? mp::MODE_TS : 0u) | (want_pl ? mp::MODE_PATH : 0u);
     *out = r;
     return MP_OK;
 }
@@ -642,7 +665,7 @@ void drop_request(Request* r)
 // ev: 1 records the requests' start events before the launch, 2 their end
 // events after it (a request made of several launches records each once).
 int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n, int precision, int schedule,
-                    int block, int spf, bool ts, cudaStream_t s, unsigned ev = 3)
+                    int block, int spf, unsigned modes, cudaStream_t s, unsigned ev = 3)
 {
     size_t off = 0;
     const size_t o_req = off; off = align256(off + sizeof(mp::Req) * (size_t)n);
@@ -670,8 +693,8 @@ int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n
     const int blk = block > 0 ? block : 128;
     if (e == cudaSuccess) {
         const mp::DevField& fd = *mp::field_device_view(f);
-        e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, ts, schedule, blk, 0, s)
-                                        : launch_track_mixed(fd, b, ts, schedule, blk, 0, s);
+        e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, modes, schedule, blk, 0, s)
+                                        : launch_track_mixed(fd, b, modes, schedule, blk, 0, s);
     }
     for (int i = 0; i < n && e == cudaSuccess && (ev & 2u); ++i) e = cudaEventRecord(rs[i]->k1, s);
     cudaFreeAsync(tbl, s);
@@ -755,32 +778,32 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
     std::vector<mp::Req> hr((size_t)n);
     std::vector<char> ts((size_t)n, 0);
     for (int i = 0; i < n; ++i) {
-        bool has_ts = false;
-        const int rc = prepare_request(ctx, groups[i], &opts[i], s, &rs[i], &hr[i], &has_ts);
+        unsigned md = 0;
+        const int rc = prepare_request(ctx, groups[i], &opts[i], s, &rs[i], &hr[i], &md);
         if (rc != MP_OK) {
             for (int k = 0; k < i; ++k) drop_request(rs[k]);
             return rc;
         }
-        ts[i] = has_ts;
+        ts[i] = (char)md;
     }
     // one launch per precision; launch options of the first request of each
     for (int prec = 0; prec < 2; ++prec) {
         std::vector<Request*> sel;
         std::vector<mp::Req> sreq;
-        bool any_ts = false;
+        unsigned any_modes = 0;
         int first = -1;
         for (int i = 0; i < n; ++i)
             if (opts[i].precision == prec) {
                 if (first < 0) first = i;
                 sel.push_back(rs[i]);
                 sreq.push_back(hr[i]);
-                any_ts = any_ts || ts[i];
+                any_modes |= (unsigned)ts[i];
             }
         if (sel.empty()) continue;
         int sched = 0, blk = 0, spf = 0;
-        resolve_launch(ctx, groups[0]->field, prec, any_ts, opts[first], &sched, &blk, &spf);
+        resolve_launch(ctx, groups[0]->field, prec, (any_modes & mp::MODE_TS) != 0, opts[first], &sched, &blk, &spf);
         const int rc = launch_requests(groups[0]->field, sel.data(), sreq.data(), (int)sel.size(), prec,
-                                       sched, blk, spf, any_ts, s);
+                                       sched, blk, spf, any_modes, s);
         if (rc != MP_OK) {
             cudaStreamSynchronize(s);
             for (int k = 0; k < n; ++k) drop_request(rs[k]);
@@ -828,8 +851,8 @@ int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* co
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Request* r = nullptr;
     mp::Req hr;
-    bool ts = false;
-    int rc = prepare_request(ctx, g, o, s, &r, &hr, &ts);
+    unsigned modes = 0;
+    int rc = prepare_request(ctx, g, o, s, &r, &hr, &modes);
     if (rc != MP_OK) return rc;
     r->fields.assign(fields, fields + n_periods);
     // the periods advance a request-owned copy of the group's state
@@ -857,8 +880,8 @@ int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* co
         h.p.cont = p > 0;
         h.p.last = last ? 1 : 0;
         int sched = 0, blk = 0, spf = 0;
-        resolve_launch(ctx, fields[p], o->precision, ts, *o, &sched, &blk, &spf);
-        rc = launch_requests(fields[p], &r, &h, 1, o->precision, sched, blk, spf, ts, s,
+        resolve_launch(ctx, fields[p], o->precision, (modes & mp::MODE_TS) != 0, *o, &sched, &blk, &spf);
+        rc = launch_requests(fields[p], &r, &h, 1, o->precision, sched, blk, spf, modes, s,
                              (p == 0 ? 1u : 0u) | (last ? 2u : 0u));
         if (rc != MP_OK) {
             cudaStreamSynchronize(s);
@@ -971,6 +994,28 @@ int mp_get_timeseries(mp_ctx* ctx, mp_req id, mp_ts_record* out, uint32_t flags,
                     (flags & MP_DEVICE_PTR) != 0, s);
 }
 
+int mp_get_pathlines(mp_ctx* ctx, mp_req id, mp_path_record* out, int64_t max_points, int64_t* n_points,
+                     uint32_t flags, void* stream)
+{
+    if (!ctx || !n_points || max_points < 0 || (max_points > 0 && !out))
+        return fail(MP_ERR_INVALID_ARG, "mp_get_pathlines: bad argument");
+    Request* r = find_req(ctx, id);
+    if (!r) return fail(MP_ERR_NOT_READY, "mp_get_pathlines: unknown request");
+    if (!r->d.path) return fail(MP_ERR_INVALID_ARG, "mp_get_pathlines: request has no pathlines");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = wait_event(r->k1, -1);
+    if (rc != MP_OK) return rc;
+    unsigned long long h[N_COUNTERS];
+    rc = read_counters(r, h);
+    if (rc != MP_OK) return rc;
+    if (h[COUNTER_ERR]) return fail(MP_ERR_DEVICE, "tracking kernel raised its error flag");
+    const long long kept = std::min<long long>((long long)h[COUNTER_PATH], r->d.path_cap);
+    const long long n = std::min<long long>(kept, max_points);
+    *n_points = n;
+    return copy_out(out, r->d.path, sizeof(mp_path_record) * (size_t)n, (flags & MP_DEVICE_PTR) != 0, s);
+}
+
 int mp_endpoints_device(mp_ctx* ctx, mp_req id, mp_endpoints* out, mp_ts_record** ts)
 {
     if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_endpoints_device: NULL");
@@ -1008,6 +1053,7 @@ int mp_get_stats(mp_ctx* ctx, mp_req id, mp_stats* out)
     MP_CUDA(cudaEventElapsedTime(&ms, r->k0, r->k1), "cudaEventElapsedTime");
     st.kernel_ms = ms;
     st.device_error = h[COUNTER_ERR] ? 1 : 0;
+    st.path_points = h[COUNTER_PATH];
     *out = st;
     return MP_OK;
 }
@@ -1069,16 +1115,16 @@ int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample
     oo.schedule = MP_SCHED_DYNAMIC;
     mp_tuning best{};
     best.ms = INFINITY;
-    bool ts = false;
+    unsigned modes = 0;
     for (size_t ci = 0; ci <= cands.size(); ++ci) {
         // the first pass warms the field and the allocator and is not counted
         const Cand c = ci == 0 ? cands[0] : cands[ci - 1];
         Request* r = nullptr;
         mp::Req hr;
-        int rc = prepare_request(ctx, g, &oo, s, &r, &hr, &ts);
+        int rc = prepare_request(ctx, g, &oo, s, &r, &hr, &modes);
         if (rc != MP_OK) return rc;
         if (sample > 0 && hr.p.n > sample) hr.p.n = sample;
-        rc = launch_requests(g->field, &r, &hr, 1, o->precision, c.sched, c.block, c.spf, ts, s);
+        rc = launch_requests(g->field, &r, &hr, 1, o->precision, c.sched, c.block, c.spf, modes, s);
         if (rc == MP_OK) rc = wait_event(r->k1, -1);
         float ms = 0.f;
         if (rc == MP_OK && cudaEventElapsedTime(&ms, r->k0, r->k1) != cudaSuccess) rc = fail(MP_ERR_CUDA, "timing");
@@ -1094,7 +1140,7 @@ int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample
     best.tried = (int32_t)cands.size();
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        ctx->tuned[TuneKey{g->field, o->precision, ts ? 1 : 0}] = best;
+        ctx->tuned[TuneKey{g->field, o->precision, (modes & mp::MODE_TS) ? 1 : 0}] = best;
     }
     *out = best;
     return MP_OK;

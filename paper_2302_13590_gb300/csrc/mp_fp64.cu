@@ -670,6 +670,15 @@ struct F64Engine {
         s.h = fnv_step(s.h, s.c);
     }
 
+    // the pathline point of the particle's current state
+    __device__ __forceinline__ void path_point(const State& s, double& x, double& y, double& z, double& t) const
+    {
+        x = gx(s);
+        y = gy(s);
+        z = gz(s);
+        t = s.t;
+    }
+
     template <bool TS>
     __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
     {
@@ -706,11 +715,11 @@ struct F64Engine {
     }
 };
 
-cudaError_t launch_track_fp64(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+cudaError_t launch_track_fp64(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                               int blocks_per_sm_cap, cudaStream_t s)
 {
     F64Engine e{f, b};
-    return launch_tracking(e, ts, schedule, block, blocks_per_sm_cap, s);
+    return launch_tracking(e, modes, schedule, block, blocks_per_sm_cap, s);
 }
 
 }  // namespace mp

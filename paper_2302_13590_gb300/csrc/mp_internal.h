@@ -97,7 +97,16 @@ enum : int { ST_SKIP = 0xFF };
 
 // counters[0] = cell-steps, [1 + s] = particles with final status s,
 // [COUNTER_ERR] = device error flag (index of the first bad access + 1)
-enum : int { COUNTER_STEPS = 0, COUNTER_STATUS = 1, COUNTER_ERR = 1 + MP_N_STATUS, N_COUNTERS = 2 + MP_N_STATUS };
+enum : int {
+    COUNTER_STEPS = 0,
+    COUNTER_STATUS = 1,
+    COUNTER_ERR = 1 + MP_N_STATUS,
+    COUNTER_PATH = 2 + MP_N_STATUS,   // pathline points appended (the append cursor)
+    N_COUNTERS = 3 + MP_N_STATUS
+};
+
+// launch modes: which outputs the kernel variant writes besides endpoints
+enum : unsigned { MODE_TS = 1u, MODE_PATH = 2u };
 
 struct DevOut {
     int32_t* cell;
@@ -116,6 +125,8 @@ struct DevOut {
     const double* times;         // device copy, [n_times]
     const float2* times_ff;      // the same times as FP32 pairs (hi, lo)
     unsigned long long* counters;  // [N_COUNTERS]
+    mp_path_record* path;        // pathline points or nullptr
+    long long path_cap;          // points that fit in path
 };
 
 struct TrackParams {
@@ -129,6 +140,7 @@ struct TrackParams {
     int cont;                    // a later flow period of one request: skip ended particles and
                                  // output times already written
     int last;                    // the request's last launch: count particles paused at its stop time
+    int pathline;                // append pathline points
     float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
 };
 
@@ -169,9 +181,9 @@ cudaError_t launch_release_box(const DevField& f, const DevState& st, long long 
 cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long long n, const int32_t* cell,
                                     const double* local, const double* t0, cudaStream_t s);
 // ts: true if any request of the batch writes timeseries records
-cudaError_t launch_track_fp64(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+cudaError_t launch_track_fp64(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                               int blocks_per_sm_cap, cudaStream_t s);
-cudaError_t launch_track_mixed(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+cudaError_t launch_track_mixed(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                                int blocks_per_sm_cap, cudaStream_t s);
 
 // Host helpers shared by the entry points: the calling thread's error

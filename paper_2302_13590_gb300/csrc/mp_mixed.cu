@@ -385,6 +385,15 @@ struct MixEngine {
         s.h = fnv_step(s.h, s.c);
     }
 
+    // the pathline point of the particle's current state
+    __device__ __forceinline__ void path_point(const State& s, double& x, double& y, double& z, double& t) const
+    {
+        x = gx(s, s.x0);
+        y = gy(s, s.x1);
+        z = gz(s, s.x2);
+        t = (double)s.th + (double)s.tl;
+    }
+
     template <bool TS>
     __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
     {
@@ -429,11 +438,11 @@ struct MixEngine {
     }
 };
 
-cudaError_t launch_track_mixed(const DevField& f, const Batch& b, bool ts, int schedule, int block,
+cudaError_t launch_track_mixed(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                                int blocks_per_sm_cap, cudaStream_t s)
 {
     MixEngine e{f, b};
-    return launch_tracking(e, ts, schedule, block, blocks_per_sm_cap, s);
+    return launch_tracking(e, modes, schedule, block, blocks_per_sm_cap, s);
 }
 
 }  // namespace mp

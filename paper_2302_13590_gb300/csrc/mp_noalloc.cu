@@ -147,8 +147,8 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     b.n_total = a->n;
     b.steps_per_fetch = p.steps_per_fetch;
     b.queue = queue;
-    e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, nt > 0, o->schedule, block, 0, s)
-                                       : launch_track_mixed(fd, b, nt > 0, o->schedule, block, 0, s);
+    e = (o->precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, nt > 0 ? MODE_TS : 0u, o->schedule, block, 0, s)
+                                       : launch_track_mixed(fd, b, nt > 0 ? MODE_TS : 0u, o->schedule, block, 0, s);
     if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: launch: ") + cudaGetErrorString(e));
     if (stats) {
         unsigned long long h[N_COUNTERS];

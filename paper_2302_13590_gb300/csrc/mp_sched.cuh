@@ -48,7 +48,7 @@ __device__ __forceinline__ void flush_counters(const E& e, unsigned long long* s
     __syncthreads();
     if (e.b.n_reqs != 1) return;
     unsigned long long* dst = e.b.reqs[0].o.counters;
-    for (int i = threadIdx.x; i < N_COUNTERS - 1; i += blockDim.x)
+    for (int i = threadIdx.x; i < COUNTER_ERR; i += blockDim.x)
         if (s_cnt[i]) atomicAdd(dst + i, s_cnt[i]);
 }
 
@@ -167,7 +167,94 @@ __device__ __forceinline__ void tail_fill(const E& e, const typename E::State& s
     }
 }
 
-template <class E, bool TS>
+// ---------------------------------------------------------------------------
+// Pathline points (Methods, "MODPATH": pathline simulations).  Every lane
+// that took a cell-step has one point to append; the warp stages them in a
+// shared-memory queue and, when it is full, appends them to the requests'
+// point arrays: records of one request take consecutive slots claimed by one
+// atomicAdd on that request's cursor (__match_any_sync groups the lanes by
+// request), so the output is dense and needs no compaction.  The order of
+// points across particles is the order the warps produce them, as with the
+// paper's threads appending to output units.
+// ---------------------------------------------------------------------------
+
+constexpr int PQ_CAP = 64;   // points per warp queue (>= 2 x 32)
+
+struct PathQ {
+    double x[PQ_CAP], y[PQ_CAP], z[PQ_CAP], t[PQ_CAP];
+    int q[PQ_CAP], c[PQ_CAP], r[PQ_CAP];
+    unsigned seq[PQ_CAP];
+    unsigned char st[PQ_CAP];
+};
+
+// one 48-byte point as three 16-byte streaming stores
+__device__ __forceinline__ void store_path(mp_path_record* dst, const PathQ& Q, int i)
+{
+    __stcs(reinterpret_cast<double2*>(dst), make_double2(Q.x[i], Q.y[i]));
+    __stcs(reinterpret_cast<double2*>(dst) + 1, make_double2(Q.z[i], Q.t[i]));
+    __stcs(reinterpret_cast<int4*>(dst) + 2, make_int4(Q.q[i], Q.c[i], (int)Q.seq[i], (int)Q.st[i]));
+}
+
+template <class E>
+__device__ __forceinline__ void pl_flush(const E& e, PathQ& Q, int& pcount)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    __syncwarp();
+    for (int base = 0; base < pcount; base += 32) {
+        const int i = base + lane;
+        const bool has = i < pcount;
+        const int r = has ? Q.r[i] : -1;
+        const unsigned peers = __match_any_sync(FULL, r);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long pos = 0;
+        if (has && lane == leader)
+            pos = atomicAdd(e.b.reqs[r].o.counters + COUNTER_PATH, (unsigned long long)__popc(peers));
+        pos = __shfl_sync(FULL, pos, leader) + (unsigned long long)__popc(peers & lt);
+        if (has) {
+            const DevOut& o = e.b.reqs[r].o;
+            if ((long long)pos < o.path_cap) store_path(o.path + pos, Q, i);
+        }
+    }
+    __syncwarp();
+    pcount = 0;
+}
+
+// Stage the point of every lane with emit set (warp-uniform call).
+template <class E>
+__device__ __forceinline__ void pl_push(const E& e, PathQ& Q, int& pcount, const typename E::State& s, long long q,
+                                        bool emit, int st)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned m = __ballot_sync(FULL, emit);
+    if (!m) return;
+    if (pcount + __popc(m) > PQ_CAP) pl_flush(e, Q, pcount);
+    if (emit) {
+        const int lane = threadIdx.x & 31;
+        const int slot = pcount + __popc(m & ((1u << lane) - 1u));
+        double x, y, z, t;
+        e.path_point(s, x, y, z, t);
+        Q.x[slot] = x; Q.y[slot] = y; Q.z[slot] = z; Q.t[slot] = t;
+        Q.q[slot] = (int)q; Q.c[slot] = s.c; Q.r[slot] = s.r;
+        Q.seq[slot] = s.steps;
+        Q.st[slot] = (unsigned char)st;
+    }
+    pcount += __popc(m);
+    __syncwarp();
+}
+
+// A particle's first point: when its request records pathlines and this
+// launch starts its line (not a later flow period); TIME (a start at or
+// after the stop time) shows as the status it was released with.
+template <class E, class S>
+__device__ __forceinline__ bool path_start(const E& e, const S& s)
+{
+    const TrackParams& p = e.b.reqs[s.r].p;
+    return p.pathline && !p.cont && s.st != ST_SKIP && s.c >= 0;
+}
+
+template <class E, bool TS, bool PL>
 __global__ void __launch_bounds__(256) k_track_static(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
@@ -176,23 +263,32 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
-    int qcount = 0;
+    PathQ* s_p = reinterpret_cast<PathQ*>(s_dyn + (TS ? sizeof(typename E::RecQ) * (blockDim.x >> 5) : 0));
+    PathQ& P = s_p[PL ? (threadIdx.x >> 5) : 0];
+    int qcount = 0, pcount = 0;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long q = 0;
     typename E::State s;
     s.r = 0;
-    bool live = false, ended = false;
+    s.steps = 0;
+    s.st = ST_SKIP;
+    s.c = -1;
+    bool live = false, ended = false, loaded = false;
     if (g < e.b.n_total) {
         const int r = request_of(e.b, g);
         q = g - __ldg(e.b.starts + r);
         e.template load<TS>(r, q, s);
         live = s.st == MP_ST_ACTIVE;
         ended = !live && s.st != ST_SKIP;
+        loaded = true;
     }
+    if (PL) pl_push(e, P, pcount, s, q, loaded && path_start(e, s), s.st == MP_ST_TIME ? MP_ST_ACTIVE : s.st);
     if (TS) tail_fill(e, s, q, ended && !paused(e, s));
     if (ended) e.template finish<TS>(q, s, s_cnt);
     while (__any_sync(FULL, live)) {
+        const unsigned before = s.steps;
         e.template step<TS>(q, s, live, Q, qcount);
+        if (PL) pl_push(e, P, pcount, s, q, live && s.steps != before && e.b.reqs[s.r].p.pathline, s.st);
         ended = live && s.st != MP_ST_ACTIVE;
         if (TS) tail_fill(e, s, q, ended && !paused(e, s));
         if (ended) {
@@ -201,10 +297,11 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
         }
     }
     if (TS) rq_drain(e, Q, qcount, true);
+    if (PL) pl_flush(e, P, pcount);
     flush_counters(e, s_cnt);
 }
 
-template <class E, bool TS>
+template <class E, bool TS, bool PL>
 __global__ void __launch_bounds__(256) k_track_dynamic(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
@@ -212,7 +309,9 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
     __syncthreads();
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
-    int qcount = 0;
+    PathQ* s_p = reinterpret_cast<PathQ*>(s_dyn + (TS ? sizeof(typename E::RecQ) * (blockDim.x >> 5) : 0));
+    PathQ& P = s_p[PL ? (threadIdx.x >> 5) : 0];
+    int qcount = 0, pcount = 0;
     const unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -223,9 +322,12 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     bool drained = false;
     typename E::State s;
     s.r = 0;
+    s.steps = 0;
+    s.st = ST_SKIP;
+    s.c = -1;
     while (true) {
         const unsigned idle = __ballot_sync(FULL, !live);
-        bool ended = false;
+        bool ended = false, loaded = false;
         if (idle && !drained) {
             const unsigned cnt = __popc(idle);
             unsigned long long base = 0;
@@ -240,9 +342,11 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
                     e.template load<TS>(r, q, s);
                     live = s.st == MP_ST_ACTIVE;
                     ended = !live && s.st != ST_SKIP;
+                    loaded = true;
                 }
             }
         }
+        if (PL) pl_push(e, P, pcount, s, q, loaded && path_start(e, s), s.st == MP_ST_TIME ? MP_ST_ACTIVE : s.st);
         if (TS) tail_fill(e, s, q, ended && !paused(e, s));
         if (ended) e.template finish<TS>(q, s, s_cnt);
         if (!__any_sync(FULL, live)) {
@@ -250,7 +354,9 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
             continue;
         }
         for (int it = 0; it < S; ++it) {
+            const unsigned before = s.steps;
             e.template step<TS>(q, s, live, Q, qcount);
+            if (PL) pl_push(e, P, pcount, s, q, live && s.steps != before && e.b.reqs[s.r].p.pathline, s.st);
             ended = live && s.st != MP_ST_ACTIVE;
             if (TS) tail_fill(e, s, q, ended && !paused(e, s));
             if (ended) {
@@ -260,39 +366,51 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
         }
     }
     if (TS) rq_drain(e, Q, qcount, true);
+    if (PL) pl_flush(e, P, pcount);
     flush_counters(e, s_cnt);
 }
 
+// One variant of the tracking kernel: opt in to more than 48 KB of dynamic
+// shared memory when the queues need it, size a persistent grid by occupancy.
+template <class E, bool TS, bool PL>
+cudaError_t launch_variant(const E& e, int schedule, int block, int blocks_per_sm_cap, size_t smem, cudaStream_t st)
+{
+    auto kern = schedule == MP_SCHED_STATIC ? k_track_static<E, TS, PL> : k_track_dynamic<E, TS, PL>;
+    cudaError_t err = cudaSuccess;
+    if (smem > 48 * 1024) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    long long grid = (e.b.n_total + block - 1) / block;
+    if (schedule != MP_SCHED_STATIC) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem)) != cudaSuccess)
+            return err;
+        if (per_sm < 1) per_sm = 1;
+        if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
+        if (grid > (long long)sms * per_sm) grid = (long long)sms * per_sm;
+    }
+    kern<<<(unsigned)grid, block, smem, st>>>(e);
+    return cudaGetLastError();
+}
+
 template <class E>
-cudaError_t launch_tracking(const E& e, bool ts, int schedule, int block, int blocks_per_sm_cap, cudaStream_t st)
+cudaError_t launch_tracking(const E& e, unsigned modes, int schedule, int block, int blocks_per_sm_cap,
+                            cudaStream_t st)
 {
     if (e.b.n_total <= 0) return cudaSuccess;
     if (block <= 0) block = 128;
     if (block > 256) block = 256;
     block = (block + 31) / 32 * 32;
-    const size_t smem = ts ? sizeof(typename E::RecQ) * (size_t)(block / 32) : 0;
-    if (schedule == MP_SCHED_STATIC) {
-        const long long grid = (e.b.n_total + block - 1) / block;
-        if (ts) k_track_static<E, true><<<(unsigned)grid, block, smem, st>>>(e);
-        else k_track_static<E, false><<<(unsigned)grid, block, smem, st>>>(e);
-        return cudaGetLastError();
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
-    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (err != cudaSuccess) return err;
-    if (ts) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, true>, block, smem);
-    else err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_track_dynamic<E, false>, block, smem);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) per_sm = 1;
-    if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
-    long long grid = (long long)sms * per_sm;
-    const long long need = (e.b.n_total + block - 1) / block;
-    if (grid > need) grid = need;
-    if (ts) k_track_dynamic<E, true><<<(unsigned)grid, block, smem, st>>>(e);
-    else k_track_dynamic<E, false><<<(unsigned)grid, block, smem, st>>>(e);
-    return cudaGetLastError();
+    const bool ts = (modes & MODE_TS) != 0, pl = (modes & MODE_PATH) != 0;
+    const size_t warps = (size_t)(block / 32);
+    const size_t smem = (ts ? sizeof(typename E::RecQ) * warps : 0) + (pl ? sizeof(PathQ) * warps : 0);
+    if (ts && pl) return launch_variant<E, true, true>(e, schedule, block, blocks_per_sm_cap, smem, st);
+    if (ts) return launch_variant<E, true, false>(e, schedule, block, blocks_per_sm_cap, smem, st);
+    if (pl) return launch_variant<E, false, true>(e, schedule, block, blocks_per_sm_cap, smem, st);
+    return launch_variant<E, false, false>(e, schedule, block, blocks_per_sm_cap, smem, st);
 }
 
 }  // namespace mp

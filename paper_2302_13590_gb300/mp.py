@@ -35,7 +35,7 @@ STATUS_NAMES = ["ACTIVE", "TIME", "SINK", "BOUNDARY", "EXIT_DOMAIN", "NO_EXIT", 
 FACE_NONE = 255
 MP_DEVICE_PTR = 1
 PREC_FP64, PREC_MIXED = 0, 1
-MODE_ENDPOINT, MODE_TIMESERIES = 1, 2
+MODE_ENDPOINT, MODE_TIMESERIES, MODE_PATHLINE = 1, 2, 4
 SCHED_STATIC, SCHED_DYNAMIC, SCHED_AUTO = 0, 1, 2
 TRACK_UPDATE_GROUP = 1
 TRACK_PASS_WEAK_SINKS = 2
@@ -44,6 +44,9 @@ RELEASE_EXPLICIT, RELEASE_BOX = 0, 1
 TS_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("cell", "<i4"), ("status", "u1"),
                       ("pad", "u1", (3,))])
 assert TS_RECORD.itemsize == 32
+PATH_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("t", "<f8"), ("particle", "<i4"),
+                        ("cell", "<i4"), ("seq", "<u4"), ("status", "u1"), ("pad", "u1", (3,))])
+assert PATH_RECORD.itemsize == 48
 
 _vp = ctypes.c_void_p
 
@@ -66,7 +69,7 @@ class TrackOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("n_times", ctypes.c_int32), ("times", _vp), ("t_stop", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("block", ctypes.c_int32), ("steps_per_fetch", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("path_capacity", ctypes.c_int64)]
 
 
 class Endpoints(ctypes.Structure):
@@ -89,7 +92,7 @@ class Tuning(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("cell_steps", ctypes.c_uint64), ("n_status", ctypes.c_uint64 * 8),
-                ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32)]
+                ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32), ("path_points", ctypes.c_uint64)]
 
 
 ENDPOINT_DTYPES = {"cell": np.int32, "x": np.float64, "y": np.float64, "z": np.float64, "px": np.float64,
@@ -123,6 +126,8 @@ SIGNATURES = {
     "mp_autotune": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), ctypes.c_int64, _vp, _P(Tuning)]),
     "mp_set_tuning": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning)]),
     "mp_group_set_field": (ctypes.c_int, [_vp, _vp]),
+    "mp_get_pathlines": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _P(ctypes.c_int64), ctypes.c_uint32,
+                                        _vp]),
     "mp_track_periods": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(_vp), _vp, _P(TrackOpts), _vp,
                                         _P(ctypes.c_int64)]),
 }
@@ -278,10 +283,10 @@ def mp_track_periods(ctx, gh, fields, t_end, opts: "TrackOpts", stream=None) -> 
 
 
 def make_opts(mode=MODE_ENDPOINT, precision=PREC_FP64, schedule=SCHED_DYNAMIC, times=None, t_stop=math.inf,
-              max_steps=0, block=0, steps_per_fetch=0, flags=0):
+              max_steps=0, block=0, steps_per_fetch=0, flags=0, path_capacity=0):
     tarr = None if times is None else _host(times, np.float64)
     o = TrackOpts(int(mode), int(precision), int(schedule), 0 if tarr is None else int(tarr.size), _ptr(tarr),
-                  float(t_stop), int(max_steps), int(block), int(steps_per_fetch), int(flags))
+                  float(t_stop), int(max_steps), int(block), int(steps_per_fetch), int(flags), int(path_capacity))
     o._keep = tarr
     return o
 
@@ -340,11 +345,25 @@ def mp_endpoints_device(ctx, req: int):
     return {k: getattr(e, k) for k, _ in Endpoints._fields_}, ts.value
 
 
+def mp_get_pathlines(ctx, req: int, max_points: int = -1, out=None, device: bool = False, stream=None):
+    """The request's pathline points (numpy PATH_RECORD array in production
+    order; or into a given host/device buffer); max_points < 0: all kept."""
+    if max_points < 0:
+        max_points = mp_get_stats(ctx, req)["path_points"]
+    if out is None:
+        out = np.empty(max_points, PATH_RECORD)
+    got = ctypes.c_int64()
+    _check(load_library().mp_get_pathlines(ctx, int(req), _ptr(out), int(max_points), ctypes.byref(got),
+                                           MP_DEVICE_PTR if device else 0, _stream(stream)))
+    return out[:got.value] if isinstance(out, np.ndarray) else out
+
+
 def mp_get_stats(ctx, req: int) -> dict:
     s = Stats()
     _check(load_library().mp_get_stats(ctx, int(req), ctypes.byref(s)))
     return {"cell_steps": int(s.cell_steps), "n_status": [int(v) for v in s.n_status],
-            "kernel_ms": float(s.kernel_ms), "device_error": int(s.device_error)}
+            "kernel_ms": float(s.kernel_ms), "device_error": int(s.device_error),
+            "path_points": int(s.path_points)}
 
 
 def mp_req_free(ctx, req: int):
@@ -480,6 +499,9 @@ class Request:
 
     def stats(self):
         return mp_get_stats(self.ctx.h, self.id)
+
+    def pathlines(self, max_points: int = -1):
+        return mp_get_pathlines(self.ctx.h, self.id, max_points)
 
     def free(self):
         mp_req_free(self.ctx.h, self.id)

@@ -50,7 +50,10 @@ int main(void) {{
          offsetof(mp_release_desc, seed), offsetof(mp_release_desc, id_offset));
   printf("%zu %zu %zu %zu\\n", sizeof(mp_track_opts), offsetof(mp_track_opts, t_stop),
          offsetof(mp_track_opts, block), offsetof(mp_track_opts, flags));
-  printf("%zu %zu %zu\\n", sizeof(mp_endpoints), sizeof(mp_stats), offsetof(mp_stats, kernel_ms));
+  printf("%zu %zu %zu %zu\\n", sizeof(mp_endpoints), sizeof(mp_stats), offsetof(mp_stats, kernel_ms),
+         offsetof(mp_stats, path_points));
+  printf("%zu %zu %zu\\n", offsetof(mp_track_opts, path_capacity), sizeof(mp_path_record),
+         offsetof(mp_path_record, seq));
   return 0;
 }}
 """)
@@ -61,7 +64,9 @@ int main(void) {{
     assert got[0] == [ctypes.sizeof(F), F.origin.offset, F.qx.offset, F.flags.offset, mp.TS_RECORD.itemsize]
     assert got[1] == [ctypes.sizeof(R), R.lo.offset, R.seed.offset, R.id_offset.offset]
     assert got[2] == [ctypes.sizeof(T), T.t_stop.offset, T.block.offset, T.flags.offset]
-    assert got[3] == [ctypes.sizeof(mp.Endpoints), ctypes.sizeof(mp.Stats), mp.Stats.kernel_ms.offset]
+    assert got[3] == [ctypes.sizeof(mp.Endpoints), ctypes.sizeof(mp.Stats), mp.Stats.kernel_ms.offset,
+                      mp.Stats.path_points.offset]
+    assert got[4] == [T.path_capacity.offset, mp.PATH_RECORD.itemsize, mp.PATH_RECORD.fields["seq"][1]]
 
 
 def test_no_device_calls_fail_cleanly_without_gpu():
