@@ -81,13 +81,13 @@ def _load():
             vp = ctypes.c_void_p
             lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
             lib.orc_philox4x32_10.restype = None
-            lib.orc_exit_time.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_int)]
+            lib.orc_exit_time.argtypes = [ctypes.c_double] * 6 + [ctypes.POINTER(ctypes.c_int)]
             lib.orc_exit_time.restype = ctypes.c_double
             lib.orc_log1p.argtypes = [ctypes.c_double]
             lib.orc_log1p.restype = ctypes.c_double
             lib.orc_expm1.argtypes = [ctypes.c_double]
             lib.orc_expm1.restype = ctypes.c_double
-            lib.orc_move.argtypes = [ctypes.c_double] * 5
+            lib.orc_move.argtypes = [ctypes.c_double] * 6
             lib.orc_move.restype = ctypes.c_double
             lib.orc_release_box.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp,
                                             ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp, vp]
@@ -142,7 +142,7 @@ def exit_time(v1, v2, A, D, p):
     """(t_exit, face) for one axis of one cell (face +1, -1 or 0 = none)."""
     lib = _load()
     face = ctypes.c_int(0)
-    t = lib.orc_exit_time(float(v1), float(v2), float(A), float(D), float(p), ctypes.byref(face))
+    t = lib.orc_exit_time(float(v1), float(v2), float(A), _inv(A), float(D), float(p), ctypes.byref(face))
     return t, face.value
 
 
@@ -155,7 +155,13 @@ def expm1(w):
 
 
 def move(v1, A, D, p, dt):
-    return _load().orc_move(float(v1), float(A), float(D), float(p), float(dt))
+    return _load().orc_move(float(v1), float(A), _inv(A), float(D), float(p), float(dt))
+
+
+def _inv(A):
+    """1 / A as the oracle forms it per cell (0 when A == 0)."""
+    A = float(A)
+    return 1.0 / A if A != 0.0 else 0.0
 
 
 def release_box(f, n, lo, hi, seed, id_offset=0):

@@ -17,10 +17,14 @@
  *   face velocities   v1 = Q1 / (n * area_a),  v2 = Q2 / (n * area_a)
  *   gradient          A  = (v2 - v1) / D_a            (D_a = cell size)
  *   velocity at p     vp = v1 + A * p                 (p = offset from face 1)
- *   motion            p(t) = p + vp * t * (e^{A t} - 1) / (A t)
- *   exit time         t_a = ln(v_exit / vp) / A = (d / vp) * ln(1 + z) / z,
- *                     d = signed distance to the exit face, z = A d / vp,
- *                     and t_a = d / vp in the limit A -> 0 (z == 0).
+ *   motion            p(t) = p + vp (e^{A t} - 1) / A     (Pollock's form;
+ *                     p + vp t when A t == 0)
+ *   exit time         t_a = ln(v_exit / vp) / A = ln(1 + z) / A,
+ *                     d = signed distance to the exit face, z = A d / vp
+ *                     (computed as A * (d / vp)), and t_a = d / vp in the
+ *                     limit A -> 0 (z == 0).
+ *   1 / A is computed once per cell (0 when A == 0) and multiplies, so a
+ *   step divides only for d / vp and inside log1p.
  *
  * A face is reachable on an axis only if the particle velocity and the
  * exit-face velocity point the same way (vp > 0 and v2 > 0 -> face 2;
@@ -148,7 +152,8 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
  *
  * expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
  * r = w - k ln2 (split as above), expm1(r) = r + r^2/2! + ... + r^14/14!
- * (|r| <= 0.347), expm1(w) = (2^k - 1) + 2^k expm1(r).
+ * (|r| <= 0.347), expm1(w) = (2^k - 1) + 2^k expm1(r); 2^k is formed with
+ * k limited to [-2000, 2000] (the same 2^k, 0 or infinity, for every k).
  */
 static const double ORC_LN2_HI = 6.93147180369123816490e-01;
 static const double ORC_LN2_LO = 1.90821492927058770002e-10;
@@ -183,13 +188,14 @@ double orc_expm1(double w)
     }
     double em = r * p;
     if (k == 0.0) return em;
-    double t = ldexp(1.0, (int)k);
+    double kc = k > 2000.0 ? 2000.0 : (k < -2000.0 ? -2000.0 : k);
+    double t = ldexp(1.0, (int)kc);
     return (t - 1.0) + t * em;
 }
 
 /* ---- the Pollock pieces ---------------------------------------------- */
 
-double orc_exit_time(double v1, double v2, double A, double D, double p, int* face)
+double orc_exit_time(double v1, double v2, double A, double iA, double D, double p, int* face)
 {
     double vp = v1 + A * p;
     double d;
@@ -199,17 +205,16 @@ double orc_exit_time(double v1, double v2, double A, double D, double p, int* fa
     double t1 = d / vp;
     double z = A * t1;
     if (z == 0.0) return t1;
-    return t1 * (orc_log1p(z) / z);
+    return orc_log1p(z) * iA;
 }
 
-double orc_move(double v1, double A, double D, double p, double dt)
+double orc_move(double v1, double A, double iA, double D, double p, double dt)
 {
     double vp = v1 + A * p;
     double s = vp * dt;
     if (s == 0.0) return p;
     double w = A * dt;
-    double f = (w == 0.0) ? 1.0 : orc_expm1(w) / w;
-    double pn = p + s * f;
+    double pn = (w == 0.0) ? p + s : p + (vp * orc_expm1(w)) * iA;
     if (pn < 0.0) pn = 0.0;
     if (pn > D) pn = D;
     return pn;
@@ -218,7 +223,7 @@ double orc_move(double v1, double A, double D, double p, double dt)
 /* ---- cell data gathered at cell entry (the per-cell "initialisation") -- */
 
 typedef struct {
-    double v1[3], v2[3], A[3], D[3];
+    double v1[3], v2[3], A[3], iA[3], D[3];
 } cellvel;
 
 static void cell_velocities(const orc_field* f, int k, int i, int j, cellvel* cv)
@@ -239,7 +244,10 @@ static void cell_velocities(const orc_field* f, int k, int i, int j, cellvel* cv
     cv->v1[1] = qy1 / (n * ay); cv->v2[1] = qy2 / (n * ay);
     cv->v1[2] = qz1 / (n * az); cv->v2[2] = qz2 / (n * az);
     cv->D[0] = dx; cv->D[1] = dy; cv->D[2] = dzz;
-    for (int a = 0; a < 3; a++) cv->A[a] = (cv->v2[a] - cv->v1[a]) / cv->D[a];
+    for (int a = 0; a < 3; a++) {
+        cv->A[a] = (cv->v2[a] - cv->v1[a]) / cv->D[a];
+        cv->iA[a] = (cv->A[a] != 0.0) ? 1.0 / cv->A[a] : 0.0;
+    }
 }
 
 /* ---- release ----------------------------------------------------------- */
@@ -395,7 +403,7 @@ int orc_track(const orc_field* f, int64_t n,
             int face[3];
             double te[3];
             for (int a = 0; a < 3; a++)
-                te[a] = orc_exit_time(cv.v1[a], cv.v2[a], cv.A[a], cv.D[a], p[a], &face[a]);
+                te[a] = orc_exit_time(cv.v1[a], cv.v2[a], cv.A[a], cv.iA[a], cv.D[a], p[a], &face[a]);
             int ax = -1;
             double tmin = INFINITY;
             for (int a = 0; a < 3; a++)
@@ -412,9 +420,9 @@ int orc_track(const orc_field* f, int64_t n,
                  * this cell; later output times still see it move inside */
                 while (kn < nt) {
                     double tau = opt->times[kn] - t;
-                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
-                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
-                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_NO_EXIT);
                     kn++;
                 }
@@ -425,13 +433,13 @@ int orc_track(const orc_field* f, int64_t n,
                 double dt = t_stop - t;
                 while (kn < nt && opt->times[kn] <= t_stop) {
                     double tau = opt->times[kn] - t;
-                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
-                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
-                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                     kn++;
                 }
-                for (int a = 0; a < 3; a++) p[a] = orc_move(cv.v1[a], cv.A[a], cv.D[a], p[a], dt);
+                for (int a = 0; a < 3; a++) p[a] = orc_move(cv.v1[a], cv.A[a], cv.iA[a], cv.D[a], p[a], dt);
                 t = t_stop;
                 st = ORC_ST_TIME;
                 break;
@@ -441,15 +449,15 @@ int orc_track(const orc_field* f, int64_t n,
             double t_end = t + dt;
             while (kn < nt && opt->times[kn] <= t_end) {
                 double tau = opt->times[kn] - t;
-                double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.D[0], p[0], tau);
-                double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.D[1], p[1], tau);
-                double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.D[2], p[2], tau);
+                double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                 write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                 kn++;
             }
             for (int a = 0; a < 3; a++) {
                 if (a == ax) p[a] = (face[a] > 0) ? cv.D[a] : 0.0;
-                else p[a] = orc_move(cv.v1[a], cv.A[a], cv.D[a], p[a], dt);
+                else p[a] = orc_move(cv.v1[a], cv.A[a], cv.iA[a], cv.D[a], p[a], dt);
             }
             t = t_end;
             exit_face = (uint8_t)(2 * ax + (face[ax] > 0 ? 1 : 0));

@@ -7,9 +7,9 @@
 // Method (Pollock 1988, the displacement scheme the paper keeps unchanged;
 // Methods, "MODPATH"): inside a cell each velocity component varies linearly
 // between its two faces, v(p) = v1 + A p with A = (v2 - v1) / D, so the
-// motion along each axis is p(t) = p + v_p t (e^{A t} - 1) / (A t) and the
-// time to reach the exit face is t_a = (d / v_p) ln(1 + z) / z with
-// z = A d / v_p (t_a = d / v_p when z == 0).  The particle leaves through the
+// motion along each axis is p(t) = p + v_p (e^{A t} - 1) / A (p + v_p t when
+// A t == 0) and the time to reach the exit face is t_a = ln(1 + z) / A with
+// z = A (d / v_p) (t_a = d / v_p when z == 0); 1 / A comes with the cell.  The particle leaves through the
 // face with the smallest t_a (lowest axis on ties) and is handed to the
 // neighbour across it, until a stopping condition holds (Methods, "MODPATH").
 #include <cfloat>
@@ -49,6 +49,7 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const do
     nb |= (unsigned long long)nb_class(f, k + 1, i, j) << 10;
     CellF64 r{};
     CellF32 s{};
+    double v2x = 0.0, v2y = 0.0, v2z = 0.0;
     const int8_t ib = f.ibound[c];
     if (ib == 1 || ib == 2) {
         const double n = por[c];
@@ -60,20 +61,29 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const do
         const double qy2 = qy[((long long)k * (nrow + 1) + i + 1) * ncol + j];
         const double qz1 = qz[((long long)k * nrow + i) * ncol + j];
         const double qz2 = qz[((long long)(k + 1) * nrow + i) * ncol + j];
-        r.v1x = qx1 / (n * ax); r.v2x = qx2 / (n * ax);
-        r.v1y = qy1 / (n * ay); r.v2y = qy2 / (n * ay);
-        r.v1z = qz1 / (n * az); r.v2z = qz2 / (n * az);
-        r.Ax = (r.v2x - r.v1x) / dx;
-        r.Ay = (r.v2y - r.v1y) / dy;
-        r.Az = (r.v2z - r.v1z) / dzz;
-        s.u1x = (float)(r.v1x / dx); s.u2x = (float)(r.v2x / dx);
-        s.u1y = (float)(r.v1y / dy); s.u2y = (float)(r.v2y / dy);
-        s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(r.v2z / dzz);
+        r.v1x = qx1 / (n * ax); v2x = qx2 / (n * ax);
+        r.v1y = qy1 / (n * ay); v2y = qy2 / (n * ay);
+        r.v1z = qz1 / (n * az); v2z = qz2 / (n * az);
+        r.Ax = (v2x - r.v1x) / dx;
+        r.Ay = (v2y - r.v1y) / dy;
+        r.Az = (v2z - r.v1z) / dzz;
+        r.iAx = r.Ax != 0.0 ? 1.0 / r.Ax : 0.0;
+        r.iAy = r.Ay != 0.0 ? 1.0 / r.Ay : 0.0;
+        r.iAz = r.Az != 0.0 ? 1.0 / r.Az : 0.0;
+        s.u1x = (float)(r.v1x / dx); s.u2x = (float)(v2x / dx);
+        s.u1y = (float)(r.v1y / dy); s.u2y = (float)(v2y / dy);
+        s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(v2z / dzz);
+    }
+    const double v1a[3] = {r.v1x, r.v1y, r.v1z}, v2a[3] = {v2x, v2y, v2z};
+    for (int a = 0; a < 3; ++a) {
+        const unsigned long long sg = (v1a[a] > 0.0 ? 1ULL : 0ULL) | (v1a[a] < 0.0 ? 2ULL : 0ULL) |
+                                      (v2a[a] > 0.0 ? 4ULL : 0ULL) | (v2a[a] < 0.0 ? 8ULL : 0ULL);
+        nb |= sg << (NB_SIGN + 4 * a);
     }
     r.nb = nb;
-    r.fv1x = (float)r.v1x; r.fv2x = (float)r.v2x; r.fAx = (float)r.Ax;
-    r.fv1y = (float)r.v1y; r.fv2y = (float)r.v2y; r.fAy = (float)r.Ay;
-    r.fv1z = (float)r.v1z; r.fv2z = (float)r.v2z; r.fAz = (float)r.Az;
+    r.fv1x = (float)r.v1x; r.fv2x = (float)v2x; r.fAx = (float)r.Ax;
+    r.fv1y = (float)r.v1y; r.fv2y = (float)v2y; r.fAy = (float)r.Ay;
+    r.fv1z = (float)r.v1z; r.fv2z = (float)v2z; r.fAz = (float)r.Az;
     s.nb = (uint32_t)nb;
     r64[c] = r;
     r32[c] = s;
@@ -204,6 +214,59 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 }
 
 // ---------------------------------------------------------------------------
+// Exact tests and scalings on the bits of a double.  GB300 runs FP64 at 1/64
+// of the FP32 rate and the FP64 kernel is bound by its FP64 pipe, so sign,
+// zero and order tests with a known sign, frexp and ldexp are done as
+// integer operations on the representation (the ALU pipe is idle); each
+// gives exactly the IEEE result for the non-NaN operands the path produces.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
+// v > 0
+__device__ __forceinline__ bool gt0(double v) { return bits(v) > 0LL; }
+// v < 0 (-0 is not)
+__device__ __forceinline__ bool lt0(double v)
+{
+    return (unsigned long long)bits(v) > 0x8000000000000000ULL;
+}
+// v == 0 (either sign)
+__device__ __forceinline__ bool eq0(double v) { return (bits(v) << 1) == 0LL; }
+// a > b for b > 0
+__device__ __forceinline__ bool gt_pos(double a, double b) { return bits(a) > bits(b); }
+// |a| < b for b > 0
+__device__ __forceinline__ bool abs_lt(double a, double b) { return (bits(a) & 0x7fffffffffffffffLL) < bits(b); }
+__device__ __forceinline__ bool is_nan(double v)
+{
+    return (bits(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+
+// frexp: u = m 2^e with m in [1/2, 1) (u == 0, inf, NaN: m = u, e = 0)
+__device__ __forceinline__ double frexp_bits(double u, int& e)
+{
+    long long b = bits(u);
+    int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0x7ff || (b << 1) == 0LL) {
+        e = 0;
+        return u;
+    }
+    if (ex == 0) {   // subnormal: scale by 2^54 (exact)
+        b = bits(u * 18014398509481984.0);
+        ex = (int)((b >> 52) & 0x7ff) - 54;
+    }
+    e = ex - 1022;
+    return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | 0x3fe0000000000000LL);
+}
+
+// 2^k as ldexp(1, k) gives it, k in [-2000, 2000]
+__device__ __forceinline__ double pow2i(int k)
+{
+    if (k >= 1024) return CUDART_INF;
+    if (k >= -1022) return __longlong_as_double((long long)(k + 1023) << 52);
+    if (k >= -1074) return __longlong_as_double(1LL << (k + 1074));
+    return 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // log1p and expm1 by argument reduction and series, with IEEE additions,
 // multiplications, divisions and explicit fused multiply-adds in a fixed
 // order (no implicit contraction: this file is built with -fmad=false), so
@@ -217,17 +280,18 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 //     + c / u, with c (below half an ulp of u) times the FP32 reciprocal.
 //   expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
 //     r = w - k ln2 (split), expm1(r) by its Taylor series to r^14 / 14!,
-//     expm1(w) = (2^k - 1) + 2^k expm1(r).
+//     expm1(w) = (2^k - 1) + 2^k expm1(r), 2^k with k limited to
+//     [-2000, 2000] (the same value for every k).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double series_log1p(double x)
 {
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
     const double u = 1.0 + x;
-    const double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
+    const double c = gt_pos(x, 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
     int e;
-    double m = frexp(u, &e);
-    if (m < 0.70710678118654752440) {
+    double m = frexp_bits(u, e);
+    if (bits(m) < bits(0.70710678118654752440)) {   // m >= 0
         m = m * 2.0;
         e = e - 1;
     }
@@ -256,7 +320,7 @@ __device__ __forceinline__ double series_log1p(double x)
 __device__ __forceinline__ double series_expm1(double w)
 {
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double k = (fabs(w) < 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
+    const double k = abs_lt(w, 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
     const double r = (w - k * ln2_hi) - k * ln2_lo;
     double p = 1.0 / 87178291200.0;           // 1/14!
     p = fma(p, r, 1.0 / 6227020800.0);           // 1/13!
@@ -273,8 +337,10 @@ __device__ __forceinline__ double series_expm1(double w)
     p = fma(p, r, 1.0 / 2.0);
     p = fma(p, r, 1.0);
     const double em = r * p;
-    if (k == 0.0) return em;
-    const double t = ldexp(1.0, (int)k);
+    if (eq0(k)) return em;
+    int ki = __double2int_rz(k);   // k is integral; out of range saturates
+    ki = ki > 2000 ? 2000 : (ki < -2000 ? -2000 : ki);
+    const double t = pow2i(ki);
     return (t - 1.0) + t * em;
 }
 
@@ -300,31 +366,39 @@ struct F64Engine {
         double tev;  // next output time or the stop time, whichever is first
     };
 
-    // Exit time along one axis (face = +1, -1, or 0 when no face is reachable).
-    // Written without branches around the divisions and log1p so that the
-    // lanes of a warp stay converged; lanes with no reachable face compute on
-    // harmless operands and select +inf.  The values equal those of the
-    // branchy form (t1 = d / vp, z = A t1, t1 when z == 0 else
-    // t1 * (log1p(z) / z)).
-    __device__ __forceinline__ static double exit_time(double v1, double v2, double A, double D, double vp,
-                                                       double pp, int& face)
+    // Exit time along one axis (face = +1, -1, or 0 when no face is
+    // reachable; v2pos / v1neg: the signs of the face velocities).  Written
+    // without branches around the division and log1p so that the lanes of a
+    // warp stay converged; lanes with no reachable face compute on harmless
+    // operands and select +inf.  The values equal those of the branchy form
+    // (t1 = d / vp, z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
+    __device__ __forceinline__ static double exit_time(double A, double iA, double D, double vp, double pp,
+                                                       bool v2pos, bool v1neg, int& face)
     {
-        const bool up = vp > 0.0 && v2 > 0.0;
-        const bool dn = vp < 0.0 && v1 < 0.0;
+        const bool up = gt0(vp) && v2pos;
+        const bool dn = lt0(vp) && v1neg;
         face = up ? 1 : (dn ? -1 : 0);
         const double d = up ? D - pp : -pp;
         const double t1 = d / (face ? vp : 1.0);
         const double z = A * t1;
-        const bool lin = (z == 0.0) || !face;
-        const double zs = lin ? 1.0 : z;
-        const double g = series_log1p(zs) / zs;
-        const double te = (z == 0.0) ? t1 : t1 * g;
+        const bool lin = eq0(z) || !face;
+        const double te = lin ? t1 : series_log1p(lin ? 0.5 : z) * iA;
         return face ? te : CUDART_INF;
     }
 
-    __device__ __forceinline__ static int face_of(double v1, double v2, double vp)
+    __device__ __forceinline__ static int face_of(double vp, bool v2pos, bool v1neg)
     {
-        return (vp > 0.0 && v2 > 0.0) ? 1 : ((vp < 0.0 && v1 < 0.0) ? -1 : 0);
+        return (gt0(vp) && v2pos) ? 1 : ((lt0(vp) && v1neg) ? -1 : 0);
+    }
+
+    // face-velocity signs of axis a from the cell's nb word
+    __device__ __forceinline__ static bool v1_neg(unsigned long long nb, int a)
+    {
+        return (nb >> (NB_SIGN + 4 * a + 1)) & 1ULL;
+    }
+    __device__ __forceinline__ static bool v2_pos(unsigned long long nb, int a)
+    {
+        return (nb >> (NB_SIGN + 4 * a + 2)) & 1ULL;
     }
 
     template <class T>
@@ -357,19 +431,18 @@ struct F64Engine {
     }
 
     // analytic motion along one axis for a time dt, clamped to the cell
-    // (the same values as: s == 0 -> pp; w == 0 -> factor 1)
-    __device__ __forceinline__ static double move(double A, double D, double vp, double pp, double dt)
+    // (the same values as: s == 0 -> pp; w == 0 -> pp + s; else
+    // pp + (vp * expm1(w)) * (1 / A))
+    __device__ __forceinline__ static double move(double A, double iA, double D, double vp, double pp, double dt)
     {
         const double s = vp * dt;
         const double w = A * dt;
-        const bool lin = (w == 0.0);
-        const double ws = lin ? 1.0 : w;
-        const double e = series_expm1(ws) / ws;
-        const double fct = lin ? 1.0 : e;
-        double pn = pp + s * fct;
-        if (pn < 0.0) pn = 0.0;
-        if (pn > D) pn = D;
-        return (s == 0.0) ? pp : pn;
+        const bool lin = eq0(w);
+        const double em = series_expm1(lin ? 0.5 : w);
+        double pn = lin ? pp + s : pp + (vp * em) * iA;
+        pn = lt0(pn) ? 0.0 : pn;
+        pn = gt_pos(pn, D) ? D : pn;
+        return eq0(s) ? pp : pn;
     }
 
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
@@ -497,13 +570,14 @@ struct F64Engine {
         const int c = Q.c[slot], i = Q.i[slot], j = Q.j[slot], k = Q.k[slot];
         const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
         const double2* rp = reinterpret_cast<const double2*>(f.rec64 + c);
-        const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r3 = __ldg(rp + 3), r4 = __ldg(rp + 4);
-        const double2 r2 = __ldg(rp + 2);
-        const double v1x = r0.x, Ax = r1.x, v1y = r1.y, Ay = r2.y, v1z = r3.x, Az = r4.x;
+        const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
+                      r4 = __ldg(rp + 4);
+        const double v1x = r0.x, Ax = r0.y, iAx = r1.x, v1y = r1.y, Ay = r2.x, iAy = r2.y;
+        const double v1z = r3.x, Az = r3.y, iAz = r4.x;
         const double D0 = __ldg(f.delr + j), D1 = __ldg(f.delc + i), D2 = __ldg(f.dz + k);
-        const double x = __ldg(f.xf + j) + move(Ax, D0, v1x + Ax * p0, p0, tau);
-        const double y = __ldg(f.yf + i) + move(Ay, D1, v1y + Ay * p1, p1, tau);
-        const double z = __ldg(f.zf + k) + move(Az, D2, v1z + Az * p2, p2, tau);
+        const double x = __ldg(f.xf + j) + move(Ax, iAx, D0, v1x + Ax * p0, p0, tau);
+        const double y = __ldg(f.yf + i) + move(Ay, iAy, D1, v1y + Ay * p1, p1, tau);
+        const double z = __ldg(f.zf + k) + move(Az, iAz, D2, v1z + Az * p2, p2, tau);
         store_record(o.ts + (long long)Q.kk[slot] * p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
     }
 
@@ -521,6 +595,7 @@ struct F64Engine {
         int path = P_NONE;
         int m = 0;
         double v1x = 0, Ax = 0, v1y = 0, Ay = 0, v1z = 0, Az = 0, D0 = 1, D1 = 1, D2 = 1;
+        double iAx = 0, iAy = 0, iAz = 0;
         double vp0 = 0, vp1 = 0, vp2 = 0, tmin = 0, t_end = 0;
         int f0 = 0, f1 = 0, f2 = 0, ax = -1;
         unsigned long long nb = 0;
@@ -536,18 +611,20 @@ struct F64Engine {
                               r4 = __ldg(rp + 4);
                 const float4* rf = reinterpret_cast<const float4*>(rp + 5);
                 const float4 g0 = __ldg(rf + 0), g1 = __ldg(rf + 1), g2 = __ldg(rf + 2);
-                v1x = r0.x; Ax = r1.x; v1y = r1.y; Ay = r2.y; v1z = r3.x; Az = r4.x;
-                const double v2x = r0.y, v2y = r2.x, v2z = r3.y;
+                v1x = r0.x; Ax = r0.y; iAx = r1.x; v1y = r1.y; Ay = r2.x; iAy = r2.y;
+                v1z = r3.x; Az = r3.y; iAz = r4.x;
                 nb = (unsigned long long)__double_as_longlong(r4.y);
+                const bool p2x = v2_pos(nb, 0), p2y = v2_pos(nb, 1), p2z = v2_pos(nb, 2);
+                const bool n1x = v1_neg(nb, 0), n1y = v1_neg(nb, 1), n1z = v1_neg(nb, 2);
                 D0 = __ldg(f.delr + s.j); D1 = __ldg(f.delc + s.i); D2 = __ldg(f.dz + s.k);
                 vp0 = v1x + Ax * s.x0;
                 vp1 = v1y + Ay * s.x1;
                 vp2 = v1z + Az * s.x2;
                 // reachable faces (the same tests as exit_time) and FP32
                 // estimates of the three exit times
-                f0 = face_of(v1x, v2x, vp0);
-                f1 = face_of(v1y, v2y, vp1);
-                f2 = face_of(v1z, v2z, vp2);
+                f0 = face_of(vp0, p2x, n1x);
+                f1 = face_of(vp1, p2y, n1y);
+                f2 = face_of(vp2, p2z, n1z);
                 bool u0, u1, u2;
                 const float e0 = estimate(f0, f0 > 0 ? D0 - s.x0 : -s.x0, vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
                 const float e1 = estimate(f1, f1 > 0 ? D1 - s.x1 : -s.x1, vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
@@ -569,18 +646,18 @@ struct F64Engine {
                     // the exact FP64 exit time of the leading candidate (one
                     // evaluation per lane, uniform across the warp)
                     int fa;
-                    const double te = exit_time(sel3(a0, v1x, v1y, v1z), sel3(a0, v2x, v2y, v2z), sel3(a0, Ax, Ay, Az),
-                                                sel3(a0, D0, D1, D2), sel3(a0, vp0, vp1, vp2),
-                                                sel3(a0, s.x0, s.x1, s.x2), fa);
+                    const double te = exit_time(sel3(a0, Ax, Ay, Az), sel3(a0, iAx, iAy, iAz), sel3(a0, D0, D1, D2),
+                                                sel3(a0, vp0, vp1, vp2), sel3(a0, s.x0, s.x1, s.x2),
+                                                sel3(a0, p2x, p2y, p2z), sel3(a0, n1x, n1y, n1z), fa);
                     tmin = te;
                     ax = a0;
-                    if ((cand & ~(1u << a0)) || !(te == te)) {
+                    if ((cand & ~(1u << a0)) || is_nan(te)) {
                         // close call (or an unusable value): every reachable
                         // axis exactly, in axis order, smallest wins
                         int fx;
-                        const double t0 = exit_time(v1x, v2x, Ax, D0, vp0, s.x0, fx);
-                        const double t1 = exit_time(v1y, v2y, Ay, D1, vp1, s.x1, fx);
-                        const double t2 = exit_time(v1z, v2z, Az, D2, vp2, s.x2, fx);
+                        const double t0 = exit_time(Ax, iAx, D0, vp0, s.x0, p2x, n1x, fx);
+                        const double t1 = exit_time(Ay, iAy, D1, vp1, s.x1, p2y, n1y, fx);
+                        const double t2 = exit_time(Az, iAz, D2, vp2, s.x2, p2z, n1z, fx);
                         tmin = CUDART_INF;
                         ax = -1;
                         if (f0 != 0 && t0 < tmin) { tmin = t0; ax = 0; }
@@ -620,9 +697,9 @@ struct F64Engine {
         }
         if (path == P_TIME) {
             const double dt = p.t_stop - s.t;
-            s.x0 = move(Ax, D0, vp0, s.x0, dt);
-            s.x1 = move(Ay, D1, vp1, s.x1, dt);
-            s.x2 = move(Az, D2, vp2, s.x2, dt);
+            s.x0 = move(Ax, iAx, D0, vp0, s.x0, dt);
+            s.x1 = move(Ay, iAy, D1, vp1, s.x1, dt);
+            s.x2 = move(Az, iAz, D2, vp2, s.x2, dt);
             s.t = p.t_stop;
             s.st = MP_ST_TIME;
             return;
@@ -632,10 +709,10 @@ struct F64Engine {
         // the exit axis is put on its face
         const double dt = tmin;
         const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
-        const double n1 = move(sel3(a1, Ax, Ay, Az), sel3(a1, D0, D1, D2), sel3(a1, vp0, vp1, vp2),
-                               sel3(a1, s.x0, s.x1, s.x2), dt);
-        const double n2 = move(sel3(a2, Ax, Ay, Az), sel3(a2, D0, D1, D2), sel3(a2, vp0, vp1, vp2),
-                               sel3(a2, s.x0, s.x1, s.x2), dt);
+        const double n1 = move(sel3(a1, Ax, Ay, Az), sel3(a1, iAx, iAy, iAz), sel3(a1, D0, D1, D2),
+                               sel3(a1, vp0, vp1, vp2), sel3(a1, s.x0, s.x1, s.x2), dt);
+        const double n2 = move(sel3(a2, Ax, Ay, Az), sel3(a2, iAx, iAy, iAz), sel3(a2, D0, D1, D2),
+                               sel3(a2, vp0, vp1, vp2), sel3(a2, s.x0, s.x1, s.x2), dt);
         const int face = ax == 0 ? f0 : (ax == 1 ? f1 : f2);
         const double Dax = ax == 0 ? D0 : (ax == 1 ? D1 : D2);
         const double onface = face > 0 ? Dax : 0.0;

@@ -1,16 +1,19 @@
 // mp_internal.h - device-side layouts and kernel launchers of libmp.
 //
 // Field layout in HBM (built once by mp_field_load):
-//   rec64[c]  128 B {v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az, nb, FP32 copies}:
-//             the FP64 face velocities v = Q / (n * area) and gradients
-//             A = (v2 - v1) / D of Pollock (1988), one line per cell-step.
+//   rec64[c]  128 B {v1x, Ax, iAx, v1y, Ay, iAy, v1z, Az, iAz, nb, FP32 copies}:
+//             the FP64 low-face velocities v1 = Q1 / (n * area), gradients
+//             A = (v2 - v1) / D of Pollock (1988) and iA = 1 / A (0 when
+//             A == 0), one line per cell-step; the FP64 path needs only the
+//             signs of v1 and v2 beyond these, kept as bits of nb.
 //   rec32[c]  32 B  {u1x, u2x, u1y, u2y, u1z, u2z, nb, pad}: the same
 //             velocities divided by the cell size (units 1/s) in FP32 for
 //             the mixed-precision path, which works in local fractions
 //             xi in [0, 1]; one 32-byte sector per cell-step.
 //   nb        2 bits per face (x-, x+, y-, y+, z-, z+): the class of the
 //             neighbour across it (0 active, 1 sink, 2 inactive or constant
-//             head, 3 outside the grid), so crossing needs no second gather.
+//             head, 3 outside the grid), so crossing needs no second gather;
+//             bits 16 + 4a .. 19 + 4a (axis a): v1 > 0, v1 < 0, v2 > 0, v2 < 0.
 //   delr/delc/dz and face coordinates xf/yf/zf (n+1 entries each, FP64).
 // Particle state (group) in SoA: cell int32, px/py/pz/t FP64, status u8.
 #pragma once
@@ -24,8 +27,10 @@ namespace mp {
 
 enum : int { NB_ACTIVE = 0, NB_SINK = 1, NB_BOUNDARY = 2, NB_OUTSIDE = 3 };
 
+enum : int { NB_SIGN = 16 };   // first face-velocity sign bit of nb
+
 struct __align__(16) CellF64 {
-    double v1x, v2x, Ax, v1y, v2y, Ay, v1z, v2z, Az;
+    double v1x, Ax, iAx, v1y, Ay, iAy, v1z, Az, iAz;
     unsigned long long nb;
     // FP32 copies of the same values, for screening the exit axis
     float fv1x, fv2x, fAx, fv1y, fv2y, fAy, fv1z, fv2z, fAz;
