@@ -98,6 +98,7 @@ extern "C" {
 typedef struct mp_ctx mp_ctx;
 typedef struct mp_field mp_field;
 typedef struct mp_group mp_group;
+typedef struct mp_graph mp_graph;
 typedef int64_t mp_req;
 
 /* Flow field.  delr/delc/dz are always host arrays; qx..ibound are host
@@ -310,6 +311,35 @@ int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample
 /* Install a launch configuration (e.g. one cached from an earlier run) for
  * (field, precision, timeseries). */
 int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t timeseries, const mp_tuning* t);
+
+/* Captured batches (the batching pattern's CUDA graphs; the paper's many
+ * particle groups, Conclusions).  n_reqs box-release requests on one field
+ * (rel[i], kind MP_RELEASE_BOX) with their options (opts[i]; no
+ * MP_TRACK_UPDATE_GROUP) become one CUDA graph: clear the counters, release
+ * every group in one launch, track them in one batched launch per
+ * precision.  Group state and outputs are allocated here, once; every
+ * mp_graph_launch re-releases and re-tracks into them (one graph launch on
+ * the stream instead of a host-side launch sequence).  The launch
+ * configuration is fixed at capture (MP_SCHED_AUTO takes the tuned one).
+ * Results are the same as mp_release_group + mp_track_batch with the same
+ * descriptors.  Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release_desc* rel,
+                    const mp_track_opts* opts, void* stream, mp_graph** out);
+/* Replace request i's box, seed and id offset for later launches (the
+ * particle count is fixed: MP_ERR_SHAPE otherwise).  Ordered after earlier
+ * work on `stream`; returns once the descriptor is on the device. */
+int mp_graph_set_release(mp_graph* g, int i, const mp_release_desc* rel, void* stream);
+/* Replay the graph on `stream` (asynchronous).  Outputs of the previous
+ * launch are overwritten: read them first (stream order). */
+int mp_graph_launch(mp_graph* g, void* stream);
+/* The request ids (n_reqs of them) through which a launch's outputs are
+ * read with mp_wait, mp_get_endpoints, mp_get_timeseries, mp_get_pathlines
+ * and mp_get_stats (kernel_ms then spans the whole graph).  They belong to
+ * the graph: mp_req_free refuses them, mp_graph_free releases them. */
+int mp_graph_requests(const mp_graph* g, mp_req* ids);
+/* Waits (bounded) for the last launch, then frees everything the graph
+ * holds.  The field must outlive the graph. */
+int mp_graph_free(mp_graph* g);
 
 /* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
  * wait is always bounded, and a negative value means 60 s) for a request.

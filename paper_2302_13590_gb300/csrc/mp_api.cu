@@ -67,6 +67,38 @@ int wait_event(cudaEvent_t ev, int64_t timeout_us)
 
 }  // namespace
 
+namespace {
+
+// A group's state arrays in one buffer (256-byte aligned SoA): cell, px,
+// py, pz, t, status, steps, hash, exit face.
+size_t group_bytes(long long n)
+{
+    const size_t u = (size_t)n;
+    const size_t b = align256(4 * u) + 4 * align256(8 * u) + align256(u) + align256(4 * u) + align256(8 * u) +
+                     align256(u);
+    return std::max<size_t>(b, 256);
+}
+
+DevState group_view(char* buf, long long n)
+{
+    const size_t u = (size_t)n;
+    size_t off = 0;
+    auto take = [&](size_t sz) { char* p = buf + off; off += align256(sz); return p; };
+    DevState d{};
+    d.cell = reinterpret_cast<int32_t*>(take(4 * u));
+    d.px = reinterpret_cast<double*>(take(8 * u));
+    d.py = reinterpret_cast<double*>(take(8 * u));
+    d.pz = reinterpret_cast<double*>(take(8 * u));
+    d.t = reinterpret_cast<double*>(take(8 * u));
+    d.status = reinterpret_cast<uint8_t*>(take(u));
+    d.steps = reinterpret_cast<uint32_t*>(take(4 * u));
+    d.hash = reinterpret_cast<unsigned long long*>(take(8 * u));
+    d.exit_face = reinterpret_cast<uint8_t*>(take(u));
+    return d;
+}
+
+}  // namespace
+
 struct mp_field {
     mp_ctx* ctx = nullptr;
     DevField d{};
@@ -96,6 +128,7 @@ struct Request {
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t k0 = nullptr, k1 = nullptr;
+    bool graph_owned = false;   // outputs of a captured graph: freed with it, events shared
 };
 
 struct TuneKey {
@@ -117,6 +150,7 @@ struct mp_ctx {
     std::map<int64_t, Request*> reqs;
     std::set<mp_field*> fields;
     std::set<mp_group*> groups;
+    std::set<mp_graph*> graphs;
     int64_t next_id = 1;
 };
 
@@ -186,6 +220,8 @@ int mp_ctx_destroy(mp_ctx* ctx)
 {
     if (!ctx) return fail(MP_ERR_INVALID_ARG, "mp_ctx_destroy: NULL");
     cudaSetDevice(ctx->device);
+    std::vector<mp_graph*> grs(ctx->graphs.begin(), ctx->graphs.end());
+    for (mp_graph* g : grs) mp_graph_free(g);
     std::vector<mp_req> ids;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -390,17 +426,7 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     }
     MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    size_t off = 0;
-    const size_t o_cell = off; off = align256(off + 4 * (size_t)n);
-    const size_t o_px = off; off = align256(off + 8 * (size_t)n);
-    const size_t o_py = off; off = align256(off + 8 * (size_t)n);
-    const size_t o_pz = off; off = align256(off + 8 * (size_t)n);
-    const size_t o_t = off; off = align256(off + 8 * (size_t)n);
-    const size_t o_st = off; off = align256(off + (size_t)n);
-    const size_t o_steps = off; off = align256(off + 4 * (size_t)n);
-    const size_t o_hash = off; off = align256(off + 8 * (size_t)n);
-    const size_t o_face = off; off = align256(off + (size_t)n);
-    const size_t bytes = std::max<size_t>(off, 256);
+    const size_t bytes = group_bytes(n);
     char* buf = nullptr;
     if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
         cudaGetLastError();
@@ -413,15 +439,7 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     g->buf = buf;
     g->bytes = bytes;
     g->stream = s;
-    g->d.cell = reinterpret_cast<int32_t*>(buf + o_cell);
-    g->d.px = reinterpret_cast<double*>(buf + o_px);
-    g->d.py = reinterpret_cast<double*>(buf + o_py);
-    g->d.pz = reinterpret_cast<double*>(buf + o_pz);
-    g->d.t = reinterpret_cast<double*>(buf + o_t);
-    g->d.status = reinterpret_cast<uint8_t*>(buf + o_st);
-    g->d.steps = reinterpret_cast<uint32_t*>(buf + o_steps);
-    g->d.hash = reinterpret_cast<unsigned long long*>(buf + o_hash);
-    g->d.exit_face = reinterpret_cast<uint8_t*>(buf + o_face);
+    g->d = group_view(buf, n);
     // a fresh particle: no steps yet (hash and exit face are read only after one)
     cudaError_t e = cudaMemsetAsync(g->d.steps, 0, 4 * (size_t)n, s);
     if (e != cudaSuccess) {
@@ -655,8 +673,10 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
 void drop_request(Request* r)
 {
     cudaFreeAsync(r->buf, r->stream);
-    cudaEventDestroy(r->k0);
-    cudaEventDestroy(r->k1);
+    if (!r->graph_owned) {
+        cudaEventDestroy(r->k0);
+        cudaEventDestroy(r->k1);
+    }
     delete r;
 }
 
@@ -1067,6 +1087,7 @@ int mp_req_free(mp_ctx* ctx, mp_req id)
         auto it = ctx->reqs.find(id);
         if (it == ctx->reqs.end()) return fail(MP_ERR_NOT_READY, "mp_req_free: unknown request");
         r = it->second;
+        if (r->graph_owned) return fail(MP_ERR_INVALID_ARG, "mp_req_free: the request belongs to a graph");
         ctx->reqs.erase(it);
     }
     cudaSetDevice(ctx->device);
@@ -1143,6 +1164,257 @@ int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample
         ctx->tuned[TuneKey{g->field, o->precision, (modes & mp::MODE_TS) ? 1 : 0}] = best;
     }
     *out = best;
+    return MP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Captured batches: release + tracking of a fixed set of box-release
+// requests as one CUDA graph, replayed with new release descriptors.
+// ---------------------------------------------------------------------------
+
+struct mp_graph {
+    mp_ctx* ctx = nullptr;
+    const mp_field* field = nullptr;
+    std::vector<mp_group*> groups;          // views into state
+    std::vector<Request*> reqs;
+    std::vector<mp_req> ids;
+    std::vector<mp::BoxRelease> desc;       // host copy of the device descriptors
+    char* state = nullptr;                  // every group's state arrays
+    char* tables = nullptr;                 // descriptors, starts, batch tables, queues
+    mp::BoxRelease* d_desc = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;
+};
+
+namespace {
+
+int graph_release_check(const mp_release_desc& r)
+{
+    if (r.kind != MP_RELEASE_BOX) return fail(MP_ERR_INVALID_ARG, "mp_graph: only box releases can be captured");
+    if (r.n < 0) return fail(MP_ERR_INVALID_ARG, "mp_graph: n < 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(r.lo[a]) || !std::isfinite(r.hi[a]) || r.hi[a] < r.lo[a])
+            return fail(MP_ERR_INVALID_ARG, "mp_graph: box must be finite with lo <= hi");
+    return MP_OK;
+}
+
+void graph_destroy(mp_graph* G)
+{
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    for (Request* r : G->reqs) drop_request(r);
+    for (mp_group* g : G->groups) delete g;
+    if (G->state) cudaFree(G->state);
+    if (G->tables) cudaFree(G->tables);
+    if (G->k0) cudaEventDestroy(G->k0);
+    if (G->k1) cudaEventDestroy(G->k1);
+    delete G;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release_desc* rel,
+                    const mp_track_opts* opts, void* stream, mp_graph** out)
+{
+    if (!ctx || !f || !rel || !opts || !out || n_reqs < 1) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: bad argument");
+    if (f->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: field of another context");
+    for (int i = 0; i < n_reqs; ++i) {
+        const int rc = graph_release_check(rel[i]);
+        if (rc != MP_OK) return rc;
+        if (opts[i].flags & MP_TRACK_UPDATE_GROUP)
+            return fail(MP_ERR_INVALID_ARG, "mp_graph_create: a replayed release makes MP_TRACK_UPDATE_GROUP moot");
+    }
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    mp_graph* G = new mp_graph();
+    G->ctx = ctx;
+    G->field = f;
+    auto bail = [&](int rc) { cudaStreamSynchronize(s); graph_destroy(G); return rc; };
+    // group state of every request in one allocation
+    std::vector<size_t> goff((size_t)n_reqs + 1, 0);
+    for (int i = 0; i < n_reqs; ++i) goff[i + 1] = goff[i] + align256(group_bytes(rel[i].n));
+    if (cudaMalloc(&G->state, goff[n_reqs]) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(MP_ERR_OOM, "mp_graph_create: device allocation failed"));
+    }
+    std::vector<long long> starts((size_t)n_reqs + 1, 0);
+    std::vector<mp::Req> hr((size_t)n_reqs);
+    std::vector<unsigned> md((size_t)n_reqs, 0);
+    for (int i = 0; i < n_reqs; ++i) {
+        mp_group* g = new mp_group();
+        g->ctx = ctx;
+        g->field = f;
+        g->n = rel[i].n;
+        g->buf = G->state + goff[i];
+        g->bytes = group_bytes(rel[i].n);
+        g->stream = s;
+        g->d = group_view(G->state + goff[i], rel[i].n);
+        G->groups.push_back(g);
+        Request* r = nullptr;
+        const int rc = prepare_request(ctx, g, &opts[i], s, &r, &hr[i], &md[i]);
+        if (rc != MP_OK) return bail(rc);
+        r->graph_owned = true;
+        cudaEventDestroy(r->k0);
+        cudaEventDestroy(r->k1);
+        r->k0 = r->k1 = nullptr;
+        G->reqs.push_back(r);
+        starts[i + 1] = starts[i] + rel[i].n;
+        mp::BoxRelease b{};
+        b.st = g->d;
+        b.n = rel[i].n;
+        for (int a = 0; a < 3; ++a) { b.lo[a] = rel[i].lo[a]; b.hi[a] = rel[i].hi[a]; }
+        b.seed = rel[i].seed;
+        b.id_offset = rel[i].id_offset;
+        G->desc.push_back(b);
+    }
+    if (cudaEventCreate(&G->k0) != cudaSuccess || cudaEventCreate(&G->k1) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "mp_graph_create: events"));
+    for (Request* r : G->reqs) { r->k0 = G->k0; r->k1 = G->k1; }
+    // device tables: release descriptors and starts, then per precision the
+    // tracking batch (request table, its starts, queue head)
+    std::vector<int> sel[2];
+    for (int i = 0; i < n_reqs; ++i) sel[opts[i].precision == MP_PREC_FP64 ? 0 : 1].push_back(i);
+    size_t off = 0;
+    const size_t o_desc = off; off = align256(off + sizeof(mp::BoxRelease) * (size_t)n_reqs);
+    const size_t o_st = off; off = align256(off + sizeof(long long) * ((size_t)n_reqs + 1));
+    size_t o_req[2], o_bst[2], o_q[2];
+    for (int p = 0; p < 2; ++p) {
+        o_req[p] = off; off = align256(off + sizeof(mp::Req) * sel[p].size());
+        o_bst[p] = off; off = align256(off + sizeof(long long) * (sel[p].size() + 1));
+        o_q[p] = off; off = align256(off + sizeof(unsigned long long));
+    }
+    if (cudaMalloc(&G->tables, off) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(MP_ERR_OOM, "mp_graph_create: device allocation failed"));
+    }
+    G->d_desc = reinterpret_cast<mp::BoxRelease*>(G->tables + o_desc);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(G->d_desc, G->desc.data(), sizeof(mp::BoxRelease) * (size_t)n_reqs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(G->tables + o_st, starts.data(), sizeof(long long) * ((size_t)n_reqs + 1),
+                       cudaMemcpyHostToDevice);
+    mp::Batch bat[2]{};
+    unsigned modes[2] = {0u, 0u};
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        std::vector<mp::Req> rq;
+        std::vector<long long> bs(1, 0);
+        for (int i : sel[p]) {
+            rq.push_back(hr[i]);
+            bs.push_back(bs.back() + rel[i].n);
+            modes[p] |= md[i];
+        }
+        if (!rq.empty())
+            e = cudaMemcpy(G->tables + o_req[p], rq.data(), sizeof(mp::Req) * rq.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !rq.empty())
+            e = cudaMemcpy(G->tables + o_bst[p], bs.data(), sizeof(long long) * bs.size(), cudaMemcpyHostToDevice);
+        bat[p].reqs = reinterpret_cast<const mp::Req*>(G->tables + o_req[p]);
+        bat[p].starts = reinterpret_cast<const long long*>(G->tables + o_bst[p]);
+        bat[p].n_reqs = (int)sel[p].size();
+        bat[p].n_total = bs.back();
+        bat[p].queue = reinterpret_cast<unsigned long long*>(G->tables + o_q[p]);
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "mp_graph_create: tables"));
+    // capture: clear counters and queue heads, release, track
+    const mp::DevField& fd = *mp::field_device_view(f);
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "mp_graph_create: stream"));
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    for (Request* r : G->reqs)
+        if (e == cudaSuccess) e = cudaMemsetAsync(r->d.counters, 0, sizeof(unsigned long long) * N_COUNTERS, cs);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+        if (!sel[p].empty()) e = cudaMemsetAsync(bat[p].queue, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess)
+        e = mp::launch_release_boxes(fd, G->d_desc, reinterpret_cast<const long long*>(G->tables + o_st), n_reqs,
+                                     starts[n_reqs], cs);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+        if (sel[p].empty()) continue;
+        const int prec = p == 0 ? MP_PREC_FP64 : MP_PREC_MIXED;
+        int sched = 0, blk = 0, spf = 0;
+        resolve_launch(ctx, f, prec, (modes[p] & mp::MODE_TS) != 0, opts[sel[p][0]], &sched, &blk, &spf);
+        bat[p].steps_per_fetch = spf > 0 ? spf : 4;
+        e = prec == MP_PREC_FP64 ? mp::launch_track_fp64(fd, bat[p], modes[p], sched, blk > 0 ? blk : 128, 0, cs)
+                                 : mp::launch_track_mixed(fd, bat[p], modes[p], sched, blk > 0 ? blk : 128, 0, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    G->graph = graph;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "mp_graph_create: capture"));
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (Request* r : G->reqs) {
+            const int64_t id = ctx->next_id++;
+            ctx->reqs[id] = r;
+            G->ids.push_back(id);
+        }
+        ctx->graphs.insert(G);
+    }
+    *out = G;
+    return MP_OK;
+}
+
+int mp_graph_set_release(mp_graph* G, int i, const mp_release_desc* rel, void* stream)
+{
+    if (!G || !rel || i < 0 || i >= (int)G->desc.size()) return fail(MP_ERR_INVALID_ARG, "mp_graph_set_release: bad argument");
+    int rc = graph_release_check(*rel);
+    if (rc != MP_OK) return rc;
+    if (rel->n != G->desc[i].n) return fail(MP_ERR_SHAPE, "mp_graph_set_release: the particle count is fixed");
+    MP_CUDA(cudaSetDevice(G->ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    mp::BoxRelease& b = G->desc[i];
+    for (int a = 0; a < 3; ++a) { b.lo[a] = rel->lo[a]; b.hi[a] = rel->hi[a]; }
+    b.seed = rel->seed;
+    b.id_offset = rel->id_offset;
+    // ordered after earlier work on the stream; synchronous so that the host
+    // copy may change again at once
+    cudaError_t e = cudaMemcpyAsync(G->d_desc + i, &b, sizeof(mp::BoxRelease), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_graph_set_release");
+    return MP_OK;
+}
+
+int mp_graph_launch(mp_graph* G, void* stream)
+{
+    if (!G) return fail(MP_ERR_INVALID_ARG, "mp_graph_launch: NULL");
+    MP_CUDA(cudaSetDevice(G->ctx->device), "cudaSetDevice");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(G->k0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(G->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(G->k1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_graph_launch");
+    for (Request* r : G->reqs) r->stream = s;
+    return MP_OK;
+}
+
+int mp_graph_requests(const mp_graph* G, mp_req* ids)
+{
+    if (!G || !ids) return fail(MP_ERR_INVALID_ARG, "mp_graph_requests: NULL");
+    for (size_t i = 0; i < G->ids.size(); ++i) ids[i] = G->ids[i];
+    return MP_OK;
+}
+
+int mp_graph_free(mp_graph* G)
+{
+    if (!G) return fail(MP_ERR_INVALID_ARG, "mp_graph_free: NULL");
+    mp_ctx* ctx = G->ctx;
+    cudaSetDevice(ctx->device);
+    int rc = wait_event(G->k1, -1);
+    if (rc != MP_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (mp_req id : G->ids) ctx->reqs.erase(id);
+        ctx->graphs.erase(G);
+    }
+    graph_destroy(G);
     return MP_OK;
 }
 

@@ -143,11 +143,11 @@ __device__ __forceinline__ uint8_t release_status(const DevField& f, long long c
 
 struct Box { double lo[3], hi[3]; };
 
-__global__ void k_release_box(DevField f, DevState st, long long n, Box b, unsigned long long seed,
-                              unsigned long long off)
+// one particle of a box release: Philox counters (id, 0) and (id, 1) under
+// the key `seed`, three 53-bit uniforms, the cell holding the point
+__device__ __forceinline__ void release_one(const DevField& f, const DevState& st, long long q, const Box& b,
+                                            unsigned long long seed, unsigned long long off)
 {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
     const unsigned long long id = (unsigned long long)q + off;
     const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     const uint4 r = philox4x32_10(make_uint4((unsigned)id, (unsigned)(id >> 32), 0u, 0u), key);
@@ -158,6 +158,7 @@ __global__ void k_release_box(DevField f, DevState st, long long n, Box b, unsig
     const double gz = b.lo[2] + uz * (b.hi[2] - b.lo[2]);
     const int j = locate(f.xf, f.ncol, gx), i = locate(f.yf, f.nrow, gy), k = locate(f.zf, f.nlay, gz);
     st.t[q] = 0.0;
+    if (st.steps) st.steps[q] = 0u;
     if (j < 0 || i < 0 || k < 0) {
         st.cell[q] = -1; st.px[q] = 0.0; st.py[q] = 0.0; st.pz[q] = 0.0;
         st.status[q] = MP_ST_INVALID_RELEASE;
@@ -171,6 +172,42 @@ __global__ void k_release_box(DevField f, DevState st, long long n, Box b, unsig
     st.cell[q] = (int32_t)c;
     st.px[q] = ox; st.py[q] = oy; st.pz[q] = oz;
     st.status[q] = release_status(f, c);
+}
+
+__global__ void k_release_box(DevField f, DevState st, long long n, Box b, unsigned long long seed,
+                              unsigned long long off)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    release_one(f, st, q, b, seed, off);
+}
+
+// Box releases of several groups in one launch: one index space over all
+// of them (starts = prefix sums of the group sizes), the descriptors read
+// from device memory, so a captured graph releases whatever they hold.
+__global__ void k_release_boxes(DevField f, const BoxRelease* d, const long long* starts, int n_reqs,
+                                long long n_total)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_total) return;
+    int lo = 0, hi = n_reqs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const BoxRelease& r = d[lo];
+    Box b;
+    for (int a = 0; a < 3; ++a) { b.lo[a] = r.lo[a]; b.hi[a] = r.hi[a]; }
+    release_one(f, r.st, g - starts[lo], b, r.seed, r.id_offset);
+}
+
+cudaError_t launch_release_boxes(const DevField& f, const BoxRelease* d, const long long* starts, int n_reqs,
+                                 long long n_total, cudaStream_t s)
+{
+    if (n_total <= 0) return cudaSuccess;
+    k_release_boxes<<<(unsigned)((n_total + 255) / 256), 256, 0, s>>>(f, d, starts, n_reqs, n_total);
+    return cudaGetLastError();
 }
 
 __global__ void k_release_explicit(DevField f, DevState st, long long n, const int32_t* cell,

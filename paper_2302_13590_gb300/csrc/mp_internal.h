@@ -178,6 +178,16 @@ inline void split_ff(double v, float& hi, float& lo)
 cudaError_t launch_validate(const double* qx, long long nqx, const double* qy, long long nqy, const double* qz,
                             long long nqz, const double* por, const int8_t* ib, long long ncell, unsigned* flags,
                             cudaStream_t s);
+// one group's box release, as a device descriptor (graph replays read it)
+struct BoxRelease {
+    DevState st;
+    long long n;
+    double lo[3], hi[3];
+    unsigned long long seed, id_offset;
+};
+
+cudaError_t launch_release_boxes(const DevField& f, const BoxRelease* d, const long long* starts, int n_reqs,
+                                 long long n_total, cudaStream_t s);
 cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, const double* qx,
                                  const double* qy, const double* qz, const double* por, cudaStream_t s);
 cudaError_t launch_release_box(const DevField& f, const DevState& st, long long n, const double lo[3],

@@ -126,6 +126,11 @@ SIGNATURES = {
     "mp_autotune": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), ctypes.c_int64, _vp, _P(Tuning)]),
     "mp_set_tuning": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning)]),
     "mp_group_set_field": (ctypes.c_int, [_vp, _vp]),
+    "mp_graph_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(ReleaseDesc), _P(TrackOpts), _vp, _P(_vp)]),
+    "mp_graph_set_release": (ctypes.c_int, [_vp, ctypes.c_int, _P(ReleaseDesc), _vp]),
+    "mp_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "mp_graph_requests": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
+    "mp_graph_free": (ctypes.c_int, [_vp]),
     "mp_get_pathlines": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _P(ctypes.c_int64), ctypes.c_uint32,
                                         _vp]),
     "mp_track_periods": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(_vp), _vp, _P(TrackOpts), _vp,
@@ -253,6 +258,37 @@ def mp_release_group(ctx, fh, *, n=None, lo=None, hi=None, seed=0, id_offset=0, 
     h = ctypes.c_void_p()
     _check(load_library().mp_release_group(ctx, fh, ctypes.byref(d), _stream(stream), ctypes.byref(h)))
     return h
+
+
+def _box_desc(n, lo, hi, seed=0, id_offset=0) -> ReleaseDesc:
+    return ReleaseDesc(int(n), RELEASE_BOX, 0, None, None, None, (ctypes.c_double * 3)(*map(float, lo)),
+                       (ctypes.c_double * 3)(*map(float, hi)), int(seed) & (2 ** 64 - 1), int(id_offset))
+
+
+def mp_graph_create(ctx, fh, releases, opts_list, stream=None):
+    """Capture box releases (objects with n, lo, hi, seed, id_offset) and
+    their tracking as one CUDA graph; returns (handle, request ids)."""
+    n = len(releases)
+    rel = (ReleaseDesc * n)(*[_box_desc(r.n, r.lo, r.hi, r.seed, getattr(r, "id_offset", 0)) for r in releases])
+    oarr = (TrackOpts * n)(*opts_list)
+    h = ctypes.c_void_p()
+    _check(load_library().mp_graph_create(ctx, fh, n, rel, oarr, _stream(stream), ctypes.byref(h)))
+    ids = (ctypes.c_int64 * n)()
+    _check(load_library().mp_graph_requests(h, ids))
+    return h, [int(v) for v in ids]
+
+
+def mp_graph_set_release(gh, i, n, lo, hi, seed=0, id_offset=0, stream=None):
+    d = _box_desc(n, lo, hi, seed, id_offset)
+    _check(load_library().mp_graph_set_release(gh, int(i), ctypes.byref(d), _stream(stream)))
+
+
+def mp_graph_launch(gh, stream=None):
+    _check(load_library().mp_graph_launch(gh, _stream(stream)))
+
+
+def mp_graph_free(gh):
+    _check(load_library().mp_graph_free(gh))
 
 
 def mp_group_free(gh):
