@@ -439,6 +439,56 @@ def run_ours(args):
                     best = {"cell_steps_per_s": steps_b / (kms / 1e3), "kernel_ms": kms, "cell_steps": steps_b,
                             "particles": int(sum(x.release.n for x in specs))}
             batch[name] = best
+        # the same kind of batch captured once as a CUDA graph (one batched
+        # release, one tracking launch per precision) and replayed, against
+        # the host-side sequence (a release per group, the batch table, the
+        # tracking launch); wall time per batch, host included
+        def wall_ms(fn, reps):
+            fn()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            return (time.perf_counter() - t0) / reps * 1e3
+
+        rng = np.random.default_rng(7)
+        Lx, Ly, Lz = w.field.extent
+        small = []
+        for i in range(256):
+            nn = int(np.exp(rng.uniform(np.log(200), np.log(2000))))
+            lo = np.array([rng.uniform(0, 0.5 * Lx), rng.uniform(0, 0.5 * Ly), 0.0])
+            small.append(I.Release(nn, tuple(lo), tuple(lo + [0.1 * Lx, 0.1 * Ly, Lz]), seed=500 + i))
+        graph = {}
+        for key, rels, optf, reps in (
+                ("small", small, lambda x: mp.make_opts(precision=mp.PREC_MIXED), 20),
+                ("batch_workload_mixed", [x.release for x in specs],
+                 lambda x: mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
+                                        precision=mp.PREC_MIXED, times=x.times), 3)):
+            opts = [optf(x) for x in (specs if key != "small" else rels)]
+
+            def direct():
+                groups = [mp.mp_release_group(ctx.h, fh, n=r.n, lo=r.lo, hi=r.hi, seed=r.seed, stream=stream)
+                          for r in rels]
+                ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
+                stream.synchronize()
+                for i in ids:
+                    mp.mp_req_free(ctx.h, i)
+                for g in groups:
+                    mp.mp_group_free(g)
+
+            gh, gids = mp.mp_graph_create(ctx.h, fh, rels, opts, stream=stream)
+
+            def replay():
+                mp.mp_graph_launch(gh, stream=stream)
+                stream.synchronize()
+
+            d_ms, g_ms = wall_ms(direct, reps), wall_ms(replay, reps)
+            steps_g = sum(mp.mp_get_stats(ctx.h, i)["cell_steps"] for i in gids)
+            mp.mp_graph_free(gh)
+            graph[key] = {"requests": len(rels), "particles": int(sum(r.n for r in rels)), "direct_ms": d_ms,
+                          "graph_ms": g_ms, "graph_cell_steps_per_s": steps_g / (g_ms / 1e3)}
+        graph["small"]["workload"] = ("256 requests of 200..2000 particles (log-uniform) in random boxes, mixed "
+                                      "precision, endpoint mode")
+        batch["graph"] = graph
 
     serving = None
     if not args.no_serve:
