@@ -7,9 +7,13 @@
 //   u_p = u1 + A xi, A = u2 - u1, exit distance d = 1 - xi or -xi,
 //   t_a = (d / u_p) g(z), z = A d / u_p, g(z) = ln(1 + z) / z,
 //   xi(t) = xi + u_p t h(A t), h(w) = (e^w - 1) / w.
-// g and h use their Taylor series for |z|, |w| < 2^-7 (exact to below FP32
-// rounding there, and free of the 0/0 at z = 0); for z < -1/2 g takes
-// ln(u_exit / u_p) / z, which keeps full FP32 accuracy as u_exit -> 0.
+// g and h are evaluated both ways and selected (no divergent branch): their
+// Taylor series near 0 (|z| < 1/8, |w| < 1/2; free of the 0/0 at 0),
+// otherwise logf and expf (about 1 ulp, and free of the internal branches
+// of log1pf and expm1f): g = ln(u) / (u - 1) with u = fl(1 + z), exact to a
+// few ulp because the rounding of 1 + z cancels (Goldberg 1991), or
+// ln(u_exit / u_p) / z for z < -1/2, where the ratio, not 1 + z, keeps full
+// FP32 accuracy as u_exit -> 0.
 //
 // The cumulative travel time is carried as an unevaluated pair of FP32
 // values (a double-float number, 48-bit significand): each step adds its
@@ -71,21 +75,40 @@ struct MixEngine {
         return __ldg(o.times_ff + kk);
     }
 
-    static constexpr float SMALL = 0.0078125f;  // 2^-7
+    static constexpr float SMALL = 0.125f;
 
-    // g(z) = ln(1 + z) / z, with 1 + z = u_exit / u_p.  Near z = -1 (exit
-    // face almost stagnant) 1 + z cancels in FP32, so the ratio of the two
-    // stored velocities is logged directly there.
+    // g(z) = ln(1 + z) / z, with 1 + z = u_exit / u_p: the series
+    // sum_k (-z)^k / (k + 1) to degree 7 for |z| < 1/8; otherwise
+    // ln(u) / (u - 1) with u = fl(1 + z), in which the rounding of 1 + z
+    // cancels (Goldberg 1991), and for z < -1/2, where 1 + z itself
+    // cancels, the logarithm of the ratio of the two stored velocities
     __device__ __forceinline__ static float g_log1p_over(float z, float ratio)
     {
-        if (fabsf(z) < SMALL) return 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
-        if (z < -0.5f) return __fdividef(logf(ratio), z);
-        return __fdividef(log1pf(z), z);
+        const float ser =
+            1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * (0.2f + z * (-1.0f / 6.0f +
+                                                                                  z * (1.0f / 7.0f + z * -0.125f))))));
+        const bool near_m1 = z < -0.5f;
+        const float u = 1.0f + z;
+        const float L = logf(near_m1 ? ratio : u);
+        const float lg = __fdividef(L, near_m1 ? z : u - 1.0f);
+        return fabsf(z) < SMALL ? ser : lg;
     }
+    // h(w) = (e^w - 1) / w: sum_k w^k / (k + 1)! to degree 8 for |w| < 1/2
+    // (truncation below 6e-10), otherwise the exponential (e^w - 1 then
+    // loses at most a factor 2.5 to cancellation)
     __device__ __forceinline__ static float h_expm1_over(float w)
     {
-        if (fabsf(w) < SMALL) return 1.0f + w * (0.5f + w * (1.0f / 6.0f + w * (1.0f / 24.0f + w * (1.0f / 120.0f))));
-        return __fdividef(expm1f(w), w);
+        const float ser =
+            1.0f + w * (0.5f + w * (1.0f / 6.0f + w * (1.0f / 24.0f + w * (1.0f / 120.0f + w * (1.0f / 720.0f +
+                        w * (1.0f / 5040.0f + w * (1.0f / 40320.0f + w * (1.0f / 362880.0f))))))));
+        const float ex = __fdividef(expf(w) - 1.0f, w);
+        return fabsf(w) < 0.5f ? ser : ex;
+    }
+
+    template <class T>
+    __device__ __forceinline__ static T sel3(int a, T x, T y, T z)
+    {
+        return a == 0 ? x : (a == 1 ? y : z);
     }
 
     // exit time along one axis in local units; branch-free around the
@@ -350,14 +373,16 @@ struct MixEngine {
             s.st = MP_ST_TIME;
             return;
         }
+        // the two other axes move by the analytic formula (two slots,
+        // uniform across lanes), the exit axis is put on its face
         const float dt = tmin;
-        const float n0 = move(Ax, up0, s.x0, dt);
-        const float n1 = move(Ay, up1, s.x1, dt);
-        const float n2 = move(Az, up2, s.x2, dt);
+        const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+        const float n1 = move(sel3(a1, Ax, Ay, Az), sel3(a1, up0, up1, up2), sel3(a1, s.x0, s.x1, s.x2), dt);
+        const float n2 = move(sel3(a2, Ax, Ay, Az), sel3(a2, up0, up1, up2), sel3(a2, s.x0, s.x1, s.x2), dt);
         const int face = ax == 0 ? f0 : (ax == 1 ? f1 : f2);
         const float onface = face > 0 ? 1.0f : 0.0f;
-        s.x0 = ax == 0 ? onface : n0;
-        s.x1 = ax == 1 ? onface : n1;
+        s.x0 = ax == 0 ? onface : n1;
+        s.x1 = ax == 1 ? onface : (ax == 0 ? n1 : n2);
         s.x2 = ax == 2 ? onface : n2;
         s.th = nh;
         s.tl = nl;
