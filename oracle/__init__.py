@@ -97,6 +97,10 @@ def _load():
             lib.orc_track.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                       ctypes.POINTER(_Opts), ctypes.POINTER(_Out)]
             lib.orc_track.restype = ctypes.c_int
+            lib.orc_usg_track.argtypes = [ctypes.POINTER(_UsgField)] + lib.orc_track.argtypes[1:]
+            lib.orc_usg_track.restype = ctypes.c_int
+            lib.orc_usg_release_explicit.argtypes = [ctypes.POINTER(_UsgField), ctypes.c_int64] + [vp] * 7
+            lib.orc_usg_release_explicit.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -125,8 +129,35 @@ class OracleField:
                         _ptr(self.porosity), _ptr(self.ibound))
 
 
-def as_oracle_field(f) -> OracleField:
-    return f if isinstance(f, OracleField) else OracleField(f)
+class _UsgField(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
+                                               ("box", "porosity", "ibound", "face_off", "nbr", "q", "rect")]
+
+
+class OracleUsgField:
+    """Contiguous copies of a rectangular unstructured field and its C view."""
+
+    def __init__(self, u):
+        c = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt).reshape(-1))
+        self.ncell = int(np.asarray(u.box).shape[0])
+        self.box = c(u.box, np.float64)
+        self.porosity, self.ibound = c(u.porosity, np.float64), c(u.ibound, np.int8)
+        self.face_off, self.nbr = c(u.face_off, np.int64), c(u.nbr, np.int32)
+        self.q, self.rect = c(u.q, np.float64), c(u.rect, np.float64)
+        assert self.box.size == 6 * self.ncell and self.face_off.size == 6 * self.ncell + 1
+        assert self.rect.size == 4 * self.nbr.size == 4 * self.q.size
+        self.c = _UsgField(self.ncell, *[_ptr(a) for a in (self.box, self.porosity, self.ibound, self.face_off,
+                                                             self.nbr, self.q, self.rect)])
+
+
+def _is_usg(f) -> bool:
+    return isinstance(f, OracleUsgField) or hasattr(f, "face_off")
+
+
+def as_oracle_field(f):
+    if isinstance(f, (OracleField, OracleUsgField)):
+        return f
+    return OracleUsgField(f) if _is_usg(f) else OracleField(f)
 
 
 def philox4x32_10(ctr, key):
@@ -189,8 +220,9 @@ def release_explicit(f, cells, frac):
     n = cells.size
     st = dict(cell=np.zeros(n, np.int32), px=np.zeros(n), py=np.zeros(n), pz=np.zeros(n),
               status=np.zeros(n, np.uint8))
-    lib.orc_release_explicit(ctypes.byref(of.c), n, _ptr(cells), _ptr(frac), _ptr(st["cell"]),
-                             _ptr(st["px"]), _ptr(st["py"]), _ptr(st["pz"]), _ptr(st["status"]))
+    rel = lib.orc_usg_release_explicit if isinstance(of, OracleUsgField) else lib.orc_release_explicit
+    rel(ctypes.byref(of.c), n, _ptr(cells), _ptr(frac), _ptr(st["cell"]), _ptr(st["px"]), _ptr(st["py"]),
+        _ptr(st["pz"]), _ptr(st["status"]))
     st["t"] = np.zeros(n)
     return st
 
@@ -243,8 +275,9 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
         path_n = np.zeros(1, np.int64)
         out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_[:17]], _ptr(path) if pathline else None, cap,
                    _ptr(path_n))
-        rc = lib.orc_track(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
-                           _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
+        fn = lib.orc_usg_track if isinstance(of, OracleUsgField) else lib.orc_track
+        rc = fn(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
+                _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
         if rc != 0:
             raise RuntimeError("orc_track failed")
         if not pathline or path_n[0] <= cap:

@@ -344,17 +344,131 @@ static void path_point(const orc_track_out* o, int64_t q, double x, double y, do
     e->pad[0] = e->pad[1] = e->pad[2] = 0;
 }
 
-int orc_track(const orc_field* f, int64_t n,
-              const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
-              const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
-              const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
+/* ---- grids ---------------------------------------------------------------
+ * The tracking loop sees a grid through three questions: the box of a cell
+ * (low corner, sizes), the cell's Pollock velocities, and the cell across a
+ * face at a given exit point (-1 outside the domain). */
+
+struct orc_grid {
+    void (*box)(const orc_grid* g, int32_t c, double o[3], double D[3]);
+    void (*vel)(const orc_grid* g, int32_t c, cellvel* cv);
+    int32_t (*across)(const orc_grid* g, int32_t c, int ax, int side, double x[3]);
+    const int8_t* ibound;
+    const orc_field* f;
+    const orc_usg_field* u;
+    const double *xf, *yf, *zf;
+};
+
+static void st_box(const orc_grid* g, int32_t c, double o[3], double D[3])
 {
-    const int nlay = f->nlay, nrow = f->nrow, ncol = f->ncol;
-    double xf[ORC_MAX_AXIS + 1], yf[ORC_MAX_AXIS + 1], zf[ORC_MAX_AXIS + 1];
-    if (ncol > ORC_MAX_AXIS || nrow > ORC_MAX_AXIS || nlay > ORC_MAX_AXIS) return -1;
-    face_coords(f->delr, ncol, f->origin[0], xf);
-    face_coords(f->delc, nrow, f->origin[1], yf);
-    face_coords(f->dz, nlay, f->origin[2], zf);
+    const orc_field* f = g->f;
+    int j = c % f->ncol, i = (c / f->ncol) % f->nrow, k = c / (f->ncol * f->nrow);
+    o[0] = g->xf[j]; o[1] = g->yf[i]; o[2] = g->zf[k];
+    D[0] = f->delr[j]; D[1] = f->delc[i]; D[2] = f->dz[k];
+}
+
+static void st_vel(const orc_grid* g, int32_t c, cellvel* cv)
+{
+    const orc_field* f = g->f;
+    cell_velocities(f, c / (f->ncol * f->nrow), (c / f->ncol) % f->nrow, c % f->ncol, cv);
+}
+
+static int32_t st_across(const orc_grid* g, int32_t c, int ax, int side, double x[3])
+{
+    const orc_field* f = g->f;
+    (void)x;
+    int j = c % f->ncol, i = (c / f->ncol) % f->nrow, k = c / (f->ncol * f->nrow);
+    if (ax == 0) j += side;
+    else if (ax == 1) i += side;
+    else k += side;
+    if (j < 0 || j >= f->ncol || i < 0 || i >= f->nrow || k < 0 || k >= f->nlay) return -1;
+    return (int32_t)(((int64_t)k * f->nrow + i) * f->ncol + j);
+}
+
+/* rectangular unstructured cells: face velocities from the total flow of
+ * each face (its sub-faces summed in list order), the cell's own face area */
+static void usg_box(const orc_grid* g, int32_t c, double o[3], double D[3])
+{
+    const double* b = g->u->box + 6 * (size_t)c;
+    o[0] = b[0]; o[1] = b[1]; o[2] = b[2];
+    D[0] = b[3]; D[1] = b[4]; D[2] = b[5];
+}
+
+static double usg_face_flow(const orc_usg_field* u, int32_t c, int fi)
+{
+    const int64_t e0 = u->face_off[6 * (size_t)c + fi], e1 = u->face_off[6 * (size_t)c + fi + 1];
+    if (e1 <= e0) return 0.0;
+    double s = u->q[e0];
+    for (int64_t e = e0 + 1; e < e1; e++) s += u->q[e];
+    return s;
+}
+
+static void usg_vel(const orc_grid* g, int32_t c, cellvel* cv)
+{
+    const orc_usg_field* u = g->u;
+    const double* b = u->box + 6 * (size_t)c;
+    double n = u->porosity[c];
+    double dx = b[3], dy = b[4], dzz = b[5];
+    double ax = dy * dzz, ay = dx * dzz, az = dx * dy;
+    cv->v1[0] = usg_face_flow(u, c, 0) / (n * ax); cv->v2[0] = usg_face_flow(u, c, 1) / (n * ax);
+    cv->v1[1] = usg_face_flow(u, c, 2) / (n * ay); cv->v2[1] = usg_face_flow(u, c, 3) / (n * ay);
+    cv->v1[2] = usg_face_flow(u, c, 4) / (n * az); cv->v2[2] = usg_face_flow(u, c, 5) / (n * az);
+    cv->D[0] = dx; cv->D[1] = dy; cv->D[2] = dzz;
+    for (int a = 0; a < 3; a++) {
+        cv->A[a] = (cv->v2[a] - cv->v1[a]) / cv->D[a];
+        cv->iA[a] = (cv->A[a] != 0.0) ? 1.0 / cv->A[a] : 0.0;
+    }
+}
+
+/* The neighbour across face (ax, side) at the exit point x: the sub-face
+ * whose rectangle holds x (first in list order; else the nearest, by the
+ * larger of the two axis distances, first on ties), provided its flow runs
+ * in the crossing direction; otherwise the nearest sub-face whose flow does
+ * (one exists: the face's total flow has that sign, or the particle would
+ * not have left through it), and x moves onto that sub-face's rectangle.
+ * No sub-face: outside. */
+static double rect_dist(const double* r, double xa, double xb)
+{
+    double da = fmax(r[0] - xa, xa - r[1]);
+    double db = fmax(r[2] - xb, xb - r[3]);
+    return fmax(fmax(da, db), 0.0);
+}
+
+static int32_t usg_across(const orc_grid* g, int32_t c, int ax, int side, double x[3])
+{
+    const orc_usg_field* u = g->u;
+    const int fi = 2 * ax + (side > 0 ? 1 : 0);
+    const int64_t e0 = u->face_off[6 * (size_t)c + fi], e1 = u->face_off[6 * (size_t)c + fi + 1];
+    if (e1 <= e0) return -1;
+    const int oa = ax == 0 ? 1 : 0, ob = ax == 2 ? 1 : 2;
+    const double xa = x[oa], xb = x[ob];
+    int64_t best = e0;
+    double bd = INFINITY;
+    for (int64_t e = e0; e < e1; e++) {
+        const double d = rect_dist(u->rect + 4 * (size_t)e, xa, xb);
+        if (d < bd) { bd = d; best = e; }
+        if (d == 0.0) break;
+    }
+    if (u->q[best] * (double)side > 0.0) return u->nbr[best];
+    int64_t alt = -1;
+    double ad = INFINITY;
+    for (int64_t e = e0; e < e1; e++) {
+        if (!(u->q[e] * (double)side > 0.0)) continue;
+        const double d = rect_dist(u->rect + 4 * (size_t)e, xa, xb);
+        if (d < ad) { ad = d; alt = e; }
+    }
+    if (alt < 0) return u->nbr[best];
+    const double* r = u->rect + 4 * (size_t)alt;
+    x[oa] = fmin(fmax(xa, r[0]), r[1]);
+    x[ob] = fmin(fmax(xb, r[2]), r[3]);
+    return u->nbr[alt];
+}
+
+static int track_core(const orc_grid* g, int64_t n,
+                      const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+                      const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+                      const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
+{
     const double t_stop = opt->t_stop;
     const int nt = (opt->times && out->ts_x) ? opt->n_times : 0;
     const int64_t max_steps = opt->max_steps > 0 ? opt->max_steps : ORC_DEFAULT_MAX_STEPS;
@@ -368,14 +482,14 @@ int orc_track(const orc_field* f, int64_t n,
         uint8_t exit_face = (steps > 0 && face0) ? face0[q] : ORC_FACE_NONE;
         uint64_t h = 0xcbf29ce484222325ULL;
         int kn = 0;
-        int j = 0, i = 0, k = 0;
+        double o[3] = {0.0, 0.0, 0.0}, D[3] = {0.0, 0.0, 0.0};   /* the cell's low corner and sizes */
         if (c >= 0) {
-            j = c % ncol; i = (c / ncol) % nrow; k = c / (ncol * nrow);
+            g->box(g, c, o, D);
             h = (steps > 0 && hash0) ? hash0[q] : fnv_step(h, c);
             /* a moving particle in a cell that is not active under this
              * field (a later flow period can change ibound) stops there */
             if (st == ORC_ST_ACTIVE) {
-                int8_t ib0 = f->ibound[c];
+                int8_t ib0 = g->ibound[c];
                 if (ib0 == 0 || ib0 == -1) st = ORC_ST_BOUNDARY;
                 else if (ib0 == 2 && !opt->pass_weak_sinks) st = ORC_ST_SINK;
             }
@@ -385,21 +499,21 @@ int orc_track(const orc_field* f, int64_t n,
         /* output times at or before the start: the release position */
         while (kn < nt && opt->times[kn] <= t) {
             if (c >= 0)
-                write_record(out, n, kn, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], c, st);
+                write_record(out, n, kn, q, o[0] + p[0], o[1] + p[1], o[2] + p[2], c, st);
             else
                 write_record(out, n, kn, q, NAN, NAN, NAN, -1, st);
             kn++;
         }
         /* pathline: the start point, with the status it starts with */
         if (opt->path_start && c >= 0)
-            path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, st);
+            path_point(out, q, o[0] + p[0], o[1] + p[1], o[2] + p[2], t, c, steps, st);
         int took = 0;   /* the last loop pass took a cell-step */
         while (st == ORC_ST_ACTIVE) {
             took = 0;
             if (t >= t_stop) { st = ORC_ST_TIME; break; }
             if (steps >= max_steps) { st = ORC_ST_STEP_CAP; break; }
             cellvel cv;
-            cell_velocities(f, k, i, j, &cv);
+            g->vel(g, c, &cv);
             int face[3];
             double te[3];
             for (int a = 0; a < 3; a++)
@@ -410,7 +524,7 @@ int orc_track(const orc_field* f, int64_t n,
                 if (face[a] != 0 && te[a] < tmin) { tmin = te[a]; ax = a; }
             steps++;
             took = 1;
-            if (ax < 0 && f->ibound[c] == 2) {
+            if (ax < 0 && g->ibound[c] == 2) {
                 /* inside a sink cell with no reachable face: captured */
                 st = ORC_ST_SINK;
                 break;
@@ -420,9 +534,9 @@ int orc_track(const orc_field* f, int64_t n,
                  * this cell; later output times still see it move inside */
                 while (kn < nt) {
                     double tau = opt->times[kn] - t;
-                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                    double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                    double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                    double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_NO_EXIT);
                     kn++;
                 }
@@ -433,9 +547,9 @@ int orc_track(const orc_field* f, int64_t n,
                 double dt = t_stop - t;
                 while (kn < nt && opt->times[kn] <= t_stop) {
                     double tau = opt->times[kn] - t;
-                    double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                    double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                    double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                    double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                    double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                    double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                     kn++;
                 }
@@ -449,9 +563,9 @@ int orc_track(const orc_field* f, int64_t n,
             double t_end = t + dt;
             while (kn < nt && opt->times[kn] <= t_end) {
                 double tau = opt->times[kn] - t;
-                double g0 = xf[j] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                double g1 = yf[i] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                double g2 = zf[k] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
+                double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
+                double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
                 write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                 kn++;
             }
@@ -461,32 +575,44 @@ int orc_track(const orc_field* f, int64_t n,
             }
             t = t_end;
             exit_face = (uint8_t)(2 * ax + (face[ax] > 0 ? 1 : 0));
-            /* hand over to the neighbour across the exit face */
-            int nj = j, ni = i, nk = k;
-            if (ax == 0) nj += face[0];
-            else if (ax == 1) ni += face[1];
-            else nk += face[2];
-            if (nj < 0 || nj >= ncol || ni < 0 || ni >= nrow || nk < 0 || nk >= nlay) {
+            /* hand over to the neighbour across the exit face (at the exit point) */
+            const int side = face[ax];
+            double xg[3] = {o[0] + p[0], o[1] + p[1], o[2] + p[2]};
+            const int32_t nc = g->across(g, c, ax, side, xg);
+            if (nc < 0) {
                 st = ORC_ST_EXIT_DOMAIN;
                 break;
             }
-            int32_t nc = (int32_t)(((int64_t)nk * nrow + ni) * ncol + nj);
-            int8_t ib = f->ibound[nc];
+            int8_t ib = g->ibound[nc];
             if (ib == 0 || ib == -1) { st = ORC_ST_BOUNDARY; break; }
             if (ib == 2 && !opt->pass_weak_sinks) { st = ORC_ST_SINK; break; }
-            j = nj; i = ni; k = nk; c = nc;
-            if (face[ax] > 0) p[ax] = 0.0;
-            else p[ax] = (ax == 0) ? f->delr[j] : (ax == 1) ? f->delc[i] : f->dz[k];
+            double on[3], Dn[3];
+            g->box(g, nc, on, Dn);
+            /* the other axes keep their global coordinate (o - on is 0
+             * between cells of one column of a rectilinear grid), clamped
+             * to the new cell; the exit axis enters on the shared face */
+            for (int a = 0; a < 3; a++) {
+                if (a == ax) continue;
+                /* a hand-over that moved the point along the face (see
+                 * usg_across) enters at the moved point */
+                double pa = (xg[a] == o[a] + p[a]) ? p[a] + (o[a] - on[a]) : xg[a] - on[a];
+                if (pa < 0.0) pa = 0.0;
+                if (pa > Dn[a]) pa = Dn[a];
+                p[a] = pa;
+            }
+            p[ax] = (side > 0) ? 0.0 : Dn[ax];
+            c = nc;
+            for (int a = 0; a < 3; a++) { o[a] = on[a]; D[a] = Dn[a]; }
             h = fnv_step(h, c);
             /* pathline: the entry point in the new cell */
-            path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, ORC_ST_ACTIVE);
+            path_point(out, q, o[0] + p[0], o[1] + p[1], o[2] + p[2], t, c, steps, ORC_ST_ACTIVE);
         }
         /* pathline: where the last step ended (stop time, sink, boundary, ...) */
-        if (took) path_point(out, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], t, c, steps, st);
+        if (took) path_point(out, q, o[0] + p[0], o[1] + p[1], o[2] + p[2], t, c, steps, st);
         /* output times after termination: the final position */
         while (kn < nt) {
             if (c >= 0)
-                write_record(out, n, kn, q, xf[j] + p[0], yf[i] + p[1], zf[k] + p[2], c, st);
+                write_record(out, n, kn, q, o[0] + p[0], o[1] + p[1], o[2] + p[2], c, st);
             else
                 write_record(out, n, kn, q, NAN, NAN, NAN, -1, st);
             kn++;
@@ -497,7 +623,7 @@ int orc_track(const orc_field* f, int64_t n,
         }
         if (out->gx) {
             if (c >= 0) {
-                out->gx[q] = xf[j] + p[0]; out->gy[q] = yf[i] + p[1]; out->gz[q] = zf[k] + p[2];
+                out->gx[q] = o[0] + p[0]; out->gy[q] = o[1] + p[1]; out->gz[q] = o[2] + p[2];
             } else {
                 out->gx[q] = NAN; out->gy[q] = NAN; out->gz[q] = NAN;
             }
@@ -507,6 +633,54 @@ int orc_track(const orc_field* f, int64_t n,
         if (out->steps) out->steps[q] = (uint32_t)steps;
         if (out->exit_face) out->exit_face[q] = exit_face;
         if (out->hash) out->hash[q] = h;
+    }
+    return 0;
+}
+
+int orc_track(const orc_field* f, int64_t n,
+              const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+              const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+              const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
+{
+    double xf[ORC_MAX_AXIS + 1], yf[ORC_MAX_AXIS + 1], zf[ORC_MAX_AXIS + 1];
+    if (f->ncol > ORC_MAX_AXIS || f->nrow > ORC_MAX_AXIS || f->nlay > ORC_MAX_AXIS) return -1;
+    face_coords(f->delr, f->ncol, f->origin[0], xf);
+    face_coords(f->delc, f->nrow, f->origin[1], yf);
+    face_coords(f->dz, f->nlay, f->origin[2], zf);
+    orc_grid g = {st_box, st_vel, st_across, f->ibound, f, NULL, xf, yf, zf};
+    return track_core(&g, n, cell0, px0, py0, pz0, t0, status0, steps0, hash0, face0, opt, out);
+}
+
+int orc_usg_track(const orc_usg_field* u, int64_t n,
+                  const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+                  const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+                  const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
+{
+    orc_grid g = {usg_box, usg_vel, usg_across, u->ibound, NULL, u, NULL, NULL, NULL};
+    return track_core(&g, n, cell0, px0, py0, pz0, t0, status0, steps0, hash0, face0, opt, out);
+}
+
+int orc_usg_release_explicit(const orc_usg_field* u, int64_t n, const int32_t* cell_in, const double* frac,
+                             int32_t* cell, double* px, double* py, double* pz, uint8_t* status)
+{
+    for (int64_t q = 0; q < n; q++) {
+        int32_t c = cell_in[q];
+        if (c < 0 || c >= u->ncell) {
+            cell[q] = -1; px[q] = py[q] = pz[q] = 0.0; status[q] = ORC_ST_INVALID_RELEASE;
+            continue;
+        }
+        const double* b = u->box + 6 * (size_t)c;
+        double fx = frac[3 * q], fy = frac[3 * q + 1], fz = frac[3 * q + 2];
+        if (fx < 0.0) fx = 0.0;
+        if (fx > 1.0) fx = 1.0;
+        if (fy < 0.0) fy = 0.0;
+        if (fy > 1.0) fy = 1.0;
+        if (fz < 0.0) fz = 0.0;
+        if (fz > 1.0) fz = 1.0;
+        cell[q] = c;
+        px[q] = fx * b[3]; py[q] = fy * b[4]; pz[q] = fz * b[5];
+        int8_t ib = u->ibound[c];
+        status[q] = (ib == 1) ? ORC_ST_ACTIVE : (ib == 2) ? ORC_ST_SINK : ORC_ST_INVALID_RELEASE;
     }
     return 0;
 }

@@ -46,6 +46,23 @@ typedef struct {
     int32_t path_start;   /* pathlines: 1 = a record at the start of every particle */
 } orc_track_opts;
 
+/* Rectangular unstructured grid: axis-aligned box cells, per cell and face
+ * (x-, x+, y-, y+, z-, z+) a list of sub-faces with the neighbour across
+ * (-1: outside), the flow through it (m^3/s along +axis) and its rectangle
+ * in the two other axes (lo_a, hi_a, lo_b, hi_b; axes in x, y, z order). */
+typedef struct {
+    int64_t ncell;
+    const double* box;        /* [ncell][6] x0, y0, z0, dx, dy, dz */
+    const double* porosity;   /* [ncell] */
+    const int8_t* ibound;     /* [ncell] */
+    const int64_t* face_off;  /* [6 ncell + 1] */
+    const int32_t* nbr;       /* [nsub] */
+    const double* q;          /* [nsub] */
+    const double* rect;       /* [nsub][4] */
+} orc_usg_field;
+
+typedef struct orc_grid orc_grid;
+
 /* One pathline point (Methods, "MODPATH": pathline simulations record the
  * path): the release point and the point reached by every cell-step. */
 typedef struct {
@@ -85,4 +102,10 @@ int orc_track(const orc_field* f, int64_t n,
               const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
               const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
               const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out);
+int orc_usg_track(const orc_usg_field* u, int64_t n,
+                  const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
+                  const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
+                  const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out);
+int orc_usg_release_explicit(const orc_usg_field* u, int64_t n, const int32_t* cell_in, const double* frac,
+                             int32_t* cell, double* px, double* py, double* pz, uint8_t* status);
 #endif

@@ -211,3 +211,107 @@ def rk4_track(f, k, i, j, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, pass_
             mark(t, k, i, j, p)
             break
     raise RuntimeError("rk4_track: too many cells")
+
+
+# ---------------------------------------------------------------------------
+# brute force on a rectangular unstructured grid (lumped face flows)
+# ---------------------------------------------------------------------------
+
+def _usg_lin(u, c):
+    """Per-axis (v at low face, v at high face, size): each face's total flow
+    over the cell's own face area and porosity."""
+    b = u.box[c]
+    n = float(u.porosity[c])
+    area = (b[4] * b[5], b[3] * b[5], b[3] * b[4])
+    out = []
+    for a in range(3):
+        ql = sum(float(v) for v in u.q[u.subfaces(c, 2 * a)])
+        qh = sum(float(v) for v in u.q[u.subfaces(c, 2 * a + 1)])
+        out.append((ql / (n * area[a]), qh / (n * area[a]), float(b[3 + a])))
+    return out
+
+
+def _usg_next(u, c, ax, side, g):
+    """Neighbour across face (ax, side) at global point g: the sub-face that
+    holds the point, or - when its flow runs against the crossing - the
+    nearest one whose flow runs with it, the point moved onto it."""
+    fi = 2 * ax + (1 if side > 0 else 0)
+    sl = u.subfaces(c, fi)
+    idx = list(range(*sl.indices(u.nsub)))
+    if not idx:
+        return -1, g
+    oa, ob = [(1, 2), (0, 2), (0, 1)][ax]
+
+    def dist(e):
+        r = u.rect[e]
+        return max(max(r[0] - g[oa], g[oa] - r[1]), max(r[2] - g[ob], g[ob] - r[3]), 0.0)
+
+    best = min(idx, key=lambda e: (dist(e), idx.index(e)))
+    inside = [e for e in idx if dist(e) == 0.0]
+    if inside:
+        best = inside[0]
+    if u.q[best] * side > 0:
+        return int(u.nbr[best]), g
+    ok = [e for e in idx if u.q[e] * side > 0]
+    alt = min(ok, key=lambda e: (dist(e), idx.index(e)))
+    r = u.rect[alt]
+    g = list(g)
+    g[oa] = min(max(g[oa], r[0]), r[1])
+    g[ob] = min(max(g[ob], r[2]), r[3])
+    return int(u.nbr[alt]), g
+
+
+def rk4_track_usg(u, c, p, t_stop=math.inf, max_cells=10_000, frac=2e-3, trace=None):
+    """RK4 with bisection on face events through a rectangular unstructured
+    grid; returns (status, cells visited, final cell, final local p, t)."""
+    p = [float(x) for x in p]
+    t = 0.0
+    seq = [int(c)]
+    for _ in range(max_cells):
+        lin = _usg_lin(u, c)
+        o = u.box[c, :3]
+        vmax = max(max(abs(a), abs(b)) for a, b, _ in lin)
+        if vmax == 0.0:
+            return 5, seq, c, p, t
+        h = frac * min(d for _, _, d in lin) / vmax
+        while True:
+            hh = h if t + h < t_stop else t_stop - t
+            q = _rk4(lin, p, hh)
+            if not any(qa < 0.0 or qa > d for qa, (_, _, d) in zip(q, lin)):
+                p, t = q, t + hh
+                if t >= t_stop:
+                    return 1, seq, c, p, t
+                continue
+            lo, hi = 0.0, hh
+            for _ in range(80):
+                mid = 0.5 * (lo + hi)
+                if any(qa < 0.0 or qa > d for qa, (_, _, d) in zip(_rk4(lin, p, mid), lin)):
+                    hi = mid
+                else:
+                    lo = mid
+            qh = _rk4(lin, p, hi)
+            ax = int(np.argmax([max(-qa, qa - d) for qa, (_, _, d) in zip(qh, lin)]))
+            side = 1 if qh[ax] > lin[ax][2] else -1
+            t = t + hi
+            p = [min(max(pa, 0.0), d) for pa, (_, _, d) in zip(qh, lin)]
+            p[ax] = lin[ax][2] if side > 0 else 0.0
+            g = [o[a] + p[a] for a in range(3)]
+            nc, g = _usg_next(u, c, ax, side, g)
+            if nc < 0:
+                if trace is not None:
+                    trace.append((t, c, g))
+                return 4, seq, c, p, t
+            ib = int(u.ibound[nc])
+            if ib in (0, -1, 2):
+                if trace is not None:
+                    trace.append((t, c, g))
+                return (3 if ib != 2 else 2), seq, c, p, t
+            on, dn = u.box[nc, :3], u.box[nc, 3:]
+            p = [min(max(g[a] - on[a], 0.0), dn[a]) for a in range(3)]
+            p[ax] = 0.0 if side > 0 else float(dn[ax])
+            c = nc
+            seq.append(int(c))
+            if trace is not None:
+                trace.append((t, c, [on[a] + p[a] for a in range(3)]))
+            break
+    raise RuntimeError("rk4_track_usg: too many cells")
