@@ -228,6 +228,37 @@ const char* mp_last_error(void);
  * MP_ERR_CUDA. */
 int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out);
 int mp_field_free(mp_field* f);
+
+/* A rectangular unstructured (quadtree) grid: the paper's TC2 also runs on
+ * a quadtree refinement of its grid.  Cells are axis-aligned boxes; each
+ * face (x-, x+, y-, y+, z-, z+) of cell c has the sub-faces
+ * face_off[6c + f] .. face_off[6c + f + 1] - 1, each with the neighbour
+ * across it (nbr, -1 outside the domain), the flow through it (q, m^3/s,
+ * positive along +axis) and its rectangle in the two other axes (rect[4]:
+ * lo_a, hi_a, lo_b, hi_b, global m; the other axes in x, y, z order).  Every
+ * connection is listed from both cells.  Host arrays (MP_DEVICE_PTR is not
+ * accepted).  Pollock's displacement uses each face's total flow over the
+ * cell's own face area; a particle leaving through a face enters the
+ * neighbour of the sub-face holding its exit point when that sub-face's
+ * flow runs with the crossing, else of the nearest one whose flow does
+ * (the point moves onto it).  Tracking: FP64 only, explicit releases
+ * (mp_release_group with MP_RELEASE_EXPLICIT), every mode (endpoint,
+ * timeseries, pathline), batches and flow periods (fields with the same
+ * boxes and sub-face layout).  Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE,
+ * MP_ERR_NONFINITE, MP_ERR_OOM, MP_ERR_CUDA. */
+typedef struct {
+    int64_t ncell;
+    const double* box;        /* [ncell][6]: x0, y0, z0, dx, dy, dz (m), sizes > 0 */
+    const double* porosity;   /* [ncell], in (0, 1] for active cells */
+    const int8_t* ibound;     /* [ncell]: 0 inactive, 1 active, -1 constant head, 2 sink */
+    const int64_t* face_off;  /* [6 ncell + 1], non-decreasing, face_off[0] = 0 */
+    const int32_t* nbr;       /* [nsub] */
+    const double* q;          /* [nsub] */
+    const double* rect;       /* [nsub][4] */
+    uint32_t flags;           /* 0 */
+} mp_usg_desc;
+
+int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out);
 /* Device bytes held by a loaded field. */
 int mp_field_bytes(const mp_field* f, size_t* bytes);
 

@@ -1,9 +1,10 @@
 """Build libmp.so (CUDA, sm_103a) in-tree with nvcc.
 
-Three translation units, compiled in parallel:
+Translation units, compiled in parallel:
   mp_api.cu    host side of the C ABI
   mp_fp64.cu   field records, release, FP64 tracking (-fmad=false: no FMA
                contraction, so FP64 results round exactly as written)
+  mp_usg.cu    FP64 tracking on rectangular unstructured grids (-fmad=false)
   mp_mixed.cu  mixed-precision tracking (contraction allowed)
   mp_noalloc.cu  the entry point that allocates no device memory
 """
@@ -24,6 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "mp_api.cu": [],
     "mp_fp64.cu": ["-fmad=false"],
+    "mp_usg.cu": ["-fmad=false"],
     "mp_mixed.cu": [],
     "mp_noalloc.cu": [],
 }

@@ -101,7 +101,9 @@ DevState group_view(char* buf, long long n)
 
 struct mp_field {
     mp_ctx* ctx = nullptr;
+    int usg = 0;           // 1: rectangular unstructured grid (u), else rectilinear (d)
     DevField d{};
+    DevUsg u{};
     void* buf = nullptr;   // one allocation for all device arrays
     size_t bytes = 0;
     std::vector<double> geom;   // dims, delr, delc, dz, origin: fields with equal geom share a grid
@@ -395,6 +397,96 @@ int mp_field_free(mp_field* f)
     return MP_OK;
 }
 
+int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
+{
+    if (!ctx || !d || !out) return fail(MP_ERR_INVALID_ARG, "mp_usg_field_load: NULL argument");
+    if (d->flags & MP_DEVICE_PTR) return fail(MP_ERR_INVALID_ARG, "mp_usg_field_load: host arrays only");
+    const long long nc = d->ncell;
+    if (nc <= 0 || nc > 0x7fffffffLL) return fail(MP_ERR_SHAPE, "mp_usg_field_load: ncell outside [1, 2^31)");
+    if (!d->box || !d->porosity || !d->ibound || !d->face_off || !d->nbr || !d->q || !d->rect)
+        return fail(MP_ERR_INVALID_ARG, "mp_usg_field_load: NULL array");
+    if (d->face_off[0] != 0) return fail(MP_ERR_SHAPE, "mp_usg_field_load: face_off[0] != 0");
+    for (long long k = 0; k < 6 * nc; ++k)
+        if (d->face_off[k + 1] < d->face_off[k]) return fail(MP_ERR_SHAPE, "mp_usg_field_load: face_off decreases");
+    const long long ns = d->face_off[6 * nc];
+    if (ns > 0x7fffffffLL) return fail(MP_ERR_SHAPE, "mp_usg_field_load: more than 2^31 sub-faces");
+    for (long long c = 0; c < nc; ++c) {
+        for (int a = 0; a < 6; ++a)
+            if (!std::isfinite(d->box[6 * c + a]) || (a >= 3 && !(d->box[6 * c + a] > 0.0)))
+                return fail(MP_ERR_NONFINITE, "mp_usg_field_load: box must be finite with sizes > 0");
+        const int8_t ib = d->ibound[c];
+        if (ib < -1 || ib > 2) return fail(MP_ERR_INVALID_ARG, "mp_usg_field_load: ibound outside {-1, 0, 1, 2}");
+        if ((ib == 1 || ib == 2) && !(d->porosity[c] > 0.0 && d->porosity[c] <= 1.0))
+            return fail(MP_ERR_NONFINITE, "mp_usg_field_load: porosity outside (0, 1] in an active cell");
+    }
+    for (long long e = 0; e < ns; ++e) {
+        if (d->nbr[e] < -1 || d->nbr[e] >= nc) return fail(MP_ERR_SHAPE, "mp_usg_field_load: neighbour out of range");
+        if (!std::isfinite(d->q[e])) return fail(MP_ERR_NONFINITE, "mp_usg_field_load: non-finite flow");
+        for (int a = 0; a < 4; ++a)
+            if (!std::isfinite(d->rect[4 * e + a])) return fail(MP_ERR_NONFINITE, "mp_usg_field_load: non-finite rect");
+    }
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    size_t off = 0;
+    const size_t o_cell = off; off = align256(off + sizeof(mp::UsgCell) * (size_t)nc);
+    const size_t o_fo = off; off = align256(off + sizeof(long long) * (size_t)(6 * nc + 1));
+    const size_t o_sub = off; off = align256(off + sizeof(mp::UsgSub) * (size_t)std::max(ns, 1LL));
+    const size_t o_ib = off; off = align256(off + (size_t)nc);
+    const size_t persistent = off;
+    const size_t o_box = off; off = align256(off + sizeof(double) * 6 * (size_t)nc);
+    const size_t o_por = off; off = align256(off + sizeof(double) * (size_t)nc);
+    char* buf = nullptr;
+    if (cudaMalloc(&buf, off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MP_ERR_OOM, "mp_usg_field_load: device allocation failed");
+    }
+    std::vector<mp::UsgSub> sub((size_t)std::max(ns, 1LL));
+    for (long long e = 0; e < ns; ++e) {
+        sub[e].nbr = d->nbr[e];
+        sub[e].pad = 0;
+        sub[e].q = d->q[e];
+        for (int a = 0; a < 4; ++a) sub[e].rect[a] = d->rect[4 * e + a];
+    }
+    mp::DevUsg u{};
+    u.ncell = nc;
+    u.nsub = ns;
+    u.cell = reinterpret_cast<mp::UsgCell*>(buf + o_cell);
+    u.face_off = reinterpret_cast<long long*>(buf + o_fo);
+    u.sub = reinterpret_cast<mp::UsgSub*>(buf + o_sub);
+    u.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
+    cudaError_t e = cudaMemcpy(buf + o_fo, d->face_off, sizeof(long long) * (size_t)(6 * nc + 1),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(buf + o_sub, sub.data(), sizeof(mp::UsgSub) * sub.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(buf + o_ib, d->ibound, (size_t)nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(buf + o_box, d->box, sizeof(double) * 6 * (size_t)nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(buf + o_por, d->porosity, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = mp::launch_build_usg(u, const_cast<mp::UsgCell*>(u.cell), reinterpret_cast<double*>(buf + o_box),
+                                 reinterpret_cast<double*>(buf + o_por), nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "mp_usg_field_load");
+    }
+    mp_field* f = new mp_field();
+    f->ctx = ctx;
+    f->usg = 1;
+    f->u = u;
+    f->buf = buf;
+    f->bytes = persistent;
+    // grid identity for flow periods: boxes and the sub-face layout
+    f->geom.assign(1, -1.0);
+    f->geom.insert(f->geom.end(), d->box, d->box + 6 * nc);
+    for (long long k = 0; k <= 6 * nc; ++k) f->geom.push_back((double)d->face_off[k]);
+    for (long long k = 0; k < ns; ++k) f->geom.push_back((double)d->nbr[k]);
+    f->geom.insert(f->geom.end(), d->rect, d->rect + 4 * ns);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->fields.insert(f);
+    }
+    *out = f;
+    return MP_OK;
+}
+
 int mp_field_bytes(const mp_field* f, size_t* bytes)
 {
     if (!f || !bytes) return fail(MP_ERR_INVALID_ARG, "mp_field_bytes: NULL");
@@ -441,6 +533,11 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
     g->stream = s;
     g->d = group_view(buf, n);
     // a fresh particle: no steps yet (hash and exit face are read only after one)
+    if (f->usg && r->kind == MP_RELEASE_BOX) {
+        cudaFreeAsync(buf, s);
+        delete g;
+        return fail(MP_ERR_INVALID_ARG, "mp_release_group: box releases need a rectilinear grid");
+    }
     cudaError_t e = cudaMemsetAsync(g->d.steps, 0, 4 * (size_t)n, s);
     if (e != cudaSuccess) {
         cudaFreeAsync(buf, s);
@@ -468,7 +565,9 @@ int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, v
             local = reinterpret_cast<double*>(tmp + o_l);
             t0 = r->t0 ? reinterpret_cast<double*>(tmp + o_t0) : nullptr;
         }
-        if (e == cudaSuccess) e = launch_release_explicit(f->d, g->d, n, cell, local, t0, s);
+        if (e == cudaSuccess)
+            e = f->usg ? launch_release_explicit_usg(f->u, g->d, n, cell, local, t0, s)
+                       : launch_release_explicit(f->d, g->d, n, cell, local, t0, s);
         if (tmp) cudaFreeAsync(tmp, s);
     }
     if (e != cudaSuccess) {
@@ -566,6 +665,8 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
         return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
     if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown precision");
+    if (g->field->usg && o->precision != MP_PREC_FP64)
+        return fail(MP_ERR_INVALID_ARG, "mp_track: unstructured grids are tracked in FP64");
     if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC && o->schedule != MP_SCHED_AUTO)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown schedule");
     if (o->block < 0 || o->block > 1024) return fail(MP_ERR_INVALID_ARG, "mp_track: block outside [0, 1024]");
@@ -713,8 +814,9 @@ int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n
     const int blk = block > 0 ? block : 128;
     if (e == cudaSuccess) {
         const mp::DevField& fd = *mp::field_device_view(f);
-        e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, modes, schedule, blk, 0, s)
-                                        : launch_track_mixed(fd, b, modes, schedule, blk, 0, s);
+        if (f->usg) e = launch_track_usg(f->u, b, modes, schedule, blk, 0, s);
+        else e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, modes, schedule, blk, 0, s)
+                                             : launch_track_mixed(fd, b, modes, schedule, blk, 0, s);
     }
     for (int i = 0; i < n && e == cudaSuccess && (ev & 2u); ++i) e = cudaEventRecord(rs[i]->k1, s);
     cudaFreeAsync(tbl, s);
@@ -1105,6 +1207,7 @@ namespace mp {
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 const DevField* field_device_view(const mp_field* f) { return &f->d; }
+bool field_is_usg(const mp_field* f) { return f->usg != 0; }
 
 }  // namespace mp
 
@@ -1223,6 +1326,7 @@ int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release
 {
     if (!ctx || !f || !rel || !opts || !out || n_reqs < 1) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: bad argument");
     if (f->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: field of another context");
+    if (f->usg) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: box releases need a rectilinear grid");
     for (int i = 0; i < n_reqs; ++i) {
         const int rc = graph_release_check(rel[i]);
         if (rc != MP_OK) return rc;

@@ -17,6 +17,7 @@
 
 #include "mp_internal.h"
 #include "mp_sched.cuh"
+#include "mp_f64math.cuh"
 
 namespace mp {
 
@@ -251,137 +252,6 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 }
 
 // ---------------------------------------------------------------------------
-// Exact tests and scalings on the bits of a double.  GB300 runs FP64 at 1/64
-// of the FP32 rate and the FP64 kernel is bound by its FP64 pipe, so sign,
-// zero and order tests with a known sign, frexp and ldexp are done as
-// integer operations on the representation (the ALU pipe is idle); each
-// gives exactly the IEEE result for the non-NaN operands the path produces.
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
-// v > 0
-__device__ __forceinline__ bool gt0(double v) { return bits(v) > 0LL; }
-// v < 0 (-0 is not)
-__device__ __forceinline__ bool lt0(double v)
-{
-    return (unsigned long long)bits(v) > 0x8000000000000000ULL;
-}
-// v == 0 (either sign)
-__device__ __forceinline__ bool eq0(double v) { return (bits(v) << 1) == 0LL; }
-// a > b for b > 0
-__device__ __forceinline__ bool gt_pos(double a, double b) { return bits(a) > bits(b); }
-// |a| < b for b > 0
-__device__ __forceinline__ bool abs_lt(double a, double b) { return (bits(a) & 0x7fffffffffffffffLL) < bits(b); }
-__device__ __forceinline__ bool is_nan(double v)
-{
-    return (bits(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-}
-
-// frexp: u = m 2^e with m in [1/2, 1) (u == 0, inf, NaN: m = u, e = 0)
-__device__ __forceinline__ double frexp_bits(double u, int& e)
-{
-    long long b = bits(u);
-    int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0x7ff || (b << 1) == 0LL) {
-        e = 0;
-        return u;
-    }
-    if (ex == 0) {   // subnormal: scale by 2^54 (exact)
-        b = bits(u * 18014398509481984.0);
-        ex = (int)((b >> 52) & 0x7ff) - 54;
-    }
-    e = ex - 1022;
-    return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | 0x3fe0000000000000LL);
-}
-
-// 2^k as ldexp(1, k) gives it, k in [-2000, 2000]
-__device__ __forceinline__ double pow2i(int k)
-{
-    if (k >= 1024) return CUDART_INF;
-    if (k >= -1022) return __longlong_as_double((long long)(k + 1023) << 52);
-    if (k >= -1074) return __longlong_as_double(1LL << (k + 1074));
-    return 0.0;
-}
-
-// ---------------------------------------------------------------------------
-// log1p and expm1 by argument reduction and series, with IEEE additions,
-// multiplications, divisions and explicit fused multiply-adds in a fixed
-// order (no implicit contraction: this file is built with -fmad=false), so
-// that the FP64 path produces the same bits as any other evaluation of the
-// same steps on the host.  Exit-axis choices near a
-// tie then agree exactly, which library functions with different last-bit
-// rounding cannot guarantee on ill-conditioned fields.
-//   log1p(x): u = 1 + x, c = its rounding error (two-sum), u = m 2^e with
-//     m in [1/sqrt2, sqrt2), f = m - 1, log(1 + f) = 2 atanh(f / (2 + f))
-//     by its odd series to the 25th power (Horner, fma), + e ln2 (split)
-//     + c / u, with c (below half an ulp of u) times the FP32 reciprocal.
-//   expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
-//     r = w - k ln2 (split), expm1(r) by its Taylor series to r^14 / 14!,
-//     expm1(w) = (2^k - 1) + 2^k expm1(r), 2^k with k limited to
-//     [-2000, 2000] (the same value for every k).
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ double series_log1p(double x)
-{
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double u = 1.0 + x;
-    const double c = gt_pos(x, 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
-    int e;
-    double m = frexp_bits(u, e);
-    if (bits(m) < bits(0.70710678118654752440)) {   // m >= 0
-        m = m * 2.0;
-        e = e - 1;
-    }
-    const double f = m - 1.0;
-    const double s = f / (2.0 + f);
-    const double z2 = s * s;
-    double p = 1.0 / 25.0;
-    p = fma(p, z2, 1.0 / 23.0);
-    p = fma(p, z2, 1.0 / 21.0);
-    p = fma(p, z2, 1.0 / 19.0);
-    p = fma(p, z2, 1.0 / 17.0);
-    p = fma(p, z2, 1.0 / 15.0);
-    p = fma(p, z2, 1.0 / 13.0);
-    p = fma(p, z2, 1.0 / 11.0);
-    p = fma(p, z2, 1.0 / 9.0);
-    p = fma(p, z2, 1.0 / 7.0);
-    p = fma(p, z2, 1.0 / 5.0);
-    p = fma(p, z2, 1.0 / 3.0);
-    p = fma(p, z2, 1.0);
-    const double logm = 2.0 * s * p;
-    const double de = (double)e;
-    const double ru = (double)__frcp_rn((float)u);
-    return de * ln2_hi + ((logm + c * ru) + de * ln2_lo);
-}
-
-__device__ __forceinline__ double series_expm1(double w)
-{
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double k = abs_lt(w, 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
-    const double r = (w - k * ln2_hi) - k * ln2_lo;
-    double p = 1.0 / 87178291200.0;           // 1/14!
-    p = fma(p, r, 1.0 / 6227020800.0);           // 1/13!
-    p = fma(p, r, 1.0 / 479001600.0);
-    p = fma(p, r, 1.0 / 39916800.0);
-    p = fma(p, r, 1.0 / 3628800.0);
-    p = fma(p, r, 1.0 / 362880.0);
-    p = fma(p, r, 1.0 / 40320.0);
-    p = fma(p, r, 1.0 / 5040.0);
-    p = fma(p, r, 1.0 / 720.0);
-    p = fma(p, r, 1.0 / 120.0);
-    p = fma(p, r, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
-    p = fma(p, r, 1.0 / 2.0);
-    p = fma(p, r, 1.0);
-    const double em = r * p;
-    if (eq0(k)) return em;
-    int ki = __double2int_rz(k);   // k is integral; out of range saturates
-    ki = ki > 2000 ? 2000 : (ki < -2000 ? -2000 : ki);
-    const double t = pow2i(ki);
-    return (t - 1.0) + t * em;
-}
-
-// ---------------------------------------------------------------------------
 // FP64 tracking engine
 // ---------------------------------------------------------------------------
 
@@ -403,24 +273,10 @@ struct F64Engine {
         double tev;  // next output time or the stop time, whichever is first
     };
 
-    // Exit time along one axis (face = +1, -1, or 0 when no face is
-    // reachable; v2pos / v1neg: the signs of the face velocities).  Written
-    // without branches around the division and log1p so that the lanes of a
-    // warp stay converged; lanes with no reachable face compute on harmless
-    // operands and select +inf.  The values equal those of the branchy form
-    // (t1 = d / vp, z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
     __device__ __forceinline__ static double exit_time(double A, double iA, double D, double vp, double pp,
                                                        bool v2pos, bool v1neg, int& face)
     {
-        const bool up = gt0(vp) && v2pos;
-        const bool dn = lt0(vp) && v1neg;
-        face = up ? 1 : (dn ? -1 : 0);
-        const double d = up ? D - pp : -pp;
-        const double t1 = d / (face ? vp : 1.0);
-        const double z = A * t1;
-        const bool lin = eq0(z) || !face;
-        const double te = lin ? t1 : series_log1p(lin ? 0.5 : z) * iA;
-        return face ? te : CUDART_INF;
+        return f64_exit_time(A, iA, D, vp, pp, v2pos, v1neg, face);
     }
 
     __device__ __forceinline__ static int face_of(double vp, bool v2pos, bool v1neg)
@@ -467,19 +323,9 @@ struct F64Engine {
         return face ? e : CUDART_INF_F;
     }
 
-    // analytic motion along one axis for a time dt, clamped to the cell
-    // (the same values as: s == 0 -> pp; w == 0 -> pp + s; else
-    // pp + (vp * expm1(w)) * (1 / A))
     __device__ __forceinline__ static double move(double A, double iA, double D, double vp, double pp, double dt)
     {
-        const double s = vp * dt;
-        const double w = A * dt;
-        const bool lin = eq0(w);
-        const double em = series_expm1(lin ? 0.5 : w);
-        double pn = lin ? pp + s : pp + (vp * em) * iA;
-        pn = lt0(pn) ? 0.0 : pn;
-        pn = gt_pos(pn, D) ? D : pn;
-        return eq0(s) ? pp : pn;
+        return f64_move(A, iA, D, vp, pp, dt);
     }
 
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,

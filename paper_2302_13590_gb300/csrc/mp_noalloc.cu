@@ -61,6 +61,7 @@ int scratch_ptr(unsigned long long** out)
 extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats)
 {
     if (!f || !a) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: NULL argument");
+    if (mp::field_is_usg(f)) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: rectilinear grids only");
     if (a->n < 0) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: n < 0");
     const mp_track_opts* o = &a->opts;
     if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))

@@ -1,0 +1,448 @@
+// mp_usg.cu - FP64 tracking on rectangular unstructured (quadtree) grids.
+//
+// The paper's second test case also runs on a quadtree grid (TC2: refined
+// near the boundary conditions); MODPATH moves particles there with the same
+// Pollock displacement.  Cells are axis-aligned boxes whose faces may border
+// several smaller cells.  Within a cell the velocity of each axis is linear
+// between the face velocities, each from the face's total flow (its
+// sub-faces summed in list order) over the cell's own face area; a particle
+// that reaches a face enters the neighbour across the sub-face holding the
+// exit point when that sub-face's flow runs with the crossing, else the
+// nearest sub-face whose flow does (the point moves onto it), so opposing
+// sub-face flows cannot bounce a particle back and forth.  Transverse
+// offsets carry over through the difference of the two cells' origins.
+//
+// Compiled with -fmad=false: the same IEEE operations, in the same order, as
+// the plain double-precision statement of the method; the cell-step itself
+// (exit times, motion) is shared with the rectilinear FP64 engine.
+#include <cfloat>
+#include <cmath>
+
+#include "mp_internal.h"
+#include "mp_sched.cuh"
+#include "mp_f64math.cuh"
+
+namespace mp {
+
+// ---------------------------------------------------------------------------
+// cell records and release
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double usg_face_flow(const DevUsg& u, long long c, int fi)
+{
+    const long long e0 = u.face_off[6 * c + fi], e1 = u.face_off[6 * c + fi + 1];
+    if (e1 <= e0) return 0.0;
+    double s = u.sub[e0].q;
+    for (long long e = e0 + 1; e < e1; ++e) s += u.sub[e].q;
+    return s;
+}
+
+__global__ void k_build_usg(DevUsg u, UsgCell* out, const double* box, const double* por)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= u.ncell) return;
+    const double* b = box + 6 * c;
+    UsgCell r{};
+    for (int a = 0; a < 3; ++a) { r.o[a] = b[a]; r.D[a] = b[3 + a]; }
+    const int8_t ib = u.ibound[c];
+    double v1[3] = {0.0, 0.0, 0.0}, v2[3] = {0.0, 0.0, 0.0};
+    if (ib == 1 || ib == 2) {
+        const double n = por[c];
+        const double dx = b[3], dy = b[4], dzz = b[5];
+        const double area[3] = {dy * dzz, dx * dzz, dx * dy};
+        for (int a = 0; a < 3; ++a) {
+            v1[a] = usg_face_flow(u, c, 2 * a) / (n * area[a]);
+            v2[a] = usg_face_flow(u, c, 2 * a + 1) / (n * area[a]);
+        }
+    }
+    double A[3], iA[3];
+    for (int a = 0; a < 3; ++a) {
+        A[a] = (v2[a] - v1[a]) / b[3 + a];
+        iA[a] = A[a] != 0.0 ? 1.0 / A[a] : 0.0;
+        const unsigned long long sg = (v1[a] > 0.0 ? 1ULL : 0ULL) | (v1[a] < 0.0 ? 2ULL : 0ULL) |
+                                      (v2[a] > 0.0 ? 4ULL : 0ULL) | (v2[a] < 0.0 ? 8ULL : 0ULL);
+        r.sg |= sg << (4 * a);
+    }
+    r.v1x = v1[0]; r.Ax = A[0]; r.iAx = iA[0];
+    r.v1y = v1[1]; r.Ay = A[1]; r.iAy = iA[1];
+    r.v1z = v1[2]; r.Az = A[2]; r.iAz = iA[2];
+    out[c] = r;
+}
+
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, const double* box, const double* por, cudaStream_t s)
+{
+    if (u.ncell <= 0) return cudaSuccess;
+    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, box, por);
+    return cudaGetLastError();
+}
+
+__global__ void k_release_explicit_usg(DevUsg u, DevState st, long long n, const int32_t* cell, const double* local,
+                                       const double* t0)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const long long c = cell[q];
+    st.t[q] = t0 ? t0[q] : 0.0;
+    if (c < 0 || c >= u.ncell) {
+        st.cell[q] = -1; st.px[q] = 0.0; st.py[q] = 0.0; st.pz[q] = 0.0;
+        st.status[q] = MP_ST_INVALID_RELEASE;
+        return;
+    }
+    const UsgCell& r = u.cell[c];
+    const double fx = fmin(fmax(local[3 * q], 0.0), 1.0);
+    const double fy = fmin(fmax(local[3 * q + 1], 0.0), 1.0);
+    const double fz = fmin(fmax(local[3 * q + 2], 0.0), 1.0);
+    st.cell[q] = (int32_t)c;
+    st.px[q] = fx * r.D[0]; st.py[q] = fy * r.D[1]; st.pz[q] = fz * r.D[2];
+    const int8_t ib = u.ibound[c];
+    st.status[q] = ib == 1 ? MP_ST_ACTIVE : (ib == 2 ? MP_ST_SINK : MP_ST_INVALID_RELEASE);
+}
+
+cudaError_t launch_release_explicit_usg(const DevUsg& u, const DevState& st, long long n, const int32_t* cell,
+                                        const double* local, const double* t0, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_release_explicit_usg<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, st, n, cell, local, t0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// tracking engine
+// ---------------------------------------------------------------------------
+
+struct UsgEngine {
+    DevUsg u;
+    Batch b;
+
+    struct State {
+        int r;
+        int c;
+        double x0, x1, x2;   // offsets (m) from the cell's low corner
+        double t;
+        unsigned steps;
+        unsigned long long h;
+        int kn;
+        int st;
+        int ef;
+        int in_sink;
+        double tev;
+    };
+
+    __device__ __forceinline__ double gx(const State& s) const { return __ldg(&u.cell[s.c].o[0]) + s.x0; }
+    __device__ __forceinline__ double gy(const State& s) const { return __ldg(&u.cell[s.c].o[1]) + s.x1; }
+    __device__ __forceinline__ double gz(const State& s) const { return __ldg(&u.cell[s.c].o[2]) + s.x2; }
+
+    __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
+                                           int st) const
+    {
+        const Req& R = b.reqs[s.r];
+        store_record(R.o.ts + (long long)kk * R.p.n + q, x, y, z, s.c, st);
+    }
+
+    __device__ __forceinline__ void final_pos(const State& s, double& x, double& y, double& z) const
+    {
+        const bool ok = s.c >= 0;
+        x = ok ? gx(s) : CUDART_NAN;
+        y = ok ? gy(s) : CUDART_NAN;
+        z = ok ? gz(s) : CUDART_NAN;
+    }
+
+    __device__ __forceinline__ double next_event(const State& s) const
+    {
+        const Req& R = b.reqs[s.r];
+        const double tk = s.kn < R.p.n_times ? __ldg(R.o.times + s.kn) : CUDART_INF;
+        return fmin(tk, R.p.t_stop);
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void load(int r, long long q, State& s) const
+    {
+        s.r = r;
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        s.c = in.cell[q];
+        s.st = in.status[q];
+        if (p.cont && s.st != MP_ST_ACTIVE) {
+            s.st = ST_SKIP;
+            return;
+        }
+        s.x0 = in.px[q]; s.x1 = in.py[q]; s.x2 = in.pz[q];
+        s.t = in.t[q];
+        s.steps = in.steps ? in.steps[q] : 0u;
+        s.h = FNV_INIT;
+        s.kn = 0;
+        s.ef = (s.steps && in.exit_face) ? (int)in.exit_face[q] : MP_FACE_NONE;
+        s.in_sink = 0;
+        if (s.c >= 0 && (long long)s.c < u.ncell) {
+            s.h = (s.steps && in.hash) ? in.hash[q] : fnv_step(s.h, s.c);
+            const int ib = __ldg(u.ibound + s.c);
+            s.in_sink = ib == 2;
+            if (s.st == MP_ST_ACTIVE) {
+                if (ib == 0 || ib == -1) s.st = MP_ST_BOUNDARY;
+                else if (ib == 2 && !p.pass_sinks) s.st = MP_ST_SINK;
+            }
+        } else {
+            s.c = -1;
+            s.st = MP_ST_INVALID_RELEASE;
+        }
+        if (TS) {
+            if (p.cont) {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) s.kn++;
+            } else {
+                while (s.kn < p.n_times && __ldg(o.times + s.kn) <= s.t) {
+                    if (s.c >= 0) record(q, s.kn, s, gx(s), gy(s), gz(s), s.st);
+                    else record(q, s.kn, s, CUDART_NAN, CUDART_NAN, CUDART_NAN, s.st);
+                    s.kn++;
+                }
+            }
+        }
+        if (s.st == MP_ST_ACTIVE && s.t >= p.t_stop) s.st = MP_ST_TIME;
+        s.tev = TS ? next_event(s) : p.t_stop;
+    }
+
+    struct RecQ {
+        double p0[RQ_CAP], p1[RQ_CAP], p2[RQ_CAP], tau[RQ_CAP];
+        long long q[RQ_CAP];
+        int c[RQ_CAP], kk[RQ_CAP], st[RQ_CAP], r[RQ_CAP];
+    };
+
+    __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
+    {
+        const Req& R = b.reqs[s.r];
+        Q.r[slot] = s.r;
+        Q.p0[slot] = s.x0; Q.p1[slot] = s.x1; Q.p2[slot] = s.x2;
+        Q.tau[slot] = __ldg(R.o.times + kk) - s.t;
+        Q.q[slot] = q;
+        Q.c[slot] = s.c;
+        Q.kk[slot] = kk; Q.st[slot] = st;
+    }
+
+    __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
+    {
+        const Req& R = b.reqs[Q.r[slot]];
+        const int c = Q.c[slot];
+        const UsgCell& k = u.cell[c];
+        const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
+        const double x = __ldg(&k.o[0]) + f64_move(__ldg(&k.Ax), __ldg(&k.iAx), __ldg(&k.D[0]),
+                                                   __ldg(&k.v1x) + __ldg(&k.Ax) * p0, p0, tau);
+        const double y = __ldg(&k.o[1]) + f64_move(__ldg(&k.Ay), __ldg(&k.iAy), __ldg(&k.D[1]),
+                                                   __ldg(&k.v1y) + __ldg(&k.Ay) * p1, p1, tau);
+        const double z = __ldg(&k.o[2]) + f64_move(__ldg(&k.Az), __ldg(&k.iAz), __ldg(&k.D[2]),
+                                                   __ldg(&k.v1z) + __ldg(&k.Az) * p2, p2, tau);
+        store_record(R.o.ts + (long long)Q.kk[slot] * R.p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
+    }
+
+    // L-infinity distance from (xa, xb) to a sub-face rectangle (0 inside)
+    __device__ __forceinline__ static double rect_dist(const UsgSub& e, double xa, double xb)
+    {
+        const double da = fmax(e.rect[0] - xa, xa - e.rect[1]);
+        const double db = fmax(e.rect[2] - xb, xb - e.rect[3]);
+        return fmax(fmax(da, db), 0.0);
+    }
+
+    // the neighbour across face (ax, side) at the exit point (xa, xb): the
+    // first sub-face holding it (else the nearest, first on ties) if its flow
+    // runs with the crossing, else the nearest one whose flow does, the point
+    // moved onto it; -1: no sub-face (outside)
+    __device__ __forceinline__ int across(int c, int ax, int side, double& xa, double& xb) const
+    {
+        const int fi = 2 * ax + (side > 0 ? 1 : 0);
+        const long long e0 = __ldg(u.face_off + 6LL * c + fi), e1 = __ldg(u.face_off + 6LL * c + fi + 1);
+        if (e1 <= e0) return -1;
+        long long best = e0;
+        double bd = CUDART_INF;
+        for (long long e = e0; e < e1; ++e) {
+            const double d = rect_dist(u.sub[e], xa, xb);
+            if (d < bd) { bd = d; best = e; }
+            if (d == 0.0) break;
+        }
+        if (u.sub[best].q * (double)side > 0.0) return u.sub[best].nbr;
+        long long alt = -1;
+        double ad = CUDART_INF;
+        for (long long e = e0; e < e1; ++e) {
+            if (!(u.sub[e].q * (double)side > 0.0)) continue;
+            const double d = rect_dist(u.sub[e], xa, xb);
+            if (d < ad) { ad = d; alt = e; }
+        }
+        if (alt < 0) return u.sub[best].nbr;
+        const UsgSub& e = u.sub[alt];
+        xa = fmin(fmax(xa, e.rect[0]), e.rect[1]);
+        xb = fmin(fmax(xb, e.rect[2]), e.rect[3]);
+        return e.nbr;
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void step(long long q, State& s, bool live, RecQ& Q, int& qcount) const
+    {
+        const Req& R = b.reqs[s.r];
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        enum { P_NONE, P_CROSS, P_TIME, P_NOEXIT, P_CAPTURE };
+        int path = P_NONE;
+        int m = 0;
+        double v1[3] = {0, 0, 0}, A[3] = {0, 0, 0}, iA[3] = {0, 0, 0}, D[3] = {1, 1, 1}, org[3] = {0, 0, 0};
+        double vp[3] = {0, 0, 0}, tmin = 0, t_end = 0;
+        int fc[3] = {0, 0, 0}, ax = -1;
+        if (live) {
+            if ((long long)s.steps >= p.max_steps) {
+                s.st = MP_ST_STEP_CAP;
+            } else if ((unsigned long long)s.c >= (unsigned long long)u.ncell) {
+                atomicCAS(o.counters + COUNTER_ERR, 0ULL, (unsigned long long)q + 1ULL);
+                s.st = MP_ST_INVALID_RELEASE;
+            } else {
+                const double2* rp = reinterpret_cast<const double2*>(u.cell + s.c);
+                const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
+                              r4 = __ldg(rp + 4), r5 = __ldg(rp + 5), r6 = __ldg(rp + 6), r7 = __ldg(rp + 7);
+                v1[0] = r0.x; A[0] = r0.y; iA[0] = r1.x; v1[1] = r1.y; A[1] = r2.x; iA[1] = r2.y;
+                v1[2] = r3.x; A[2] = r3.y; iA[2] = r4.x;
+                const unsigned long long sg = (unsigned long long)__double_as_longlong(r4.y);
+                org[0] = r5.x; org[1] = r5.y; org[2] = r6.x; D[0] = r6.y; D[1] = r7.x; D[2] = r7.y;
+                const double pp[3] = {s.x0, s.x1, s.x2};
+                double te[3];
+                #pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    vp[a] = v1[a] + A[a] * pp[a];
+                    te[a] = f64_exit_time(A[a], iA[a], D[a], vp[a], pp[a], (sg >> (4 * a + 2)) & 1ULL,
+                                          (sg >> (4 * a + 1)) & 1ULL, fc[a]);
+                }
+                tmin = CUDART_INF;
+                if (fc[0] != 0 && te[0] < tmin) { tmin = te[0]; ax = 0; }
+                if (fc[1] != 0 && te[1] < tmin) { tmin = te[1]; ax = 1; }
+                if (fc[2] != 0 && te[2] < tmin) { tmin = te[2]; ax = 2; }
+                s.steps++;
+                t_end = s.t + tmin;
+                if (ax < 0 && s.in_sink) path = P_CAPTURE;
+                else if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
+                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                else path = P_CROSS;
+                if (TS && path != P_CAPTURE && (ax < 0 || t_end >= s.tev)) {
+                    const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
+                    int kk = s.kn;
+                    while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                    m = kk - s.kn;
+                }
+            }
+        }
+        if (TS && __any_sync(0xffffffffu, m > 0)) {
+            rq_push(*this, Q, qcount, s, q, s.kn, m, path == P_NOEXIT ? MP_ST_NO_EXIT : MP_ST_ACTIVE);
+            if (m) {
+                s.kn += m;
+                s.tev = next_event(s);
+            }
+        }
+        if (path == P_NONE) return;
+        if (path == P_CAPTURE) {
+            s.st = MP_ST_SINK;
+            return;
+        }
+        if (path == P_NOEXIT) {
+            s.st = MP_ST_NO_EXIT;
+            return;
+        }
+        double pp[3] = {s.x0, s.x1, s.x2};
+        if (path == P_TIME) {
+            const double dt = p.t_stop - s.t;
+            #pragma unroll
+            for (int a = 0; a < 3; ++a) pp[a] = f64_move(A[a], iA[a], D[a], vp[a], pp[a], dt);
+            s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
+            s.t = p.t_stop;
+            s.st = MP_ST_TIME;
+            return;
+        }
+        const double dt = tmin;
+        #pragma unroll
+        for (int a = 0; a < 3; ++a)
+            pp[a] = a == ax ? (fc[a] > 0 ? D[a] : 0.0) : f64_move(A[a], iA[a], D[a], vp[a], pp[a], dt);
+        s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
+        s.t = t_end;
+        const int side = fc[ax];
+        s.ef = 2 * ax + (side > 0 ? 1 : 0);
+        // hand over at the exit point
+        double xg[3] = {org[0] + pp[0], org[1] + pp[1], org[2] + pp[2]};
+        const int oa = ax == 0 ? 1 : 0, ob = ax == 2 ? 1 : 2;
+        const int nc = across(s.c, ax, side, xg[oa], xg[ob]);
+        if (nc < 0) {
+            s.st = MP_ST_EXIT_DOMAIN;
+            return;
+        }
+        const int ib = __ldg(u.ibound + nc);
+        if (ib == 0 || ib == -1) {
+            s.st = MP_ST_BOUNDARY;
+            return;
+        }
+        if (ib == 2 && !p.pass_sinks) {
+            s.st = MP_ST_SINK;
+            return;
+        }
+        s.in_sink = ib == 2;
+        const UsgCell& n = u.cell[nc];
+        double on[3], Dn[3];
+        #pragma unroll
+        for (int a = 0; a < 3; ++a) { on[a] = __ldg(&n.o[a]); Dn[a] = __ldg(&n.D[a]); }
+        #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == ax) continue;
+            // the other axes keep their global coordinate; a hand-over that
+            // moved the point enters at the moved point
+            double pa = (xg[a] == org[a] + pp[a]) ? pp[a] + (org[a] - on[a]) : xg[a] - on[a];
+            if (pa < 0.0) pa = 0.0;
+            if (pa > Dn[a]) pa = Dn[a];
+            pp[a] = pa;
+        }
+        pp[ax] = side > 0 ? 0.0 : Dn[ax];
+        s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
+        s.c = nc;
+        s.h = fnv_step(s.h, s.c);
+    }
+
+    __device__ __forceinline__ void path_point(const State& s, double& x, double& y, double& z, double& t) const
+    {
+        x = gx(s);
+        y = gy(s);
+        z = gz(s);
+        t = s.t;
+    }
+
+    template <bool TS>
+    __device__ __forceinline__ void finish(long long q, const State& s, unsigned long long* s_cnt) const
+    {
+        const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
+        const DevOut& o = R.o;
+        const TrackParams& p = R.p;
+        const bool ok = s.c >= 0;
+        const unsigned base = in.steps ? in.steps[q] : 0u;
+        const double x = ok ? gx(s) : CUDART_NAN, y = ok ? gy(s) : CUDART_NAN, z = ok ? gz(s) : CUDART_NAN;
+        o.cell[q] = s.c;
+        o.x[q] = x; o.y[q] = y; o.z[q] = z;
+        o.px[q] = s.x0; o.py[q] = s.x1; o.pz[q] = s.x2;
+        o.t[q] = s.t;
+        o.status[q] = (uint8_t)s.st;
+        o.steps[q] = s.steps;
+        o.exit_face[q] = (uint8_t)s.ef;
+        o.hash[q] = s.h;
+        if (p.update_group && ok) {
+            in.cell[q] = s.c;
+            in.px[q] = s.x0; in.py[q] = s.x1; in.pz[q] = s.x2;
+            in.t[q] = s.t;
+            in.status[q] = (uint8_t)((s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) ? MP_ST_ACTIVE : s.st);
+            if (in.steps) {
+                in.steps[q] = s.steps;
+                in.hash[q] = s.h;
+                in.exit_face[q] = (uint8_t)s.ef;
+            }
+        }
+        count_ended(b, s.r, s.steps - base, s.st, s_cnt, p.last || !(s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP));
+    }
+};
+
+cudaError_t launch_track_usg(const DevUsg& u, const Batch& b, unsigned modes, int schedule, int block,
+                             int blocks_per_sm_cap, cudaStream_t s)
+{
+    UsgEngine e{u, b};
+    return launch_tracking(e, modes, schedule, block, blocks_per_sm_cap, s);
+}
+
+}  // namespace mp

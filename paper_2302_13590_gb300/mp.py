@@ -72,6 +72,11 @@ class TrackOpts(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("path_capacity", ctypes.c_int64)]
 
 
+class UsgDesc(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int64)] + [(k, _vp) for k in ("box", "porosity", "ibound", "face_off", "nbr",
+                                                                 "q", "rect")] + [("flags", ctypes.c_uint32)]
+
+
 class Endpoints(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ("cell", "x", "y", "z", "px", "py", "pz", "t", "status", "steps",
                                    "exit_face", "hash")]
@@ -126,6 +131,7 @@ SIGNATURES = {
     "mp_autotune": (ctypes.c_int, [_vp, _vp, _P(TrackOpts), ctypes.c_int64, _vp, _P(Tuning)]),
     "mp_set_tuning": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _P(Tuning)]),
     "mp_group_set_field": (ctypes.c_int, [_vp, _vp]),
+    "mp_usg_field_load": (ctypes.c_int, [_vp, _P(UsgDesc), _P(_vp)]),
     "mp_graph_create": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(ReleaseDesc), _P(TrackOpts), _vp, _P(_vp)]),
     "mp_graph_set_release": (ctypes.c_int, [_vp, ctypes.c_int, _P(ReleaseDesc), _vp]),
     "mp_graph_launch": (ctypes.c_int, [_vp, _vp]),
@@ -224,6 +230,17 @@ def mp_field_load(ctx, field, device_arrays: bool = False):
                   MP_DEVICE_PTR if device_arrays else 0)
     h = ctypes.c_void_p()
     _check(load_library().mp_field_load(ctx, ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def mp_usg_field_load(ctx, u):
+    """Load a rectangular unstructured grid (an object with box, porosity,
+    ibound, face_off, nbr, q, rect; see inputs.usg.UsgField)."""
+    arrs = [_host(u.box, np.float64), _host(u.porosity, np.float64), _host(u.ibound, np.int8),
+            _host(u.face_off, np.int64), _host(u.nbr, np.int32), _host(u.q, np.float64), _host(u.rect, np.float64)]
+    d = UsgDesc(int(arrs[0].size // 6), *[_ptr(a) for a in arrs], 0)
+    h = ctypes.c_void_p()
+    _check(load_library().mp_usg_field_load(ctx, ctypes.byref(d), ctypes.byref(h)))
     return h
 
 
@@ -493,6 +510,8 @@ class Context:
         self.close()
 
     def field(self, f, device_arrays=False):
+        if hasattr(f, "face_off"):
+            return mp_usg_field_load(self.h, f)
         return mp_field_load(self.h, f, device_arrays=device_arrays)
 
     def release_box(self, fh, n, lo, hi, seed, id_offset=0, stream=None):
