@@ -37,6 +37,7 @@ UNIT = "cell-steps/s"
 WORKLOAD = ("200x200x20 cells (5x5x1 m), lnK N(-9.2,1) exp. cov. (10,10,2) cells, porosity 0.3, CH west/east, "
             "PCG head solve; 1e6 particles on the west face of column 1; endpoint + timeseries at 50 log times")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+SEED_QUADTREE = 0x2302135906
 
 
 # Algorithmic work per cell-step (one exit-time evaluation), FP64 form, as
@@ -490,6 +491,38 @@ def run_ours(args):
                                       "precision, endpoint mode")
         batch["graph"] = graph
 
+    quadtree = None
+    if not args.no_quadtree:
+        # the second grid shape (TC2's quadtree refinement): FP64 tracking on
+        # a rectangular unstructured grid, the same metric
+        from paper_2302_13590_gb300.inputs import usg as U
+        tq = time.perf_counter()
+        u = U.quadtree_field(10, 100, 100, seed=SEED_QUADTREE, n_wells=20, refine_frac=0.15, solver="cg")
+        gen_s = time.perf_counter() - tq
+        fu = ctx.field(u)
+        nq = 1_000_000
+        qc, qf = U.explicit_particles(u, nq, seed=SEED_QUADTREE + 1)
+        ghq = mp.mp_release_group(ctx.h, fu, cell=qc, local=qf, stream=stream)
+        kms = []
+        for rep in range(4):
+            r = ctx.track(ghq, stream=stream, precision=mp.PREC_FP64, schedule=mp.SCHED_DYNAMIC)
+            st = r.stats()
+            if rep > 0:
+                kms.append(st["kernel_ms"])
+            r.free()
+        km = float(np.mean(kms))
+        rate = st["cell_steps"] / (km / 1e3)
+        achieved = FP64_FLOPS_PER_STEP * rate / 1e12
+        quadtree = {"workload": f"quadtree: 10 x 100 x 100 base cells, 15 % of the columns and the 20 wells' "
+                                f"neighbourhoods split 2 x 2 ({u.ncell} cells, {u.nsub} sub-faces), lnK variance 1, "
+                                f"1e6 particles in the western fifth, endpoint mode, FP64",
+                    "cell_steps_per_s": rate, "particles_per_s": nq / (km / 1e3), "kernel_ms": km,
+                    "cell_steps": st["cell_steps"], "field_generation_s": gen_s,
+                    "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell_step": FP64_FLOPS_PER_STEP}}
+        mp.mp_group_free(ghq)
+        mp.mp_field_free(fu)
+
     serving = None
     if not args.no_serve:
         from paper_2302_13590_gb300 import serve as SV
@@ -527,6 +560,7 @@ def run_ours(args):
         "status_counts": f64["status_counts"],
         "serving": serving,
         "batch": batch,
+        "quadtree": quadtree,
         "tuning": tuning or None,
     }
     print(json.dumps(line), flush=True)
@@ -552,6 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-quadtree", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
