@@ -428,6 +428,7 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     size_t off = 0;
     const size_t o_cell = off; off = align256(off + sizeof(mp::UsgCell) * (size_t)nc);
+    const size_t o_geo = off; off = align256(off + sizeof(mp::UsgGeo) * (size_t)nc);
     const size_t o_fo = off; off = align256(off + sizeof(long long) * (size_t)(6 * nc + 1));
     const size_t o_sub = off; off = align256(off + sizeof(mp::UsgSub) * (size_t)std::max(ns, 1LL));
     const size_t o_ib = off; off = align256(off + (size_t)nc);
@@ -450,6 +451,7 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     u.ncell = nc;
     u.nsub = ns;
     u.cell = reinterpret_cast<mp::UsgCell*>(buf + o_cell);
+    u.geo = reinterpret_cast<mp::UsgGeo*>(buf + o_geo);
     u.face_off = reinterpret_cast<long long*>(buf + o_fo);
     u.sub = reinterpret_cast<mp::UsgSub*>(buf + o_sub);
     u.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
@@ -460,8 +462,9 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_box, d->box, sizeof(double) * 6 * (size_t)nc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_por, d->porosity, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = mp::launch_build_usg(u, const_cast<mp::UsgCell*>(u.cell), reinterpret_cast<double*>(buf + o_box),
-                                 reinterpret_cast<double*>(buf + o_por), nullptr);
+        e = mp::launch_build_usg(u, const_cast<mp::UsgCell*>(u.cell), const_cast<mp::UsgGeo*>(u.geo),
+                                 reinterpret_cast<double*>(buf + o_box), reinterpret_cast<double*>(buf + o_por),
+                                 nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(buf);

@@ -300,27 +300,9 @@ struct F64Engine {
         return a == 0 ? x : (a == 1 ? y : z);
     }
 
-    // FP32 estimate of an exit time from the exact FP64 distance d and
-    // particle velocity vp.  Relative error: the two conversions and the
-    // approximate division give ~5e-7 on t1 = d / vp and on z = A t1;
-    // g(z) = ln(1 + z) / z is evaluated by its series (|z| < 2^-7), by
-    // log1pf, or for z < -1/2 by ln(u_exit / vp) (the ratio, not 1 + z,
-    // carries the information there), which keeps its error below ~1.5e-6;
-    // in all, below ~3e-6.  Velocities too small for FP32 (|vp| < 1e-30) or
-    // a NaN mark the estimate as untrusted.
     __device__ __forceinline__ static float estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
     {
-        const float vf = (float)vp;
-        const float vs = face ? vf : 1.0f;
-        const float t1 = __fdividef((float)d, vs);
-        const float z = fA * t1;
-        float g;
-        if (fabsf(z) < 0.0078125f) g = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
-        else if (z < -0.5f) g = __fdividef(logf(__fdividef(fue, vs)), z);
-        else g = __fdividef(log1pf(z), z);
-        const float e = t1 * g;
-        unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(e == e));
-        return face ? e : CUDART_INF_F;
+        return f32_estimate(face, d, vp, fA, fue, unsafe);
     }
 
     __device__ __forceinline__ static double move(double A, double iA, double D, double vp, double pp, double dt)

@@ -179,21 +179,21 @@ cudaError_t launch_validate(const double* qx, long long nqx, const double* qy, l
                             long long nqz, const double* por, const int8_t* ib, long long ncell, unsigned* flags,
                             cudaStream_t s);
 // Rectangular unstructured grid (device form, built by mp_usg_field_load):
-//   cell[c]  128 B {v1x, Ax, iAx, v1y, Ay, iAy, v1z, Az, iAz, signs, origin, sizes}:
-//            Pollock velocities from each face's total flow (sub-faces
-//            summed in list order), the face-velocity sign bits as in nb
-//            (bits 4a .. 4a + 3: v1 > 0, v1 < 0, v2 > 0, v2 < 0), the low
-//            corner and the sizes of the box
+//   cell[c]  128 B, the layout of CellF64: {v1x, Ax, iAx, v1y, Ay, iAy, v1z,
+//            Az, iAz, sg, FP32 copies of v1, v2, A}: Pollock velocities from
+//            each face's total flow (sub-faces summed in list order); sg
+//            holds the face-velocity sign bits (bits 4a .. 4a + 3: v1 > 0,
+//            v1 < 0, v2 > 0, v2 < 0)
+//   geo[c]   48 B {low corner, sizes} of the box
 //   face_off[6 c + f] .. face_off[6 c + f + 1] - 1: sub-faces of face f
 //   sub[e]   48 B {neighbour (-1 outside), flow along +axis, rectangle in
 //            the two other axes (lo_a, hi_a, lo_b, hi_b)}
-struct __align__(16) UsgCell {
-    double v1x, Ax, iAx, v1y, Ay, iAy, v1z, Az, iAz;
-    unsigned long long sg;
+using UsgCell = CellF64;
+
+struct __align__(16) UsgGeo {
     double o[3];
     double D[3];
 };
-static_assert(sizeof(UsgCell) == 128, "UsgCell is one 128-byte line");
 
 struct __align__(16) UsgSub {
     int nbr;
@@ -206,12 +206,14 @@ struct DevUsg {
     long long ncell;
     long long nsub;
     const UsgCell* cell;
+    const UsgGeo* geo;
     const long long* face_off;
     const UsgSub* sub;
     const int8_t* ibound;
 };
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, const double* box, const double* por, cudaStream_t s);
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, const double* box, const double* por,
+                             cudaStream_t s);
 cudaError_t launch_release_explicit_usg(const DevUsg& u, const DevState& st, long long n, const int32_t* cell,
                                         const double* local, const double* t0, cudaStream_t s);
 cudaError_t launch_track_usg(const DevUsg& u, const Batch& b, unsigned modes, int schedule, int block,

@@ -37,13 +37,13 @@ __device__ __forceinline__ double usg_face_flow(const DevUsg& u, long long c, in
     return s;
 }
 
-__global__ void k_build_usg(DevUsg u, UsgCell* out, const double* box, const double* por)
+__global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, const double* box, const double* por)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= u.ncell) return;
     const double* b = box + 6 * c;
-    UsgCell r{};
-    for (int a = 0; a < 3; ++a) { r.o[a] = b[a]; r.D[a] = b[3 + a]; }
+    UsgGeo gm{};
+    for (int a = 0; a < 3; ++a) { gm.o[a] = b[a]; gm.D[a] = b[3 + a]; }
     const int8_t ib = u.ibound[c];
     double v1[3] = {0.0, 0.0, 0.0}, v2[3] = {0.0, 0.0, 0.0};
     if (ib == 1 || ib == 2) {
@@ -56,23 +56,31 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, const double* box, const dou
         }
     }
     double A[3], iA[3];
+    UsgCell r{};
+    unsigned long long sg = 0;
     for (int a = 0; a < 3; ++a) {
         A[a] = (v2[a] - v1[a]) / b[3 + a];
         iA[a] = A[a] != 0.0 ? 1.0 / A[a] : 0.0;
-        const unsigned long long sg = (v1[a] > 0.0 ? 1ULL : 0ULL) | (v1[a] < 0.0 ? 2ULL : 0ULL) |
-                                      (v2[a] > 0.0 ? 4ULL : 0ULL) | (v2[a] < 0.0 ? 8ULL : 0ULL);
-        r.sg |= sg << (4 * a);
+        const unsigned long long bits4 = (v1[a] > 0.0 ? 1ULL : 0ULL) | (v1[a] < 0.0 ? 2ULL : 0ULL) |
+                                         (v2[a] > 0.0 ? 4ULL : 0ULL) | (v2[a] < 0.0 ? 8ULL : 0ULL);
+        sg |= bits4 << (4 * a);
     }
     r.v1x = v1[0]; r.Ax = A[0]; r.iAx = iA[0];
     r.v1y = v1[1]; r.Ay = A[1]; r.iAy = iA[1];
     r.v1z = v1[2]; r.Az = A[2]; r.iAz = iA[2];
+    r.nb = sg;
+    r.fv1x = (float)v1[0]; r.fv2x = (float)v2[0]; r.fAx = (float)A[0];
+    r.fv1y = (float)v1[1]; r.fv2y = (float)v2[1]; r.fAy = (float)A[1];
+    r.fv1z = (float)v1[2]; r.fv2z = (float)v2[2]; r.fAz = (float)A[2];
     out[c] = r;
+    geo[c] = gm;
 }
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, const double* box, const double* por, cudaStream_t s)
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, const double* box, const double* por,
+                             cudaStream_t s)
 {
     if (u.ncell <= 0) return cudaSuccess;
-    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, box, por);
+    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, geo, box, por);
     return cudaGetLastError();
 }
 
@@ -88,7 +96,7 @@ __global__ void k_release_explicit_usg(DevUsg u, DevState st, long long n, const
         st.status[q] = MP_ST_INVALID_RELEASE;
         return;
     }
-    const UsgCell& r = u.cell[c];
+    const UsgGeo& r = u.geo[c];
     const double fx = fmin(fmax(local[3 * q], 0.0), 1.0);
     const double fy = fmin(fmax(local[3 * q + 1], 0.0), 1.0);
     const double fz = fmin(fmax(local[3 * q + 2], 0.0), 1.0);
@@ -128,9 +136,9 @@ struct UsgEngine {
         double tev;
     };
 
-    __device__ __forceinline__ double gx(const State& s) const { return __ldg(&u.cell[s.c].o[0]) + s.x0; }
-    __device__ __forceinline__ double gy(const State& s) const { return __ldg(&u.cell[s.c].o[1]) + s.x1; }
-    __device__ __forceinline__ double gz(const State& s) const { return __ldg(&u.cell[s.c].o[2]) + s.x2; }
+    __device__ __forceinline__ double gx(const State& s) const { return __ldg(&u.geo[s.c].o[0]) + s.x0; }
+    __device__ __forceinline__ double gy(const State& s) const { return __ldg(&u.geo[s.c].o[1]) + s.x1; }
+    __device__ __forceinline__ double gz(const State& s) const { return __ldg(&u.geo[s.c].o[2]) + s.x2; }
 
     __device__ __forceinline__ void record(long long q, int kk, const State& s, double x, double y, double z,
                                            int st) const
@@ -224,12 +232,13 @@ struct UsgEngine {
         const Req& R = b.reqs[Q.r[slot]];
         const int c = Q.c[slot];
         const UsgCell& k = u.cell[c];
+        const UsgGeo& g = u.geo[c];
         const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
-        const double x = __ldg(&k.o[0]) + f64_move(__ldg(&k.Ax), __ldg(&k.iAx), __ldg(&k.D[0]),
+        const double x = __ldg(&g.o[0]) + f64_move(__ldg(&k.Ax), __ldg(&k.iAx), __ldg(&g.D[0]),
                                                    __ldg(&k.v1x) + __ldg(&k.Ax) * p0, p0, tau);
-        const double y = __ldg(&k.o[1]) + f64_move(__ldg(&k.Ay), __ldg(&k.iAy), __ldg(&k.D[1]),
+        const double y = __ldg(&g.o[1]) + f64_move(__ldg(&k.Ay), __ldg(&k.iAy), __ldg(&g.D[1]),
                                                    __ldg(&k.v1y) + __ldg(&k.Ay) * p1, p1, tau);
-        const double z = __ldg(&k.o[2]) + f64_move(__ldg(&k.Az), __ldg(&k.iAz), __ldg(&k.D[2]),
+        const double z = __ldg(&g.o[2]) + f64_move(__ldg(&k.Az), __ldg(&k.iAz), __ldg(&g.D[2]),
                                                    __ldg(&k.v1z) + __ldg(&k.Az) * p2, p2, tau);
         store_record(R.o.ts + (long long)Q.kk[slot] * R.p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
     }
@@ -294,23 +303,62 @@ struct UsgEngine {
             } else {
                 const double2* rp = reinterpret_cast<const double2*>(u.cell + s.c);
                 const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
-                              r4 = __ldg(rp + 4), r5 = __ldg(rp + 5), r6 = __ldg(rp + 6), r7 = __ldg(rp + 7);
+                              r4 = __ldg(rp + 4);
+                const float4* rf = reinterpret_cast<const float4*>(rp + 5);
+                const float4 g0 = __ldg(rf + 0), g1 = __ldg(rf + 1), g2 = __ldg(rf + 2);
+                const double2* gp = reinterpret_cast<const double2*>(u.geo + s.c);
+                const double2 q0 = __ldg(gp + 0), q1 = __ldg(gp + 1), q2 = __ldg(gp + 2);
                 v1[0] = r0.x; A[0] = r0.y; iA[0] = r1.x; v1[1] = r1.y; A[1] = r2.x; iA[1] = r2.y;
                 v1[2] = r3.x; A[2] = r3.y; iA[2] = r4.x;
                 const unsigned long long sg = (unsigned long long)__double_as_longlong(r4.y);
-                org[0] = r5.x; org[1] = r5.y; org[2] = r6.x; D[0] = r6.y; D[1] = r7.x; D[2] = r7.y;
+                org[0] = q0.x; org[1] = q0.y; org[2] = q1.x; D[0] = q1.y; D[1] = q2.x; D[2] = q2.y;
                 const double pp[3] = {s.x0, s.x1, s.x2};
-                double te[3];
+                bool p2[3], n1[3];
                 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     vp[a] = v1[a] + A[a] * pp[a];
-                    te[a] = f64_exit_time(A[a], iA[a], D[a], vp[a], pp[a], (sg >> (4 * a + 2)) & 1ULL,
-                                          (sg >> (4 * a + 1)) & 1ULL, fc[a]);
+                    p2[a] = (sg >> (4 * a + 2)) & 1ULL;
+                    n1[a] = (sg >> (4 * a + 1)) & 1ULL;
+                    fc[a] = (gt0(vp[a]) && p2[a]) ? 1 : ((lt0(vp[a]) && n1[a]) ? -1 : 0);
                 }
+                // FP32 estimates of the three exit times; the exact FP64 time
+                // of the leading one, and of every axis within 2^-10 of it
+                // or with an untrusted estimate (the same exit axis and time
+                // as evaluating all three exactly)
+                bool u0, u1, u2;
+                const float e0 = f32_estimate(fc[0], fc[0] > 0 ? D[0] - pp[0] : -pp[0], vp[0], g0.z,
+                                              fc[0] > 0 ? g0.y : g0.x, u0);
+                const float e1 = f32_estimate(fc[1], fc[1] > 0 ? D[1] - pp[1] : -pp[1], vp[1], g1.y,
+                                              fc[1] > 0 ? g1.x : g0.w, u1);
+                const float e2 = f32_estimate(fc[2], fc[2] > 0 ? D[2] - pp[2] : -pp[2], vp[2], g2.x,
+                                              fc[2] > 0 ? g1.w : g1.z, u2);
+                float em = CUDART_INF_F;
+                int a0 = -1;
+                if (fc[0] && !u0 && e0 < em) { em = e0; a0 = 0; }
+                if (fc[1] && !u1 && e1 < em) { em = e1; a0 = 1; }
+                if (fc[2] && !u2 && e2 < em) { em = e2; a0 = 2; }
+                const float thr = em * (1.0f + 0.0009765625f);
+                const unsigned cand = ((fc[0] && (u0 || e0 <= thr)) ? 1u : 0u) | ((fc[1] && (u1 || e1 <= thr)) ? 2u : 0u) |
+                                      ((fc[2] && (u2 || e2 <= thr)) ? 4u : 0u);
+                if (a0 < 0 && cand) a0 = __ffs(cand) - 1;
                 tmin = CUDART_INF;
-                if (fc[0] != 0 && te[0] < tmin) { tmin = te[0]; ax = 0; }
-                if (fc[1] != 0 && te[1] < tmin) { tmin = te[1]; ax = 1; }
-                if (fc[2] != 0 && te[2] < tmin) { tmin = te[2]; ax = 2; }
+                if (a0 >= 0) {
+                    int fa;
+                    const double te = f64_exit_time(A[a0], iA[a0], D[a0], vp[a0], pp[a0], p2[a0], n1[a0], fa);
+                    tmin = te;
+                    ax = a0;
+                    if ((cand & ~(1u << a0)) || is_nan(te)) {
+                        double te3[3];
+                        int fx;
+                        #pragma unroll
+                        for (int a = 0; a < 3; ++a) te3[a] = f64_exit_time(A[a], iA[a], D[a], vp[a], pp[a], p2[a], n1[a], fx);
+                        tmin = CUDART_INF;
+                        ax = -1;
+                        if (fc[0] != 0 && te3[0] < tmin) { tmin = te3[0]; ax = 0; }
+                        if (fc[1] != 0 && te3[1] < tmin) { tmin = te3[1]; ax = 1; }
+                        if (fc[2] != 0 && te3[2] < tmin) { tmin = te3[2]; ax = 2; }
+                    }
+                }
                 s.steps++;
                 t_end = s.t + tmin;
                 if (ax < 0 && s.in_sink) path = P_CAPTURE;
@@ -351,10 +399,15 @@ struct UsgEngine {
             s.st = MP_ST_TIME;
             return;
         }
+        // the two other axes move (two slots, uniform across lanes), the exit
+        // axis is put on its face
         const double dt = tmin;
-        #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            pp[a] = a == ax ? (fc[a] > 0 ? D[a] : 0.0) : f64_move(A[a], iA[a], D[a], vp[a], pp[a], dt);
+        const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+        const double n1v = f64_move(A[a1], iA[a1], D[a1], vp[a1], pp[a1], dt);
+        const double n2v = f64_move(A[a2], iA[a2], D[a2], vp[a2], pp[a2], dt);
+        pp[a1] = n1v;
+        pp[a2] = n2v;
+        pp[ax] = fc[ax] > 0 ? D[ax] : 0.0;
         s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
         s.t = t_end;
         const int side = fc[ax];
@@ -377,7 +430,7 @@ struct UsgEngine {
             return;
         }
         s.in_sink = ib == 2;
-        const UsgCell& n = u.cell[nc];
+        const UsgGeo& n = u.geo[nc];
         double on[3], Dn[3];
         #pragma unroll
         for (int a = 0; a < 3; ++a) { on[a] = __ldg(&n.o[a]); Dn[a] = __ldg(&n.D[a]); }
