@@ -63,8 +63,8 @@ BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # the output records, both in proportion to the particle count.  It holds
 # only for the kernel sources it was taken from (their hash below);
 # otherwise the bench reports traffic as null.
-TRAFFIC = {"src": "a8469d6be6e414b4", "fp64": 5 * (353.340928e6 + 307.202816e6),
-           "mixed": 5 * (46.633472e6 + 290.423040e6)}
+TRAFFIC = {"src": "a44adb23dffa27c4", "fp64": 5 * (352.326400e6 + 306.868480e6),
+           "mixed": 5 * (46.994688e6 + 290.419712e6)}
 
 
 def kernel_src_hash() -> str:
@@ -213,6 +213,39 @@ def run_reference(args):
             "cpu_baseline": {**vals[-1], "value": value},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_quadtree(ctx, stream) -> dict:
+    """The second grid shape (TC2's quadtree refinement): FP64 tracking on a
+    rectangular unstructured grid, the same metric."""
+    from paper_2302_13590_gb300.inputs import usg as U
+    tq = time.perf_counter()
+    u = U.quadtree_field(10, 100, 100, seed=SEED_QUADTREE, n_wells=20, refine_frac=0.15, solver="cg")
+    gen_s = time.perf_counter() - tq
+    fu = ctx.field(u)
+    nq = 1_000_000
+    qc, qf = U.explicit_particles(u, nq, seed=SEED_QUADTREE + 1)
+    ghq = mp.mp_release_group(ctx.h, fu, cell=qc, local=qf, stream=stream)
+    kms = []
+    for rep in range(4):
+        r = ctx.track(ghq, stream=stream, precision=mp.PREC_FP64, schedule=mp.SCHED_DYNAMIC)
+        st = r.stats()
+        if rep > 0:
+            kms.append(st["kernel_ms"])
+        r.free()
+    km = float(np.mean(kms))
+    rate = st["cell_steps"] / (km / 1e3)
+    achieved = FP64_FLOPS_PER_STEP * rate / 1e12
+    quadtree = {"workload": f"quadtree: 10 x 100 x 100 base cells, 15 % of the columns and the 20 wells' "
+                            f"neighbourhoods split 2 x 2 ({u.ncell} cells, {u.nsub} sub-faces), lnK variance 1, "
+                            f"1e6 particles in the western fifth, endpoint mode, FP64",
+                "cell_steps_per_s": rate, "particles_per_s": nq / (km / 1e3), "kernel_ms": km,
+                "cell_steps": st["cell_steps"], "field_generation_s": gen_s,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell_step": FP64_FLOPS_PER_STEP}}
+    mp.mp_group_free(ghq)
+    mp.mp_field_free(fu)
+    return quadtree
 
 
 def run_ours(args):
@@ -491,37 +524,7 @@ def run_ours(args):
                                       "precision, endpoint mode")
         batch["graph"] = graph
 
-    quadtree = None
-    if not args.no_quadtree:
-        # the second grid shape (TC2's quadtree refinement): FP64 tracking on
-        # a rectangular unstructured grid, the same metric
-        from paper_2302_13590_gb300.inputs import usg as U
-        tq = time.perf_counter()
-        u = U.quadtree_field(10, 100, 100, seed=SEED_QUADTREE, n_wells=20, refine_frac=0.15, solver="cg")
-        gen_s = time.perf_counter() - tq
-        fu = ctx.field(u)
-        nq = 1_000_000
-        qc, qf = U.explicit_particles(u, nq, seed=SEED_QUADTREE + 1)
-        ghq = mp.mp_release_group(ctx.h, fu, cell=qc, local=qf, stream=stream)
-        kms = []
-        for rep in range(4):
-            r = ctx.track(ghq, stream=stream, precision=mp.PREC_FP64, schedule=mp.SCHED_DYNAMIC)
-            st = r.stats()
-            if rep > 0:
-                kms.append(st["kernel_ms"])
-            r.free()
-        km = float(np.mean(kms))
-        rate = st["cell_steps"] / (km / 1e3)
-        achieved = FP64_FLOPS_PER_STEP * rate / 1e12
-        quadtree = {"workload": f"quadtree: 10 x 100 x 100 base cells, 15 % of the columns and the 20 wells' "
-                                f"neighbourhoods split 2 x 2 ({u.ncell} cells, {u.nsub} sub-faces), lnK variance 1, "
-                                f"1e6 particles in the western fifth, endpoint mode, FP64",
-                    "cell_steps_per_s": rate, "particles_per_s": nq / (km / 1e3), "kernel_ms": km,
-                    "cell_steps": st["cell_steps"], "field_generation_s": gen_s,
-                    "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_cell_step": FP64_FLOPS_PER_STEP}}
-        mp.mp_group_free(ghq)
-        mp.mp_field_free(fu)
+    quadtree = None if args.no_quadtree else run_quadtree(ctx, stream)
 
     serving = None
     if not args.no_serve:
@@ -587,6 +590,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
+    ap.add_argument("--only-quadtree", action="store_true", help="run the quadtree line alone (profiling)")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
@@ -595,6 +599,14 @@ def main():
     ap.add_argument("--traffic-mixed", type=float, default=None,
                     help="ncu dram bytes per full launch of the mixed kernel (from profiles/)")
     args = ap.parse_args()
+    if args.only_quadtree:
+        import torch
+        torch.cuda.set_device(0)
+        ctx = mp.Context(0)
+        stream = torch.cuda.Stream()
+        print(json.dumps({"quadtree": run_quadtree(ctx, stream)}), flush=True)
+        ctx.close()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
