@@ -218,6 +218,7 @@ def run_reference(args):
 def run_quadtree(ctx, stream) -> dict:
     """The second grid shape (TC2's quadtree refinement): FP64 tracking on a
     rectangular unstructured grid, the same metric."""
+    from paper_2302_13590_gb300 import mp
     from paper_2302_13590_gb300.inputs import usg as U
     tq = time.perf_counter()
     u = U.quadtree_field(10, 100, 100, seed=SEED_QUADTREE, n_wells=20, refine_frac=0.15, solver="cg")
@@ -601,6 +602,7 @@ def main():
     args = ap.parse_args()
     if args.only_quadtree:
         import torch
+        from paper_2302_13590_gb300 import mp
         torch.cuda.set_device(0)
         ctx = mp.Context(0)
         stream = torch.cuda.Stream()
