@@ -53,6 +53,29 @@ __device__ __forceinline__ double frexp_bits(double u, int& e)
     return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | 0x3fe0000000000000LL);
 }
 
+// (double)e for |e| < 2^30, exactly
+__device__ __forceinline__ double i2d_exact(int e)
+{
+    if (e == 0) return 0.0;
+    const unsigned long long sgn = e < 0 ? 0x8000000000000000ULL : 0ULL;
+    const unsigned a = (unsigned)(e < 0 ? -e : e);
+    const int msb = 31 - __clz(a);
+    const unsigned long long mant = ((unsigned long long)a << (52 - msb)) & 0x000fffffffffffffULL;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb) << 52) | mant));
+}
+
+// (int)k for an integral k, saturating beyond 2^31 (as __double2int_rz)
+__device__ __forceinline__ int d2i_integral(double k)
+{
+    const long long b = bits(k);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < 0) return 0;
+    if (e >= 31) return b < 0 ? (-2147483647 - 1) : 2147483647;
+    const unsigned long long m = (unsigned long long)(b & 0x000fffffffffffffLL) | 0x0010000000000000ULL;
+    const int v = (int)(m >> (52 - e));
+    return b < 0 ? -v : v;
+}
+
 // 2^k as ldexp(1, k) gives it, k in [-2000, 2000]
 __device__ __forceinline__ double pow2i(int k)
 {
@@ -108,7 +131,7 @@ __device__ __forceinline__ double series_log1p(double x)
     p = fma(p, z2, 1.0 / 3.0);
     p = fma(p, z2, 1.0);
     const double logm = 2.0 * s * p;
-    const double de = (double)e;
+    const double de = i2d_exact(e);
     const double ru = (double)__frcp_rn((float)u);
     return de * ln2_hi + ((logm + c * ru) + de * ln2_lo);
 }
@@ -134,7 +157,7 @@ __device__ __forceinline__ double series_expm1(double w)
     p = fma(p, r, 1.0);
     const double em = r * p;
     if (eq0(k)) return em;
-    int ki = __double2int_rz(k);   // k is integral; out of range saturates
+    int ki = d2i_integral(k);   // k is integral; out of range saturates
     ki = ki > 2000 ? 2000 : (ki < -2000 ? -2000 : ki);
     const double t = pow2i(ki);
     return (t - 1.0) + t * em;
@@ -175,19 +198,33 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
     return eq0(s) ? pp : pn;
 }
 
+// FP64 -> FP32 by truncating the significand on the ALU pipe (the FP64
+// pipe, the binding unit of the FP64 kernels, is spared the conversion):
+// relative error below 2^-23; magnitudes below the FP32 normal range give
+// 0, above it (and infinities, NaN) give infinity, with the sign.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const long long b = bits(x);
+    const unsigned s = (unsigned)((unsigned long long)b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126) return __uint_as_float(s);
+    if (e > 127) return __uint_as_float(s | 0x7f800000u);
+    return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+
 // FP32 estimate of an exit time from the exact FP64 distance d and
-// particle velocity vp.  Relative error: the two conversions and the
-// approximate division give ~5e-7 on t1 = d / vp and on z = A t1;
+// particle velocity vp.  Relative error: the two truncating conversions
+// and the approximate division give ~6e-7 on t1 = d / vp and on z = A t1;
 // g(z) = ln(1 + z) / z is evaluated by its series (|z| < 2^-7), by
 // log1pf, or for z < -1/2 by ln(u_exit / vp) (the ratio, not 1 + z,
 // carries the information there), which keeps its error below ~1.5e-6;
-// in all, below ~3e-6.  Velocities too small for FP32 (|vp| < 1e-30) or
+// in all, below ~3.2e-6.  Velocities too small for FP32 (|vp| < 1e-30) or
 // a NaN mark the estimate as untrusted.
 __device__ __forceinline__ float f32_estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
 {
-    const float vf = (float)vp;
+    const float vf = f32_trunc(vp);
     const float vs = face ? vf : 1.0f;
-    const float t1 = __fdividef((float)d, vs);
+    const float t1 = __fdividef(f32_trunc(d), vs);
     const float z = fA * t1;
     float g;
     if (fabsf(z) < 0.0078125f) g = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
