@@ -78,21 +78,27 @@ class Server:
     """Continuous-batching request loop over loaded fields.
 
     fields: name -> mp field handle.  precision / schedule apply to every
-    request.  memory_budget: bytes that requests in flight may hold.
+    request.  memory_budget: bytes that requests in flight may hold; by
+    default the given share of the device memory free when the server
+    starts (admission by free device memory).
     """
 
     def __init__(self, ctx: mp.Context, fields: Dict[str, object], precision=mp.PREC_MIXED,
                  schedule=mp.SCHED_STATIC, n_streams: int = 4, max_inflight: int = 256,
-                 memory_budget: int = 64 << 30, keep_results: Optional[set] = None, torch_mod=None):
+                 memory_budget: Optional[int] = None, free_share: float = 0.8,
+                 keep_results: Optional[set] = None, torch_mod=None):
         self.ctx = ctx
         self.fields = fields
         self.precision = precision
         self.schedule = schedule
         self.max_inflight = max_inflight
-        self.budget = memory_budget
         self.keep = keep_results or set()
         if torch_mod is None:
-            import torch as torch_mod  # streams only
+            import torch as torch_mod  # streams and the free-memory query only
+        if memory_budget is None:
+            free, _ = torch_mod.cuda.mem_get_info()
+            memory_budget = int(free_share * free)
+        self.budget = memory_budget
         self.streams = [torch_mod.cuda.Stream() for _ in range(n_streams)]
         self._next_stream = 0
 

@@ -24,6 +24,9 @@ def test_served_results_equal_alone(setup, precision):
     torch, ctx, fields = setup
     specs = I.serving_workload(n_req=30, rate_hz=2000.0, n_min=1e2, n_max=2e4, seed=91)
     srv = S.Server(ctx, fields, precision=precision, max_inflight=6, keep_results={id(s) for s in specs})
+    # the default budget is a share of the free device memory
+    free, total = torch.cuda.mem_get_info()
+    assert 0 < srv.budget <= total and abs(srv.budget - 0.8 * free) <= 0.05 * total
     rep = srv.run(specs, realtime=True)
     summ = rep.summary()
     assert summ["requests"] == 30 and summ["p50_ms"] <= summ["p99_ms"]
