@@ -46,13 +46,13 @@ SEED_QUADTREE = 0x2302135906
 # cell, not the step).  Counting FP64 add/mul/compare as 1 flop, an FMA as
 # 2 and an IEEE division as 10 (reciprocal seed, two Newton steps and a
 # remainder correction):
-#   log1p: 17 add/mul/compare + 13 FMA + 1 division             =  54
-#   expm1: 12 add/mul/compare + 14 FMA                          =  40
-#   exit time, 3 axes: (10 add/mul/compare + 1 div + log1p) x 3 = 222
+#   log1p (bucket table, series to r^8): 8 add/mul + 10 FMA     =  28
+#   expm1 (32-entry table, series to r^7): 1 mul + 11 FMA       =  23
+#   exit time, 3 axes: (10 add/mul/compare + 1 div + log1p) x 3 = 144
 #   smallest time, step end, stop test                          =   5
-#   motion, 2 axes: (11 add/mul/compare + expm1) x 2            = 102
-#   total                                                       = 329 flops.
-FP64_FLOPS_PER_STEP = 329.0
+#   motion, 2 axes: (11 add/mul/compare + expm1) x 2            =  68
+#   total                                                       = 217 flops.
+FP64_FLOPS_PER_STEP = 217.0
 # Bytes per cell-step an ideal gather needs: FP64 field 6 x 8 (face flows) +
 # 8 (porosity) + 1 (neighbour ibound) = 57 B; FP32 field copy 6 x 4 + 4 + 1.
 BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}

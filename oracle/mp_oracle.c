@@ -135,62 +135,126 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
     return h;
 }
 
-/* ---- log1p and expm1 from their series --------------------------------
- * Both are evaluated with IEEE additions, multiplications, divisions and
- * fused multiply-adds (C99 fma, one rounding) only, plus the exact
- * frexp/ldexp/rint and one FP32 reciprocal, in a fixed order, so that any
- * other implementation of the same steps produces the same bits.  Accuracy
- * (pinned against the C library in the tests): within a few ulp.
+/* ---- log1p and expm1: argument reduction, a table, a short series ------
+ * Both are evaluated with IEEE additions, multiplications and fused
+ * multiply-adds (C99 fma, one rounding), exact bit operations on the
+ * representation, one FP32 reciprocal and FP32 products, in a fixed order,
+ * so that any other implementation of the same steps produces the same
+ * bits.  The tables (orc_tables.h, written by gen_tables.py) hold correctly
+ * rounded constants.  Accuracy (pinned against the C library in the tests):
+ * within a few ulp.
  *
  * log1p(x): u = 1 + x rounded, c = the rounding error of that sum (exact by
- * the two-sum argument), u = m 2^e with m in [1/sqrt2, sqrt2), f = m - 1
- * (exact), log(1 + f) = 2 atanh(s) with s = f / (2 + f), |s| < 0.1716:
- * 2 s (1 + s^2/3 + s^4/5 + ... + s^24/25) by Horner's rule with fma;
- * log1p(x) = e ln2 + log(1 + f) + c / u, ln 2 split in a high part exact in
- * products with e and a low part; c is below half an ulp of u, so c / u is
- * taken as c times the FP32 reciprocal of u.
+ * the two-sum argument); u = m 2^e with m in [1/sqrt2, sqrt2); the bucket of
+ * m (its exponent and top 8 fraction bits) gives R, an 8-bit approximation
+ * of 1/m, and -ln R = Lh + Ll; r = m R - 1 is exact (one fma: a multiple of
+ * 2^-60 below 2^-7); ln(1 + r) = r - r^2/2 + ... - r^8/8 (|r| < 0.006);
+ * log1p(x) = (e ln2_hi + Lh) + ((ln(1 + r) + c / u) + (e ln2_lo + Ll)), the
+ * first sum exact (both terms are multiples of 2^-32), c / u taken as c
+ * times the FP32 reciprocal of u (c is below half an ulp of u).
+ * u = +inf gives +inf, u = 0 gives -inf, a NaN gives NaN.
  *
- * expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
- * r = w - k ln2 (split as above), expm1(r) = r + r^2/2! + ... + r^14/14!
- * (|r| <= 0.347), expm1(w) = (2^k - 1) + 2^k expm1(r); 2^k is formed with
- * k limited to [-2000, 2000] (the same 2^k, 0 or infinity, for every k).
+ * expm1(w): |w| limited to 800 (beyond, the result is -1 or +inf either
+ * way); k = nearest integer to w 32/ln2, evaluated in FP32 on the
+ * significand-truncated w (any nearby integer is a valid reduction);
+ * j = k mod 32, m = (k - j)/32; r = (w - k ln2_hi/32) - k ln2_lo/32 (the
+ * first product and difference exact); expm1(r) = r + r^2 (1/2 + r/6 + ...
+ * + r^5/5040) (|r| < 0.0109); 2^(j/32) = Th + Tl; S = Th expm1(r) + Tl;
+ * expm1(w) = (2^m Th - 1) + 2^m S, and for m > 1023 (2^m not finite)
+ * ((Th + S) 2^(m - 1023)) 2^1023.
  */
-static const double ORC_LN2_HI = 6.93147180369123816490e-01;
+#include "orc_tables.h"
+
+static const double ORC_LN2_HI = 6.93147180369123816490e-01;   /* a multiple of 2^-32 */
 static const double ORC_LN2_LO = 1.90821492927058770002e-10;
+
+static double orc_from_bits(uint64_t b)
+{
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+static uint64_t orc_bits(double v)
+{
+    uint64_t b;
+    memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+/* FP64 -> FP32 with the significand truncated (magnitudes below the FP32
+ * normal range -> signed 0, above it -> signed infinity) */
+static float orc_f32_trunc(double x)
+{
+    uint64_t b = orc_bits(x);
+    uint32_t sgn = (uint32_t)(b >> 63) << 31;
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    uint32_t f;
+    if (e < -126) f = sgn;
+    else if (e > 127) f = sgn | 0x7f800000u;
+    else f = sgn | ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffff);
+    float v;
+    memcpy(&v, &f, sizeof v);
+    return v;
+}
 
 double orc_log1p(double x)
 {
     double u = 1.0 + x;
+    if (!(u > 0.0) || u == INFINITY) return u == 0.0 ? -INFINITY : (u == INFINITY ? INFINITY : NAN);
     double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
     int e;
     double m = frexp(u, &e);
     if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
-    double f = m - 1.0;
-    double s = f / (2.0 + f);
-    double z2 = s * s;
-    double p = 1.0 / 25.0;
-    for (int j = 11; j >= 0; j--) p = fma(p, z2, 1.0 / (double)(2 * j + 1));
-    double logm = 2.0 * s * p;
+    int key = (int)(orc_bits(m) >> 44) - ORC_LOG_KEY0;
+    double R = orc_from_bits(orc_log_tab[key][0]);
+    double Lh = orc_from_bits(orc_log_tab[key][1]);
+    double Ll = orc_from_bits(orc_log_tab[key][2]);
+    double r = fma(m, R, -1.0);
+    double r2 = r * r;
+    double p = -1.0 / 8.0;
+    p = fma(p, r, 1.0 / 7.0);
+    p = fma(p, r, -1.0 / 6.0);
+    p = fma(p, r, 1.0 / 5.0);
+    p = fma(p, r, -1.0 / 4.0);
+    p = fma(p, r, 1.0 / 3.0);
+    double q = fma(r, p, -0.5);
+    double lg = fma(r2, q, r);
     double de = (double)e;
     double ru = (double)(1.0f / (float)u);
-    return de * ORC_LN2_HI + ((logm + c * ru) + de * ORC_LN2_LO);
+    double hi = fma(de, ORC_LN2_HI, Lh);
+    double lo = (lg + c * ru) + fma(de, ORC_LN2_LO, Ll);
+    return hi + lo;
 }
 
 double orc_expm1(double w)
 {
-    double k = (fabs(w) < 0.5 * ORC_LN2_HI) ? 0.0 : rint(w * 1.44269504088896338700e+00);
-    double r = (w - k * ORC_LN2_HI) - k * ORC_LN2_LO;
-    double p = 1.0 / 87178291200.0;   /* 1/14! */
-    double fact = 87178291200.0;
-    for (int j = 13; j >= 1; j--) {
-        fact = fact / (double)(j + 1);
-        p = fma(p, r, 1.0 / fact);
-    }
-    double em = r * p;
-    if (k == 0.0) return em;
-    double kc = k > 2000.0 ? 2000.0 : (k < -2000.0 ? -2000.0 : k);
-    double t = ldexp(1.0, (int)kc);
-    return (t - 1.0) + t * em;
+    double wc = w;
+    if (fabs(w) > 800.0) wc = w < 0.0 ? -800.0 : 800.0;
+    float y = orc_f32_trunc(wc) * 46.16624069213867f;     /* 32/ln2 rounded to FP32 */
+    float sh = y + 12582912.0f;                            /* 1.5 2^23: rounds y to an integer */
+    uint32_t sb;
+    memcpy(&sb, &sh, sizeof sb);
+    int k = (int)sb - 0x4b400000;
+    int j = k & 31;
+    int m = (k - j) / 32;
+    double dk = (double)k;
+    double r = fma(-dk, ORC_LN2_HI / 32.0, wc);
+    r = fma(-dk, ORC_LN2_LO / 32.0, r);
+    double r2 = r * r;
+    double p = 1.0 / 5040.0;
+    p = fma(p, r, 1.0 / 720.0);
+    p = fma(p, r, 1.0 / 120.0);
+    p = fma(p, r, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 1.0 / 2.0);
+    double em = fma(r2, p, r);
+    double Th = orc_from_bits(orc_exp_tab[j][0]);
+    double Tl = orc_from_bits(orc_exp_tab[j][1]);
+    double S = fma(Th, em, Tl);
+    if (m > 1023) return ((Th + S) * ldexp(1.0, m - 1023)) * ldexp(1.0, 1023);
+    double t = ldexp(1.0, m);
+    return fma(t, S, fma(t, Th, -1.0));
 }
 
 /* ---- the Pollock pieces ---------------------------------------------- */

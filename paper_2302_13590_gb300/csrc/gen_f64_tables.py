@@ -1,0 +1,99 @@
+"""Write ``mp_f64_tables.h``: the constant tables of the FP64 kernels'
+table-driven log1p and expm1.
+
+Each entry is a correctly rounded value of a mathematical constant,
+evaluated here with Python's ``decimal`` module at 90 significant digits
+(its ln, exp and power are correctly rounded at that precision) and then
+rounded exactly to the binary format:
+
+* logarithm table, 257 buckets of the reduced argument m in [1/sqrt2, sqrt2);
+  a bucket is one value of (exponent, top 8 fraction bits) of the double m,
+  c its midpoint; R = 1/c rounded to 8 significant bits (nearest, ties to
+  even), Lh = -ln R rounded to the nearest multiple of 2^-32, Ll = -ln R - Lh
+  rounded to the nearest double.  With 8-bit R, m * R - 1 is a multiple of
+  2^-60 below 2^-7 in magnitude, so one fused multiply-add gives it exactly;
+  with Lh and e * ln2_hi both multiples of 2^-32, their sum is exact.
+* exponential table, j = 0..31: Th = 2^(j/32) and Tl = 2^(j/32) - Th, each
+  rounded to the nearest double.
+
+Run: python gen_f64_tables.py   (rewrites the header next to this file)
+"""
+import decimal
+import os
+import struct
+from decimal import Decimal
+from fractions import Fraction
+
+KEY0 = (1022 << 8) + 106
+N_LOG = 257
+N_EXP = 32
+
+
+def _round_to(x: Fraction, unit: Fraction) -> Fraction:
+    q = x / unit
+    n = q.numerator // q.denominator
+    rem = q - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return n * unit
+
+
+def _sig8(x: Fraction) -> Fraction:
+    e = 0
+    while Fraction(2) ** (e + 1) <= x:
+        e += 1
+    while Fraction(2) ** e > x:
+        e -= 1
+    return _round_to(x, Fraction(2) ** (e - 7))
+
+
+def _hex(v: float) -> str:
+    return "0x%016xULL" % struct.unpack("<Q", struct.pack("<d", v))[0]
+
+
+def tables():
+    ctx = decimal.Context(prec=90)
+    logs = []
+    for i in range(N_LOG):
+        key = KEY0 + i
+        e, k = key >> 8, key & 255
+        c = Fraction(2) ** (e - 1023) * Fraction(512 + 2 * k + 1, 512)
+        R = _sig8(1 / c)
+        lnR = ctx.ln(ctx.divide(Decimal(R.numerator), Decimal(R.denominator)))
+        L = -Fraction(lnR)
+        Lh = _round_to(L, Fraction(1, 2 ** 32))
+        logs.append((float(R), float(Lh), float(L - Lh)))
+    exps = []
+    for j in range(N_EXP):
+        T = Fraction(ctx.power(Decimal(2), ctx.divide(Decimal(j), Decimal(32))))
+        Th = float(T)
+        exps.append((Th, float(T - Fraction(Th))))
+    return logs, exps
+
+
+def render() -> str:
+    logs, exps = tables()
+    out = ["// mp_f64_tables.h - constant tables of the FP64 log1p and expm1 (bit",
+           "// patterns of IEEE doubles), written by gen_f64_tables.py; the definitions",
+           "// are in that script's docstring.",
+           "#pragma once", "",
+           "namespace mp {", "",
+           f"constexpr int F64_LOG_KEY0 = {KEY0};", f"constexpr int F64_LOG_N = {N_LOG};",
+           f"constexpr int F64_EXP_N = {N_EXP};", "",
+           "// per bucket: R, Lh, Ll, 0 (32 bytes)",
+           "static __device__ __align__(16) const unsigned long long f64_log_tab[F64_LOG_N * 4] = {"]
+    for R, Lh, Ll in logs:
+        out.append(f"    {_hex(R)}, {_hex(Lh)}, {_hex(Ll)}, 0x0ULL,")
+    out += ["};", "", "// per j: Th, Tl (16 bytes)",
+            "static __device__ __align__(16) const unsigned long long f64_exp_tab[F64_EXP_N * 2] = {"]
+    for Th, Tl in exps:
+        out.append(f"    {_hex(Th)}, {_hex(Tl)},")
+    out += ["};", "", "}  // namespace mp", ""]
+    return "\n".join(out)
+
+
+if __name__ == "__main__":
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mp_f64_tables.h")
+    with open(path, "w") as f:
+        f.write(render())
+    print(path)

@@ -7,6 +7,8 @@
 
 #include <math_constants.h>
 
+#include "mp_f64_tables.h"
+
 namespace mp {
 
 // ---------------------------------------------------------------------------
@@ -85,82 +87,111 @@ __device__ __forceinline__ double pow2i(int k)
     return 0.0;
 }
 
+// FP64 -> FP32 by truncating the significand on the ALU pipe (the FP64
+// pipe, the binding unit of the FP64 kernels, is spared the conversion):
+// relative error below 2^-23; magnitudes below the FP32 normal range give
+// 0, above it (and infinities, NaN) give infinity, with the sign.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const long long b = bits(x);
+    const unsigned s = (unsigned)((unsigned long long)b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -126) return __uint_as_float(s);
+    if (e > 127) return __uint_as_float(s | 0x7f800000u);
+    return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+
 // ---------------------------------------------------------------------------
-// log1p and expm1 by argument reduction and series, with IEEE additions,
-// multiplications, divisions and explicit fused multiply-adds in a fixed
-// order (no implicit contraction: this file is built with -fmad=false), so
-// that the FP64 path produces the same bits as any other evaluation of the
-// same steps on the host.  Exit-axis choices near a
+// log1p and expm1 by argument reduction, a table and a short series, with
+// IEEE additions, multiplications and explicit fused multiply-adds in a
+// fixed order (no implicit contraction: this file is built with
+// -fmad=false), exact bit operations on the ALU pipe, one FP32 reciprocal
+// and FP32 products, so that the FP64 path produces the same bits as any
+// other evaluation of the same steps on the host.  Exit-axis choices near a
 // tie then agree exactly, which library functions with different last-bit
-// rounding cannot guarantee on ill-conditioned fields.
-//   log1p(x): u = 1 + x, c = its rounding error (two-sum), u = m 2^e with
-//     m in [1/sqrt2, sqrt2), f = m - 1, log(1 + f) = 2 atanh(f / (2 + f))
-//     by its odd series to the 25th power (Horner, fma), + e ln2 (split)
-//     + c / u, with c (below half an ulp of u) times the FP32 reciprocal.
-//   expm1(w): k = nearest integer to w / ln2 (0 when |w| < ln2 / 2),
-//     r = w - k ln2 (split), expm1(r) by its Taylor series to r^14 / 14!,
-//     expm1(w) = (2^k - 1) + 2^k expm1(r), 2^k with k limited to
-//     [-2000, 2000] (the same value for every k).
+// rounding cannot guarantee on ill-conditioned fields.  The tables
+// (mp_f64_tables.h) hold correctly rounded constants.
+//   log1p(x): u = 1 + x, c = its rounding error (two-sum); u = m 2^e with
+//     m in [1/sqrt2, sqrt2); the bucket of m (exponent and top 8 fraction
+//     bits) gives R ~ 1/m with 8 significant bits and -ln R = Lh + Ll;
+//     r = m R - 1 exactly (one fma); ln(1 + r) by its series to r^8
+//     (|r| < 0.006); (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
+//     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u.
+//     u = +inf -> +inf, u = 0 -> -inf, NaN -> NaN.
+//   expm1(w): |w| limited to 800; k = nearest integer to w 32/ln2 in FP32
+//     on the truncated w; j = k mod 32, m = (k - j) / 32;
+//     r = (w - k ln2_hi/32) - k ln2_lo/32; expm1(r) by its series to r^7
+//     (|r| < 0.0109); 2^(j/32) = Th + Tl, S = Th expm1(r) + Tl;
+//     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
+//     2^m is not finite).  About 18 and 12 FP64 operations.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double series_log1p(double x)
 {
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
     const double u = 1.0 + x;
+    const long long ub = bits(u);
+    const bool ok = ub > 0LL && ub < 0x7ff0000000000000LL;   // 0 < u < inf
     const double c = gt_pos(x, 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
     int e;
-    double m = frexp_bits(u, e);
-    if (bits(m) < bits(0.70710678118654752440)) {   // m >= 0
-        m = m * 2.0;
+    double m = frexp_bits(ok ? u : 1.0, e);
+    if (bits(m) < bits(0.70710678118654752440)) {   // m in [1/2, 1/sqrt2): m * 2, exactly
+        m = __longlong_as_double(bits(m) + (1LL << 52));
         e = e - 1;
     }
-    const double f = m - 1.0;
-    const double s = f / (2.0 + f);
-    const double z2 = s * s;
-    double p = 1.0 / 25.0;
-    p = fma(p, z2, 1.0 / 23.0);
-    p = fma(p, z2, 1.0 / 21.0);
-    p = fma(p, z2, 1.0 / 19.0);
-    p = fma(p, z2, 1.0 / 17.0);
-    p = fma(p, z2, 1.0 / 15.0);
-    p = fma(p, z2, 1.0 / 13.0);
-    p = fma(p, z2, 1.0 / 11.0);
-    p = fma(p, z2, 1.0 / 9.0);
-    p = fma(p, z2, 1.0 / 7.0);
-    p = fma(p, z2, 1.0 / 5.0);
-    p = fma(p, z2, 1.0 / 3.0);
-    p = fma(p, z2, 1.0);
-    const double logm = 2.0 * s * p;
+    const int key = (int)(bits(m) >> 44) - F64_LOG_KEY0;
+    const double2* tp = reinterpret_cast<const double2*>(f64_log_tab) + 2 * key;
+    const double2 t0 = __ldg(tp), t1 = __ldg(tp + 1);
+    const double R = t0.x, Lh = t0.y, Ll = t1.x;
+    const double r = fma(m, R, -1.0);
+    const double r2 = r * r;
+    double p = -1.0 / 8.0;
+    p = fma(p, r, 1.0 / 7.0);
+    p = fma(p, r, -1.0 / 6.0);
+    p = fma(p, r, 1.0 / 5.0);
+    p = fma(p, r, -1.0 / 4.0);
+    p = fma(p, r, 1.0 / 3.0);
+    const double q = fma(r, p, -0.5);
+    const double lg = fma(r2, q, r);
     const double de = i2d_exact(e);
     const double ru = (double)__frcp_rn((float)u);
-    return de * ln2_hi + ((logm + c * ru) + de * ln2_lo);
+    const double hi = fma(de, ln2_hi, Lh);
+    const double lo = (lg + c * ru) + fma(de, ln2_lo, Ll);
+    const double special = eq0(u) ? -CUDART_INF : (ub == 0x7ff0000000000000LL ? CUDART_INF : CUDART_NAN);
+    return ok ? hi + lo : special;
+}
+
+// expm1 where 2^m overflows (w > ~709.4); kept out of line
+static __device__ __noinline__ double expm1_big(double Th, double S, int m)
+{
+    return ((Th + S) * pow2i(m - 1023 > 2000 ? 2000 : m - 1023)) * pow2i(1023);
 }
 
 __device__ __forceinline__ double series_expm1(double w)
 {
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double k = abs_lt(w, 0.5 * ln2_hi) ? 0.0 : rint(w * 1.44269504088896338700e+00);
-    const double r = (w - k * ln2_hi) - k * ln2_lo;
-    double p = 1.0 / 87178291200.0;           // 1/14!
-    p = fma(p, r, 1.0 / 6227020800.0);           // 1/13!
-    p = fma(p, r, 1.0 / 479001600.0);
-    p = fma(p, r, 1.0 / 39916800.0);
-    p = fma(p, r, 1.0 / 3628800.0);
-    p = fma(p, r, 1.0 / 362880.0);
-    p = fma(p, r, 1.0 / 40320.0);
-    p = fma(p, r, 1.0 / 5040.0);
+    const double wc = (abs_lt(w, 800.0) || is_nan(w)) ? w : (lt0(w) ? -800.0 : 800.0);
+    const float y = __fmul_rn(f32_trunc(wc), 46.16624069213867f);   // 32/ln2 in FP32
+    const float sh = __fadd_rn(y, 12582912.0f);                      // rounds y to an integer
+    const int k = (int)__float_as_uint(sh) - 0x4b400000;
+    const int j = k & 31;
+    const int m = (k - j) >> 5;
+    const double dk = i2d_exact(k);
+    double r = fma(-dk, ln2_hi / 32.0, wc);
+    r = fma(-dk, ln2_lo / 32.0, r);
+    const double r2 = r * r;
+    double p = 1.0 / 5040.0;
     p = fma(p, r, 1.0 / 720.0);
     p = fma(p, r, 1.0 / 120.0);
     p = fma(p, r, 1.0 / 24.0);
     p = fma(p, r, 1.0 / 6.0);
     p = fma(p, r, 1.0 / 2.0);
-    p = fma(p, r, 1.0);
-    const double em = r * p;
-    if (eq0(k)) return em;
-    int ki = d2i_integral(k);   // k is integral; out of range saturates
-    ki = ki > 2000 ? 2000 : (ki < -2000 ? -2000 : ki);
-    const double t = pow2i(ki);
-    return (t - 1.0) + t * em;
+    const double em = fma(r2, p, r);
+    const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);
+    const double S = fma(T.x, em, T.y);
+    if (m > 1023) return expm1_big(T.x, S, m);
+    const double t = pow2i(m < -2000 ? -2000 : m);
+    return fma(t, S, fma(t, T.x, -1.0));
 }
 
 // Exit time along one axis (face = +1, -1, or 0 when no face is
@@ -196,20 +227,6 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
     return eq0(s) ? pp : pn;
-}
-
-// FP64 -> FP32 by truncating the significand on the ALU pipe (the FP64
-// pipe, the binding unit of the FP64 kernels, is spared the conversion):
-// relative error below 2^-23; magnitudes below the FP32 normal range give
-// 0, above it (and infinities, NaN) give infinity, with the sign.
-__device__ __forceinline__ float f32_trunc(double x)
-{
-    const long long b = bits(x);
-    const unsigned s = (unsigned)((unsigned long long)b >> 63) << 31;
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126) return __uint_as_float(s);
-    if (e > 127) return __uint_as_float(s | 0x7f800000u);
-    return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
 }
 
 // FP32 estimate of an exit time from the exact FP64 distance d and

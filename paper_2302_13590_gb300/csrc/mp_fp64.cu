@@ -516,7 +516,7 @@ struct F64Engine {
                                                 sel3(a0, p2x, p2y, p2z), sel3(a0, n1x, n1y, n1z), fa);
                     tmin = te;
                     ax = a0;
-                    if ((cand & ~(1u << a0)) || is_nan(te)) {
+                    if ((cand & ~(1u << a0)) || !(te < CUDART_INF)) {
                         // close call (or an unusable value): every reachable
                         // axis exactly, in axis order, smallest wins
                         int fx;

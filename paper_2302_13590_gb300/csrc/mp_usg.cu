@@ -347,7 +347,7 @@ struct UsgEngine {
                     const double te = f64_exit_time(A[a0], iA[a0], D[a0], vp[a0], pp[a0], p2[a0], n1[a0], fa);
                     tmin = te;
                     ax = a0;
-                    if ((cand & ~(1u << a0)) || is_nan(te)) {
+                    if ((cand & ~(1u << a0)) || !(te < CUDART_INF)) {
                         double te3[3];
                         int fx;
                         #pragma unroll

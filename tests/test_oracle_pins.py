@@ -231,8 +231,9 @@ def test_exact_tie_goes_to_lowest_axis():
 
 
 def test_series_log1p_expm1_against_libm():
-    """The oracle's own log1p/expm1 (argument reduction + series, IEEE basic
-    operations only) stay within a few ulp of the C library across the
+    """The oracle's own log1p/expm1 (argument reduction, a table of correctly
+    rounded constants and a short series, IEEE basic operations only) stay
+    within a few ulp of the C library across the
     ranges the tracker meets, and keep the limits exact."""
     rng = np.random.default_rng(0)
     xs = np.concatenate([-np.exp(-rng.uniform(0, 40, 4000)), np.exp(rng.uniform(-60, 15, 4000)),

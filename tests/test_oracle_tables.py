@@ -1,0 +1,191 @@
+"""Pins of the table-driven log1p and expm1 (the oracle's, and the constant
+tables the FP64 kernels carry), from outside both:
+
+* every table entry equals the correctly rounded value of its definition,
+  evaluated here with mpmath at 300 bits (the oracle's generator uses exact
+  integer arithmetic, the device generator Python's decimal module);
+* the logarithm's reduction r = m R - 1 is exactly representable in every
+  bucket (so one fma gives it exactly) and stays below the bound the series
+  is sized for; e ln2_hi + Lh is exact for every exponent;
+* the exponential's reduction, with k rounded in FP32 from the truncated
+  argument, keeps |r| below the bound its series is sized for;
+* the oracle's log1p and expm1 stay within 1 and 2 ulp of the correctly
+  rounded result (mpmath) for arguments in every bucket and every j.
+"""
+import math
+import os
+import re
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+mpmath = pytest.importorskip("mpmath")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEY0 = (1022 << 8) + 106
+LN2_HI = 6.93147180369123816490e-01
+LN2_LO = 1.90821492927058770002e-10
+
+
+def _d(b):
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def _read(path, per_log):
+    words = [int(x, 16) for x in re.findall(r"0x([0-9a-f]{16})ULL", open(path).read())]
+    n_log = 257 * per_log
+    log = [tuple(_d(w) for w in words[i:i + 3]) for i in range(0, n_log, per_log)]
+    exp = [(_d(words[n_log + 2 * j]), _d(words[n_log + 2 * j + 1])) for j in range(32)]
+    assert len(words) == n_log + 64
+    return log, exp
+
+
+def _tables():
+    oracle = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3)
+    # the device header pads each bucket with a literal 0x0ULL (not matched)
+    device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3)
+    return {"oracle": oracle, "device": device}
+
+
+def _bucket_c(i):
+    key = KEY0 + i
+    e, k = key >> 8, key & 255
+    return Fraction(2) ** (e - 1023) * Fraction(512 + 2 * k + 1, 512)
+
+
+def _rn8(x):
+    e = math.floor(math.log2(x))
+    unit = Fraction(2) ** (e - 7)
+    q = x / unit
+    n = q.numerator // q.denominator
+    rem = q - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2):
+        n += 1
+    return n * unit
+
+
+def _expected():
+    mpmath.mp.prec = 300
+    log = []
+    for i in range(257):
+        R = _rn8(1 / _bucket_c(i))
+        L = -mpmath.log(mpmath.mpf(R.numerator) / R.denominator)
+        Lh = mpmath.nint(L * 2 ** 32) / 2 ** 32
+        log.append((float(R), float(Lh), float(L - Lh)))
+    exp = []
+    for j in range(32):
+        T = mpmath.power(2, mpmath.mpf(j) / 32)
+        Th = float(T)
+        exp.append((Th, float(T - Th)))
+    return log, exp
+
+
+@pytest.fixture(scope="module")
+def expected():
+    return _expected()
+
+
+@pytest.mark.parametrize("which", ["oracle", "device"])
+def test_tables_are_correctly_rounded(which, expected):
+    log, exp = _tables()[which]
+    assert log == expected[0]
+    assert exp == expected[1]
+    # the bucket of 1 (from either side) needs no table correction
+    assert log[150][0] == 1.0 and log[149][0] == 1.0 and log[150][1] == 0.0
+
+
+def test_log_reduction_exact_in_every_bucket():
+    log, _ = _tables()["oracle"]
+    rng = np.random.default_rng(3)
+    for i, (R, Lh, _) in enumerate(log):
+        key = KEY0 + i
+        lo = _d(key << 44)
+        hi = _d(((key + 1) << 44) - 1)
+        lo, hi = max(lo, 1 / math.sqrt(2)), min(hi, math.nextafter(math.sqrt(2), 0))
+        ms = [lo, hi] + list(rng.uniform(lo, hi, 20))
+        for m in ms:
+            r = Fraction(m) * Fraction(R) - 1
+            assert Fraction(float(r)) == r, (i, m)            # one fma is exact
+            assert abs(r) < Fraction(3, 500), (i, m)          # |r| < 0.006
+        assert (Fraction(Lh) * 2 ** 32).denominator == 1
+    assert (Fraction(LN2_HI) * 2 ** 32).denominator == 1
+    for e in (-1075, -1022, -1, 1, 1023, 1024):
+        s = Fraction(e) * Fraction(LN2_HI) + Fraction(log[0][1])
+        assert Fraction(float(s)) == s
+
+
+def _f32_trunc(x):
+    b = struct.unpack("<Q", struct.pack("<d", x))[0]
+    s = (b >> 63) << 31
+    e = ((b >> 52) & 0x7ff) - 1023
+    if e < -126:
+        f = s
+    elif e > 127:
+        f = s | 0x7f800000
+    else:
+        f = s | ((e + 127) << 23) | ((b >> 29) & 0x7fffff)
+    return np.frombuffer(struct.pack("<I", f), np.float32)[0]
+
+
+def test_exp_reduction_bound():
+    mpmath.mp.prec = 200
+    ln2_32 = mpmath.log(2) / 32
+    rng = np.random.default_rng(4)
+    edges = [(k + 0.5) * math.log(2) / 32 for k in range(-36934, 36934, 977)]
+    ws = list(rng.uniform(-800, 800, 3000)) + edges + [math.nextafter(x, 0) for x in edges] + [800.0, -800.0]
+    worst = 0.0
+    for w in ws:
+        y = np.float32(_f32_trunc(w)) * np.float32(46.16624069213867)
+        sh = np.float32(y) + np.float32(12582912.0)
+        k = int(np.frombuffer(np.float32(sh).tobytes(), np.uint32)[0]) - 0x4B400000
+        worst = max(worst, abs(float(mpmath.mpf(w) - k * ln2_32)))
+    assert worst < 0.0109
+
+
+def _ulps(a, ref):
+    return abs(a - ref) / np.spacing(abs(ref)) if ref != 0 else abs(a)
+
+
+def test_log1p_within_one_ulp_in_every_bucket():
+    mpmath.mp.prec = 200
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for i in range(257):
+        key = KEY0 + i
+        lo = max(_d(key << 44), 1 / math.sqrt(2))
+        hi = min(_d(((key + 1) << 44) - 1), math.nextafter(math.sqrt(2), 0))
+        for m in (lo, hi, float(rng.uniform(lo, hi))):
+            for e in (-40, -2, 0, 1, 30):
+                x = math.ldexp(m, e) - 1.0
+                if x <= -1.0 or x == 0.0:
+                    continue
+                ref = float(mpmath.log1p(mpmath.mpf(x)))
+                worst = max(worst, _ulps(O.log1p(x), ref))
+    for x in list(rng.uniform(-1e-6, 1e-6, 200)) + list(-np.exp(-rng.uniform(30, 36, 50))):
+        worst = max(worst, _ulps(O.log1p(x), float(mpmath.log1p(mpmath.mpf(x)))))
+    assert worst <= 1.0
+    assert O.log1p(math.inf) == math.inf and O.log1p(-1.0) == -math.inf and math.isnan(O.log1p(-2.0))
+
+
+def test_expm1_within_two_ulp_for_every_j():
+    mpmath.mp.prec = 200
+    rng = np.random.default_rng(6)
+    worst = 0.0
+    h = math.log(2) / 32
+    for m in (-1100, -40, -2, -1, 0, 1, 3, 20, 1000, 1022):
+        for j in range(32):
+            c = (32 * m + j) * h
+            for d in (0.0, 0.49 * h, -0.49 * h, float(rng.uniform(-0.5, 0.5)) * h):
+                w = c + d
+                if w == 0.0 or w > 709.7:
+                    continue
+                worst = max(worst, _ulps(O.expm1(w), float(mpmath.expm1(mpmath.mpf(w)))))
+    assert worst <= 2.0
+    # 2^m beyond the double range: the product is formed in two steps
+    for w in (709.5, 709.78, 709.782):
+        assert O.expm1(w) == float(mpmath.expm1(mpmath.mpf(w)))
+    assert O.expm1(709.8) == math.inf and O.expm1(1e300) == math.inf and O.expm1(-1e300) == -1.0
