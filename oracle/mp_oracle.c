@@ -16,9 +16,10 @@
  *
  *   face velocities   v1 = Q1 / (n * area_a),  v2 = Q2 / (n * area_a)
  *   gradient          A  = (v2 - v1) / D_a            (D_a = cell size)
- *   velocity at p     vp = v1 + A * p                 (p = offset from face 1)
+ *   velocity at p     vp = v1 + A * p  (one fma)      (p = offset from face 1)
  *   motion            p(t) = p + vp (e^{A t} - 1) / A     (Pollock's form;
- *                     p + vp t when A t == 0)
+ *                     p + vp t when A t == 0; the product by 1/A and the
+ *                     sum in one fma)
  *   exit time         t_a = ln(v_exit / vp) / A = ln(1 + z) / A,
  *                     d = signed distance to the exit face, z = A d / vp
  *                     (computed as A * (d / vp)), and t_a = d / vp in the
@@ -149,7 +150,8 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
  * m (its exponent and top 8 fraction bits) gives R, an 8-bit approximation
  * of 1/m, and -ln R = Lh + Ll; r = m R - 1 is exact (one fma: a multiple of
  * 2^-60 below 2^-7); ln(1 + r) = r - r^2/2 + ... - r^8/8 (|r| < 0.006);
- * log1p(x) = (e ln2_hi + Lh) + ((ln(1 + r) + c / u) + (e ln2_lo + Ll)), the
+ * log1p(x) = (e ln2_hi + Lh) + ((ln(1 + r) + c / u) + (e ln2_lo + Ll)) (the
+ * inner sum with c / u in one fma), the
  * first sum exact (both terms are multiples of 2^-32), c / u taken as c
  * times the FP32 reciprocal of u (c is below half an ulp of u).
  * u = +inf gives +inf, u = 0 gives -inf, a NaN gives NaN.
@@ -223,7 +225,7 @@ double orc_log1p(double x)
     double de = (double)e;
     double ru = (double)(1.0f / (float)u);
     double hi = fma(de, ORC_LN2_HI, Lh);
-    double lo = (lg + c * ru) + fma(de, ORC_LN2_LO, Ll);
+    double lo = fma(c, ru, lg) + fma(de, ORC_LN2_LO, Ll);
     return hi + lo;
 }
 
@@ -261,7 +263,7 @@ double orc_expm1(double w)
 
 double orc_exit_time(double v1, double v2, double A, double iA, double D, double p, int* face)
 {
-    double vp = v1 + A * p;
+    double vp = fma(A, p, v1);
     double d;
     if (vp > 0.0 && v2 > 0.0) { *face = 1; d = D - p; }
     else if (vp < 0.0 && v1 < 0.0) { *face = -1; d = -p; }
@@ -274,11 +276,11 @@ double orc_exit_time(double v1, double v2, double A, double iA, double D, double
 
 double orc_move(double v1, double A, double iA, double D, double p, double dt)
 {
-    double vp = v1 + A * p;
+    double vp = fma(A, p, v1);
     double s = vp * dt;
     if (s == 0.0) return p;
     double w = A * dt;
-    double pn = (w == 0.0) ? p + s : p + (vp * orc_expm1(w)) * iA;
+    double pn = (w == 0.0) ? p + s : fma(vp * orc_expm1(w), iA, p);
     if (pn < 0.0) pn = 0.0;
     if (pn > D) pn = D;
     return pn;

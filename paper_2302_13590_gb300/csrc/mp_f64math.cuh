@@ -38,6 +38,12 @@ __device__ __forceinline__ bool is_nan(double v)
     return (bits(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
 
+// -v (the sign bit flipped, as IEEE negation)
+__device__ __forceinline__ double neg(double v)
+{
+    return __longlong_as_double(bits(v) ^ (long long)0x8000000000000000ULL);
+}
+
 // frexp: u = m 2^e with m in [1/2, 1) (u == 0, inf, NaN: m = u, e = 0)
 __device__ __forceinline__ double frexp_bits(double u, int& e)
 {
@@ -101,6 +107,33 @@ __device__ __forceinline__ float f32_trunc(double x)
     return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
 }
 
+// (float)u rounded to nearest even, for u >= 2^-126 (the values 1 + x
+// takes in log1p are >= 2^-53), on the ALU pipe; above the FP32 range:
+// infinity, as the conversion gives
+__device__ __forceinline__ float f32_rn_pos(double u)
+{
+    const long long b = bits(u);
+    const int e = (int)(b >> 52) - 1023;
+    if (e > 127) return CUDART_INF_F;
+    unsigned fb = ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+    const unsigned rem = (unsigned)(b & 0x1fffffff);
+    fb += (rem > 0x10000000u || (rem == 0x10000000u && (fb & 1u))) ? 1u : 0u;
+    return __uint_as_float(fb);
+}
+
+// FP32 subnormals to FP64 (rare: kept out of line)
+static __device__ __noinline__ double f2d_subnormal(float f) { return (double)f; }
+
+// (double)f for f >= 0 (normal, zero, infinity: on the ALU pipe)
+__device__ __forceinline__ double f2d_pos(float f)
+{
+    const unsigned fb = __float_as_uint(f);
+    const unsigned fe = fb >> 23;
+    if (fe == 0u) return fb == 0u ? 0.0 : f2d_subnormal(f);
+    if (fe == 255u) return CUDART_INF;
+    return __longlong_as_double(((long long)(fe + 896u) << 52) | ((long long)(fb & 0x7fffffu) << 29));
+}
+
 // ---------------------------------------------------------------------------
 // log1p and expm1 by argument reduction, a table and a short series, with
 // IEEE additions, multiplications and explicit fused multiply-adds in a
@@ -154,9 +187,9 @@ __device__ __forceinline__ double series_log1p(double x)
     const double q = fma(r, p, -0.5);
     const double lg = fma(r2, q, r);
     const double de = i2d_exact(e);
-    const double ru = (double)__frcp_rn((float)u);
+    const double ru = f2d_pos(__frcp_rn(f32_rn_pos(ok ? u : 1.0)));   // (double)(1.0f / (float)u)
     const double hi = fma(de, ln2_hi, Lh);
-    const double lo = (lg + c * ru) + fma(de, ln2_lo, Ll);
+    const double lo = fma(c, ru, lg) + fma(de, ln2_lo, Ll);
     const double special = eq0(u) ? -CUDART_INF : (ub == 0x7ff0000000000000LL ? CUDART_INF : CUDART_NAN);
     return ok ? hi + lo : special;
 }
@@ -194,19 +227,14 @@ __device__ __forceinline__ double series_expm1(double w)
     return fma(t, S, fma(t, T.x, -1.0));
 }
 
-// Exit time along one axis (face = +1, -1, or 0 when no face is
-// reachable; v2pos / v1neg: the signs of the face velocities).  Written
-// without branches around the division and log1p so that the lanes of a
-// warp stay converged; lanes with no reachable face compute on harmless
-// operands and select +inf.  The values equal those of the branchy form
-// (t1 = d / vp, z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
-__device__ __forceinline__ double f64_exit_time(double A, double iA, double D, double vp, double pp, bool v2pos,
-                                                bool v1neg, int& face)
+// Exit time along one axis from the distance d to the reachable face
+// (face = +1, -1, or 0 when no face is reachable: +inf).  Written without
+// branches around the division and log1p so that the lanes of a warp stay
+// converged; lanes with no reachable face compute on harmless operands and
+// select +inf.  The values equal those of the branchy form (t1 = d / vp,
+// z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
+__device__ __forceinline__ double f64_exit_time_d(double A, double iA, double d, double vp, int face)
 {
-    const bool up = gt0(vp) && v2pos;
-    const bool dn = lt0(vp) && v1neg;
-    face = up ? 1 : (dn ? -1 : 0);
-    const double d = up ? D - pp : -pp;
     const double t1 = d / (face ? vp : 1.0);
     const double z = A * t1;
     const bool lin = eq0(z) || !face;
@@ -214,16 +242,38 @@ __device__ __forceinline__ double f64_exit_time(double A, double iA, double D, d
     return face ? te : CUDART_INF;
 }
 
+// the reachable face (v2pos / v1neg: the signs of the face velocities)
+__device__ __forceinline__ int f64_face(double vp, bool v2pos, bool v1neg)
+{
+    return (gt0(vp) && v2pos) ? 1 : ((lt0(vp) && v1neg) ? -1 : 0);
+}
+
+// the signed distance to that face (D - pp up, -pp down and otherwise)
+__device__ __forceinline__ double f64_face_dist(int face, double D, double pp)
+{
+    return face > 0 ? D - pp : neg(pp);
+}
+
+__device__ __forceinline__ double f64_exit_time(double A, double iA, double D, double vp, double pp, bool v2pos,
+                                                bool v1neg, int& face)
+{
+    face = f64_face(vp, v2pos, v1neg);
+    return f64_exit_time_d(A, iA, f64_face_dist(face, D, pp), vp, face);
+}
+
+// particle velocity at offset pp from face 1: v1 + A pp, one rounding
+__device__ __forceinline__ double f64_vel(double v1, double A, double pp) { return fma(A, pp, v1); }
+
 // analytic motion along one axis for a time dt, clamped to the cell
 // (the same values as: s == 0 -> pp; w == 0 -> pp + s; else
-// pp + (vp * expm1(w)) * (1 / A))
+// pp + (vp * expm1(w)) * (1 / A), the last product and sum in one fma)
 __device__ __forceinline__ double f64_move(double A, double iA, double D, double vp, double pp, double dt)
 {
     const double s = vp * dt;
     const double w = A * dt;
     const bool lin = eq0(w);
     const double em = series_expm1(lin ? 0.5 : w);
-    double pn = lin ? pp + s : pp + (vp * em) * iA;
+    double pn = lin ? pp + s : fma(vp * em, iA, pp);
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
     return eq0(s) ? pp : pn;

@@ -273,15 +273,9 @@ struct F64Engine {
         double tev;  // next output time or the stop time, whichever is first
     };
 
-    __device__ __forceinline__ static double exit_time(double A, double iA, double D, double vp, double pp,
-                                                       bool v2pos, bool v1neg, int& face)
-    {
-        return f64_exit_time(A, iA, D, vp, pp, v2pos, v1neg, face);
-    }
-
     __device__ __forceinline__ static int face_of(double vp, bool v2pos, bool v1neg)
     {
-        return (gt0(vp) && v2pos) ? 1 : ((lt0(vp) && v1neg) ? -1 : 0);
+        return f64_face(vp, v2pos, v1neg);
     }
 
     // face-velocity signs of axis a from the cell's nb word
@@ -440,9 +434,9 @@ struct F64Engine {
         const double v1x = r0.x, Ax = r0.y, iAx = r1.x, v1y = r1.y, Ay = r2.x, iAy = r2.y;
         const double v1z = r3.x, Az = r3.y, iAz = r4.x;
         const double D0 = __ldg(f.delr + j), D1 = __ldg(f.delc + i), D2 = __ldg(f.dz + k);
-        const double x = __ldg(f.xf + j) + move(Ax, iAx, D0, v1x + Ax * p0, p0, tau);
-        const double y = __ldg(f.yf + i) + move(Ay, iAy, D1, v1y + Ay * p1, p1, tau);
-        const double z = __ldg(f.zf + k) + move(Az, iAz, D2, v1z + Az * p2, p2, tau);
+        const double x = __ldg(f.xf + j) + move(Ax, iAx, D0, f64_vel(v1x, Ax, p0), p0, tau);
+        const double y = __ldg(f.yf + i) + move(Ay, iAy, D1, f64_vel(v1y, Ay, p1), p1, tau);
+        const double z = __ldg(f.zf + k) + move(Az, iAz, D2, f64_vel(v1z, Az, p2), p2, tau);
         store_record(o.ts + (long long)Q.kk[slot] * p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
     }
 
@@ -482,18 +476,22 @@ struct F64Engine {
                 const bool p2x = v2_pos(nb, 0), p2y = v2_pos(nb, 1), p2z = v2_pos(nb, 2);
                 const bool n1x = v1_neg(nb, 0), n1y = v1_neg(nb, 1), n1z = v1_neg(nb, 2);
                 D0 = __ldg(f.delr + s.j); D1 = __ldg(f.delc + s.i); D2 = __ldg(f.dz + s.k);
-                vp0 = v1x + Ax * s.x0;
-                vp1 = v1y + Ay * s.x1;
-                vp2 = v1z + Az * s.x2;
-                // reachable faces (the same tests as exit_time) and FP32
+                vp0 = f64_vel(v1x, Ax, s.x0);
+                vp1 = f64_vel(v1y, Ay, s.x1);
+                vp2 = f64_vel(v1z, Az, s.x2);
+                // reachable faces and FP32
                 // estimates of the three exit times
                 f0 = face_of(vp0, p2x, n1x);
                 f1 = face_of(vp1, p2y, n1y);
                 f2 = face_of(vp2, p2z, n1z);
+                // signed distances to the reachable faces (shared by the
+                // estimates and the exact evaluations)
+                const double d0 = f64_face_dist(f0, D0, s.x0), d1 = f64_face_dist(f1, D1, s.x1),
+                             d2 = f64_face_dist(f2, D2, s.x2);
                 bool u0, u1, u2;
-                const float e0 = estimate(f0, f0 > 0 ? D0 - s.x0 : -s.x0, vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
-                const float e1 = estimate(f1, f1 > 0 ? D1 - s.x1 : -s.x1, vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
-                const float e2 = estimate(f2, f2 > 0 ? D2 - s.x2 : -s.x2, vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
+                const float e0 = estimate(f0, d0, vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
+                const float e1 = estimate(f1, d1, vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
+                const float e2 = estimate(f2, d2, vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
                 // candidates: every axis whose estimate is within 2^-10 of the
                 // smallest (the estimates are within ~3e-6 of the exact times),
                 // and every axis whose estimate cannot be trusted
@@ -510,24 +508,31 @@ struct F64Engine {
                 if (a0 >= 0) {
                     // the exact FP64 exit time of the leading candidate (one
                     // evaluation per lane, uniform across the warp)
-                    int fa;
-                    const double te = exit_time(sel3(a0, Ax, Ay, Az), sel3(a0, iAx, iAy, iAz), sel3(a0, D0, D1, D2),
-                                                sel3(a0, vp0, vp1, vp2), sel3(a0, s.x0, s.x1, s.x2),
-                                                sel3(a0, p2x, p2y, p2z), sel3(a0, n1x, n1y, n1z), fa);
-                    tmin = te;
-                    ax = a0;
-                    if ((cand & ~(1u << a0)) || !(te < CUDART_INF)) {
-                        // close call (or an unusable value): every reachable
-                        // axis exactly, in axis order, smallest wins
-                        int fx;
-                        const double t0 = exit_time(Ax, iAx, D0, vp0, s.x0, p2x, n1x, fx);
-                        const double t1 = exit_time(Ay, iAy, D1, vp1, s.x1, p2y, n1y, fx);
-                        const double t2 = exit_time(Az, iAz, D2, vp2, s.x2, p2z, n1z, fx);
-                        tmin = CUDART_INF;
-                        ax = -1;
-                        if (f0 != 0 && t0 < tmin) { tmin = t0; ax = 0; }
-                        if (f1 != 0 && t1 < tmin) { tmin = t1; ax = 1; }
-                        if (f2 != 0 && t2 < tmin) { tmin = t2; ax = 2; }
+                    const double te = f64_exit_time_d(sel3(a0, Ax, Ay, Az), sel3(a0, iAx, iAy, iAz),
+                                                      sel3(a0, d0, d1, d2), sel3(a0, vp0, vp1, vp2),
+                                                      sel3(a0, f0, f1, f2));
+                    // then the other candidates exactly (a close call; every
+                    // reachable axis when the leading time is unusable): the
+                    // smallest time wins, ties to the lower axis - the
+                    // oracle's rule over all axes, since a non-candidate's
+                    // exact time exceeds the leading one's
+                    unsigned rest = cand & ~(1u << a0);
+                    if (te < CUDART_INF) {
+                        tmin = te;
+                        ax = a0;
+                    } else {
+                        rest = ((f0 ? 1u : 0u) | (f1 ? 2u : 0u) | (f2 ? 4u : 0u)) & ~(1u << a0);
+                    }
+                    while (rest) {
+                        const int a = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        const double t = f64_exit_time_d(sel3(a, Ax, Ay, Az), sel3(a, iAx, iAy, iAz),
+                                                         sel3(a, d0, d1, d2), sel3(a, vp0, vp1, vp2),
+                                                         sel3(a, f0, f1, f2));
+                        if (t < tmin || (t == tmin && a < ax)) {
+                            tmin = t;
+                            ax = a;
+                        }
                     }
                 }
                 s.steps++;

@@ -122,6 +122,12 @@ struct UsgEngine {
     DevUsg u;
     Batch b;
 
+    template <class T>
+    __device__ __forceinline__ static T sel3(int a, T x, T y, T z)
+    {
+        return a == 0 ? x : (a == 1 ? y : z);
+    }
+
     struct State {
         int r;
         int c;
@@ -235,11 +241,11 @@ struct UsgEngine {
         const UsgGeo& g = u.geo[c];
         const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
         const double x = __ldg(&g.o[0]) + f64_move(__ldg(&k.Ax), __ldg(&k.iAx), __ldg(&g.D[0]),
-                                                   __ldg(&k.v1x) + __ldg(&k.Ax) * p0, p0, tau);
+                                                   f64_vel(__ldg(&k.v1x), __ldg(&k.Ax), p0), p0, tau);
         const double y = __ldg(&g.o[1]) + f64_move(__ldg(&k.Ay), __ldg(&k.iAy), __ldg(&g.D[1]),
-                                                   __ldg(&k.v1y) + __ldg(&k.Ay) * p1, p1, tau);
+                                                   f64_vel(__ldg(&k.v1y), __ldg(&k.Ay), p1), p1, tau);
         const double z = __ldg(&g.o[2]) + f64_move(__ldg(&k.Az), __ldg(&k.iAz), __ldg(&g.D[2]),
-                                                   __ldg(&k.v1z) + __ldg(&k.Az) * p2, p2, tau);
+                                                   f64_vel(__ldg(&k.v1z), __ldg(&k.Az), p2), p2, tau);
         store_record(R.o.ts + (long long)Q.kk[slot] * R.p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
     }
 
@@ -314,23 +320,25 @@ struct UsgEngine {
                 org[0] = q0.x; org[1] = q0.y; org[2] = q1.x; D[0] = q1.y; D[1] = q2.x; D[2] = q2.y;
                 const double pp[3] = {s.x0, s.x1, s.x2};
                 bool p2[3], n1[3];
+                double dd[3];
                 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    vp[a] = v1[a] + A[a] * pp[a];
+                    vp[a] = f64_vel(v1[a], A[a], pp[a]);
                     p2[a] = (sg >> (4 * a + 2)) & 1ULL;
                     n1[a] = (sg >> (4 * a + 1)) & 1ULL;
-                    fc[a] = (gt0(vp[a]) && p2[a]) ? 1 : ((lt0(vp[a]) && n1[a]) ? -1 : 0);
+                    fc[a] = f64_face(vp[a], p2[a], n1[a]);
+                    dd[a] = f64_face_dist(fc[a], D[a], pp[a]);
                 }
                 // FP32 estimates of the three exit times; the exact FP64 time
                 // of the leading one, and of every axis within 2^-10 of it
                 // or with an untrusted estimate (the same exit axis and time
                 // as evaluating all three exactly)
                 bool u0, u1, u2;
-                const float e0 = f32_estimate(fc[0], fc[0] > 0 ? D[0] - pp[0] : -pp[0], vp[0], g0.z,
+                const float e0 = f32_estimate(fc[0], dd[0], vp[0], g0.z,
                                               fc[0] > 0 ? g0.y : g0.x, u0);
-                const float e1 = f32_estimate(fc[1], fc[1] > 0 ? D[1] - pp[1] : -pp[1], vp[1], g1.y,
+                const float e1 = f32_estimate(fc[1], dd[1], vp[1], g1.y,
                                               fc[1] > 0 ? g1.x : g0.w, u1);
-                const float e2 = f32_estimate(fc[2], fc[2] > 0 ? D[2] - pp[2] : -pp[2], vp[2], g2.x,
+                const float e2 = f32_estimate(fc[2], dd[2], vp[2], g2.x,
                                               fc[2] > 0 ? g1.w : g1.z, u2);
                 float em = CUDART_INF_F;
                 int a0 = -1;
@@ -343,20 +351,27 @@ struct UsgEngine {
                 if (a0 < 0 && cand) a0 = __ffs(cand) - 1;
                 tmin = CUDART_INF;
                 if (a0 >= 0) {
-                    int fa;
-                    const double te = f64_exit_time(A[a0], iA[a0], D[a0], vp[a0], pp[a0], p2[a0], n1[a0], fa);
-                    tmin = te;
-                    ax = a0;
-                    if ((cand & ~(1u << a0)) || !(te < CUDART_INF)) {
-                        double te3[3];
-                        int fx;
-                        #pragma unroll
-                        for (int a = 0; a < 3; ++a) te3[a] = f64_exit_time(A[a], iA[a], D[a], vp[a], pp[a], p2[a], n1[a], fx);
-                        tmin = CUDART_INF;
-                        ax = -1;
-                        if (fc[0] != 0 && te3[0] < tmin) { tmin = te3[0]; ax = 0; }
-                        if (fc[1] != 0 && te3[1] < tmin) { tmin = te3[1]; ax = 1; }
-                        if (fc[2] != 0 && te3[2] < tmin) { tmin = te3[2]; ax = 2; }
+                    const double te = f64_exit_time_d(A[a0], iA[a0], dd[a0], vp[a0], fc[a0]);
+                    // the other candidates (every reachable axis when the
+                    // leading time is unusable): smallest wins, ties to the
+                    // lower axis
+                    unsigned rest = cand & ~(1u << a0);
+                    if (te < CUDART_INF) {
+                        tmin = te;
+                        ax = a0;
+                    } else {
+                        rest = ((fc[0] ? 1u : 0u) | (fc[1] ? 2u : 0u) | (fc[2] ? 4u : 0u)) & ~(1u << a0);
+                    }
+                    while (rest) {
+                        const int a = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        const double t = f64_exit_time_d(sel3(a, A[0], A[1], A[2]), sel3(a, iA[0], iA[1], iA[2]),
+                                                         sel3(a, dd[0], dd[1], dd[2]), sel3(a, vp[0], vp[1], vp[2]),
+                                                         sel3(a, fc[0], fc[1], fc[2]));
+                        if (t < tmin || (t == tmin && a < ax)) {
+                            tmin = t;
+                            ax = a;
+                        }
                     }
                 }
                 s.steps++;

@@ -135,6 +135,33 @@ def test_fp64_no_exit_divide(ctx):
     mp.mp_field_free(fh)
 
 
+def test_fp64_exact_ties(ctx):
+    """Two- and three-way exact ties of the exit time (equal flows, equal
+    cell sizes, symmetric positions), mixed in one warp with plain steps:
+    the lowest axis wins, as in the oracle; the screening path evaluates the
+    other candidates exactly."""
+    for q1, q2 in ((1e-4, 1e-4), (1e-4, 3e-4), (-3e-4, -1e-4)):
+        f = H.single_cell_field(q1, q2, q1, q2, q1, q2, d=(2.0, 2.0, 2.0), por=0.25)
+        fh = ctx.field(f)
+        rng = np.random.default_rng(8)
+        frac = rng.uniform(0.05, 0.95, (96, 3))
+        frac[0::3, 1] = frac[0::3, 0]                  # x-y ties
+        frac[1::3, 2] = frac[1::3, 1]                  # y-z ties
+        frac[2::6, 1] = frac[2::6, 0]                  # x-y-z ties
+        frac[2::6, 2] = frac[2::6, 0]
+        cells = np.zeros(frac.shape[0], np.int32)
+        ref = O.track(f, O.release_explicit(f, cells, frac))
+        for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+            ep, _, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, schedule=sch)
+            G.compare_fp64(ep, ref, dmin=G.dmin(f))
+        ef = ref["exit_face"]
+        assert not np.isin(ef[0::3], (2, 3)).any()    # an x-y tie never exits through y
+        assert not np.isin(ef[1::3], (4, 5)).any()    # a y-z tie never exits through z
+        assert np.isin(ef[2::6], (0, 1)).all()        # a three-way tie exits through x
+        assert np.isin(ef[0::3], (0, 1)).sum() > 10
+        mp.mp_field_free(fh)
+
+
 @pytest.mark.parametrize("scale,seed", [(30.0, 40), (1.0, 40), (30.0, 45)])
 def test_weak_sinks_pass_through(ctx, scale, seed):
     """Weak sinks: particles enter well cells and leave through reachable
