@@ -385,7 +385,7 @@ def run_ours(args):
         results[name] = dict(r, ms_max=ms_max, cell_steps_all=steps_all, value=value,
                              particles_per_s=summed(n * args.steps) / (ms_max / 1e3))
 
-    # end to end through the C ABI with host buffers: pinned host release
+    # end to end through the C ABI with host buffers (mp_track_host): pinned host release
     # arrays in, endpoint and timeseries records out, every step
     e2e = None
     if not args.no_e2e:
@@ -416,21 +416,20 @@ def run_ours(args):
             tot_steps = 0
             barrier()
             t0 = time.perf_counter()
+            opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=prec,
+                                schedule=args.schedule, times=w.times)
             for _ in range(args.steps):
-                gh = mp.mp_release_group(ctx.h, fh, cell=cells_h, local=local_h, stream=stream)
-                opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=prec,
-                                    schedule=args.schedule, times=w.times)
-                rid = mp.mp_track(ctx.h, gh, opts, stream)
-                mp.mp_get_endpoints(ctx.h, rid, n, out=ep_host)
-                mp.mp_get_timeseries(ctx.h, rid, n, nt, out=ts_host)
-                tot_steps += mp.mp_get_stats(ctx.h, rid)["cell_steps"]
-                mp.mp_req_free(ctx.h, rid)
-                mp.mp_group_free(gh)
+                # one call: chunked release + tracking on two streams, result
+                # copies of one chunk overlapping the tracking of the next
+                _, _, st = mp.mp_track_host(ctx.h, fh, cells_h, local_h, opts, n_chunks=args.e2e_chunks,
+                                            out=ep_host, ts_out=ts_host)
+                tot_steps += st["cell_steps"]
             barrier()
             el = maxed(time.perf_counter() - t0)
             e2e_vals[name] = summed(tot_steps) / el
         e2e = {"value": e2e_vals["fp64"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "mixed": e2e_vals["mixed"]}
+               "mixed": e2e_vals["mixed"],
+               "call": "mp_track_host: pinned host arrays in and out; chunks on two streams, copies overlapped"}
 
     if rank != 0:
         ctx.close()
@@ -617,6 +616,7 @@ def main():
     ap.add_argument("--mode", default="endpoint+timeseries", choices=["endpoint+timeseries", "endpoint"],
                     help="profiling cases only; the benchmark line uses endpoint+timeseries")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=0, help="chunks of the end-to-end call (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

@@ -418,6 +418,33 @@ int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes);
 /* Number of CUDA kernel launches mp_track issues for these options. */
 int mp_track_launches(const mp_track_opts* o, int32_t* launches);
 
+/* ---- host to host, transfers overlapped with tracking ----------------------
+ * Track n particles given in host memory and write their results to host
+ * memory in one call.  Release as mp_release_group with MP_RELEASE_EXPLICIT:
+ * cell[n] (int32), local[3 n] (fractions in [0, 1]^3 of the cell's extent,
+ * particle-major), t0[n] (release times; NULL: 0).  Results as
+ * mp_get_endpoints (ep: any pointer may be NULL) and, when o->mode has
+ * MP_MODE_TIMESERIES and ts is not NULL, the [n_times][n] records into
+ * ts (row stride n).  Particles move independently (Methods, "MODPATH"), so
+ * the call splits them into n_chunks contiguous chunks (n_chunks <= 0:
+ * chunks of about 128 K particles, 2 to 16 of them) and runs chunk c's
+ * copy-in, release, tracking and copy-out in order on the second of two
+ * internal streams when c is odd, the first otherwise: the result copies of
+ * one chunk overlap the tracking of the next.  The results are those of one
+ * mp_release_group + mp_track + mp_get_endpoints / mp_get_timeseries over
+ * all n particles (bit for bit: the kernels are the same, particle by
+ * particle).  Page-locked host buffers make the copies asynchronous;
+ * pageable ones work, without the overlap.  The host arrays are owned by
+ * the caller; the call returns after the last copy has landed (bounded
+ * wait, 60 s) and frees what it allocated.  stats (may be NULL): the sums of
+ * the chunks' counters; kernel_ms = device time from the first chunk's
+ * start to the last chunk's last copy.  MP_MODE_PATHLINE is rejected.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NONFINITE, MP_ERR_OOM, MP_ERR_TIMEOUT,
+ * MP_ERR_DEVICE, MP_ERR_CUDA. */
+int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell, const double* local,
+                  const double* t0, const mp_track_opts* o, int32_t n_chunks, const mp_endpoints* ep,
+                  mp_ts_record* ts, mp_stats* stats);
+
 /* ---- tracking without device allocation ----------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot allocate device memory where they track: code that runs inside a

@@ -18,8 +18,8 @@
  *   gradient          A  = (v2 - v1) / D_a            (D_a = cell size)
  *   velocity at p     vp = v1 + A * p  (one fma)      (p = offset from face 1)
  *   motion            p(t) = p + vp (e^{A t} - 1) / A     (Pollock's form;
- *                     p + vp t when A t == 0; the product by 1/A and the
- *                     sum in one fma)
+ *                     p + vp t (one fma) when A t == 0; the product by
+ *                     1/A and the sum in one fma)
  *   exit time         t_a = ln(v_exit / vp) / A = ln(1 + z) / A,
  *                     d = signed distance to the exit face, z = A d / vp
  *                     (computed as A * (d / vp)), and t_a = d / vp in the
@@ -280,7 +280,7 @@ double orc_move(double v1, double A, double iA, double D, double p, double dt)
     double s = vp * dt;
     if (s == 0.0) return p;
     double w = A * dt;
-    double pn = (w == 0.0) ? p + s : fma(vp * orc_expm1(w), iA, p);
+    double pn = (w == 0.0) ? fma(vp, dt, p) : fma(vp * orc_expm1(w), iA, p);
     if (pn < 0.0) pn = 0.0;
     if (pn > D) pn = D;
     return pn;

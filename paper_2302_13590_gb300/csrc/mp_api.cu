@@ -1203,6 +1203,121 @@ int mp_req_free(mp_ctx* ctx, mp_req id)
     return MP_OK;
 }
 
+int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell, const double* local,
+                  const double* t0, const mp_track_opts* o, int32_t n_chunks, const mp_endpoints* ep,
+                  mp_ts_record* ts, mp_stats* stats)
+{
+    if (!ctx || !f || !o || !ep || n < 0) return fail(MP_ERR_INVALID_ARG, "mp_track_host: bad argument");
+    if (n > 0 && (!cell || !local)) return fail(MP_ERR_INVALID_ARG, "mp_track_host: NULL cell/local");
+    if (o->mode & MP_MODE_PATHLINE) return fail(MP_ERR_INVALID_ARG, "mp_track_host: pathline mode not supported");
+    const bool want_ts = (o->mode & MP_MODE_TIMESERIES) != 0 && ts != nullptr;
+    if (stats) *stats = mp_stats{};
+    if (n == 0) return MP_OK;
+    MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // chunks of about 128 K particles (2 to 16 of them) unless the caller says
+    long long nc = n_chunks > 0 ? n_chunks : std::min<long long>(16, std::max<long long>(2, (n + 131071) / 131072));
+    nc = std::min<long long>(nc, n);
+    const long long m = (n + nc - 1) / nc;
+    nc = (n + m - 1) / m;
+
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_join = nullptr, ev_end = nullptr;
+    std::vector<mp_group*> groups;
+    std::vector<mp_req> ids;
+    int rc = MP_OK;
+    auto cu = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && rc == MP_OK) rc = cuda_fail(e, what);
+        return rc == MP_OK;
+    };
+    cu(cudaStreamCreateWithFlags(&st[0], cudaStreamNonBlocking), "mp_track_host: stream") &&
+        cu(cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking), "mp_track_host: stream") &&
+        cu(cudaEventCreate(&ev_start), "mp_track_host: event") &&
+        cu(cudaEventCreate(&ev_join), "mp_track_host: event") && cu(cudaEventCreate(&ev_end), "mp_track_host: event") &&
+        cu(cudaEventRecord(ev_start, st[0]), "mp_track_host: event") &&
+        cu(cudaStreamWaitEvent(st[1], ev_start, 0), "mp_track_host: event");
+    for (long long c = 0; c < nc && rc == MP_OK; ++c) {
+        const long long off = c * m, cnt = std::min<long long>(m, n - off);
+        cudaStream_t s = st[c & 1];
+        mp_release_desc rd{};
+        rd.n = cnt;
+        rd.kind = MP_RELEASE_EXPLICIT;
+        rd.flags = 0;
+        rd.cell = cell + off;
+        rd.local = local + 3 * off;
+        rd.t0 = t0 ? t0 + off : nullptr;
+        mp_group* g = nullptr;
+        if ((rc = mp_release_group(ctx, f, &rd, s, &g)) != MP_OK) break;
+        groups.push_back(g);
+        mp_req id = 0;
+        if ((rc = mp_track(ctx, g, o, s, &id)) != MP_OK) break;
+        ids.push_back(id);
+        Request* r = find_req(ctx, id);
+        const size_t u = (size_t)cnt, q = (size_t)off;
+        struct { void* dst; const void* src; size_t bytes; } cp[] = {
+            {ep->cell ? ep->cell + q : nullptr, r->d.cell, 4 * u},
+            {ep->x ? ep->x + q : nullptr, r->d.x, 8 * u},
+            {ep->y ? ep->y + q : nullptr, r->d.y, 8 * u},
+            {ep->z ? ep->z + q : nullptr, r->d.z, 8 * u},
+            {ep->px ? ep->px + q : nullptr, r->d.px, 8 * u},
+            {ep->py ? ep->py + q : nullptr, r->d.py, 8 * u},
+            {ep->pz ? ep->pz + q : nullptr, r->d.pz, 8 * u},
+            {ep->t ? ep->t + q : nullptr, r->d.t, 8 * u},
+            {ep->status ? ep->status + q : nullptr, r->d.status, u},
+            {ep->steps ? ep->steps + q : nullptr, r->d.steps, 4 * u},
+            {ep->exit_face ? ep->exit_face + q : nullptr, r->d.exit_face, u},
+            {ep->hash ? ep->hash + q : nullptr, r->d.hash, 8 * u},
+        };
+        for (auto& x : cp)
+            if (x.dst && !cu(cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, s), "mp_track_host: copy"))
+                break;
+        if (rc == MP_OK && want_ts && r->d.ts && r->n_times > 0)
+            cu(cudaMemcpy2DAsync(ts + q, sizeof(mp_ts_record) * (size_t)n, r->d.ts, sizeof(mp_ts_record) * u,
+                                 sizeof(mp_ts_record) * u, (size_t)r->n_times, cudaMemcpyDeviceToHost, s),
+               "mp_track_host: timeseries copy");
+    }
+    // join the streams, then wait (bounded) for the last copy
+    if (st[0] && st[1] && ev_join && ev_end) {
+        cudaError_t e = cudaEventRecord(ev_join, st[1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[0], ev_join, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_end, st[0]);
+        if (e == cudaSuccess) {
+            const int w = wait_event(ev_end, -1);
+            if (w != MP_OK && rc == MP_OK) rc = w;
+        } else {
+            cu(e, "mp_track_host: join");
+            cudaStreamSynchronize(st[0]);
+            cudaStreamSynchronize(st[1]);
+        }
+    }
+    mp_stats sum{};
+    for (mp_req id : ids) {
+        mp_stats one{};
+        const int g = mp_get_stats(ctx, id, &one);
+        if (g != MP_OK) {
+            if (rc == MP_OK) rc = g;
+            continue;
+        }
+        sum.cell_steps += one.cell_steps;
+        for (int k = 0; k < MP_N_STATUS; ++k) sum.n_status[k] += one.n_status[k];
+        sum.device_error |= one.device_error;
+    }
+    if (rc == MP_OK && sum.device_error) rc = fail(MP_ERR_DEVICE, "mp_track_host: tracking kernel raised its error flag");
+    if (ev_start && ev_end && rc == MP_OK) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_start, ev_end) == cudaSuccess) sum.kernel_ms = ms;
+    }
+    if (stats) *stats = sum;
+    for (mp_req id : ids) mp_req_free(ctx, id);
+    for (mp_group* g : groups) mp_group_free(g);
+    if (st[0]) cudaStreamSynchronize(st[0]);
+    if (st[1]) cudaStreamSynchronize(st[1]);
+    for (cudaEvent_t e : {ev_start, ev_join, ev_end})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t x : st)
+        if (x) cudaStreamDestroy(x);
+    return rc;
+}
+
 }  // extern "C"
 
 namespace mp {

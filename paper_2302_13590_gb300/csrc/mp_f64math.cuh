@@ -165,7 +165,10 @@ __device__ __forceinline__ double series_log1p(double x)
     const double u = 1.0 + x;
     const long long ub = bits(u);
     const bool ok = ub > 0LL && ub < 0x7ff0000000000000LL;   // 0 < u < inf
-    const double c = gt_pos(x, 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
+    // two-sum error of 1 + x: (1 - (u - x)) when x > 1, else (x - (u - 1));
+    // the operands are selected, so both lane groups share two FP64 adds
+    const bool big = gt_pos(x, 1.0);
+    const double c = (big ? 1.0 : x) - (u - (big ? x : 1.0));
     int e;
     double m = frexp_bits(ok ? u : 1.0, e);
     if (bits(m) < bits(0.70710678118654752440)) {   // m in [1/2, 1/sqrt2): m * 2, exactly
@@ -265,15 +268,18 @@ __device__ __forceinline__ double f64_exit_time(double A, double iA, double D, d
 __device__ __forceinline__ double f64_vel(double v1, double A, double pp) { return fma(A, pp, v1); }
 
 // analytic motion along one axis for a time dt, clamped to the cell
-// (the same values as: s == 0 -> pp; w == 0 -> pp + s; else
-// pp + (vp * expm1(w)) * (1 / A), the last product and sum in one fma)
+// (the same values as: vp dt == 0 -> pp; w == 0 -> pp + vp dt in one fma;
+// else pp + (vp * expm1(w)) * (1 / A), the last product and sum in one
+// fma); the operands are selected, so every lane issues one product and
+// one fma
 __device__ __forceinline__ double f64_move(double A, double iA, double D, double vp, double pp, double dt)
 {
     const double s = vp * dt;
     const double w = A * dt;
     const bool lin = eq0(w);
     const double em = series_expm1(lin ? 0.5 : w);
-    double pn = lin ? pp + s : fma(vp * em, iA, pp);
+    const double vem = vp * em;
+    double pn = fma(lin ? vp : vem, lin ? dt : iA, pp);
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
     return eq0(s) ? pp : pn;

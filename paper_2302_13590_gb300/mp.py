@@ -141,6 +141,8 @@ SIGNATURES = {
                                         _vp]),
     "mp_track_periods": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(_vp), _vp, _P(TrackOpts), _vp,
                                         _P(ctypes.c_int64)]),
+    "mp_track_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _P(TrackOpts), ctypes.c_int32,
+                                     _P(Endpoints), _vp, _P(Stats)]),
 }
 
 _lib = None
@@ -417,6 +419,28 @@ def mp_get_stats(ctx, req: int) -> dict:
     return {"cell_steps": int(s.cell_steps), "n_status": [int(v) for v in s.n_status],
             "kernel_ms": float(s.kernel_ms), "device_error": int(s.device_error),
             "path_points": int(s.path_points)}
+
+
+def mp_track_host(ctx, fh, cell, local, opts: "TrackOpts", t0=None, n_chunks: int = 0, out=None, ts_out=None):
+    """Host-to-host tracking with transfers overlapped (chunked, two streams).
+    cell (n,), local (n, 3) host arrays; out: dict of host endpoint arrays
+    (None: allocated); ts_out: [n_times, n] TS_RECORD array for timeseries
+    mode (None: allocated when the mode asks for it).  Returns (endpoints,
+    timeseries or None, stats)."""
+    c, l = _host(cell, np.int32), _host(local, np.float64)
+    t = None if t0 is None else _host(t0, np.float64)
+    n = c.size
+    if out is None:
+        out = {k: np.empty(n, dt) for k, dt in ENDPOINT_DTYPES.items()}
+    if ts_out is None and (opts.mode & MODE_TIMESERIES) and opts.n_times > 0:
+        ts_out = np.empty((opts.n_times, n), TS_RECORD)
+    e = Endpoints(*[_ptr(out.get(k)) for k, _ in Endpoints._fields_])
+    st = Stats()
+    _check(load_library().mp_track_host(ctx, fh, int(n), _ptr(c), _ptr(l), _ptr(t), ctypes.byref(opts),
+                                        int(n_chunks), ctypes.byref(e), _ptr(ts_out), ctypes.byref(st)))
+    stats = {"cell_steps": int(st.cell_steps), "n_status": [int(v) for v in st.n_status],
+             "kernel_ms": float(st.kernel_ms), "device_error": int(st.device_error)}
+    return out, ts_out, stats
 
 
 def mp_req_free(ctx, req: int):
