@@ -430,7 +430,9 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches);
  * chunks of about 128 K particles, 2 to 16 of them) and runs chunk c's
  * copy-in, release, tracking and copy-out in order on the second of two
  * internal streams when c is odd, the first otherwise: the result copies of
- * one chunk overlap the tracking of the next.  The results are those of one
+ * one chunk overlap the tracking of the next.  MP_SCHED_AUTO runs the chunks
+ * with the static schedule (its blocks retire as their particles finish, so
+ * the next chunk's blocks take their SMs).  The results are those of one
  * mp_release_group + mp_track + mp_get_endpoints / mp_get_timeseries over
  * all n particles (bit for bit: the kernels are the same, particle by
  * particle).  Page-locked host buffers make the copies asynchronous;

@@ -1219,6 +1219,11 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
     nc = std::min<long long>(nc, n);
     const long long m = (n + nc - 1) / nc;
     nc = (n + m - 1) / m;
+    // MP_SCHED_AUTO: the static schedule, whose blocks retire as their
+    // particles finish so that the next chunk's blocks fill the SMs (the
+    // persistent schedule holds its blocks until its queue drains)
+    mp_track_opts oc = *o;
+    if (oc.schedule == MP_SCHED_AUTO) oc.schedule = MP_SCHED_STATIC;
 
     cudaStream_t st[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr, ev_join = nullptr, ev_end = nullptr;
@@ -1249,7 +1254,7 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
         if ((rc = mp_release_group(ctx, f, &rd, s, &g)) != MP_OK) break;
         groups.push_back(g);
         mp_req id = 0;
-        if ((rc = mp_track(ctx, g, o, s, &id)) != MP_OK) break;
+        if ((rc = mp_track(ctx, g, &oc, s, &id)) != MP_OK) break;
         ids.push_back(id);
         Request* r = find_req(ctx, id);
         const size_t u = (size_t)cnt, q = (size_t)off;
