@@ -63,8 +63,13 @@ BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # the output records, both in proportion to the particle count.  It holds
 # only for the kernel sources it was taken from (their hash below);
 # otherwise the bench reports traffic as null.
-TRAFFIC = {"src": "a44adb23dffa27c4", "fp64": 5 * (352.326400e6 + 306.868480e6),
-           "mixed": 5 * (46.994688e6 + 290.419712e6)}
+TRAFFIC = {"src": "085cc734e1776056", "fp64": 5 * (351.011584e6 + 307.677952e6),
+           "mixed": 5 * (46.453760e6 + 290.294272e6)}
+# From the same capture: the FP64 pipe's busy fraction in the FP64 kernel
+# (sm__pipe_fp64_cycles_active, % of peak sustained active), the executed
+# counterpart of the algorithmic fraction (which charges every axis's exit
+# time while the kernel evaluates the exact one of about 1.1 axes a step).
+FP64_PIPE_ACTIVE = {"src": "085cc734e1776056", "value": 0.8508}
 
 
 def kernel_src_hash() -> str:
@@ -466,6 +471,8 @@ def run_ours(args):
                         "nominal_peak": FP64_PEAK_TFLOPS, "frac_of_nominal": achieved / FP64_PEAK_TFLOPS,
                         "flops_per_cell_step": FP64_FLOPS_PER_STEP, "kernel_ms": kms,
                         "cell_steps_per_launch": steps_per_launch,
+                        "fp64_pipe_active_ncu": (FP64_PIPE_ACTIVE["value"]
+                                                 if kernel_src_hash() == FP64_PIPE_ACTIVE["src"] else None),
                         "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                      "bytes_per_cell_step": BYTES_PER_STEP[name]}}
         else:
