@@ -38,6 +38,21 @@ __device__ __forceinline__ bool is_nan(double v)
     return (bits(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
 
+// an integer key whose order is the IEEE order of non-NaN doubles (-0 and
+// +0 share key 0): a >= b exactly when dkey(a) >= dkey(b)
+__device__ __forceinline__ long long dkey(double v)
+{
+    const long long b = bits(v);
+    return b >= 0LL ? b : -(b & 0x7fffffffffffffffLL);
+}
+// a >= b for non-NaN a, b
+__device__ __forceinline__ bool ge_d(double a, double b) { return dkey(a) >= dkey(b); }
+// v < +inf (false for +inf and NaN)
+__device__ __forceinline__ bool lt_inf(double v)
+{
+    return (bits(v) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL || bits(v) == (long long)0xfff0000000000000ULL;
+}
+
 // -v (the sign bit flipped, as IEEE negation)
 __device__ __forceinline__ double neg(double v)
 {

@@ -517,7 +517,7 @@ struct F64Engine {
                     // oracle's rule over all axes, since a non-candidate's
                     // exact time exceeds the leading one's
                     unsigned rest = cand & ~(1u << a0);
-                    if (te < CUDART_INF) {
+                    if (lt_inf(te)) {
                         tmin = te;
                         ax = a0;
                     } else {
@@ -539,9 +539,9 @@ struct F64Engine {
                 t_end = s.t + tmin;
                 if (ax < 0 && s.in_sink) path = P_CAPTURE;
                 else if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
-                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                else if (ax < 0 || ge_d(t_end, p.t_stop)) path = P_TIME;
                 else path = P_CROSS;
-                if (TS && path != P_CAPTURE && (ax < 0 || t_end >= s.tev)) {
+                if (TS && path != P_CAPTURE && (ax < 0 || ge_d(t_end, s.tev))) {
                     const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
                     int kk = s.kn;
                     while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;

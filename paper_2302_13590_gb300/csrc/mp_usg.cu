@@ -257,15 +257,31 @@ struct UsgEngine {
         return fmax(fmax(da, db), 0.0);
     }
 
-    // the neighbour across face (ax, side) at the exit point (xa, xb): the
-    // first sub-face holding it (else the nearest, first on ties) if its flow
-    // runs with the crossing, else the nearest one whose flow does, the point
-    // moved onto it; -1: no sub-face (outside)
-    __device__ __forceinline__ int across(int c, int ax, int side, double& xa, double& xb) const
+    // the flow of sub-face e runs with a crossing to `side` (q * side > 0;
+    // face flows are finite)
+    __device__ __forceinline__ bool with_flow(long long e, int side) const
     {
+        const double qe = __ldg(&u.sub[e].q);
+        return side > 0 ? gt0(qe) : lt0(qe);
+    }
+
+    // the neighbour across face (ax, side) at the exit point (xa, xb) =
+    // cell origin + offset on the two other axes: the first sub-face holding
+    // it (else the nearest, first on ties) if its flow runs with the
+    // crossing, else the nearest one whose flow does, the point moved onto
+    // it (mva / mvb: that coordinate changed); -1: no sub-face (outside).  A
+    // face with one sub-face hands over to its neighbour either way, so
+    // neither the exit point nor a distance is formed there.
+    __device__ __forceinline__ int across(int c, int ax, int side, double oa_, double pa_, double ob_, double pb_,
+                                          double& xa, double& xb, bool& mva, bool& mvb) const
+    {
+        mva = mvb = false;
         const int fi = 2 * ax + (side > 0 ? 1 : 0);
         const long long e0 = __ldg(u.face_off + 6LL * c + fi), e1 = __ldg(u.face_off + 6LL * c + fi + 1);
         if (e1 <= e0) return -1;
+        if (e1 - e0 == 1) return __ldg(&u.sub[e0].nbr);
+        xa = oa_ + pa_;
+        xb = ob_ + pb_;
         long long best = e0;
         double bd = CUDART_INF;
         for (long long e = e0; e < e1; ++e) {
@@ -273,18 +289,22 @@ struct UsgEngine {
             if (d < bd) { bd = d; best = e; }
             if (d == 0.0) break;
         }
-        if (u.sub[best].q * (double)side > 0.0) return u.sub[best].nbr;
+        if (with_flow(best, side)) return u.sub[best].nbr;
         long long alt = -1;
         double ad = CUDART_INF;
         for (long long e = e0; e < e1; ++e) {
-            if (!(u.sub[e].q * (double)side > 0.0)) continue;
+            if (!with_flow(e, side)) continue;
             const double d = rect_dist(u.sub[e], xa, xb);
             if (d < ad) { ad = d; alt = e; }
         }
         if (alt < 0) return u.sub[best].nbr;
         const UsgSub& e = u.sub[alt];
-        xa = fmin(fmax(xa, e.rect[0]), e.rect[1]);
-        xb = fmin(fmax(xb, e.rect[2]), e.rect[3]);
+        const double na = fmin(fmax(xa, e.rect[0]), e.rect[1]);
+        const double nb = fmin(fmax(xb, e.rect[2]), e.rect[3]);
+        mva = dkey(na) != dkey(xa);
+        mvb = dkey(nb) != dkey(xb);
+        xa = na;
+        xb = nb;
         return e.nbr;
     }
 
@@ -356,7 +376,7 @@ struct UsgEngine {
                     // leading time is unusable): smallest wins, ties to the
                     // lower axis
                     unsigned rest = cand & ~(1u << a0);
-                    if (te < CUDART_INF) {
+                    if (lt_inf(te)) {
                         tmin = te;
                         ax = a0;
                     } else {
@@ -378,9 +398,9 @@ struct UsgEngine {
                 t_end = s.t + tmin;
                 if (ax < 0 && s.in_sink) path = P_CAPTURE;
                 else if (ax < 0 && !(p.t_stop < CUDART_INF)) path = P_NOEXIT;
-                else if (ax < 0 || t_end >= p.t_stop) path = P_TIME;
+                else if (ax < 0 || ge_d(t_end, p.t_stop)) path = P_TIME;
                 else path = P_CROSS;
-                if (TS && path != P_CAPTURE && (ax < 0 || t_end >= s.tev)) {
+                if (TS && path != P_CAPTURE && (ax < 0 || ge_d(t_end, s.tev))) {
                     const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
                     int kk = s.kn;
                     while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
@@ -428,9 +448,11 @@ struct UsgEngine {
         const int side = fc[ax];
         s.ef = 2 * ax + (side > 0 ? 1 : 0);
         // hand over at the exit point
-        double xg[3] = {org[0] + pp[0], org[1] + pp[1], org[2] + pp[2]};
         const int oa = ax == 0 ? 1 : 0, ob = ax == 2 ? 1 : 2;
-        const int nc = across(s.c, ax, side, xg[oa], xg[ob]);
+        double xa = 0.0, xb = 0.0;
+        bool mva, mvb;
+        const int nc = across(s.c, ax, side, sel3(oa, org[0], org[1], org[2]), sel3(oa, pp[0], pp[1], pp[2]),
+                              sel3(ob, org[0], org[1], org[2]), sel3(ob, pp[0], pp[1], pp[2]), xa, xb, mva, mvb);
         if (nc < 0) {
             s.st = MP_ST_EXIT_DOMAIN;
             return;
@@ -454,9 +476,10 @@ struct UsgEngine {
             if (a == ax) continue;
             // the other axes keep their global coordinate; a hand-over that
             // moved the point enters at the moved point
-            double pa = (xg[a] == org[a] + pp[a]) ? pp[a] + (org[a] - on[a]) : xg[a] - on[a];
-            if (pa < 0.0) pa = 0.0;
-            if (pa > Dn[a]) pa = Dn[a];
+            const bool mv = a == oa ? mva : mvb;
+            double pa = mv ? (a == oa ? xa : xb) - on[a] : pp[a] + (org[a] - on[a]);
+            pa = lt0(pa) ? 0.0 : pa;
+            pa = gt_pos(pa, Dn[a]) ? Dn[a] : pa;
             pp[a] = pa;
         }
         pp[ax] = side > 0 ? 0.0 : Dn[ax];

@@ -114,6 +114,29 @@ def test_quadtree_periods_and_resume(ctx):
         mp.mp_field_free(fh)
 
 
+def test_hand_over_moved_point_vs_oracle(ctx):
+    """A refined face whose sub-faces carry opposite flows (the hand-made
+    two-cell case of the oracle tests): particles reaching the face where
+    its flow runs back enter the other sub-face's cell at the moved point;
+    the GPU's cells, faces, times and every pathline point equal the
+    oracle's."""
+    from tests.test_oracle_usg import _two_cells
+    for q_lo, q_hi in ((1e-4, 3e-4), (-1e-4, 5e-4), (4e-4, -1e-4)):
+        u = _two_cells(q_lo, q_hi)
+        fh = ctx.field(u)
+        rng = np.random.default_rng(21)
+        frac = np.column_stack([rng.uniform(0.02, 0.3, 97), rng.uniform(0.02, 0.98, 97), rng.uniform(0.1, 0.9, 97)])
+        cells = np.zeros(97, np.int32)
+        ref = O.track(u, O.release_explicit(u, cells, frac), pathline=True)
+        ep, _, st, path = _run(ctx, fh, cells, frac, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE, path_capacity=20 * 97)
+        G.compare_fp64(ep, ref, dmin=_dmin(u))
+        g, r = (np.sort(x, order=["particle", "seq"]) for x in (path, ref["path"]))
+        assert g.tobytes() == r.tobytes()
+        if q_lo < 0:
+            assert (ref["cell"] == 2).all()          # every particle crosses into the northern cell
+        mp.mp_field_free(fh)
+
+
 def test_usg_rejections(ctx):
     u = U.quadtree_field(2, 6, 8, seed=3, n_wells=1)
     fh = ctx.field(u)
