@@ -63,13 +63,13 @@ BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # the output records, both in proportion to the particle count.  It holds
 # only for the kernel sources it was taken from (their hash below);
 # otherwise the bench reports traffic as null.
-TRAFFIC = {"src": "085cc734e1776056", "fp64": 5 * (351.011584e6 + 307.677952e6),
-           "mixed": 5 * (46.453760e6 + 290.294272e6)}
+TRAFFIC = {"src": "403af91f2f9ede86", "fp64": 5 * (349.683456e6 + 307.090432e6),
+           "mixed": 5 * (46.412288e6 + 290.178304e6)}
 # From the same capture: the FP64 pipe's busy fraction in the FP64 kernel
 # (sm__pipe_fp64_cycles_active, % of peak sustained active), the executed
 # counterpart of the algorithmic fraction (which charges every axis's exit
 # time while the kernel evaluates the exact one of about 1.1 axes a step).
-FP64_PIPE_ACTIVE = {"src": "085cc734e1776056", "value": 0.8508}
+FP64_PIPE_ACTIVE = {"src": "403af91f2f9ede86", "value": 0.8493}
 
 
 def kernel_src_hash() -> str:
@@ -426,17 +426,22 @@ def run_ours(args):
                                  ts_out=ts_host)
             barrier()
             t0 = time.perf_counter()
+            calls = []
             for _ in range(args.steps):
                 # one call: chunked release + tracking on two streams, result
                 # copies of one chunk overlapping the tracking of the next
+                tc = time.perf_counter()
                 _, _, st = mp.mp_track_host(ctx.h, fh, cells_h, local_h, opts, n_chunks=args.e2e_chunks,
                                             out=ep_host, ts_out=ts_host)
+                calls.append(round((time.perf_counter() - tc) * 1e3, 2))
                 tot_steps += st["cell_steps"]
             barrier()
             el = maxed(time.perf_counter() - t0)
             e2e_vals[name] = summed(tot_steps) / el
+            e2e_vals[name + "_ms_per_call"] = calls
         e2e = {"value": e2e_vals["fp64"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "mixed": e2e_vals["mixed"],
+               "mixed": e2e_vals["mixed"], "ms_per_call": {"fp64": e2e_vals["fp64_ms_per_call"],
+                                                           "mixed": e2e_vals["mixed_ms_per_call"]},
                "call": "mp_track_host: pinned host arrays in and out; chunks on two streams, copies overlapped"}
 
     if rank != 0:
