@@ -70,6 +70,14 @@ TRAFFIC = {"src": "403af91f2f9ede86", "fp64": 5 * (349.683456e6 + 307.090432e6),
 # counterpart of the algorithmic fraction (which charges every axis's exit
 # time while the kernel evaluates the exact one of about 1.1 axes a step).
 FP64_PIPE_ACTIVE = {"src": "403af91f2f9ede86", "value": 0.8493}
+# Warp-instructions per cell-step of the mixed kernel in the same capture
+# (smsp__inst_executed.sum / cell-steps on 2e5 particles; the 1e6 launch
+# drains relatively less, so this slightly overstates its count): the mixed
+# kernel is issue-bound, and its issue view compares the implied issue rate
+# with one warp-instruction per clock per SM sub-partition (152 SMs x 4 x
+# 2.07 GHz).
+MIXED_INST_PER_STEP = {"src": "403af91f2f9ede86", "value": 1398650501.0 / 5.483e7}
+ISSUE_PEAK_TINST = 152 * 4 * 2.07e9 / 1e12
 
 
 def kernel_src_hash() -> str:
@@ -490,6 +498,13 @@ def run_ours(args):
                         "cell_steps_per_launch": steps_per_launch,
                         "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
                                     "peak_source": "measured in this run: L2-resident 64 MB read"}}
+            if kernel_src_hash() == MIXED_INST_PER_STEP["src"]:
+                ti = MIXED_INST_PER_STEP["value"] * rate / 1e12
+                rf[name]["issue_view"] = {"achieved": ti, "peak": ISSUE_PEAK_TINST, "unit": "Twarp-inst/s",
+                                          "frac": ti / ISSUE_PEAK_TINST,
+                                          "warp_inst_per_cell_step": MIXED_INST_PER_STEP["value"],
+                                          "peak_source": "nominal: 1 warp-instruction/clk per SMSP, 608 SMSPs, "
+                                                         "2.07 GHz"}
     batch = None
     if not args.no_batch:
         specs = I.batch_workload()
