@@ -78,6 +78,10 @@ FP64_PIPE_ACTIVE = {"src": "403af91f2f9ede86", "value": 0.8493}
 # 2.07 GHz).
 MIXED_INST_PER_STEP = {"src": "403af91f2f9ede86", "value": 1398650501.0 / 5.483e7}
 ISSUE_PEAK_TINST = 152 * 4 * 2.07e9 / 1e12
+# L2 read bytes per cell-step in the same capture (lts__t_sectors_srcunit_tex_op_read
+# x 32 B / cell-steps): the record gather, cell sizes, output times.
+L2_READ_PER_STEP = {"src": "403af91f2f9ede86", "fp64": 248730538.0 * 32 / 5.483e7,
+                    "mixed": 62416893.0 * 32 / 5.483e7}
 
 
 def kernel_src_hash() -> str:
@@ -480,6 +484,11 @@ def run_ours(args):
         traffic = args.traffic_fp64 if name == "fp64" else args.traffic_mixed
         if traffic is None and kernel_src_hash() == TRAFFIC["src"]:
             traffic = TRAFFIC[name]
+        l2_ncu = None
+        if kernel_src_hash() == L2_READ_PER_STEP["src"]:
+            l2_ncu = {"bytes_per_cell_step": L2_READ_PER_STEP[name],
+                      "gbs": L2_READ_PER_STEP[name] * rate / 1e9, "peak_gbs": l2,
+                      "frac": L2_READ_PER_STEP[name] * rate / 1e9 / l2}
         if name == "fp64":
             achieved = FP64_FLOPS_PER_STEP * rate / 1e12
             rf[name] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -490,14 +499,16 @@ def run_ours(args):
                         "fp64_pipe_active_ncu": (FP64_PIPE_ACTIVE["value"]
                                                  if kernel_src_hash() == FP64_PIPE_ACTIVE["src"] else None),
                         "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                                     "bytes_per_cell_step": BYTES_PER_STEP[name]}}
+                                     "bytes_per_cell_step": BYTES_PER_STEP[name]},
+                        "l2_read_ncu": l2_ncu}
         else:
             rf[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                         "traffic": traffic, "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
                         "bytes_per_cell_step": BYTES_PER_STEP[name], "kernel_ms": kms,
                         "cell_steps_per_launch": steps_per_launch,
                         "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
-                                    "peak_source": "measured in this run: L2-resident 64 MB read"}}
+                                    "peak_source": "measured in this run: L2-resident 64 MB read"},
+                        "l2_read_ncu": l2_ncu}
             if kernel_src_hash() == MIXED_INST_PER_STEP["src"]:
                 ti = MIXED_INST_PER_STEP["value"] * rate / 1e12
                 rf[name]["issue_view"] = {"achieved": ti, "peak": ISSUE_PEAK_TINST, "unit": "Twarp-inst/s",
@@ -603,6 +614,9 @@ def run_ours(args):
         serving["workload"] = ("Poisson arrivals at 200 requests/s on the 50x50x1 and 200x200x20 fields (p = 1/2), "
                                "group sizes log-uniform in 1e3..1e6, endpoint or 20-time timeseries at random")
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, seconds=args.cpu_seconds)
+    if cpu is not None:
+        one = cpu_baseline(w, seconds=min(args.cpu_seconds, 3.0), threads=1)
+        cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
     f64 = results["fp64"]
     line = {
         "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
