@@ -90,7 +90,16 @@ extern "C" {
                                    a reachable face; a particle that has none
                                    inside a sink cell is captured (SINK)
                                    (the paper's second test case lets
-                                   particles pass through weak sinks) */
+                                   particles pass through weak sinks).  With
+                                   mp_track_opts.weak_sink_fraction f > 0 a
+                                   sink cell still stops particles (SINK, on
+                                   the face, as a strong sink) when its sink
+                                   extracts at least f of the cell's inflow:
+                                   (inflow - outflow) / inflow over the face
+                                   flows, summed face by face in the order
+                                   x-, x+, y-, y+, z-, z+ (a quadtree face:
+                                   its sub-faces summed in list order); a
+                                   cell without inflow extracts all of it */
 
 #define MP_RELEASE_EXPLICIT 0
 #define MP_RELEASE_BOX 1
@@ -153,6 +162,9 @@ typedef struct {
     int32_t steps_per_fetch; /* dynamic schedule, 0 = auto      */
     uint32_t flags;          /* MP_TRACK_* bits                 */
     int64_t path_capacity;   /* pathline points the request keeps; <= 0: 64 per particle */
+    double weak_sink_fraction; /* in [0, 1]; > 0 with MP_TRACK_PASS_WEAK_SINKS: a sink
+                                  cell whose sink extracts at least this fraction of
+                                  its inflow still stops particles (see below) */
 } mp_track_opts;
 
 /* Endpoint arrays (SoA, particle order).  Any pointer may be NULL to skip
@@ -278,8 +290,9 @@ int mp_group_size(const mp_group* g, int64_t* n);
  * group's state becomes the final state, terminated particles keep their
  * status).  A moving particle whose cell is inactive or constant-head under
  * the group's field ends there (BOUNDARY, no step), in a sink cell (SINK)
- * unless MP_TRACK_PASS_WEAK_SINKS.
- * Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+ * unless MP_TRACK_PASS_WEAK_SINKS lets that sink pass.
+ * Errors: MP_ERR_INVALID_ARG (also: weak_sink_fraction outside [0, 1]),
+ * MP_ERR_OOM, MP_ERR_CUDA. */
 int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out);
 
 /* Rebind a group to another field on the same grid (same dims, cell sizes

@@ -59,7 +59,7 @@ class _Field(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
                 ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32),
-                ("path_start", ctypes.c_int32)]
+                ("path_start", ctypes.c_int32), ("weak_sink_fraction", ctypes.c_double)]
 
 
 # one pathline point (orc_path_rec)
@@ -233,7 +233,7 @@ def subset(state, idx):
 
 
 def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False,
-          pathline=False, path_start=True):
+          pathline=False, path_start=True, weak_sink_fraction=0.0):
     """Track every particle of ``state`` (dict of cell, px, py, pz, t, status,
     and optionally steps, hash and exit_face carried by a resumed particle).
 
@@ -269,7 +269,8 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
             res[k] = np.zeros((nt, n))
         res["ts_cell"] = np.zeros((nt, n), np.int32)
         res["ts_status"] = np.zeros((nt, n), np.uint8)
-    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)), int(bool(path_start)))
+    opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)), int(bool(path_start)),
+                 float(weak_sink_fraction))
     cap = 64 * n + 16
     while True:
         path = np.zeros(cap if pathline else 0, PATH_RECORD)
@@ -302,7 +303,7 @@ def resume_state(out):
 
 
 def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False,
-                  pathline=False):
+                  pathline=False, weak_sink_fraction=0.0):
     """Piecewise-steady flow (Methods, "MODPATH": the outer loop runs over the
     flow model's time steps and updates the flow arrays at each step's end).
 
@@ -338,7 +339,7 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
         wt = None if window is None or window.size == 0 else tarr[window]
         moved = (cur["status"] == ST_ACTIVE) | (p == 0)
         out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks,
-                    pathline=pathline, path_start=p == 0)
+                    pathline=pathline, path_start=p == 0, weak_sink_fraction=weak_sink_fraction)
         if pathline:
             paths.append(out.pop("path"))
         if res is None:

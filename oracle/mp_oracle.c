@@ -48,6 +48,9 @@
  *     enters a sink cell like any other and leaves through a face it can
  *     reach; when no face is reachable inside a sink cell the sink captures
  *     it (SINK) where it is; a particle released in a sink cell stays SINK;
+ *     with a weak-sink fraction f > 0 as well, a sink cell whose sink
+ *     extracts at least f of its inflow stops particles as a strong sink
+ *     does, the others are passed (sink_fraction below);
  *   - a cell-step is one exit-time evaluation, including zero-length steps
  *     and the final partial step; max_steps caps them (STEP_CAP), counted
  *     from the release (a resumed particle carries its count and its hash);
@@ -418,6 +421,7 @@ static void path_point(const orc_track_out* o, int64_t q, double x, double y, do
 struct orc_grid {
     void (*box)(const orc_grid* g, int32_t c, double o[3], double D[3]);
     void (*vel)(const orc_grid* g, int32_t c, cellvel* cv);
+    void (*flows)(const orc_grid* g, int32_t c, double q[6]);   /* total flow per face, +axis direction */
     int32_t (*across)(const orc_grid* g, int32_t c, int ax, int side, double x[3]);
     const int8_t* ibound;
     const orc_field* f;
@@ -437,6 +441,19 @@ static void st_vel(const orc_grid* g, int32_t c, cellvel* cv)
 {
     const orc_field* f = g->f;
     cell_velocities(f, c / (f->ncol * f->nrow), (c / f->ncol) % f->nrow, c % f->ncol, cv);
+}
+
+static void st_flows(const orc_grid* g, int32_t c, double q[6])
+{
+    const orc_field* f = g->f;
+    const int nrow = f->nrow, ncol = f->ncol;
+    int j = c % ncol, i = (c / ncol) % nrow, k = c / (ncol * nrow);
+    q[0] = f->qx[((size_t)k * nrow + i) * (ncol + 1) + j];
+    q[1] = f->qx[((size_t)k * nrow + i) * (ncol + 1) + j + 1];
+    q[2] = f->qy[((size_t)k * (nrow + 1) + i) * ncol + j];
+    q[3] = f->qy[((size_t)k * (nrow + 1) + i + 1) * ncol + j];
+    q[4] = f->qz[((size_t)k * nrow + i) * ncol + j];
+    q[5] = f->qz[((size_t)(k + 1) * nrow + i) * ncol + j];
 }
 
 static int32_t st_across(const orc_grid* g, int32_t c, int ax, int side, double x[3])
@@ -467,6 +484,11 @@ static double usg_face_flow(const orc_usg_field* u, int32_t c, int fi)
     double s = u->q[e0];
     for (int64_t e = e0 + 1; e < e1; e++) s += u->q[e];
     return s;
+}
+
+static void usg_flows(const orc_grid* g, int32_t c, double q[6])
+{
+    for (int fi = 0; fi < 6; fi++) q[fi] = usg_face_flow(g->u, c, fi);
 }
 
 static void usg_vel(const orc_grid* g, int32_t c, cellvel* cv)
@@ -530,6 +552,34 @@ static int32_t usg_across(const orc_grid* g, int32_t c, int ax, int side, double
     return u->nbr[alt];
 }
 
+/* Weak sinks with a threshold (Introduction: how weak sink cells are
+ * treated is a choice of the tracking configuration): the fraction of a
+ * cell's inflow its sink extracts, from the volume balance of its face
+ * flows (inflow: flow entering through a face; extraction: inflow minus
+ * outflow), summed face by face in the order x1, x2, y1, y2, z1, z2; a cell
+ * without inflow counts as extracting all of it. */
+static double sink_fraction(const orc_grid* g, int32_t c)
+{
+    double q[6];
+    g->flows(g, c, q);
+    double in = 0.0, out = 0.0;
+    for (int a = 0; a < 3; a++) {
+        const double q1 = q[2 * a], q2 = q[2 * a + 1];
+        if (q1 > 0.0) in += q1; else out += -q1;   /* low face: +axis flow enters */
+        if (q2 < 0.0) in += -q2; else out += q2;   /* high face: +axis flow leaves */
+    }
+    return in > 0.0 ? (in - out) / in : 1.0;
+}
+
+/* a sink cell stops particles (entering it or released in it): always
+ * without pass-through; with it, when its sink extracts at least
+ * weak_sink_fraction (> 0) of its inflow */
+static int sink_stops(const orc_grid* g, int32_t c, const orc_track_opts* opt)
+{
+    if (!opt->pass_weak_sinks) return 1;
+    return opt->weak_sink_fraction > 0.0 && sink_fraction(g, c) >= opt->weak_sink_fraction;
+}
+
 static int track_core(const orc_grid* g, int64_t n,
                       const int32_t* cell0, const double* px0, const double* py0, const double* pz0,
                       const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
@@ -557,7 +607,7 @@ static int track_core(const orc_grid* g, int64_t n,
             if (st == ORC_ST_ACTIVE) {
                 int8_t ib0 = g->ibound[c];
                 if (ib0 == 0 || ib0 == -1) st = ORC_ST_BOUNDARY;
-                else if (ib0 == 2 && !opt->pass_weak_sinks) st = ORC_ST_SINK;
+                else if (ib0 == 2 && sink_stops(g, c, opt)) st = ORC_ST_SINK;
             }
         } else {
             st = ORC_ST_INVALID_RELEASE;
@@ -651,7 +701,7 @@ static int track_core(const orc_grid* g, int64_t n,
             }
             int8_t ib = g->ibound[nc];
             if (ib == 0 || ib == -1) { st = ORC_ST_BOUNDARY; break; }
-            if (ib == 2 && !opt->pass_weak_sinks) { st = ORC_ST_SINK; break; }
+            if (ib == 2 && sink_stops(g, nc, opt)) { st = ORC_ST_SINK; break; }
             double on[3], Dn[3];
             g->box(g, nc, on, Dn);
             /* the other axes keep their global coordinate (o - on is 0
@@ -713,7 +763,7 @@ int orc_track(const orc_field* f, int64_t n,
     face_coords(f->delr, f->ncol, f->origin[0], xf);
     face_coords(f->delc, f->nrow, f->origin[1], yf);
     face_coords(f->dz, f->nlay, f->origin[2], zf);
-    orc_grid g = {st_box, st_vel, st_across, f->ibound, f, NULL, xf, yf, zf};
+    orc_grid g = {st_box, st_vel, st_flows, st_across, f->ibound, f, NULL, xf, yf, zf};
     return track_core(&g, n, cell0, px0, py0, pz0, t0, status0, steps0, hash0, face0, opt, out);
 }
 
@@ -722,7 +772,7 @@ int orc_usg_track(const orc_usg_field* u, int64_t n,
                   const double* t0, const uint8_t* status0, const uint32_t* steps0, const uint64_t* hash0,
                   const uint8_t* face0, const orc_track_opts* opt, const orc_track_out* out)
 {
-    orc_grid g = {usg_box, usg_vel, usg_across, u->ibound, NULL, u, NULL, NULL, NULL};
+    orc_grid g = {usg_box, usg_vel, usg_flows, usg_across, u->ibound, NULL, u, NULL, NULL, NULL};
     return track_core(&g, n, cell0, px0, py0, pz0, t0, status0, steps0, hash0, face0, opt, out);
 }
 

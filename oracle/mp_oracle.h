@@ -44,6 +44,9 @@ typedef struct {
     int64_t max_steps;    /* <= 0: default */
     int32_t pass_weak_sinks; /* 1: enter sink cells, leave through outflow faces */
     int32_t path_start;   /* pathlines: 1 = a record at the start of every particle */
+    double weak_sink_fraction; /* > 0 with pass_weak_sinks: a sink cell that
+                                  extracts at least this fraction of its
+                                  inflow still stops particles */
 } orc_track_opts;
 
 /* Rectangular unstructured grid: axis-aligned box cells, per cell and face

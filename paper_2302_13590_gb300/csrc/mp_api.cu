@@ -270,6 +270,7 @@ int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
     const size_t o_yf = off; off = align256(off + sizeof(double) * (nr + 1));
     const size_t o_zf = off; off = align256(off + sizeof(double) * (nl + 1));
     const size_t o_ib = off; off = align256(off + ncell);
+    const size_t o_sf = off; off = align256(off + sizeof(double) * ncell);
     const size_t o_flag = off; off = align256(off + sizeof(unsigned));
     const size_t persistent = off;
     const bool dev_in = (d->flags & MP_DEVICE_PTR) != 0;
@@ -351,10 +352,11 @@ int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
     f->d.yf = reinterpret_cast<double*>(buf + o_yf);
     f->d.zf = reinterpret_cast<double*>(buf + o_zf);
     f->d.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
+    f->d.sinkfrac = reinterpret_cast<double*>(buf + o_sf);
     f->d.m_ncol = div_magic((unsigned)nc);
     f->d.m_nrow = div_magic((unsigned)nr);
-    e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32), qx, qy, qz,
-                             por, s);
+    e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32),
+                             reinterpret_cast<double*>(buf + o_sf), qx, qy, qz, por, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (stage) cudaFree(stage);
@@ -432,6 +434,7 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     const size_t o_fo = off; off = align256(off + sizeof(long long) * (size_t)(6 * nc + 1));
     const size_t o_sub = off; off = align256(off + sizeof(mp::UsgSub) * (size_t)std::max(ns, 1LL));
     const size_t o_ib = off; off = align256(off + (size_t)nc);
+    const size_t o_sf = off; off = align256(off + sizeof(double) * (size_t)nc);
     const size_t persistent = off;
     const size_t o_box = off; off = align256(off + sizeof(double) * 6 * (size_t)nc);
     const size_t o_por = off; off = align256(off + sizeof(double) * (size_t)nc);
@@ -455,6 +458,7 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     u.face_off = reinterpret_cast<long long*>(buf + o_fo);
     u.sub = reinterpret_cast<mp::UsgSub*>(buf + o_sub);
     u.ibound = reinterpret_cast<int8_t*>(buf + o_ib);
+    u.sinkfrac = reinterpret_cast<double*>(buf + o_sf);
     cudaError_t e = cudaMemcpy(buf + o_fo, d->face_off, sizeof(long long) * (size_t)(6 * nc + 1),
                                cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_sub, sub.data(), sizeof(mp::UsgSub) * sub.size(), cudaMemcpyHostToDevice);
@@ -463,8 +467,8 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_por, d->porosity, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = mp::launch_build_usg(u, const_cast<mp::UsgCell*>(u.cell), const_cast<mp::UsgGeo*>(u.geo),
-                                 reinterpret_cast<double*>(buf + o_box), reinterpret_cast<double*>(buf + o_por),
-                                 nullptr);
+                                 reinterpret_cast<double*>(buf + o_sf), reinterpret_cast<double*>(buf + o_box),
+                                 reinterpret_cast<double*>(buf + o_por), nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(buf);
@@ -674,6 +678,8 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown schedule");
     if (o->block < 0 || o->block > 1024) return fail(MP_ERR_INVALID_ARG, "mp_track: block outside [0, 1024]");
     if (std::isnan(o->t_stop)) return fail(MP_ERR_INVALID_ARG, "mp_track: t_stop is NaN");
+    if (!(o->weak_sink_fraction >= 0.0 && o->weak_sink_fraction <= 1.0))
+        return fail(MP_ERR_INVALID_ARG, "mp_track: weak_sink_fraction outside [0, 1]");
     const bool want_ts = (o->mode & MP_MODE_TIMESERIES) != 0;
     if (want_ts && (o->n_times <= 0 || !o->times))
         return fail(MP_ERR_INVALID_ARG, "mp_track: timeseries mode needs output times");
@@ -762,6 +768,7 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
     p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
+    p.sink_frac = o->weak_sink_fraction;
     p.cont = 0;
     p.last = 1;
     split_ff(t_stop, p.tstop_hi, p.tstop_lo);

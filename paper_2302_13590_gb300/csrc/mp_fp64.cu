@@ -34,8 +34,22 @@ __device__ __forceinline__ int nb_class(const DevField& f, int k, int i, int j)
     return NB_BOUNDARY;
 }
 
-__global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const double* qx, const double* qy,
-                                const double* qz, const double* por)
+// fraction of a cell's inflow its sink extracts, from the volume balance of
+// its six face flows (+axis direction), face by face in the order x-, x+,
+// y-, y+, z-, z+; no inflow: 1
+__device__ double sink_fraction6(const double q[6])
+{
+    double in = 0.0, out = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double q1 = q[2 * a], q2 = q[2 * a + 1];
+        if (q1 > 0.0) in += q1; else out += -q1;
+        if (q2 < 0.0) in += -q2; else out += q2;
+    }
+    return in > 0.0 ? (in - out) / in : 1.0;
+}
+
+__global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, double* sinkfrac, const double* qx,
+                                const double* qy, const double* qz, const double* por)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= f.ncell) return;
@@ -74,7 +88,12 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const do
         s.u1x = (float)(r.v1x / dx); s.u2x = (float)(v2x / dx);
         s.u1y = (float)(r.v1y / dy); s.u2y = (float)(v2y / dy);
         s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(v2z / dzz);
+        if (ib == 2) {
+            const double q6[6] = {qx1, qx2, qy1, qy2, qz1, qz2};
+            sinkfrac[c] = sink_fraction6(q6);
+        }
     }
+    if (ib != 2) sinkfrac[c] = 0.0;
     const double v1a[3] = {r.v1x, r.v1y, r.v1z}, v2a[3] = {v2x, v2y, v2z};
     for (int a = 0; a < 3; ++a) {
         const unsigned long long sg = (v1a[a] > 0.0 ? 1ULL : 0ULL) | (v1a[a] < 0.0 ? 2ULL : 0ULL) |
@@ -90,13 +109,14 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, const do
     r32[c] = s;
 }
 
-cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, const double* qx,
-                                 const double* qy, const double* qz, const double* por, cudaStream_t s)
+cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, double* sinkfrac,
+                                 const double* qx, const double* qy, const double* qz, const double* por,
+                                 cudaStream_t s)
 {
     if (f.ncell <= 0) return cudaSuccess;
     const int b = 256;
     const long long g = (f.ncell + b - 1) / b;
-    k_build_records<<<(unsigned)g, b, 0, s>>>(f, rec64, rec32, qx, qy, qz, por);
+    k_build_records<<<(unsigned)g, b, 0, s>>>(f, rec64, rec32, sinkfrac, qx, qy, qz, por);
     return cudaGetLastError();
 }
 
@@ -374,7 +394,7 @@ struct F64Engine {
             s.in_sink = ib == 2;
             if (s.st == MP_ST_ACTIVE) {
                 if (ib == 0 || ib == -1) s.st = MP_ST_BOUNDARY;
-                else if (ib == 2 && !p.pass_sinks) s.st = MP_ST_SINK;
+                else if (ib == 2 && sink_stops(p, f.sinkfrac, s.c)) s.st = MP_ST_SINK;
             }
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
@@ -593,13 +613,14 @@ struct F64Engine {
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3ULL);
-        if (cls != NB_ACTIVE && !(cls == NB_SINK && p.pass_sinks)) {
+        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
+        if (cls != NB_ACTIVE &&
+            !(cls == NB_SINK && !sink_stops(p, f.sinkfrac, s.c + dj + di * f.ncol + dk * f.ncol * f.nrow))) {
             s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
             return;
         }
         s.in_sink = cls == NB_SINK;
         // hand over to the neighbour; the exit coordinate enters on the shared face
-        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
         s.j += dj;
         s.i += di;
         s.k += dk;

@@ -57,6 +57,7 @@ struct DevField {
     const double* yf;  // [nrow+1]
     const double* zf;  // [nlay+1]
     const int8_t* ibound;
+    const double* sinkfrac;   // per cell: fraction of the inflow a sink cell extracts
     // x / ncol and x / nrow as a 64-bit multiply-high (x < 2^32):
     // floor(x / d) == umul64hi(x, floor((2^64 - 1) / d) + 1) for 1 < d < 2^32
     unsigned long long m_ncol, m_nrow;
@@ -142,12 +143,22 @@ struct TrackParams {
     int steps_per_fetch;
     int update_group;
     int pass_sinks;              // enter sink cells, leave through outflow faces
+    double sink_frac;            // > 0 with pass_sinks: sinks extracting at least this fraction still stop
     int cont;                    // a later flow period of one request: skip ended particles and
                                  // output times already written
     int last;                    // the request's last launch: count particles paused at its stop time
     int pathline;                // append pathline points
     float tstop_hi, tstop_lo;    // t_stop as an FP32 pair (inf, 0 when infinite)
 };
+
+#ifdef __CUDACC__
+// a sink cell with extraction fraction sf stops particles (entering it or
+// resumed in it): always without pass-through, with it when sf >= sink_frac > 0
+__device__ __forceinline__ bool sink_stops(const TrackParams& p, const double* sinkfrac, long long c)
+{
+    return !p.pass_sinks || (p.sink_frac > 0.0 && __ldg(sinkfrac + c) >= p.sink_frac);
+}
+#endif
 
 // One tracking request of a launch: its particle state, outputs and options.
 struct Req {
@@ -210,10 +221,11 @@ struct DevUsg {
     const long long* face_off;
     const UsgSub* sub;
     const int8_t* ibound;
+    const double* sinkfrac;   // per cell: fraction of the inflow a sink cell extracts
 };
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, const double* box, const double* por,
-                             cudaStream_t s);
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, const double* box,
+                             const double* por, cudaStream_t s);
 cudaError_t launch_release_explicit_usg(const DevUsg& u, const DevState& st, long long n, const int32_t* cell,
                                         const double* local, const double* t0, cudaStream_t s);
 cudaError_t launch_track_usg(const DevUsg& u, const Batch& b, unsigned modes, int schedule, int block,
@@ -229,8 +241,9 @@ struct BoxRelease {
 
 cudaError_t launch_release_boxes(const DevField& f, const BoxRelease* d, const long long* starts, int n_reqs,
                                  long long n_total, cudaStream_t s);
-cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, const double* qx,
-                                 const double* qy, const double* qz, const double* por, cudaStream_t s);
+cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, double* sinkfrac,
+                                 const double* qx, const double* qy, const double* qz, const double* por,
+                                 cudaStream_t s);
 cudaError_t launch_release_box(const DevField& f, const DevState& st, long long n, const double lo[3],
                                const double hi[3], unsigned long long seed, unsigned long long id_offset,
                                cudaStream_t s);

@@ -225,7 +225,7 @@ struct MixEngine {
             s.in_sink = ib == 2;
             if (s.st == MP_ST_ACTIVE) {
                 if (ib == 0 || ib == -1) s.st = MP_ST_BOUNDARY;
-                else if (ib == 2 && !p.pass_sinks) s.st = MP_ST_SINK;
+                else if (ib == 2 && sink_stops(p, f.sinkfrac, s.c)) s.st = MP_ST_SINK;
             }
         } else {
             s.c = -1; s.i = s.j = s.k = 0;
@@ -393,12 +393,13 @@ struct MixEngine {
         const int fidx = 2 * ax + (face > 0 ? 1 : 0);
         s.ef = fidx;
         const int cls = (int)((nb >> (2 * fidx)) & 3u);
-        if (cls != NB_ACTIVE && !(cls == NB_SINK && p.pass_sinks)) {
+        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
+        if (cls != NB_ACTIVE &&
+            !(cls == NB_SINK && !sink_stops(p, f.sinkfrac, s.c + dj + di * f.ncol + dk * f.ncol * f.nrow))) {
             s.st = cls == NB_OUTSIDE ? MP_ST_EXIT_DOMAIN : (cls == NB_BOUNDARY ? MP_ST_BOUNDARY : MP_ST_SINK);
             return;
         }
         s.in_sink = cls == NB_SINK;
-        const int dj = ax == 0 ? face : 0, di = ax == 1 ? face : 0, dk = ax == 2 ? face : 0;
         s.j += dj;
         s.i += di;
         s.k += dk;

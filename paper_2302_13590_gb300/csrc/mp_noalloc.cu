@@ -71,6 +71,8 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     if (o->schedule != MP_SCHED_STATIC && o->schedule != MP_SCHED_DYNAMIC)
         return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: unknown schedule");
     if (std::isnan(o->t_stop)) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: t_stop is NaN");
+    if (!(o->weak_sink_fraction >= 0.0 && o->weak_sink_fraction <= 1.0))
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: weak_sink_fraction outside [0, 1]");
     const bool want_ts = (o->mode & MP_MODE_TIMESERIES) != 0;
     const int nt = want_ts ? o->n_times : 0;
     if (want_ts && (nt <= 0 || !o->times || !a->ts))
@@ -128,6 +130,7 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     p.steps_per_fetch = o->steps_per_fetch > 0 ? o->steps_per_fetch : 4;
     p.update_group = (o->flags & MP_TRACK_UPDATE_GROUP) ? 1 : 0;
     p.pass_sinks = (o->flags & MP_TRACK_PASS_WEAK_SINKS) ? 1 : 0;
+    p.sink_frac = o->weak_sink_fraction;
     p.cont = 0;
     p.last = 1;
     split_ff(p.t_stop, p.tstop_hi, p.tstop_lo);

@@ -37,7 +37,21 @@ __device__ __forceinline__ double usg_face_flow(const DevUsg& u, long long c, in
     return s;
 }
 
-__global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, const double* box, const double* por)
+// fraction of a cell's inflow its sink extracts (face totals in the order
+// x-, x+, y-, y+, z-, z+, as the rectilinear grid's); no inflow: 1
+__device__ double usg_sink_fraction(const double q[6])
+{
+    double in = 0.0, out = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double q1 = q[2 * a], q2 = q[2 * a + 1];
+        if (q1 > 0.0) in += q1; else out += -q1;
+        if (q2 < 0.0) in += -q2; else out += q2;
+    }
+    return in > 0.0 ? (in - out) / in : 1.0;
+}
+
+__global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfrac, const double* box,
+                            const double* por)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= u.ncell) return;
@@ -46,15 +60,20 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, const double* b
     for (int a = 0; a < 3; ++a) { gm.o[a] = b[a]; gm.D[a] = b[3 + a]; }
     const int8_t ib = u.ibound[c];
     double v1[3] = {0.0, 0.0, 0.0}, v2[3] = {0.0, 0.0, 0.0};
+    double sf = 0.0;
     if (ib == 1 || ib == 2) {
         const double n = por[c];
         const double dx = b[3], dy = b[4], dzz = b[5];
         const double area[3] = {dy * dzz, dx * dzz, dx * dy};
+        double q6[6];
+        for (int fi = 0; fi < 6; ++fi) q6[fi] = usg_face_flow(u, c, fi);
         for (int a = 0; a < 3; ++a) {
-            v1[a] = usg_face_flow(u, c, 2 * a) / (n * area[a]);
-            v2[a] = usg_face_flow(u, c, 2 * a + 1) / (n * area[a]);
+            v1[a] = q6[2 * a] / (n * area[a]);
+            v2[a] = q6[2 * a + 1] / (n * area[a]);
         }
+        if (ib == 2) sf = usg_sink_fraction(q6);
     }
+    sinkfrac[c] = sf;
     double A[3], iA[3];
     UsgCell r{};
     unsigned long long sg = 0;
@@ -76,11 +95,11 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, const double* b
     geo[c] = gm;
 }
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, const double* box, const double* por,
-                             cudaStream_t s)
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, const double* box,
+                             const double* por, cudaStream_t s)
 {
     if (u.ncell <= 0) return cudaSuccess;
-    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, geo, box, por);
+    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, geo, sinkfrac, box, por);
     return cudaGetLastError();
 }
 
@@ -195,7 +214,7 @@ struct UsgEngine {
             s.in_sink = ib == 2;
             if (s.st == MP_ST_ACTIVE) {
                 if (ib == 0 || ib == -1) s.st = MP_ST_BOUNDARY;
-                else if (ib == 2 && !p.pass_sinks) s.st = MP_ST_SINK;
+                else if (ib == 2 && sink_stops(p, u.sinkfrac, s.c)) s.st = MP_ST_SINK;
             }
         } else {
             s.c = -1;
@@ -462,7 +481,7 @@ struct UsgEngine {
             s.st = MP_ST_BOUNDARY;
             return;
         }
-        if (ib == 2 && !p.pass_sinks) {
+        if (ib == 2 && sink_stops(p, u.sinkfrac, nc)) {
             s.st = MP_ST_SINK;
             return;
         }

@@ -69,7 +69,7 @@ class TrackOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("n_times", ctypes.c_int32), ("times", _vp), ("t_stop", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("block", ctypes.c_int32), ("steps_per_fetch", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("path_capacity", ctypes.c_int64)]
+                ("flags", ctypes.c_uint32), ("path_capacity", ctypes.c_int64), ("weak_sink_fraction", ctypes.c_double)]
 
 
 class UsgDesc(ctypes.Structure):
@@ -338,10 +338,11 @@ def mp_track_periods(ctx, gh, fields, t_end, opts: "TrackOpts", stream=None) -> 
 
 
 def make_opts(mode=MODE_ENDPOINT, precision=PREC_FP64, schedule=SCHED_DYNAMIC, times=None, t_stop=math.inf,
-              max_steps=0, block=0, steps_per_fetch=0, flags=0, path_capacity=0):
+              max_steps=0, block=0, steps_per_fetch=0, flags=0, path_capacity=0, weak_sink_fraction=0.0):
     tarr = None if times is None else _host(times, np.float64)
     o = TrackOpts(int(mode), int(precision), int(schedule), 0 if tarr is None else int(tarr.size), _ptr(tarr),
-                  float(t_stop), int(max_steps), int(block), int(steps_per_fetch), int(flags), int(path_capacity))
+                  float(t_stop), int(max_steps), int(block), int(steps_per_fetch), int(flags), int(path_capacity),
+                  float(weak_sink_fraction))
     o._keep = tarr
     return o
 

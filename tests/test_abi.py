@@ -52,8 +52,8 @@ int main(void) {{
          offsetof(mp_track_opts, block), offsetof(mp_track_opts, flags));
   printf("%zu %zu %zu %zu\\n", sizeof(mp_endpoints), sizeof(mp_stats), offsetof(mp_stats, kernel_ms),
          offsetof(mp_stats, path_points));
-  printf("%zu %zu %zu\\n", offsetof(mp_track_opts, path_capacity), sizeof(mp_path_record),
-         offsetof(mp_path_record, seq));
+  printf("%zu %zu %zu %zu\\n", offsetof(mp_track_opts, path_capacity), sizeof(mp_path_record),
+         offsetof(mp_path_record, seq), offsetof(mp_track_opts, weak_sink_fraction));
   return 0;
 }}
 """)
@@ -66,7 +66,8 @@ int main(void) {{
     assert got[2] == [ctypes.sizeof(T), T.t_stop.offset, T.block.offset, T.flags.offset]
     assert got[3] == [ctypes.sizeof(mp.Endpoints), ctypes.sizeof(mp.Stats), mp.Stats.kernel_ms.offset,
                       mp.Stats.path_points.offset]
-    assert got[4] == [T.path_capacity.offset, mp.PATH_RECORD.itemsize, mp.PATH_RECORD.fields["seq"][1]]
+    assert got[4] == [T.path_capacity.offset, mp.PATH_RECORD.itemsize, mp.PATH_RECORD.fields["seq"][1],
+                      T.weak_sink_fraction.offset]
 
 
 def test_no_device_calls_fail_cleanly_without_gpu():

@@ -162,6 +162,57 @@ def test_fp64_exact_ties(ctx):
         mp.mp_field_free(fh)
 
 
+def test_weak_sink_fraction_vs_oracle(ctx):
+    """Weak sinks with a threshold: sink cells extracting at least the given
+    fraction of their inflow stop particles, the others are passed (FP64
+    bit-exact against the oracle at thresholds below, between and above the
+    wells' fractions, both schedules, with timeseries and pathlines; mixed
+    precision: the same statuses on particles whose path matches).
+    Fractions outside [0, 1] are rejected."""
+    from tests.test_oracle_weak_sinks import _fractions_structured
+    f = I.random_box_field(3, 10, 14, seed=40, lnk_var=0.5, n_wells=5, well_scale=10.0)
+    fh = ctx.field(f)
+    fr = _fractions_structured(f)
+    fs = np.sort(fr[f.ibound.reshape(-1) == 2])
+    assert fs[0] > 0 and fs[-1] < 1
+    cells, frac = I.explicit_particles(f, 3001, seed=17, cols=(1, 6))
+    st0 = O.release_explicit(f, cells, frac)
+    full = O.track(f, st0, pass_weak_sinks=True)
+    times = np.quantile(full["t"], [0.2, 0.5, 0.9])
+    thresholds = [fs[0] / 2] + list((fs[:-1] + fs[1:]) / 2) + [(fs[-1] + 1) / 2]
+    for thr in thresholds:
+        ref = O.track(f, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True)
+        for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+            gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
+            req = ctx.track(gh, mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES | mp.MODE_PATHLINE, times=times,
+                            schedule=sch, flags=mp.TRACK_PASS_WEAK_SINKS, weak_sink_fraction=thr,
+                            path_capacity=400 * cells.size)
+            req.wait()
+            ep, ts, path = req.endpoints(), req.timeseries(), req.pathlines()
+            G.compare_fp64(ep, ref, dmin=G.dmin(f))
+            G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+            g, r = (np.sort(x, order=["particle", "seq"]) for x in (path, ref["path"]))
+            assert np.array_equal(g[["particle", "cell", "seq", "status"]], r[["particle", "cell", "seq", "status"]])
+            req.free()
+            mp.mp_group_free(gh)
+        gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
+        req = ctx.track(gh, precision=mp.PREC_MIXED, flags=mp.TRACK_PASS_WEAK_SINKS, weak_sink_fraction=thr)
+        req.wait()
+        mx = req.endpoints()
+        req.free()
+        mp.mp_group_free(gh)
+        keep = mx["hash"] == ref["hash"]
+        assert keep.mean() >= 0.98
+        assert np.array_equal(mx["status"][keep], ref["status"][keep])
+    gh = mp.mp_release_group(ctx.h, fh, cell=cells[:10], local=frac[:10])
+    for bad in (1.5, -0.1, float("nan")):
+        with pytest.raises(mp.MPError) as e:
+            ctx.track(gh, flags=mp.TRACK_PASS_WEAK_SINKS, weak_sink_fraction=bad)
+        assert e.value.code == mp.ERR_INVALID_ARG
+    mp.mp_group_free(gh)
+    mp.mp_field_free(fh)
+
+
 @pytest.mark.parametrize("scale,seed", [(30.0, 40), (1.0, 40), (30.0, 45)])
 def test_weak_sinks_pass_through(ctx, scale, seed):
     """Weak sinks: particles enter well cells and leave through reachable

@@ -137,6 +137,26 @@ def test_hand_over_moved_point_vs_oracle(ctx):
         mp.mp_field_free(fh)
 
 
+def test_quadtree_weak_sink_fraction_vs_oracle(ctx):
+    """Weak sinks with a threshold on a quadtree (sink fractions from the
+    faces' total flows): FP64 bit-exact against the oracle below, between
+    and above the wells' fractions."""
+    from tests.test_oracle_weak_sinks import _fractions_usg
+    u = U.quadtree_field(2, 8, 12, seed=15, n_wells=3, well_rate=0.05)
+    fh = ctx.field(u)
+    fs = np.sort(_fractions_usg(u)[u.ibound == U.IB_SINK])
+    cells, frac = U.explicit_particles(u, 2000, seed=6)
+    st0 = O.release_explicit(u, cells, frac)
+    for thr in [fs[0] / 2] + list((fs[:-1] + fs[1:]) / 2) + [(fs[-1] + 1) / 2]:
+        ref = O.track(u, st0, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True)
+        ep, _, st, path = _run(ctx, fh, cells, frac, flags=mp.TRACK_PASS_WEAK_SINKS, weak_sink_fraction=thr,
+                               mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE, path_capacity=200 * cells.size)
+        G.compare_fp64(ep, ref, dmin=_dmin(u))
+        g, r = (np.sort(x, order=["particle", "seq"]) for x in (path, ref["path"]))
+        assert np.array_equal(g[["particle", "cell", "seq", "status"]], r[["particle", "cell", "seq", "status"]])
+    mp.mp_field_free(fh)
+
+
 def test_usg_rejections(ctx):
     u = U.quadtree_field(2, 6, 8, seed=3, n_wells=1)
     fh = ctx.field(u)
