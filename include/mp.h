@@ -453,7 +453,10 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches);
  * the caller; the call returns after the last copy has landed (bounded
  * wait, 60 s) and frees what it allocated.  stats (may be NULL): the sums of
  * the chunks' counters; kernel_ms = device time from the first chunk's
- * start to the last chunk's last copy.  MP_MODE_PATHLINE is rejected.
+ * start to the last chunk's last copy.  The two streams belong to the
+ * context and are kept for its later calls (the chunks' buffers are then
+ * reused in stream order); calls on one context run one at a time.
+ * MP_MODE_PATHLINE is rejected.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_NONFINITE, MP_ERR_OOM, MP_ERR_TIMEOUT,
  * MP_ERR_DEVICE, MP_ERR_CUDA. */
 int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell, const double* local,

@@ -148,6 +148,8 @@ struct TuneKey {
 struct mp_ctx {
     int device = 0;
     std::mutex mu;
+    std::mutex host_mu;                             // one mp_track_host at a time per context
+    cudaStream_t host_st[2] = {nullptr, nullptr};   // its two streams, made on first use
     std::map<TuneKey, mp_tuning> tuned;
     std::map<int64_t, Request*> reqs;
     std::set<mp_field*> fields;
@@ -235,6 +237,8 @@ int mp_ctx_destroy(mp_ctx* ctx)
     std::vector<mp_field*> fs(ctx->fields.begin(), ctx->fields.end());
     for (mp_field* f : fs) mp_field_free(f);
     cudaDeviceSynchronize();
+    for (cudaStream_t x : ctx->host_st)
+        if (x) cudaStreamDestroy(x);
     delete ctx;
     return MP_OK;
 }
@@ -1232,7 +1236,9 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
     mp_track_opts oc = *o;
     if (oc.schedule == MP_SCHED_AUTO) oc.schedule = MP_SCHED_STATIC;
 
-    cudaStream_t st[2] = {nullptr, nullptr};
+    // the context's two streams, kept across calls so that the chunks'
+    // buffers are reused in stream order from the memory pool
+    std::lock_guard<std::mutex> host_lk(ctx->host_mu);
     cudaEvent_t ev_start = nullptr, ev_join = nullptr, ev_end = nullptr;
     std::vector<mp_group*> groups;
     std::vector<mp_req> ids;
@@ -1241,9 +1247,10 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
         if (e != cudaSuccess && rc == MP_OK) rc = cuda_fail(e, what);
         return rc == MP_OK;
     };
-    cu(cudaStreamCreateWithFlags(&st[0], cudaStreamNonBlocking), "mp_track_host: stream") &&
-        cu(cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking), "mp_track_host: stream") &&
-        cu(cudaEventCreate(&ev_start), "mp_track_host: event") &&
+    for (cudaStream_t& x : ctx->host_st)
+        if (!x) cu(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "mp_track_host: stream");
+    cudaStream_t* st = ctx->host_st;
+    (rc == MP_OK) && cu(cudaEventCreate(&ev_start), "mp_track_host: event") &&
         cu(cudaEventCreate(&ev_join), "mp_track_host: event") && cu(cudaEventCreate(&ev_end), "mp_track_host: event") &&
         cu(cudaEventRecord(ev_start, st[0]), "mp_track_host: event") &&
         cu(cudaStreamWaitEvent(st[1], ev_start, 0), "mp_track_host: event");
@@ -1325,8 +1332,6 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
     if (st[1]) cudaStreamSynchronize(st[1]);
     for (cudaEvent_t e : {ev_start, ev_join, ev_end})
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t x : st)
-        if (x) cudaStreamDestroy(x);
     return rc;
 }
 
