@@ -93,6 +93,28 @@ def test_host_call_pinned_buffers_and_endpoint_mode(ctx, case):
     assert np.array_equal(ep2["cell"], ref_ep["cell"]) and np.array_equal(ep2["t"], ref_ep["t"])
 
 
+def test_host_call_on_a_quadtree(ctx):
+    """The host call on a quadtree grid (FP64, weak sinks with a threshold):
+    equal to one request bit for bit, and to the oracle."""
+    from paper_2302_13590_gb300.inputs import usg as U
+    u = U.quadtree_field(2, 8, 12, seed=15, n_wells=3, well_rate=0.05)
+    fu = ctx.field(u)
+    cells, frac = U.explicit_particles(u, 1500, seed=8)
+    st0 = O.release_explicit(u, cells, frac)
+    times = np.quantile(O.track(u, st0, pass_weak_sinks=True)["t"], [0.3, 0.7])
+    opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, times=times, flags=mp.TRACK_PASS_WEAK_SINKS,
+                        weak_sink_fraction=0.5)
+    ref_ep, ref_ts, _ = _one_request(ctx, fu, cells, frac, None, opts)
+    ep, ts, st = mp.mp_track_host(ctx.h, fu, cells, frac, opts, n_chunks=4)
+    for k in ref_ep:
+        assert np.array_equal(ep[k], ref_ep[k], equal_nan=True), k
+    assert ts.tobytes() == ref_ts.tobytes()
+    ref = O.track(u, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=0.5)
+    G.compare_fp64(ep, ref, dmin=u.extent)
+    G.compare_timeseries_fp64(ts, ref, dmin=u.extent)
+    mp.mp_field_free(fu)
+
+
 def test_host_call_rejections_and_empty(ctx, case):
     f, fh, cells, frac, t0, times = case
     with pytest.raises(mp.MPError) as e:

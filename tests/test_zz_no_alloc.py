@@ -41,8 +41,9 @@ def _host(out):
     return h
 
 
-@pytest.mark.parametrize("precision", [mp.PREC_FP64, mp.PREC_MIXED])
-def test_noalloc_matches_track(precision):
+@pytest.mark.parametrize("precision,flags,wsf", [(mp.PREC_FP64, 0, 0.0), (mp.PREC_MIXED, 0, 0.0),
+                                                 (mp.PREC_FP64, mp.TRACK_PASS_WEAK_SINKS, 0.5)])
+def test_noalloc_matches_track(precision, flags, wsf):
     torch = pytest.importorskip("torch")
     w = I.workload("cfg1")
     with mp.Context(0) as ctx:
@@ -52,7 +53,7 @@ def test_noalloc_matches_track(precision):
         ep0 = r0.endpoints()
         r0.free()
         ref_req = ctx.track(gh, mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=precision,
-                            schedule=mp.SCHED_DYNAMIC, times=w.times)
+                            schedule=mp.SCHED_DYNAMIC, times=w.times, flags=flags, weak_sink_fraction=wsf)
         ref = ref_req.endpoints()
         ref_ts = ref_req.timeseries()
         ref_st = ref_req.stats()
@@ -60,7 +61,7 @@ def test_noalloc_matches_track(precision):
         n, nt = w.release.n, len(w.times)
         state = _device_state(torch, ep0)
         opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, precision=precision,
-                            schedule=mp.SCHED_DYNAMIC, times=w.times)
+                            schedule=mp.SCHED_DYNAMIC, times=w.times, flags=flags, weak_sink_fraction=wsf)
         for call in range(2):
             out = _device_out(torch, n)
             ts = torch.empty(nt * n * 32, dtype=torch.uint8, device="cuda")
