@@ -50,14 +50,16 @@ def _run(ctx, fhs, T, cells, frac, t0=None, **kw):
     return ep, ts, st
 
 
-@pytest.mark.parametrize("schedule,pass_sinks", [(mp.SCHED_STATIC, False), (mp.SCHED_DYNAMIC, False),
-                                                  (mp.SCHED_DYNAMIC, True)])
-def test_periods_fp64_vs_oracle(ctx, small, schedule, pass_sinks):
+@pytest.mark.parametrize("schedule,pass_sinks,wsf", [(mp.SCHED_STATIC, False, 0.0), (mp.SCHED_DYNAMIC, False, 0.0),
+                                                      (mp.SCHED_DYNAMIC, True, 0.0), (mp.SCHED_STATIC, True, 0.3)])
+def test_periods_fp64_vs_oracle(ctx, small, schedule, pass_sinks, wsf):
+    """Flow periods (and weak sinks, passed or with a threshold: each
+    period's field has its own sink fractions) against the oracle."""
     f, fs, fhs, cells, frac, st0, full, T = small
     times = np.sort(np.concatenate([np.quantile(full["t"], [0.02, 0.1, 0.4, 0.8, 0.97]) * 1.01, T]))
     flags = mp.TRACK_PASS_WEAK_SINKS if pass_sinks else 0
-    ref = O.track_periods(fs, T, st0, times=times, pass_weak_sinks=pass_sinks)
-    ep, ts, st = _run(ctx, fhs, T, cells, frac, times=times, schedule=schedule, flags=flags)
+    ref = O.track_periods(fs, T, st0, times=times, pass_weak_sinks=pass_sinks, weak_sink_fraction=wsf)
+    ep, ts, st = _run(ctx, fhs, T, cells, frac, times=times, schedule=schedule, flags=flags, weak_sink_fraction=wsf)
     G.compare_fp64(ep, ref, dmin=G.dmin(f))
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
     assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
