@@ -226,10 +226,13 @@ typedef struct {
 /* Context on one CUDA device.  The device is made current on the calling
  * thread.  Errors: MP_ERR_INVALID_ARG, MP_ERR_CUDA. */
 int mp_ctx_create(int device, mp_ctx** out);
-/* Frees every field, group and request still owned by the context. */
+/* Frees every field, group, request and graph still owned by the context
+ * (waiting, bounded, for their work).  Errors: MP_ERR_INVALID_ARG (NULL). */
 int mp_ctx_destroy(mp_ctx* ctx);
 
-/* Message for this thread's last failed call ("" if none). */
+/* Message for this thread's last failed call ("" if none); the string is
+ * owned by the library and valid until the thread's next failing call.
+ * Never fails. */
 const char* mp_last_error(void);
 
 /* Copy (or read, MP_DEVICE_PTR) a flow field and build its device form:
@@ -271,7 +274,7 @@ typedef struct {
 } mp_usg_desc;
 
 int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out);
-/* Device bytes held by a loaded field. */
+/* Device bytes held by a loaded field.  Errors: MP_ERR_INVALID_ARG (NULL). */
 int mp_field_bytes(const mp_field* f, size_t* bytes);
 
 /* Create a particle group on the field (state resident on the device).
@@ -353,7 +356,9 @@ typedef struct {
 int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample, void* stream, mp_tuning* out);
 
 /* Install a launch configuration (e.g. one cached from an earlier run) for
- * (field, precision, timeseries). */
+ * (field, precision, timeseries).  Errors: MP_ERR_INVALID_ARG (NULL, a
+ * schedule other than static or dynamic, block outside [32, 256], or a
+ * negative steps per fetch). */
 int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t timeseries, const mp_tuning* t);
 
 /* Captured batches (the batching pattern's CUDA graphs; the paper's many
@@ -371,18 +376,22 @@ int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release
                     const mp_track_opts* opts, void* stream, mp_graph** out);
 /* Replace request i's box, seed and id offset for later launches (the
  * particle count is fixed: MP_ERR_SHAPE otherwise).  Ordered after earlier
- * work on `stream`; returns once the descriptor is on the device. */
+ * work on `stream`; returns once the descriptor is on the device.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_CUDA. */
 int mp_graph_set_release(mp_graph* g, int i, const mp_release_desc* rel, void* stream);
 /* Replay the graph on `stream` (asynchronous).  Outputs of the previous
- * launch are overwritten: read them first (stream order). */
+ * launch are overwritten: read them first (stream order).
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_CUDA. */
 int mp_graph_launch(mp_graph* g, void* stream);
 /* The request ids (n_reqs of them) through which a launch's outputs are
  * read with mp_wait, mp_get_endpoints, mp_get_timeseries, mp_get_pathlines
  * and mp_get_stats (kernel_ms then spans the whole graph).  They belong to
- * the graph: mp_req_free refuses them, mp_graph_free releases them. */
+ * the graph: mp_req_free refuses them, mp_graph_free releases them.
+ * ids has room for n_reqs entries.  Errors: MP_ERR_INVALID_ARG (NULL). */
 int mp_graph_requests(const mp_graph* g, mp_req* ids);
 /* Waits (bounded) for the last launch, then frees everything the graph
- * holds.  The field must outlive the graph. */
+ * holds.  The field must outlive the graph.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_TIMEOUT (then nothing is freed). */
 int mp_graph_free(mp_graph* g);
 
 /* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
@@ -416,19 +425,28 @@ int mp_get_pathlines(mp_ctx* ctx, mp_req id, mp_path_record* out, int64_t max_po
                      uint32_t flags, void* stream);
 
 /* Device views of the request's own output buffers (valid until
- * mp_req_free); any out-pointer may be NULL. */
+ * mp_req_free); any out-pointer may be NULL.  The pointers are the
+ * library's: read them in stream order after the request.
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (unknown id). */
 int mp_endpoints_device(mp_ctx* ctx, mp_req r, mp_endpoints* out, mp_ts_record** ts);
 
-/* Counters of a finished request (waits, bounded, like mp_get_endpoints). */
+/* Counters of a finished request (waits, bounded, like mp_get_endpoints).
+ * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (unknown id),
+ * MP_ERR_TIMEOUT, MP_ERR_CUDA. */
 int mp_get_stats(mp_ctx* ctx, mp_req r, mp_stats* out);
 
-/* Release a request's outputs (stream-ordered after its work). */
+/* Release a request's outputs (stream-ordered after its work); the id is
+ * unknown afterwards.  Errors: MP_ERR_INVALID_ARG (NULL, or a request
+ * owned by a graph), MP_ERR_NOT_READY (unknown id). */
 int mp_req_free(mp_ctx* ctx, mp_req r);
 
-/* Device bytes mp_track allocates for n particles under options o. */
+/* Device bytes mp_track allocates for n particles under options o (the
+ * serving layer's admission uses it).  Errors: MP_ERR_INVALID_ARG. */
 int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes);
 
-/* Number of CUDA kernel launches mp_track issues for these options. */
+/* Number of CUDA kernel launches mp_track issues for these options (one
+ * tracking launch per request; mp_track_periods: one per period).
+ * Errors: MP_ERR_INVALID_ARG (NULL). */
 int mp_track_launches(const mp_track_opts* o, int32_t* launches);
 
 /* ---- host to host, transfers overlapped with tracking ----------------------
