@@ -244,6 +244,24 @@ const char* mp_last_error(void);
 int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out);
 int mp_field_free(mp_field* f);
 
+/* Volume balance of a loaded field (rectilinear or quadtree), computed once
+ * when it is loaded from its face flows (the face totals the velocities use):
+ * per cell, inflow = the flow entering through its faces and outflow = the
+ * flow leaving, summed face by face in the order x-, x+, y-, y+, z-, z+.
+ * Pollock's method assumes every active cell conserves volume; a sink cell
+ * extracts inflow - outflow.  All sums in cell order. */
+typedef struct {
+    double max_abs_residual;  /* active cells (ibound 1): max |inflow - outflow| (m^3/s) */
+    int64_t max_abs_cell;     /* the first active cell with that residual; -1: none */
+    double max_rel_residual;  /* active cells with inflow: max |inflow - outflow| / inflow */
+    double sink_extraction;   /* sink cells (ibound 2): sum of inflow - outflow (m^3/s) */
+    int64_t active_cells;
+    int64_t sink_cells;
+} mp_balance;
+
+/* Errors: MP_ERR_INVALID_ARG (NULL). */
+int mp_field_balance(const mp_field* f, mp_balance* out);
+
 /* A rectangular unstructured (quadtree) grid: the paper's TC2 also runs on
  * a quadtree refinement of its grid.  Cells are axis-aligned boxes; each
  * face (x-, x+, y-, y+, z-, z+) of cell c has the sub-faces

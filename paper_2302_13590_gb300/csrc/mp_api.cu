@@ -101,6 +101,7 @@ DevState group_view(char* buf, long long n)
 
 struct mp_field {
     mp_ctx* ctx = nullptr;
+    mp_balance balance{};  // volume balance of the face flows (at load)
     int usg = 0;           // 1: rectangular unstructured grid (u), else rectilinear (d)
     DevField d{};
     DevUsg u{};
@@ -191,6 +192,39 @@ int read_counters(Request* r, unsigned long long* h)
 {
     MP_CUDA(cudaMemcpy(h, r->d.counters, sizeof(unsigned long long) * N_COUNTERS, cudaMemcpyDeviceToHost),
             "copy counters");
+    return MP_OK;
+}
+
+// The balance report from per-cell (inflow, outflow) and ibound, in cell order.
+mp_balance reduce_balance(const std::vector<double2>& io, const int8_t* ib, long long ncell)
+{
+    mp_balance b{};
+    b.max_abs_cell = -1;
+    for (long long c = 0; c < ncell; ++c) {
+        const double in = io[(size_t)c].x, out = io[(size_t)c].y;
+        if (ib[c] == 1) {
+            const double r = std::fabs(in - out);
+            if (b.max_abs_cell < 0 || r > b.max_abs_residual) {
+                b.max_abs_residual = r;
+                b.max_abs_cell = c;
+            }
+            if (in > 0.0) b.max_rel_residual = std::max(b.max_rel_residual, r / in);
+            b.active_cells++;
+        } else if (ib[c] == 2) {
+            b.sink_extraction += in - out;
+            b.sink_cells++;
+        }
+    }
+    return b;
+}
+
+// per-cell (inflow, outflow) from the device, reduced on the host
+int balance_from_device(const double2* dio, const int8_t* host_ib, long long ncell, mp_balance* out)
+{
+    std::vector<double2> io((size_t)ncell);
+    if (ncell > 0)
+        MP_CUDA(cudaMemcpy(io.data(), dio, sizeof(double2) * (size_t)ncell, cudaMemcpyDeviceToHost), "balance copy");
+    *out = reduce_balance(io, host_ib, ncell);
     return MP_OK;
 }
 
@@ -359,11 +393,26 @@ int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out)
     f->d.sinkfrac = reinterpret_cast<double*>(buf + o_sf);
     f->d.m_ncol = div_magic((unsigned)nc);
     f->d.m_nrow = div_magic((unsigned)nr);
-    e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32),
-                             reinterpret_cast<double*>(buf + o_sf), qx, qy, qz, por, s);
+    double2* dio = nullptr;
+    e = cudaMalloc(&dio, sizeof(double2) * (size_t)std::max(ncell, 1LL));
+    if (e == cudaSuccess)
+        e = launch_build_records(f->d, const_cast<CellF64*>(f->d.rec64), const_cast<CellF32*>(f->d.rec32),
+                                 reinterpret_cast<double*>(buf + o_sf), dio, qx, qy, qz, por, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (stage) cudaFree(stage);
+    if (e == cudaSuccess) {
+        // the balance report (ibound on the host: the caller's array, or a copy)
+        std::vector<int8_t> hib;
+        const int8_t* ibh = d->ibound;
+        if (dev_in) {
+            hib.resize((size_t)ncell);
+            e = cudaMemcpy(hib.data(), buf + o_ib, (size_t)ncell, cudaMemcpyDeviceToHost);
+            ibh = hib.data();
+        }
+        if (e == cudaSuccess && balance_from_device(dio, ibh, ncell, &f->balance) != MP_OK) e = cudaErrorUnknown;
+    }
+    if (dio) cudaFree(dio);
     if (e != cudaSuccess) {
         delete f;
         cudaFree(buf);
@@ -469,17 +518,23 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_ib, d->ibound, (size_t)nc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_box, d->box, sizeof(double) * 6 * (size_t)nc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(buf + o_por, d->porosity, sizeof(double) * (size_t)nc, cudaMemcpyHostToDevice);
+    double2* dio = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&dio, sizeof(double2) * (size_t)std::max(nc, 1LL));
     if (e == cudaSuccess)
         e = mp::launch_build_usg(u, const_cast<mp::UsgCell*>(u.cell), const_cast<mp::UsgGeo*>(u.geo),
-                                 reinterpret_cast<double*>(buf + o_sf), reinterpret_cast<double*>(buf + o_box),
+                                 reinterpret_cast<double*>(buf + o_sf), dio, reinterpret_cast<double*>(buf + o_box),
                                  reinterpret_cast<double*>(buf + o_por), nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    mp_balance bal{};
+    if (e == cudaSuccess && balance_from_device(dio, d->ibound, nc, &bal) != MP_OK) e = cudaErrorUnknown;
+    if (dio) cudaFree(dio);
     if (e != cudaSuccess) {
         cudaFree(buf);
         return cuda_fail(e, "mp_usg_field_load");
     }
     mp_field* f = new mp_field();
     f->ctx = ctx;
+    f->balance = bal;
     f->usg = 1;
     f->u = u;
     f->buf = buf;
@@ -495,6 +550,13 @@ int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out)
         ctx->fields.insert(f);
     }
     *out = f;
+    return MP_OK;
+}
+
+int mp_field_balance(const mp_field* f, mp_balance* out)
+{
+    if (!f || !out) return fail(MP_ERR_INVALID_ARG, "mp_field_balance: NULL");
+    *out = f->balance;
     return MP_OK;
 }
 

@@ -34,10 +34,9 @@ __device__ __forceinline__ int nb_class(const DevField& f, int k, int i, int j)
     return NB_BOUNDARY;
 }
 
-// fraction of a cell's inflow its sink extracts, from the volume balance of
-// its six face flows (+axis direction), face by face in the order x-, x+,
-// y-, y+, z-, z+; no inflow: 1
-__device__ double sink_fraction6(const double q[6])
+// a cell's inflow and outflow from its six face flows (+axis direction),
+// face by face in the order x-, x+, y-, y+, z-, z+
+__device__ double2 face_inout(const double q[6])
 {
     double in = 0.0, out = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -45,11 +44,17 @@ __device__ double sink_fraction6(const double q[6])
         if (q1 > 0.0) in += q1; else out += -q1;
         if (q2 < 0.0) in += -q2; else out += q2;
     }
-    return in > 0.0 ? (in - out) / in : 1.0;
+    return make_double2(in, out);
 }
 
-__global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, double* sinkfrac, const double* qx,
-                                const double* qy, const double* qz, const double* por)
+// fraction of a cell's inflow its sink extracts; no inflow: 1
+__device__ double sink_fraction(double2 io)
+{
+    return io.x > 0.0 ? (io.x - io.y) / io.x : 1.0;
+}
+
+__global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, double* sinkfrac, double2* inout,
+                                const double* qx, const double* qy, const double* qz, const double* por)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= f.ncell) return;
@@ -88,10 +93,12 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, double* 
         s.u1x = (float)(r.v1x / dx); s.u2x = (float)(v2x / dx);
         s.u1y = (float)(r.v1y / dy); s.u2y = (float)(v2y / dy);
         s.u1z = (float)(r.v1z / dzz); s.u2z = (float)(v2z / dzz);
-        if (ib == 2) {
-            const double q6[6] = {qx1, qx2, qy1, qy2, qz1, qz2};
-            sinkfrac[c] = sink_fraction6(q6);
-        }
+        const double q6[6] = {qx1, qx2, qy1, qy2, qz1, qz2};
+        const double2 io = face_inout(q6);
+        inout[c] = io;
+        if (ib == 2) sinkfrac[c] = sink_fraction(io);
+    } else {
+        inout[c] = make_double2(0.0, 0.0);
     }
     if (ib != 2) sinkfrac[c] = 0.0;
     const double v1a[3] = {r.v1x, r.v1y, r.v1z}, v2a[3] = {v2x, v2y, v2z};
@@ -110,13 +117,13 @@ __global__ void k_build_records(DevField f, CellF64* r64, CellF32* r32, double* 
 }
 
 cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, double* sinkfrac,
-                                 const double* qx, const double* qy, const double* qz, const double* por,
-                                 cudaStream_t s)
+                                 double2* inout, const double* qx, const double* qy, const double* qz,
+                                 const double* por, cudaStream_t s)
 {
     if (f.ncell <= 0) return cudaSuccess;
     const int b = 256;
     const long long g = (f.ncell + b - 1) / b;
-    k_build_records<<<(unsigned)g, b, 0, s>>>(f, rec64, rec32, sinkfrac, qx, qy, qz, por);
+    k_build_records<<<(unsigned)g, b, 0, s>>>(f, rec64, rec32, sinkfrac, inout, qx, qy, qz, por);
     return cudaGetLastError();
 }
 

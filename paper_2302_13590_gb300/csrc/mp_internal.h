@@ -224,8 +224,8 @@ struct DevUsg {
     const double* sinkfrac;   // per cell: fraction of the inflow a sink cell extracts
 };
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, const double* box,
-                             const double* por, cudaStream_t s);
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, double2* inout,
+                             const double* box, const double* por, cudaStream_t s);
 cudaError_t launch_release_explicit_usg(const DevUsg& u, const DevState& st, long long n, const int32_t* cell,
                                         const double* local, const double* t0, cudaStream_t s);
 cudaError_t launch_track_usg(const DevUsg& u, const Batch& b, unsigned modes, int schedule, int block,
@@ -242,8 +242,8 @@ struct BoxRelease {
 cudaError_t launch_release_boxes(const DevField& f, const BoxRelease* d, const long long* starts, int n_reqs,
                                  long long n_total, cudaStream_t s);
 cudaError_t launch_build_records(const DevField& f, CellF64* rec64, CellF32* rec32, double* sinkfrac,
-                                 const double* qx, const double* qy, const double* qz, const double* por,
-                                 cudaStream_t s);
+                                 double2* inout, const double* qx, const double* qy, const double* qz,
+                                 const double* por, cudaStream_t s);
 cudaError_t launch_release_box(const DevField& f, const DevState& st, long long n, const double lo[3],
                                const double hi[3], unsigned long long seed, unsigned long long id_offset,
                                cudaStream_t s);

@@ -37,9 +37,9 @@ __device__ __forceinline__ double usg_face_flow(const DevUsg& u, long long c, in
     return s;
 }
 
-// fraction of a cell's inflow its sink extracts (face totals in the order
-// x-, x+, y-, y+, z-, z+, as the rectilinear grid's); no inflow: 1
-__device__ double usg_sink_fraction(const double q[6])
+// a cell's inflow and outflow from its face totals, face by face in the
+// order x-, x+, y-, y+, z-, z+ (as the rectilinear grid's)
+__device__ double2 usg_face_inout(const double q[6])
 {
     double in = 0.0, out = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -47,11 +47,11 @@ __device__ double usg_sink_fraction(const double q[6])
         if (q1 > 0.0) in += q1; else out += -q1;
         if (q2 < 0.0) in += -q2; else out += q2;
     }
-    return in > 0.0 ? (in - out) / in : 1.0;
+    return make_double2(in, out);
 }
 
-__global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfrac, const double* box,
-                            const double* por)
+__global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfrac, double2* inout,
+                            const double* box, const double* por)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= u.ncell) return;
@@ -61,6 +61,7 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfra
     const int8_t ib = u.ibound[c];
     double v1[3] = {0.0, 0.0, 0.0}, v2[3] = {0.0, 0.0, 0.0};
     double sf = 0.0;
+    double2 io = make_double2(0.0, 0.0);
     if (ib == 1 || ib == 2) {
         const double n = por[c];
         const double dx = b[3], dy = b[4], dzz = b[5];
@@ -71,9 +72,11 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfra
             v1[a] = q6[2 * a] / (n * area[a]);
             v2[a] = q6[2 * a + 1] / (n * area[a]);
         }
-        if (ib == 2) sf = usg_sink_fraction(q6);
+        io = usg_face_inout(q6);
+        if (ib == 2) sf = io.x > 0.0 ? (io.x - io.y) / io.x : 1.0;
     }
     sinkfrac[c] = sf;
+    inout[c] = io;
     double A[3], iA[3];
     UsgCell r{};
     unsigned long long sg = 0;
@@ -95,11 +98,11 @@ __global__ void k_build_usg(DevUsg u, UsgCell* out, UsgGeo* geo, double* sinkfra
     geo[c] = gm;
 }
 
-cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, const double* box,
-                             const double* por, cudaStream_t s)
+cudaError_t launch_build_usg(const DevUsg& u, UsgCell* cell, UsgGeo* geo, double* sinkfrac, double2* inout,
+                             const double* box, const double* por, cudaStream_t s)
 {
     if (u.ncell <= 0) return cudaSuccess;
-    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, geo, sinkfrac, box, por);
+    k_build_usg<<<(unsigned)((u.ncell + 255) / 256), 256, 0, s>>>(u, cell, geo, sinkfrac, inout, box, por);
     return cudaGetLastError();
 }
 

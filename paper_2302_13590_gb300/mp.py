@@ -77,6 +77,12 @@ class UsgDesc(ctypes.Structure):
                                                                  "q", "rect")] + [("flags", ctypes.c_uint32)]
 
 
+class Balance(ctypes.Structure):
+    _fields_ = [("max_abs_residual", ctypes.c_double), ("max_abs_cell", ctypes.c_int64),
+                ("max_rel_residual", ctypes.c_double), ("sink_extraction", ctypes.c_double),
+                ("active_cells", ctypes.c_int64), ("sink_cells", ctypes.c_int64)]
+
+
 class Endpoints(ctypes.Structure):
     _fields_ = [(n, _vp) for n in ("cell", "x", "y", "z", "px", "py", "pz", "t", "status", "steps",
                                    "exit_face", "hash")]
@@ -113,6 +119,7 @@ SIGNATURES = {
     "mp_field_load": (ctypes.c_int, [_vp, _P(FieldDesc), _P(_vp)]),
     "mp_field_free": (ctypes.c_int, [_vp]),
     "mp_field_bytes": (ctypes.c_int, [_vp, _P(ctypes.c_size_t)]),
+    "mp_field_balance": (ctypes.c_int, [_vp, _P(Balance)]),
     "mp_release_group": (ctypes.c_int, [_vp, _vp, _P(ReleaseDesc), _vp, _P(_vp)]),
     "mp_group_free": (ctypes.c_int, [_vp]),
     "mp_group_size": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
@@ -254,6 +261,13 @@ def mp_field_bytes(fh) -> int:
     b = ctypes.c_size_t()
     _check(load_library().mp_field_bytes(fh, ctypes.byref(b)))
     return b.value
+
+
+def mp_field_balance(fh) -> dict:
+    """Volume balance of a loaded field (computed at load from its face flows)."""
+    b = Balance()
+    _check(load_library().mp_field_balance(fh, ctypes.byref(b)))
+    return {k: getattr(b, k) for k, _ in Balance._fields_}
 
 
 def mp_release_group(ctx, fh, *, n=None, lo=None, hi=None, seed=0, id_offset=0, cell=None, local=None,

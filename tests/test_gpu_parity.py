@@ -162,6 +162,45 @@ def test_fp64_exact_ties(ctx):
         mp.mp_field_free(fh)
 
 
+def _balance_np(qfaces, ibound):
+    """Per-cell inflow/outflow from face flows [ncell][6] (+axis direction),
+    face by face in the order x-, x+, y-, y+, z-, z+, and the report."""
+    inflow = np.zeros(qfaces.shape[0])
+    outflow = np.zeros(qfaces.shape[0])
+    for a in range(3):
+        q1, q2 = qfaces[:, 2 * a], qfaces[:, 2 * a + 1]
+        inflow = inflow + np.where(q1 > 0, q1, 0.0)
+        outflow = outflow + np.where(q1 > 0, 0.0, -q1)
+        inflow = inflow + np.where(q2 < 0, -q2, 0.0)
+        outflow = outflow + np.where(q2 < 0, 0.0, q2)
+    act, snk = ibound == 1, ibound == 2
+    r = np.abs(inflow - outflow)
+    ra = np.where(act, r, -1.0)
+    rel = np.where(act & (inflow > 0), r / np.where(inflow > 0, inflow, 1.0), 0.0)
+    ext = 0.0
+    for c in np.nonzero(snk)[0]:
+        ext += inflow[c] - outflow[c]
+    return {"max_abs_residual": ra.max(), "max_abs_cell": int(np.argmax(ra)), "max_rel_residual": rel.max(),
+            "sink_extraction": ext, "active_cells": int(act.sum()), "sink_cells": int(snk.sum())}
+
+
+def test_field_balance_report(ctx):
+    """The volume-balance report of a loaded field equals the same sums
+    made here from the face flows."""
+    f = I.random_box_field(3, 10, 14, seed=40, lnk_var=0.5, n_wells=5, well_scale=10.0, n_inactive=4)
+    fh = ctx.field(f)
+    nl, nr, nc = f.nlay, f.nrow, f.ncol
+    qx = np.asarray(f.qx).reshape(nl, nr, nc + 1)
+    qy = np.asarray(f.qy).reshape(nl, nr + 1, nc)
+    qz = np.asarray(f.qz).reshape(nl + 1, nr, nc)
+    q6 = np.stack([qx[:, :, :-1], qx[:, :, 1:], qy[:, :-1, :], qy[:, 1:, :], qz[:-1], qz[1:]], -1).reshape(-1, 6)
+    ref = _balance_np(q6, f.ibound.reshape(-1))
+    got = mp.mp_field_balance(fh)
+    assert got == ref
+    assert got["max_rel_residual"] <= 1e-9 and got["sink_cells"] == 5 and got["sink_extraction"] > 0
+    mp.mp_field_free(fh)
+
+
 def test_weak_sink_fraction_vs_oracle(ctx):
     """Weak sinks with a threshold: sink cells extracting at least the given
     fraction of their inflow stop particles, the others are passed (FP64

@@ -157,6 +157,24 @@ def test_quadtree_weak_sink_fraction_vs_oracle(ctx):
     mp.mp_field_free(fh)
 
 
+def test_quadtree_balance_report(ctx):
+    """The quadtree field's volume-balance report equals the sums made here
+    from the face totals (sub-faces summed in list order)."""
+    from tests.test_gpu_parity import _balance_np
+    u = U.quadtree_field(2, 8, 12, seed=15, n_wells=3, well_rate=0.05)
+    fh = ctx.field(u)
+    q6 = np.zeros((u.ncell, 6))
+    for c in range(u.ncell):
+        for fi in range(6):
+            sl = u.subfaces(c, fi)
+            acc = 0.0
+            for e in range(sl.start, sl.stop):
+                acc = float(u.q[e]) if e == sl.start else acc + float(u.q[e])
+            q6[c, fi] = acc
+    assert mp.mp_field_balance(fh) == _balance_np(q6, np.asarray(u.ibound))
+    mp.mp_field_free(fh)
+
+
 def test_usg_rejections(ctx):
     u = U.quadtree_field(2, 6, 8, seed=3, n_wells=1)
     fh = ctx.field(u)
