@@ -18,6 +18,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <cstddef>
+
 #include "mp_internal.h"
 #include "mp_sched.cuh"
 #include "mp_f64math.cuh"
@@ -271,6 +273,8 @@ struct UsgEngine {
         store_record(R.o.ts + (long long)Q.kk[slot] * R.p.n + Q.q[slot], x, y, z, c, Q.st[slot]);
     }
 
+    static_assert(offsetof(UsgSub, rect) % 16 == 0, "sub-face rectangles are read as 16-byte pairs");
+
     // L-infinity distance from (xa, xb) to a sub-face rectangle (0 inside)
     __device__ __forceinline__ static double rect_dist(const UsgSub& e, double xa, double xb)
     {
@@ -293,7 +297,11 @@ struct UsgEngine {
     // crossing, else the nearest one whose flow does, the point moved onto
     // it (mva / mvb: that coordinate changed); -1: no sub-face (outside).  A
     // face with one sub-face hands over to its neighbour either way, so
-    // neither the exit point nor a distance is formed there.
+    // neither the exit point nor a distance is formed there.  Whether a
+    // rectangle holds the point is decided on the integer keys of the
+    // coordinates (the ALU pipe): only a lane crossing a refined face runs
+    // this, so FP64 work here would hold the whole warp's FP64 pipe for a
+    // few lanes; distances are formed only when no rectangle holds it.
     __device__ __forceinline__ int across(int c, int ax, int side, double oa_, double pa_, double ob_, double pb_,
                                           double& xa, double& xb, bool& mva, bool& mvb) const
     {
@@ -304,12 +312,23 @@ struct UsgEngine {
         if (e1 - e0 == 1) return __ldg(&u.sub[e0].nbr);
         xa = oa_ + pa_;
         xb = ob_ + pb_;
-        long long best = e0;
-        double bd = CUDART_INF;
+        const long long ka = dkey(xa), kb = dkey(xb);
+        long long best = -1;
         for (long long e = e0; e < e1; ++e) {
-            const double d = rect_dist(u.sub[e], xa, xb);
-            if (d < bd) { bd = d; best = e; }
-            if (d == 0.0) break;
+            const double2* r = reinterpret_cast<const double2*>(u.sub[e].rect);
+            const double2 ra = __ldg(r), rb = __ldg(r + 1);
+            if (dkey(ra.x) <= ka && ka <= dkey(ra.y) && dkey(rb.x) <= kb && kb <= dkey(rb.y)) {
+                best = e;
+                break;
+            }
+        }
+        if (best < 0) {
+            best = e0;
+            double bd = CUDART_INF;
+            for (long long e = e0; e < e1; ++e) {
+                const double d = rect_dist(u.sub[e], xa, xb);
+                if (d < bd) { bd = d; best = e; }
+            }
         }
         if (with_flow(best, side)) return u.sub[best].nbr;
         long long alt = -1;
