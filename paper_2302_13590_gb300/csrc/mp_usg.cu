@@ -275,12 +275,15 @@ struct UsgEngine {
 
     static_assert(offsetof(UsgSub, rect) % 16 == 0, "sub-face rectangles are read as 16-byte pairs");
 
-    // L-infinity distance from (xa, xb) to a sub-face rectangle (0 inside)
+    // the larger of a and b (non-NaN), chosen on the integer keys
+    __device__ __forceinline__ static double kmax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+
+    // L-infinity distance from (xa, xb) to a sub-face rectangle (0 inside):
+    // four FP64 differences, the maxima taken on the ALU
     __device__ __forceinline__ static double rect_dist(const UsgSub& e, double xa, double xb)
     {
-        const double da = fmax(e.rect[0] - xa, xa - e.rect[1]);
-        const double db = fmax(e.rect[2] - xb, xb - e.rect[3]);
-        return fmax(fmax(da, db), 0.0);
+        const double m = kmax(kmax(e.rect[0] - xa, xa - e.rect[1]), kmax(e.rect[2] - xb, xb - e.rect[3]));
+        return lt0(m) ? 0.0 : m;
     }
 
     // the flow of sub-face e runs with a crossing to `side` (q * side > 0;
@@ -327,7 +330,7 @@ struct UsgEngine {
             double bd = CUDART_INF;
             for (long long e = e0; e < e1; ++e) {
                 const double d = rect_dist(u.sub[e], xa, xb);
-                if (d < bd) { bd = d; best = e; }
+                if (dkey(d) < dkey(bd)) { bd = d; best = e; }
             }
         }
         if (with_flow(best, side)) return u.sub[best].nbr;
@@ -336,7 +339,7 @@ struct UsgEngine {
         for (long long e = e0; e < e1; ++e) {
             if (!with_flow(e, side)) continue;
             const double d = rect_dist(u.sub[e], xa, xb);
-            if (d < ad) { ad = d; alt = e; }
+            if (dkey(d) < dkey(ad)) { ad = d; alt = e; }
         }
         if (alt < 0) return u.sub[best].nbr;
         const UsgSub& e = u.sub[alt];
@@ -412,7 +415,9 @@ struct UsgEngine {
                 if (a0 < 0 && cand) a0 = __ffs(cand) - 1;
                 tmin = CUDART_INF;
                 if (a0 >= 0) {
-                    const double te = f64_exit_time_d(A[a0], iA[a0], dd[a0], vp[a0], fc[a0]);
+                    const double te = f64_exit_time_d(sel3(a0, A[0], A[1], A[2]), sel3(a0, iA[0], iA[1], iA[2]),
+                                                      sel3(a0, dd[0], dd[1], dd[2]), sel3(a0, vp[0], vp[1], vp[2]),
+                                                      sel3(a0, fc[0], fc[1], fc[2]));
                     // the other candidates (every reachable axis when the
                     // leading time is unusable): smallest wins, ties to the
                     // lower axis
@@ -479,14 +484,19 @@ struct UsgEngine {
         // axis is put on its face
         const double dt = tmin;
         const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
-        const double n1v = f64_move(A[a1], iA[a1], D[a1], vp[a1], pp[a1], dt);
-        const double n2v = f64_move(A[a2], iA[a2], D[a2], vp[a2], pp[a2], dt);
-        pp[a1] = n1v;
-        pp[a2] = n2v;
-        pp[ax] = fc[ax] > 0 ? D[ax] : 0.0;
+        const double n1v = f64_move(sel3(a1, A[0], A[1], A[2]), sel3(a1, iA[0], iA[1], iA[2]),
+                                    sel3(a1, D[0], D[1], D[2]), sel3(a1, vp[0], vp[1], vp[2]),
+                                    sel3(a1, pp[0], pp[1], pp[2]), dt);
+        const double n2v = f64_move(sel3(a2, A[0], A[1], A[2]), sel3(a2, iA[0], iA[1], iA[2]),
+                                    sel3(a2, D[0], D[1], D[2]), sel3(a2, vp[0], vp[1], vp[2]),
+                                    sel3(a2, pp[0], pp[1], pp[2]), dt);
+        const int side = sel3(ax, fc[0], fc[1], fc[2]);
+        const double pf = side > 0 ? sel3(ax, D[0], D[1], D[2]) : 0.0;
+        pp[0] = ax == 0 ? pf : n1v;
+        pp[1] = ax == 1 ? pf : (ax == 0 ? n1v : n2v);
+        pp[2] = ax == 2 ? pf : n2v;
         s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
         s.t = t_end;
-        const int side = fc[ax];
         s.ef = 2 * ax + (side > 0 ? 1 : 0);
         // hand over at the exit point
         const int oa = ax == 0 ? 1 : 0, ob = ax == 2 ? 1 : 2;
@@ -512,19 +522,27 @@ struct UsgEngine {
         double on[3], Dn[3];
         #pragma unroll
         for (int a = 0; a < 3; ++a) { on[a] = __ldg(&n.o[a]); Dn[a] = __ldg(&n.D[a]); }
+        // the other two axes keep their global coordinate, p + (o - o'); a
+        // hand-over that moved the point enters at the moved point x, as
+        // x + (-o') (the rounding of x - o').  One form with operands chosen
+        // on the ALU, so every lane runs the same two additions per axis.
+        double pt[2];
         #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == ax) continue;
-            // the other axes keep their global coordinate; a hand-over that
-            // moved the point enters at the moved point
-            const bool mv = a == oa ? mva : mvb;
-            double pa = mv ? (a == oa ? xa : xb) - on[a] : pp[a] + (org[a] - on[a]);
+        for (int t = 0; t < 2; ++t) {
+            const int a = t == 0 ? oa : ob;
+            const bool mv = t == 0 ? mva : mvb;
+            const double on_a = sel3(a, on[0], on[1], on[2]);
+            const double dor = sel3(a, org[0], org[1], org[2]) - on_a;
+            const double X = mv ? (t == 0 ? xa : xb) : sel3(a, pp[0], pp[1], pp[2]);
+            double pa = X + (mv ? neg(on_a) : dor);
+            const double Da = sel3(a, Dn[0], Dn[1], Dn[2]);
             pa = lt0(pa) ? 0.0 : pa;
-            pa = gt_pos(pa, Dn[a]) ? Dn[a] : pa;
-            pp[a] = pa;
+            pt[t] = gt_pos(pa, Da) ? Da : pa;
         }
-        pp[ax] = side > 0 ? 0.0 : Dn[ax];
-        s.x0 = pp[0]; s.x1 = pp[1]; s.x2 = pp[2];
+        const double pe = side > 0 ? 0.0 : sel3(ax, Dn[0], Dn[1], Dn[2]);
+        s.x0 = ax == 0 ? pe : pt[0];
+        s.x1 = ax == 1 ? pe : (ax == 0 ? pt[0] : pt[1]);
+        s.x2 = ax == 2 ? pe : pt[1];
         s.c = nc;
         s.h = fnv_step(s.h, s.c);
     }
