@@ -225,14 +225,19 @@ typedef struct {
 
 /* Context on one CUDA device.  The device is made current on the calling
  * thread.  Errors: MP_ERR_INVALID_ARG, MP_ERR_CUDA. */
+/* Passage: none (infrastructure: a context binds the library to one GPU; the paper runs its
+ * particle loop on one desktop computer, Methods, "Synthetic test cases"). */
 int mp_ctx_create(int device, mp_ctx** out);
 /* Frees every field, group, request and graph still owned by the context
  * (waiting, bounded, for their work).  Errors: MP_ERR_INVALID_ARG (NULL). */
+/* Passage: none (infrastructure). */
 int mp_ctx_destroy(mp_ctx* ctx);
 
 /* Message for this thread's last failed call ("" if none); the string is
  * owned by the library and valid until the thread's next failing call.
  * Never fails. */
+/* Passage: none (infrastructure; thread-local and context-free, so it also reports failures of
+ * calls that had no context). */
 const char* mp_last_error(void);
 
 /* Copy (or read, MP_DEVICE_PTR) a flow field and build its device form:
@@ -241,7 +246,10 @@ const char* mp_last_error(void);
  * coordinates.  Validates shapes, finiteness and porosity.  Synchronous.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_NONFINITE, MP_ERR_OOM,
  * MP_ERR_CUDA. */
+/* Passage: Methods, "MODPATH" (the tracking reads the flow model's cell data) and
+ * "Multiprocessing" (flow-related arrays stored once, centrally, reached through a pointer). */
 int mp_field_load(mp_ctx* ctx, const mp_field_desc* d, mp_field** out);
+/* Passage: none (infrastructure). */
 int mp_field_free(mp_field* f);
 
 /* Volume balance of a loaded field (rectilinear or quadtree), computed once
@@ -260,6 +268,8 @@ typedef struct {
 } mp_balance;
 
 /* Errors: MP_ERR_INVALID_ARG (NULL). */
+/* Passage: none (a check of the input: the tracking assumes the converged, volume-conserving flow
+ * solution of Methods, "Synthetic test cases"). */
 int mp_field_balance(const mp_field* f, mp_balance* out);
 
 /* A rectangular unstructured (quadtree) grid: the paper's TC2 also runs on
@@ -291,17 +301,24 @@ typedef struct {
     uint32_t flags;           /* 0 */
 } mp_usg_desc;
 
+/* Passage: Methods, "MODPATH" (structured and rectangular unstructured grids) and Results, "Grid
+ * complexity" (TC2 on a quadtree refinement). */
 int mp_usg_field_load(mp_ctx* ctx, const mp_usg_desc* d, mp_field** out);
 /* Device bytes held by a loaded field.  Errors: MP_ERR_INVALID_ARG (NULL). */
+/* Passage: none (infrastructure). */
 int mp_field_bytes(const mp_field* f, size_t* bytes);
 
 /* Create a particle group on the field (state resident on the device).
  * Runs on `stream` (a cudaStream_t, NULL = legacy default) and returns when
  * the release is enqueued; the state is ready in stream order.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+/* Passage: Methods, "Synthetic test cases" (particles injected uniformly at x_o in TC1; TC2
+ * injects groups in stages) and Introduction (several particle groups). */
 int mp_release_group(mp_ctx* ctx, const mp_field* f, const mp_release_desc* r, void* stream,
                      mp_group** out);
+/* Passage: none (infrastructure). */
 int mp_group_free(mp_group* g);
+/* Passage: none (infrastructure). */
 int mp_group_size(const mp_group* g, int64_t* n);
 
 /* Track a group (Methods, "MODPATH": the particle loop) asynchronously on
@@ -314,6 +331,9 @@ int mp_group_size(const mp_group* g, int64_t* n);
  * unless MP_TRACK_PASS_WEAK_SINKS lets that sink pass.
  * Errors: MP_ERR_INVALID_ARG (also: weak_sink_fraction outside [0, 1]),
  * MP_ERR_OOM, MP_ERR_CUDA. */
+/* Passage: Introduction and Methods, "MODPATH" (the particle loop: one displacement per cell,
+ * hand-over to the neighbour, the stopping conditions; endpoint, timeseries and pathline
+ * simulations). */
 int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_req* out);
 
 /* Rebind a group to another field on the same grid (same dims, cell sizes
@@ -321,6 +341,7 @@ int mp_track(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, void* stream, mp_
  * of a piecewise-steady model.  Requests already enqueued keep the field
  * they were launched with.  Not concurrent with mp_track on the same group.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE (another grid). */
+/* Passage: Methods, "MODPATH" (the time step loop updates the flow arrays at ts_max). */
 int mp_group_set_field(mp_group* g, const mp_field* f);
 
 /* Piecewise-steady (transient) flow (Methods, "MODPATH": the outermost loop
@@ -339,6 +360,7 @@ int mp_group_set_field(mp_group* g, const mp_field* f);
  * only with MP_TRACK_UPDATE_GROUP, which also rebinds it to the last field.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_NONFINITE, MP_ERR_OOM,
  * MP_ERR_CUDA. */
+/* Passage: Methods, "MODPATH" (the time step loop over the flow model's stress periods). */
 int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* const* fields, const double* t_end,
                      const mp_track_opts* o, void* stream, mp_req* out);
 
@@ -351,6 +373,8 @@ int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* co
  * come from the first request of that precision.  out[n] receives request
  * ids that behave as mp_track's (own outputs and counters; kernel_ms is the
  * shared launch's time).  Errors: as mp_track; on error no request exists. */
+/* Passage: Methods, "Multiprocessing" (dynamic scheduling of one particle loop) and Results,
+ * "Thread scheduling". */
 int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_opts* opts, void* stream,
                    mp_req* out);
 
@@ -371,12 +395,14 @@ typedef struct {
  * it.  Synchronous (bounded waits).  The paper's scheduling study (Results,
  * "Thread scheduling") is this choice made by measurement.
  * Errors: as mp_track, MP_ERR_TIMEOUT. */
+/* Passage: Results, "Thread scheduling" (the schedule chosen by measurement). */
 int mp_autotune(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, int64_t sample, void* stream, mp_tuning* out);
 
 /* Install a launch configuration (e.g. one cached from an earlier run) for
  * (field, precision, timeseries).  Errors: MP_ERR_INVALID_ARG (NULL, a
  * schedule other than static or dynamic, block outside [32, 256], or a
  * negative steps per fetch). */
+/* Passage: Results, "Thread scheduling" (a measured launch choice kept across runs). */
 int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t timeseries, const mp_tuning* t);
 
 /* Captured batches (the batching pattern's CUDA graphs; the paper's many
@@ -390,35 +416,44 @@ int mp_set_tuning(mp_ctx* ctx, const mp_field* f, int32_t precision, int32_t tim
  * configuration is fixed at capture (MP_SCHED_AUTO takes the tuned one).
  * Results are the same as mp_release_group + mp_track_batch with the same
  * descriptors.  Errors: MP_ERR_INVALID_ARG, MP_ERR_OOM, MP_ERR_CUDA. */
+/* Passage: Introduction and Conclusions (simultaneous displacement of several particle groups).
+ * */
 int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release_desc* rel,
                     const mp_track_opts* opts, void* stream, mp_graph** out);
 /* Replace request i's box, seed and id offset for later launches (the
  * particle count is fixed: MP_ERR_SHAPE otherwise).  Ordered after earlier
  * work on `stream`; returns once the descriptor is on the device.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_SHAPE, MP_ERR_CUDA. */
+/* Passage: Introduction and Conclusions (several particle groups). */
 int mp_graph_set_release(mp_graph* g, int i, const mp_release_desc* rel, void* stream);
 /* Replay the graph on `stream` (asynchronous).  Outputs of the previous
  * launch are overwritten: read them first (stream order).
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_CUDA. */
+/* Passage: Introduction and Conclusions (several particle groups). */
 int mp_graph_launch(mp_graph* g, void* stream);
 /* The request ids (n_reqs of them) through which a launch's outputs are
  * read with mp_wait, mp_get_endpoints, mp_get_timeseries, mp_get_pathlines
  * and mp_get_stats (kernel_ms then spans the whole graph).  They belong to
  * the graph: mp_req_free refuses them, mp_graph_free releases them.
  * ids has room for n_reqs entries.  Errors: MP_ERR_INVALID_ARG (NULL). */
+/* Passage: none (infrastructure). */
 int mp_graph_requests(const mp_graph* g, mp_req* ids);
 /* Waits (bounded) for the last launch, then frees everything the graph
  * holds.  The field must outlive the graph.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_TIMEOUT (then nothing is freed). */
+/* Passage: none (infrastructure). */
 int mp_graph_free(mp_graph* g);
 
 /* Wait up to timeout_us microseconds (< 0: no limit is not offered; the
  * wait is always bounded, and a negative value means 60 s) for a request.
  * Errors: MP_ERR_TIMEOUT (still running), MP_ERR_NOT_READY (unknown id),
  * MP_ERR_DEVICE (kernel error flag), MP_ERR_CUDA. */
+/* Passage: none (infrastructure: the paper's loop runs synchronously; here a request is awaited
+ * with a bound). */
 int mp_wait(mp_ctx* ctx, mp_req r, int64_t timeout_us);
 
 /* 1 if the request's work has finished, 0 if not; negative on error. */
+/* Passage: none (infrastructure). */
 int mp_query(mp_ctx* ctx, mp_req r);
 
 /* Copy endpoint arrays out.  flags & MP_DEVICE_PTR: destinations are device
@@ -426,10 +461,15 @@ int mp_query(mp_ctx* ctx, mp_req r);
  * returns at once; otherwise destinations are host memory and the call
  * waits (bounded, 60 s) for the request and the copies.
  * Errors: MP_ERR_NOT_READY, MP_ERR_TIMEOUT, MP_ERR_CUDA. */
+/* Passage: Methods, "MODPATH" (endpoint simulations) and "Synthetic test cases" (endpoint output
+ * written after the outermost loop). */
 int mp_get_endpoints(mp_ctx* ctx, mp_req r, const mp_endpoints* out, uint32_t flags, void* stream);
 
 /* Copy the [n_times][n] timeseries records out (same rules as endpoints).
  * Errors: MP_ERR_INVALID_ARG (request has no timeseries), as above. */
+/* Passage: Methods, "MODPATH" (timeseries simulations: particle positions at user-defined times)
+ * and "Multiprocessing" (records written from inside the particle loop to thread-exclusive units).
+ * */
 int mp_get_timeseries(mp_ctx* ctx, mp_req r, mp_ts_record* out, uint32_t flags, void* stream);
 
 /* Copy a pathline request's points (MP_MODE_PATHLINE) to host memory, or
@@ -439,6 +479,8 @@ int mp_get_timeseries(mp_ctx* ctx, mp_req r, mp_ts_record* out, uint32_t flags, 
  * (mp_stats.path_points) but not kept.  Waits (bounded) for the request.
  * Errors: MP_ERR_INVALID_ARG (no pathlines), MP_ERR_NOT_READY (unknown id),
  * MP_ERR_TIMEOUT, MP_ERR_DEVICE, MP_ERR_CUDA. */
+/* Passage: Methods, "MODPATH" (pathline simulations) and "Multiprocessing" (records written from
+ * inside the particle loop). */
 int mp_get_pathlines(mp_ctx* ctx, mp_req id, mp_path_record* out, int64_t max_points, int64_t* n_points,
                      uint32_t flags, void* stream);
 
@@ -446,25 +488,31 @@ int mp_get_pathlines(mp_ctx* ctx, mp_req id, mp_path_record* out, int64_t max_po
  * mp_req_free); any out-pointer may be NULL.  The pointers are the
  * library's: read them in stream order after the request.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (unknown id). */
+/* Passage: none (infrastructure). */
 int mp_endpoints_device(mp_ctx* ctx, mp_req r, mp_endpoints* out, mp_ts_record** ts);
 
 /* Counters of a finished request (waits, bounded, like mp_get_endpoints).
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_NOT_READY (unknown id),
  * MP_ERR_TIMEOUT, MP_ERR_CUDA. */
+/* Passage: Methods, "Multiprocessing" (counters summed over the parallel loop by a reduction); the
+ * cell-step count is this library's work measure. */
 int mp_get_stats(mp_ctx* ctx, mp_req r, mp_stats* out);
 
 /* Release a request's outputs (stream-ordered after its work); the id is
  * unknown afterwards.  Errors: MP_ERR_INVALID_ARG (NULL, or a request
  * owned by a graph), MP_ERR_NOT_READY (unknown id). */
+/* Passage: none (infrastructure). */
 int mp_req_free(mp_ctx* ctx, mp_req r);
 
 /* Device bytes mp_track allocates for n particles under options o (the
  * serving layer's admission uses it).  Errors: MP_ERR_INVALID_ARG. */
+/* Passage: none (infrastructure for admitting particle groups, Conclusions). */
 int mp_query_bytes(const mp_track_opts* o, int64_t n, size_t* bytes);
 
 /* Number of CUDA kernel launches mp_track issues for these options (one
  * tracking launch per request; mp_track_periods: one per period).
  * Errors: MP_ERR_INVALID_ARG (NULL). */
+/* Passage: none (infrastructure). */
 int mp_track_launches(const mp_track_opts* o, int32_t* launches);
 
 /* ---- host to host, transfers overlapped with tracking ----------------------
@@ -495,34 +543,43 @@ int mp_track_launches(const mp_track_opts* o, int32_t* launches);
  * MP_MODE_PATHLINE is rejected.
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_NONFINITE, MP_ERR_OOM, MP_ERR_TIMEOUT,
  * MP_ERR_DEVICE, MP_ERR_CUDA. */
+/* Passage: Introduction and Methods, "MODPATH" (independent particles, so they can be tracked in
+ * chunks). */
 int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell, const double* local,
                   const double* t0, const mp_track_opts* o, int32_t n_chunks, const mp_endpoints* ep,
                   mp_ts_record* ts, mp_stats* stats);
 
 /* ---- tracking without device allocation ----------------------------------
- * The paper has no counterpart of this call; it exists for callers that
+ * The paper has no counterpart of this call.  It exists for callers that
  * cannot allocate device memory where they track: code that runs inside a
- * caller-owned memory budget or arena, inside a CUDA stream capture (where
- * cudaMalloc is not allowed), or on a path that must not synchronise the
- * device.  The caller passes every buffer: the particle state (device arrays
- * in the layout of a group: cell int32, px/py/pz offsets in m from the cell's
- * low faces and t as FP64, status u8), the endpoint arrays (device, all
- * required) and, in timeseries mode, the [n_times][n] record buffer (device).
- * times stays a host array.  The call allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine.  Its only other device memory is a
- * fixed file-scope array of 8 + 11 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words
- * plus the launch's request descriptor (queue head, counters, the output
- * times in FP64 and as FP32 pairs; about 66 KB) that every
- * GPU that loads the library holds until the process exits.
- *   - The first call on each device takes the array's device address; make
- *     that first call before any stream capture.
+ * memory budget it does not control (an embedding application that hands
+ * out one fixed arena and forbids further cudaMalloc), or code that must not
+ * let a library grow the device's memory pool behind its back.  The caller
+ * passes every buffer: the particle state (device arrays in the layout of a
+ * group: cell int32, px/py/pz offsets in m from the cell's low faces and t
+ * as FP64, status u8), the endpoint arrays (device, all required) and, in
+ * timeseries mode, the [n_times][n] record buffer (device).  times stays a
+ * host array.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  Its only other device memory is a fixed
+ * file-scope array of 8 + 11 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words plus
+ * the launch's request descriptor (queue head, counters, the output times in
+ * FP64 and as FP32 pairs; about 66 KB) that every GPU that loads the library
+ * holds until the process exits.
+ *   - The call runs on the device of f's context and restores the caller's
+ *     current device before it returns.
+ *   - The first call on each device takes the array's device address
+ *     (cudaGetSymbolAddress) and keeps it.
+ *   - The output times and the request descriptor reach the device through
+ *     cudaMemcpyAsync from pageable host memory, which may block the calling
+ *     thread until `stream` reaches the copy.  A stream that is capturing is
+ *     refused (MP_ERR_INVALID_ARG).
  *   - Every call shares the array, which keeps the last call's contents; the
  *     call clears the queue head and counters itself.  Calls that overlap on
  *     the GPU (different streams, or a second call before the first has run)
  *     race on it: run them one after another on one stream.
  *   - n_times > MP_NOALLOC_MAX_TIMES is rejected with MP_ERR_INVALID_ARG.
- *   - stats == NULL: the call only enqueues work on `stream`.  Otherwise it
- *     waits for the stream and fills *stats (kernel_ms is 0).
+ *   - stats == NULL: the call returns once the work is enqueued on `stream`.
+ *     Otherwise it waits for the stream and fills *stats (kernel_ms is 0).
  * Errors: MP_ERR_INVALID_ARG, MP_ERR_NONFINITE, MP_ERR_CUDA, MP_ERR_DEVICE. */
 #define MP_NOALLOC_MAX_TIMES 4096
 
@@ -536,6 +593,7 @@ typedef struct {
     mp_track_opts opts;
 } mp_noalloc_args;
 
+/* Passage: none: the paper has no counterpart (see the block above). */
 int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats);
 
 #ifdef __cplusplus

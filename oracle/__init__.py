@@ -7,7 +7,14 @@ nothing from the product.
 
 The arithmetic lives in ``mp_oracle.c`` (plain single-threaded IEEE double,
 compiled with ``-O2 -ffp-contract=off``); this file only compiles it and
-marshals numpy arrays.  A field is any object with the attributes
+marshals numpy arrays.
+
+Two arithmetic modes (``arith``): ``"plain"``, the reference, evaluates the
+in-cell solution as its formulas read (the C library's log1p and expm1,
+IEEE division, no fused multiply-add); ``"mirror"`` evaluates the same
+solution by fixed table-driven steps with fused multiply-adds, so that an
+implementation of the same steps can be checked bit for bit.  Both modes
+are held to the same pins.  A field is any object with the attributes
 ``nlay, nrow, ncol, delr, delc, dz, origin, qx, qy, qz, porosity, ibound``.
 
 Pins: every function here is checked against closed forms, brute-force RK4
@@ -59,7 +66,21 @@ class _Field(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
                 ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32),
-                ("path_start", ctypes.c_int32), ("weak_sink_fraction", ctypes.c_double)]
+                ("path_start", ctypes.c_int32), ("weak_sink_fraction", ctypes.c_double),
+                ("arith", ctypes.c_int32)]
+
+
+ARITH = {"plain": 0, "mirror": 1}
+# the mode used where a call names none; "plain" is the reference
+DEFAULT_ARITH = "plain"
+
+
+def _arith(arith) -> int:
+    if arith is None:
+        arith = DEFAULT_ARITH
+    if arith not in ARITH:
+        raise ValueError(f"arith must be one of {sorted(ARITH)}, got {arith!r}")
+    return ARITH[arith]
 
 
 # one pathline point (orc_path_rec)
@@ -67,11 +88,17 @@ PATH_RECORD = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("t", "<f8"), 
                         ("cell", "<i4"), ("seq", "<u4"), ("status", "u1"), ("pad", "u1", (3,))])
 
 
+# one traced cell-step (orc_trace_rec)
+TRACE_RECORD = np.dtype([("te", "<f8", (3,)), ("vp", "<f8", (3,)), ("vf", "<f8", (3,)), ("t", "<f8"), ("particle", "<i4"),
+                         ("cell", "<i4"), ("face", "i1", (3,)), ("ax", "i1"), ("pad", "u1", (4,))])
+
+
 class _Out(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("cell", "px", "py", "pz", "gx", "gy", "gz", "t", "status", "steps", "exit_face", "hash",
                  "ts_x", "ts_y", "ts_z", "ts_cell", "ts_status", "path")] + \
-        [("path_cap", ctypes.c_int64), ("path_n", ctypes.c_void_p)]
+        [("path_cap", ctypes.c_int64), ("path_n", ctypes.c_void_p),
+         ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64), ("trace_n", ctypes.c_void_p)]
 
 
 def _load():
@@ -90,6 +117,10 @@ def _load():
             lib.orc_expm1.restype = ctypes.c_double
             lib.orc_move.argtypes = [ctypes.c_double] * 6
             lib.orc_move.restype = ctypes.c_double
+            lib.orc_exit_time_plain.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_int)]
+            lib.orc_exit_time_plain.restype = ctypes.c_double
+            lib.orc_move_plain.argtypes = [ctypes.c_double] * 5
+            lib.orc_move_plain.restype = ctypes.c_double
             lib.orc_release_box.argtypes = [ctypes.POINTER(_Field), ctypes.c_int64, vp, vp,
                                             ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp, vp]
             lib.orc_release_box.restype = ctypes.c_int
@@ -170,24 +201,32 @@ def philox4x32_10(ctr, key):
     return o
 
 
-def exit_time(v1, v2, A, D, p):
+def exit_time(v1, v2, A, D, p, arith=None):
     """(t_exit, face) for one axis of one cell (face +1, -1 or 0 = none)."""
     lib = _load()
     face = ctypes.c_int(0)
-    t = lib.orc_exit_time(float(v1), float(v2), float(A), _inv(A), float(D), float(p), ctypes.byref(face))
+    if _arith(arith) == ARITH["mirror"]:
+        t = lib.orc_exit_time(float(v1), float(v2), float(A), _inv(A), float(D), float(p), ctypes.byref(face))
+    else:
+        t = lib.orc_exit_time_plain(float(v1), float(v2), float(A), float(D), float(p), ctypes.byref(face))
     return t, face.value
 
 
 def log1p(x):
+    """The mirror mode's table-driven log1p (the plain mode calls the C library's)."""
     return _load().orc_log1p(float(x))
 
 
 def expm1(w):
+    """The mirror mode's table-driven expm1 (the plain mode calls the C library's)."""
     return _load().orc_expm1(float(w))
 
 
-def move(v1, A, D, p, dt):
-    return _load().orc_move(float(v1), float(A), _inv(A), float(D), float(p), float(dt))
+def move(v1, A, D, p, dt, arith=None):
+    lib = _load()
+    if _arith(arith) == ARITH["mirror"]:
+        return lib.orc_move(float(v1), float(A), _inv(A), float(D), float(p), float(dt))
+    return lib.orc_move_plain(float(v1), float(A), float(D), float(p), float(dt))
 
 
 def _inv(A):
@@ -233,7 +272,7 @@ def subset(state, idx):
 
 
 def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False,
-          pathline=False, path_start=True, weak_sink_fraction=0.0):
+          pathline=False, path_start=True, weak_sink_fraction=0.0, arith=None, trace=False):
     """Track every particle of ``state`` (dict of cell, px, py, pz, t, status,
     and optionally steps, hash and exit_face carried by a resumed particle).
 
@@ -242,7 +281,10 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
     arrays ts_x/ts_y/ts_z/ts_cell/ts_status of shape [n_times, n].  With
     ``pathline``, ``path`` holds the pathline points (PATH_RECORD) in the
     order produced: per particle its start point (if ``path_start``) and the
-    point every cell-step ends at.
+    point every cell-step ends at.  ``arith`` selects the arithmetic mode
+    ("plain", the reference, or "mirror"; None: ``DEFAULT_ARITH``).  With ``trace``, ``trace`` holds
+    one TRACE_RECORD per cell-step (exit times, faces and particle velocity
+    per axis, the axis taken).
     """
     lib = _load()
     of = as_oracle_field(f)
@@ -270,23 +312,30 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
         res["ts_cell"] = np.zeros((nt, n), np.int32)
         res["ts_status"] = np.zeros((nt, n), np.uint8)
     opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)), int(bool(path_start)),
-                 float(weak_sink_fraction))
+                 float(weak_sink_fraction), _arith(arith))
     cap = 64 * n + 16
+    tcap = 64 * n + 16
     while True:
         path = np.zeros(cap if pathline else 0, PATH_RECORD)
         path_n = np.zeros(1, np.int64)
+        trc = np.zeros(tcap if trace else 0, TRACE_RECORD)
+        trace_n = np.zeros(1, np.int64)
         out = _Out(*[_ptr(res.get(k)) for k, _ in _Out._fields_[:17]], _ptr(path) if pathline else None, cap,
-                   _ptr(path_n))
+                   _ptr(path_n), _ptr(trc) if trace else None, tcap, _ptr(trace_n))
         fn = lib.orc_usg_track if isinstance(of, OracleUsgField) else lib.orc_track
         rc = fn(ctypes.byref(of.c), n, _ptr(cell0), _ptr(px0), _ptr(py0), _ptr(pz0), _ptr(t0),
                 _ptr(s0), _ptr(k0), _ptr(h0), _ptr(e0), ctypes.byref(opts), ctypes.byref(out))
         if rc != 0:
             raise RuntimeError("orc_track failed")
-        if not pathline or path_n[0] <= cap:
+        if (not pathline or path_n[0] <= cap) and (not trace or trace_n[0] <= tcap):
             break
-        cap = int(path_n[0])   # the run is deterministic: repeat with room for every point
+        # the run is deterministic: repeat with room for every point
+        cap = max(cap, int(path_n[0]))
+        tcap = max(tcap, int(trace_n[0]))
     if pathline:
         res["path"] = path[:int(path_n[0])]
+    if trace:
+        res["trace"] = trc[:int(trace_n[0])]
     return res
 
 
@@ -303,7 +352,7 @@ def resume_state(out):
 
 
 def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False,
-                  pathline=False, weak_sink_fraction=0.0):
+                  pathline=False, weak_sink_fraction=0.0, arith=None):
     """Piecewise-steady flow (Methods, "MODPATH": the outer loop runs over the
     flow model's time steps and updates the flow arrays at each step's end).
 
@@ -339,7 +388,7 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
         wt = None if window is None or window.size == 0 else tarr[window]
         moved = (cur["status"] == ST_ACTIVE) | (p == 0)
         out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks,
-                    pathline=pathline, path_start=p == 0, weak_sink_fraction=weak_sink_fraction)
+                    pathline=pathline, path_start=p == 0, weak_sink_fraction=weak_sink_fraction, arith=arith)
         if pathline:
             paths.append(out.pop("path"))
         if res is None:

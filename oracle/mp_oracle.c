@@ -3,9 +3,9 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
  * benchmark's CPU-baseline leg may load this file's library.  It shares no
- * code with the CUDA path and is deliberately plain: one particle at a time,
- * one cell at a time, IEEE double precision, no FMA contraction
- * (-ffp-contract=off), no vectorisation.
+ * code with the CUDA path: one particle at a time, one cell at a time, IEEE
+ * double precision, no FMA contraction by the compiler (-ffp-contract=off),
+ * no vectorisation.
  *
  * What it computes.  The paper (Introduction; Methods, "MODPATH") moves each
  * particle independently with the semi-analytical solution of Pollock (1988):
@@ -16,16 +16,33 @@
  *
  *   face velocities   v1 = Q1 / (n * area_a),  v2 = Q2 / (n * area_a)
  *   gradient          A  = (v2 - v1) / D_a            (D_a = cell size)
- *   velocity at p     vp = v1 + A * p  (one fma)      (p = offset from face 1)
- *   motion            p(t) = p + vp (e^{A t} - 1) / A     (Pollock's form;
- *                     p + vp t (one fma) when A t == 0; the product by
- *                     1/A and the sum in one fma)
- *   exit time         t_a = ln(v_exit / vp) / A = ln(1 + z) / A,
- *                     d = signed distance to the exit face, z = A d / vp
- *                     (computed as A * (d / vp)), and t_a = d / vp in the
- *                     limit A -> 0 (z == 0).
- *   1 / A is computed once per cell (0 when A == 0) and multiplies, so a
- *   step divides only for d / vp and inside log1p.
+ *   velocity at p     vp = v1 + A * p                 (p = offset from face 1)
+ *   exit time         t_a = ln(v_exit / vp) / A, with d the signed distance
+ *                     to the exit face and z = A d / vp (v_exit / vp = 1 + z)
+ *   motion            p(t) = p + vp (e^{A t} - 1) / A
+ *   and the limits A -> 0: t_a = d / vp, p(t) = p + vp t.
+ *
+ * Two arithmetic modes evaluate these (opts->arith):
+ *
+ *   PLAIN, the reference: the formulas as they read, with the A -> 0 limit
+ *   built in through the well-conditioned factors log1p(z)/z and
+ *   expm1(w)/w:  vp = v1 + A p;  t_a = (d / vp) (log1p(z) / z), z = A (d / vp)
+ *   (t_a = d / vp when z == 0);  p(t) = p + (vp t) (expm1(w) / w), w = A t
+ *   (p + vp t when w == 0).  log1p and expm1 are the C library's; every
+ *   division is IEEE; no fused multiply-add.
+ *
+ *   MIRROR: the same solution evaluated in Pollock's own forms,
+ *   t_a = ln(1 + z) / A and p + vp (e^{A t} - 1) / A, with 1/A formed once
+ *   per cell and multiplied, v1 + A p and the motion's last product and sum
+ *   as single fused multiply-adds (C99 fma), and log1p / expm1 evaluated by
+ *   fixed table-driven steps (Tang's method: P. T. P. Tang, "Table-driven
+ *   implementation of the exponential function in IEEE floating-point
+ *   arithmetic", ACM TOMS 15(2), 1989, and "Table-driven implementation of
+ *   the logarithm function ...", ACM TOMS 16(4), 1990).  Any other
+ *   implementation of these exact steps produces the same bits, which makes
+ *   this mode a bit-for-bit check of such an implementation.  Its results
+ *   differ from PLAIN's by rounding only (a few ulp per step); the tests
+ *   hold both modes to the same pins.
  *
  * A face is reachable on an axis only if the particle velocity and the
  * exit-face velocity point the same way (vp > 0 and v2 > 0 -> face 2;
@@ -289,6 +306,33 @@ double orc_move(double v1, double A, double iA, double D, double p, double dt)
     return pn;
 }
 
+/* ---- the plain reading (PLAIN mode) -------------------------------- */
+
+double orc_exit_time_plain(double v1, double v2, double A, double D, double p, int* face)
+{
+    double vp = v1 + A * p;
+    double d;
+    if (vp > 0.0 && v2 > 0.0) { *face = 1; d = D - p; }
+    else if (vp < 0.0 && v1 < 0.0) { *face = -1; d = -p; }
+    else { *face = 0; return INFINITY; }
+    double t1 = d / vp;
+    double z = A * t1;
+    if (z == 0.0) return t1;
+    return t1 * (log1p(z) / z);
+}
+
+double orc_move_plain(double v1, double A, double D, double p, double dt)
+{
+    double vp = v1 + A * p;
+    double s = vp * dt;
+    if (s == 0.0) return p;
+    double w = A * dt;
+    double pn = (w == 0.0) ? p + s : p + s * (expm1(w) / w);
+    if (pn < 0.0) pn = 0.0;
+    if (pn > D) pn = D;
+    return pn;
+}
+
 /* ---- cell data gathered at cell entry (the per-cell "initialisation") -- */
 
 typedef struct {
@@ -317,6 +361,21 @@ static void cell_velocities(const orc_field* f, int k, int i, int j, cellvel* cv
         cv->A[a] = (cv->v2[a] - cv->v1[a]) / cv->D[a];
         cv->iA[a] = (cv->A[a] != 0.0) ? 1.0 / cv->A[a] : 0.0;
     }
+}
+
+/* the exit time and the motion of axis a in the mode opt->arith selects */
+static double ex_time(const orc_track_opts* opt, const cellvel* cv, int a, double p, int* face)
+{
+    if (opt->arith == ORC_ARITH_MIRROR)
+        return orc_exit_time(cv->v1[a], cv->v2[a], cv->A[a], cv->iA[a], cv->D[a], p, face);
+    return orc_exit_time_plain(cv->v1[a], cv->v2[a], cv->A[a], cv->D[a], p, face);
+}
+
+static double mv(const orc_track_opts* opt, const cellvel* cv, int a, double p, double dt)
+{
+    if (opt->arith == ORC_ARITH_MIRROR)
+        return orc_move(cv->v1[a], cv->A[a], cv->iA[a], cv->D[a], p, dt);
+    return orc_move_plain(cv->v1[a], cv->A[a], cv->D[a], p, dt);
 }
 
 /* ---- release ----------------------------------------------------------- */
@@ -411,6 +470,26 @@ static void path_point(const orc_track_out* o, int64_t q, double x, double y, do
     e->x = x; e->y = y; e->z = z; e->t = t;
     e->particle = (int32_t)q; e->cell = cell; e->seq = (uint32_t)seq; e->status = st;
     e->pad[0] = e->pad[1] = e->pad[2] = 0;
+}
+
+static void trace_step(const orc_track_out* o, int64_t q, int32_t cell, double t, const cellvel* cv,
+                       const orc_track_opts* opt, const double p[3], const double te[3], const int face[3],
+                       int ax)
+{
+    int64_t r = (*o->trace_n)++;
+    if (r >= o->trace_cap) return;
+    orc_trace_rec* e = &o->trace[r];
+    memset(e, 0, sizeof *e);
+    for (int a = 0; a < 3; a++) {
+        e->te[a] = te[a];
+        e->vp[a] = (opt->arith == ORC_ARITH_MIRROR) ? fma(cv->A[a], p[a], cv->v1[a]) : cv->v1[a] + cv->A[a] * p[a];
+        e->vf[a] = fmax(fabs(cv->v1[a]), fabs(cv->v2[a]));
+        e->face[a] = (int8_t)face[a];
+    }
+    e->t = t;
+    e->particle = (int32_t)q;
+    e->cell = cell;
+    e->ax = (int8_t)ax;
 }
 
 /* ---- grids ---------------------------------------------------------------
@@ -633,13 +712,15 @@ static int track_core(const orc_grid* g, int64_t n,
             int face[3];
             double te[3];
             for (int a = 0; a < 3; a++)
-                te[a] = orc_exit_time(cv.v1[a], cv.v2[a], cv.A[a], cv.iA[a], cv.D[a], p[a], &face[a]);
+                te[a] = ex_time(opt, &cv, a, p[a], &face[a]);
             int ax = -1;
             double tmin = INFINITY;
             for (int a = 0; a < 3; a++)
                 if (face[a] != 0 && te[a] < tmin) { tmin = te[a]; ax = a; }
             steps++;
             took = 1;
+            if (out->trace) trace_step(out, q, c, t, &cv, opt, p, te, face,
+                                       (ax >= 0 && t + tmin < t_stop) ? ax : -1);
             if (ax < 0 && g->ibound[c] == 2) {
                 /* inside a sink cell with no reachable face: captured */
                 st = ORC_ST_SINK;
@@ -650,9 +731,9 @@ static int track_core(const orc_grid* g, int64_t n,
                  * this cell; later output times still see it move inside */
                 while (kn < nt) {
                     double tau = opt->times[kn] - t;
-                    double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                    double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                    double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                    double g0 = o[0] + mv(opt, &cv, 0, p[0], tau);
+                    double g1 = o[1] + mv(opt, &cv, 1, p[1], tau);
+                    double g2 = o[2] + mv(opt, &cv, 2, p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_NO_EXIT);
                     kn++;
                 }
@@ -663,13 +744,13 @@ static int track_core(const orc_grid* g, int64_t n,
                 double dt = t_stop - t;
                 while (kn < nt && opt->times[kn] <= t_stop) {
                     double tau = opt->times[kn] - t;
-                    double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                    double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                    double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                    double g0 = o[0] + mv(opt, &cv, 0, p[0], tau);
+                    double g1 = o[1] + mv(opt, &cv, 1, p[1], tau);
+                    double g2 = o[2] + mv(opt, &cv, 2, p[2], tau);
                     write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                     kn++;
                 }
-                for (int a = 0; a < 3; a++) p[a] = orc_move(cv.v1[a], cv.A[a], cv.iA[a], cv.D[a], p[a], dt);
+                for (int a = 0; a < 3; a++) p[a] = mv(opt, &cv, a, p[a], dt);
                 t = t_stop;
                 st = ORC_ST_TIME;
                 break;
@@ -679,15 +760,15 @@ static int track_core(const orc_grid* g, int64_t n,
             double t_end = t + dt;
             while (kn < nt && opt->times[kn] <= t_end) {
                 double tau = opt->times[kn] - t;
-                double g0 = o[0] + orc_move(cv.v1[0], cv.A[0], cv.iA[0], cv.D[0], p[0], tau);
-                double g1 = o[1] + orc_move(cv.v1[1], cv.A[1], cv.iA[1], cv.D[1], p[1], tau);
-                double g2 = o[2] + orc_move(cv.v1[2], cv.A[2], cv.iA[2], cv.D[2], p[2], tau);
+                double g0 = o[0] + mv(opt, &cv, 0, p[0], tau);
+                double g1 = o[1] + mv(opt, &cv, 1, p[1], tau);
+                double g2 = o[2] + mv(opt, &cv, 2, p[2], tau);
                 write_record(out, n, kn, q, g0, g1, g2, c, ORC_ST_ACTIVE);
                 kn++;
             }
             for (int a = 0; a < 3; a++) {
                 if (a == ax) p[a] = (face[a] > 0) ? cv.D[a] : 0.0;
-                else p[a] = orc_move(cv.v1[a], cv.A[a], cv.iA[a], cv.D[a], p[a], dt);
+                else p[a] = mv(opt, &cv, a, p[a], dt);
             }
             t = t_end;
             exit_face = (uint8_t)(2 * ax + (face[ax] > 0 ? 1 : 0));

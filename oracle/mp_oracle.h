@@ -47,7 +47,20 @@ typedef struct {
     double weak_sink_fraction; /* > 0 with pass_weak_sinks: a sink cell that
                                   extracts at least this fraction of its
                                   inflow still stops particles */
+    int32_t arith;        /* ORC_ARITH_PLAIN (0, the reference) or ORC_ARITH_MIRROR */
 } orc_track_opts;
+
+/* Arithmetic of the in-cell solution.
+ * PLAIN (the reference): the method's formulas written out as they read,
+ *   vp = v1 + A p, t = (d / vp) (log1p(z) / z) with z = A (d / vp),
+ *   p(t) = p + vp t (expm1(w) / w) with w = A t, the C library's log1p and
+ *   expm1, IEEE division, no fused multiply-add.
+ * MIRROR: the same solution in Pollock's own forms, ln(1 + z) / A and
+ *   p + vp (e^{At} - 1) / A, with 1/A formed once per cell, fused
+ *   multiply-adds and table-driven log1p / expm1 evaluated by fixed steps,
+ *   so that another implementation of the same steps gives the same bits. */
+#define ORC_ARITH_PLAIN 0
+#define ORC_ARITH_MIRROR 1
 
 /* Rectangular unstructured grid: axis-aligned box cells, per cell and face
  * (x-, x+, y-, y+, z-, z+) a list of sub-faces with the neighbour across
@@ -77,6 +90,20 @@ typedef struct {
     uint8_t pad[3];
 } orc_path_rec;
 
+/* One cell-step as the oracle evaluated it: the exit time and the reachable
+ * face of every axis, the particle velocity per axis, the time at the start
+ * of the step and the axis taken (-1: none). */
+typedef struct orc_trace_rec {
+    double te[3];         /* exit time per axis (+inf: no reachable face) */
+    double vp[3];         /* particle velocity per axis at the step's start */
+    double vf[3];         /* the larger face velocity magnitude per axis */
+    double t;             /* time at the start of the step */
+    int32_t particle, cell;
+    int8_t face[3];       /* +1 high face, -1 low face, 0 none */
+    int8_t ax;            /* axis of the exit taken; -1 none (stop time, capture, no exit) */
+    uint8_t pad[4];
+} orc_trace_rec;
+
 typedef struct {
     int32_t* cell; double *px, *py, *pz; double *gx, *gy, *gz; double* t;
     uint8_t* status; uint32_t* steps; uint8_t* exit_face; uint64_t* hash;
@@ -85,6 +112,9 @@ typedef struct {
     /* pathline points, appended in the order produced; path == NULL disables;
      * *path_n counts every point, also those beyond path_cap */
     orc_path_rec* path; int64_t path_cap; int64_t* path_n;
+    /* per-step trace (diagnostics: where two evaluations of one path part);
+     * trace == NULL disables; *trace_n counts every step */
+    struct orc_trace_rec* trace; int64_t trace_cap; int64_t* trace_n;
 } orc_track_out;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -92,6 +122,8 @@ double orc_log1p(double x);
 double orc_expm1(double w);
 double orc_exit_time(double v1, double v2, double A, double iA, double D, double p, int* face);
 double orc_move(double v1, double A, double iA, double D, double p, double dt);
+double orc_exit_time_plain(double v1, double v2, double A, double D, double p, int* face);
+double orc_move_plain(double v1, double A, double D, double p, double dt);
 int orc_release_box(const orc_field* f, int64_t n, const double lo[3], const double hi[3],
                     uint64_t seed, uint64_t id_offset,
                     int32_t* cell, double* px, double* py, double* pz, uint8_t* status);

@@ -1405,6 +1405,7 @@ void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 const DevField* field_device_view(const mp_field* f) { return &f->d; }
 bool field_is_usg(const mp_field* f) { return f->usg != 0; }
+int field_device(const mp_field* f) { return f->ctx->device; }
 
 }  // namespace mp
 

@@ -157,7 +157,12 @@ __device__ __forceinline__ double f2d_pos(float f)
 // and FP32 products, so that the FP64 path produces the same bits as any
 // other evaluation of the same steps on the host.  Exit-axis choices near a
 // tie then agree exactly, which library functions with different last-bit
-// rounding cannot guarantee on ill-conditioned fields.  The tables
+// rounding cannot guarantee on ill-conditioned fields.  The method is
+// Tang's table-driven one (P. T. P. Tang, "Table-driven implementation of
+// the exponential function in IEEE floating-point arithmetic", ACM TOMS
+// 15(2), 1989; "Table-driven implementation of the logarithm function in
+// IEEE floating-point arithmetic", ACM TOMS 16(4), 1990), with tables and
+// series lengths of this file's own choosing.  The tables
 // (mp_f64_tables.h) hold correctly rounded constants.
 //   log1p(x): u = 1 + x, c = its rounding error (two-sum); u = m 2^e with
 //     m in [1/sqrt2, sqrt2); the bucket of m (exponent and top 8 fraction

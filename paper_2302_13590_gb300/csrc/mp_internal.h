@@ -260,5 +260,6 @@ cudaError_t launch_track_mixed(const DevField& f, const Batch& b, unsigned modes
 void set_last_error(const char* msg);
 const DevField* field_device_view(const mp_field* f);
 bool field_is_usg(const mp_field* f);
+int field_device(const mp_field* f);   // the device of the field's context
 
 }  // namespace mp

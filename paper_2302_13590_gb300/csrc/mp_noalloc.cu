@@ -1,13 +1,16 @@
 // mp_noalloc.cu - tracking entry point that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the point where they track
-// particles: code running under a caller-owned memory budget (an embedding
-// application that hands out a fixed arena), inside a stream capture where
-// cudaMalloc is not permitted, or on a path that must not synchronise the
-// device.  mp_track_noalloc serves them: the caller passes every input and
-// output buffer, and the only other device memory the call uses is the small
-// file-scope array below, which every GPU that loads this library holds
-// until the process exits.
+// particles: code that runs under a memory budget it does not control (an
+// embedding application that hands out one fixed arena and forbids further
+// cudaMalloc), or code that must not let a library grow the device's memory
+// pool behind its back.  mp_track_noalloc serves them: the caller passes
+// every input and output buffer, and the only other device memory the call
+// uses is the small file-scope array below, which every GPU that loads this
+// library holds until the process exits.  The call does copy its small
+// host-side inputs (output times, the request descriptor) with
+// cudaMemcpyAsync from pageable host memory, which may block the calling
+// thread until the stream reaches the copy.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -36,8 +39,7 @@ int na_fail(int code, const std::string& m)
 }
 
 // Device address of the scratch array for the current device; taken once per
-// device (the first call on a device does it, so that call should come
-// before any stream capture).
+// device, by the first call on that device.
 int scratch_ptr(unsigned long long** out)
 {
     int dev = 0;
@@ -56,12 +58,16 @@ int scratch_ptr(unsigned long long** out)
     return MP_OK;
 }
 
-}  // namespace
-
-extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats)
+int track_noalloc(const mp_field* f, const mp_noalloc_args* a, cudaStream_t s, mp_stats* stats)
 {
-    if (!f || !a) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: NULL argument");
-    if (mp::field_is_usg(f)) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: rectilinear grids only");
+    // the copies below read host memory that does not outlive the call, so
+    // the call refuses a stream that is being captured into a graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess)
+        return na_fail(MP_ERR_CUDA, std::string("mp_track_noalloc: cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: the stream is capturing; call it outside stream capture");
     if (a->n < 0) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: n < 0");
     const mp_track_opts* o = &a->opts;
     if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES)) == 0 || (o->mode & ~3))
@@ -92,7 +98,6 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
     unsigned long long* scratch = nullptr;
     int rc = scratch_ptr(&scratch);
     if (rc != MP_OK) return rc;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned long long* queue = scratch;
     unsigned long long* counters = scratch + 8;
     double* times = reinterpret_cast<double*>(scratch + 8 + N_COUNTERS);
@@ -168,4 +173,25 @@ extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, voi
         if (h[COUNTER_ERR]) return na_fail(MP_ERR_DEVICE, "mp_track_noalloc: kernel raised its error flag");
     }
     return MP_OK;
+}
+
+}  // namespace
+
+extern "C" int mp_track_noalloc(const mp_field* f, const mp_noalloc_args* a, void* stream, mp_stats* stats)
+{
+    if (!f || !a) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: NULL argument");
+    if (mp::field_is_usg(f)) return na_fail(MP_ERR_INVALID_ARG, "mp_track_noalloc: rectilinear grids only");
+    // run on the field's device (its arrays and its copy of the scratch array
+    // live there) and give the caller back the device it had current
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    const int dev = mp::field_device(f);
+    if (dev != prev) {
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return na_fail(MP_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    const int rc = track_noalloc(f, a, reinterpret_cast<cudaStream_t>(stream), stats);
+    if (dev != prev) cudaSetDevice(prev);
+    return rc;
 }

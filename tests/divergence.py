@@ -1,0 +1,84 @@
+"""Where two evaluations of one particle path part, and by how much they had
+to disagree there.
+
+The oracle's two arithmetic modes evaluate the same solution with different
+rounding (a few ulp per step).  On a particle whose cell sequences differ,
+the first cell-step at which the two traces choose differently is one of:
+
+- ``axis``: both leave the cell, through faces of different axes; the gap is
+  the difference of the two competing exit times in the reference trace;
+- ``face``: the same axis, opposite faces (the particle velocity changes
+  sign between the two evaluations); the gap is the reference's velocity on
+  that axis, against the larger face velocity of the axis;
+- ``stop``: one reaches the stop time inside the cell, the other leaves it;
+  the gap is the distance of the reference's step end from the stop time;
+- ``cell``: the same exit, different cells entered (a quadtree hand-over);
+- ``end``: the traces agree step by step but one ends earlier (a status
+  decided differently after the last common step).
+
+The gap is measured against a scale (the time at the end of the step, or the
+face velocity), so ``gap <= rtol * scale`` says that the two choices cannot be
+told apart at the relative tolerance the results are compared at.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+import oracle as O
+
+
+@dataclass
+class Divergence:
+    particle: int
+    step: int
+    kind: str
+    gap: float
+    scale: float
+
+    @property
+    def rel(self) -> float:
+        return self.gap / self.scale if self.scale > 0 else (0.0 if self.gap == 0 else np.inf)
+
+
+def first_divergence(ref, other, t_stop=np.inf, particle=-1) -> Divergence:
+    """Compare two TRACE_RECORD arrays of one particle (``ref`` the reference
+    evaluation) and classify the first step at which they choose differently."""
+    n = min(ref.size, other.size)
+    for s in range(n):
+        a, b = ref[s], other[s]
+        if a["cell"] != b["cell"]:
+            return Divergence(particle, s, "cell", 0.0, 1.0)
+        ax_a, ax_b = int(a["ax"]), int(b["ax"])
+        if ax_a == ax_b and (ax_a < 0 or a["face"][ax_a] == b["face"][ax_b]):
+            continue
+        t = float(a["t"])
+        if ax_a >= 0 and ax_b >= 0 and ax_a != ax_b:
+            ta, tb = float(a["te"][ax_a]), float(a["te"][ax_b])
+            if np.isfinite(tb):
+                return Divergence(particle, s, "axis", abs(tb - ta), t + tb)
+            # the other evaluation's axis has no reachable face here: its
+            # particle velocity changed sign
+            return Divergence(particle, s, "face", abs(float(a["vp"][ax_b])), float(a["vf"][ax_b]))
+        if ax_a >= 0 and ax_b >= 0:
+            return Divergence(particle, s, "face", abs(float(a["vp"][ax_a])), float(a["vf"][ax_a]))
+        ax = ax_a if ax_a >= 0 else ax_b
+        te = float(a["te"][ax])
+        if not np.isfinite(te):
+            return Divergence(particle, s, "face", abs(float(a["vp"][ax])), float(a["vf"][ax]))
+        return Divergence(particle, s, "stop", abs(t + te - t_stop), float(t_stop))
+    return Divergence(particle, n, "end", np.inf, 1.0)
+
+
+def analyse(field, state, which, *, t_stop=np.inf, times=None, ref="plain", other="mirror", **kw):
+    """Trace particles ``which`` of ``state`` in both arithmetic modes and
+    return one Divergence per particle (kind ``end`` with an infinite gap
+    where the traces agree step by step but end differently)."""
+    out = []
+    for q in np.asarray(which, dtype=np.int64):
+        s1 = O.subset(state, [int(q)])
+        ta = O.track(field, s1, t_stop=t_stop, times=times, arith=ref, trace=True, **kw)["trace"]
+        tb = O.track(field, s1, t_stop=t_stop, times=times, arith=other, trace=True, **kw)["trace"]
+        out.append(first_divergence(ta, tb, t_stop=t_stop, particle=int(q)))
+    return out

@@ -105,3 +105,44 @@ def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0),
         assert np.array_equal(np.isfinite(a), fin)
         e = rel_err(a[fin], b[fin], scale=pos_scale(dmin[ax], b[fin]))
         assert e.max(initial=0.0) <= rtol, f"ts {gk}: max rel err {e.max()}"
+
+
+def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None, t_stop=np.inf, rtol=1e-10,
+                       label="", **track_kw):
+    """FP64 GPU results against the plain-arithmetic oracle (the reference).
+
+    Particles whose cell sequence (FNV hash) matches: statuses, cells, step
+    counts and exit faces equal, travel times and positions (endpoint and
+    timeseries) within ``rtol``.  Particles whose sequence differs are traced
+    in both oracle modes (the mirror mode equals the GPU bit for bit, which
+    the caller checks separately) and each must part at a near-tie: at the
+    first step where the evaluations choose differently, the reference's two
+    competing choices lie within ``rtol`` of each other (divergence.py).
+    ``state`` is the oracle state of the compared particles (``idx`` of the
+    GPU arrays).  Returns (number of divergent particles, max relative time
+    error, max relative position error) and prints them."""
+    from tests import divergence as D
+    sel = slice(None) if idx is None else idx
+    hsame = ep["hash"][sel] == plain["hash"]
+    ndiv = compare_fp64(ep, plain, idx=idx, rtol=rtol, dmin=dmin(field), allow_divergent=1.0)
+    if ts is not None:
+        compare_timeseries_fp64(ts, plain, idx=idx, rtol=rtol, dmin=dmin(field), keep=hsame)
+    keep = np.nonzero(hsame)[0]
+    tg = np.asarray(ep["t"])[sel][keep]
+    tp = plain["t"][keep]
+    fin = np.isfinite(tp)
+    t_err = rel_err(tg[fin], tp[fin]).max(initial=0.0)
+    p_err = 0.0
+    for ax, (gk, ok) in enumerate((("x", "gx"), ("y", "gy"), ("z", "gz"))):
+        a, b = np.asarray(ep[gk])[sel][keep], plain[ok][keep]
+        f2 = np.isfinite(b)
+        p_err = max(p_err, rel_err(a[f2], b[f2], scale=pos_scale(dmin(field)[ax], b[f2])).max(initial=0.0))
+    bad = []
+    if ndiv:
+        for d in D.analyse(field, state, np.nonzero(~hsame)[0], t_stop=t_stop, times=times, **track_kw):
+            if not d.rel <= rtol:
+                bad.append(d)
+    print(f"fp64 vs plain oracle {label}: {hsame.size} particles, {ndiv} divergent "
+          f"({ndiv / max(hsame.size, 1):.2e}), max rel t err {t_err:.2e}, max rel pos err {p_err:.2e}")
+    assert not bad, f"{len(bad)} divergent particles that are not near-ties, first {bad[:3]}"
+    return ndiv, t_err, p_err

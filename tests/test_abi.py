@@ -26,6 +26,22 @@ def test_header_declares_the_boundary_calls():
         assert required in names
 
 
+def test_every_declared_call_cites_its_passage():
+    """Each call of the boundary names the passage of the paper it follows
+    (or says that it is infrastructure with no passage) in a comment that
+    ends directly above its declaration."""
+    src = open(HEADER).read()
+    for name in declared_functions():
+        m = re.search(r"^(?:const\s+)?\w+\**\s+\**" + name + r"\s*\(", src, flags=re.M)
+        assert m, name
+        before = src[:m.start()].rstrip()
+        assert before.endswith("*/"), f"{name}: no comment directly above its declaration"
+        comment = before[before.rindex("/*"):]
+        assert "Passage:" in comment, f"{name}: comment names no passage"
+        body = comment.split("Passage:", 1)[1]
+        assert re.search(r"(Introduction|Methods|Results|Conclusions|none)", body), name
+
+
 def test_library_loads_and_exports_every_declared_symbol():
     lib = mp.load_library()
     names = declared_functions()

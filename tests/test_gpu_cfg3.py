@@ -4,7 +4,9 @@ persistent work-queue kernel and 100 output times, measured against the FP64
 oracle on a 1e4-particle subsample and against the spread of the oracle's
 own results under 1e-7 start perturbations (the field is so ill-conditioned
 that such a perturbation changes ~90 % of cell sequences).  The FP64 path on
-a subsample matches the oracle exactly."""
+a subsample matches the oracle's mirror arithmetic exactly and departs from
+its plain arithmetic less than a 1e-14 start perturbation moves the plain
+oracle itself."""
 import time
 
 import numpy as np
@@ -63,7 +65,7 @@ def test_cfg3_mixed_full_size_vs_oracle(cfg3):
     idx = np.sort(np.random.default_rng(4).choice(n, 10000, replace=False))
     s0 = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
     sub = O.subset(s0, idx)
-    ref = O.track(w.field, sub, times=w.times)
+    ref = O.track(w.field, sub, times=w.times, arith="mirror")
     # the problem's own conditioning: the FP64 oracle from start positions
     # moved by +-1e-7 cell widths (the FP32 resolution of a local coordinate)
     rng = np.random.default_rng(5)
@@ -72,7 +74,7 @@ def test_cfg3_mixed_full_size_vs_oracle(cfg3):
     pert = {kk: v.copy() for kk, v in sub.items()}
     pert["py"] = np.clip(pert["py"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.delc[i0], 0, w.field.delc[i0])
     pert["pz"] = np.clip(pert["pz"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.dz[k0], 0, w.field.dz[k0])
-    refp = O.track(w.field, pert)
+    refp = O.track(w.field, pert, arith="mirror")
 
     def errs(a_t, a_x, a_y, a_z, a_hash):
         same = a_hash == ref["hash"]
@@ -117,12 +119,35 @@ def test_cfg3_fp64_subsample_exact(cfg3):
     frac = np.stack([s0["px"] / w.field.delr[j], s0["py"] / w.field.delc[i], s0["pz"] / w.field.dz[k]], axis=1)
     # explicit release of the same particles (fractions re-derived from offsets)
     st = O.release_explicit(w.field, c, frac)
-    ref = O.track(w.field, st, times=w.times[::10])
+    ref = O.track(w.field, st, times=w.times[::10], arith="mirror")
     ep, ts, stats = G.gpu_run(ctx, fh, cells=c, frac=frac, times=w.times[::10], schedule=mp.SCHED_DYNAMIC)
-    # the oracle alone changes ~31 % of these paths for start perturbations
-    # of 1e-13, so agreement needs the same bits: both sides evaluate log1p
-    # and expm1 by the same series steps
+    # against the oracle's mirror arithmetic (the kernel's own evaluation
+    # steps): every result bit-exact
     ndiv = G.compare_fp64(ep, ref, dmin=G.dmin(w.field))
     keep = ep["hash"] == ref["hash"]
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(w.field), keep=keep)
-    print(f"cfg3 FP64 subsample: {ndiv} of {keep.size} cell sequences differ from the oracle")
+    assert ndiv == 0
+    # against the plain arithmetic (the reference).  This field is
+    # ill-conditioned: along a path of ~800 cells a difference of one
+    # rounding grows about tenfold every 70 cell-steps, so two correct FP64
+    # evaluations part on ~10 % of paths.  The GPU must depart from the
+    # reference no more than the reference departs from itself when its start
+    # positions move by 1e-14 relative (~45 ulp): fewer divergent sequences
+    # and a smaller mean travel-time change.
+    plain = O.track_parallel(w.field, st, 8, times=w.times[::10])
+    pert = {kk: v.copy() for kk, v in st.items()}
+    pert["py"] = np.clip(pert["py"] * (1 + 1e-14), 0, w.field.delc[i])
+    pert["pz"] = np.clip(pert["pz"] * (1 - 1e-14), 0, w.field.dz[k])
+    plain_p = O.track_parallel(w.field, pert, 8, times=w.times[::10])
+
+    def dev(h, t):
+        d = h != plain["hash"]
+        rt = np.abs(t - plain["t"]) / plain["t"]
+        return d.mean(), rt[~d], rt.mean()
+
+    dg, sg, mg = dev(ep["hash"], ep["t"])
+    dq, sq, mq = dev(plain_p["hash"], plain_p["t"])
+    print(f"cfg3 FP64 vs plain oracle ({keep.size} particles): divergent {dg:.3f}, same-sequence t err median "
+          f"{np.median(sg):.1e}, mean |dt|/t {mg:.2e} | plain oracle moved 1e-14: divergent {dq:.3f}, median "
+          f"{np.median(sq):.1e}, mean {mq:.2e}")
+    assert dg <= dq and mg <= mq

@@ -28,7 +28,7 @@ def case(ctx):
     fh = ctx.field(f)
     cells, frac = I.explicit_particles(f, 3001, seed=12, cols=(1, 5))
     t0 = np.random.default_rng(3).uniform(0.0, 50.0, cells.size)
-    full = O.track(f, _oracle_state(f, cells, frac, t0))
+    full = O.track(f, _oracle_state(f, cells, frac, t0), arith="mirror")
     times = np.quantile(full["t"], [0.1, 0.4, 0.8, 0.97])
     yield f, fh, cells, frac, t0, times
     mp.mp_field_free(fh)
@@ -64,7 +64,7 @@ def test_host_call_equals_one_request(ctx, case, precision, n_chunks):
     assert st["cell_steps"] == ref_st["cell_steps"] and st["n_status"] == ref_st["n_status"]
     assert st["device_error"] == 0 and st["kernel_ms"] > 0
     if precision == mp.PREC_FP64:
-        ref = O.track(f, _oracle_state(f, cells, frac, t0), times=times)
+        ref = O.track(f, _oracle_state(f, cells, frac, t0), times=times, arith="mirror")
         G.compare_fp64(ep, ref, dmin=G.dmin(f))
         G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
 
@@ -101,7 +101,7 @@ def test_host_call_on_a_quadtree(ctx):
     fu = ctx.field(u)
     cells, frac = U.explicit_particles(u, 1500, seed=8)
     st0 = O.release_explicit(u, cells, frac)
-    times = np.quantile(O.track(u, st0, pass_weak_sinks=True)["t"], [0.3, 0.7])
+    times = np.quantile(O.track(u, st0, pass_weak_sinks=True, arith="mirror")["t"], [0.3, 0.7])
     opts = mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, times=times, flags=mp.TRACK_PASS_WEAK_SINKS,
                         weak_sink_fraction=0.5)
     ref_ep, ref_ts, _ = _one_request(ctx, fu, cells, frac, None, opts)
@@ -109,7 +109,7 @@ def test_host_call_on_a_quadtree(ctx):
     for k in ref_ep:
         assert np.array_equal(ep[k], ref_ep[k], equal_nan=True), k
     assert ts.tobytes() == ref_ts.tobytes()
-    ref = O.track(u, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=0.5)
+    ref = O.track(u, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=0.5, arith="mirror")
     G.compare_fp64(ep, ref, dmin=u.extent)
     G.compare_timeseries_fp64(ts, ref, dmin=u.extent)
     mp.mp_field_free(fu)

@@ -1,7 +1,12 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-FP64: exit-cell sequences (FNV hash), statuses, cells, step counts and exit
-faces bit-exact; positions and travel times within 1e-10 relative.  Mixed
+FP64, against the oracle's plain arithmetic (the reference: the formulas as
+they read, the C library's log1p/expm1): exit-cell sequences (FNV hash),
+statuses, cells, step counts and exit faces equal and positions and travel
+times within 1e-10 relative on every particle whose sequence matches; a
+particle whose sequence differs must part at a near-tie (the two competing
+choices within 1e-10).  FP64 against the oracle's mirror arithmetic (the
+same solution by the kernel's own evaluation steps): everything bit-exact.  Mixed
 precision: travel time within 1e-5 relative and endpoint within 1e-4 cell
 widths for particles whose cell sequence matches; the fraction of particles
 whose sequence diverges at near-ties is reported and bounded.
@@ -66,9 +71,11 @@ def test_fp64_cfg1_full(ctx, cfg1, schedule):
     w, fh = cfg1
     ep, ts, st = G.gpu_run(ctx, fh, release=w.release, times=w.times, schedule=schedule)
     ostate = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
-    ref = O.track(w.field, ostate, times=w.times)
+    ref = O.track(w.field, ostate, times=w.times, arith="mirror")
     G.compare_fp64(ep, ref, dmin=G.dmin(w.field))
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(w.field))
+    plain = O.track(w.field, ostate, times=w.times)
+    G.compare_fp64_plain(ep, plain, field=w.field, state=ostate, ts=ts, times=w.times, label="cfg1")
     assert st["cell_steps"] == int(ref["steps"].sum())
     assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
     assert st["device_error"] == 0
@@ -82,13 +89,15 @@ def test_fp64_random_fields(ctx, seed, n, schedule, t_frac):
     fh = ctx.field(f)
     cells, frac = I.explicit_particles(f, n, seed=seed, cols=(1, 6))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0)
+    full = O.track(f, st0, arith="mirror")
     t_stop = np.inf if t_frac is None else float(np.quantile(full["t"], t_frac))
     times = np.quantile(full["t"], [0.0, 0.05, 0.2, 0.5, 0.8, 0.99]) * 1.01
-    ref = O.track(f, st0, t_stop=t_stop, times=times)
+    ref = O.track(f, st0, t_stop=t_stop, times=times, arith="mirror")
     ep, ts, stats = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, t_stop=t_stop, schedule=schedule)
     G.compare_fp64(ep, ref, dmin=G.dmin(f))
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+    plain = O.track(f, st0, t_stop=t_stop, times=times)
+    G.compare_fp64_plain(ep, plain, field=f, state=st0, ts=ts, times=times, t_stop=t_stop, label=f"random {seed}")
     for k in ("px", "py", "pz"):
         assert np.max(G.rel_err(ep[k], ref[k], scale=1.0)) <= 1e-10
     mp.mp_field_free(fh)
@@ -107,12 +116,15 @@ def test_fp64_edge_cases(ctx):
                      [0.3, 0.7, 0.2]])
     st0 = O.release_explicit(f, cells, frac)
     for t_stop, max_steps in ((np.inf, 0), (0.0, 0), (np.inf, 2), (1e3, 0)):
-        ref = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, times=[0.0, 10.0, 1e4])
+        ref = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, times=[0.0, 10.0, 1e4], arith="mirror")
         for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
             ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, max_steps=max_steps,
                                   times=[0.0, 10.0, 1e4], schedule=sch)
             G.compare_fp64(ep, ref, dmin=G.dmin(f))
             G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+            plain = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, times=[0.0, 10.0, 1e4])
+            G.compare_fp64_plain(ep, plain, field=f, state=st0, ts=ts, times=[0.0, 10.0, 1e4], t_stop=t_stop,
+                                 max_steps=max_steps, label="edge cases")
     # an empty group
     ep, ts, st = G.gpu_run(ctx, fh, cells=np.zeros(0, np.int32), frac=np.zeros((0, 3)))
     assert ep["cell"].size == 0 and st["cell_steps"] == 0
@@ -128,10 +140,13 @@ def test_fp64_no_exit_divide(ctx):
     frac = np.array([[0.5, 0.5, 0.5], [0.2, 0.1, 0.9], [0.9, 0.5, 0.5]])
     st0 = O.release_explicit(f, cells, frac)
     for t_stop in (np.inf, 5e3):
-        ref = O.track(f, st0, t_stop=t_stop, times=[1.0, 1e3, 4e3])
+        ref = O.track(f, st0, t_stop=t_stop, times=[1.0, 1e3, 4e3], arith="mirror")
         ep, ts, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, times=[1.0, 1e3, 4e3])
         G.compare_fp64(ep, ref, dmin=G.dmin(f))
         G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+        plain = O.track(f, st0, t_stop=t_stop, times=[1.0, 1e3, 4e3])
+        G.compare_fp64_plain(ep, plain, field=f, state=st0, ts=ts, times=[1.0, 1e3, 4e3], t_stop=t_stop,
+                             label="divide")
     mp.mp_field_free(fh)
 
 
@@ -150,10 +165,13 @@ def test_fp64_exact_ties(ctx):
         frac[2::6, 1] = frac[2::6, 0]                  # x-y-z ties
         frac[2::6, 2] = frac[2::6, 0]
         cells = np.zeros(frac.shape[0], np.int32)
-        ref = O.track(f, O.release_explicit(f, cells, frac))
+        st0 = O.release_explicit(f, cells, frac)
+        ref = O.track(f, st0, arith="mirror")
+        plain = O.track(f, st0)
         for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
             ep, _, _ = G.gpu_run(ctx, fh, cells=cells, frac=frac, schedule=sch)
             G.compare_fp64(ep, ref, dmin=G.dmin(f))
+            G.compare_fp64_plain(ep, plain, field=f, state=st0, label="exact ties")
         ef = ref["exit_face"]
         assert not np.isin(ef[0::3], (2, 3)).any()    # an x-y tie never exits through y
         assert not np.isin(ef[1::3], (4, 5)).any()    # a y-z tie never exits through z
@@ -216,11 +234,11 @@ def test_weak_sink_fraction_vs_oracle(ctx):
     assert fs[0] > 0 and fs[-1] < 1
     cells, frac = I.explicit_particles(f, 3001, seed=17, cols=(1, 6))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0, pass_weak_sinks=True)
+    full = O.track(f, st0, pass_weak_sinks=True, arith="mirror")
     times = np.quantile(full["t"], [0.2, 0.5, 0.9])
     thresholds = [fs[0] / 2] + list((fs[:-1] + fs[1:]) / 2) + [(fs[-1] + 1) / 2]
     for thr in thresholds:
-        ref = O.track(f, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True)
+        ref = O.track(f, st0, times=times, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True, arith="mirror")
         for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
             gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
             req = ctx.track(gh, mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES | mp.MODE_PATHLINE, times=times,
@@ -263,10 +281,10 @@ def test_weak_sinks_pass_through(ctx, scale, seed):
     sink = int(np.nonzero(f.ibound.reshape(-1) == 2)[0][0])
     cells[:3] = sink  # released inside a sink cell: SINK at release
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0, pass_weak_sinks=True)
+    full = O.track(f, st0, pass_weak_sinks=True, arith="mirror")
     times = np.quantile(full["t"], [0.1, 0.5, 0.9])
-    ref = O.track(f, st0, times=times, pass_weak_sinks=True)
-    strong = O.track(f, st0)
+    ref = O.track(f, st0, times=times, pass_weak_sinks=True, arith="mirror")
+    strong = O.track(f, st0, arith="mirror")
     assert not np.array_equal(ref["hash"], strong["hash"])
     for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
         ep, ts, stats = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, schedule=sch,
@@ -284,9 +302,9 @@ def test_weak_sinks_pass_through(ctx, scale, seed):
     G.compare_fp64(ep0, strong, dmin=G.dmin(f))
     # stop and resume: particles stopped inside a well cell continue from there
     T1 = float(np.quantile(full["t"][full["t"] > 0], 0.3))
-    a = O.track(f, st0, t_stop=T1, pass_weak_sinks=True)
+    a = O.track(f, st0, t_stop=T1, pass_weak_sinks=True, arith="mirror")
     in_well = (a["status"] == O.ST_TIME) & (f.ibound.reshape(-1)[np.maximum(a["cell"], 0)] == 2)
-    b = O.track(f, O.resume_state(a), pass_weak_sinks=True)
+    b = O.track(f, O.resume_state(a), pass_weak_sinks=True, arith="mirror")
     gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
     flags = mp.TRACK_PASS_WEAK_SINKS | mp.TRACK_UPDATE_GROUP
     r1 = ctx.track(gh, t_stop=T1, flags=flags)
@@ -310,9 +328,12 @@ def test_fp64_cfg2_full_size_sampled(ctx, cfg2):
     rng = np.random.default_rng(1)
     idx = np.unique(np.concatenate([rng.choice(n, 20000, replace=False), np.arange(64), np.arange(n - 64, n)]))
     full_state = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
-    ref = O.track(w.field, O.subset(full_state, idx), times=w.times)
+    sub = O.subset(full_state, idx)
+    ref = O.track(w.field, sub, times=w.times, arith="mirror")
     G.compare_fp64(ep, ref, idx=idx, dmin=G.dmin(w.field))
     G.compare_timeseries_fp64(ts, ref, idx=idx, dmin=G.dmin(w.field))
+    plain = O.track_parallel(w.field, sub, 8, times=w.times)
+    G.compare_fp64_plain(ep, plain, field=w.field, state=sub, idx=idx, ts=ts, times=w.times, label="cfg2 sample")
     # whole-run invariants at full size
     assert st["cell_steps"] == int(ep["steps"].astype(np.uint64).sum())
     assert st["n_status"] == np.bincount(ep["status"], minlength=8).tolist()
@@ -342,8 +363,8 @@ def test_update_group_resume(ctx, cfg1):
     r2 = ctx.track(gh, t_stop=T2, flags=mp.TRACK_UPDATE_GROUP)
     ep = r2.endpoints()
     s0 = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
-    a = O.track(w.field, s0, t_stop=T1)
-    b = O.track(w.field, O.resume_state(a), t_stop=T2)
+    a = O.track(w.field, s0, t_stop=T1, arith="mirror")
+    b = O.track(w.field, O.resume_state(a), t_stop=T2, arith="mirror")
     # steps, hash and exit face are carried through the pause
     for k in ("status", "cell", "steps", "exit_face", "hash"):
         assert np.array_equal(ep[k], b[k]), k
@@ -378,7 +399,7 @@ def test_mixed_cfg1(ctx, cfg1):
     w, fh = cfg1
     ep, ts, _ = G.gpu_run(ctx, fh, release=w.release, times=w.times, precision=mp.PREC_MIXED)
     s0 = O.release_box(w.field, w.release.n, w.release.lo, w.release.hi, w.release.seed)
-    ref = O.track(w.field, s0, times=w.times)
+    ref = O.track(w.field, s0, times=w.times, arith="mirror")
     frac_div, t_err, pos_err = _mixed_report(ep, ref, w.field)
     print(f"mixed cfg1: divergent {frac_div:.2e} t_err {t_err:.2e} pos_err {pos_err:.2e}")
     assert frac_div <= 0.01
@@ -418,14 +439,14 @@ def test_mixed_cfg2_sampled(ctx, cfg2):
     idx = np.sort(np.random.default_rng(2).choice(n, 10000, replace=False))
     s0 = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
     sub0 = O.subset(s0, idx)
-    ref = O.track(w.field, sub0, times=w.times)
+    ref = O.track(w.field, sub0, times=w.times, arith="mirror")
     rng = np.random.default_rng(5)
     pert = {k: v.copy() for k, v in sub0.items()}
     c = pert["cell"]
     j, i, k = c % w.field.ncol, (c // w.field.ncol) % w.field.nrow, c // (w.field.ncol * w.field.nrow)
     pert["py"] = np.clip(pert["py"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.delc[i], 0, w.field.delc[i])
     pert["pz"] = np.clip(pert["pz"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.dz[k], 0, w.field.dz[k])
-    refp = O.track(w.field, pert, times=w.times)
+    refp = O.track(w.field, pert, times=w.times, arith="mirror")
     sub = {kk: v[idx] for kk, v in ep.items()}
     div_m, t_m, p_m = _dist(sub, ref, w.field)
     refp_ep = dict(refp, x=refp["gx"], y=refp["gy"], z=refp["gz"])

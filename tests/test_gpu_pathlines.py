@@ -63,9 +63,9 @@ def test_pathlines_fp64(ctx, fld, schedule, with_ts):
     f, fh = fld
     cells, frac = I.explicit_particles(f, 2500, seed=21, cols=(1, 5))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0)
+    full = O.track(f, st0, arith="mirror")
     times = np.quantile(full["t"], [0.1, 0.5, 0.9]) if with_ts else None
-    ref = O.track(f, st0, times=times, pathline=True)
+    ref = O.track(f, st0, times=times, pathline=True, arith="mirror")
     mode = mp.MODE_ENDPOINT | mp.MODE_PATHLINE | (mp.MODE_TIMESERIES if with_ts else 0)
     ep, ts, st, path = _run(ctx, fh, cells, frac, mode=mode, times=times, schedule=schedule)
     assert st["path_points"] == ref["path"].size == int(ref["steps"].sum()) + cells.size
@@ -79,11 +79,11 @@ def test_pathlines_stop_time_cap_and_staged_release(ctx, fld):
     f, fh = fld
     cells, frac = I.explicit_particles(f, 700, seed=22, cols=(1, 5))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0)
+    full = O.track(f, st0, arith="mirror")
     t0 = np.where(np.arange(cells.size) % 3 == 0, 0.4 * np.median(full["t"]), 0.0)
     st0["t"] = t0
     for t_stop, max_steps in ((float(np.median(full["t"])), 0), (np.inf, 5)):
-        ref = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, pathline=True)
+        ref = O.track(f, st0, t_stop=t_stop, max_steps=max_steps, pathline=True, arith="mirror")
         ep, _, st, path = _run(ctx, fh, cells, frac, t0=t0, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE,
                                t_stop=t_stop, max_steps=max_steps)
         compare_paths(path, ref["path"], f)
@@ -94,7 +94,7 @@ def test_pathline_capacity_overflow(ctx, fld):
     f, fh = fld
     cells, frac = I.explicit_particles(f, 500, seed=23, cols=(1, 5))
     st0 = O.release_explicit(f, cells, frac)
-    ref = _sorted(O.track(f, st0, pathline=True)["path"])
+    ref = _sorted(O.track(f, st0, pathline=True, arith="mirror")["path"])
     cap = ref.size // 3
     _, _, st, path = _run(ctx, fh, cells, frac, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE, path_capacity=cap)
     assert st["path_points"] == ref.size and path.size == cap
@@ -115,7 +115,7 @@ def test_pathlines_in_a_batch(ctx, fld):
         groups.append(mp.mp_release_group(ctx.h, fh, cell=cells, local=frac))
         pl = i != 1
         specs.append(mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_PATHLINE if pl else 0)))
-        refs.append(O.track(f, O.release_explicit(f, cells, frac), pathline=pl))
+        refs.append(O.track(f, O.release_explicit(f, cells, frac), pathline=pl, arith="mirror"))
     ids = mp.mp_track_batch(ctx.h, groups, specs)
     for i, rid in enumerate(ids):
         mp.mp_wait(ctx.h, rid)
@@ -132,11 +132,11 @@ def test_pathlines_through_periods(ctx, fld):
     f, fh = fld
     cells, frac = I.explicit_particles(f, 1500, seed=24, cols=(1, 5))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0)
+    full = O.track(f, st0, arith="mirror")
     fs = I.period_fields(f, seed=9, head_scale=(1.0, 0.5, -0.6), new_wells=(0, 1, 0))
     fhs = [fh] + [ctx.field(g) for g in fs[1:]]
     T = np.quantile(full["t"], [0.3, 0.6])
-    ref = O.track_periods(fs, T, st0, pathline=True)
+    ref = O.track_periods(fs, T, st0, pathline=True, arith="mirror")
     gh = mp.mp_release_group(ctx.h, fh, cell=cells, local=frac)
     req = ctx.track_periods(gh, fhs, T, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE)
     req.wait()
@@ -152,7 +152,7 @@ def test_pathlines_mixed(ctx, fld):
     f, fh = fld
     cells, frac = I.explicit_particles(f, 2000, seed=25, cols=(1, 5))
     st0 = O.release_explicit(f, cells, frac)
-    ref = O.track(f, st0, pathline=True)
+    ref = O.track(f, st0, pathline=True, arith="mirror")
     ep, _, st, path = _run(ctx, fh, cells, frac, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE,
                            precision=mp.PREC_MIXED)
     same = np.nonzero(ep["hash"] == ref["hash"])[0]
@@ -187,7 +187,7 @@ def test_pathlines_cfg2_sampled(ctx):
     keep = torch.isin(buf[:, 8], torch.as_tensor(idx, dtype=torch.int32, device="cuda"))
     path = buf[keep].cpu().numpy().view(mp.PATH_RECORD).reshape(-1)
     s0 = O.subset(O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed), idx)
-    ref = O.track(w.field, s0, pathline=True)["path"]
+    ref = O.track(w.field, s0, pathline=True, arith="mirror")["path"]
     ref["particle"] = idx[ref["particle"]]
     compare_paths(path, ref, w.field)
     print(f"cfg2 pathlines: {st['path_points']:.3e} points, {st['cell_steps']:.3e} cell-steps in "

@@ -29,7 +29,7 @@ def small(ctx):
     fhs = [ctx.field(g) for g in fs]
     cells, frac = I.explicit_particles(f, 3000, seed=12, cols=(1, 4))
     st0 = O.release_explicit(f, cells, frac)
-    full = O.track(f, st0)
+    full = O.track(f, st0, arith="mirror")
     T = np.quantile(full["t"], [0.25, 0.6])
     yield f, fs, fhs, cells, frac, st0, full, T
     for fh in fhs:
@@ -58,7 +58,7 @@ def test_periods_fp64_vs_oracle(ctx, small, schedule, pass_sinks, wsf):
     f, fs, fhs, cells, frac, st0, full, T = small
     times = np.sort(np.concatenate([np.quantile(full["t"], [0.02, 0.1, 0.4, 0.8, 0.97]) * 1.01, T]))
     flags = mp.TRACK_PASS_WEAK_SINKS if pass_sinks else 0
-    ref = O.track_periods(fs, T, st0, times=times, pass_weak_sinks=pass_sinks, weak_sink_fraction=wsf)
+    ref = O.track_periods(fs, T, st0, times=times, pass_weak_sinks=pass_sinks, weak_sink_fraction=wsf, arith="mirror")
     ep, ts, st = _run(ctx, fhs, T, cells, frac, times=times, schedule=schedule, flags=flags, weak_sink_fraction=wsf)
     G.compare_fp64(ep, ref, dmin=G.dmin(f))
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
@@ -72,7 +72,7 @@ def test_periods_fp64_vs_oracle(ctx, small, schedule, pass_sinks, wsf):
 def test_periods_with_stop_time_and_step_cap(ctx, small):
     f, fs, fhs, cells, frac, st0, full, T = small
     for t_stop, max_steps in ((0.5 * (T[0] + T[1]), 0), (np.inf, 9)):
-        ref = O.track_periods(fs, T, st0, t_stop=t_stop, max_steps=max_steps)
+        ref = O.track_periods(fs, T, st0, t_stop=t_stop, max_steps=max_steps, arith="mirror")
         ep, _, st = _run(ctx, fhs, T, cells, frac, t_stop=t_stop, max_steps=max_steps)
         G.compare_fp64(ep, ref, dmin=G.dmin(f))
         assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
@@ -101,8 +101,8 @@ def test_periods_update_group_then_continue(ctx, small):
     # the group now sits in the last period's field: continue there
     r2 = ctx.track(gh)
     r2.wait()
-    a = O.track_periods(fs, T, st0, t_stop=t1)
-    b = O.track(fs[-1], O.resume_state(a))
+    a = O.track_periods(fs, T, st0, t_stop=t1, arith="mirror")
+    b = O.track(fs[-1], O.resume_state(a), arith="mirror")
     G.compare_fp64(r2.endpoints(), b, dmin=G.dmin(f))
     for r in (r1, r2):
         r.free()
@@ -111,7 +111,7 @@ def test_periods_update_group_then_continue(ctx, small):
 
 def test_periods_mixed(ctx, small):
     f, fs, fhs, cells, frac, st0, full, T = small
-    ref = O.track_periods(fs, T, st0)
+    ref = O.track_periods(fs, T, st0, arith="mirror")
     ep, _, st = _run(ctx, fhs, T, cells, frac, precision=mp.PREC_MIXED)
     same = ep["hash"] == ref["hash"]
     assert same.mean() >= 0.98
@@ -157,7 +157,7 @@ def test_periods_cfg2_sampled(ctx):
     assert st["device_error"] == 0 and sum(st["n_status"]) == n
     idx = np.sort(np.random.default_rng(3).choice(n, 3000, replace=False))
     s0 = O.subset(O.release_box(w.field, n, rel.lo, rel.hi, rel.seed), idx)
-    ref = O.track_periods(fs, T, s0, times=times)
+    ref = O.track_periods(fs, T, s0, times=times, arith="mirror")
     ndiv = G.compare_fp64(ep, ref, idx=idx, dmin=G.dmin(w.field), allow_divergent=0.002)
     keep = ep["hash"][idx] == ref["hash"]
     G.compare_timeseries_fp64(ts, ref, idx=idx, dmin=G.dmin(w.field), keep=keep)
@@ -181,10 +181,10 @@ def test_staged_release_fp64(ctx, small, with_periods):
     st["t"] = t0
     times = np.linspace(0.0, 2.0 * T[1], 9)
     if with_periods:
-        ref = O.track_periods(fs, T, st, times=times)
+        ref = O.track_periods(fs, T, st, times=times, arith="mirror")
         ep, ts, stats = _run(ctx, fhs, T, cell, fr, times=times, t0=t0)
     else:
-        ref = O.track(f, st, times=times)
+        ref = O.track(f, st, times=times, arith="mirror")
         ep, ts, stats = G.gpu_run(ctx, fhs[0], cells=cell, frac=fr, t0=t0, times=times)
     G.compare_fp64(ep, ref, dmin=G.dmin(f))
     G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))

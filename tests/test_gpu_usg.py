@@ -45,7 +45,7 @@ def test_structured_as_unstructured_equals_rectilinear_path(ctx):
     u = U.from_structured(f)
     fs, fu = ctx.field(f), ctx.field(u)
     cells, frac = I.explicit_particles(f, 2000, seed=4, cols=(1, 6))
-    full = O.track(f, O.release_explicit(f, cells, frac))
+    full = O.track(f, O.release_explicit(f, cells, frac), arith="mirror")
     times = np.quantile(full["t"], [0.05, 0.5, 0.95])
     for sched in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
         a = _run(ctx, fs, cells, frac, times=times, schedule=sched,
@@ -69,10 +69,10 @@ def test_quadtree_fp64_vs_oracle(ctx, seed, n, schedule, pass_sinks):
     fh = ctx.field(u)
     cells, frac = U.explicit_particles(u, n, seed=seed)
     st0 = O.release_explicit(u, cells, frac)
-    full = O.track(u, st0, pass_weak_sinks=pass_sinks)
+    full = O.track(u, st0, pass_weak_sinks=pass_sinks, arith="mirror")
     times = np.quantile(full["t"], [0.0, 0.2, 0.6, 0.99]) * 1.01
     flags = mp.TRACK_PASS_WEAK_SINKS if pass_sinks else 0
-    ref = O.track(u, st0, times=times, pathline=True, pass_weak_sinks=pass_sinks)
+    ref = O.track(u, st0, times=times, pathline=True, pass_weak_sinks=pass_sinks, arith="mirror")
     ep, ts, st, path = _run(ctx, fh, cells, frac, times=times, schedule=schedule, flags=flags,
                             mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES | mp.MODE_PATHLINE, path_capacity=200 * n)
     G.compare_fp64(ep, ref, dmin=_dmin(u))
@@ -95,17 +95,17 @@ def test_quadtree_periods_and_resume(ctx):
     fhs = [ctx.field(x) for x in us]
     cells, frac = I.explicit_particles(base, 1500, seed=9, cols=(1, 4))
     st0 = O.release_explicit(us[0], cells, frac)
-    full = O.track(us[0], st0)
+    full = O.track(us[0], st0, arith="mirror")
     T = np.quantile(full["t"], [0.3, 0.6])
-    ref = O.track_periods(us, T, st0)
+    ref = O.track_periods(us, T, st0, arith="mirror")
     gh = mp.mp_release_group(ctx.h, fhs[0], cell=cells, local=frac)
     req = ctx.track_periods(gh, fhs, T, flags=mp.TRACK_UPDATE_GROUP, t_stop=float(T[1] * 1.2))
     req.wait()
-    a = O.track_periods(us, T, st0, t_stop=float(T[1] * 1.2))
+    a = O.track_periods(us, T, st0, t_stop=float(T[1] * 1.2), arith="mirror")
     G.compare_fp64(req.endpoints(), a, dmin=_dmin(us[0]))
     r2 = ctx.track(gh)
     r2.wait()
-    G.compare_fp64(r2.endpoints(), O.track(us[-1], O.resume_state(a)), dmin=_dmin(us[0]))
+    G.compare_fp64(r2.endpoints(), O.track(us[-1], O.resume_state(a), arith="mirror"), dmin=_dmin(us[0]))
     del ref
     for r in (req, r2):
         r.free()
@@ -127,7 +127,7 @@ def test_hand_over_moved_point_vs_oracle(ctx):
         rng = np.random.default_rng(21)
         frac = np.column_stack([rng.uniform(0.02, 0.3, 97), rng.uniform(0.02, 0.98, 97), rng.uniform(0.1, 0.9, 97)])
         cells = np.zeros(97, np.int32)
-        ref = O.track(u, O.release_explicit(u, cells, frac), pathline=True)
+        ref = O.track(u, O.release_explicit(u, cells, frac), pathline=True, arith="mirror")
         ep, _, st, path = _run(ctx, fh, cells, frac, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE, path_capacity=20 * 97)
         G.compare_fp64(ep, ref, dmin=_dmin(u))
         g, r = (np.sort(x, order=["particle", "seq"]) for x in (path, ref["path"]))
@@ -148,7 +148,7 @@ def test_quadtree_weak_sink_fraction_vs_oracle(ctx):
     cells, frac = U.explicit_particles(u, 2000, seed=6)
     st0 = O.release_explicit(u, cells, frac)
     for thr in [fs[0] / 2] + list((fs[:-1] + fs[1:]) / 2) + [(fs[-1] + 1) / 2]:
-        ref = O.track(u, st0, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True)
+        ref = O.track(u, st0, pass_weak_sinks=True, weak_sink_fraction=thr, pathline=True, arith="mirror")
         ep, _, st, path = _run(ctx, fh, cells, frac, flags=mp.TRACK_PASS_WEAK_SINKS, weak_sink_fraction=thr,
                                mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE, path_capacity=200 * cells.size)
         G.compare_fp64(ep, ref, dmin=_dmin(u))
@@ -206,7 +206,7 @@ def test_quadtree_larger_sampled(ctx):
     ep, st = req.endpoints(), req.stats()
     assert st["device_error"] == 0 and sum(st["n_status"]) == n
     idx = np.sort(np.random.default_rng(1).choice(n, 2000, replace=False))
-    ref = O.track(u, O.release_explicit(u, cells[idx], frac[idx]))
+    ref = O.track(u, O.release_explicit(u, cells[idx], frac[idx]), arith="mirror")
     G.compare_fp64(ep, ref, idx=idx, dmin=_dmin(u))
     print(f"quadtree {u.ncell} cells: {st['cell_steps']:.3e} cell-steps in {st['kernel_ms']:.2f} ms = "
           f"{st['cell_steps'] / st['kernel_ms'] * 1e3:.3e}/s")

@@ -15,6 +15,9 @@ import oracle as O
 from paper_2302_13590_gb300 import inputs as I
 from tests import helpers as H
 
+# every pin holds for both arithmetic modes of the oracle
+pytestmark = pytest.mark.usefixtures("oracle_arith")
+
 
 @pytest.fixture(scope="module")
 def fld():

@@ -18,9 +18,13 @@ import oracle as O
 from paper_2302_13590_gb300 import inputs as I
 from tests import helpers as H
 
+# every pin holds for both arithmetic modes of the oracle
+pytestmark = pytest.mark.usefixtures("oracle_arith")
 
-@pytest.fixture(scope="module")
-def base():
+
+@pytest.fixture
+def base(oracle_arith):
+    # per test: the reference run depends on the oracle's arithmetic mode
     f = I.random_box_field(2, 5, 8, seed=40, lnk_var=0.5, n_wells=1)
     cells, frac = I.explicit_particles(f, 120, seed=9, cols=(1, 3))
     st0 = O.release_explicit(f, cells, frac)

@@ -18,6 +18,12 @@ from paper_2302_13590_gb300 import inputs as I
 from paper_2302_13590_gb300.inputs import usg as U
 from tests import helpers as H
 
+# every pin holds for both arithmetic modes of the oracle
+pytestmark = pytest.mark.usefixtures("oracle_arith")
+
+
+_RK4_CACHE = {}
+
 
 @pytest.fixture(scope="module")
 def quad():
@@ -74,10 +80,14 @@ def test_quadtree_against_rk4(quad):
     path = np.sort(r["path"], order=["particle", "seq"])
     ext = max(u.extent)
     kinds = set()
+    if "quad" not in _RK4_CACHE:   # independent of the oracle's arithmetic mode: integrated once
+        runs = []
+        for q in range(cells.size):
+            tr = []
+            runs.append((H.rk4_track_usg(u, int(cells[q]), [st0["px"][q], st0["py"][q], st0["pz"][q]], trace=tr), tr))
+        _RK4_CACHE["quad"] = runs
     for q in range(cells.size):
-        c = int(cells[q])
-        tr = []
-        status, seq, _, p, t = H.rk4_track_usg(u, c, [st0["px"][q], st0["py"][q], st0["pz"][q]], trace=tr)
+        (status, seq, _, p, t), tr = _RK4_CACHE["quad"][q]
         assert status == r["status"][q], q
         assert H.fnv_hash(seq) == int(r["hash"][q]), q
         assert r["t"][q] == pytest.approx(t, rel=1e-7)

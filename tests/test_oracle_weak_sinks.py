@@ -14,10 +14,14 @@ Pins from outside the oracle:
   that never enter one are those of plain pass-through.
 """
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_2302_13590_gb300 import inputs as I
 from paper_2302_13590_gb300.inputs import usg as U
+
+# every pin holds for both arithmetic modes of the oracle
+pytestmark = pytest.mark.usefixtures("oracle_arith")
 
 
 def _fractions_structured(f):
