@@ -197,19 +197,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(w, seconds: float = 10.0, threads: int = 0):
-    """The oracle as it stands on the host cores: particles handed out in
-    chunks to `threads` threads until `seconds` have passed."""
+def cpu_baseline(w, seconds: float = 10.0, threads: int = 0, idx=None, keep: bool = False, repeats: int = 1):
+    """The oracle as it stands (its plain arithmetic, the reference) on the
+    host cores: particles handed out in chunks to `threads` threads (the
+    paper's dynamic schedule) until `seconds` have passed, in a random
+    order; or, with `idx`, exactly those particles, in full.  keep: also
+    return the oracle's endpoints of the tracked particles (idx order).
+    repeats: track the idx sample that many times over (a workload too small
+    to time once)."""
     import oracle as O
     threads = threads or os.cpu_count() or 1
     n = w.release.n
     state = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
     of = O.as_oracle_field(w.field)
-    perm = np.random.default_rng(0).permutation(n)
-    chunk = 512
+    if idx is None:
+        order = np.random.default_rng(0).permutation(n)
+    else:
+        order = np.tile(np.asarray(idx, dtype=np.int64), max(1, repeats))
+        seconds = float("inf")
+    chunk = 512 if order.size >= 64 * threads else max(1, order.size // (4 * threads))
     lock = threading.Lock()
     nxt = [0]
     done = {"steps": 0, "particles": 0}
+    parts = {}
     t_end = time.perf_counter() + seconds
 
     def worker():
@@ -217,13 +227,15 @@ def cpu_baseline(w, seconds: float = 10.0, threads: int = 0):
             with lock:
                 s = nxt[0]
                 nxt[0] += chunk
-            if s >= n:
+            if s >= order.size:
                 return
-            idx = perm[s:s + chunk]
-            r = O.track(of, O.subset(state, idx), times=w.times)
+            sel = order[s:s + chunk]
+            r = O.track(of, O.subset(state, sel), times=w.times)
             with lock:
                 done["steps"] += int(r["steps"].astype(np.int64).sum())
-                done["particles"] += idx.size
+                done["particles"] += sel.size
+                if keep:
+                    parts[s] = r
 
     t0 = time.perf_counter()
     ths = [threading.Thread(target=worker) for _ in range(threads)]
@@ -232,10 +244,42 @@ def cpu_baseline(w, seconds: float = 10.0, threads: int = 0):
     for t in ths:
         t.join()
     el = time.perf_counter() - t0
-    return {"value": done["steps"] / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{done['particles']} of the 1e6 particles (random subset), endpoint + 50 output times, "
-                      f"{el:.1f} s wall on {threads} host threads",
-            "particles_per_s": done["particles"] / el, "seconds": el}
+    what = ("random subset" if idx is None else
+            "a fixed random sample, every one tracked" if repeats <= 1 else
+            f"all {len(idx)} of them tracked {repeats} times over")
+    out = {"value": done["steps"] / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{done['particles']} of the {n:.0e} particles ({what}), endpoint + {len(w.times)} output "
+                     f"times, {el:.1f} s wall on {threads} host threads",
+           "particles_per_s": done["particles"] / el, "seconds": el}
+    if keep:
+        ks = sorted(parts)
+        out["endpoints"] = {k: np.concatenate([parts[s][k] for s in ks])
+                            for k in ("hash", "t", "gx", "gy", "gz", "cell", "status", "steps")}
+    return out
+
+
+def cpu_baselines(args, w2, w1, w3, idx3):
+    """The oracle timed on the host cores, 1 thread and all of them, on the
+    50x50x1 workload in full, the 200x200x20 workload (all cores: every
+    particle; 1 thread: a 3 s sample) and a 1e4-particle sample of the
+    400x400x40 workload.  Returns the report and the oracle's endpoints on
+    the last sample (used for the accuracy figures of that workload)."""
+    cpu = cpu_baseline(w2, seconds=args.cpu_seconds)
+    one = cpu_baseline(w2, seconds=min(args.cpu_seconds, 3.0), threads=1)
+    cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+    strip = lambda d: {k: v for k, v in d.items() if k not in ("endpoints", "unit", "kind")}
+    wl = {"cfg2_200x200x20": {"all_cores": strip(cpu), "one_thread": strip(one)}}
+    all1 = np.arange(w1.release.n)
+    wl["cfg1_50x50x1"] = {"all_cores": strip(cpu_baseline(w1, idx=all1, repeats=1000)),
+                          "one_thread": strip(cpu_baseline(w1, idx=all1, threads=1, repeats=100))}
+    ref3 = None
+    if w3 is not None:
+        a3 = cpu_baseline(w3, idx=idx3, keep=True)
+        ref3 = a3.pop("endpoints")
+        wl["cfg3_400x400x40_1e4_sample"] = {"all_cores": strip(a3),
+                                             "one_thread": strip(cpu_baseline(w3, idx=idx3, threads=1))}
+    cpu["workloads"] = wl
+    return cpu, ref3
 
 
 def run_reference(args):
@@ -296,6 +340,112 @@ def run_quadtree(ctx, stream) -> dict:
     mp.mp_group_free(ghq)
     mp.mp_field_free(fu)
     return quadtree
+
+
+CFG3_WORKLOAD = ("400x400x40 cells (5x5x1 m), lnK variance 4, exp. cov. 8 cells, porosity U(0.2, 0.35) per cell, "
+                 "20 seeded pumping wells (strong sinks), PCG head solve; 1e7 particles on a seeded plane x = x0; "
+                 "endpoint + timeseries at 100 log times (32 GB of records); autotuned persistent launch")
+
+
+def run_cfg3(ctx, stream, args):
+    """The strongly heterogeneous workload the mixed form is quoted on: both
+    precisions, each with its autotuned launch (tuned on a 2e6-particle
+    prefix), two timed launches after an untimed one.  Returns the report,
+    the workload, a 1e4-particle sample and the GPU endpoints on it."""
+    from paper_2302_13590_gb300 import inputs as I
+    from paper_2302_13590_gb300 import mp
+    tg = time.perf_counter()
+    w3 = I.workload("cfg3", n_particles=args.cfg3_particles or None)
+    gen_s = time.perf_counter() - tg
+    fh3 = ctx.field(w3.field)
+    n3 = w3.release.n
+    idx3 = np.sort(np.random.default_rng(4).choice(n3, min(10_000, n3), replace=False))
+    rep3 = {"workload": CFG3_WORKLOAD, "particles": n3, "output_times": len(w3.times),
+            "field_generation_s": gen_s, "field_bytes": mp.mp_field_bytes(fh3)}
+    eps = {}
+    mode = mp.MODE_ENDPOINT | mp.MODE_TIMESERIES
+    for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
+        gh = mp.mp_release_group(ctx.h, fh3, n=n3, lo=w3.release.lo, hi=w3.release.hi, seed=w3.release.seed,
+                                 stream=stream)
+        tuned = mp.mp_autotune(ctx.h, gh, mp.make_opts(mode=mode, precision=prec, times=w3.times),
+                               sample=min(n3, 2_000_000), stream=stream)
+        mp.mp_group_free(gh)
+        kms, steps = [], 0
+        for rep in range(3):
+            gh = mp.mp_release_group(ctx.h, fh3, n=n3, lo=w3.release.lo, hi=w3.release.hi, seed=w3.release.seed,
+                                     stream=stream)
+            r = ctx.track(gh, stream=stream, mode=mode, precision=prec, schedule=mp.SCHED_AUTO, times=w3.times)
+            st = r.stats()
+            assert st["device_error"] == 0
+            if rep > 0:
+                kms.append(st["kernel_ms"])
+                steps = st["cell_steps"]
+            if rep == 2:
+                ep = r.endpoints()
+                eps[name] = {k: ep[k][idx3] for k in ("hash", "t", "x", "y", "z", "cell", "status")}
+            r.free()
+            mp.mp_group_free(gh)
+        km = float(np.mean(kms))
+        rep3[name] = {"cell_steps_per_s": steps / (km / 1e3), "particles_per_s": n3 / (km / 1e3), "kernel_ms": km,
+                      "cell_steps": steps, "tuning": tuned}
+    mp.mp_field_free(fh3)
+    return rep3, w3, idx3, eps
+
+
+def accuracy(field, ep, ref) -> dict:
+    """GPU endpoints against the oracle's (both on the same particles):
+    share of diverging cell sequences; on the others, relative travel-time
+    error and endpoint error in cell widths (median, p99, max, share within
+    the mixed form's stated 1e-5 and 1e-4)."""
+    same = ep["hash"] == ref["hash"]
+    fin = same & np.isfinite(ref["t"]) & (ref["t"] > 0)
+    t_err = np.abs(ep["t"][fin] - ref["t"][fin]) / ref["t"][fin]
+    c = ref["cell"][fin]
+    j, i, k = c % field.ncol, (c // field.ncol) % field.nrow, c // (field.ncol * field.nrow)
+    pos = np.maximum(np.abs(ep["x"][fin] - ref["gx"][fin]) / field.delr[j],
+                     np.maximum(np.abs(ep["y"][fin] - ref["gy"][fin]) / field.delc[i],
+                                np.abs(ep["z"][fin] - ref["gz"][fin]) / field.dz[k]))
+    q = lambda a, v: float(np.quantile(a, v)) if a.size else 0.0
+    return {"particles": int(same.size), "divergent_fraction": float(1.0 - same.mean()),
+            "t_rel_err": {"median": q(t_err, 0.5), "p99": q(t_err, 0.99), "max": q(t_err, 1.0),
+                          "within_1e-5": float(np.mean(t_err <= 1e-5)) if t_err.size else 1.0},
+            "pos_err_cells": {"median": q(pos, 0.5), "p99": q(pos, 0.99), "max": q(pos, 1.0),
+                              "within_1e-4": float(np.mean(pos <= 1e-4)) if pos.size else 1.0},
+            "reference": "oracle, plain arithmetic (C library log1p/expm1, FP64)"}
+
+
+def summary(line) -> dict:
+    """The figures a reader needs first, last on the line (so a truncated
+    log keeps them): both precisions on both heterogeneous workloads, their
+    roofline fractions, batch and serving."""
+    g = lambda d, *ks: (None if d is None else (g(d.get(ks[0]), *ks[1:]) if ks else d))
+    r3 = lambda v: None if v is None else float(f"{v:.3g}")
+    out = {"fp64_cfg2": r3(line["value"]), "fp64_cfg2_frac_alu": r3(g(line, "roofline", "frac")),
+           "mixed_cfg2": r3(g(line, "mixed", "value")),
+           "mixed_cfg2_frac_hbm": r3(g(line, "mixed", "roofline", "frac")),
+           "mixed_cfg2_frac_l2": r3(g(line, "mixed", "roofline", "l2_view", "frac")),
+           "e2e_fp64": r3(g(line, "e2e", "value")), "e2e_mixed": r3(g(line, "e2e", "mixed"))}
+    c3 = line.get("cfg3")
+    if c3:
+        for nm in ("mixed", "fp64"):
+            out[f"{nm}_cfg3"] = r3(g(c3, nm, "cell_steps_per_s"))
+            out[f"{nm}_cfg3_particles_per_s"] = r3(g(c3, nm, "particles_per_s"))
+            out[f"{nm}_cfg3_frac"] = r3(g(c3, nm, "roofline", "frac"))
+            acc = g(c3, nm, "accuracy")
+            if acc:
+                out[f"{nm}_cfg3_divergent"] = r3(acc["divergent_fraction"])
+                out[f"{nm}_cfg3_t_err_p99"] = r3(acc["t_rel_err"]["p99"])
+    b = line.get("batch")
+    if b:
+        out["batch_mixed"] = r3(g(b, "mixed", "cell_steps_per_s"))
+        out["batch_fp64"] = r3(g(b, "fp64", "cell_steps_per_s"))
+    sv = line.get("serving")
+    if sv:
+        for nm in ("mixed", "fp64"):
+            out[f"serve_{nm}_p50_p99_ms"] = [r3(g(sv, nm, "p50_ms")), r3(g(sv, nm, "p99_ms"))]
+            out[f"serve_{nm}_requests"] = g(sv, nm, "requests")
+            out[f"serve_{nm}_particles_per_s"] = r3(g(sv, nm, "particles_per_s"))
+    return out
 
 
 def run_ours(args):
@@ -530,14 +680,30 @@ def run_ours(args):
     if not args.no_batch:
         specs = I.batch_workload()
         batch = {"workload": "256 requests on the 200x200x20 field, sizes log-uniform in 1e2..1e6 (3.0e7 particles), "
-                             "random boxes, half with 20 output times; one launch per precision"}
+                             "random boxes, half with 20 output times; one launch per precision, autotuned"}
+        # autotune the batch's launch per precision and mode on its largest
+        # request (the launch takes the tuned configuration of its first
+        # request of that precision)
+        big = max(specs, key=lambda x: x.release.n)
+        ts_times = next(x.times for x in specs if x.timeseries)
+        batch_tuning = {}
+        for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
+            for tsm in (False, True):
+                gh = mp.mp_release_group(ctx.h, fh, n=big.release.n, lo=big.release.lo, hi=big.release.hi,
+                                         seed=big.release.seed, stream=stream)
+                o = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if tsm else 0), precision=prec,
+                                 times=ts_times if tsm else None)
+                batch_tuning[f"{name}_{'timeseries' if tsm else 'endpoint'}"] = mp.mp_autotune(ctx.h, gh, o, sample=0,
+                                                                                             stream=stream)
+                mp.mp_group_free(gh)
+        batch["tuning"] = batch_tuning
         for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
             best = None
             for rep in range(2):
                 groups = [mp.mp_release_group(ctx.h, fh, n=x.release.n, lo=x.release.lo, hi=x.release.hi,
                                               seed=x.release.seed, stream=stream) for x in specs]
                 opts = [mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
-                                     precision=prec, schedule=mp.SCHED_DYNAMIC, times=x.times) for x in specs]
+                                     precision=prec, schedule=mp.SCHED_AUTO, times=x.times) for x in specs]
                 ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
                 sts = [mp.mp_get_stats(ctx.h, i) for i in ids]
                 steps_b = sum(x["cell_steps"] for x in sts)
@@ -613,7 +779,7 @@ def run_ours(args):
         fields = {"cfg1": ctx.field(I.cfg1_field()), "cfg2": fh}
         serving = {}
         for name, prec, nreq in (("mixed", mp.PREC_MIXED, args.serve_requests),
-                                 ("fp64", mp.PREC_FP64, max(1, args.serve_requests // 5))):
+                                 ("fp64", mp.PREC_FP64, args.serve_requests)):
             specs = I.serving_workload(n_req=nreq, rate_hz=200.0)
             srv = SV.Server(ctx, fields, precision=prec, schedule=mp.SCHED_STATIC)
             rep = srv.run(specs, realtime=True)
@@ -623,10 +789,30 @@ def run_ours(args):
             serving[name] = sm
         serving["workload"] = ("Poisson arrivals at 200 requests/s on the 50x50x1 and 200x200x20 fields (p = 1/2), "
                                "group sizes log-uniform in 1e3..1e6, endpoint or 20-time timeseries at random")
-    cpu = None if args.no_cpu_baseline else cpu_baseline(w, seconds=args.cpu_seconds)
-    if cpu is not None:
-        one = cpu_baseline(w, seconds=min(args.cpu_seconds, 3.0), threads=1)
-        cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+    cfg3 = w3 = idx3 = eps3 = None
+    if not args.no_cfg3:
+        cfg3, w3, idx3, eps3 = run_cfg3(ctx, stream, args)
+        for name in ("mixed", "fp64"):
+            rate = cfg3[name]["cell_steps_per_s"]
+            gbs = BYTES_PER_STEP[name] * rate / 1e9
+            if name == "fp64":
+                a = FP64_FLOPS_PER_STEP * rate / 1e12
+                cfg3[name]["roofline"] = {"bound": "alu", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
+                                          "frac": a / fp64_peak, "peak_source": fp64_src,
+                                          "hbm_view": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm}}
+            else:
+                cfg3[name]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                          "frac": gbs / hbm, "bytes_per_cell_step": BYTES_PER_STEP[name],
+                                          "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                                          "l2_view": {"achieved": gbs, "peak": l2, "frac": gbs / l2}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu, ref3 = cpu_baselines(args, w, I.workload("cfg1"), w3, idx3)
+        if ref3 is not None:
+            # the oracle's endpoints of the timed sample against the GPU's on
+            # the same particles (numpy only)
+            for name in ("mixed", "fp64"):
+                cfg3[name]["accuracy"] = accuracy(w3.field, eps3[name], ref3)
     f64 = results["fp64"]
     line = {
         "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -648,8 +834,10 @@ def run_ours(args):
         "serving": serving,
         "batch": batch,
         "quadtree": quadtree,
+        "cfg3": cfg3,
         "tuning": tuning or None,
     }
+    line["summary"] = summary(line)
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -676,7 +864,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-quadtree", action="store_true")
     ap.add_argument("--only-quadtree", action="store_true", help="run the quadtree line alone (profiling)")
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=5000)
+    ap.add_argument("--no-cfg3", action="store_true")
+    ap.add_argument("--cfg3-particles", type=int, default=0, help="override cfg3's 1e7 particles (quick checks)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--traffic-fp64", type=float, default=None,
