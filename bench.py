@@ -87,7 +87,7 @@ L2_READ_PER_STEP = {"src": "753189249556e18e", "fp64": 248577327.0 * 32 / 5.483e
 # Sources of the device code the counters above were taken from: the kernel
 # units and every header they include (the host side of the C ABI,
 # mp_api.cu and mp_noalloc.cu, compiles no tracking kernel).
-KERNEL_SOURCES = ("mp_fp64.cu", "mp_mixed.cu", "mp_usg.cu")
+KERNEL_SOURCES = ("mp_fp64.cu", "mp_mixed.cu", "mp_mixed_f64t.cu", "mp_usg.cu")
 
 
 def kernel_src_hash() -> str:
@@ -422,6 +422,7 @@ def summary(line) -> dict:
     r3 = lambda v: None if v is None else float(f"{v:.3g}")
     out = {"fp64_cfg2": r3(line["value"]), "fp64_cfg2_frac_alu": r3(g(line, "roofline", "frac")),
            "mixed_cfg2": r3(g(line, "mixed", "value")),
+           "mixed_f64t_cfg2": r3(g(line, "mixed", "f64t_form", "cell_steps_per_s")),
            "mixed_cfg2_frac_hbm": r3(g(line, "mixed", "roofline", "frac")),
            "mixed_cfg2_frac_l2": r3(g(line, "mixed", "roofline", "l2_view", "frac")),
            "e2e_fp64": r3(g(line, "e2e", "value")), "e2e_mixed": r3(g(line, "e2e", "mixed"))}
@@ -445,6 +446,7 @@ def summary(line) -> dict:
             out[f"serve_{nm}_p50_p99_ms"] = [r3(g(sv, nm, "p50_ms")), r3(g(sv, nm, "p99_ms"))]
             out[f"serve_{nm}_requests"] = g(sv, nm, "requests")
             out[f"serve_{nm}_particles_per_s"] = r3(g(sv, nm, "particles_per_s"))
+            out[f"serve_{nm}_max_concurrent_batches"] = g(sv, nm, "max_concurrent_batches")
     return out
 
 
@@ -561,6 +563,25 @@ def run_ours(args):
         steps_all, ms_max, value = replicas.job_rate(r["cell_steps"], r["ms"], world, dev)
         results[name] = dict(r, ms_max=ms_max, cell_steps_all=steps_all, value=value,
                              particles_per_s=summed(n * args.steps) / (ms_max / 1e3))
+
+    # the mixed form with FP64 kept for the cumulative time and the near-zero
+    # branch of the exit time (MP_PREC_MIXED_F64T), same workload: what those
+    # two FP64 pieces cost on this GPU
+    f64t = None
+    if "mixed" in args.precisions and not args.particles:
+        gh = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset,
+                                 stream=stream)
+        kms = []
+        for rep in range(3):
+            r = ctx.track(gh, stream=stream, mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES,
+                          precision=mp.PREC_MIXED_F64T, schedule=mp.SCHED_DYNAMIC, times=w.times)
+            st = r.stats()
+            if rep > 0:
+                kms.append(st["kernel_ms"])
+            r.free()
+        mp.mp_group_free(gh)
+        f64t = {"cell_steps_per_s": st["cell_steps"] / (np.mean(kms) / 1e3), "kernel_ms": float(np.mean(kms)),
+                "what": "FP64 cumulative time and FP64 log1p(z)/z near z = 0; dynamic schedule, 128 threads"}
 
     # end to end through the C ABI with host buffers (mp_track_host): pinned host release
     # arrays in, endpoint and timeseries records out, every step
@@ -829,7 +850,7 @@ def run_ours(args):
         "clocks": f64["clocks"],
         "mixed": {"value": results["mixed"]["value"], "ms_per_step": results["mixed"]["ms_max"] / args.steps,
                   "particles_per_s": results["mixed"]["particles_per_s"], "dtype": "f32+f64",
-                  "roofline": rf["mixed"], "clocks": results["mixed"]["clocks"]},
+                  "roofline": rf["mixed"], "clocks": results["mixed"]["clocks"], "f64t_form": f64t},
         "status_counts": f64["status_counts"],
         "serving": serving,
         "batch": batch,

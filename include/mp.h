@@ -73,7 +73,15 @@ extern "C" {
 
 #define MP_PREC_FP64 0          /* IEEE double throughout                     */
 #define MP_PREC_MIXED 1         /* FP32 in-cell coordinates and velocities,
-                                   FP64 travel time and global position      */
+                                   travel time as an FP32 pair (~48 bits),
+                                   FP64 output times and global positions    */
+#define MP_PREC_MIXED_F64T 2    /* as MP_PREC_MIXED, with FP64 kept for the
+                                   cumulative travel time and for the
+                                   near-zero branch of the exit time
+                                   (log1p(z)/z in FP64): the accuracy
+                                   reference of the FP32 pair and series;
+                                   rectilinear grids, not in graphs or
+                                   mp_track_noalloc                          */
 
 #define MP_MODE_ENDPOINT 1      /* bit: endpoint record per particle          */
 #define MP_MODE_TIMESERIES 2    /* bit: a record per output time per particle */
@@ -221,6 +229,12 @@ typedef struct {
     int32_t device_error;            /* kernel error flag (0 = none)     */
     uint64_t path_points;            /* pathline points produced (also beyond
                                         the capacity: rerun with more room)  */
+    uint64_t t_begin_ns, t_end_ns;   /* the tracking launch's window on the
+                                        device's global timer (ns): earliest
+                                        block start, latest block end (a
+                                        batch's requests share their launch's;
+                                        over all launches of mp_track_periods);
+                                        0 when nothing was launched          */
 } mp_stats;
 
 /* Context on one CUDA device.  The device is made current on the calling
@@ -561,7 +575,7 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
  * timeseries mode, the [n_times][n] record buffer (device).  times stays a
  * host array.  The call allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.  Its only other device memory is a fixed
- * file-scope array of 8 + 11 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words plus
+ * file-scope array of 8 + 13 + 2 * MP_NOALLOC_MAX_TIMES 64-bit words plus
  * the launch's request descriptor (queue head, counters, the output times in
  * FP64 and as FP32 pairs; about 66 KB) that every GPU that loads the library
  * holds until the process exits.

@@ -67,7 +67,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("n_times", ctypes.c_int32),
                 ("times", ctypes.c_void_p), ("max_steps", ctypes.c_int64), ("pass_weak_sinks", ctypes.c_int32),
                 ("path_start", ctypes.c_int32), ("weak_sink_fraction", ctypes.c_double),
-                ("arith", ctypes.c_int32)]
+                ("arith", ctypes.c_int32), ("jitter", ctypes.c_double), ("jitter_seed", ctypes.c_uint64),
+                ("jitter_id0", ctypes.c_int64)]
 
 
 ARITH = {"plain": 0, "mirror": 1}
@@ -272,7 +273,8 @@ def subset(state, idx):
 
 
 def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pass_weak_sinks=False,
-          pathline=False, path_start=True, weak_sink_fraction=0.0, arith=None, trace=False):
+          pathline=False, path_start=True, weak_sink_fraction=0.0, arith=None, trace=False, jitter=0.0,
+          jitter_seed=0, jitter_id0=0):
     """Track every particle of ``state`` (dict of cell, px, py, pz, t, status,
     and optionally steps, hash and exit_face carried by a resumed particle).
 
@@ -284,7 +286,9 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
     point every cell-step ends at.  ``arith`` selects the arithmetic mode
     ("plain", the reference, or "mirror"; None: ``DEFAULT_ARITH``).  With ``trace``, ``trace`` holds
     one TRACE_RECORD per cell-step (exit times, faces and particle velocity
-    per axis, the axis taken).
+    per axis, the axis taken).  ``jitter`` > 0 perturbs every crossing by
+    about that relative amount (a test instrument, mp_oracle.h), seeded by
+    ``jitter_seed`` and the particle's index in ``state``.
     """
     lib = _load()
     of = as_oracle_field(f)
@@ -312,7 +316,8 @@ def track(f, state, t_stop=np.inf, times=None, max_steps=0, timeseries=None, pas
         res["ts_cell"] = np.zeros((nt, n), np.int32)
         res["ts_status"] = np.zeros((nt, n), np.uint8)
     opts = _Opts(float(t_stop), nt, _ptr(tarr), int(max_steps), int(bool(pass_weak_sinks)), int(bool(path_start)),
-                 float(weak_sink_fraction), _arith(arith))
+                 float(weak_sink_fraction), _arith(arith), float(jitter), int(jitter_seed) & (2**64 - 1),
+                 int(jitter_id0))
     cap = 64 * n + 16
     tcap = 64 * n + 16
     while True:
@@ -352,7 +357,7 @@ def resume_state(out):
 
 
 def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, pass_weak_sinks=False,
-                  pathline=False, weak_sink_fraction=0.0, arith=None):
+                  pathline=False, weak_sink_fraction=0.0, arith=None, jitter=0.0, jitter_seed=0):
     """Piecewise-steady flow (Methods, "MODPATH": the outer loop runs over the
     flow model's time steps and updates the flow arrays at each step's end).
 
@@ -388,7 +393,8 @@ def track_periods(fields, t_end, state, t_stop=np.inf, times=None, max_steps=0, 
         wt = None if window is None or window.size == 0 else tarr[window]
         moved = (cur["status"] == ST_ACTIVE) | (p == 0)
         out = track(f, cur, t_stop=tp, times=wt, max_steps=max_steps, pass_weak_sinks=pass_weak_sinks,
-                    pathline=pathline, path_start=p == 0, weak_sink_fraction=weak_sink_fraction, arith=arith)
+                    pathline=pathline, path_start=p == 0, weak_sink_fraction=weak_sink_fraction, arith=arith,
+                    jitter=jitter, jitter_seed=jitter_seed + p)
         if pathline:
             paths.append(out.pop("path"))
         if res is None:
@@ -435,7 +441,8 @@ def track_parallel(f, state, threads: int, chunk: int = 256, **kw):
             if s >= n:
                 return
             idx = slice(s, min(n, s + chunk))
-            parts[s] = track(of, {k: v[idx] for k, v in state.items()}, **kw)
+            ckw = dict(kw, jitter_id0=kw.get("jitter_id0", 0) + s) if kw.get("jitter") else kw
+            parts[s] = track(of, {k: v[idx] for k, v in state.items()}, **ckw)
 
     ths = [threading.Thread(target=worker) for _ in range(max(1, threads))]
     for t in ths:

@@ -450,6 +450,24 @@ int orc_release_explicit(const orc_field* f, int64_t n, const int32_t* cell_in, 
     return 0;
 }
 
+/* ---- jitter (test instrument) ------------------------------------------- */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) finaliser of a counter */
+static uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9e3779b97f4a7c15ULL;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    return x ^ (x >> 31);
+}
+
+/* uniform in [-1, 1) for (seed, particle, step, slot) */
+static double jitter_u(uint64_t seed, int64_t q, int64_t step, int slot)
+{
+    uint64_t h = splitmix64(seed ^ splitmix64((uint64_t)q ^ splitmix64(((uint64_t)step << 3) | (uint64_t)slot)));
+    return (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
 /* ---- tracking ------------------------------------------------------------ */
 
 static void write_record(const orc_track_out* o, int64_t n, int kk, int64_t q,
@@ -757,7 +775,8 @@ static int track_core(const orc_grid* g, int64_t n,
             }
             /* displacement to the exit face of axis ax */
             double dt = tmin;
-            double t_end = t + dt;
+            double t_end = t + (opt->jitter > 0.0 ? dt * (1.0 + opt->jitter * jitter_u(opt->jitter_seed, opt->jitter_id0 + q, steps, 0))
+                                                   : dt);
             while (kn < nt && opt->times[kn] <= t_end) {
                 double tau = opt->times[kn] - t;
                 double g0 = o[0] + mv(opt, &cv, 0, p[0], tau);
@@ -798,6 +817,13 @@ static int track_core(const orc_grid* g, int64_t n,
                 p[a] = pa;
             }
             p[ax] = (side > 0) ? 0.0 : Dn[ax];
+            if (opt->jitter > 0.0) {
+                for (int a = 0; a < 3; a++) {
+                    if (a == ax) continue;
+                    double pa = p[a] + opt->jitter * jitter_u(opt->jitter_seed, opt->jitter_id0 + q, steps, 1 + a) * Dn[a];
+                    p[a] = pa < 0.0 ? 0.0 : (pa > Dn[a] ? Dn[a] : pa);
+                }
+            }
             c = nc;
             for (int a = 0; a < 3; a++) { o[a] = on[a]; D[a] = Dn[a]; }
             h = fnv_step(h, c);

@@ -48,7 +48,20 @@ typedef struct {
                                   extracts at least this fraction of its
                                   inflow still stops particles */
     int32_t arith;        /* ORC_ARITH_PLAIN (0, the reference) or ORC_ARITH_MIRROR */
+    double jitter;        /* > 0: perturb every crossing (tests only, see below) */
+    uint64_t jitter_seed;
+    int64_t jitter_id0;   /* particle q draws as particle jitter_id0 + q */
 } orc_track_opts;
+
+/* Jitter (a test instrument, not part of the method): with jitter = e > 0
+ * every completed cell-step's time is multiplied by (1 + e u1) and, after
+ * the hand-over, every transverse offset moves by e u2 D (clamped to the
+ * cell), u1, u2 uniform in [-1, 1) from a counter-based generator (SplitMix64
+ * of the seed, the particle's index plus jitter_id0, the step count and the
+ * axis).  Runs with
+ * e of the order of one FP32 rounding show how far a particle's result moves
+ * under perturbations of that size at every step: the spread a
+ * reduced-precision evaluation is measured against. */
 
 /* Arithmetic of the in-cell solution.
  * PLAIN (the reference): the method's formulas written out as they read,

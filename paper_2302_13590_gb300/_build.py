@@ -6,6 +6,7 @@ Translation units, compiled in parallel:
                contraction, so FP64 results round exactly as written)
   mp_usg.cu    FP64 tracking on rectangular unstructured grids (-fmad=false)
   mp_mixed.cu  mixed-precision tracking (contraction allowed)
+  mp_mixed_f64t.cu  the same with FP64 travel time and near-zero branch
   mp_noalloc.cu  the entry point that allocates no device memory
 """
 from __future__ import annotations
@@ -27,6 +28,7 @@ UNITS = {
     "mp_fp64.cu": ["-fmad=false"],
     "mp_usg.cu": ["-fmad=false"],
     "mp_mixed.cu": [],
+    "mp_mixed_f64t.cu": [],
     "mp_noalloc.cu": [],
 }
 

@@ -736,7 +736,7 @@ int prepare_request(mp_ctx* ctx, mp_group* g, const mp_track_opts* o, cudaStream
     if (g->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_track: group belongs to another context");
     if ((o->mode & (MP_MODE_ENDPOINT | MP_MODE_TIMESERIES | MP_MODE_PATHLINE)) == 0 || (o->mode & ~7))
         return fail(MP_ERR_INVALID_ARG, "mp_track: mode must be a non-empty set of MP_MODE_* bits");
-    if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED)
+    if (o->precision != MP_PREC_FP64 && o->precision != MP_PREC_MIXED && o->precision != MP_PREC_MIXED_F64T)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unknown precision");
     if (g->field->usg && o->precision != MP_PREC_FP64)
         return fail(MP_ERR_INVALID_ARG, "mp_track: unstructured grids are tracked in FP64");
@@ -891,8 +891,10 @@ int launch_requests(const mp_field* f, Request** rs, const mp::Req* hreqs, int n
     if (e == cudaSuccess) {
         const mp::DevField& fd = *mp::field_device_view(f);
         if (f->usg) e = launch_track_usg(f->u, b, modes, schedule, blk, 0, s);
-        else e = (precision == MP_PREC_FP64) ? launch_track_fp64(fd, b, modes, schedule, blk, 0, s)
-                                             : launch_track_mixed(fd, b, modes, schedule, blk, 0, s);
+        else e = (precision == MP_PREC_FP64)    ? launch_track_fp64(fd, b, modes, schedule, blk, 0, s)
+                 : (precision == MP_PREC_MIXED) ? launch_track_mixed(fd, b, modes, schedule, blk, 0, s)
+                                                : launch_track_mixed_f64t(fd, b, modes, schedule, blk, 0, s);
+        if (e == cudaSuccess) e = mp::launch_spread_window(b, s);
     }
     for (int i = 0; i < n && e == cudaSuccess && (ev & 2u); ++i) e = cudaEventRecord(rs[i]->k1, s);
     cudaFreeAsync(tbl, s);
@@ -985,7 +987,7 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
         ts[i] = (char)md;
     }
     // one launch per precision; launch options of the first request of each
-    for (int prec = 0; prec < 2; ++prec) {
+    for (int prec = 0; prec < 3; ++prec) {
         std::vector<Request*> sel;
         std::vector<mp::Req> sreq;
         unsigned any_modes = 0;
@@ -1252,6 +1254,8 @@ int mp_get_stats(mp_ctx* ctx, mp_req id, mp_stats* out)
     st.kernel_ms = ms;
     st.device_error = h[COUNTER_ERR] ? 1 : 0;
     st.path_points = h[COUNTER_PATH];
+    st.t_begin_ns = h[COUNTER_T_BEGIN] ? ~h[COUNTER_T_BEGIN] : 0ULL;
+    st.t_end_ns = h[COUNTER_T_END];
     *out = st;
     return MP_OK;
 }
@@ -1381,6 +1385,8 @@ int mp_track_host(mp_ctx* ctx, const mp_field* f, int64_t n, const int32_t* cell
         sum.cell_steps += one.cell_steps;
         for (int k = 0; k < MP_N_STATUS; ++k) sum.n_status[k] += one.n_status[k];
         sum.device_error |= one.device_error;
+        if (one.t_begin_ns && (!sum.t_begin_ns || one.t_begin_ns < sum.t_begin_ns)) sum.t_begin_ns = one.t_begin_ns;
+        if (one.t_end_ns > sum.t_end_ns) sum.t_end_ns = one.t_end_ns;
     }
     if (rc == MP_OK && sum.device_error) rc = fail(MP_ERR_DEVICE, "mp_track_host: tracking kernel raised its error flag");
     if (ev_start && ev_end && rc == MP_OK) {
@@ -1530,6 +1536,8 @@ int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release
         if (rc != MP_OK) return rc;
         if (opts[i].flags & MP_TRACK_UPDATE_GROUP)
             return fail(MP_ERR_INVALID_ARG, "mp_graph_create: a replayed release makes MP_TRACK_UPDATE_GROUP moot");
+        if (opts[i].precision != MP_PREC_FP64 && opts[i].precision != MP_PREC_MIXED)
+            return fail(MP_ERR_INVALID_ARG, "mp_graph_create: precision must be MP_PREC_FP64 or MP_PREC_MIXED");
     }
     MP_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1643,6 +1651,7 @@ int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release
         bat[p].steps_per_fetch = spf > 0 ? spf : 4;
         e = prec == MP_PREC_FP64 ? mp::launch_track_fp64(fd, bat[p], modes[p], sched, blk > 0 ? blk : 128, 0, cs)
                                  : mp::launch_track_mixed(fd, bat[p], modes[p], sched, blk > 0 ? blk : 128, 0, cs);
+        if (e == cudaSuccess) e = mp::launch_spread_window(bat[p], cs);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

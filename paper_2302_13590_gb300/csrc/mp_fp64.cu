@@ -690,6 +690,25 @@ struct F64Engine {
     }
 };
 
+// The tracking kernels keep a launch's device-time window in its first
+// request's counters; a batch's other requests get a copy.
+__global__ void k_spread_window(const Req* reqs, int n)
+{
+    const unsigned long long* src = reqs[0].o.counters + COUNTER_T_BEGIN;
+    const unsigned long long t0 = src[0], t1 = src[1];
+    for (int i = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x); i < n; i += (int)(gridDim.x * blockDim.x)) {
+        reqs[i].o.counters[COUNTER_T_BEGIN] = t0;
+        reqs[i].o.counters[COUNTER_T_END] = t1;
+    }
+}
+
+cudaError_t launch_spread_window(const Batch& b, cudaStream_t s)
+{
+    if (b.n_reqs <= 1 || b.n_total <= 0) return cudaSuccess;
+    k_spread_window<<<1, 256, 0, s>>>(b.reqs, b.n_reqs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_track_fp64(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                               int blocks_per_sm_cap, cudaStream_t s)
 {

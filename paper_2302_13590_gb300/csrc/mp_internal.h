@@ -102,13 +102,18 @@ struct DevState {
 enum : int { ST_SKIP = 0xFF };
 
 // counters[0] = cell-steps, [1 + s] = particles with final status s,
-// [COUNTER_ERR] = device error flag (index of the first bad access + 1)
+// [COUNTER_ERR] = device error flag (index of the first bad access + 1),
+// [COUNTER_T_BEGIN] / [COUNTER_T_END] = the launch's device-time window:
+// the complement of the global timer (ns) at the earliest block start and
+// the timer at the latest block end (both kept with atomicMax from zero)
 enum : int {
     COUNTER_STEPS = 0,
     COUNTER_STATUS = 1,
     COUNTER_ERR = 1 + MP_N_STATUS,
     COUNTER_PATH = 2 + MP_N_STATUS,   // pathline points appended (the append cursor)
-    N_COUNTERS = 3 + MP_N_STATUS
+    COUNTER_T_BEGIN = 3 + MP_N_STATUS,
+    COUNTER_T_END = 4 + MP_N_STATUS,
+    N_COUNTERS = 5 + MP_N_STATUS
 };
 
 // launch modes: which outputs the kernel variant writes besides endpoints
@@ -253,6 +258,10 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 cudaError_t launch_track_fp64(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                               int blocks_per_sm_cap, cudaStream_t s);
 cudaError_t launch_track_mixed(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
+                               int blocks_per_sm_cap, cudaStream_t s);
+// copy the first request's launch window into the other requests of a batch
+cudaError_t launch_spread_window(const Batch& b, cudaStream_t s);
+cudaError_t launch_track_mixed_f64t(const DevField& f, const Batch& b, unsigned modes, int schedule, int block,
                                int blocks_per_sm_cap, cudaStream_t s);
 
 // Host helpers shared by the entry points: the calling thread's error

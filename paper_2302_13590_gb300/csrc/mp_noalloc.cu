@@ -167,6 +167,8 @@ int track_noalloc(const mp_field* f, const mp_noalloc_args* a, cudaStream_t s, m
         mp_stats out{};
         out.cell_steps = h[COUNTER_STEPS];
         for (int k = 0; k < MP_N_STATUS; ++k) out.n_status[k] = h[COUNTER_STATUS + k];
+        out.t_begin_ns = h[COUNTER_T_BEGIN] ? ~h[COUNTER_T_BEGIN] : 0ULL;
+        out.t_end_ns = h[COUNTER_T_END];
         out.kernel_ms = 0.0f;
         out.device_error = h[COUNTER_ERR] ? 1 : 0;
         *stats = out;

@@ -68,6 +68,25 @@ __device__ __forceinline__ bool paused(const E& e, const S& s)
     return (s.st == MP_ST_TIME || s.st == MP_ST_STEP_CAP) && !e.b.reqs[s.r].p.last;
 }
 
+// The launch's device-time window (global timer, ns), kept in the first
+// request's counters: earliest block start, latest block end.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void window_begin(const Batch& b)
+{
+    if (threadIdx.x == 0) atomicMax(b.reqs[0].o.counters + COUNTER_T_BEGIN, ~global_ns());
+}
+
+__device__ __forceinline__ void window_end(const Batch& b)
+{
+    if (threadIdx.x == 0) atomicMax(b.reqs[0].o.counters + COUNTER_T_END, global_ns());
+}
+
 // request of global particle index g (starts ascending, starts[0] = 0)
 __device__ __forceinline__ int request_of(const Batch& b, long long g)
 {
@@ -260,6 +279,7 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
     __shared__ unsigned long long s_cnt[N_COUNTERS];
     typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
+    window_begin(e.b);
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
@@ -299,6 +319,7 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
     if (TS) rq_drain(e, Q, qcount, true);
     if (PL) pl_flush(e, P, pcount);
     flush_counters(e, s_cnt);
+    window_end(e.b);
 }
 
 template <class E, bool TS, bool PL>
@@ -307,6 +328,7 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     __shared__ unsigned long long s_cnt[N_COUNTERS];
     typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);
     for (int i = threadIdx.x; i < N_COUNTERS; i += blockDim.x) s_cnt[i] = 0ULL;
+    window_begin(e.b);
     __syncthreads();
     typename E::RecQ& Q = s_q[TS ? (threadIdx.x >> 5) : 0];
     PathQ* s_p = reinterpret_cast<PathQ*>(s_dyn + (TS ? sizeof(typename E::RecQ) * (blockDim.x >> 5) : 0));
@@ -368,6 +390,7 @@ __global__ void __launch_bounds__(256) k_track_dynamic(E e)
     if (TS) rq_drain(e, Q, qcount, true);
     if (PL) pl_flush(e, P, pcount);
     flush_counters(e, s_cnt);
+    window_end(e.b);
 }
 
 // One variant of the tracking kernel: opt in to more than 48 KB of dynamic

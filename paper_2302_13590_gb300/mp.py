@@ -34,7 +34,7 @@ ST_ACTIVE, ST_TIME, ST_SINK, ST_BOUNDARY, ST_EXIT_DOMAIN, ST_NO_EXIT, ST_STEP_CA
 STATUS_NAMES = ["ACTIVE", "TIME", "SINK", "BOUNDARY", "EXIT_DOMAIN", "NO_EXIT", "STEP_CAP", "INVALID_RELEASE"]
 FACE_NONE = 255
 MP_DEVICE_PTR = 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_F64T = 0, 1, 2
 MODE_ENDPOINT, MODE_TIMESERIES, MODE_PATHLINE = 1, 2, 4
 SCHED_STATIC, SCHED_DYNAMIC, SCHED_AUTO = 0, 1, 2
 TRACK_UPDATE_GROUP = 1
@@ -103,7 +103,8 @@ class Tuning(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("cell_steps", ctypes.c_uint64), ("n_status", ctypes.c_uint64 * 8),
-                ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32), ("path_points", ctypes.c_uint64)]
+                ("kernel_ms", ctypes.c_float), ("device_error", ctypes.c_int32), ("path_points", ctypes.c_uint64),
+                ("t_begin_ns", ctypes.c_uint64), ("t_end_ns", ctypes.c_uint64)]
 
 
 ENDPOINT_DTYPES = {"cell": np.int32, "x": np.float64, "y": np.float64, "z": np.float64, "px": np.float64,
@@ -433,7 +434,7 @@ def mp_get_stats(ctx, req: int) -> dict:
     _check(load_library().mp_get_stats(ctx, int(req), ctypes.byref(s)))
     return {"cell_steps": int(s.cell_steps), "n_status": [int(v) for v in s.n_status],
             "kernel_ms": float(s.kernel_ms), "device_error": int(s.device_error),
-            "path_points": int(s.path_points)}
+            "path_points": int(s.path_points), "t_begin_ns": int(s.t_begin_ns), "t_end_ns": int(s.t_end_ns)}
 
 
 def mp_track_host(ctx, fh, cell, local, opts: "TrackOpts", t0=None, n_chunks: int = 0, out=None, ts_out=None):

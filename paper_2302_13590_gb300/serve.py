@@ -47,6 +47,8 @@ class Served:
     bytes: int = 0
     cell_steps: int = 0
     result: Optional[dict] = None
+    batch: int = -1
+    window_ns: tuple = (0, 0)   # its launch's window on the device's global timer
 
 
 @dataclass
@@ -72,6 +74,44 @@ class ServeReport:
                 "queue_p50_ms": float(np.percentile(self.queue_ms, 50)),
                 "queue_p99_ms": float(np.percentile(self.queue_ms, 99)),
                 "batches": self.batches, "max_inflight": self.max_inflight, **self.extra}
+
+
+def batch_windows(finished) -> List[tuple]:
+    """(begin, end) of every batch's tracking launch on the device's global
+    timer (ns), from its requests' stats; batches without a window (nothing
+    launched) are left out."""
+    w: Dict[int, tuple] = {}
+    for s in finished:
+        b, e = s.window_ns
+        if s.batch < 0 or not b or not e:
+            continue
+        lo, hi = w.get(s.batch, (b, e))
+        w[s.batch] = (min(lo, b), max(hi, e))
+    return sorted(w.values())
+
+
+def device_overlap(windows: List[tuple]) -> dict:
+    """How much batches ran at the same time on the device: the largest
+    number of launch windows open at one instant, and the sum of the
+    windows' lengths over the length of their union (1: one at a time)."""
+    if not windows:
+        return {"max_concurrent_batches": 0, "device_concurrency": 0.0}
+    ev = sorted([(b, 1) for b, _ in windows] + [(e, -1) for _, e in windows], key=lambda x: (x[0], x[1]))
+    cur = top = 0
+    for _, d in ev:
+        cur += d
+        top = max(top, cur)
+    union = 0
+    lo, hi = windows[0]
+    for b, e in windows[1:]:
+        if b > hi:
+            union += hi - lo
+            lo, hi = b, e
+        else:
+            hi = max(hi, e)
+    union += hi - lo
+    total = sum(e - b for b, e in windows)
+    return {"max_concurrent_batches": top, "device_concurrency": total / union if union > 0 else 0.0}
 
 
 class Server:
@@ -139,6 +179,7 @@ class Server:
                     if st["device_error"]:
                         raise RuntimeError("tracking kernel raised its error flag")
                     s.cell_steps = st["cell_steps"]
+                    s.window_ns = (st["t_begin_ns"], st["t_end_ns"])
                     if id(s.spec) in self.keep:
                         s.result = mp.mp_get_endpoints(self.ctx.h, s.rid, s.spec.release.n)
                     mp.mp_req_free(self.ctx.h, s.rid)
@@ -176,6 +217,7 @@ class Server:
                                             stream)
                     for s, rid in zip(group, ids):
                         s.rid = rid
+                        s.batch = batches
                     batches += 1
                 inflight.extend(admit)
                 peak = max(peak, len(inflight))
@@ -188,6 +230,8 @@ class Server:
         lat = np.array([(s.done - s.arrival) * 1e3 for s in finished])
         qms = np.array([(s.admitted - s.arrival) * 1e3 for s in finished])
         self.results = {id(s.spec): s.result for s in finished if s.result is not None}
+        self.windows = batch_windows(finished)
         return ServeReport(n, wall, int(sum(s.spec.release.n for s in finished)),
                            int(sum(s.cell_steps for s in finished)), lat, qms, batches, peak,
-                           extra={"peak_bytes": peak_bytes, "budget_bytes": self.budget})
+                           extra={"peak_bytes": peak_bytes, "budget_bytes": self.budget,
+                                  **device_overlap(self.windows)})

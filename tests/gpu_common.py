@@ -146,3 +146,76 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
           f"({ndiv / max(hsame.size, 1):.2e}), max rel t err {t_err:.2e}, max rel pos err {p_err:.2e}")
     assert not bad, f"{len(bad)} divergent particles that are not near-ties, first {bad[:3]}"
     return ndiv, t_err, p_err
+
+
+# One FP32 rounding of a local coordinate or a step time, relative: the size
+# of the oracle's per-step jitter that calibrates the mixed-precision bounds.
+FP32_JITTER = 1e-7
+
+
+def mixed_errors(ep, ref, field, idx=None):
+    """Per particle (of ``ref``'s): relative travel-time error and endpoint
+    error in cell widths of ``ep`` against ``ref``, +inf where the cell
+    sequence differs."""
+    sel = slice(None) if idx is None else idx
+    g = {k: np.asarray(ep[k])[sel] for k in ("hash", "t", "x", "y", "z")}
+    c = ref["cell"]
+    j, i, k = c % field.ncol, (c // field.ncol) % field.nrow, c // (field.ncol * field.nrow)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        dt = np.abs(g["t"] - ref["t"]) / np.abs(ref["t"])
+        dt = np.where(g["t"] == ref["t"], 0.0, dt)
+    dx = np.maximum.reduce([np.abs(g["x"] - ref["gx"]) / field.delr[j], np.abs(g["y"] - ref["gy"]) / field.delc[i],
+                            np.abs(g["z"] - ref["gz"]) / field.dz[k]])
+    div = g["hash"] != ref["hash"]
+    return np.where(div, np.inf, dt), np.where(div, np.inf, dx)
+
+
+def check_mixed(ep, *, field, state, times=None, idx=None, t_stop=np.inf, c=4.0, runs=4, threads=8, label="",
+                oracle_run=None, **track_kw):
+    """Mixed precision against the FP64 oracle (plain arithmetic), particle
+    by particle, calibrated by the problem's own sensitivity to rounding.
+
+    The oracle is run ``runs`` more times with every crossing jittered by
+    about one FP32 rounding (FP32_JITTER relative on the step time and the
+    transverse offsets; oracle/mp_oracle.h).  s_i = the largest change of
+    particle i's travel time (relative) and endpoint (cell widths) over those
+    runs, +inf where a jittered run changes its cell sequence.  Every
+    particle whose cell sequence matches the oracle's must satisfy
+    |dt|/t <= max(1e-5, c s_i^t) and |dx| <= max(1e-4 cells, c s_i^x); the
+    share of particles whose sequence differs may not exceed the jittered
+    runs' mean share plus 0.5 %.  ``oracle_run(**jitter_kw)`` replaces the
+    default oracle call (track_parallel over ``state``) where the run is
+    another (flow periods).  Returns the report (also printed)."""
+    import oracle as O
+    if oracle_run is None:
+        def oracle_run(**jk):
+            return O.track_parallel(field, state, threads, times=times, t_stop=t_stop, **track_kw, **jk)
+    ref = oracle_run()
+    dt, dx = mixed_errors(ep, ref, field, idx)
+    s_t = np.zeros(dt.size)
+    s_x = np.zeros(dt.size)
+    div_j = []
+    for r in range(runs):
+        rj = oracle_run(jitter=FP32_JITTER, jitter_seed=1000 + r)
+        jt, jx = mixed_errors({"hash": rj["hash"], "t": rj["t"], "x": rj["gx"], "y": rj["gy"], "z": rj["gz"]},
+                              ref, field)
+        s_t = np.maximum(s_t, jt)
+        s_x = np.maximum(s_x, jx)
+        div_j.append(float(np.isinf(jt).mean()))
+    same = np.isfinite(dt)
+    bad_t = np.nonzero(same & ~(dt <= np.maximum(1e-5, c * s_t)))[0]
+    bad_x = np.nonzero(same & ~(dx <= np.maximum(1e-4, c * s_x)))[0]
+    q = lambda a, v: float(np.quantile(a, v)) if a.size else 0.0
+    rep = {"particles": int(dt.size), "divergent": float(1.0 - same.mean()), "jittered_divergent": float(np.mean(div_j)),
+           "t_median": q(dt[same], 0.5), "t_p99": q(dt[same], 0.99), "t_max": q(dt[same], 1.0),
+           "within_1e-5": float(np.mean(dt[same] <= 1e-5)) if same.any() else 1.0,
+           "x_median": q(dx[same], 0.5), "x_p99": q(dx[same], 0.99),
+           "within_1e-4": float(np.mean(dx[same] <= 1e-4)) if same.any() else 1.0,
+           "bound_fail_t": int(bad_t.size), "bound_fail_x": int(bad_x.size)}
+    print(f"mixed vs oracle {label}: " + ", ".join(f"{k} {v:.3g}" if isinstance(v, float) else f"{k} {v}"
+                                                  for k, v in rep.items()))
+    assert bad_t.size == 0, f"{bad_t.size} particles beyond max(1e-5, {c} s_i) in time, first {bad_t[:5]}: " \
+                            f"{dt[bad_t[:5]]} vs s_i {s_t[bad_t[:5]]}"
+    assert bad_x.size == 0, f"{bad_x.size} particles beyond max(1e-4, {c} s_i) in position, first {bad_x[:5]}"
+    assert rep["divergent"] <= rep["jittered_divergent"] + 0.005
+    return rep

@@ -81,7 +81,7 @@ def test_batch_mixed_precisions_and_oracle(ctx):
                 G.compare_timeseries_fp64(mp.mp_get_timeseries(ctx.h, rid, s.release.n, len(s.times)), ref,
                                           dmin=G.dmin(f))
         else:
-            assert np.mean(ep["hash"] == ref["hash"]) >= 0.98
+            G.check_mixed(ep, field=f, state=st0, times=s.times, label=f"batch request {rid}")
         mp.mp_req_free(ctx.h, rid)
     for g in groups:
         mp.mp_group_free(g)
@@ -91,8 +91,8 @@ def test_batch_mixed_precisions_and_oracle(ctx):
 def test_batch_256_requests_full_size(ctx):
     """The 256-request workload (sizes log-uniform in 1e2..1e6, half with 20
     output times) in one persistent mixed-precision launch: every request's
-    counters are consistent and sampled particles of a few requests match
-    the oracle within the mixed-precision tolerances."""
+    counters are consistent and sampled particles of a few requests meet the
+    mixed-precision per-particle bound against the oracle."""
     specs = I.batch_workload()
     f = I.cfg2_field()
     fh = ctx.field(f)
@@ -112,11 +112,7 @@ def test_batch_256_requests_full_size(ctx):
             assert int(ep["steps"].astype(np.int64).sum()) == st["cell_steps"]
             idx = np.sort(rng.choice(s.release.n, min(200, s.release.n), replace=False))
             st0 = O.release_box(f, s.release.n, s.release.lo, s.release.hi, s.release.seed)
-            ref = O.track(f, O.subset(st0, idx), times=s.times, arith="mirror")
-            same = ep["hash"][idx] == ref["hash"]
-            assert same.mean() >= 0.97
-            rel = np.abs(ep["t"][idx][same] - ref["t"][same]) / ref["t"][same]
-            assert np.median(rel) <= 1e-5
+            G.check_mixed(ep, field=f, state=O.subset(st0, idx), times=s.times, idx=idx, label=f"request {r}")
         mp.mp_req_free(ctx.h, rid)
     assert total > 1e7
     for g in groups:

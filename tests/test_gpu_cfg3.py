@@ -2,8 +2,9 @@
 variance 4, 20 wells, 1e7 particles on a plane, mixed precision with the
 persistent work-queue kernel and 100 output times, measured against the FP64
 oracle on a 1e4-particle subsample and against the spread of the oracle's
-own results under 1e-7 start perturbations (the field is so ill-conditioned
-that such a perturbation changes ~90 % of cell sequences).  The FP64 path on
+own results under per-step perturbations of one FP32 rounding (the field is
+so ill-conditioned that such perturbations change ~92 % of cell
+sequences).  The FP64 path on
 a subsample matches the oracle's mirror arithmetic exactly and departs from
 its plain arithmetic less than a 1e-14 start perturbation moves the plain
 oracle itself."""
@@ -65,38 +66,11 @@ def test_cfg3_mixed_full_size_vs_oracle(cfg3):
     idx = np.sort(np.random.default_rng(4).choice(n, 10000, replace=False))
     s0 = O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed)
     sub = O.subset(s0, idx)
-    ref = O.track(w.field, sub, times=w.times, arith="mirror")
-    # the problem's own conditioning: the FP64 oracle from start positions
-    # moved by +-1e-7 cell widths (the FP32 resolution of a local coordinate)
-    rng = np.random.default_rng(5)
-    c0 = sub["cell"]
-    i0, k0 = (c0 // w.field.ncol) % w.field.nrow, c0 // (w.field.ncol * w.field.nrow)
-    pert = {kk: v.copy() for kk, v in sub.items()}
-    pert["py"] = np.clip(pert["py"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.delc[i0], 0, w.field.delc[i0])
-    pert["pz"] = np.clip(pert["pz"] + rng.uniform(-1, 1, idx.size) * 1e-7 * w.field.dz[k0], 0, w.field.dz[k0])
-    refp = O.track(w.field, pert, arith="mirror")
-
-    def errs(a_t, a_x, a_y, a_z, a_hash):
-        same = a_hash == ref["hash"]
-        fin = same & (ref["t"] > 0)
-        t_err = np.abs(a_t[fin] - ref["t"][fin]) / ref["t"][fin]
-        c = ref["cell"][fin]
-        j, i, k = c % w.field.ncol, (c // w.field.ncol) % w.field.nrow, c // (w.field.ncol * w.field.nrow)
-        pos = np.maximum(np.abs(a_x[fin] - ref["gx"][fin]) / w.field.delr[j],
-                         np.maximum(np.abs(a_y[fin] - ref["gy"][fin]) / w.field.delc[i],
-                                    np.abs(a_z[fin] - ref["gz"][fin]) / w.field.dz[k]))
-        return 1 - same.mean(), t_err, pos, np.mean(np.abs(a_t - ref["t"]) / ref["t"])
-
-    dm, tm, pm, am = errs(ep["t"][idx], ep["x"][idx], ep["y"][idx], ep["z"][idx], ep["hash"][idx])
-    dp, tp, pp, ap = errs(refp["t"], refp["gx"], refp["gy"], refp["gz"], refp["hash"])
-    print(f"cfg3 mixed vs FP64 oracle (1e4 sample): divergent {dm:.3f} (FP64 oracle perturbed 1e-7: {dp:.3f}); "
-          f"same-sequence t_err median {np.median(tm):.1e} p99 {np.quantile(tm, .99):.1e} within1e-5 "
-          f"{np.mean(tm <= 1e-5):.3f} (perturbed: median {np.median(tp):.1e} p99 {np.quantile(tp, .99):.1e}); "
-          f"mean |dt|/t over all {am:.2e} (perturbed {ap:.2e}); pos median {np.median(pm):.1e} within1e-4 "
-          f"{np.mean(pm <= 1e-4):.3f}")
-    assert dm <= dp + 0.05
-    assert am <= 3 * ap + 1e-6
-    assert np.median(tm) <= 1e-5 and np.quantile(tm, 0.99) <= 10 * np.quantile(tp, 0.99) + 1e-6
+    # per particle against the FP64 oracle, calibrated by each particle's own
+    # spread under per-step perturbations of one FP32 rounding: the field is
+    # so ill-conditioned that such perturbations change ~92 % of its paths
+    G.check_mixed(ep, field=w.field, state=sub, times=w.times, idx=idx, threads=16, label="cfg3 full size")
+    ref = O.track_parallel(w.field, sub, 16, times=w.times)
     same = ep["hash"][idx] == ref["hash"]
     # timeseries rows of the sampled particles, gathered on the device
     _, tsp = mp.mp_endpoints_device(ctx.h, req.id)
@@ -107,6 +81,30 @@ def test_cfg3_mixed_full_size_vs_oracle(cfg3):
     assert agree.mean() >= 0.97
     req.free()
     mp.mp_group_free(gh)
+
+
+def test_cfg3_mixed_forms_equally_accurate(cfg3):
+    """On a 1e4 sample of the large workload (explicit release of the same
+    particles): the default mixed form (FP32-pair time, FP32 series near
+    z = 0) and the form that keeps FP64 for both (MP_PREC_MIXED_F64T) meet
+    the same per-particle bound, with the same error distribution."""
+    torch, ctx, fh, w = cfg3
+    n = w.release.n
+    idx = np.sort(np.random.default_rng(4).choice(n, 10000, replace=False))
+    s0 = O.subset(O.release_box(w.field, n, w.release.lo, w.release.hi, w.release.seed), idx)
+    c = s0["cell"]
+    j, i, k = c % w.field.ncol, (c // w.field.ncol) % w.field.nrow, c // (w.field.ncol * w.field.nrow)
+    frac = np.stack([s0["px"] / w.field.delr[j], s0["py"] / w.field.delc[i], s0["pz"] / w.field.dz[k]], axis=1)
+    st = O.release_explicit(w.field, c, frac)
+    reps = {}
+    for name, prec in (("mixed", mp.PREC_MIXED), ("f64t", mp.PREC_MIXED_F64T)):
+        ep, _, stats = G.gpu_run(ctx, fh, cells=c, frac=frac, precision=prec, schedule=mp.SCHED_DYNAMIC)
+        assert stats["device_error"] == 0
+        reps[name] = G.check_mixed(ep, field=w.field, state=st, threads=16, label=f"cfg3 sample {name}")
+    a, b = reps["mixed"], reps["f64t"]
+    assert a["divergent"] <= b["divergent"] + 0.01
+    assert a["t_median"] <= 1.5 * b["t_median"] + 1e-8 and a["t_p99"] <= 1.5 * b["t_p99"] + 1e-7
+    assert a["within_1e-5"] >= b["within_1e-5"] - 0.01
 
 
 def test_cfg3_fp64_subsample_exact(cfg3):

@@ -156,7 +156,7 @@ def test_pathlines_mixed(ctx, fld):
     ep, _, st, path = _run(ctx, fh, cells, frac, mode=mp.MODE_ENDPOINT | mp.MODE_PATHLINE,
                            precision=mp.PREC_MIXED)
     same = np.nonzero(ep["hash"] == ref["hash"])[0]
-    assert same.size >= 0.98 * cells.size
+    G.check_mixed(ep, field=f, state=st0, label="pathline run")
     g = _sorted(path[np.isin(path["particle"], same)])
     r = _sorted(ref["path"][np.isin(ref["path"]["particle"], same)])
     assert g.size == r.size

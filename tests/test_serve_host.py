@@ -48,11 +48,14 @@ class FakeLib:
     def track_batch(self, ctx, groups, opts, stream):
         assert len({id(g["fh"]) for g in groups}) == 1     # one field per batch
         self.batches.append([g["fh"] for g in groups])
+        # a launch window per batch: batch k runs on the device from 100 k to
+        # 100 k + 250 (ns), so neighbouring batches overlap
+        k = len(self.batches) - 1
         ids = []
         for g in groups:
             rid = self.next_id
             self.next_id += 1
-            self.polls[rid] = [0, g["n"]]
+            self.polls[rid] = [0, g["n"], (1000 + 100 * k, 1250 + 100 * k)]
             ids.append(rid)
         return ids
 
@@ -61,7 +64,8 @@ class FakeLib:
         return self.polls[rid][0] >= 3
 
     def get_stats(self, ctx, rid):
-        return {"device_error": 0, "cell_steps": 10 * self.polls[rid][1]}
+        b, e = self.polls[rid][2]
+        return {"device_error": 0, "cell_steps": 10 * self.polls[rid][1], "t_begin_ns": b, "t_end_ns": e}
 
     def req_free(self, ctx, rid):
         self.freed_req.append(rid)
@@ -136,3 +140,24 @@ def test_budget_defaults_to_a_share_of_free_memory():
     assert srv.budget == int(0.8 * 10_000_000)
     srv = SV.Server(Ctx(), {}, free_share=0.5, torch_mod=FakeTorch)
     assert srv.budget == 5_000_000
+
+
+def test_device_overlap_of_batch_windows(fake):
+    """Per-batch launch windows (shared by a batch's requests) and their
+    overlap: batch k holds [1000 + 100 k, 1250 + 100 k]."""
+    specs = _specs([10] * 12, fields=("a",))
+    srv = SV.Server(Ctx(), {"a": object()}, max_inflight=2, torch_mod=FakeTorch)
+    rep = srv.run(specs, realtime=False)
+    nb = len(fake.batches)
+    assert srv.windows == [(1000 + 100 * k, 1250 + 100 * k) for k in range(nb)]
+    sm = rep.summary()
+    assert sm["max_concurrent_batches"] == min(3, nb)
+    assert sm["device_concurrency"] == pytest.approx(250 * nb / (100 * (nb - 1) + 250))
+
+
+def test_device_overlap_arithmetic():
+    assert SV.device_overlap([]) == {"max_concurrent_batches": 0, "device_concurrency": 0.0}
+    assert SV.device_overlap([(0, 10), (10, 20)])["max_concurrent_batches"] == 1
+    r = SV.device_overlap([(0, 10), (5, 15), (20, 30), (21, 22)])
+    assert r["max_concurrent_batches"] == 2 and r["device_concurrency"] == pytest.approx(31 / 25)
+
