@@ -378,7 +378,7 @@ int mp_group_set_field(mp_group* g, const mp_field* f);
 int mp_track_periods(mp_ctx* ctx, mp_group* g, int n_periods, const mp_field* const* fields, const double* t_end,
                      const mp_track_opts* o, void* stream, mp_req* out);
 
-/* Track several groups in one launch per precision: the particles of all
+/* Track several groups (fewer than 2^24) in one launch per precision: the particles of all
  * groups form one index space handed out by the persistent work queue (or
  * one thread each), the GPU form of the paper's dynamic schedule over one
  * particle loop (Methods, "Multiprocessing"; Results, "Thread scheduling").

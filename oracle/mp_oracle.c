@@ -775,8 +775,8 @@ static int track_core(const orc_grid* g, int64_t n,
             }
             /* displacement to the exit face of axis ax */
             double dt = tmin;
-            double t_end = t + (opt->jitter > 0.0 ? dt * (1.0 + opt->jitter * jitter_u(opt->jitter_seed, opt->jitter_id0 + q, steps, 0))
-                                                   : dt);
+            if (opt->jitter > 0.0) dt = dt * (1.0 + opt->jitter * jitter_u(opt->jitter_seed, opt->jitter_id0 + q, steps, 0));
+            double t_end = t + dt;
             while (kn < nt && opt->times[kn] <= t_end) {
                 double tau = opt->times[kn] - t;
                 double g0 = o[0] + mv(opt, &cv, 0, p[0], tau);

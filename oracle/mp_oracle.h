@@ -54,7 +54,8 @@ typedef struct {
 } orc_track_opts;
 
 /* Jitter (a test instrument, not part of the method): with jitter = e > 0
- * every completed cell-step's time is multiplied by (1 + e u1) and, after
+ * every completed cell-step's time (which moves the other axes and the clock)
+ * is multiplied by (1 + e u1) and, after
  * the hand-over, every transverse offset moves by e u2 D (clamped to the
  * cell), u1, u2 uniform in [-1, 1) from a counter-based generator (SplitMix64
  * of the seed, the particle's index plus jitter_id0, the step count and the

@@ -242,11 +242,17 @@ int mp_ctx_create(int device, mp_ctx** out)
     if (device < 0 || device >= ndev) return fail(MP_ERR_INVALID_ARG, "mp_ctx_create: no such device");
     MP_CUDA(cudaSetDevice(device), "cudaSetDevice");
     MP_CUDA(cudaFree(nullptr), "context init");
-    // keep freed request buffers in the stream-ordered pool for reuse
+    // keep freed request buffers in the stream-ordered pool for reuse, but
+    // never by making an allocation wait for another stream's work: a
+    // request freed on one stream (behind batches still queued there) would
+    // otherwise hold back the next allocation on another stream, and with it
+    // the overlap of independent requests
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
+        int no = 0;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     mp_ctx* c = new mp_ctx();
     c->device = device;
@@ -966,6 +972,7 @@ int mp_track_batch(mp_ctx* ctx, int n, mp_group* const* groups, const mp_track_o
                    mp_req* out)
 {
     if (!ctx || !groups || !opts || !out || n < 0) return fail(MP_ERR_INVALID_ARG, "mp_track_batch: bad argument");
+    if (n >= (1 << 24)) return fail(MP_ERR_INVALID_ARG, "mp_track_batch: more than 2^24 - 1 requests");
     if (n == 0) return MP_OK;
     for (int i = 0; i < n; ++i) {
         if (!groups[i]) return fail(MP_ERR_INVALID_ARG, "mp_track_batch: NULL group");
@@ -1529,6 +1536,7 @@ int mp_graph_create(mp_ctx* ctx, const mp_field* f, int n_reqs, const mp_release
                     const mp_track_opts* opts, void* stream, mp_graph** out)
 {
     if (!ctx || !f || !rel || !opts || !out || n_reqs < 1) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: bad argument");
+    if (n_reqs >= (1 << 24)) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: more than 2^24 - 1 requests");
     if (f->ctx != ctx) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: field of another context");
     if (f->usg) return fail(MP_ERR_INVALID_ARG, "mp_graph_create: box releases need a rectilinear grid");
     for (int i = 0; i < n_reqs; ++i) {

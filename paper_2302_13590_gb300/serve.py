@@ -200,13 +200,14 @@ class Server:
                 held += b
                 admit.append(s)
             if admit:
-                stream = self.streams[self._next_stream % len(self.streams)]
-                self._next_stream += 1
                 by_field: Dict[str, List[Served]] = {}
                 for s in admit:
                     by_field.setdefault(s.spec.field_name, []).append(s)
                 tnow = time.perf_counter() - t0
                 for name, group in by_field.items():
+                    # every batch on the next stream of the pool
+                    stream = self.streams[self._next_stream % len(self.streams)]
+                    self._next_stream += 1
                     fh = self.fields[name]
                     for s in group:
                         r = s.spec.release
