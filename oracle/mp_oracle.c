@@ -709,6 +709,14 @@ static int track_core(const orc_grid* g, int64_t n,
         } else {
             st = ORC_ST_INVALID_RELEASE;
         }
+        /* jitter (test instrument): the start position, as it would be
+         * rounded when a reduced-precision evaluation loads it */
+        if (opt->jitter > 0.0 && c >= 0 && st == ORC_ST_ACTIVE) {
+            for (int a = 0; a < 3; a++) {
+                double pa = p[a] + opt->jitter * jitter_u(opt->jitter_seed, opt->jitter_id0 + q, steps, 4 + a) * D[a];
+                p[a] = pa < 0.0 ? 0.0 : (pa > D[a] ? D[a] : pa);
+            }
+        }
         /* output times at or before the start: the release position */
         while (kn < nt && opt->times[kn] <= t) {
             if (c >= 0)

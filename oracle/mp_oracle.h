@@ -55,9 +55,10 @@ typedef struct {
 
 /* Jitter (a test instrument, not part of the method): with jitter = e > 0
  * every completed cell-step's time (which moves the other axes and the clock)
- * is multiplied by (1 + e u1) and, after
- * the hand-over, every transverse offset moves by e u2 D (clamped to the
- * cell), u1, u2 uniform in [-1, 1) from a counter-based generator (SplitMix64
+ * is multiplied by (1 + e u1), after the hand-over every transverse offset
+ * moves by e u2 D, and a moving particle's start offsets move by e u3 D
+ * (clamped to the cell), u1, u2, u3 uniform in [-1, 1) from a counter-based
+ * generator (SplitMix64
  * of the seed, the particle's index plus jitter_id0, the step count and the
  * axis).  Runs with
  * e of the order of one FP32 rounding show how far a particle's result moves

@@ -283,6 +283,9 @@ cudaError_t launch_release_explicit(const DevField& f, const DevState& st, long 
 // ---------------------------------------------------------------------------
 
 struct F64Engine {
+    // blocks of 256 threads to keep resident per SM (0: no target; the
+    // kernels are FP64-pipe bound)
+    static constexpr int min_blocks(bool, bool, bool) { return 0; }
     DevField f;
     Batch b;
 

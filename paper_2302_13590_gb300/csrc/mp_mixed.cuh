@@ -43,6 +43,11 @@ namespace mp {
 
 template <bool F64T>
 struct MixEngine {
+    // blocks of 256 threads to keep resident per SM: the kernels are issue
+    // bound, and without a target the compiler gives the static endpoint
+    // kernel fewer registers than it needs (spills); four blocks (at most 64
+    // registers) fit both static kernels without spills
+    static constexpr int min_blocks(bool dynamic, bool, bool pl) { return (!dynamic && !pl) ? 4 : 0; }
     DevField f;
     Batch b;
 
@@ -280,48 +285,48 @@ struct MixEngine {
     }
 
     // per-warp queue of deferred timeseries records (structure of arrays)
-    // per record three 16-byte vectors: {x0, x1, x2, tau}, {c, i, j, k},
-    // {q low, q high, kk, r | status << 24} (requests per launch < 2^24)
     struct RecQ {
-        float4 xt[RQ_CAP];
-        int4 cell[RQ_CAP];
-        int4 meta[RQ_CAP];
+        float x0[RQ_CAP], x1[RQ_CAP], x2[RQ_CAP], tau[RQ_CAP];
+        long long q[RQ_CAP];
+        int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP], r[RQ_CAP];
     };
 
     __device__ __forceinline__ void rec_put(RecQ& Q, int slot, const State& s, long long q, int kk, int st) const
     {
         const Req& R = b.reqs[s.r];
+        const DevState& in = R.in;
         const DevOut& o = R.o;
-        float tau;
+        const TrackParams& p = R.p;
+        (void)in; (void)o; (void)p;
+        Q.r[slot] = s.r;
+        Q.x0[slot] = s.x0; Q.x1[slot] = s.x1; Q.x2[slot] = s.x2;
         if constexpr (F64T) {
-            tau = (float)(__ldg(o.times + kk) - s.t);
+            Q.tau[slot] = (float)(__ldg(o.times + kk) - s.t);
         } else {
             const float2 tk = time_pair(o, kk);
-            tau = ff_diff(tk.x, tk.y, s.th, s.tl);
+            Q.tau[slot] = ff_diff(tk.x, tk.y, s.th, s.tl);
         }
-        Q.xt[slot] = make_float4(s.x0, s.x1, s.x2, tau);
-        Q.cell[slot] = make_int4(s.c, s.i, s.j, s.k);
-        Q.meta[slot] = make_int4((int)(unsigned)(q & 0xffffffffLL), (int)(q >> 32), kk, s.r | (st << 24));
+        Q.q[slot] = q;
+        Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
+        Q.kk[slot] = kk; Q.st[slot] = st;
     }
 
     __device__ __forceinline__ void rec_eval(const RecQ& Q, int slot) const
     {
-        const float4 xt = Q.xt[slot];
-        const int4 ce = Q.cell[slot], me = Q.meta[slot];
-        const Req& R = b.reqs[me.w & 0xffffff];
+        const Req& R = b.reqs[Q.r[slot]];
         const DevOut& o = R.o;
         const TrackParams& p = R.p;
         State r;
-        r.c = ce.x; r.i = ce.y; r.j = ce.z; r.k = ce.w;
-        const float tau = xt.w;
+        r.c = Q.c[slot]; r.i = Q.i[slot]; r.j = Q.j[slot]; r.k = Q.k[slot];
+        const float tau = Q.tau[slot];
         const float4* rp = reinterpret_cast<const float4*>(f.rec32 + r.c);
         const float4 ra = __ldg(rp), rb = __ldg(rp + 1);
         const float Ax = ra.y - ra.x, Ay = ra.w - ra.z, Az = rb.y - rb.x;
-        const double x = gx(r, move(Ax, ra.x + Ax * xt.x, xt.x, tau));
-        const double y = gy(r, move(Ay, ra.z + Ay * xt.y, xt.y, tau));
-        const double z = gz(r, move(Az, rb.x + Az * xt.z, xt.z, tau));
-        const long long q = (long long)(((unsigned long long)(unsigned)me.y << 32) | (unsigned)me.x);
-        store_record(o.ts + (long long)me.z * p.n + q, x, y, z, r.c, (int)((unsigned)me.w >> 24));
+        const float a0 = Q.x0[slot], a1 = Q.x1[slot], a2 = Q.x2[slot];
+        const double x = gx(r, move(Ax, ra.x + Ax * a0, a0, tau));
+        const double y = gy(r, move(Ay, ra.z + Ay * a1, a1, tau));
+        const double z = gz(r, move(Az, rb.x + Az * a2, a2, tau));
+        store_record(o.ts + (long long)Q.kk[slot] * p.n + Q.q[slot], x, y, z, r.c, Q.st[slot]);
     }
 
     template <bool TS>

@@ -135,17 +135,6 @@ __device__ __forceinline__ void rq_push(const E& e, typename E::RecQ& Q, int& qc
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    // usual case: no lane has more than one record this step; the queue
-    // holds fewer than 32 (it is drained at 32), so all of them fit, and a
-    // ballot gives every lane its slot
-    if (!__any_sync(FULL, m > 1)) {
-        const unsigned has = __ballot_sync(FULL, m > 0);
-        if (m > 0) e.rec_put(Q, qcount + __popc(has & ((1u << lane) - 1u)), s, q, kn0, st);
-        qcount += __popc(has);
-        __syncwarp();
-        rq_drain(e, Q, qcount, false);
-        return;
-    }
     int done = 0;
     while (true) {
         const int want = m - done;
@@ -285,7 +274,7 @@ __device__ __forceinline__ bool path_start(const E& e, const S& s)
 }
 
 template <class E, bool TS, bool PL>
-__global__ void __launch_bounds__(256) k_track_static(E e)
+__global__ void __launch_bounds__(256, E::min_blocks(false, TS, PL)) k_track_static(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
     typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);
@@ -334,7 +323,7 @@ __global__ void __launch_bounds__(256) k_track_static(E e)
 }
 
 template <class E, bool TS, bool PL>
-__global__ void __launch_bounds__(256) k_track_dynamic(E e)
+__global__ void __launch_bounds__(256, E::min_blocks(true, TS, PL)) k_track_dynamic(E e)
 {
     __shared__ unsigned long long s_cnt[N_COUNTERS];
     typename E::RecQ* s_q = reinterpret_cast<typename E::RecQ*>(s_dyn);

@@ -143,6 +143,7 @@ cudaError_t launch_release_explicit_usg(const DevUsg& u, const DevState& st, lon
 // ---------------------------------------------------------------------------
 
 struct UsgEngine {
+    static constexpr int min_blocks(bool, bool, bool) { return 0; }
     DevUsg u;
     Batch b;
 
