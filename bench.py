@@ -568,7 +568,7 @@ def run_ours(args):
     # branch of the exit time (MP_PREC_MIXED_F64T), same workload: what those
     # two FP64 pieces cost on this GPU
     f64t = None
-    if "mixed" in args.precisions and not args.particles:
+    if "mixed" in args.precisions and not args.particles and not args.no_f64t_form:
         gh = mp.mp_release_group(ctx.h, fh, n=n, lo=rel.lo, hi=rel.hi, seed=rel.seed, id_offset=rel.id_offset,
                                  stream=stream)
         kms = []
@@ -887,6 +887,7 @@ def main():
     ap.add_argument("--only-quadtree", action="store_true", help="run the quadtree line alone (profiling)")
     ap.add_argument("--serve-requests", type=int, default=5000)
     ap.add_argument("--no-cfg3", action="store_true")
+    ap.add_argument("--no-f64t-form", action="store_true", help="skip timing the FP64-time mixed form (profiling)")
     ap.add_argument("--cfg3-particles", type=int, default=0, help="override cfg3's 1e7 particles (quick checks)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
