@@ -58,30 +58,30 @@ FP64_FLOPS_PER_STEP = 217.0
 BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # DRAM traffic per full launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # of the two tracking kernels, from one ncu capture of the same kernels on
-# 2e5 particles of this workload (profiles/k_track_cfg2_200k.md), scaled by
+# 2e5 particles of this workload in their tuned launch configurations
+# (profiles/k_track_cfg2_200k.md), scaled by
 # 5 to the 1e6-particle launch: reads grow with the cell-steps, writes with
 # the output records, both in proportion to the particle count.  It holds
 # only for the kernel sources it was taken from (their hash below);
 # otherwise the bench reports traffic as null.
-TRAFFIC = {"src": "753189249556e18e", "fp64": 5 * (351.046912e6 + 307.223040e6),
-           "mixed": 5 * (46.528512e6 + 289.981440e6)}
+TRAFFIC = {"src": "46413a7624432cb5", "fp64": 5 * (352.305664e6 + 307.299584e6),
+           "mixed": 5 * (43.280128e6 + 287.389184e6)}
 # From the same capture: the FP64 pipe's busy fraction in the FP64 kernel
 # (sm__pipe_fp64_cycles_active, % of peak sustained active), the executed
 # counterpart of the algorithmic fraction (which charges every axis's exit
 # time while the kernel evaluates the exact one of about 1.1 axes a step).
-FP64_PIPE_ACTIVE = {"src": "753189249556e18e", "value": 0.8487}
+FP64_PIPE_ACTIVE = {"src": "46413a7624432cb5", "value": 0.8471}
 # Warp-instructions per cell-step of the mixed kernel in the same capture
-# (smsp__inst_executed.sum / cell-steps on 2e5 particles; the 1e6 launch
-# drains relatively less, so this slightly overstates its count): the mixed
-# kernel is issue-bound, and its issue view compares the implied issue rate
-# with one warp-instruction per clock per SM sub-partition (152 SMs x 4 x
-# 2.07 GHz).
-MIXED_INST_PER_STEP = {"src": "753189249556e18e", "value": 1401142002.0 / 5.483e7}
+# (smsp__inst_executed.sum / cell-steps on 2e5 particles, static schedule,
+# 256 threads: the tuned launch): the mixed kernel is issue-bound, and its
+# issue view compares the implied issue rate with one warp-instruction per
+# clock per SM sub-partition (152 SMs x 4 x 2.07 GHz).
+MIXED_INST_PER_STEP = {"src": "46413a7624432cb5", "value": 1154103429.0 / 54832447.0}
 ISSUE_PEAK_TINST = 152 * 4 * 2.07e9 / 1e12
 # L2 read bytes per cell-step in the same capture (lts__t_sectors_srcunit_tex_op_read
 # x 32 B / cell-steps): the record gather, cell sizes, output times.
-L2_READ_PER_STEP = {"src": "753189249556e18e", "fp64": 248577327.0 * 32 / 5.483e7,
-                    "mixed": 62376351.0 * 32 / 5.483e7}
+L2_READ_PER_STEP = {"src": "46413a7624432cb5", "fp64": 248998414.0 * 32 / 54832426.0,
+                    "mixed": 61315161.0 * 32 / 54832447.0}
 
 
 # Sources of the device code the counters above were taken from: the kernel
