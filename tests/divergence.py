@@ -82,3 +82,35 @@ def analyse(field, state, which, *, t_stop=np.inf, times=None, ref="plain", othe
         tb = O.track(field, s1, t_stop=t_stop, times=times, arith=other, trace=True, **kw)["trace"]
         out.append(first_divergence(ta, tb, t_stop=t_stop, particle=int(q)))
     return out
+
+
+def first_time_split(ref, other, rtol):
+    """Two TRACE_RECORD arrays of one particle that take the same cells:
+    the first step whose chosen exit time differs by more than ``rtol`` of
+    the time at the end of the step, and there the particle velocity on the
+    exit axis relative to its face velocity (a value near zero means the exit
+    starts from a stagnation surface, where the exit time, ln(v_exit / v_p)
+    / A, is set by the rounding of a vanishing v_p).  Returns (step,
+    |v_p| / v_face) or (-1, inf) when no step differs."""
+    for s in range(min(ref.size, other.size)):
+        a, b = ref[s], other[s]
+        ax = int(a["ax"])
+        if ax < 0 or int(b["ax"]) != ax:
+            continue
+        ta, tb = float(a["te"][ax]), float(b["te"][ax])
+        if abs(ta - tb) > rtol * (float(a["t"]) + max(ta, tb)):
+            return s, abs(float(a["vp"][ax])) / max(float(a["vf"][ax]), 1e-300)
+    return -1, float("inf")
+
+
+def stagnation_exits(field, state, which, *, rtol, t_stop=np.inf, times=None, **kw):
+    """For particles ``which`` (same cell sequence in both arithmetic modes,
+    results further apart than ``rtol``): (particle, step, |v_p| / v_face) at
+    the first step whose exit times part."""
+    out = []
+    for q in np.asarray(which, dtype=np.int64):
+        s1 = O.subset(state, [int(q)])
+        ta = O.track(field, s1, t_stop=t_stop, times=times, arith="plain", trace=True, **kw)["trace"]
+        tb = O.track(field, s1, t_stop=t_stop, times=times, arith="mirror", trace=True, **kw)["trace"]
+        out.append((int(q),) + first_time_split(ta, tb, rtol))
+    return out

@@ -113,39 +113,63 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
 
     Particles whose cell sequence (FNV hash) matches: statuses, cells, step
     counts and exit faces equal, travel times and positions (endpoint and
-    timeseries) within ``rtol``.  Particles whose sequence differs are traced
-    in both oracle modes (the mirror mode equals the GPU bit for bit, which
-    the caller checks separately) and each must part at a near-tie: at the
-    first step where the evaluations choose differently, the reference's two
-    competing choices lie within ``rtol`` of each other (divergence.py).
-    ``state`` is the oracle state of the compared particles (``idx`` of the
-    GPU arrays).  Returns (number of divergent particles, max relative time
-    error, max relative position error) and prints them."""
+    timeseries) within ``rtol``, except where an exit starts from a
+    stagnation surface: a particle beyond ``rtol`` is traced in both oracle
+    modes and passes only if the first step whose exit times part has a
+    particle velocity within 1e-12 of zero (relative to the face velocity),
+    where the exit time ln(v_exit / v_p) / A is set by the rounding of a
+    vanishing v_p.  Particles whose sequence differs are traced the same way
+    (the mirror mode equals the GPU bit for bit, which the caller checks
+    separately) and each must part at a near-tie: at the first step where the
+    evaluations choose differently, the reference's two competing choices
+    lie within ``rtol`` of each other (divergence.py).  ``state`` is the
+    oracle state of the compared particles (``idx`` of the GPU arrays).
+    Returns (divergent, max relative time error, max relative position
+    error, stagnation exits) and prints them."""
     from tests import divergence as D
     sel = slice(None) if idx is None else idx
-    hsame = ep["hash"][sel] == plain["hash"]
-    ndiv = compare_fp64(ep, plain, idx=idx, rtol=rtol, dmin=dmin(field), allow_divergent=1.0)
-    if ts is not None:
-        compare_timeseries_fp64(ts, plain, idx=idx, rtol=rtol, dmin=dmin(field), keep=hsame)
+    g = {k: np.asarray(v)[sel] for k, v in ep.items()}
+    hsame = g["hash"] == plain["hash"]
+    ndiv = int((~hsame).sum())
     keep = np.nonzero(hsame)[0]
-    tg = np.asarray(ep["t"])[sel][keep]
-    tp = plain["t"][keep]
-    fin = np.isfinite(tp)
-    t_err = rel_err(tg[fin], tp[fin]).max(initial=0.0)
-    p_err = 0.0
+    for k in ("status", "cell", "steps", "exit_face"):
+        bad = keep[g[k][keep] != plain[k][keep]]
+        assert bad.size == 0, f"{k}: {bad.size} mismatches on matching cell sequences, first {bad[:5]}"
+    err_t = np.zeros(plain["t"].size)
+    err_p = np.zeros(plain["t"].size)
+    fin = np.isfinite(plain["t"])
+    assert np.array_equal(np.isfinite(g["t"][keep]), fin[keep]), "t finiteness"
+    err_t[fin] = rel_err(g["t"][fin], plain["t"][fin])
     for ax, (gk, ok) in enumerate((("x", "gx"), ("y", "gy"), ("z", "gz"))):
-        a, b = np.asarray(ep[gk])[sel][keep], plain[ok][keep]
+        b = plain[ok]
         f2 = np.isfinite(b)
-        p_err = max(p_err, rel_err(a[f2], b[f2], scale=pos_scale(dmin(field)[ax], b[f2])).max(initial=0.0))
+        assert np.array_equal(np.isfinite(g[gk][keep]), f2[keep]), gk
+        err_p[f2] = np.maximum(err_p[f2], rel_err(g[gk][f2], b[f2], scale=pos_scale(dmin(field)[ax], b[f2])))
+    over = keep[np.maximum(err_t[keep], err_p[keep]) > rtol]
+    stagn = []
+    if over.size:
+        for q, step, ratio in D.stagnation_exits(field, state, over, rtol=rtol, t_stop=t_stop, times=times, **track_kw):
+            assert ratio <= 1e-12, (f"particle {q}: time or position beyond {rtol} on the same cell sequence "
+                                    f"(t err {err_t[q]:.3g}, pos err {err_p[q]:.3g}), not from a stagnation exit "
+                                    f"(step {step}, |v_p|/v_face {ratio:.3g})")
+            stagn.append(q)
+    good = np.setdiff1d(keep, np.asarray(stagn, dtype=np.int64))
+    if ts is not None:
+        mask = np.zeros(hsame.size, dtype=bool)
+        mask[good] = True
+        compare_timeseries_fp64(ts, plain, idx=idx, rtol=rtol, dmin=dmin(field), keep=mask)
+    t_err = err_t[good].max(initial=0.0)
+    p_err = err_p[good].max(initial=0.0)
     bad = []
     if ndiv:
         for d in D.analyse(field, state, np.nonzero(~hsame)[0], t_stop=t_stop, times=times, **track_kw):
             if not d.rel <= rtol:
                 bad.append(d)
     print(f"fp64 vs plain oracle {label}: {hsame.size} particles, {ndiv} divergent "
-          f"({ndiv / max(hsame.size, 1):.2e}), max rel t err {t_err:.2e}, max rel pos err {p_err:.2e}")
+          f"({ndiv / max(hsame.size, 1):.2e}), {len(stagn)} stagnation exits, max rel t err {t_err:.2e}, "
+          f"max rel pos err {p_err:.2e}")
     assert not bad, f"{len(bad)} divergent particles that are not near-ties, first {bad[:3]}"
-    return ndiv, t_err, p_err
+    return ndiv, t_err, p_err, len(stagn)
 
 
 # One FP32 rounding of a local coordinate or a step time, relative: the size

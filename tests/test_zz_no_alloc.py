@@ -231,3 +231,28 @@ def test_noalloc_refuses_a_capturing_stream():
         del g
         assert err is not None and err.code == -1 and "capturing" in str(err)
 
+
+
+def test_noalloc_at_the_maximum_number_of_times():
+    """Exactly MP_NOALLOC_MAX_TIMES output times (the largest request the
+    static array holds) give mp_track's records."""
+    torch = pytest.importorskip("torch")
+    w = I.workload("cfg1", n_particles=97)
+    times = np.linspace(0.0, 2.0 * w.t_adv, mp.NOALLOC_MAX_TIMES)
+    with mp.Context(0) as ctx:
+        fh = ctx.field(w.field)
+        gh = ctx.release_box(fh, w.release.n, w.release.lo, w.release.hi, w.release.seed)
+        r0 = ctx.track(gh, t_stop=0.0, schedule=mp.SCHED_STATIC)
+        ep0 = r0.endpoints()
+        r0.free()
+        req = ctx.track(gh, mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, times=times)
+        ref, ref_ts = req.endpoints(), req.timeseries()
+        req.free()
+        n, nt = w.release.n, times.size
+        out = _device_out(torch, n)
+        ts = torch.empty(nt * n * 32, dtype=torch.uint8, device="cuda")
+        st = mp.mp_track_noalloc(fh, _device_state(torch, ep0), out, ts=ts,
+                                 opts=mp.make_opts(mode=mp.MODE_ENDPOINT | mp.MODE_TIMESERIES, times=times))
+        assert st["device_error"] == 0
+        _check(_host(out), ts.cpu().numpy().view(mp.TS_RECORD).reshape(nt, n), ref, ref_ts, w.field)
+        mp.mp_group_free(gh)
