@@ -699,141 +699,158 @@ def run_ours(args):
                                                          "2.07 GHz"}
     batch = None
     if not args.no_batch:
-        specs = I.batch_workload()
-        batch = {"workload": "256 requests on the 200x200x20 field, sizes log-uniform in 1e2..1e6 (3.0e7 particles), "
-                             "random boxes, half with 20 output times; one launch per precision, autotuned"}
-        # autotune the batch's launch per precision and mode on its largest
-        # request (the launch takes the tuned configuration of its first
-        # request of that precision)
-        big = max(specs, key=lambda x: x.release.n)
-        ts_times = next(x.times for x in specs if x.timeseries)
-        batch_tuning = {}
-        for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
-            for tsm in (False, True):
-                gh = mp.mp_release_group(ctx.h, fh, n=big.release.n, lo=big.release.lo, hi=big.release.hi,
-                                         seed=big.release.seed, stream=stream)
-                o = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if tsm else 0), precision=prec,
-                                 times=ts_times if tsm else None)
-                batch_tuning[f"{name}_{'timeseries' if tsm else 'endpoint'}"] = mp.mp_autotune(ctx.h, gh, o, sample=0,
-                                                                                             stream=stream)
-                mp.mp_group_free(gh)
-        batch["tuning"] = batch_tuning
-        for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
-            best = None
-            for rep in range(2):
-                groups = [mp.mp_release_group(ctx.h, fh, n=x.release.n, lo=x.release.lo, hi=x.release.hi,
-                                              seed=x.release.seed, stream=stream) for x in specs]
-                opts = [mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
-                                     precision=prec, schedule=mp.SCHED_AUTO, times=x.times) for x in specs]
-                ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
-                sts = [mp.mp_get_stats(ctx.h, i) for i in ids]
-                steps_b = sum(x["cell_steps"] for x in sts)
-                kms = sts[0]["kernel_ms"]
-                for i in ids:
-                    mp.mp_req_free(ctx.h, i)
-                for g in groups:
-                    mp.mp_group_free(g)
-                if rep == 1:
-                    best = {"cell_steps_per_s": steps_b / (kms / 1e3), "kernel_ms": kms, "cell_steps": steps_b,
-                            "particles": int(sum(x.release.n for x in specs))}
-            batch[name] = best
-        # the same kind of batch captured once as a CUDA graph (one batched
-        # release, one tracking launch per precision) and replayed, against
-        # the host-side sequence (a release per group, the batch table, the
-        # tracking launch); wall time per batch, host included
-        def wall_ms(fn, reps):
-            fn()
-            t0 = time.perf_counter()
-            for _ in range(reps):
+        try:
+            specs = I.batch_workload()
+            batch = {"workload": "256 requests on the 200x200x20 field, sizes log-uniform in 1e2..1e6 (3.0e7 particles), "
+                                 "random boxes, half with 20 output times; one launch per precision, autotuned"}
+            # autotune the batch's launch per precision and mode on its largest
+            # request (the launch takes the tuned configuration of its first
+            # request of that precision)
+            big = max(specs, key=lambda x: x.release.n)
+            ts_times = next(x.times for x in specs if x.timeseries)
+            batch_tuning = {}
+            for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
+                for tsm in (False, True):
+                    gh = mp.mp_release_group(ctx.h, fh, n=big.release.n, lo=big.release.lo, hi=big.release.hi,
+                                             seed=big.release.seed, stream=stream)
+                    o = mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if tsm else 0), precision=prec,
+                                     times=ts_times if tsm else None)
+                    batch_tuning[f"{name}_{'timeseries' if tsm else 'endpoint'}"] = mp.mp_autotune(ctx.h, gh, o, sample=0,
+                                                                                                 stream=stream)
+                    mp.mp_group_free(gh)
+            batch["tuning"] = batch_tuning
+            for name, prec in (("mixed", mp.PREC_MIXED), ("fp64", mp.PREC_FP64)):
+                best = None
+                for rep in range(2):
+                    groups = [mp.mp_release_group(ctx.h, fh, n=x.release.n, lo=x.release.lo, hi=x.release.hi,
+                                                  seed=x.release.seed, stream=stream) for x in specs]
+                    opts = [mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
+                                         precision=prec, schedule=mp.SCHED_AUTO, times=x.times) for x in specs]
+                    ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
+                    sts = [mp.mp_get_stats(ctx.h, i) for i in ids]
+                    steps_b = sum(x["cell_steps"] for x in sts)
+                    kms = sts[0]["kernel_ms"]
+                    for i in ids:
+                        mp.mp_req_free(ctx.h, i)
+                    for g in groups:
+                        mp.mp_group_free(g)
+                    if rep == 1:
+                        best = {"cell_steps_per_s": steps_b / (kms / 1e3), "kernel_ms": kms, "cell_steps": steps_b,
+                                "particles": int(sum(x.release.n for x in specs))}
+                batch[name] = best
+            # the same kind of batch captured once as a CUDA graph (one batched
+            # release, one tracking launch per precision) and replayed, against
+            # the host-side sequence (a release per group, the batch table, the
+            # tracking launch); wall time per batch, host included
+            def wall_ms(fn, reps):
                 fn()
-            return (time.perf_counter() - t0) / reps * 1e3
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    fn()
+                return (time.perf_counter() - t0) / reps * 1e3
 
-        rng = np.random.default_rng(7)
-        Lx, Ly, Lz = w.field.extent
-        small = []
-        for i in range(256):
-            nn = int(np.exp(rng.uniform(np.log(200), np.log(2000))))
-            lo = np.array([rng.uniform(0, 0.5 * Lx), rng.uniform(0, 0.5 * Ly), 0.0])
-            small.append(I.Release(nn, tuple(lo), tuple(lo + [0.1 * Lx, 0.1 * Ly, Lz]), seed=500 + i))
-        graph = {}
-        for key, rels, optf, reps in (
-                ("small", small, lambda x: mp.make_opts(precision=mp.PREC_MIXED), 20),
-                ("batch_workload_mixed", [x.release for x in specs],
-                 lambda x: mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
-                                        precision=mp.PREC_MIXED, times=x.times), 3)):
-            opts = [optf(x) for x in (specs if key != "small" else rels)]
+            rng = np.random.default_rng(7)
+            Lx, Ly, Lz = w.field.extent
+            small = []
+            for i in range(256):
+                nn = int(np.exp(rng.uniform(np.log(200), np.log(2000))))
+                lo = np.array([rng.uniform(0, 0.5 * Lx), rng.uniform(0, 0.5 * Ly), 0.0])
+                small.append(I.Release(nn, tuple(lo), tuple(lo + [0.1 * Lx, 0.1 * Ly, Lz]), seed=500 + i))
+            graph = {}
+            for key, rels, optf, reps in (
+                    ("small", small, lambda x: mp.make_opts(precision=mp.PREC_MIXED), 20),
+                    ("batch_workload_mixed", [x.release for x in specs],
+                     lambda x: mp.make_opts(mode=mp.MODE_ENDPOINT | (mp.MODE_TIMESERIES if x.timeseries else 0),
+                                            precision=mp.PREC_MIXED, times=x.times), 3)):
+                opts = [optf(x) for x in (specs if key != "small" else rels)]
 
-            def direct():
-                groups = [mp.mp_release_group(ctx.h, fh, n=r.n, lo=r.lo, hi=r.hi, seed=r.seed, stream=stream)
-                          for r in rels]
-                ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
-                stream.synchronize()
-                for i in ids:
-                    mp.mp_req_free(ctx.h, i)
-                for g in groups:
-                    mp.mp_group_free(g)
+                def direct():
+                    groups = [mp.mp_release_group(ctx.h, fh, n=r.n, lo=r.lo, hi=r.hi, seed=r.seed, stream=stream)
+                              for r in rels]
+                    ids = mp.mp_track_batch(ctx.h, groups, opts, stream)
+                    stream.synchronize()
+                    for i in ids:
+                        mp.mp_req_free(ctx.h, i)
+                    for g in groups:
+                        mp.mp_group_free(g)
 
-            gh, gids = mp.mp_graph_create(ctx.h, fh, rels, opts, stream=stream)
+                gh, gids = mp.mp_graph_create(ctx.h, fh, rels, opts, stream=stream)
 
-            def replay():
-                mp.mp_graph_launch(gh, stream=stream)
-                stream.synchronize()
+                def replay():
+                    mp.mp_graph_launch(gh, stream=stream)
+                    stream.synchronize()
 
-            d_ms, g_ms = wall_ms(direct, reps), wall_ms(replay, reps)
-            steps_g = sum(mp.mp_get_stats(ctx.h, i)["cell_steps"] for i in gids)
-            mp.mp_graph_free(gh)
-            graph[key] = {"requests": len(rels), "particles": int(sum(r.n for r in rels)), "direct_ms": d_ms,
-                          "graph_ms": g_ms, "graph_cell_steps_per_s": steps_g / (g_ms / 1e3)}
-        graph["small"]["workload"] = ("256 requests of 200..2000 particles (log-uniform) in random boxes, mixed "
-                                      "precision, endpoint mode")
-        batch["graph"] = graph
+                d_ms, g_ms = wall_ms(direct, reps), wall_ms(replay, reps)
+                steps_g = sum(mp.mp_get_stats(ctx.h, i)["cell_steps"] for i in gids)
+                mp.mp_graph_free(gh)
+                graph[key] = {"requests": len(rels), "particles": int(sum(r.n for r in rels)), "direct_ms": d_ms,
+                              "graph_ms": g_ms, "graph_cell_steps_per_s": steps_g / (g_ms / 1e3)}
+            graph["small"]["workload"] = ("256 requests of 200..2000 particles (log-uniform) in random boxes, mixed "
+                                          "precision, endpoint mode")
+            batch["graph"] = graph
+        except Exception as exc:   # an extra block must not cost the headline line
+            batch = {"error": repr(exc)}
 
-    quadtree = None if args.no_quadtree else run_quadtree(ctx, stream)
-    if quadtree is not None:
+    quadtree = None
+    if not args.no_quadtree:
+        try:
+            quadtree = run_quadtree(ctx, stream)
+        except Exception as exc:   # an extra block must not cost the headline line
+            quadtree = {"error": repr(exc)}
+    if quadtree is not None and "roofline" in quadtree:
         qr = quadtree["roofline"]
         qr.update(peak=fp64_peak, frac=qr["achieved"] / fp64_peak, peak_source=fp64_src,
                   nominal_peak=FP64_PEAK_TFLOPS, frac_of_nominal=qr["achieved"] / FP64_PEAK_TFLOPS)
 
     serving = None
     if not args.no_serve:
-        from paper_2302_13590_gb300 import serve as SV
-        fields = {"cfg1": ctx.field(I.cfg1_field()), "cfg2": fh}
-        serving = {}
-        for name, prec, nreq in (("mixed", mp.PREC_MIXED, args.serve_requests),
-                                 ("fp64", mp.PREC_FP64, args.serve_requests)):
-            specs = I.serving_workload(n_req=nreq, rate_hz=200.0)
-            srv = SV.Server(ctx, fields, precision=prec, schedule=mp.SCHED_STATIC)
-            rep = srv.run(specs, realtime=True)
-            sm = rep.summary()
-            sm["offered_requests_per_s"] = 200.0
-            sm["offered_particles_per_s"] = float(sum(x.release.n for x in specs)) / specs[-1].arrival_s
-            serving[name] = sm
-        serving["workload"] = ("Poisson arrivals at 200 requests/s on the 50x50x1 and 200x200x20 fields (p = 1/2), "
-                               "group sizes log-uniform in 1e3..1e6, endpoint or 20-time timeseries at random")
+        try:
+            from paper_2302_13590_gb300 import serve as SV
+            fields = {"cfg1": ctx.field(I.cfg1_field()), "cfg2": fh}
+            serving = {}
+            for name, prec, nreq in (("mixed", mp.PREC_MIXED, args.serve_requests),
+                                     ("fp64", mp.PREC_FP64, args.serve_requests)):
+                specs = I.serving_workload(n_req=nreq, rate_hz=200.0)
+                srv = SV.Server(ctx, fields, precision=prec, schedule=mp.SCHED_STATIC)
+                rep = srv.run(specs, realtime=True)
+                sm = rep.summary()
+                sm["offered_requests_per_s"] = 200.0
+                sm["offered_particles_per_s"] = float(sum(x.release.n for x in specs)) / specs[-1].arrival_s
+                serving[name] = sm
+            serving["workload"] = ("Poisson arrivals at 200 requests/s on the 50x50x1 and 200x200x20 fields (p = 1/2), "
+                                   "group sizes log-uniform in 1e3..1e6, endpoint or 20-time timeseries at random")
+        except Exception as exc:   # an extra block must not cost the headline line
+            serving = {"error": repr(exc)}
     cfg3 = w3 = idx3 = eps3 = None
     if not args.no_cfg3:
-        cfg3, w3, idx3, eps3 = run_cfg3(ctx, stream, args)
-        for name in ("mixed", "fp64"):
-            rate = cfg3[name]["cell_steps_per_s"]
-            gbs = BYTES_PER_STEP[name] * rate / 1e9
-            if name == "fp64":
-                a = FP64_FLOPS_PER_STEP * rate / 1e12
-                cfg3[name]["roofline"] = {"bound": "alu", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
-                                          "frac": a / fp64_peak, "peak_source": fp64_src,
-                                          "hbm_view": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm}}
-            else:
-                cfg3[name]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                          "frac": gbs / hbm, "bytes_per_cell_step": BYTES_PER_STEP[name],
-                                          "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
-                                          "l2_view": {"achieved": gbs, "peak": l2, "frac": gbs / l2}}
+        try:
+            cfg3, w3, idx3, eps3 = run_cfg3(ctx, stream, args)
+            for name in ("mixed", "fp64"):
+                rate = cfg3[name]["cell_steps_per_s"]
+                gbs = BYTES_PER_STEP[name] * rate / 1e9
+                if name == "fp64":
+                    a = FP64_FLOPS_PER_STEP * rate / 1e12
+                    cfg3[name]["roofline"] = {"bound": "alu", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
+                                              "frac": a / fp64_peak, "peak_source": fp64_src,
+                                              "hbm_view": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm}}
+                else:
+                    cfg3[name]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                              "frac": gbs / hbm, "bytes_per_cell_step": BYTES_PER_STEP[name],
+                                              "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+                                              "l2_view": {"achieved": gbs, "peak": l2, "frac": gbs / l2}}
+        except Exception as exc:   # an extra block must not cost the headline line
+            cfg3 = {"error": repr(exc)}
     cpu = None
     if not args.no_cpu_baseline:
-        cpu, ref3 = cpu_baselines(args, w, I.workload("cfg1"), w3, idx3)
-        if ref3 is not None:
-            # the oracle's endpoints of the timed sample against the GPU's on
-            # the same particles (numpy only)
-            for name in ("mixed", "fp64"):
-                cfg3[name]["accuracy"] = accuracy(w3.field, eps3[name], ref3)
+        try:
+            cpu, ref3 = cpu_baselines(args, w, I.workload("cfg1"), w3, idx3)
+            if ref3 is not None:
+                # the oracle's endpoints of the timed sample against the GPU's on
+                # the same particles (numpy only)
+                for name in ("mixed", "fp64"):
+                    cfg3[name]["accuracy"] = accuracy(w3.field, eps3[name], ref3)
+        except Exception as exc:   # an extra block must not cost the headline line
+            cpu = {"error": repr(exc)}
     f64 = results["fp64"]
     line = {
         "metric": METRIC, "value": f64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
