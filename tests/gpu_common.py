@@ -49,6 +49,8 @@ def rel_err(a, b, scale=None):
 
 def dmin(f):
     """Position scale per axis: the extent of the grid along that axis."""
+    if not hasattr(f, "delr"):   # a quadtree grid
+        return tuple(float(v) for v in f.extent)
     return (float(np.sum(f.delr)), float(np.sum(f.delc)), float(np.sum(f.dz)))
 
 

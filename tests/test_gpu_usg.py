@@ -1,7 +1,8 @@
 """Rectangular unstructured (quadtree) grids on the GPU against the oracle:
-FP64 cell sequences, statuses, steps and exit faces bit-exact, positions and
-times within 1e-10; a rectilinear grid written as an unstructured one gives
-the rectilinear GPU path's results bit for bit."""
+FP64 cell sequences, statuses, steps and exit faces bit-exact with its
+mirror arithmetic and equal (near-ties apart) with its plain arithmetic,
+positions and times within 1e-10; a rectilinear grid written as an
+unstructured one gives the rectilinear GPU path's results bit for bit."""
 import numpy as np
 import pytest
 
@@ -78,6 +79,10 @@ def test_quadtree_fp64_vs_oracle(ctx, seed, n, schedule, pass_sinks):
     G.compare_fp64(ep, ref, dmin=_dmin(u))
     G.compare_timeseries_fp64(ts, ref, dmin=_dmin(u))
     assert st["n_status"] == np.bincount(ref["status"], minlength=8).tolist()
+    # against the plain arithmetic (the reference)
+    plain = O.track(u, st0, times=times, pass_weak_sinks=pass_sinks)
+    G.compare_fp64_plain(ep, plain, field=u, state=st0, ts=ts, times=times, pass_weak_sinks=pass_sinks,
+                         label=f"quadtree {seed}")
     assert st["cell_steps"] == int(ref["steps"].astype(np.int64).sum())
     g, r = (np.sort(x, order=["particle", "seq"]) for x in (path, ref["path"]))
     assert g.size == r.size
