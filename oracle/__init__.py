@@ -116,6 +116,8 @@ def _load():
             lib.orc_log1p.restype = ctypes.c_double
             lib.orc_expm1.argtypes = [ctypes.c_double]
             lib.orc_expm1.restype = ctypes.c_double
+            lib.orc_div.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_div.restype = ctypes.c_double
             lib.orc_move.argtypes = [ctypes.c_double] * 6
             lib.orc_move.restype = ctypes.c_double
             lib.orc_exit_time_plain.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_int)]
@@ -221,6 +223,12 @@ def log1p(x):
 def expm1(w):
     """The mirror mode's table-driven expm1 (the plain mode calls the C library's)."""
     return _load().orc_expm1(float(w))
+
+
+def div(d, v):
+    """The mirror mode's quotient d / v: d times a Newton-refined reciprocal
+    (the plain mode divides in IEEE double)."""
+    return _load().orc_div(float(d), float(v))
 
 
 def move(v1, A, D, p, dt, arith=None):

@@ -135,6 +135,7 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_log1p(double x);
 double orc_expm1(double w);
+double orc_div(double d, double v);
 double orc_exit_time(double v1, double v2, double A, double iA, double D, double p, int* face);
 double orc_move(double v1, double A, double iA, double D, double p, double dt);
 double orc_exit_time_plain(double v1, double v2, double A, double D, double p, int* face);

@@ -149,6 +149,45 @@ __device__ __forceinline__ double f2d_pos(float f)
     return __longlong_as_double(((long long)(fe + 896u) << 52) | ((long long)(fb & 0x7fffffu) << 29));
 }
 
+// (double)f for f of either sign (normal, zero, infinity: on the ALU pipe)
+__device__ __forceinline__ double f2d_signed(float f)
+{
+    const double a = f2d_pos(fabsf(f));
+    return __longlong_as_double(bits(a) | (long long)((unsigned long long)(__float_as_uint(f) >> 31) << 63));
+}
+
+// fl(a b) == 0, decided on the ALU pipe from the exponents when both are
+// finite and normal and the product is clearly above or below the
+// underflow threshold 2^-1075 (the usual case), otherwise by the product
+static __device__ __noinline__ bool prod_zero_slow(double a, double b) { return eq0(a * b); }
+
+__device__ __forceinline__ bool prod_zero(double a, double b)
+{
+    const int ea = (int)((bits(a) >> 52) & 0x7ff), eb = (int)((bits(b) >> 52) & 0x7ff);
+    if ((eq0(a) && eb != 0x7ff) || (eq0(b) && ea != 0x7ff)) return true;
+    const bool normal = ea != 0 && eb != 0 && ea != 0x7ff && eb != 0x7ff;
+    if (normal && ea + eb >= 972) return false;   // |a b| >= 2^-1074
+    if (normal && ea + eb <= 969) return true;    // |a b| <  2^-1075
+    return prod_zero_slow(a, b);
+}
+
+// d / v as d times 1 / v: the IEEE FP32 reciprocal of the truncated v
+// (relative error below 1.8e-7) and two Newton steps y += y (1 - v y)
+// (each squares the error, then one rounding), so 1 / v within about half
+// an ulp and the quotient within about one.  |v| outside [2^-120, 2^121)
+// (and 0, infinity, NaN) takes the IEEE division.
+static __device__ __noinline__ double div_ieee(double a, double b) { return a / b; }
+
+__device__ __forceinline__ double f64_div(double d, double v)
+{
+    const int e = (int)((bits(v) >> 52) & 0x7ff) - 1023;
+    if (e < -120 || e > 120) return div_ieee(d, v);
+    const double y0 = f2d_signed(__frcp_rn(f32_trunc(v)));
+    const double y1 = fma(y0, fma(-v, y0, 1.0), y0);
+    const double y2 = fma(y1, fma(-v, y1, 1.0), y1);
+    return d * y2;
+}
+
 // ---------------------------------------------------------------------------
 // log1p and expm1 by argument reduction, a table and a short series, with
 // IEEE additions, multiplications and explicit fused multiply-adds in a
@@ -168,15 +207,16 @@ __device__ __forceinline__ double f2d_pos(float f)
 //     m in [1/sqrt2, sqrt2); the bucket of m (exponent and top 8 fraction
 //     bits) gives R ~ 1/m with 8 significant bits and -ln R = Lh + Ll;
 //     r = m R - 1 exactly (one fma); ln(1 + r) by its series to r^8
-//     (|r| < 0.006); (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
+//     (|r| < 0.006), the factor of r^5 in FP32 on the truncated r;
+//     (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
 //     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u.
 //     u = +inf -> +inf, u = 0 -> -inf, NaN -> NaN.
 //   expm1(w): |w| limited to 800; k = nearest integer to w 32/ln2 in FP32
 //     on the truncated w; j = k mod 32, m = (k - j) / 32;
 //     r = (w - k ln2_hi/32) - k ln2_lo/32; expm1(r) by its series to r^7
-//     (|r| < 0.0109); 2^(j/32) = Th + Tl, S = Th expm1(r) + Tl;
+//     (|r| < 0.0109), the factor of r^5 in FP32 on the truncated r; 2^(j/32) = Th + Tl, S = Th expm1(r) + Tl;
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite).  About 18 and 12 FP64 operations.
+//     2^m is not finite).  About 15 and 10 FP64 operations.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double series_log1p(double x)
@@ -201,13 +241,16 @@ __device__ __forceinline__ double series_log1p(double x)
     const double R = t0.x, Lh = t0.y, Ll = t1.x;
     const double r = fma(m, R, -1.0);
     const double r2 = r * r;
-    double p = -1.0 / 8.0;
-    p = fma(p, r, 1.0 / 7.0);
-    p = fma(p, r, -1.0 / 6.0);
-    p = fma(p, r, 1.0 / 5.0);
-    p = fma(p, r, -1.0 / 4.0);
-    p = fma(p, r, 1.0 / 3.0);
-    const double q = fma(r, p, -0.5);
+    // the series' tail 1/5 - r/6 + r^2/7 - r^3/8 in FP32: it enters scaled
+    // by r^5, below 2.6e-10 of the result, so its FP32 error stays below
+    // 0.15 ulp (and the FP64 pipe is spared three fmas)
+    const float rf = f32_trunc(r);
+    float pf = __fmaf_rn(-0x1.0p-3f, rf, 0x1.24924ap-3f);   // -1/8, 1/7
+    pf = __fmaf_rn(pf, rf, -0x1.555556p-3f);                // -1/6
+    pf = __fmaf_rn(pf, rf, 0x1.99999ap-3f);                 // 1/5
+    double q = fma(r, f2d_pos(pf), -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
     const double lg = fma(r2, q, r);
     const double de = i2d_exact(e);
     const double ru = f2d_pos(__frcp_rn(f32_rn_pos(ok ? u : 1.0)));   // (double)(1.0f / (float)u)
@@ -236,10 +279,12 @@ __device__ __forceinline__ double series_expm1(double w)
     double r = fma(-dk, ln2_hi / 32.0, wc);
     r = fma(-dk, ln2_lo / 32.0, r);
     const double r2 = r * r;
-    double p = 1.0 / 5040.0;
-    p = fma(p, r, 1.0 / 720.0);
-    p = fma(p, r, 1.0 / 120.0);
-    p = fma(p, r, 1.0 / 24.0);
+    // the tail 1/120 + r/720 + r^2/5040 in FP32: scaled by r^5 (below
+    // 1.2e-10 of the result) its FP32 error stays below 0.1 ulp
+    const float rf = f32_trunc(r);
+    float pf = __fmaf_rn(0x1.a01a02p-13f, rf, 0x1.6c16c2p-10f);   // 1/5040, 1/720
+    pf = __fmaf_rn(pf, rf, 0x1.111112p-7f);                         // 1/120
+    double p = fma(f2d_pos(pf), r, 1.0 / 24.0);
     p = fma(p, r, 1.0 / 6.0);
     p = fma(p, r, 1.0 / 2.0);
     const double em = fma(r2, p, r);
@@ -252,13 +297,13 @@ __device__ __forceinline__ double series_expm1(double w)
 
 // Exit time along one axis from the distance d to the reachable face
 // (face = +1, -1, or 0 when no face is reachable: +inf).  Written without
-// branches around the division and log1p so that the lanes of a warp stay
+// branches around the quotient and log1p so that the lanes of a warp stay
 // converged; lanes with no reachable face compute on harmless operands and
-// select +inf.  The values equal those of the branchy form (t1 = d / vp,
-// z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
+// select +inf.  The values equal those of the branchy form (t1 = d / vp by
+// f64_div, z = A t1, t1 when z == 0 else log1p(z) * (1 / A)).
 __device__ __forceinline__ double f64_exit_time_d(double A, double iA, double d, double vp, int face)
 {
-    const double t1 = d / (face ? vp : 1.0);
+    const double t1 = f64_div(d, face ? vp : 1.0);
     const double z = A * t1;
     const bool lin = eq0(z) || !face;
     const double te = lin ? t1 : series_log1p(lin ? 0.5 : z) * iA;
@@ -294,7 +339,6 @@ __device__ __forceinline__ double f64_vel(double v1, double A, double pp) { retu
 // one fma
 __device__ __forceinline__ double f64_move(double A, double iA, double D, double vp, double pp, double dt)
 {
-    const double s = vp * dt;
     const double w = A * dt;
     const bool lin = eq0(w);
     const double em = series_expm1(lin ? 0.5 : w);
@@ -302,22 +346,23 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
     double pn = fma(lin ? vp : vem, lin ? dt : iA, pp);
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
-    return eq0(s) ? pp : pn;
+    return prod_zero(vp, dt) ? pp : pn;
 }
 
-// FP32 estimate of an exit time from the exact FP64 distance d and
-// particle velocity vp.  Relative error: the two truncating conversions
-// and the approximate division give ~6e-7 on t1 = d / vp and on z = A t1;
-// g(z) = ln(1 + z) / z is evaluated by its series (|z| < 2^-7), by
-// log1pf, or for z < -1/2 by ln(u_exit / vp) (the ratio, not 1 + z,
-// carries the information there), which keeps its error below ~1.5e-6;
-// in all, below ~3.2e-6.  Velocities too small for FP32 (|vp| < 1e-30) or
-// a NaN mark the estimate as untrusted.
-__device__ __forceinline__ float f32_estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
+// FP32 estimate of an exit time from an FP32 distance d and the FP64
+// particle velocity vp.  Relative error: with d the truncated FP64
+// distance, the two truncating conversions and the approximate division
+// give ~6e-7 on t1 = d / vp and on z = A t1; g(z) = ln(1 + z) / z is
+// evaluated by its series (|z| < 2^-7), by log1pf, or for z < -1/2 by
+// ln(u_exit / vp) (the ratio, not 1 + z, carries the information there),
+// which keeps its error below ~1.5e-6; in all, below ~3.2e-6 (below ~7e-5
+// with d from f32_face_dist).  Velocities too small for FP32
+// (|vp| < 1e-30) or a NaN mark the estimate as untrusted.
+__device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, float fA, float fue, bool& unsafe)
 {
     const float vf = f32_trunc(vp);
     const float vs = face ? vf : 1.0f;
-    const float t1 = __fdividef(f32_trunc(d), vs);
+    const float t1 = __fdividef(d, vs);
     const float z = fA * t1;
     float g;
     if (fabsf(z) < 0.0078125f) g = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
@@ -326,6 +371,28 @@ __device__ __forceinline__ float f32_estimate(int face, double d, double vp, flo
     const float e = t1 * g;
     unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(e == e));
     return face ? e : CUDART_INF_F;
+}
+
+// the same from the FP64 distance
+__device__ __forceinline__ float f32_estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
+{
+    return f32_estimate_f(face, f32_trunc(d), vp, fA, fue, unsafe);
+}
+
+// FP32 distance to the reachable face for the estimates without an FP64
+// subtraction: -pp truncated, or D - pp from the truncated operands (error
+// below 2^-23 D plus one FP32 rounding, so below 6.2e-5 relative while the
+// distance is at least 2^-9 D); nearer the face (rare) the truncated FP64
+// difference, out of line
+static __device__ __noinline__ float f32_dist_near(double D, double pp) { return f32_trunc(D - pp); }
+
+__device__ __forceinline__ float f32_face_dist(int face, double D, double pp)
+{
+    const float pf = f32_trunc(pp);
+    if (face <= 0) return -pf;
+    const float Df = f32_trunc(D);
+    const float d = Df - pf;
+    return d >= Df * 0x1.0p-9f ? d : f32_dist_near(D, pp);
 }
 
 }  // namespace mp

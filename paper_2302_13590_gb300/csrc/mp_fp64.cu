@@ -324,9 +324,9 @@ struct F64Engine {
         return a == 0 ? x : (a == 1 ? y : z);
     }
 
-    __device__ __forceinline__ static float estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
+    __device__ __forceinline__ static float estimate(int face, float d, double vp, float fA, float fue, bool& unsafe)
     {
-        return f32_estimate(face, d, vp, fA, fue, unsafe);
+        return f32_estimate_f(face, d, vp, fA, fue, unsafe);
     }
 
     __device__ __forceinline__ static double move(double A, double iA, double D, double vp, double pp, double dt)
@@ -514,16 +514,14 @@ struct F64Engine {
                 f0 = face_of(vp0, p2x, n1x);
                 f1 = face_of(vp1, p2y, n1y);
                 f2 = face_of(vp2, p2z, n1z);
-                // signed distances to the reachable faces (shared by the
-                // estimates and the exact evaluations)
-                const double d0 = f64_face_dist(f0, D0, s.x0), d1 = f64_face_dist(f1, D1, s.x1),
-                             d2 = f64_face_dist(f2, D2, s.x2);
+                // estimates from FP32 distances to the reachable faces (the
+                // FP64 distance is formed for the axes evaluated exactly)
                 bool u0, u1, u2;
-                const float e0 = estimate(f0, d0, vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
-                const float e1 = estimate(f1, d1, vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
-                const float e2 = estimate(f2, d2, vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
+                const float e0 = estimate(f0, f32_face_dist(f0, D0, s.x0), vp0, g0.z, f0 > 0 ? g0.y : g0.x, u0);
+                const float e1 = estimate(f1, f32_face_dist(f1, D1, s.x1), vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
+                const float e2 = estimate(f2, f32_face_dist(f2, D2, s.x2), vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
                 // candidates: every axis whose estimate is within 2^-10 of the
-                // smallest (the estimates are within ~3e-6 of the exact times),
+                // smallest (the estimates are within ~7e-5 of the exact times),
                 // and every axis whose estimate cannot be trusted
                 float em = CUDART_INF_F;
                 int a0 = -1;
@@ -538,9 +536,11 @@ struct F64Engine {
                 if (a0 >= 0) {
                     // the exact FP64 exit time of the leading candidate (one
                     // evaluation per lane, uniform across the warp)
-                    const double te = f64_exit_time_d(sel3(a0, Ax, Ay, Az), sel3(a0, iAx, iAy, iAz),
-                                                      sel3(a0, d0, d1, d2), sel3(a0, vp0, vp1, vp2),
-                                                      sel3(a0, f0, f1, f2));
+                    const int fa0 = sel3(a0, f0, f1, f2);
+                    const double te = f64_exit_time_d(
+                        sel3(a0, Ax, Ay, Az), sel3(a0, iAx, iAy, iAz),
+                        f64_face_dist(fa0, sel3(a0, D0, D1, D2), sel3(a0, s.x0, s.x1, s.x2)),
+                        sel3(a0, vp0, vp1, vp2), fa0);
                     // then the other candidates exactly (a close call; every
                     // reachable axis when the leading time is unusable): the
                     // smallest time wins, ties to the lower axis - the
@@ -556,9 +556,11 @@ struct F64Engine {
                     while (rest) {
                         const int a = __ffs(rest) - 1;
                         rest &= rest - 1;
-                        const double t = f64_exit_time_d(sel3(a, Ax, Ay, Az), sel3(a, iAx, iAy, iAz),
-                                                         sel3(a, d0, d1, d2), sel3(a, vp0, vp1, vp2),
-                                                         sel3(a, f0, f1, f2));
+                        const int fa = sel3(a, f0, f1, f2);
+                        const double t = f64_exit_time_d(
+                            sel3(a, Ax, Ay, Az), sel3(a, iAx, iAy, iAz),
+                            f64_face_dist(fa, sel3(a, D0, D1, D2), sel3(a, s.x0, s.x1, s.x2)),
+                            sel3(a, vp0, vp1, vp2), fa);
                         if (t < tmin || (t == tmin && a < ax)) {
                             tmin = t;
                             ax = a;

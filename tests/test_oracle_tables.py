@@ -189,3 +189,33 @@ def test_expm1_within_two_ulp_for_every_j():
     for w in (709.5, 709.78, 709.782):
         assert O.expm1(w) == float(mpmath.expm1(mpmath.mpf(w)))
     assert O.expm1(709.8) == math.inf and O.expm1(1e300) == math.inf and O.expm1(-1e300) == -1.0
+
+
+def test_quotient_within_one_ulp():
+    """The mirror quotient d / v (the single-precision IEEE reciprocal of the
+    truncated v, two Newton steps, one product) is within one ulp of the
+    correctly rounded quotient over the range of v it serves, exact where
+    1 / v is a power of two, and outside that range (|v| < 2^-120 or
+    >= 2^121, zero, infinity, NaN) it is the IEEE division."""
+    rng = np.random.default_rng(3)
+    n = 20000
+    v = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-120, 121, n)) * rng.choice([-1.0, 1.0], n)
+    d = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-60, 60, n)) * rng.choice([-1.0, 1.0], n)
+    v[:200] = np.ldexp(1.0, rng.integers(-120, 121, 200)) * rng.choice([-1.0, 1.0], 200)
+    worst = 0.0
+    exact = 0
+    for a, b in zip(d, v):
+        q, ref = O.div(a, b), a / b
+        worst = max(worst, abs(q - ref) / np.spacing(abs(ref)))
+        exact += q == ref
+    assert worst <= 1.0
+    assert exact >= 0.7 * n          # measured: 73 %
+    assert all(O.div(a, b) == a / b for a, b in zip(d[:200], v[:200]))
+    with np.errstate(all="ignore"):
+        for b in [2.0 ** -121, -(2.0 ** -121) * 1.5, 2.0 ** 121, -(2.0 ** 125), 5e-324, 0.0, -0.0, math.inf,
+                  -math.inf, math.nan]:
+            for a in [1.7, -3.25, 0.0]:
+                q, ref = O.div(a, b), float(np.float64(a) / np.float64(b))
+                assert (q == ref and math.copysign(1, q) == math.copysign(1, ref)) or (math.isnan(q) and math.isnan(ref))
+    # signed zeros as the division gives them
+    assert math.copysign(1, O.div(0.0, -3.0)) == -1 and math.copysign(1, O.div(-0.0, -3.0)) == 1
