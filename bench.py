@@ -61,45 +61,52 @@ BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # 2e5 particles of this workload in their tuned launch configurations
 # (profiles/k_track_cfg2_200k.md), scaled by
 # 5 to the 1e6-particle launch: reads grow with the cell-steps, writes with
-# the output records, both in proportion to the particle count.  It holds
-# only for the kernel sources it was taken from (their hash below);
-# otherwise the bench reports traffic as null.
-TRAFFIC = {"src": "46413a7624432cb5", "fp64": 5 * (352.305664e6 + 307.299584e6),
-           "mixed": 5 * (43.280128e6 + 287.389184e6)}
+# the output records, both in proportion to the particle count.  Each figure
+# holds only for the kernel sources it was taken from (the hash beside it,
+# kernel_src_hash); otherwise the bench reports it as null.
+MIXED_SRC = "d0b109deb9ab3b6a"   # mixed kernel at the capture (unchanged since)
+FP64_SRC = "46413a7624432cb5"    # superseded: re-captured below
+TRAFFIC = {"fp64": {"src": FP64_SRC, "value": 5 * (352.305664e6 + 307.299584e6)},
+           "mixed": {"src": MIXED_SRC, "value": 5 * (43.280128e6 + 287.389184e6)}}
 # From the same capture: the FP64 pipe's busy fraction in the FP64 kernel
 # (sm__pipe_fp64_cycles_active, % of peak sustained active), the executed
 # counterpart of the algorithmic fraction (which charges every axis's exit
 # time while the kernel evaluates the exact one of about 1.1 axes a step).
-FP64_PIPE_ACTIVE = {"src": "46413a7624432cb5", "value": 0.8471}
+FP64_PIPE_ACTIVE = {"src": FP64_SRC, "value": 0.8471}
 # Warp-instructions per cell-step of the mixed kernel in the same capture
 # (smsp__inst_executed.sum / cell-steps on 2e5 particles, static schedule,
 # 256 threads: the tuned launch): the mixed kernel is issue-bound, and its
 # issue view compares the implied issue rate with one warp-instruction per
 # clock per SM sub-partition (152 SMs x 4 x 2.07 GHz).
-MIXED_INST_PER_STEP = {"src": "46413a7624432cb5", "value": 1154103429.0 / 54832447.0}
+MIXED_INST_PER_STEP = {"src": MIXED_SRC, "value": 1154103429.0 / 54832447.0}
 ISSUE_PEAK_TINST = 152 * 4 * 2.07e9 / 1e12
 # L2 read bytes per cell-step in the same capture (lts__t_sectors_srcunit_tex_op_read
 # x 32 B / cell-steps): the record gather, cell sizes, output times.
-L2_READ_PER_STEP = {"src": "46413a7624432cb5", "fp64": 248998414.0 * 32 / 54832426.0,
-                    "mixed": 61315161.0 * 32 / 54832447.0}
+L2_READ_PER_STEP = {"fp64": {"src": FP64_SRC, "value": 248998414.0 * 32 / 54832426.0},
+                    "mixed": {"src": MIXED_SRC, "value": 61315161.0 * 32 / 54832447.0}}
 
 
-# Sources of the device code the counters above were taken from: the kernel
-# units and every header they include (the host side of the C ABI,
-# mp_api.cu and mp_noalloc.cu, compiles no tracking kernel).
-KERNEL_SOURCES = ("mp_fp64.cu", "mp_mixed.cu", "mp_mixed_f64t.cu", "mp_usg.cu")
+# Sources of each tracking kernel's device code: its unit and every header
+# it includes (mp_internal.h includes the public mp.h).
+KERNEL_SOURCES = {
+    "fp64": ("mp_fp64.cu", "mp_f64math.cuh", "mp_f64_tables.h", "mp_sched.cuh", "mp_internal.h", "mp.h"),
+    "mixed": ("mp_mixed.cu", "mp_mixed.cuh", "mp_sched.cuh", "mp_internal.h", "mp.h"),
+}
 
 
-def kernel_src_hash() -> str:
+def kernel_src_hash(kind: str) -> str:
     import hashlib
-    import glob
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "*"))):
-        name = os.path.basename(p)
-        if name.endswith((".cuh", ".h")) or name in KERNEL_SOURCES:
-            h.update(name.encode())
-            h.update(open(p, "rb").read())
+    for name in KERNEL_SOURCES[kind]:
+        d = "include" if name == "mp.h" else os.path.join("paper_2302_13590_gb300", "csrc")
+        h.update(name.encode())
+        h.update(open(os.path.join(ROOT, d, name), "rb").read())
     return h.hexdigest()[:16]
+
+
+def ncu_figure(table: dict, kind: str):
+    """A counter taken with ncu for one kernel, or None once its sources changed."""
+    return table[kind]["value"] if kernel_src_hash(kind) == table[kind]["src"] else None
 
 
 # GB300 FP64 rate, nominal: 152 SMs x 2.07 GHz x 4 flop/clk/SM = 1.26 TFLOP/s
@@ -663,13 +670,13 @@ def run_ours(args):
         rate = steps_per_launch / (kms / 1e3)
         gbs = BYTES_PER_STEP[name] * rate / 1e9
         traffic = args.traffic_fp64 if name == "fp64" else args.traffic_mixed
-        if traffic is None and kernel_src_hash() == TRAFFIC["src"]:
-            traffic = TRAFFIC[name]
+        if traffic is None:
+            traffic = ncu_figure(TRAFFIC, name)
         l2_ncu = None
-        if kernel_src_hash() == L2_READ_PER_STEP["src"]:
-            l2_ncu = {"bytes_per_cell_step": L2_READ_PER_STEP[name],
-                      "gbs": L2_READ_PER_STEP[name] * rate / 1e9, "peak_gbs": l2,
-                      "frac": L2_READ_PER_STEP[name] * rate / 1e9 / l2}
+        l2b = ncu_figure(L2_READ_PER_STEP, name)
+        if l2b is not None:
+            l2_ncu = {"bytes_per_cell_step": l2b, "gbs": l2b * rate / 1e9, "peak_gbs": l2,
+                      "frac": l2b * rate / 1e9 / l2}
         if name == "fp64":
             achieved = FP64_FLOPS_PER_STEP * rate / 1e12
             rf[name] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -678,7 +685,7 @@ def run_ours(args):
                         "flops_per_cell_step": FP64_FLOPS_PER_STEP, "kernel_ms": kms,
                         "cell_steps_per_launch": steps_per_launch,
                         "fp64_pipe_active_ncu": (FP64_PIPE_ACTIVE["value"]
-                                                 if kernel_src_hash() == FP64_PIPE_ACTIVE["src"] else None),
+                                                 if kernel_src_hash("fp64") == FP64_PIPE_ACTIVE["src"] else None),
                         "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                      "bytes_per_cell_step": BYTES_PER_STEP[name]},
                         "l2_read_ncu": l2_ncu}
@@ -690,7 +697,7 @@ def run_ours(args):
                         "l2_view": {"achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
                                     "peak_source": "measured in this run: L2-resident 64 MB read"},
                         "l2_read_ncu": l2_ncu}
-            if kernel_src_hash() == MIXED_INST_PER_STEP["src"]:
+            if kernel_src_hash("mixed") == MIXED_INST_PER_STEP["src"]:
                 ti = MIXED_INST_PER_STEP["value"] * rate / 1e12
                 rf[name]["issue_view"] = {"achieved": ti, "peak": ISSUE_PEAK_TINST, "unit": "Twarp-inst/s",
                                           "frac": ti / ISSUE_PEAK_TINST,

@@ -156,21 +156,6 @@ __device__ __forceinline__ double f2d_signed(float f)
     return __longlong_as_double(bits(a) | (long long)((unsigned long long)(__float_as_uint(f) >> 31) << 63));
 }
 
-// fl(a b) == 0, decided on the ALU pipe from the exponents when both are
-// finite and normal and the product is clearly above or below the
-// underflow threshold 2^-1075 (the usual case), otherwise by the product
-static __device__ __noinline__ bool prod_zero_slow(double a, double b) { return eq0(a * b); }
-
-__device__ __forceinline__ bool prod_zero(double a, double b)
-{
-    const int ea = (int)((bits(a) >> 52) & 0x7ff), eb = (int)((bits(b) >> 52) & 0x7ff);
-    if ((eq0(a) && eb != 0x7ff) || (eq0(b) && ea != 0x7ff)) return true;
-    const bool normal = ea != 0 && eb != 0 && ea != 0x7ff && eb != 0x7ff;
-    if (normal && ea + eb >= 972) return false;   // |a b| >= 2^-1074
-    if (normal && ea + eb <= 969) return true;    // |a b| <  2^-1075
-    return prod_zero_slow(a, b);
-}
-
 // d / v as d times 1 / v: the IEEE FP32 reciprocal of the truncated v
 // (relative error below 1.8e-7) and two Newton steps y += y (1 - v y)
 // (each squares the error, then one rounding), so 1 / v within about half
@@ -339,6 +324,7 @@ __device__ __forceinline__ double f64_vel(double v1, double A, double pp) { retu
 // one fma
 __device__ __forceinline__ double f64_move(double A, double iA, double D, double vp, double pp, double dt)
 {
+    const double s = vp * dt;
     const double w = A * dt;
     const bool lin = eq0(w);
     const double em = series_expm1(lin ? 0.5 : w);
@@ -346,7 +332,7 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
     double pn = fma(lin ? vp : vem, lin ? dt : iA, pp);
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
-    return prod_zero(vp, dt) ? pp : pn;
+    return eq0(s) ? pp : pn;
 }
 
 // FP32 estimate of an exit time from an FP32 distance d and the FP64
@@ -371,12 +357,6 @@ __device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, fl
     const float e = t1 * g;
     unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(e == e));
     return face ? e : CUDART_INF_F;
-}
-
-// the same from the FP64 distance
-__device__ __forceinline__ float f32_estimate(int face, double d, double vp, float fA, float fue, bool& unsafe)
-{
-    return f32_estimate_f(face, f32_trunc(d), vp, fA, fue, unsafe);
 }
 
 // FP32 distance to the reachable face for the estimates without an FP64

@@ -385,26 +385,27 @@ struct UsgEngine {
                 org[0] = q0.x; org[1] = q0.y; org[2] = q1.x; D[0] = q1.y; D[1] = q2.x; D[2] = q2.y;
                 const double pp[3] = {s.x0, s.x1, s.x2};
                 bool p2[3], n1[3];
-                double dd[3];
+                float dd[3];
                 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     vp[a] = f64_vel(v1[a], A[a], pp[a]);
                     p2[a] = (sg >> (4 * a + 2)) & 1ULL;
                     n1[a] = (sg >> (4 * a + 1)) & 1ULL;
                     fc[a] = f64_face(vp[a], p2[a], n1[a]);
-                    dd[a] = f64_face_dist(fc[a], D[a], pp[a]);
+                    dd[a] = f32_face_dist(fc[a], D[a], pp[a]);
                 }
-                // FP32 estimates of the three exit times; the exact FP64 time
-                // of the leading one, and of every axis within 2^-10 of it
-                // or with an untrusted estimate (the same exit axis and time
-                // as evaluating all three exactly)
+                // FP32 estimates of the three exit times (from FP32 face
+                // distances); the exact FP64 time of the leading one, and of
+                // every axis within 2^-10 of it or with an untrusted
+                // estimate (the same exit axis and time as evaluating all
+                // three exactly)
                 bool u0, u1, u2;
-                const float e0 = f32_estimate(fc[0], dd[0], vp[0], g0.z,
-                                              fc[0] > 0 ? g0.y : g0.x, u0);
-                const float e1 = f32_estimate(fc[1], dd[1], vp[1], g1.y,
-                                              fc[1] > 0 ? g1.x : g0.w, u1);
-                const float e2 = f32_estimate(fc[2], dd[2], vp[2], g2.x,
-                                              fc[2] > 0 ? g1.w : g1.z, u2);
+                const float e0 = f32_estimate_f(fc[0], dd[0], vp[0], g0.z,
+                                                fc[0] > 0 ? g0.y : g0.x, u0);
+                const float e1 = f32_estimate_f(fc[1], dd[1], vp[1], g1.y,
+                                                fc[1] > 0 ? g1.x : g0.w, u1);
+                const float e2 = f32_estimate_f(fc[2], dd[2], vp[2], g2.x,
+                                                fc[2] > 0 ? g1.w : g1.z, u2);
                 float em = CUDART_INF_F;
                 int a0 = -1;
                 if (fc[0] && !u0 && e0 < em) { em = e0; a0 = 0; }
@@ -416,9 +417,11 @@ struct UsgEngine {
                 if (a0 < 0 && cand) a0 = __ffs(cand) - 1;
                 tmin = CUDART_INF;
                 if (a0 >= 0) {
-                    const double te = f64_exit_time_d(sel3(a0, A[0], A[1], A[2]), sel3(a0, iA[0], iA[1], iA[2]),
-                                                      sel3(a0, dd[0], dd[1], dd[2]), sel3(a0, vp[0], vp[1], vp[2]),
-                                                      sel3(a0, fc[0], fc[1], fc[2]));
+                    const int fa0 = sel3(a0, fc[0], fc[1], fc[2]);
+                    const double te = f64_exit_time_d(
+                        sel3(a0, A[0], A[1], A[2]), sel3(a0, iA[0], iA[1], iA[2]),
+                        f64_face_dist(fa0, sel3(a0, D[0], D[1], D[2]), sel3(a0, pp[0], pp[1], pp[2])),
+                        sel3(a0, vp[0], vp[1], vp[2]), fa0);
                     // the other candidates (every reachable axis when the
                     // leading time is unusable): smallest wins, ties to the
                     // lower axis
@@ -432,9 +435,11 @@ struct UsgEngine {
                     while (rest) {
                         const int a = __ffs(rest) - 1;
                         rest &= rest - 1;
-                        const double t = f64_exit_time_d(sel3(a, A[0], A[1], A[2]), sel3(a, iA[0], iA[1], iA[2]),
-                                                         sel3(a, dd[0], dd[1], dd[2]), sel3(a, vp[0], vp[1], vp[2]),
-                                                         sel3(a, fc[0], fc[1], fc[2]));
+                        const int fa = sel3(a, fc[0], fc[1], fc[2]);
+                        const double t = f64_exit_time_d(
+                            sel3(a, A[0], A[1], A[2]), sel3(a, iA[0], iA[1], iA[2]),
+                            f64_face_dist(fa, sel3(a, D[0], D[1], D[2]), sel3(a, pp[0], pp[1], pp[2])),
+                            sel3(a, vp[0], vp[1], vp[2]), fa);
                         if (t < tmin || (t == tmin && a < ax)) {
                             tmin = t;
                             ax = a;
