@@ -19,7 +19,15 @@ namespace mp {
 // gives exactly the IEEE result for the non-NaN operands the path produces.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
+// The representation of v, opaque to the optimiser (an empty asm): without
+// it the compiler folds tests such as (bits << 1) == 0 back into FP64
+// compares, which run on the FP64 pipe.
+__device__ __forceinline__ long long bits(double v)
+{
+    long long b = __double_as_longlong(v);
+    asm("" : "+l"(b));
+    return b;
+}
 // v > 0
 __device__ __forceinline__ bool gt0(double v) { return bits(v) > 0LL; }
 // v < 0 (-0 is not)
@@ -68,9 +76,11 @@ __device__ __forceinline__ double frexp_bits(double u, int& e)
         e = 0;
         return u;
     }
-    if (ex == 0) {   // subnormal: scale by 2^54 (exact)
-        b = bits(u * 18014398509481984.0);
-        ex = (int)((b >> 52) & 0x7ff) - 54;
+    if (ex == 0) {   // subnormal: normalise the fraction (nonzero here) on the integer side
+        const unsigned long long fr = (unsigned long long)b & 0x000fffffffffffffULL;
+        const int sh = __clzll((long long)fr) - 11;   // brings the leading 1 to bit 52
+        b = (b & (long long)0x8000000000000000ULL) | (long long)((fr << sh) & 0x000fffffffffffffULL);
+        ex = 1 - sh;
     }
     e = ex - 1022;
     return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | 0x3fe0000000000000LL);
@@ -241,8 +251,10 @@ __device__ __forceinline__ double series_log1p(double x)
     const double ru = f2d_pos(__frcp_rn(f32_rn_pos(ok ? u : 1.0)));   // (double)(1.0f / (float)u)
     const double hi = fma(de, ln2_hi, Lh);
     const double lo = fma(c, ru, lg) + fma(de, ln2_lo, Ll);
-    const double special = eq0(u) ? -CUDART_INF : (ub == 0x7ff0000000000000LL ? CUDART_INF : CUDART_NAN);
-    return ok ? hi + lo : special;
+    const long long special = eq0(u) ? (long long)0xfff0000000000000ULL
+                                     : (ub == 0x7ff0000000000000LL ? 0x7ff0000000000000LL
+                                                                   : (long long)0xfff8000000000000ULL);
+    return __longlong_as_double(ok ? bits(hi + lo) : special);   // -inf, +inf, NaN
 }
 
 // expm1 where 2^m overflows (w > ~709.4); kept out of line
@@ -254,7 +266,10 @@ static __device__ __noinline__ double expm1_big(double Th, double S, int m)
 __device__ __forceinline__ double series_expm1(double w)
 {
     const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double wc = (abs_lt(w, 800.0) || is_nan(w)) ? w : (lt0(w) ? -800.0 : 800.0);
+    const double wc = __longlong_as_double((abs_lt(w, 800.0) || is_nan(w))
+                                               ? bits(w)
+                                               : (lt0(w) ? (long long)0xc089000000000000ULL    // -800
+                                                         : 0x4089000000000000LL));             // 800
     const float y = __fmul_rn(f32_trunc(wc), 46.16624069213867f);   // 32/ln2 in FP32
     const float sh = __fadd_rn(y, 12582912.0f);                      // rounds y to an integer
     const int k = (int)__float_as_uint(sh) - 0x4b400000;
