@@ -318,8 +318,9 @@ double orc_exit_time(double v1, double v2, double A, double iA, double D, double
 double orc_move(double v1, double A, double iA, double D, double p, double dt)
 {
     double vp = fma(A, p, v1);
-    double s = vp * dt;
-    if (s == 0.0) return p;
+    /* no motion when vp or dt is zero (the plain mode tests the product,
+     * which differs only where vp dt underflows) */
+    if (vp == 0.0 || dt == 0.0) return p;
     double w = A * dt;
     double pn = (w == 0.0) ? fma(vp, dt, p) : fma(vp * orc_expm1(w), iA, p);
     if (pn < 0.0) pn = 0.0;

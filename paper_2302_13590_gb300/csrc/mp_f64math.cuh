@@ -333,13 +333,13 @@ __device__ __forceinline__ double f64_exit_time(double A, double iA, double D, d
 __device__ __forceinline__ double f64_vel(double v1, double A, double pp) { return fma(A, pp, v1); }
 
 // analytic motion along one axis for a time dt, clamped to the cell
-// (the same values as: vp dt == 0 -> pp; w == 0 -> pp + vp dt in one fma;
+// (the same values as: vp == 0 or dt == 0 -> pp; w == 0 -> pp + vp dt in one fma;
 // else pp + (vp * expm1(w)) * (1 / A), the last product and sum in one
 // fma); the operands are selected, so every lane issues one product and
 // one fma
 __device__ __forceinline__ double f64_move(double A, double iA, double D, double vp, double pp, double dt)
 {
-    const double s = vp * dt;
+    const bool still = eq0(vp) || eq0(dt);
     const double w = A * dt;
     const bool lin = eq0(w);
     const double em = series_expm1(lin ? 0.5 : w);
@@ -347,7 +347,7 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
     double pn = fma(lin ? vp : vem, lin ? dt : iA, pp);
     pn = lt0(pn) ? 0.0 : pn;
     pn = gt_pos(pn, D) ? D : pn;
-    return eq0(s) ? pp : pn;
+    return still ? pp : pn;
 }
 
 // FP32 estimate of an exit time from an FP32 distance d and the FP64
