@@ -11,11 +11,11 @@ computed here in exact integer fixed-point arithmetic (2^-256 units):
   R = 1/c rounded to 8 significant bits (nearest, ties to even);
   Lh = -ln R rounded to the nearest multiple of 2^-32; Ll = -ln R - Lh
   rounded to the nearest double.
-* exponential table, j = 0..31: Th = 2^(j/32) rounded to the nearest
-  double, Tl = 2^(j/32) - Th rounded to the nearest double.
+* exponential table, j = 0..255: Th = 2^(j/256) rounded to the nearest
+  double, Tl = 2^(j/256) - Th rounded to the nearest double.
 
 ln is evaluated as 2 atanh((a - b) / (a + b)) for R = a / b by its odd
-series; 2^(j/32) as the integer 32nd root of 2^(j + 32 P).
+series; 2^(j/256) as the integer 256th root of 2^(j + 256 P).
 
 Run: python oracle/gen_tables.py   (rewrites the header next to this file)
 """
@@ -27,7 +27,7 @@ from fractions import Fraction
 P = 256                      # fixed-point fraction bits
 KEY0 = (1022 << 8) + 106     # first bucket: exponent of 0.5, fraction bits 106/256
 N_LOG = 257
-N_EXP = 32
+N_EXP = 256
 
 
 def rn53(num: int, scale: int) -> float:
@@ -116,7 +116,7 @@ def log_table():
 def exp_table():
     rows = []
     for j in range(N_EXP):
-        T = iroot(1 << (j + 32 * P), 32)          # floor(2^(j/32) 2^P)
+        T = iroot(1 << (j + N_EXP * P), N_EXP)    # floor(2^(j/256) 2^P)
         Th = rn53(T, P)
         Tl = rn53(T - int(Fraction(Th) * (1 << P)), P)
         rows.append((Th, Tl))

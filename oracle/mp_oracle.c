@@ -257,25 +257,23 @@ double orc_expm1(double w)
 {
     double wc = w;
     if (fabs(w) > 800.0) wc = w < 0.0 ? -800.0 : 800.0;
-    float y = orc_f32_trunc(wc) * 46.16624069213867f;     /* 32/ln2 rounded to FP32 */
+    float y = orc_f32_trunc(wc) * 0x1.715476p+8f;          /* 256/ln2 rounded to FP32 */
     float sh = y + 12582912.0f;                            /* 1.5 2^23: rounds y to an integer */
     uint32_t sb;
     memcpy(&sb, &sh, sizeof sb);
     int k = (int)sb - 0x4b400000;
-    int j = k & 31;
-    int m = (k - j) / 32;
+    int j = k & 255;
+    int m = (k - j) / 256;
     double dk = (double)k;
-    double r = fma(-dk, ORC_LN2_HI / 32.0, wc);
-    r = fma(-dk, ORC_LN2_LO / 32.0, r);
+    double r = fma(-dk, ORC_LN2_HI / 256.0, wc);
+    r = fma(-dk, ORC_LN2_LO / 256.0, r);
     double r2 = r * r;
-    /* e^r - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r P))), with
-     * P = 1/120 + r/720 + r^2/5040 in single precision on the truncated r:
-     * scaled by r^5 (|r| < 0.0109) its error stays below 0.1 ulp */
-    float rf = orc_f32_trunc(r);
-    float pf = fmaf(0x1.a01a02p-13f, rf, 0x1.6c16c2p-10f);   /* 1/5040, 1/720 */
-    pf = fmaf(pf, rf, 0x1.111112p-7f);                        /* 1/120 */
-    double p = fma((double)pf, r, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    /* e^r - 1 = r + r^2 (1/2 + r (1/6 + r P)) to r^5 (|r| < 0.0016: the
+     * next term is below 1.5e-17 of the result), with P = 1/24 + r/120 in
+     * single precision on the truncated r: scaled by r^4 its error stays
+     * below 0.1 ulp */
+    float pf = fmaf(0x1.111112p-7f, orc_f32_trunc(r), 0x1.555556p-5f);   /* 1/120, 1/24 */
+    double p = fma((double)pf, r, 1.0 / 6.0);
     p = fma(p, r, 1.0 / 2.0);
     double em = fma(r2, p, r);
     double Th = orc_from_bits(orc_exp_tab[j][0]);

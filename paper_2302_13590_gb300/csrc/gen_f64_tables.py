@@ -13,8 +13,8 @@ rounded exactly to the binary format:
   rounded to the nearest double.  With 8-bit R, m * R - 1 is a multiple of
   2^-60 below 2^-7 in magnitude, so one fused multiply-add gives it exactly;
   with Lh and e * ln2_hi both multiples of 2^-32, their sum is exact.
-* exponential table, j = 0..31: Th = 2^(j/32) and Tl = 2^(j/32) - Th, each
-  rounded to the nearest double.
+* exponential table, j = 0..255: Th = 2^(j/256) and Tl = 2^(j/256) - Th,
+  each rounded to the nearest double.
 
 Run: python gen_f64_tables.py   (rewrites the header next to this file)
 """
@@ -26,7 +26,7 @@ from fractions import Fraction
 
 KEY0 = (1022 << 8) + 106
 N_LOG = 257
-N_EXP = 32
+N_EXP = 256
 
 
 def _round_to(x: Fraction, unit: Fraction) -> Fraction:
@@ -65,7 +65,7 @@ def tables():
         logs.append((float(R), float(Lh), float(L - Lh)))
     exps = []
     for j in range(N_EXP):
-        T = Fraction(ctx.power(Decimal(2), ctx.divide(Decimal(j), Decimal(32))))
+        T = Fraction(ctx.power(Decimal(2), ctx.divide(Decimal(j), Decimal(N_EXP))))
         Th = float(T)
         exps.append((Th, float(T - Fraction(Th))))
     return logs, exps

@@ -206,12 +206,13 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
 //     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u.
 //     u = +inf -> +inf, u = 0 -> -inf, NaN -> NaN.
-//   expm1(w): |w| limited to 800; k = nearest integer to w 32/ln2 in FP32
-//     on the truncated w; j = k mod 32, m = (k - j) / 32;
-//     r = (w - k ln2_hi/32) - k ln2_lo/32; expm1(r) by its series to r^7
-//     (|r| < 0.0109), the factor of r^5 in FP32 on the truncated r; 2^(j/32) = Th + Tl, S = Th expm1(r) + Tl;
+//   expm1(w): |w| limited to 800; k = nearest integer to w 256/ln2 in FP32
+//     on the truncated w; j = k mod 256, m = (k - j) / 256;
+//     r = (w - k ln2_hi/256) - k ln2_lo/256; expm1(r) by its series to r^5
+//     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r;
+//     2^(j/256) = Th + Tl, S = Th expm1(r) + Tl;
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite).  About 15 and 10 FP64 operations.
+//     2^m is not finite).  About 14 and 9 FP64 operations.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double series_log1p(double x)
@@ -270,25 +271,23 @@ __device__ __forceinline__ double series_expm1(double w)
                                                ? bits(w)
                                                : (lt0(w) ? (long long)0xc089000000000000ULL    // -800
                                                          : 0x4089000000000000LL));             // 800
-    const float y = __fmul_rn(f32_trunc(wc), 46.16624069213867f);   // 32/ln2 in FP32
-    const float sh = __fadd_rn(y, 12582912.0f);                      // rounds y to an integer
+    const float y = __fmul_rn(f32_trunc(wc), 0x1.715476p+8f);   // 256/ln2 in FP32
+    const float sh = __fadd_rn(y, 12582912.0f);                  // rounds y to an integer
     const int k = (int)__float_as_uint(sh) - 0x4b400000;
-    const int j = k & 31;
-    const int m = (k - j) >> 5;
+    const int j = k & 255;
+    const int m = (k - j) >> 8;
     const double dk = i2d_exact(k);
-    double r = fma(-dk, ln2_hi / 32.0, wc);
-    r = fma(-dk, ln2_lo / 32.0, r);
+    double r = fma(-dk, ln2_hi / 256.0, wc);
+    r = fma(-dk, ln2_lo / 256.0, r);
     const double r2 = r * r;
-    // the tail 1/120 + r/720 + r^2/5040 in FP32: scaled by r^5 (below
-    // 1.2e-10 of the result) its FP32 error stays below 0.1 ulp
-    const float rf = f32_trunc(r);
-    float pf = __fmaf_rn(0x1.a01a02p-13f, rf, 0x1.6c16c2p-10f);   // 1/5040, 1/720
-    pf = __fmaf_rn(pf, rf, 0x1.111112p-7f);                         // 1/120
-    double p = fma(f2d_pos(pf), r, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    // the factor of r^4, 1/24 + r/120 (the series' next term is below
+    // 1.5e-17 of the result), in FP32: scaled by r^4 (below 1.7e-10 of the
+    // result) its FP32 error stays below 0.1 ulp
+    const float pf = __fmaf_rn(0x1.111112p-7f, f32_trunc(r), 0x1.555556p-5f);   // 1/120, 1/24
+    double p = fma(f2d_pos(pf), r, 1.0 / 6.0);
     p = fma(p, r, 1.0 / 2.0);
     const double em = fma(r2, p, r);
-    const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);
+    const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);   // 2^(j/256)
     const double S = fma(T.x, em, T.y);
     if (m > 1023) return expm1_big(T.x, S, m);
     const double t = pow2i(m < -2000 ? -2000 : m);

@@ -35,12 +35,15 @@ def _d(b):
     return struct.unpack("<d", struct.pack("<Q", b))[0]
 
 
+N_EXP = 256                  # entries 2^(j/256) of the exponential table
+
+
 def _read(path, per_log):
     words = [int(x, 16) for x in re.findall(r"0x([0-9a-f]{16})ULL", open(path).read())]
     n_log = 257 * per_log
     log = [tuple(_d(w) for w in words[i:i + 3]) for i in range(0, n_log, per_log)]
-    exp = [(_d(words[n_log + 2 * j]), _d(words[n_log + 2 * j + 1])) for j in range(32)]
-    assert len(words) == n_log + 64
+    exp = [(_d(words[n_log + 2 * j]), _d(words[n_log + 2 * j + 1])) for j in range(N_EXP)]
+    assert len(words) == n_log + 2 * N_EXP
     return log, exp
 
 
@@ -77,8 +80,8 @@ def _expected():
         Lh = mpmath.nint(L * 2 ** 32) / 2 ** 32
         log.append((float(R), float(Lh), float(L - Lh)))
     exp = []
-    for j in range(32):
-        T = mpmath.power(2, mpmath.mpf(j) / 32)
+    for j in range(N_EXP):
+        T = mpmath.power(2, mpmath.mpf(j) / N_EXP)
         Th = float(T)
         exp.append((Th, float(T - Th)))
     return log, exp
@@ -133,17 +136,19 @@ def _f32_trunc(x):
 
 def test_exp_reduction_bound():
     mpmath.mp.prec = 200
-    ln2_32 = mpmath.log(2) / 32
+    ln2_n = mpmath.log(2) / N_EXP
     rng = np.random.default_rng(4)
-    edges = [(k + 0.5) * math.log(2) / 32 for k in range(-36934, 36934, 977)]
+    edges = [(k + 0.5) * math.log(2) / N_EXP for k in range(-295464, 295464, 7817)]
     ws = list(rng.uniform(-800, 800, 3000)) + edges + [math.nextafter(x, 0) for x in edges] + [800.0, -800.0]
     worst = 0.0
+    c32 = np.float32(float.fromhex("0x1.715476p+8"))     # 256/ln2 rounded to FP32
+    assert c32 == np.float32(N_EXP / math.log(2))
     for w in ws:
-        y = np.float32(_f32_trunc(w)) * np.float32(46.16624069213867)
+        y = np.float32(_f32_trunc(w)) * c32
         sh = np.float32(y) + np.float32(12582912.0)
         k = int(np.frombuffer(np.float32(sh).tobytes(), np.uint32)[0]) - 0x4B400000
-        worst = max(worst, abs(float(mpmath.mpf(w) - k * ln2_32)))
-    assert worst < 0.0109
+        worst = max(worst, abs(float(mpmath.mpf(w) - k * ln2_n)))
+    assert worst < 0.0016
 
 
 def _ulps(a, ref):
@@ -175,10 +180,10 @@ def test_expm1_within_two_ulp_for_every_j():
     mpmath.mp.prec = 200
     rng = np.random.default_rng(6)
     worst = 0.0
-    h = math.log(2) / 32
+    h = math.log(2) / N_EXP
     for m in (-1100, -40, -2, -1, 0, 1, 3, 20, 1000, 1022):
-        for j in range(32):
-            c = (32 * m + j) * h
+        for j in range(N_EXP):
+            c = (N_EXP * m + j) * h
             for d in (0.0, 0.49 * h, -0.49 * h, float(rng.uniform(-0.5, 0.5)) * h):
                 w = c + d
                 if w == 0.0 or w > 709.7:
