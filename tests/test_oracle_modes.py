@@ -41,6 +41,37 @@ def test_modes_agree_on_random_fields(seed):
     _agree(O.track(f, st, arith="plain"), O.track(f, st, arith="mirror"), 1e-12)
 
 
+def _scaled(f, s):
+    """The same field with every face flow times s: velocities scale by s,
+    travel times by 1/s, paths stay the same."""
+    import dataclasses
+    return dataclasses.replace(f, qx=f.qx * s, qy=f.qy * s, qz=f.qz * s)
+
+
+@pytest.mark.parametrize("scale", [1e-40, 1e42])
+def test_modes_agree_at_extreme_velocity_scales(scale):
+    """Velocities below 2^-120 and above 2^121 (the mirror's quotient falls
+    back to the IEEE division there): both modes take the paths of the
+    unscaled field, with travel times scaled by 1/s to rounding."""
+    f = I.random_box_field(2, 5, 7, seed=321, lnk_var=1.0, n_wells=1, n_inactive=1)
+    cells, frac = I.explicit_particles(f, 200, seed=4, cols=(1, 3))
+    st = O.release_explicit(f, cells, frac)
+    base = O.track(f, st, arith="plain")
+    fs = _scaled(f, scale)
+    # typical x velocity q / (n A): beyond the reciprocal's range on the scaled field
+    area = np.outer(f.dz, f.delc)[:, :, None]
+    v = np.abs(fs.qx[:, :, 1:-1]) / (np.asarray(f.porosity).reshape(f.qx[:, :, 1:].shape)[:, :, :-1] * area)
+    vmed = float(np.median(v[v > 0]))
+    assert (vmed < 2.0 ** -120) if scale < 1 else (vmed > 2.0 ** 121)
+    a, b = O.track(fs, st, arith="plain"), O.track(fs, st, arith="mirror")
+    _agree(a, b, 1e-12)
+    assert np.array_equal(a["hash"], base["hash"])
+    ok = base["t"] > 0
+    assert np.max(np.abs(a["t"][ok] * scale - base["t"][ok]) / base["t"][ok]) <= 1e-12
+    for k in ("gx", "gy", "gz"):
+        assert np.max(np.abs(a[k] - base[k])) <= 1e-9
+
+
 def test_modes_differ_by_rounding_only():
     """The two modes are distinct evaluations (not one code path twice):
     on a heterogeneous field their travel times differ in the last bits."""
