@@ -356,8 +356,9 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
 // evaluated by its series (|z| < 2^-7), by log1pf, or for z < -1/2 by
 // ln(u_exit / vp) (the ratio, not 1 + z, carries the information there),
 // which keeps its error below ~1.5e-6; in all, below ~3.2e-6 (below ~7e-5
-// with d from f32_face_dist).  Velocities too small for FP32
-// (|vp| < 1e-30) or a NaN mark the estimate as untrusted.
+// with d from f32_face_dist).  Velocities outside [1e-30, 1e30] (FP32
+// could not hold the quotients, and __fdividef gives 0 for divisors
+// beyond 2^126) or a NaN mark the estimate as untrusted.
 __device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, float fA, float fue, bool& unsafe)
 {
     const float vf = f32_trunc(vp);
@@ -369,7 +370,7 @@ __device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, fl
     else if (z < -0.5f) g = __fdividef(logf(__fdividef(fue, vs)), z);
     else g = __fdividef(log1pf(z), z);
     const float e = t1 * g;
-    unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(e == e));
+    unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(fabsf(vf) <= 1e30f) || !(e == e));
     return face ? e : CUDART_INF_F;
 }
 

@@ -133,6 +133,35 @@ def test_fp64_edge_cases(ctx):
     mp.mp_field_free(fh)
 
 
+@pytest.mark.parametrize("scale", [1e-40, 1e42])
+def test_fp64_extreme_velocity_scales(ctx, scale):
+    """Every face flow times 1e-40 or 1e42: velocities below 2^-120 or above
+    2^121, where the quotient d / v_p falls back to the IEEE division and
+    the FP32 screening sees zero, subnormal or tiny estimates.  The same
+    bits as the mirror arithmetic, within 1e-10 of the plain one, and the
+    unscaled field's paths."""
+    import dataclasses
+    f0 = I.random_box_field(2, 5, 7, seed=321, lnk_var=1.0, n_wells=1, n_inactive=1)
+    f = dataclasses.replace(f0, qx=f0.qx * scale, qy=f0.qy * scale, qz=f0.qz * scale)
+    fh = ctx.field(f)
+    cells, frac = I.explicit_particles(f, 300, seed=4, cols=(1, 3))
+    st0 = O.release_explicit(f, cells, frac)
+    base = O.track(f0, st0)
+    tt = base["t"][base["t"] > 0]
+    times = np.sort(np.concatenate([[0.0], np.quantile(tt, [0.1, 0.5, 0.9])])) / scale
+    for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+        ep, ts, st = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, schedule=sch)
+        assert st["device_error"] == 0
+        ref = O.track(f, st0, times=times, arith="mirror")
+        G.compare_fp64(ep, ref, dmin=G.dmin(f))
+        G.compare_timeseries_fp64(ts, ref, dmin=G.dmin(f))
+        plain = O.track(f, st0, times=times)
+        G.compare_fp64_plain(ep, plain, field=f, state=st0, ts=ts, times=times, t_stop=np.inf,
+                             label=f"scale {scale:g}")
+        assert np.array_equal(ep["hash"], base["hash"])
+    mp.mp_field_free(fh)
+
+
 def test_fp64_no_exit_divide(ctx):
     """Flow diverging inside a cell: no face reachable (NO_EXIT), and with a
     stop time the particle keeps moving inside the cell."""
