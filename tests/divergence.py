@@ -11,7 +11,9 @@ the first cell-step at which the two traces choose differently is one of:
   sign between the two evaluations); the gap is the reference's velocity on
   that axis, against the larger face velocity of the axis;
 - ``stop``: one reaches the stop time inside the cell, the other leaves it;
-  the gap is the distance of the reference's step end from the stop time;
+  the gap is the distance of the reference's step end from the stop time
+  (where one leaves and the other has no reachable face on that axis, the
+  kind is ``face``);
 - ``cell``: the same exit, different cells entered (a quadtree hand-over);
 - ``end``: the traces agree step by step but one ends earlier (a status
   decided differently after the last common step).
@@ -63,9 +65,12 @@ def first_divergence(ref, other, t_stop=np.inf, particle=-1) -> Divergence:
             return Divergence(particle, s, "face", abs(float(a["vp"][ax_b])), float(a["vf"][ax_b]))
         if ax_a >= 0 and ax_b >= 0:
             return Divergence(particle, s, "face", abs(float(a["vp"][ax_a])), float(a["vf"][ax_a]))
+        # one leaves the cell, the other does not: either the other has no
+        # reachable face on that axis (its particle velocity vanished or
+        # changed sign) or it reached the stop time first
         ax = ax_a if ax_a >= 0 else ax_b
-        te = float(a["te"][ax])
-        if not np.isfinite(te):
+        te, te_b = float(a["te"][ax]), float(b["te"][ax])
+        if not (np.isfinite(te) and np.isfinite(te_b)):
             return Divergence(particle, s, "face", abs(float(a["vp"][ax])), float(a["vf"][ax]))
         return Divergence(particle, s, "stop", abs(t + te - t_stop), float(t_stop))
     return Divergence(particle, n, "end", np.inf, 1.0)

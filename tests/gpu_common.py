@@ -109,6 +109,56 @@ def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0),
         assert e.max(initial=0.0) <= rtol, f"ts {gk}: max rel err {e.max()}"
 
 
+def ts_pos_err(ts_xyz, ref, field):
+    """Per particle: the largest timeseries position error (relative to
+    pos_scale) of records ``ts_xyz`` = (x, y, z) arrays [n_times, n] against
+    ``ref``'s ts_x/ts_y/ts_z; NaN records (before release, invalid) compare
+    by finiteness."""
+    err = np.zeros(ref["ts_x"].shape[1] if np.ndim(ref["ts_x"]) == 2 else 0)
+    for ax, (a, ok) in enumerate(zip(ts_xyz, ("ts_x", "ts_y", "ts_z"))):
+        b = ref[ok]
+        fin = np.isfinite(b)
+        e = np.where(fin, rel_err(np.where(fin, a, 0.0), np.where(fin, b, 0.0),
+                                  scale=pos_scale(dmin(field)[ax], np.where(fin, b, 0.0))), 0.0)
+        e = np.where(np.isfinite(a) == fin, e, np.inf)
+        err = np.maximum(err, e.max(axis=0, initial=0.0))
+    return err
+
+
+# the jitter (oracle/mp_oracle.h) of about one FP64 rounding: 2^-52 relative
+FP64_JITTER = 2.0 ** -52
+
+
+def fp64_spread(field, state, which, *, runs=4, t_stop=np.inf, times=None, **track_kw):
+    """The plain oracle's own sensitivity to rounding, per particle of
+    ``which``: the largest change of the travel time (relative) and of the
+    endpoint (relative to pos_scale) over ``runs`` runs with every crossing
+    jittered by about one FP64 rounding; +inf where a run changes the cell
+    sequence."""
+    import oracle as O
+    which = np.asarray(which, dtype=np.int64)
+    sub = O.subset(state, which)
+    ref = O.track(field, sub, t_stop=t_stop, times=times, arith="plain", **track_kw)
+    s_t = np.zeros(which.size)
+    s_p = np.zeros(which.size)
+    for r in range(runs):
+        rj = O.track(field, sub, t_stop=t_stop, times=times, arith="plain", jitter=FP64_JITTER,
+                     jitter_seed=2000 + r, **track_kw)
+        div = rj["hash"] != ref["hash"]
+        fin = np.isfinite(ref["t"])
+        jt = np.zeros(which.size)
+        jt[fin] = rel_err(rj["t"][fin], ref["t"][fin])
+        jp = np.zeros(which.size)
+        for ax, k in enumerate(("gx", "gy", "gz")):
+            f2 = np.isfinite(ref[k])
+            jp[f2] = np.maximum(jp[f2], rel_err(rj[k][f2], ref[k][f2], scale=pos_scale(dmin(field)[ax], ref[k][f2])))
+        if times is not None:
+            jp = np.maximum(jp, ts_pos_err((rj["ts_x"], rj["ts_y"], rj["ts_z"]), ref, field))
+        s_t = np.maximum(s_t, np.where(div, np.inf, jt))
+        s_p = np.maximum(s_p, np.where(div, np.inf, jp))
+    return s_t, s_p
+
+
 def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None, t_stop=np.inf, rtol=1e-10,
                        label="", **track_kw):
     """FP64 GPU results against the plain-arithmetic oracle (the reference).
@@ -120,11 +170,19 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
     modes and passes only if the first step whose exit times part has a
     particle velocity within 1e-12 of zero (relative to the face velocity),
     where the exit time ln(v_exit / v_p) / A is set by the rounding of a
-    vanishing v_p.  Particles whose sequence differs are traced the same way
+    vanishing v_p; any other such particle must stay within 4 times the
+    plain oracle's own spread under a jitter of about one FP64 rounding per
+    crossing (fp64_spread: a particle near an unstable stagnation line,
+    whose transverse offset grows like e^(A t), moves by far more than an
+    ulp when its crossings are perturbed by one).  Particles whose sequence
+    differs are traced the same way
     (the mirror mode equals the GPU bit for bit, which the caller checks
     separately) and each must part at a near-tie: at the first step where the
     evaluations choose differently, the reference's two competing choices
-    lie within ``rtol`` of each other (divergence.py).  ``state`` is the
+    lie within ``rtol`` of each other (divergence.py), or else a
+    one-rounding jitter of the plain oracle must change that particle's
+    cell sequence as well (a rounding difference amplified over the steps
+    before, near a stagnation line, decides).  ``state`` is the
     oracle state of the compared particles (``idx`` of the GPU arrays).
     Returns (divergent, max relative time error, max relative position
     error, stagnation exits) and prints them."""
@@ -147,14 +205,24 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
         f2 = np.isfinite(b)
         assert np.array_equal(np.isfinite(g[gk][keep]), f2[keep]), gk
         err_p[f2] = np.maximum(err_p[f2], rel_err(g[gk][f2], b[f2], scale=pos_scale(dmin(field)[ax], b[f2])))
+    if ts is not None:
+        tsel = np.arange(ts.shape[1])[sel]
+        err_ts = ts_pos_err((ts["x"][:, tsel], ts["y"][:, tsel], ts["z"][:, tsel]), plain, field)
+        err_p = np.maximum(err_p, np.where(hsame, err_ts, 0.0))
     over = keep[np.maximum(err_t[keep], err_p[keep]) > rtol]
     stagn = []
+    rest = []
     if over.size:
         for q, step, ratio in D.stagnation_exits(field, state, over, rtol=rtol, t_stop=t_stop, times=times, **track_kw):
-            assert ratio <= 1e-12, (f"particle {q}: time or position beyond {rtol} on the same cell sequence "
-                                    f"(t err {err_t[q]:.3g}, pos err {err_p[q]:.3g}), not from a stagnation exit "
-                                    f"(step {step}, |v_p|/v_face {ratio:.3g})")
-            stagn.append(q)
+            (stagn if ratio <= 1e-12 else rest).append(q)
+    if rest:
+        s_t, s_p = fp64_spread(field, state, rest, t_stop=t_stop, times=times, **track_kw)
+        for n, q in enumerate(rest):
+            assert err_t[q] <= max(rtol, 4 * s_t[n]) and err_p[q] <= max(rtol, 4 * s_p[n]), (
+                f"particle {q}: time or position beyond {rtol} on the same cell sequence (t err {err_t[q]:.3g}, "
+                f"pos err {err_p[q]:.3g}), not from a stagnation exit and beyond 4 x the oracle's own spread "
+                f"under one-rounding jitter (t {s_t[n]:.3g}, pos {s_p[n]:.3g})")
+        stagn += rest
     good = np.setdiff1d(keep, np.asarray(stagn, dtype=np.int64))
     if ts is not None:
         mask = np.zeros(hsame.size, dtype=bool)
@@ -167,8 +235,19 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
         for d in D.analyse(field, state, np.nonzero(~hsame)[0], t_stop=t_stop, times=times, **track_kw):
             if not d.rel <= rtol:
                 bad.append(d)
+    n_sens = 0
+    if bad:
+        # a divergence that is not a near-tie where it happens is still
+        # rounding's when a one-rounding jitter of the plain oracle also
+        # changes that particle's cell sequence (the decision was prepared
+        # by an amplified rounding difference a few steps earlier)
+        s_t, _ = fp64_spread(field, state, [d.particle for d in bad], t_stop=t_stop, times=times, **track_kw)
+        n_sens = int(np.isinf(s_t).sum())
+        bad = [d for d, s in zip(bad, s_t) if not np.isinf(s)]
     print(f"fp64 vs plain oracle {label}: {hsame.size} particles, {ndiv} divergent "
-          f"({ndiv / max(hsame.size, 1):.2e}), {len(stagn)} stagnation exits, max rel t err {t_err:.2e}, "
+          f"({ndiv / max(hsame.size, 1):.2e}; {n_sens} of them not at a near-tie but parted by one-rounding jitter "
+          f"too), {len(stagn) - len(rest)} stagnation exits, {len(rest)} within the "
+          f"oracle's rounding spread, max rel t err {t_err:.2e}, "
           f"max rel pos err {p_err:.2e}")
     assert not bad, f"{len(bad)} divergent particles that are not near-ties, first {bad[:3]}"
     return ndiv, t_err, p_err, len(stagn)

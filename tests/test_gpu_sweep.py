@@ -13,7 +13,10 @@ one seed, and runs both precisions through the C ABI:
 
 Uniform-flow fields (A = 0 in every cell: the exit time is distance over
 velocity, the limit the log form must reach) and fields with wells strong
-enough to capture every particle that reaches them are part of the sweep.
+enough to capture every particle that reaches them are part of the sweep,
+and so are strongly anisotropic fields (cell sizes 1e-3 to 1e3 m across
+the axes, porosity down to 0.01), whose exit times differ by orders of
+magnitude between the axes of one cell.
 """
 import numpy as np
 import pytest
@@ -78,4 +81,45 @@ def test_sweep_against_plain_oracle(ctx, seed):
     epm, _, stm = G.gpu_run(ctx, fh, cells=cells, frac=frac, t_stop=t_stop, precision=mp.PREC_MIXED)
     assert stm["device_error"] == 0
     G.check_mixed(epm, field=f, state=st0, t_stop=t_stop, label=f"sweep {seed}")
+    mp.mp_field_free(fh)
+
+
+def _aniso_case(seed):
+    rng = np.random.default_rng(9000 + seed)
+    sizes = [(0.001, 0.01), (0.02, 0.1), (1.0, 5.0), (100.0, 1000.0)]
+    order = rng.permutation(4)[:3]
+    f = I.random_box_field(int(rng.integers(1, 4)), int(rng.integers(3, 9)), int(rng.integers(5, 12)),
+                           seed=9500 + seed, lnk_var=float(rng.uniform(1.0, 4.0)), dx=sizes[order[0]],
+                           dy=sizes[order[1]], dz=sizes[order[2]], porosity=(0.01, 0.3),
+                           n_wells=int(rng.integers(0, 3)), n_inactive=int(rng.integers(0, 3)))
+    n = int(rng.choice([33, 257, 1000]))
+    act = np.nonzero(np.asarray(f.ibound).reshape(-1) == 1)[0]
+    cells = rng.choice(act, n).astype(np.int32)
+    frac = rng.random((n, 3))
+    on = rng.random((n, 3)) < 0.2
+    frac[on] = rng.integers(0, 2, size=int(on.sum())).astype(np.float64)
+    return f, cells, frac, rng
+
+
+@pytest.mark.parametrize("seed", list(range(6)))
+def test_sweep_anisotropic(ctx, seed):
+    f, cells, frac, rng = _aniso_case(seed)
+    fh = ctx.field(f)
+    st0 = O.release_explicit(f, cells, frac)
+    full = O.track(f, st0)
+    tt = full["t"][np.isfinite(full["t"]) & (full["t"] > 0)]
+    scale = float(np.median(tt)) if tt.size else 1.0
+    times = np.sort(rng.uniform(0.0, 1.2, 5)) * scale
+    for sch in (mp.SCHED_STATIC, mp.SCHED_DYNAMIC):
+        ep, ts, st = G.gpu_run(ctx, fh, cells=cells, frac=frac, times=times, schedule=sch)
+        assert st["device_error"] == 0
+        mirror = O.track(f, st0, times=times, arith="mirror")
+        G.compare_fp64(ep, mirror, dmin=G.dmin(f))
+        G.compare_timeseries_fp64(ts, mirror, dmin=G.dmin(f))
+        plain = O.track(f, st0, times=times)
+        G.compare_fp64_plain(ep, plain, field=f, state=st0, ts=ts, times=times, t_stop=np.inf,
+                             label=f"anisotropic {seed}")
+    epm, _, stm = G.gpu_run(ctx, fh, cells=cells, frac=frac, precision=mp.PREC_MIXED)
+    assert stm["device_error"] == 0
+    G.check_mixed(epm, field=f, state=st0, t_stop=np.inf, label=f"anisotropic {seed}")
     mp.mp_field_free(fh)

@@ -135,6 +135,13 @@ def test_first_divergence_kinds():
     s2 = _trace(_rec((4.0, np.inf, np.inf), 0, t=6.0))
     d = D.first_divergence(s1, s2, t_stop=10.0 + 1e-9)
     assert d.kind == "stop" and d.gap == pytest.approx(1e-9, rel=1e-3)
+    # one leaves through a face the other cannot reach (its particle
+    # velocity rounded to zero): a face divergence at that velocity, not a stop
+    x1 = _trace(_rec((2.8e9, np.inf, np.inf), 0, vp=(1.4e-20, 1.0, 1.0), vf=(1.06e-5, 1.0, 1.0), t=6.0))
+    x2 = _trace(_rec((np.inf, np.inf, np.inf), -1, face=(0, 0, 0), vp=(0.0, 1.0, 1.0), vf=(1.06e-5, 1.0, 1.0),
+                     t=6.0))
+    d = D.first_divergence(x1, x2)
+    assert d.kind == "face" and d.rel == pytest.approx(1.4e-20 / 1.06e-5)
     # identical steps, one trace longer: an unexplained end
     assert D.first_divergence(_trace(same), _trace(same, same)).kind == "end"
     # a different cell after the same exit (a hand-over)
