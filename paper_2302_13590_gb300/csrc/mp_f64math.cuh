@@ -67,55 +67,36 @@ __device__ __forceinline__ double neg(double v)
     return __longlong_as_double(bits(v) ^ (long long)0x8000000000000000ULL);
 }
 
-// frexp: u = m 2^e with m in [1/2, 1) (u == 0, inf, NaN: m = u, e = 0)
-__device__ __forceinline__ double frexp_bits(double u, int& e)
+// The helpers below compute every case and select (no branch): the FP64
+// kernels' lanes then stay converged through them.
+
+// frexp of a positive normal finite u: u = m 2^e with m in [1/2, 1)
+__device__ __forceinline__ double frexp_normal(double u, int& e)
 {
-    long long b = bits(u);
-    int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0x7ff || (b << 1) == 0LL) {
-        e = 0;
-        return u;
-    }
-    if (ex == 0) {   // subnormal: normalise the fraction (nonzero here) on the integer side
-        const unsigned long long fr = (unsigned long long)b & 0x000fffffffffffffULL;
-        const int sh = __clzll((long long)fr) - 11;   // brings the leading 1 to bit 52
-        b = (b & (long long)0x8000000000000000ULL) | (long long)((fr << sh) & 0x000fffffffffffffULL);
-        ex = 1 - sh;
-    }
-    e = ex - 1022;
-    return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | 0x3fe0000000000000LL);
+    const long long b = bits(u);
+    e = (int)(b >> 52) - 1022;
+    return __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
 }
 
 // (double)e for |e| < 2^30, exactly
 __device__ __forceinline__ double i2d_exact(int e)
 {
-    if (e == 0) return 0.0;
     const unsigned long long sgn = e < 0 ? 0x8000000000000000ULL : 0ULL;
     const unsigned a = (unsigned)(e < 0 ? -e : e);
-    const int msb = 31 - __clz(a);
+    const int msb = 31 - __clz(a | 1u);
     const unsigned long long mant = ((unsigned long long)a << (52 - msb)) & 0x000fffffffffffffULL;
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb) << 52) | mant));
-}
-
-// (int)k for an integral k, saturating beyond 2^31 (as __double2int_rz)
-__device__ __forceinline__ int d2i_integral(double k)
-{
-    const long long b = bits(k);
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < 0) return 0;
-    if (e >= 31) return b < 0 ? (-2147483647 - 1) : 2147483647;
-    const unsigned long long m = (unsigned long long)(b & 0x000fffffffffffffLL) | 0x0010000000000000ULL;
-    const int v = (int)(m >> (52 - e));
-    return b < 0 ? -v : v;
+    const unsigned long long r = sgn | ((unsigned long long)(1023 + msb) << 52) | mant;
+    return __longlong_as_double(a == 0u ? 0LL : (long long)r);
 }
 
 // 2^k as ldexp(1, k) gives it, k in [-2000, 2000]
 __device__ __forceinline__ double pow2i(int k)
 {
-    if (k >= 1024) return CUDART_INF;
-    if (k >= -1022) return __longlong_as_double((long long)(k + 1023) << 52);
-    if (k >= -1074) return __longlong_as_double(1LL << (k + 1074));
-    return 0.0;
+    const unsigned long long nrm = (unsigned long long)(k + 1023) << 52;        // -1022 <= k <= 1023
+    const unsigned long long sub = 1ULL << ((unsigned)(k + 1074) & 63u);        // -1074 <= k < -1022
+    unsigned long long r = k >= -1022 ? nrm : (k >= -1074 ? sub : 0ULL);
+    r = k >= 1024 ? 0x7ff0000000000000ULL : r;
+    return __longlong_as_double((long long)r);
 }
 
 // FP64 -> FP32 by truncating the significand on the ALU pipe (the FP64
@@ -127,9 +108,8 @@ __device__ __forceinline__ float f32_trunc(double x)
     const long long b = bits(x);
     const unsigned s = (unsigned)((unsigned long long)b >> 63) << 31;
     const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    if (e < -126) return __uint_as_float(s);
-    if (e > 127) return __uint_as_float(s | 0x7f800000u);
-    return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    const unsigned nrm = s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+    return __uint_as_float(e < -126 ? s : (e > 127 ? (s | 0x7f800000u) : nrm));
 }
 
 // (float)u rounded to nearest even, for u >= 2^-126 (the values 1 + x
@@ -139,31 +119,35 @@ __device__ __forceinline__ float f32_rn_pos(double u)
 {
     const long long b = bits(u);
     const int e = (int)(b >> 52) - 1023;
-    if (e > 127) return CUDART_INF_F;
     unsigned fb = ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
     const unsigned rem = (unsigned)(b & 0x1fffffff);
     fb += (rem > 0x10000000u || (rem == 0x10000000u && (fb & 1u))) ? 1u : 0u;
-    return __uint_as_float(fb);
+    return __uint_as_float(e > 127 ? 0x7f800000u : fb);
 }
 
-// FP32 subnormals to FP64 (rare: kept out of line)
-static __device__ __noinline__ double f2d_subnormal(float f) { return (double)f; }
-
-// (double)f for f >= 0 (normal, zero, infinity: on the ALU pipe)
+// (double)f for f >= 0 (zero, subnormal, normal, infinity: on the ALU pipe;
+// a subnormal's fraction is normalised by its leading-zero count)
 __device__ __forceinline__ double f2d_pos(float f)
 {
     const unsigned fb = __float_as_uint(f);
     const unsigned fe = fb >> 23;
-    if (fe == 0u) return fb == 0u ? 0.0 : f2d_subnormal(f);
-    if (fe == 255u) return CUDART_INF;
-    return __longlong_as_double(((long long)(fe + 896u) << 52) | ((long long)(fb & 0x7fffffu) << 29));
+    const unsigned fm = fb & 0x7fffffu;
+    const int sh = __clz(fm | 1u) - 8;   // brings a subnormal's leading 1 to bit 23
+    const unsigned long long sub = ((unsigned long long)(897 - sh) << 52) |
+                                   ((unsigned long long)((fm << sh) & 0x7fffffu) << 29);
+    const unsigned long long nrm = ((unsigned long long)(fe + 896u) << 52) | ((unsigned long long)fm << 29);
+    unsigned long long r = fe == 0u ? (fm == 0u ? 0ULL : sub) : nrm;
+    r = fe == 255u ? 0x7ff0000000000000ULL : r;
+    return __longlong_as_double((long long)r);
 }
 
-// (double)f for f of either sign (normal, zero, infinity: on the ALU pipe)
-__device__ __forceinline__ double f2d_signed(float f)
+// (double)f for a normal f of either sign (no branch: the callers' values
+// are normal by construction)
+__device__ __forceinline__ double f2d_normal(float f)
 {
-    const double a = f2d_pos(fabsf(f));
-    return __longlong_as_double(bits(a) | (long long)((unsigned long long)(__float_as_uint(f) >> 31) << 63));
+    const unsigned fb = __float_as_uint(f);
+    return __longlong_as_double(((long long)(fb >> 31) << 63) | ((long long)(((fb >> 23) & 0xffu) + 896u) << 52) |
+                                ((long long)(fb & 0x7fffffu) << 29));
 }
 
 // d / v as d times 1 / v: the IEEE FP32 reciprocal of the truncated v
@@ -177,7 +161,7 @@ __device__ __forceinline__ double f64_div(double d, double v)
 {
     const int e = (int)((bits(v) >> 52) & 0x7ff) - 1023;
     if (e < -120 || e > 120) return div_ieee(d, v);
-    const double y0 = f2d_signed(__frcp_rn(f32_trunc(v)));
+    const double y0 = f2d_normal(__frcp_rn(f32_trunc(v)));   // |1 / v| in (2^-121, 2^120]: normal
     const double y1 = fma(y0, fma(-v, y0, 1.0), y0);
     const double y2 = fma(y1, fma(-v, y1, 1.0), y1);
     return d * y2;
@@ -226,11 +210,10 @@ __device__ __forceinline__ double series_log1p(double x)
     const bool big = gt_pos(x, 1.0);
     const double c = (big ? 1.0 : x) - (u - (big ? x : 1.0));
     int e;
-    double m = frexp_bits(ok ? u : 1.0, e);
-    if (bits(m) < bits(0.70710678118654752440)) {   // m in [1/2, 1/sqrt2): m * 2, exactly
-        m = __longlong_as_double(bits(m) + (1LL << 52));
-        e = e - 1;
-    }
+    double m = frexp_normal(ok ? u : 1.0, e);   // u >= 2^-53 when ok
+    const bool below = bits(m) < bits(0.70710678118654752440);   // m in [1/2, 1/sqrt2): m * 2, exactly
+    m = __longlong_as_double(bits(m) + (below ? (1LL << 52) : 0LL));
+    e -= below ? 1 : 0;
     const int key = (int)(bits(m) >> 44) - F64_LOG_KEY0;
     const double2* tp = reinterpret_cast<const double2*>(f64_log_tab) + 2 * key;
     const double2 t0 = __ldg(tp), t1 = __ldg(tp + 1);
@@ -244,7 +227,7 @@ __device__ __forceinline__ double series_log1p(double x)
     float pf = __fmaf_rn(-0x1.0p-3f, rf, 0x1.24924ap-3f);   // -1/8, 1/7
     pf = __fmaf_rn(pf, rf, -0x1.555556p-3f);                // -1/6
     pf = __fmaf_rn(pf, rf, 0x1.99999ap-3f);                 // 1/5
-    double q = fma(r, f2d_pos(pf), -0.25);
+    double q = fma(r, f2d_normal(pf), -0.25);   // pf near 1/5: normal
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     const double lg = fma(r2, q, r);
@@ -284,7 +267,7 @@ __device__ __forceinline__ double series_expm1(double w)
     // 1.5e-17 of the result), in FP32: scaled by r^4 (below 1.7e-10 of the
     // result) its FP32 error stays below 0.1 ulp
     const float pf = __fmaf_rn(0x1.111112p-7f, f32_trunc(r), 0x1.555556p-5f);   // 1/120, 1/24
-    double p = fma(f2d_pos(pf), r, 1.0 / 6.0);
+    double p = fma(f2d_normal(pf), r, 1.0 / 6.0);   // pf near 1/24: normal
     p = fma(p, r, 1.0 / 2.0);
     const double em = fma(r2, p, r);
     const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);   // 2^(j/256)
@@ -350,13 +333,16 @@ __device__ __forceinline__ double f64_move(double A, double iA, double D, double
 }
 
 // FP32 estimate of an exit time from an FP32 distance d and the FP64
-// particle velocity vp.  Relative error: with d the truncated FP64
-// distance, the two truncating conversions and the approximate division
-// give ~6e-7 on t1 = d / vp and on z = A t1; g(z) = ln(1 + z) / z is
-// evaluated by its series (|z| < 2^-7), by log1pf, or for z < -1/2 by
-// ln(u_exit / vp) (the ratio, not 1 + z, carries the information there),
-// which keeps its error below ~1.5e-6; in all, below ~3.2e-6 (below ~7e-5
-// with d from f32_face_dist).  Velocities outside [1e-30, 1e30] (FP32
+// particle velocity vp.  Relative error: the truncating conversions and
+// the approximate division give ~6e-7 on t1 = d / vp and on z = A t1, and
+// d from f32_face_dist below 6.2e-5; g(z) = ln(1 + z) / z is its series
+// for |z| < 2^-7, else __logf (absolute error at most 2^-21.41 on [1/2, 2],
+// 3 ulp outside) of u = fl(1 + z) over u - 1, in which the rounding of
+// 1 + z cancels (Goldberg 1991), or for z < -1/2 of the velocity ratio
+// u_exit / vp over z (the ratio, not 1 + z, carries the information
+// there): below 4.6e-5, since |ln u| >= 0.0078 wherever __logf is used.  In
+// all below 1.2e-4, a quarter of the 2^-11 that the candidate margin of
+// 2^-10 allows.  Velocities outside [1e-30, 1e30] (FP32
 // could not hold the quotients, and __fdividef gives 0 for divisors
 // beyond 2^126) or a NaN mark the estimate as untrusted.
 __device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, float fA, float fue, bool& unsafe)
@@ -365,10 +351,13 @@ __device__ __forceinline__ float f32_estimate_f(int face, float d, double vp, fl
     const float vs = face ? vf : 1.0f;
     const float t1 = __fdividef(d, vs);
     const float z = fA * t1;
-    float g;
-    if (fabsf(z) < 0.0078125f) g = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
-    else if (z < -0.5f) g = __fdividef(logf(__fdividef(fue, vs)), z);
-    else g = __fdividef(log1pf(z), z);
+    // both forms, selected (no divergent branch)
+    const bool near_m1 = z < -0.5f;
+    const float u = 1.0f + z;
+    const float L = __logf(near_m1 ? __fdividef(fue, vs) : u);
+    const float gl = __fdividef(L, near_m1 ? z : u - 1.0f);
+    const float gs = 1.0f + z * (-0.5f + z * (1.0f / 3.0f + z * (-0.25f + z * 0.2f)));
+    const float g = fabsf(z) < 0.0078125f ? gs : gl;
     const float e = t1 * g;
     unsafe = face != 0 && (!(fabsf(vf) >= 1e-30f) || !(fabsf(vf) <= 1e30f) || !(e == e));
     return face ? e : CUDART_INF_F;

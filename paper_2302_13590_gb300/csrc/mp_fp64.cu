@@ -521,7 +521,7 @@ struct F64Engine {
                 const float e1 = estimate(f1, f32_face_dist(f1, D1, s.x1), vp1, g1.y, f1 > 0 ? g1.x : g0.w, u1);
                 const float e2 = estimate(f2, f32_face_dist(f2, D2, s.x2), vp2, g2.x, f2 > 0 ? g1.w : g1.z, u2);
                 // candidates: every axis whose estimate is within 2^-10 of the
-                // smallest (the estimates are within ~7e-5 of the exact times),
+                // smallest (the estimates are within ~1.2e-4 of the exact times),
                 // and every axis whose estimate cannot be trusted
                 float em = CUDART_INF_F;
                 int a0 = -1;
@@ -637,16 +637,14 @@ struct F64Engine {
         s.i += di;
         s.k += dk;
         s.c += dj + di * f.ncol + dk * f.ncol * f.nrow;
-        if (face < 0) {
-            const double Dn = ax == 0 ? __ldg(f.delr + s.j) : (ax == 1 ? __ldg(f.delc + s.i) : __ldg(f.dz + s.k));
-            if (ax == 0) s.x0 = Dn;
-            else if (ax == 1) s.x1 = Dn;
-            else s.x2 = Dn;
-        } else {
-            if (ax == 0) s.x0 = 0.0;
-            else if (ax == 1) s.x1 = 0.0;
-            else s.x2 = 0.0;
-        }
+        // (the new cell's size along the exit axis, loaded by every lane:
+        // one selected load instead of a branch on the direction)
+        const double* sz = ax == 0 ? f.delr : (ax == 1 ? f.delc : f.dz);
+        const int si = ax == 0 ? s.j : (ax == 1 ? s.i : s.k);
+        const double entry = face < 0 ? __ldg(sz + si) : 0.0;
+        s.x0 = ax == 0 ? entry : s.x0;
+        s.x1 = ax == 1 ? entry : s.x1;
+        s.x2 = ax == 2 ? entry : s.x2;
         s.h = fnv_step(s.h, s.c);
     }
 
