@@ -61,9 +61,15 @@ def pos_scale(field, b):
     return np.maximum(np.abs(b), b * 0 + field)
 
 
-def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), allow_divergent=0.0):
+def _same_bits(a, b):
+    return int(np.count_nonzero(np.ascontiguousarray(a).view(np.int64) != np.ascontiguousarray(b).view(np.int64)))
+
+
+def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), allow_divergent=0.0, exact=True):
     """FP64 parity: exact cell sequences and statuses; travel times within
-    rtol relative; positions within rtol relative to max(|x|, grid extent).
+    rtol relative; positions within rtol relative to max(|x|, grid extent);
+    with ``exact`` (the reference is the oracle's mirror arithmetic or
+    another run of the kernels) travel times and positions bit for bit.
 
     allow_divergent: fraction of particles whose cell sequence may differ
     (for strongly ill-conditioned fields, where a 1-ulp difference between
@@ -88,12 +94,15 @@ def compare_fp64(ep, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), allow_dive
         scale = None if gk == "t" else pos_scale(dmin[ax], b[fin])
         e = rel_err(a[fin], b[fin], scale=scale)
         assert e.max(initial=0.0) <= rtol, f"{gk}: max rel err {e.max()}"
+        if exact:
+            nb = _same_bits(a[fin], b[fin])
+            assert nb == 0, f"{gk}: {nb} of {int(fin.sum())} values not bit-identical (max rel err {e.max()})"
     return ndiv
 
 
-def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), keep=None):
+def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0), keep=None, exact=True):
     """Timeseries parity; keep = boolean mask of particles (of the sample) to
-    check (those whose cell sequence matches)."""
+    check (those whose cell sequence matches); ``exact`` as in compare_fp64."""
     sel = slice(None) if idx is None else idx
     if keep is not None:
         base = np.arange(ts.shape[1])[sel]
@@ -107,6 +116,9 @@ def compare_timeseries_fp64(ts, ref, idx=None, rtol=1e-10, dmin=(1.0, 1.0, 1.0),
         assert np.array_equal(np.isfinite(a), fin)
         e = rel_err(a[fin], b[fin], scale=pos_scale(dmin[ax], b[fin]))
         assert e.max(initial=0.0) <= rtol, f"ts {gk}: max rel err {e.max()}"
+        if exact:
+            nb = _same_bits(a[fin], b[fin])
+            assert nb == 0, f"ts {gk}: {nb} of {int(fin.sum())} records not bit-identical (max rel err {e.max()})"
 
 
 def ts_pos_err(ts_xyz, ref, field):
@@ -227,7 +239,7 @@ def compare_fp64_plain(ep, plain, *, field, state, idx=None, ts=None, times=None
     if ts is not None:
         mask = np.zeros(hsame.size, dtype=bool)
         mask[good] = True
-        compare_timeseries_fp64(ts, plain, idx=idx, rtol=rtol, dmin=dmin(field), keep=mask)
+        compare_timeseries_fp64(ts, plain, idx=idx, rtol=rtol, dmin=dmin(field), keep=mask, exact=False)
     t_err = err_t[good].max(initial=0.0)
     p_err = err_p[good].max(initial=0.0)
     bad = []
