@@ -260,8 +260,10 @@ __device__ __forceinline__ double series_expm1(double w)
     const int j = k & 255;
     const int m = (k - j) >> 8;
     const double dk = i2d_exact(k);
-    double r = fma(-dk, ln2_hi / 256.0, wc);
-    r = fma(-dk, ln2_lo / 256.0, r);
+    // (the constants negated, not k: the same products, and no separate
+    // negation of k on the FP64 pipe)
+    double r = fma(dk, -(ln2_hi / 256.0), wc);
+    r = fma(dk, -(ln2_lo / 256.0), r);
     const double r2 = r * r;
     // the factor of r^4, 1/24 + r/120 (the series' next term is below
     // 1.5e-17 of the result), in FP32: scaled by r^4 (below 1.7e-10 of the
