@@ -15,6 +15,10 @@ rounded exactly to the binary format:
   with Lh and e * ln2_hi both multiples of 2^-32, their sum is exact.
 * exponential table, j = 0..255: Th = 2^(j/256) and Tl = 2^(j/256) - Th,
   each rounded to the nearest double.
+* the logarithm's exponent terms for e = -1..2, per bucket: e ln2_hi + Lh
+  (exact: both are multiples of 2^-32) and e ln2_lo + Ll rounded to the
+  nearest double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo
+  the two doubles the kernels use.
 
 Run: python gen_f64_tables.py   (rewrites the header next to this file)
 """
@@ -27,6 +31,9 @@ from fractions import Fraction
 KEY0 = (1022 << 8) + 106
 N_LOG = 257
 N_EXP = 256
+E0, N_E = -1, 4                       # exponent rows of the log table's e terms
+LN2_HI = 6.93147180369123816490e-01   # the kernels' split of ln 2
+LN2_LO = 1.90821492927058770002e-10
 
 
 def _round_to(x: Fraction, unit: Fraction) -> Fraction:
@@ -71,6 +78,17 @@ def tables():
     return logs, exps
 
 
+def e_terms(logs):
+    """(e ln2_hi + Lh, e ln2_lo + Ll rounded) for e = E0 .. E0 + N_E - 1, per bucket."""
+    rows = []
+    for e in range(E0, E0 + N_E):
+        for R, Lh, Ll in logs:
+            hi = e * Fraction(LN2_HI) + Fraction(Lh)
+            assert Fraction(float(hi)) == hi
+            rows.append((float(hi), float(e * Fraction(LN2_LO) + Fraction(Ll))))
+    return rows
+
+
 def render() -> str:
     logs, exps = tables()
     out = ["// mp_f64_tables.h - constant tables of the FP64 log1p and expm1 (bit",
@@ -88,6 +106,11 @@ def render() -> str:
             "static __device__ __align__(16) const unsigned long long f64_exp_tab[F64_EXP_N * 2] = {"]
     for Th, Tl in exps:
         out.append(f"    {_hex(Th)}, {_hex(Tl)},")
+    out += ["};", "", f"constexpr int F64_LOG_E0 = {E0};", f"constexpr int F64_LOG_NE = {N_E};",
+            "// per exponent e (rows E0 ..) and bucket: e ln2_hi + Lh, RN(e ln2_lo + Ll) (16 bytes)",
+            "static __device__ __align__(16) const unsigned long long f64_log_e_tab[F64_LOG_NE * F64_LOG_N * 2] = {"]
+    for hi, lo in e_terms(logs):
+        out.append(f"    {_hex(hi)}, {_hex(lo)},")
     out += ["};", "", "}  // namespace mp", ""]
     return "\n".join(out)
 

@@ -188,7 +188,9 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     r = m R - 1 exactly (one fma); ln(1 + r) by its series to r^8
 //     (|r| < 0.006), the factor of r^5 in FP32 on the truncated r;
 //     (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
-//     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u.
+//     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u; the two
+//     e terms come from a table for e in [-1, 2] (the same values as the
+//     fmas that give them otherwise).
 //     u = +inf -> +inf, u = 0 -> -inf, NaN -> NaN.
 //   expm1(w): |w| limited to 800; k = nearest integer to w 256/ln2 in FP32
 //     on the truncated w; j = k mod 256, m = (k - j) / 256;
@@ -196,12 +198,23 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r;
 //     2^(j/256) = Th + Tl, S = Th expm1(r) + Tl;
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite).  About 14 and 9 FP64 operations.
+//     2^m is not finite).  About 12 and 9 FP64 operations.
 // ---------------------------------------------------------------------------
+
+// e ln2_hi + Lh and e ln2_lo + Ll by the fmas, for exponents outside the
+// e-term table (rare; out of line, and a side effect keeps the call from
+// being evaluated speculatively)
+static __device__ __noinline__ double2 log_e_terms(int e, double Lh, int key)
+{
+    asm volatile("");
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double Ll = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key + 1).x;
+    const double de = i2d_exact(e);
+    return make_double2(fma(de, ln2_hi, Lh), fma(de, ln2_lo, Ll));
+}
 
 __device__ __forceinline__ double series_log1p(double x)
 {
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
     const double u = 1.0 + x;
     const long long ub = bits(u);
     const bool ok = ub > 0LL && ub < 0x7ff0000000000000LL;   // 0 < u < inf
@@ -215,9 +228,8 @@ __device__ __forceinline__ double series_log1p(double x)
     m = __longlong_as_double(bits(m) + (below ? (1LL << 52) : 0LL));
     e -= below ? 1 : 0;
     const int key = (int)(bits(m) >> 44) - F64_LOG_KEY0;
-    const double2* tp = reinterpret_cast<const double2*>(f64_log_tab) + 2 * key;
-    const double2 t0 = __ldg(tp), t1 = __ldg(tp + 1);
-    const double R = t0.x, Lh = t0.y, Ll = t1.x;
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key);
+    const double R = t0.x, Lh = t0.y;
     const double r = fma(m, R, -1.0);
     const double r2 = r * r;
     // the series' tail 1/5 - r/6 + r^2/7 - r^3/8 in FP32: it enters scaled
@@ -231,10 +243,18 @@ __device__ __forceinline__ double series_log1p(double x)
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     const double lg = fma(r2, q, r);
-    const double de = i2d_exact(e);
     const double ru = f2d_pos(__frcp_rn(f32_rn_pos(ok ? u : 1.0)));   // (double)(1.0f / (float)u)
-    const double hi = fma(de, ln2_hi, Lh);
-    const double lo = fma(c, ru, lg) + fma(de, ln2_lo, Ll);
+    // e ln2_hi + Lh (exact) and fma(e, ln2_lo, Ll): from the e-term table for
+    // e in [-1, 2] (u in [1/(2 sqrt2), 4 sqrt2): all but a few in a thousand
+    // exit-time evaluations), else by the two fmas
+    const unsigned er = (unsigned)(e - F64_LOG_E0);
+    double2 hl;
+    if (er < (unsigned)F64_LOG_NE)
+        hl = __ldg(reinterpret_cast<const double2*>(f64_log_e_tab) + er * F64_LOG_N + key);
+    else
+        hl = log_e_terms(e, Lh, key);
+    const double hi = hl.x;
+    const double lo = fma(c, ru, lg) + hl.y;
     const long long special = eq0(u) ? (long long)0xfff0000000000000ULL
                                      : (ub == 0x7ff0000000000000LL ? 0x7ff0000000000000LL
                                                                    : (long long)0xfff8000000000000ULL);

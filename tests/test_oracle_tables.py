@@ -38,19 +38,26 @@ def _d(b):
 N_EXP = 256                  # entries 2^(j/256) of the exponential table
 
 
-def _read(path, per_log):
-    words = [int(x, 16) for x in re.findall(r"0x([0-9a-f]{16})ULL", open(path).read())]
+N_E = 4                      # device e-term rows, e = -1 .. 2
+
+
+def _words(path):
+    return [int(x, 16) for x in re.findall(r"0x([0-9a-f]{16})ULL", open(path).read())]
+
+
+def _read(path, per_log, extra=0):
+    words = _words(path)
     n_log = 257 * per_log
     log = [tuple(_d(w) for w in words[i:i + 3]) for i in range(0, n_log, per_log)]
     exp = [(_d(words[n_log + 2 * j]), _d(words[n_log + 2 * j + 1])) for j in range(N_EXP)]
-    assert len(words) == n_log + 2 * N_EXP
+    assert len(words) == n_log + 2 * N_EXP + extra
     return log, exp
 
 
 def _tables():
     oracle = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3)
     # the device header pads each bucket with a literal 0x0ULL (not matched)
-    device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3)
+    device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3, extra=2 * N_E * 257)
     return {"oracle": oracle, "device": device}
 
 
@@ -224,3 +231,21 @@ def test_quotient_within_one_ulp():
                 assert (q == ref and math.copysign(1, q) == math.copysign(1, ref)) or (math.isnan(q) and math.isnan(ref))
     # signed zeros as the division gives them
     assert math.copysign(1, O.div(0.0, -3.0)) == -1 and math.copysign(1, O.div(-0.0, -3.0)) == 1
+
+
+def test_log_e_terms_table():
+    """The device's e-term rows of the logarithm (e = -1 .. 2): e ln2_hi + Lh
+    exactly and e ln2_lo + Ll rounded to the nearest double, which is what
+    fma(e, ln2_lo, Ll) gives, so the table and the fmas are interchangeable
+    bit for bit."""
+    path = os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h")
+    words = _words(path)
+    log, _ = _read(path, 3, extra=2 * N_E * 257)
+    base = 257 * 3 + 2 * N_EXP
+    for r in range(N_E):
+        e = r - 1
+        for i, (R, Lh, Ll) in enumerate(log):
+            hi, lo = _d(words[base + 2 * (r * 257 + i)]), _d(words[base + 2 * (r * 257 + i) + 1])
+            assert Fraction(hi) == e * Fraction(LN2_HI) + Fraction(Lh)
+            assert lo == float(e * Fraction(LN2_LO) + Fraction(Ll))
+            assert lo == math.fma(float(e), LN2_LO, Ll) if hasattr(math, "fma") else True
