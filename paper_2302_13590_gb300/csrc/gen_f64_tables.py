@@ -19,6 +19,8 @@ rounded exactly to the binary format:
   (exact: both are multiples of 2^-32) and e ln2_lo + Ll rounded to the
   nearest double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo
   the two doubles the kernels use.
+* the exponential's 2^m Th - 1 for m = -1 and 0, per j (exact: Th - 2 and
+  Th - 1 are doubles by Sterbenz's lemma, and halving is exact).
 
 Run: python gen_f64_tables.py   (rewrites the header next to this file)
 """
@@ -32,6 +34,7 @@ KEY0 = (1022 << 8) + 106
 N_LOG = 257
 N_EXP = 256
 E0, N_E = -1, 4                       # exponent rows of the log table's e terms
+M0, N_M = -1, 2                       # exponent rows of the exp table's 2^m Th - 1
 LN2_HI = 6.93147180369123816490e-01   # the kernels' split of ln 2
 LN2_LO = 1.90821492927058770002e-10
 
@@ -89,6 +92,17 @@ def e_terms(logs):
     return rows
 
 
+def m_terms(exps):
+    """2^m Th - 1 for m = M0 .. M0 + N_M - 1, per j (exact doubles)."""
+    rows = []
+    for m in range(M0, M0 + N_M):
+        for Th, Tl in exps:
+            v = Fraction(2) ** m * Fraction(Th) - 1
+            assert Fraction(float(v)) == v
+            rows.append(float(v))
+    return rows
+
+
 def render() -> str:
     logs, exps = tables()
     out = ["// mp_f64_tables.h - constant tables of the FP64 log1p and expm1 (bit",
@@ -111,6 +125,11 @@ def render() -> str:
             "static __device__ __align__(16) const unsigned long long f64_log_e_tab[F64_LOG_NE * F64_LOG_N * 2] = {"]
     for hi, lo in e_terms(logs):
         out.append(f"    {_hex(hi)}, {_hex(lo)},")
+    out += ["};", "", f"constexpr int F64_EXP_M0 = {M0};", f"constexpr int F64_EXP_NM = {N_M};",
+            "// per exponent m (rows M0 ..) and j: 2^m Th - 1 (8 bytes)",
+            "static __device__ __align__(16) const unsigned long long f64_exp_m_tab[F64_EXP_NM * F64_EXP_N] = {"]
+    for v in m_terms(exps):
+        out.append(f"    {_hex(v)},")
     out += ["};", "", "}  // namespace mp", ""]
     return "\n".join(out)
 

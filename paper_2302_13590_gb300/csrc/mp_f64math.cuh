@@ -198,7 +198,8 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r;
 //     2^(j/256) = Th + Tl, S = Th expm1(r) + Tl;
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite).  About 12 and 9 FP64 operations.
+//     2^m is not finite), 2^m Th - 1 from a table for m in {-1, 0}.  About
+//     12 and 8 FP64 operations.
 // ---------------------------------------------------------------------------
 
 // e ln2_hi + Lh and e ln2_lo + Ll by the fmas, for exponents outside the
@@ -261,6 +262,14 @@ __device__ __forceinline__ double series_log1p(double x)
     return __longlong_as_double(ok ? bits(hi + lo) : special);   // -inf, +inf, NaN
 }
 
+// 2^m Th - 1 by the fma, for exponents outside the m-term table (rare; out
+// of line, not evaluated speculatively)
+static __device__ __noinline__ double exp_m_term(double t, double Th)
+{
+    asm volatile("");
+    return fma(t, Th, -1.0);
+}
+
 // expm1 where 2^m overflows (w > ~709.4); kept out of line
 static __device__ __noinline__ double expm1_big(double Th, double S, int m)
 {
@@ -296,7 +305,15 @@ __device__ __forceinline__ double series_expm1(double w)
     const double S = fma(T.x, em, T.y);
     if (m > 1023) return expm1_big(T.x, S, m);
     const double t = pow2i(m < -2000 ? -2000 : m);
-    return fma(t, S, fma(t, T.x, -1.0));
+    // 2^m Th - 1 from the m-term table for m in {-1, 0} (|w| below ln 2
+    // about: all but a few in a thousand motions), else by the fma
+    const unsigned mr = (unsigned)(m - F64_EXP_M0);
+    double tm;
+    if (mr < (unsigned)F64_EXP_NM)
+        tm = __longlong_as_double((long long)__ldg(f64_exp_m_tab + mr * F64_EXP_N + j));
+    else
+        tm = exp_m_term(t, T.x);
+    return fma(t, S, tm);
 }
 
 // Exit time along one axis from the distance d to the reachable face

@@ -39,6 +39,8 @@ N_EXP = 256                  # entries 2^(j/256) of the exponential table
 
 
 N_E = 4                      # device e-term rows, e = -1 .. 2
+N_M = 2                      # device m-term rows, m = -1, 0
+DEV_EXTRA = 2 * N_E * 257 + N_M * N_EXP
 
 
 def _words(path):
@@ -57,7 +59,7 @@ def _read(path, per_log, extra=0):
 def _tables():
     oracle = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3)
     # the device header pads each bucket with a literal 0x0ULL (not matched)
-    device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3, extra=2 * N_E * 257)
+    device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3, extra=DEV_EXTRA)
     return {"oracle": oracle, "device": device}
 
 
@@ -240,7 +242,7 @@ def test_log_e_terms_table():
     bit for bit."""
     path = os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h")
     words = _words(path)
-    log, _ = _read(path, 3, extra=2 * N_E * 257)
+    log, _ = _read(path, 3, extra=DEV_EXTRA)
     base = 257 * 3 + 2 * N_EXP
     for r in range(N_E):
         e = r - 1
@@ -249,3 +251,16 @@ def test_log_e_terms_table():
             assert Fraction(hi) == e * Fraction(LN2_HI) + Fraction(Lh)
             assert lo == float(e * Fraction(LN2_LO) + Fraction(Ll))
             assert lo == math.fma(float(e), LN2_LO, Ll) if hasattr(math, "fma") else True
+
+
+def test_exp_m_terms_table():
+    """The device's m-term rows of the exponential (m = -1, 0): 2^m Th - 1,
+    exact doubles, so the table equals fma(2^m, Th, -1) bit for bit."""
+    path = os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h")
+    words = _words(path)
+    _, exp = _read(path, 3, extra=DEV_EXTRA)
+    base = 257 * 3 + 2 * N_EXP + 2 * N_E * 257
+    for r in range(N_M):
+        m = r - 1
+        for j, (Th, Tl) in enumerate(exp):
+            assert Fraction(_d(words[base + r * N_EXP + j])) == Fraction(2) ** m * Fraction(Th) - 1
