@@ -13,6 +13,9 @@ computed here in exact integer fixed-point arithmetic (2^-256 units):
   rounded to the nearest double.
 * exponential table, j = 0..255: Th = 2^(j/256) rounded to the nearest
   double, Tl = 2^(j/256) - Th rounded to the nearest double.
+* for m = -1 and 0, per j: A = 2^m Th (exact) and B = 2^m 2^(j/256) - 1
+  rounded to the nearest double (e^w - 1 = A em + B to one rounding
+  when w = (256 m + j) ln2/256 + r and em = e^r - 1).
 
 ln is evaluated as 2 atanh((a - b) / (a + b)) for R = a / b by its odd
 series; 2^(j/256) as the integer 256th root of 2^(j + 256 P).
@@ -123,6 +126,17 @@ def exp_table():
     return rows
 
 
+def exp_ab_table():
+    rows = []
+    for m in (-1, 0):
+        for j in range(N_EXP):
+            T = iroot(1 << (j + N_EXP * P), N_EXP)    # floor(2^(j/256) 2^P)
+            Th = rn53(T, P)
+            # 2^m T - 1 in units of 2^-(P - m): T - 2^(P - m)
+            rows.append((math.ldexp(Th, m), rn53(T - (1 << (P - m)), P - m)))
+    return rows
+
+
 def render() -> str:
     out = ["/* orc_tables.h - constant tables of the oracle's log1p and expm1, written by",
            " * oracle/gen_tables.py (exact integer arithmetic; see there for the",
@@ -136,6 +150,14 @@ def render() -> str:
     out += ["};", "", "/* per j: Th, Tl */", "static const uint64_t orc_exp_tab[ORC_EXP_N][2] = {"]
     for Th, Tl in exp_table():
         out.append(f"    {{0x{bits_of(Th):016x}ULL, 0x{bits_of(Tl):016x}ULL}},")
+    out += ["};", "", "/* per m = -1, 0 and j: A = 2^m Th, B = RN(2^m 2^(j/256) - 1) */",
+            "static const uint64_t orc_exp_ab[2][ORC_EXP_N][2] = {"]
+    for r, (A, B) in enumerate(exp_ab_table()):
+        if r % N_EXP == 0:
+            out.append("  {")
+        out.append(f"    {{0x{bits_of(A):016x}ULL, 0x{bits_of(B):016x}ULL}},")
+        if r % N_EXP == N_EXP - 1:
+            out.append("  },")
     out += ["};", ""]
     return "\n".join(out)
 

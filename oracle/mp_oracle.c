@@ -276,6 +276,13 @@ double orc_expm1(double w)
     double p = fma((double)pf, r, 1.0 / 6.0);
     p = fma(p, r, 1.0 / 2.0);
     double em = fma(r2, p, r);
+    if (m == -1 || m == 0) {
+        /* e^w - 1 = 2^m 2^(j/256) (1 + em) - 1 = A em + B, A = 2^m Th,
+         * B = 2^m 2^(j/256) - 1 rounded: one fma */
+        double A = orc_from_bits(orc_exp_ab[m + 1][j][0]);
+        double B = orc_from_bits(orc_exp_ab[m + 1][j][1]);
+        return fma(A, em, B);
+    }
     double Th = orc_from_bits(orc_exp_tab[j][0]);
     double Tl = orc_from_bits(orc_exp_tab[j][1]);
     double S = fma(Th, em, Tl);

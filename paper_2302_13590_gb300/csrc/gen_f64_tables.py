@@ -19,8 +19,9 @@ rounded exactly to the binary format:
   (exact: both are multiples of 2^-32) and e ln2_lo + Ll rounded to the
   nearest double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo
   the two doubles the kernels use.
-* the exponential's 2^m Th - 1 for m = -1 and 0, per j (exact: Th - 2 and
-  Th - 1 are doubles by Sterbenz's lemma, and halving is exact).
+* for m = -1 and 0, per j: A = 2^m Th (exact) and B = 2^m 2^(j/256) - 1
+  rounded to the nearest double (e^w - 1 = A em + B to one rounding when
+  w = (256 m + j) ln2/256 + r and em = e^r - 1).
 
 Run: python gen_f64_tables.py   (rewrites the header next to this file)
 """
@@ -92,14 +93,16 @@ def e_terms(logs):
     return rows
 
 
-def m_terms(exps):
-    """2^m Th - 1 for m = M0 .. M0 + N_M - 1, per j (exact doubles)."""
+def ab_terms():
+    """(2^m Th, RN(2^m 2^(j/256) - 1)) for m = M0 .. M0 + N_M - 1, per j."""
+    ctx = decimal.Context(prec=90)
     rows = []
     for m in range(M0, M0 + N_M):
-        for Th, Tl in exps:
-            v = Fraction(2) ** m * Fraction(Th) - 1
-            assert Fraction(float(v)) == v
-            rows.append(float(v))
+        for j in range(N_EXP):
+            T = Fraction(ctx.power(Decimal(2), ctx.divide(Decimal(j), Decimal(N_EXP))))
+            A = Fraction(2) ** m * Fraction(float(T))
+            assert Fraction(float(A)) == A
+            rows.append((float(A), float(Fraction(2) ** m * T - 1)))
     return rows
 
 
@@ -126,10 +129,10 @@ def render() -> str:
     for hi, lo in e_terms(logs):
         out.append(f"    {_hex(hi)}, {_hex(lo)},")
     out += ["};", "", f"constexpr int F64_EXP_M0 = {M0};", f"constexpr int F64_EXP_NM = {N_M};",
-            "// per exponent m (rows M0 ..) and j: 2^m Th - 1 (8 bytes)",
-            "static __device__ __align__(16) const unsigned long long f64_exp_m_tab[F64_EXP_NM * F64_EXP_N] = {"]
-    for v in m_terms(exps):
-        out.append(f"    {_hex(v)},")
+            "// per exponent m (rows M0 ..) and j: 2^m Th, RN(2^m 2^(j/256) - 1) (16 bytes)",
+            "static __device__ __align__(16) const unsigned long long f64_exp_ab_tab[F64_EXP_NM * F64_EXP_N * 2] = {"]
+    for A, B in ab_terms():
+        out.append(f"    {_hex(A)}, {_hex(B)},")
     out += ["};", "", "}  // namespace mp", ""]
     return "\n".join(out)
 

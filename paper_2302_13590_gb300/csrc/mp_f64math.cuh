@@ -198,8 +198,9 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r;
 //     2^(j/256) = Th + Tl, S = Th expm1(r) + Tl;
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite), 2^m Th - 1 from a table for m in {-1, 0}.  About
-//     12 and 8 FP64 operations.
+//     2^m is not finite); for m in {-1, 0} A em + B in one fma, with
+//     A = 2^m Th and B = 2^m 2^(j/256) - 1 rounded from a table.  About 12
+//     and 7 FP64 operations.
 // ---------------------------------------------------------------------------
 
 // e ln2_hi + Lh and e ln2_lo + Ll by the fmas, for exponents outside the
@@ -262,18 +263,17 @@ __device__ __forceinline__ double series_log1p(double x)
     return __longlong_as_double(ok ? bits(hi + lo) : special);   // -inf, +inf, NaN
 }
 
-// 2^m Th - 1 by the fma, for exponents outside the m-term table (rare; out
-// of line, not evaluated speculatively)
-static __device__ __noinline__ double exp_m_term(double t, double Th)
+// expm1's reconstruction for m outside {-1, 0} (rare; out of line, not
+// evaluated speculatively): S = Th em + Tl, (2^m Th - 1) + 2^m S, and
+// (Th + S) 2^(m-1023) 2^1023 where 2^m overflows
+static __device__ __noinline__ double expm1_far(double em, int j, int m)
 {
     asm volatile("");
-    return fma(t, Th, -1.0);
-}
-
-// expm1 where 2^m overflows (w > ~709.4); kept out of line
-static __device__ __noinline__ double expm1_big(double Th, double S, int m)
-{
-    return ((Th + S) * pow2i(m - 1023 > 2000 ? 2000 : m - 1023)) * pow2i(1023);
+    const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);   // 2^(j/256)
+    const double S = fma(T.x, em, T.y);
+    if (m > 1023) return ((T.x + S) * pow2i(m - 1023 > 2000 ? 2000 : m - 1023)) * pow2i(1023);
+    const double t = pow2i(m < -2000 ? -2000 : m);
+    return fma(t, S, fma(t, T.x, -1.0));
 }
 
 __device__ __forceinline__ double series_expm1(double w)
@@ -301,19 +301,15 @@ __device__ __forceinline__ double series_expm1(double w)
     double p = fma(f2d_normal(pf), r, 1.0 / 6.0);   // pf near 1/24: normal
     p = fma(p, r, 1.0 / 2.0);
     const double em = fma(r2, p, r);
-    const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);   // 2^(j/256)
-    const double S = fma(T.x, em, T.y);
-    if (m > 1023) return expm1_big(T.x, S, m);
-    const double t = pow2i(m < -2000 ? -2000 : m);
-    // 2^m Th - 1 from the m-term table for m in {-1, 0} (|w| below ln 2
-    // about: all but a few in a thousand motions), else by the fma
+    // m in {-1, 0} (|w| below ln 2 about: all but a few in a thousand
+    // motions): e^w - 1 = A em + B with A = 2^m Th and B = 2^m 2^(j/256) - 1
+    // rounded, from the table, in one fma
     const unsigned mr = (unsigned)(m - F64_EXP_M0);
-    double tm;
-    if (mr < (unsigned)F64_EXP_NM)
-        tm = __longlong_as_double((long long)__ldg(f64_exp_m_tab + mr * F64_EXP_N + j));
-    else
-        tm = exp_m_term(t, T.x);
-    return fma(t, S, tm);
+    if (mr < (unsigned)F64_EXP_NM) {
+        const double2 ab = __ldg(reinterpret_cast<const double2*>(f64_exp_ab_tab) + mr * F64_EXP_N + j);
+        return fma(ab.x, em, ab.y);
+    }
+    return expm1_far(em, j, m);
 }
 
 // Exit time along one axis from the distance d to the reachable face

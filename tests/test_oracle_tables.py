@@ -39,8 +39,9 @@ N_EXP = 256                  # entries 2^(j/256) of the exponential table
 
 
 N_E = 4                      # device e-term rows, e = -1 .. 2
-N_M = 2                      # device m-term rows, m = -1, 0
-DEV_EXTRA = 2 * N_E * 257 + N_M * N_EXP
+N_M = 2                      # reconstruction rows (A, B), m = -1, 0
+DEV_EXTRA = 2 * N_E * 257 + 2 * N_M * N_EXP
+ORC_EXTRA = 2 * N_M * N_EXP
 
 
 def _words(path):
@@ -57,7 +58,7 @@ def _read(path, per_log, extra=0):
 
 
 def _tables():
-    oracle = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3)
+    oracle = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3, extra=ORC_EXTRA)
     # the device header pads each bucket with a literal 0x0ULL (not matched)
     device = _read(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"), 3, extra=DEV_EXTRA)
     return {"oracle": oracle, "device": device}
@@ -253,14 +254,21 @@ def test_log_e_terms_table():
             assert lo == math.fma(float(e), LN2_LO, Ll) if hasattr(math, "fma") else True
 
 
-def test_exp_m_terms_table():
-    """The device's m-term rows of the exponential (m = -1, 0): 2^m Th - 1,
-    exact doubles, so the table equals fma(2^m, Th, -1) bit for bit."""
-    path = os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h")
-    words = _words(path)
-    _, exp = _read(path, 3, extra=DEV_EXTRA)
-    base = 257 * 3 + 2 * N_EXP + 2 * N_E * 257
+def test_exp_reconstruction_table():
+    """The exponential's fused reconstruction for m = -1, 0: A = 2^m Th
+    exactly and B = 2^m 2^(j/256) - 1 correctly rounded (mpmath at 300 bits),
+    the same words in the oracle's table and the device's."""
+    mpmath.mp.prec = 300
+    dev = _words(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"))
+    orc = _words(os.path.join(ROOT, "oracle", "orc_tables.h"))
+    _, exp = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3, extra=ORC_EXTRA)
+    dbase = 257 * 3 + 2 * N_EXP + 2 * N_E * 257
+    obase = 257 * 3 + 2 * N_EXP
     for r in range(N_M):
         m = r - 1
         for j, (Th, Tl) in enumerate(exp):
-            assert Fraction(_d(words[base + r * N_EXP + j])) == Fraction(2) ** m * Fraction(Th) - 1
+            n = 2 * (r * N_EXP + j)
+            A, B = _d(dev[dbase + n]), _d(dev[dbase + n + 1])
+            assert (dev[dbase + n], dev[dbase + n + 1]) == (orc[obase + n], orc[obase + n + 1])
+            assert A == math.ldexp(Th, m)
+            assert B == float(mpmath.ldexp(mpmath.power(2, mpmath.mpf(j) / N_EXP), m) - 1)
