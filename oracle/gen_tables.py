@@ -13,12 +13,17 @@ computed here in exact integer fixed-point arithmetic (2^-256 units):
   rounded to the nearest double.
 * exponential table, j = 0..255: Th = 2^(j/256) rounded to the nearest
   double, Tl = 2^(j/256) - Th rounded to the nearest double.
-* for m = -1 and 0, per j: A = 2^m Th (exact) and B = 2^m 2^(j/256) - 1
-  rounded to the nearest double (e^w - 1 = A em + B to one rounding
-  when w = (256 m + j) ln2/256 + r and em = e^r - 1).
+* for k = 256 m + j with m = -1 and 0 (k = -256 .. 255): A = e^(k c) and
+  B = e^(k c) - 1, each rounded to the nearest double, where c is the
+  double ln2_hi / 256 (ln2_hi = 0x3fe62e42fee00000, a multiple of 2^-32).
+  With r = w - k c (exact) and em = e^r - 1, e^w - 1 = e^(k c) (1 + em) - 1
+  = A em + B to one rounding: the low part of k ln2/256 is in the table,
+  not in the reduction.
 
 ln is evaluated as 2 atanh((a - b) / (a + b)) for R = a / b by its odd
-series; 2^(j/256) as the integer 256th root of 2^(j + 256 P).
+series; 2^(j/256) as the integer 256th root of 2^(j + 256 P); e^(k c) by
+its Taylor series (|k c| < 0.7), with a bound on the truncation that the
+rounding to a double is checked against.
 
 Run: python oracle/gen_tables.py   (rewrites the header next to this file)
 """
@@ -126,14 +131,38 @@ def exp_table():
     return rows
 
 
+LN2_HI = 0x3fe62e42fee00000      # bit pattern of the double ln2_hi
+
+
+def exp_fixed(x: Fraction):
+    """Bounds (lo, hi) on e^x 2^P for |x| < 1, lo <= e^x 2^P <= hi."""
+    X = x * (1 << P)
+    assert X.denominator == 1                  # x is a multiple of 2^-P
+    X = X.numerator
+    if X == 0:
+        return 1 << P, 1 << P
+    s, term, n = 1 << P, 1 << P, 0
+    while term:
+        n += 1
+        term = (term * X >> P) // n if X >= 0 else -((term * -X >> P) // n)
+        s += term
+    return s - 2 * n - 2, s + 2 * n + 2        # each term truncated by < 1 + its carry
+
+
+def rn53_checked(lo: int, hi: int, scale: int) -> float:
+    a, b = rn53(lo, scale), rn53(hi, scale)
+    assert a == b, "bounds round apart"
+    return a
+
+
 def exp_ab_table():
+    lh = struct.unpack("<d", struct.pack("<Q", LN2_HI))[0]
+    c = Fraction(lh) / 256                     # a multiple of 2^-40
     rows = []
-    for m in (-1, 0):
-        for j in range(N_EXP):
-            T = iroot(1 << (j + N_EXP * P), N_EXP)    # floor(2^(j/256) 2^P)
-            Th = rn53(T, P)
-            # 2^m T - 1 in units of 2^-(P - m): T - 2^(P - m)
-            rows.append((math.ldexp(Th, m), rn53(T - (1 << (P - m)), P - m)))
+    for k in range(-N_EXP, N_EXP):
+        lo, hi = exp_fixed(k * c)
+        one = 1 << P
+        rows.append((rn53_checked(lo, hi, P), rn53_checked(lo - one, hi - one, P)))
     return rows
 
 
@@ -150,7 +179,8 @@ def render() -> str:
     out += ["};", "", "/* per j: Th, Tl */", "static const uint64_t orc_exp_tab[ORC_EXP_N][2] = {"]
     for Th, Tl in exp_table():
         out.append(f"    {{0x{bits_of(Th):016x}ULL, 0x{bits_of(Tl):016x}ULL}},")
-    out += ["};", "", "/* per m = -1, 0 and j: A = 2^m Th, B = RN(2^m 2^(j/256) - 1) */",
+    out += ["};", "", "/* per m = -1, 0 and j (k = 256 m + j): A = RN(e^(k c)), B = RN(e^(k c) - 1),",
+            " * c = ln2_hi / 256 */",
             "static const uint64_t orc_exp_ab[2][ORC_EXP_N][2] = {"]
     for r, (A, B) in enumerate(exp_ab_table()):
         if r % N_EXP == 0:

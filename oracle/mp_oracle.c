@@ -166,25 +166,29 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
  * rounded constants.  Accuracy (pinned against the C library in the tests):
  * within a few ulp.
  *
- * log1p(x): u = 1 + x rounded, c = the rounding error of that sum (exact by
- * the two-sum argument); u = m 2^e with m in [1/sqrt2, sqrt2); the bucket of
- * m (its exponent and top 8 fraction bits) gives R, an 8-bit approximation
- * of 1/m, and -ln R = Lh + Ll; r = m R - 1 is exact (one fma: a multiple of
- * 2^-60 below 2^-7); ln(1 + r) = r - r^2/2 + ... - r^8/8 (|r| < 0.006);
- * log1p(x) = (e ln2_hi + Lh) + ((ln(1 + r) + c / u) + (e ln2_lo + Ll)) (the
- * inner sum with c / u in one fma), the
- * first sum exact (both terms are multiples of 2^-32), c / u taken as c
- * times the FP32 reciprocal of u (c is below half an ulp of u).
+ * log1p(x): u = 1 + x rounded; u = m 2^e with m in [1/sqrt2, sqrt2); the
+ * bucket of m (its exponent and top 8 fraction bits) gives R, an 8-bit
+ * approximation of 1/m, and -ln R = Lh + Ll.  For e in [-1, 2] (u in
+ * [1/(2 sqrt2), 4 sqrt2)): r = (1 + x) R 2^-e - 1 = x R' + (R' - 1) with
+ * R' = R 2^-e, in one fma (both terms exact), so r carries the exact
+ * 1 + x; otherwise r = m R - 1 (exact: a multiple of 2^-60 below 2^-7, one
+ * fma) and the rounding error c of 1 + x (two-sum) enters as c / u, c
+ * times the FP32 reciprocal of u.  ln(1 + r) = r - r^2/2 + ... - r^8/8
+ * (|r| < 0.006); log1p(x) = (e ln2_hi + Lh) + (ln(1 + r) + (e ln2_lo + Ll))
+ * (with c / u added to ln(1 + r) in one fma in the second form), the
+ * first sum exact (both terms are multiples of 2^-32).
  * u = +inf gives +inf, u = 0 gives -inf, a NaN gives NaN.
  *
  * expm1(w): |w| limited to 800 (beyond, the result is -1 or +inf either
- * way); k = nearest integer to w 32/ln2, evaluated in FP32 on the
+ * way); k = nearest integer to w 256/ln2, evaluated in FP32 on the
  * significand-truncated w (any nearby integer is a valid reduction);
- * j = k mod 32, m = (k - j)/32; r = (w - k ln2_hi/32) - k ln2_lo/32 (the
- * first product and difference exact); expm1(r) = r + r^2 (1/2 + r/6 + ...
- * + r^5/5040) (|r| < 0.0109); 2^(j/32) = Th + Tl; S = Th expm1(r) + Tl;
- * expm1(w) = (2^m Th - 1) + 2^m S, and for m > 1023 (2^m not finite)
- * ((Th + S) 2^(m - 1023)) 2^1023.
+ * j = k mod 256, m = (k - j)/256; r = w - k ln2_hi/256 (exact);
+ * expm1(r) = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120) (|r| < 0.0016).
+ * For m in {-1, 0}: expm1(w) = A em + B, A = e^(k ln2_hi/256) and
+ * B = A - 1 rounded from the table (the low part of k ln2/256 is in the
+ * table).  Otherwise r -= k ln2_lo/256 first; 2^(j/256) = Th + Tl;
+ * S = Th expm1(r) + Tl; expm1(w) = (2^m Th - 1) + 2^m S, and for m > 1023
+ * (2^m not finite) ((Th + S) 2^(m - 1023)) 2^1023.
  */
 #include "orc_tables.h"
 
@@ -221,23 +225,12 @@ static float orc_f32_trunc(double x)
     return v;
 }
 
-double orc_log1p(double x)
+/* ln(1 + r) = r + r^2 (-1/2 + r (1/3 + r (-1/4 + r P))), with
+ * P = 1/5 - r/6 + r^2/7 - r^3/8 in single precision on the truncated r:
+ * it enters scaled by r^5 (|r| < 0.006), below 0.15 ulp of error */
+static double orc_log1p_series(double r)
 {
-    double u = 1.0 + x;
-    if (!(u > 0.0) || u == INFINITY) return u == 0.0 ? -INFINITY : (u == INFINITY ? INFINITY : NAN);
-    double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
-    int e;
-    double m = frexp(u, &e);
-    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
-    int key = (int)(orc_bits(m) >> 44) - ORC_LOG_KEY0;
-    double R = orc_from_bits(orc_log_tab[key][0]);
-    double Lh = orc_from_bits(orc_log_tab[key][1]);
-    double Ll = orc_from_bits(orc_log_tab[key][2]);
-    double r = fma(m, R, -1.0);
     double r2 = r * r;
-    /* ln(1 + r) = r + r^2 (-1/2 + r (1/3 + r (-1/4 + r P))), with
-     * P = 1/5 - r/6 + r^2/7 - r^3/8 in single precision on the truncated r:
-     * it enters scaled by r^5 (|r| < 0.006), below 0.15 ulp of error */
     float rf = orc_f32_trunc(r);
     float pf = fmaf(-0x1.0p-3f, rf, 0x1.24924ap-3f);     /* -1/8, 1/7 */
     pf = fmaf(pf, rf, -0x1.555556p-3f);                  /* -1/6 */
@@ -245,12 +238,52 @@ double orc_log1p(double x)
     double q = fma(r, (double)pf, -0.25);
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
-    double lg = fma(r2, q, r);
+    return fma(r2, q, r);
+}
+
+double orc_log1p(double x)
+{
+    double u = 1.0 + x;
+    if (!(u > 0.0) || u == INFINITY) return u == 0.0 ? -INFINITY : (u == INFINITY ? INFINITY : NAN);
+    int e;
+    double m = frexp(u, &e);
+    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
+    int key = (int)(orc_bits(m) >> 44) - ORC_LOG_KEY0;
+    double R = orc_from_bits(orc_log_tab[key][0]);
+    double Lh = orc_from_bits(orc_log_tab[key][1]);
+    double Ll = orc_from_bits(orc_log_tab[key][2]);
     double de = (double)e;
+    if (e >= -1 && e <= 2) {
+        /* r = (1 + x) R 2^-e - 1 from x itself, to one rounding:
+         * x (R 2^-e) + (R 2^-e - 1) in one fma, both terms exact (R has 8
+         * significant bits), so the rounding of 1 + x never enters */
+        double Rp = ldexp(R, -e);
+        double r = fma(x, Rp, Rp - 1.0);
+        double lg = orc_log1p_series(r);
+        return fma(de, ORC_LN2_HI, Lh) + (lg + fma(de, ORC_LN2_LO, Ll));
+    }
+    /* other exponents: r = m R - 1 exact, and the rounding error c of
+     * 1 + x (two-sum) added as c / u */
+    double c = (x > 1.0) ? (1.0 - (u - x)) : (x - (u - 1.0));
+    double r = fma(m, R, -1.0);
+    double lg = orc_log1p_series(r);
     double ru = (double)(1.0f / (float)u);
     double hi = fma(de, ORC_LN2_HI, Lh);
     double lo = fma(c, ru, lg) + fma(de, ORC_LN2_LO, Ll);
     return hi + lo;
+}
+
+/* e^r - 1 = r + r^2 (1/2 + r (1/6 + r P)) to r^5 (|r| < 0.0016: the next
+ * term is below 1.5e-17 of the result), with P = 1/24 + r/120 in single
+ * precision on the truncated r: scaled by r^4 its error stays below
+ * 0.1 ulp */
+static double orc_expm1_series(double r)
+{
+    double r2 = r * r;
+    float pf = fmaf(0x1.111112p-7f, orc_f32_trunc(r), 0x1.555556p-5f);   /* 1/120, 1/24 */
+    double p = fma((double)pf, r, 1.0 / 6.0);
+    p = fma(p, r, 1.0 / 2.0);
+    return fma(r2, p, r);
 }
 
 double orc_expm1(double w)
@@ -265,24 +298,17 @@ double orc_expm1(double w)
     int j = k & 255;
     int m = (k - j) / 256;
     double dk = (double)k;
-    double r = fma(-dk, ORC_LN2_HI / 256.0, wc);
-    r = fma(-dk, ORC_LN2_LO / 256.0, r);
-    double r2 = r * r;
-    /* e^r - 1 = r + r^2 (1/2 + r (1/6 + r P)) to r^5 (|r| < 0.0016: the
-     * next term is below 1.5e-17 of the result), with P = 1/24 + r/120 in
-     * single precision on the truncated r: scaled by r^4 its error stays
-     * below 0.1 ulp */
-    float pf = fmaf(0x1.111112p-7f, orc_f32_trunc(r), 0x1.555556p-5f);   /* 1/120, 1/24 */
-    double p = fma((double)pf, r, 1.0 / 6.0);
-    p = fma(p, r, 1.0 / 2.0);
-    double em = fma(r2, p, r);
+    double r = fma(-dk, ORC_LN2_HI / 256.0, wc);           /* exact */
     if (m == -1 || m == 0) {
-        /* e^w - 1 = 2^m 2^(j/256) (1 + em) - 1 = A em + B, A = 2^m Th,
-         * B = 2^m 2^(j/256) - 1 rounded: one fma */
+        /* e^w - 1 = e^(k ln2_hi/256) (1 + em) - 1 = A em + B with
+         * em = e^r - 1, A = e^(k ln2_hi/256) and B = A - 1 rounded from
+         * the table: one fma */
         double A = orc_from_bits(orc_exp_ab[m + 1][j][0]);
         double B = orc_from_bits(orc_exp_ab[m + 1][j][1]);
-        return fma(A, em, B);
+        return fma(A, orc_expm1_series(r), B);
     }
+    r = fma(-dk, ORC_LN2_LO / 256.0, r);
+    double em = orc_expm1_series(r);
     double Th = orc_from_bits(orc_exp_tab[j][0]);
     double Tl = orc_from_bits(orc_exp_tab[j][1]);
     double S = fma(Th, em, Tl);

@@ -15,13 +15,16 @@ rounded exactly to the binary format:
   with Lh and e * ln2_hi both multiples of 2^-32, their sum is exact.
 * exponential table, j = 0..255: Th = 2^(j/256) and Tl = 2^(j/256) - Th,
   each rounded to the nearest double.
-* the logarithm's exponent terms for e = -1..2, per bucket: e ln2_hi + Lh
-  (exact: both are multiples of 2^-32) and e ln2_lo + Ll rounded to the
-  nearest double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo
-  the two doubles the kernels use.
-* for m = -1 and 0, per j: A = 2^m Th (exact) and B = 2^m 2^(j/256) - 1
-  rounded to the nearest double (e^w - 1 = A em + B to one rounding when
-  w = (256 m + j) ln2/256 + r and em = e^r - 1).
+* the logarithm's rows for e = -1..2, per bucket: e ln2_hi + Lh (exact:
+  both are multiples of 2^-32), e ln2_lo + Ll rounded to the nearest
+  double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo the two
+  doubles the kernels use, and R' = R 2^-e and R' - 1 (both exact: R has 8
+  significant bits), so that r = (1 + x) R' - 1 = x R' + (R' - 1) is one
+  fma on x itself.
+* for k = 256 m + j with m = -1 and 0: A = e^(k c) and B = e^(k c) - 1,
+  each rounded to the nearest double, c the double ln2_hi / 256; with
+  r = w - k c (exact) and em = e^r - 1, e^w - 1 = A em + B to one
+  rounding (the low part of k ln2/256 is in the table).
 
 Run: python gen_f64_tables.py   (rewrites the header next to this file)
 """
@@ -83,26 +86,28 @@ def tables():
 
 
 def e_terms(logs):
-    """(e ln2_hi + Lh, e ln2_lo + Ll rounded) for e = E0 .. E0 + N_E - 1, per bucket."""
+    """(e ln2_hi + Lh, e ln2_lo + Ll rounded, R 2^-e, R 2^-e - 1) for
+    e = E0 .. E0 + N_E - 1, per bucket."""
     rows = []
     for e in range(E0, E0 + N_E):
         for R, Lh, Ll in logs:
             hi = e * Fraction(LN2_HI) + Fraction(Lh)
-            assert Fraction(float(hi)) == hi
-            rows.append((float(hi), float(e * Fraction(LN2_LO) + Fraction(Ll))))
+            Rp = Fraction(R) / Fraction(2) ** e
+            for v in (hi, Rp, Rp - 1):
+                assert Fraction(float(v)) == v
+            rows.append((float(hi), float(e * Fraction(LN2_LO) + Fraction(Ll)), float(Rp), float(Rp - 1)))
     return rows
 
 
 def ab_terms():
-    """(2^m Th, RN(2^m 2^(j/256) - 1)) for m = M0 .. M0 + N_M - 1, per j."""
+    """(RN(e^(k c)), RN(e^(k c) - 1)) for k = 256 M0 .. 256 (M0 + N_M) - 1,
+    c = ln2_hi / 256."""
     ctx = decimal.Context(prec=90)
+    c = ctx.divide(Decimal(LN2_HI), Decimal(256))    # exact: Decimal(float) is the binary value
     rows = []
-    for m in range(M0, M0 + N_M):
-        for j in range(N_EXP):
-            T = Fraction(ctx.power(Decimal(2), ctx.divide(Decimal(j), Decimal(N_EXP))))
-            A = Fraction(2) ** m * Fraction(float(T))
-            assert Fraction(float(A)) == A
-            rows.append((float(A), float(Fraction(2) ** m * T - 1)))
+    for k in range(N_EXP * M0, N_EXP * (M0 + N_M)):
+        T = Fraction(ctx.exp(ctx.multiply(Decimal(k), c)))
+        rows.append((float(T), float(T - 1)))
     return rows
 
 
@@ -124,12 +129,14 @@ def render() -> str:
     for Th, Tl in exps:
         out.append(f"    {_hex(Th)}, {_hex(Tl)},")
     out += ["};", "", f"constexpr int F64_LOG_E0 = {E0};", f"constexpr int F64_LOG_NE = {N_E};",
-            "// per exponent e (rows E0 ..) and bucket: e ln2_hi + Lh, RN(e ln2_lo + Ll) (16 bytes)",
-            "static __device__ __align__(16) const unsigned long long f64_log_e_tab[F64_LOG_NE * F64_LOG_N * 2] = {"]
-    for hi, lo in e_terms(logs):
-        out.append(f"    {_hex(hi)}, {_hex(lo)},")
+            "// per exponent e (rows E0 ..) and bucket: e ln2_hi + Lh, RN(e ln2_lo + Ll), R 2^-e,",
+            "// R 2^-e - 1 (32 bytes)",
+            "static __device__ __align__(16) const unsigned long long f64_log_e_tab[F64_LOG_NE * F64_LOG_N * 4] = {"]
+    for hi, lo, Rp, Rm in e_terms(logs):
+        out.append(f"    {_hex(hi)}, {_hex(lo)}, {_hex(Rp)}, {_hex(Rm)},")
     out += ["};", "", f"constexpr int F64_EXP_M0 = {M0};", f"constexpr int F64_EXP_NM = {N_M};",
-            "// per exponent m (rows M0 ..) and j: 2^m Th, RN(2^m 2^(j/256) - 1) (16 bytes)",
+            "// per exponent m (rows M0 ..) and j, k = 256 m + j: RN(e^(k c)), RN(e^(k c) - 1),",
+            "// c = ln2_hi / 256 (16 bytes)",
             "static __device__ __align__(16) const unsigned long long f64_exp_ab_tab[F64_EXP_NM * F64_EXP_N * 2] = {"]
     for A, B in ab_terms():
         out.append(f"    {_hex(A)}, {_hex(B)},")

@@ -182,61 +182,37 @@ __device__ __forceinline__ double f64_div(double d, double v)
 // IEEE floating-point arithmetic", ACM TOMS 16(4), 1990), with tables and
 // series lengths of this file's own choosing.  The tables
 // (mp_f64_tables.h) hold correctly rounded constants.
-//   log1p(x): u = 1 + x, c = its rounding error (two-sum); u = m 2^e with
-//     m in [1/sqrt2, sqrt2); the bucket of m (exponent and top 8 fraction
-//     bits) gives R ~ 1/m with 8 significant bits and -ln R = Lh + Ll;
-//     r = m R - 1 exactly (one fma); ln(1 + r) by its series to r^8
-//     (|r| < 0.006), the factor of r^5 in FP32 on the truncated r;
-//     (e ln2_hi + Lh) (exact) + ((ln(1 + r) + c / u) +
-//     (e ln2_lo + Ll)), c / u as c times the FP32 reciprocal of u; the two
-//     e terms come from a table for e in [-1, 2] (the same values as the
-//     fmas that give them otherwise).
-//     u = +inf -> +inf, u = 0 -> -inf, NaN -> NaN.
+//   log1p(x): u = 1 + x; u = m 2^e with m in [1/sqrt2, sqrt2); the bucket
+//     of m (exponent and top 8 fraction bits) gives R ~ 1/m with 8
+//     significant bits and -ln R = Lh + Ll.  For e in [-1, 2] (u in
+//     [1/(2 sqrt2), 4 sqrt2): all but a few in a thousand exit times) a
+//     table row per (e, bucket) holds e ln2_hi + Lh (exact), e ln2_lo + Ll
+//     rounded, R' = R 2^-e and R' - 1 (exact), and r = (1 + x) R' - 1 =
+//     x R' + (R' - 1) is one fma on x itself, so the rounding of 1 + x never
+//     enters; otherwise (out of line) r = m R - 1 exactly and the rounding
+//     error c of 1 + x (two-sum) is added as c times the FP32 reciprocal of
+//     u.  ln(1 + r) by its series to r^8 (|r| < 0.006), the factor of r^5
+//     in FP32 on the truncated r; result (e ln2_hi + Lh) +
+//     (ln(1 + r) + (e ln2_lo + Ll)).  u = +inf -> +inf, u = 0 -> -inf,
+//     NaN -> NaN.
 //   expm1(w): |w| limited to 800; k = nearest integer to w 256/ln2 in FP32
 //     on the truncated w; j = k mod 256, m = (k - j) / 256;
-//     r = (w - k ln2_hi/256) - k ln2_lo/256; expm1(r) by its series to r^5
-//     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r;
-//     2^(j/256) = Th + Tl, S = Th expm1(r) + Tl;
+//     r = w - k ln2_hi/256 (exact); expm1(r) by its series to r^5
+//     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r.  For
+//     m in {-1, 0} (all but a few in a thousand motions) expm1(w) =
+//     A em + B in one fma, A = e^(k ln2_hi/256) and B = A - 1 rounded from
+//     a table (the low part of k ln2/256 is in the table); otherwise (out
+//     of line) r -= k ln2_lo/256, 2^(j/256) = Th + Tl, S = Th expm1(r) + Tl,
 //     expm1(w) = (2^m Th - 1) + 2^m S ((Th + S) 2^(m-1023) 2^1023 when
-//     2^m is not finite); for m in {-1, 0} A em + B in one fma, with
-//     A = 2^m Th and B = 2^m 2^(j/256) - 1 rounded from a table.  About 12
-//     and 7 FP64 operations.
+//     2^m is not finite).  About 9 and 6 FP64 operations.
 // ---------------------------------------------------------------------------
 
-// e ln2_hi + Lh and e ln2_lo + Ll by the fmas, for exponents outside the
-// e-term table (rare; out of line, and a side effect keeps the call from
-// being evaluated speculatively)
-static __device__ __noinline__ double2 log_e_terms(int e, double Lh, int key)
+// ln(1 + r) by its series to r^8; the tail 1/5 - r/6 + r^2/7 - r^3/8 in
+// FP32: it enters scaled by r^5, below 2.6e-10 of the result, so its FP32
+// error stays below 0.15 ulp (and the FP64 pipe is spared three fmas)
+__device__ __forceinline__ double log1p_series(double r)
 {
-    asm volatile("");
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
-    const double Ll = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key + 1).x;
-    const double de = i2d_exact(e);
-    return make_double2(fma(de, ln2_hi, Lh), fma(de, ln2_lo, Ll));
-}
-
-__device__ __forceinline__ double series_log1p(double x)
-{
-    const double u = 1.0 + x;
-    const long long ub = bits(u);
-    const bool ok = ub > 0LL && ub < 0x7ff0000000000000LL;   // 0 < u < inf
-    // two-sum error of 1 + x: (1 - (u - x)) when x > 1, else (x - (u - 1));
-    // the operands are selected, so both lane groups share two FP64 adds
-    const bool big = gt_pos(x, 1.0);
-    const double c = (big ? 1.0 : x) - (u - (big ? x : 1.0));
-    int e;
-    double m = frexp_normal(ok ? u : 1.0, e);   // u >= 2^-53 when ok
-    const bool below = bits(m) < bits(0.70710678118654752440);   // m in [1/2, 1/sqrt2): m * 2, exactly
-    m = __longlong_as_double(bits(m) + (below ? (1LL << 52) : 0LL));
-    e -= below ? 1 : 0;
-    const int key = (int)(bits(m) >> 44) - F64_LOG_KEY0;
-    const double2 t0 = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key);
-    const double R = t0.x, Lh = t0.y;
-    const double r = fma(m, R, -1.0);
     const double r2 = r * r;
-    // the series' tail 1/5 - r/6 + r^2/7 - r^3/8 in FP32: it enters scaled
-    // by r^5, below 2.6e-10 of the result, so its FP32 error stays below
-    // 0.15 ulp (and the FP64 pipe is spared three fmas)
     const float rf = f32_trunc(r);
     float pf = __fmaf_rn(-0x1.0p-3f, rf, 0x1.24924ap-3f);   // -1/8, 1/7
     pf = __fmaf_rn(pf, rf, -0x1.555556p-3f);                // -1/6
@@ -244,31 +220,75 @@ __device__ __forceinline__ double series_log1p(double x)
     double q = fma(r, f2d_normal(pf), -0.25);   // pf near 1/5: normal
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
-    const double lg = fma(r2, q, r);
-    const double ru = f2d_pos(__frcp_rn(f32_rn_pos(ok ? u : 1.0)));   // (double)(1.0f / (float)u)
-    // e ln2_hi + Lh (exact) and fma(e, ln2_lo, Ll): from the e-term table for
-    // e in [-1, 2] (u in [1/(2 sqrt2), 4 sqrt2): all but a few in a thousand
-    // exit-time evaluations), else by the two fmas
+    return fma(r2, q, r);
+}
+
+// log1p for exponents e outside the table rows (rare; out of line, and a
+// side effect keeps the call from being evaluated speculatively):
+// r = m R - 1 exactly and the two-sum error c of u = 1 + x as c / u
+static __device__ __noinline__ double log1p_far(double x, double u, double m, int e, int key)
+{
+    asm volatile("");
+    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    // (1 - (u - x)) when x > 1, else (x - (u - 1))
+    const bool big = gt_pos(x, 1.0);
+    const double c = (big ? 1.0 : x) - (u - (big ? x : 1.0));
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key);       // R, Lh
+    const double Ll = __ldg(reinterpret_cast<const double2*>(f64_log_tab) + 2 * key + 1).x;
+    const double lg = log1p_series(fma(m, t0.x, -1.0));
+    const double ru = f2d_pos(__frcp_rn(f32_rn_pos(u)));   // (double)(1.0f / (float)u)
+    const double de = i2d_exact(e);
+    return fma(de, ln2_hi, t0.y) + (fma(c, ru, lg) + fma(de, ln2_lo, Ll));
+}
+
+__device__ __forceinline__ double series_log1p(double x)
+{
+    const double u = 1.0 + x;
+    const long long ub = bits(u);
+    const bool ok = ub > 0LL && ub < 0x7ff0000000000000LL;   // 0 < u < inf
+    int e;
+    double m = frexp_normal(ok ? u : 1.0, e);   // u >= 2^-53 when ok
+    const bool below = bits(m) < bits(0.70710678118654752440);   // m in [1/2, 1/sqrt2): m * 2, exactly
+    m = __longlong_as_double(bits(m) + (below ? (1LL << 52) : 0LL));
+    e -= below ? 1 : 0;
+    const int key = (int)(bits(m) >> 44) - F64_LOG_KEY0;
     const unsigned er = (unsigned)(e - F64_LOG_E0);
-    double2 hl;
-    if (er < (unsigned)F64_LOG_NE)
-        hl = __ldg(reinterpret_cast<const double2*>(f64_log_e_tab) + er * F64_LOG_N + key);
-    else
-        hl = log_e_terms(e, Lh, key);
-    const double hi = hl.x;
-    const double lo = fma(c, ru, lg) + hl.y;
+    double res;
+    if (er < (unsigned)F64_LOG_NE) {
+        // (e ln2_hi + Lh, RN(e ln2_lo + Ll)), (R 2^-e, R 2^-e - 1)
+        const double2* row = reinterpret_cast<const double2*>(f64_log_e_tab) + 2 * (er * F64_LOG_N + key);
+        const double2 hl = __ldg(row), rp = __ldg(row + 1);
+        const double lg = log1p_series(fma(x, rp.x, rp.y));
+        res = hl.x + (lg + hl.y);
+    } else {
+        res = log1p_far(x, u, m, e, key);
+    }
     const long long special = eq0(u) ? (long long)0xfff0000000000000ULL
                                      : (ub == 0x7ff0000000000000LL ? 0x7ff0000000000000LL
                                                                    : (long long)0xfff8000000000000ULL);
-    return __longlong_as_double(ok ? bits(hi + lo) : special);   // -inf, +inf, NaN
+    return __longlong_as_double(ok ? bits(res) : special);   // -inf, +inf, NaN
 }
 
-// expm1's reconstruction for m outside {-1, 0} (rare; out of line, not
-// evaluated speculatively): S = Th em + Tl, (2^m Th - 1) + 2^m S, and
-// (Th + S) 2^(m-1023) 2^1023 where 2^m overflows
-static __device__ __noinline__ double expm1_far(double em, int j, int m)
+// e^r - 1 by its series to r^5 (the next term is below 1.5e-17 of the
+// result); the factor of r^4, 1/24 + r/120, in FP32: scaled by r^4 (below
+// 1.7e-10 of the result) its FP32 error stays below 0.1 ulp
+__device__ __forceinline__ double expm1_series(double r)
+{
+    const double r2 = r * r;
+    const float pf = __fmaf_rn(0x1.111112p-7f, f32_trunc(r), 0x1.555556p-5f);   // 1/120, 1/24
+    double p = fma(f2d_normal(pf), r, 1.0 / 6.0);   // pf near 1/24: normal
+    p = fma(p, r, 1.0 / 2.0);
+    return fma(r2, p, r);
+}
+
+// expm1 for m outside {-1, 0} (rare; out of line, not evaluated
+// speculatively): r -= k ln2_lo/256, S = Th em + Tl, (2^m Th - 1) + 2^m S,
+// and (Th + S) 2^(m-1023) 2^1023 where 2^m overflows
+static __device__ __noinline__ double expm1_far(double r, double dk, int j, int m)
 {
     asm volatile("");
+    const double ln2_lo = 1.90821492927058770002e-10;
+    const double em = expm1_series(fma(dk, -(ln2_lo / 256.0), r));
     const double2 T = __ldg(reinterpret_cast<const double2*>(f64_exp_tab) + j);   // 2^(j/256)
     const double S = fma(T.x, em, T.y);
     if (m > 1023) return ((T.x + S) * pow2i(m - 1023 > 2000 ? 2000 : m - 1023)) * pow2i(1023);
@@ -278,7 +298,7 @@ static __device__ __noinline__ double expm1_far(double em, int j, int m)
 
 __device__ __forceinline__ double series_expm1(double w)
 {
-    const double ln2_hi = 6.93147180369123816490e-01, ln2_lo = 1.90821492927058770002e-10;
+    const double ln2_hi = 6.93147180369123816490e-01;
     const double wc = __longlong_as_double((abs_lt(w, 800.0) || is_nan(w))
                                                ? bits(w)
                                                : (lt0(w) ? (long long)0xc089000000000000ULL    // -800
@@ -289,27 +309,17 @@ __device__ __forceinline__ double series_expm1(double w)
     const int j = k & 255;
     const int m = (k - j) >> 8;
     const double dk = i2d_exact(k);
-    // (the constants negated, not k: the same products, and no separate
+    // w - k ln2_hi/256, exact (the constant negated, not k: no separate
     // negation of k on the FP64 pipe)
-    double r = fma(dk, -(ln2_hi / 256.0), wc);
-    r = fma(dk, -(ln2_lo / 256.0), r);
-    const double r2 = r * r;
-    // the factor of r^4, 1/24 + r/120 (the series' next term is below
-    // 1.5e-17 of the result), in FP32: scaled by r^4 (below 1.7e-10 of the
-    // result) its FP32 error stays below 0.1 ulp
-    const float pf = __fmaf_rn(0x1.111112p-7f, f32_trunc(r), 0x1.555556p-5f);   // 1/120, 1/24
-    double p = fma(f2d_normal(pf), r, 1.0 / 6.0);   // pf near 1/24: normal
-    p = fma(p, r, 1.0 / 2.0);
-    const double em = fma(r2, p, r);
-    // m in {-1, 0} (|w| below ln 2 about: all but a few in a thousand
-    // motions): e^w - 1 = A em + B with A = 2^m Th and B = 2^m 2^(j/256) - 1
+    const double r = fma(dk, -(ln2_hi / 256.0), wc);
+    // m in {-1, 0}: e^w - 1 = A em + B, A = e^(k ln2_hi/256) and B = A - 1
     // rounded, from the table, in one fma
     const unsigned mr = (unsigned)(m - F64_EXP_M0);
     if (mr < (unsigned)F64_EXP_NM) {
         const double2 ab = __ldg(reinterpret_cast<const double2*>(f64_exp_ab_tab) + mr * F64_EXP_N + j);
-        return fma(ab.x, em, ab.y);
+        return fma(ab.x, expm1_series(r), ab.y);
     }
-    return expm1_far(em, j, m);
+    return expm1_far(r, dk, j, m);
 }
 
 // Exit time along one axis from the distance d to the reachable face

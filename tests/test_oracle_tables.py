@@ -39,8 +39,8 @@ N_EXP = 256                  # entries 2^(j/256) of the exponential table
 
 
 N_E = 4                      # device e-term rows, e = -1 .. 2
-N_M = 2                      # reconstruction rows (A, B), m = -1, 0
-DEV_EXTRA = 2 * N_E * 257 + 2 * N_M * N_EXP
+N_M = 2                      # reconstruction rows (A, B), m = -1, 0 (k = -256 .. 255)
+DEV_EXTRA = 4 * N_E * 257 + 2 * N_M * N_EXP
 ORC_EXTRA = 2 * N_M * N_EXP
 
 
@@ -182,6 +182,18 @@ def test_log1p_within_one_ulp_in_every_bucket():
                 worst = max(worst, _ulps(O.log1p(x), ref))
     for x in list(rng.uniform(-1e-6, 1e-6, 200)) + list(-np.exp(-rng.uniform(30, 36, 50))):
         worst = max(worst, _ulps(O.log1p(x), float(mpmath.log1p(mpmath.mpf(x)))))
+    # arguments whose 1 + x is inexact (the rounding of the sum must not
+    # enter), in every bucket and every exponent row of the table and
+    # either side of it
+    for i in range(257):
+        key = KEY0 + i
+        lo = max(_d(key << 44), 1 / math.sqrt(2))
+        hi = min(_d(((key + 1) << 44) - 1), math.nextafter(math.sqrt(2), 0))
+        for e in (-2, -1, 0, 1, 2, 3):
+            u = math.ldexp(float(rng.uniform(lo, hi)), e)
+            x = (u - 1.0) + float(rng.uniform(-0.5, 0.5)) * math.ulp(u)
+            if x > -1.0:
+                worst = max(worst, _ulps(O.log1p(x), float(mpmath.log1p(mpmath.mpf(x)))))
     assert worst <= 1.0
     assert O.log1p(math.inf) == math.inf and O.log1p(-1.0) == -math.inf and math.isnan(O.log1p(-2.0))
 
@@ -237,10 +249,11 @@ def test_quotient_within_one_ulp():
 
 
 def test_log_e_terms_table():
-    """The device's e-term rows of the logarithm (e = -1 .. 2): e ln2_hi + Lh
-    exactly and e ln2_lo + Ll rounded to the nearest double, which is what
+    """The device's rows of the logarithm for e = -1 .. 2: e ln2_hi + Lh
+    exactly and e ln2_lo + Ll rounded to the nearest double (which is what
     fma(e, ln2_lo, Ll) gives, so the table and the fmas are interchangeable
-    bit for bit."""
+    bit for bit), and R' = R 2^-e and R' - 1 exactly, so that
+    fma(x, R', R' - 1) is (1 + x) R' - 1 to one rounding."""
     path = os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h")
     words = _words(path)
     log, _ = _read(path, 3, extra=DEV_EXTRA)
@@ -248,21 +261,24 @@ def test_log_e_terms_table():
     for r in range(N_E):
         e = r - 1
         for i, (R, Lh, Ll) in enumerate(log):
-            hi, lo = _d(words[base + 2 * (r * 257 + i)]), _d(words[base + 2 * (r * 257 + i) + 1])
+            hi, lo, Rp, Rm = (_d(w) for w in words[base + 4 * (r * 257 + i):base + 4 * (r * 257 + i) + 4])
             assert Fraction(hi) == e * Fraction(LN2_HI) + Fraction(Lh)
             assert lo == float(e * Fraction(LN2_LO) + Fraction(Ll))
             assert lo == math.fma(float(e), LN2_LO, Ll) if hasattr(math, "fma") else True
+            assert Fraction(Rp) == Fraction(R) / 2 ** e and Fraction(Rm) == Fraction(R) / 2 ** e - 1
 
 
 def test_exp_reconstruction_table():
-    """The exponential's fused reconstruction for m = -1, 0: A = 2^m Th
-    exactly and B = 2^m 2^(j/256) - 1 correctly rounded (mpmath at 300 bits),
-    the same words in the oracle's table and the device's."""
+    """The exponential's fused reconstruction for m = -1, 0 (k = 256 m + j):
+    A = e^(k c) and B = e^(k c) - 1 correctly rounded (mpmath at 300 bits),
+    c the double ln2_hi / 256, the same words in the oracle's table and the
+    device's; A is 2^(k/256) up to the low part of k ln2/256 (below 2e-10
+    relative)."""
     mpmath.mp.prec = 300
     dev = _words(os.path.join(ROOT, "paper_2302_13590_gb300", "csrc", "mp_f64_tables.h"))
     orc = _words(os.path.join(ROOT, "oracle", "orc_tables.h"))
     _, exp = _read(os.path.join(ROOT, "oracle", "orc_tables.h"), 3, extra=ORC_EXTRA)
-    dbase = 257 * 3 + 2 * N_EXP + 2 * N_E * 257
+    dbase = 257 * 3 + 2 * N_EXP + 4 * N_E * 257
     obase = 257 * 3 + 2 * N_EXP
     for r in range(N_M):
         m = r - 1
@@ -270,5 +286,6 @@ def test_exp_reconstruction_table():
             n = 2 * (r * N_EXP + j)
             A, B = _d(dev[dbase + n]), _d(dev[dbase + n + 1])
             assert (dev[dbase + n], dev[dbase + n + 1]) == (orc[obase + n], orc[obase + n + 1])
-            assert A == math.ldexp(Th, m)
-            assert B == float(mpmath.ldexp(mpmath.power(2, mpmath.mpf(j) / N_EXP), m) - 1)
+            x = (N_EXP * m + j) * mpmath.mpf(LN2_HI) / 256
+            assert A == float(mpmath.exp(x)) and B == float(mpmath.exp(x) - 1)
+            assert abs(A / math.ldexp(Th, m) - 1) < 2e-10
