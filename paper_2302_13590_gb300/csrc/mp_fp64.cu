@@ -366,7 +366,10 @@ struct F64Engine {
         const TrackParams& p = R.p;
         (void)in; (void)o; (void)p;
         const double tk = s.kn < p.n_times ? __ldg(o.times + s.kn) : CUDART_INF;
-        return fmin(tk, p.t_stop);
+        // fmin on the integer side: only the lanes with output times in the
+        // step take this, and an FP64 compare would hold the whole warp's
+        // FP64 pipe slot for them
+        return ge_d(tk, p.t_stop) ? p.t_stop : tk;
     }
 
     template <bool TS>
@@ -429,7 +432,7 @@ struct F64Engine {
 
     // per-warp queue of deferred timeseries records (structure of arrays)
     struct RecQ {
-        double p0[RQ_CAP], p1[RQ_CAP], p2[RQ_CAP], tau[RQ_CAP];
+        double p0[RQ_CAP], p1[RQ_CAP], p2[RQ_CAP], t[RQ_CAP];
         long long q[RQ_CAP];
         int c[RQ_CAP], i[RQ_CAP], j[RQ_CAP], k[RQ_CAP], kk[RQ_CAP], st[RQ_CAP], r[RQ_CAP];
     };
@@ -443,7 +446,7 @@ struct F64Engine {
         (void)in; (void)o; (void)p;
         Q.r[slot] = s.r;
         Q.p0[slot] = s.x0; Q.p1[slot] = s.x1; Q.p2[slot] = s.x2;
-        Q.tau[slot] = __ldg(o.times + kk) - s.t;
+        Q.t[slot] = s.t;   // tau = times[kk] - t is formed in rec_eval, where all 32 lanes take it
         Q.q[slot] = q;
         Q.c[slot] = s.c; Q.i[slot] = s.i; Q.j[slot] = s.j; Q.k[slot] = s.k;
         Q.kk[slot] = kk; Q.st[slot] = st;
@@ -457,7 +460,8 @@ struct F64Engine {
         const DevOut& o = R.o;
         const TrackParams& p = R.p;
         const int c = Q.c[slot], i = Q.i[slot], j = Q.j[slot], k = Q.k[slot];
-        const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot], tau = Q.tau[slot];
+        const double p0 = Q.p0[slot], p1 = Q.p1[slot], p2 = Q.p2[slot];
+        const double tau = __ldg(o.times + Q.kk[slot]) - Q.t[slot];
         const double2* rp = reinterpret_cast<const double2*>(f.rec64 + c);
         const double2 r0 = __ldg(rp + 0), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3),
                       r4 = __ldg(rp + 4);
@@ -576,7 +580,8 @@ struct F64Engine {
                 if (TS && path != P_CAPTURE && (ax < 0 || ge_d(t_end, s.tev))) {
                     const double t_rec = path == P_NOEXIT ? CUDART_INF : (path == P_TIME ? p.t_stop : t_end);
                     int kk = s.kn;
-                    while (kk < p.n_times && __ldg(o.times + kk) <= t_rec) kk++;
+                    // (the comparison on the integer side, as in next_event)
+                    while (kk < p.n_times && ge_d(t_rec, __ldg(o.times + kk))) kk++;
                     m = kk - s.kn;
                 }
             }

@@ -194,6 +194,11 @@ def test_log1p_within_one_ulp_in_every_bucket():
             x = (u - 1.0) + float(rng.uniform(-0.5, 0.5)) * math.ulp(u)
             if x > -1.0:
                 worst = max(worst, _ulps(O.log1p(x), float(mpmath.log1p(mpmath.mpf(x)))))
+    # around -1/2, near -1, large arguments and the edges of the table rows
+    for x in (-0.5, math.nextafter(-0.5, -1.0), math.nextafter(-0.5, 0.0), math.nextafter(-1.0, 0.0),
+              -1.0 + 2.0 ** -40, 2.0 ** 24, 2.0 ** 24 + 1.0, 2.0 ** 128, 1e300, 5e-324, -5e-324,
+              4 * math.sqrt(2) - 1, math.nextafter(4 * math.sqrt(2) - 1, 0.0), 1 / (2 * math.sqrt(2)) - 1):
+        worst = max(worst, _ulps(O.log1p(x), float(mpmath.log1p(mpmath.mpf(x)))))
     assert worst <= 1.0
     assert O.log1p(math.inf) == math.inf and O.log1p(-1.0) == -math.inf and math.isnan(O.log1p(-2.0))
 
