@@ -13,7 +13,7 @@ computed here in exact integer fixed-point arithmetic (2^-256 units):
   rounded to the nearest double.
 * exponential table, j = 0..255: Th = 2^(j/256) rounded to the nearest
   double, Tl = 2^(j/256) - Th rounded to the nearest double.
-* for k = 256 m + j with m = -1 and 0 (k = -256 .. 255): A = e^(k c) and
+* for k = 256 m + j with m = -2 .. 1 (k = -512 .. 511): A = e^(k c) and
   B = e^(k c) - 1, each rounded to the nearest double, where c is the
   double ln2_hi / 256 (ln2_hi = 0x3fe62e42fee00000, a multiple of 2^-32).
   With r = w - k c (exact) and em = e^r - 1, e^w - 1 = e^(k c) (1 + em) - 1
@@ -36,6 +36,7 @@ P = 256                      # fixed-point fraction bits
 KEY0 = (1022 << 8) + 106     # first bucket: exponent of 0.5, fraction bits 106/256
 N_LOG = 257
 N_EXP = 256
+M0, N_M = -2, 4             # exponent rows of the reconstruction table
 
 
 def rn53(num: int, scale: int) -> float:
@@ -159,7 +160,7 @@ def exp_ab_table():
     lh = struct.unpack("<d", struct.pack("<Q", LN2_HI))[0]
     c = Fraction(lh) / 256                     # a multiple of 2^-40
     rows = []
-    for k in range(-N_EXP, N_EXP):
+    for k in range(N_EXP * M0, N_EXP * (M0 + N_M)):
         lo, hi = exp_fixed(k * c)
         one = 1 << P
         rows.append((rn53_checked(lo, hi, P), rn53_checked(lo - one, hi - one, P)))
@@ -171,7 +172,8 @@ def render() -> str:
            " * oracle/gen_tables.py (exact integer arithmetic; see there for the",
            " * definitions).  Bit patterns of IEEE doubles. */",
            "#pragma once", "#include <stdint.h>", "",
-           f"#define ORC_LOG_KEY0 {KEY0}", f"#define ORC_LOG_N {N_LOG}", f"#define ORC_EXP_N {N_EXP}", "",
+           f"#define ORC_LOG_KEY0 {KEY0}", f"#define ORC_LOG_N {N_LOG}", f"#define ORC_EXP_N {N_EXP}",
+           f"#define ORC_EXP_M0 ({M0})", f"#define ORC_EXP_NM {N_M}", "",
            "/* per bucket: R, Lh, Ll */",
            "static const uint64_t orc_log_tab[ORC_LOG_N][3] = {"]
     for R, Lh, Ll in log_table():
@@ -179,9 +181,9 @@ def render() -> str:
     out += ["};", "", "/* per j: Th, Tl */", "static const uint64_t orc_exp_tab[ORC_EXP_N][2] = {"]
     for Th, Tl in exp_table():
         out.append(f"    {{0x{bits_of(Th):016x}ULL, 0x{bits_of(Tl):016x}ULL}},")
-    out += ["};", "", "/* per m = -1, 0 and j (k = 256 m + j): A = RN(e^(k c)), B = RN(e^(k c) - 1),",
+    out += ["};", "", "/* per m = -2 .. 1 and j (k = 256 m + j): A = RN(e^(k c)), B = RN(e^(k c) - 1),",
             " * c = ln2_hi / 256 */",
-            "static const uint64_t orc_exp_ab[2][ORC_EXP_N][2] = {"]
+            "static const uint64_t orc_exp_ab[ORC_EXP_NM][ORC_EXP_N][2] = {"]
     for r, (A, B) in enumerate(exp_ab_table()):
         if r % N_EXP == 0:
             out.append("  {")

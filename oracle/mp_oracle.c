@@ -168,8 +168,8 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
  *
  * log1p(x): u = 1 + x rounded; u = m 2^e with m in [1/sqrt2, sqrt2); the
  * bucket of m (its exponent and top 8 fraction bits) gives R, an 8-bit
- * approximation of 1/m, and -ln R = Lh + Ll.  For e in [-1, 2] (u in
- * [1/(2 sqrt2), 4 sqrt2)): r = (1 + x) R 2^-e - 1 = x R' + (R' - 1) with
+ * approximation of 1/m, and -ln R = Lh + Ll.  For e in [-2, 3] (u in
+ * [1/(4 sqrt2), 8 sqrt2)): r = (1 + x) R 2^-e - 1 = x R' + (R' - 1) with
  * R' = R 2^-e, in one fma (both terms exact), so r carries the exact
  * 1 + x; otherwise r = m R - 1 (exact: a multiple of 2^-60 below 2^-7, one
  * fma) and the rounding error c of 1 + x (two-sum) enters as c / u, c
@@ -184,7 +184,7 @@ static uint64_t fnv_step(uint64_t h, int32_t c)
  * significand-truncated w (any nearby integer is a valid reduction);
  * j = k mod 256, m = (k - j)/256; r = w - k ln2_hi/256 (exact);
  * expm1(r) = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120) (|r| < 0.0016).
- * For m in {-1, 0}: expm1(w) = A em + B, A = e^(k ln2_hi/256) and
+ * For m in [-2, 1]: expm1(w) = A em + B, A = e^(k ln2_hi/256) and
  * B = A - 1 rounded from the table (the low part of k ln2/256 is in the
  * table).  Otherwise r -= k ln2_lo/256 first; 2^(j/256) = Th + Tl;
  * S = Th expm1(r) + Tl; expm1(w) = (2^m Th - 1) + 2^m S, and for m > 1023
@@ -253,7 +253,7 @@ double orc_log1p(double x)
     double Lh = orc_from_bits(orc_log_tab[key][1]);
     double Ll = orc_from_bits(orc_log_tab[key][2]);
     double de = (double)e;
-    if (e >= -1 && e <= 2) {
+    if (e >= -2 && e <= 3) {
         /* r = (1 + x) R 2^-e - 1 from x itself, to one rounding:
          * x (R 2^-e) + (R 2^-e - 1) in one fma, both terms exact (R has 8
          * significant bits), so the rounding of 1 + x never enters */
@@ -299,12 +299,12 @@ double orc_expm1(double w)
     int m = (k - j) / 256;
     double dk = (double)k;
     double r = fma(-dk, ORC_LN2_HI / 256.0, wc);           /* exact */
-    if (m == -1 || m == 0) {
+    if (m >= ORC_EXP_M0 && m < ORC_EXP_M0 + ORC_EXP_NM) {
         /* e^w - 1 = e^(k ln2_hi/256) (1 + em) - 1 = A em + B with
          * em = e^r - 1, A = e^(k ln2_hi/256) and B = A - 1 rounded from
          * the table: one fma */
-        double A = orc_from_bits(orc_exp_ab[m + 1][j][0]);
-        double B = orc_from_bits(orc_exp_ab[m + 1][j][1]);
+        double A = orc_from_bits(orc_exp_ab[m - ORC_EXP_M0][j][0]);
+        double B = orc_from_bits(orc_exp_ab[m - ORC_EXP_M0][j][1]);
         return fma(A, orc_expm1_series(r), B);
     }
     r = fma(-dk, ORC_LN2_LO / 256.0, r);

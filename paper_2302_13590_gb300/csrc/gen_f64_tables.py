@@ -15,13 +15,13 @@ rounded exactly to the binary format:
   with Lh and e * ln2_hi both multiples of 2^-32, their sum is exact.
 * exponential table, j = 0..255: Th = 2^(j/256) and Tl = 2^(j/256) - Th,
   each rounded to the nearest double.
-* the logarithm's rows for e = -1..2, per bucket: e ln2_hi + Lh (exact:
+* the logarithm's rows for e = -2..3, per bucket: e ln2_hi + Lh (exact:
   both are multiples of 2^-32), e ln2_lo + Ll rounded to the nearest
   double (what fma(e, ln2_lo, Ll) gives), with ln2_hi and ln2_lo the two
   doubles the kernels use, and R' = R 2^-e and R' - 1 (both exact: R has 8
   significant bits), so that r = (1 + x) R' - 1 = x R' + (R' - 1) is one
   fma on x itself.
-* for k = 256 m + j with m = -1 and 0: A = e^(k c) and B = e^(k c) - 1,
+* for k = 256 m + j with m = -2..1: A = e^(k c) and B = e^(k c) - 1,
   each rounded to the nearest double, c the double ln2_hi / 256; with
   r = w - k c (exact) and em = e^r - 1, e^w - 1 = A em + B to one
   rounding (the low part of k ln2/256 is in the table).
@@ -37,8 +37,8 @@ from fractions import Fraction
 KEY0 = (1022 << 8) + 106
 N_LOG = 257
 N_EXP = 256
-E0, N_E = -1, 4                       # exponent rows of the log table's e terms
-M0, N_M = -1, 2                       # exponent rows of the exp table's 2^m Th - 1
+E0, N_E = -2, 6                       # exponent rows of the log table's e terms
+M0, N_M = -2, 4                       # exponent rows of the exp table's 2^m Th - 1
 LN2_HI = 6.93147180369123816490e-01   # the kernels' split of ln 2
 LN2_LO = 1.90821492927058770002e-10
 

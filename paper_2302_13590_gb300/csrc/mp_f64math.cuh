@@ -184,8 +184,9 @@ __device__ __forceinline__ double f64_div(double d, double v)
 // (mp_f64_tables.h) hold correctly rounded constants.
 //   log1p(x): u = 1 + x; u = m 2^e with m in [1/sqrt2, sqrt2); the bucket
 //     of m (exponent and top 8 fraction bits) gives R ~ 1/m with 8
-//     significant bits and -ln R = Lh + Ll.  For e in [-1, 2] (u in
-//     [1/(2 sqrt2), 4 sqrt2): all but a few in a thousand exit times) a
+//     significant bits and -ln R = Lh + Ll.  For e in [-2, 3] (u in
+//     [1/(4 sqrt2), 8 sqrt2): all but a few in ten thousand exit times,
+//     also on strongly heterogeneous fields with wells) a
 //     table row per (e, bucket) holds e ln2_hi + Lh (exact), e ln2_lo + Ll
 //     rounded, R' = R 2^-e and R' - 1 (exact), and r = (1 + x) R' - 1 =
 //     x R' + (R' - 1) is one fma on x itself, so the rounding of 1 + x never
@@ -199,7 +200,8 @@ __device__ __forceinline__ double f64_div(double d, double v)
 //     on the truncated w; j = k mod 256, m = (k - j) / 256;
 //     r = w - k ln2_hi/256 (exact); expm1(r) by its series to r^5
 //     (|r| < 0.0016), the factor of r^4 in FP32 on the truncated r.  For
-//     m in {-1, 0} (all but a few in a thousand motions) expm1(w) =
+//     m in [-2, 1] (|w| below about 2 ln2: all but a few in a thousand
+//     motions, also on strongly heterogeneous fields with wells) expm1(w) =
 //     A em + B in one fma, A = e^(k ln2_hi/256) and B = A - 1 rounded from
 //     a table (the low part of k ln2/256 is in the table); otherwise (out
 //     of line) r -= k ln2_lo/256, 2^(j/256) = Th + Tl, S = Th expm1(r) + Tl,
@@ -281,7 +283,7 @@ __device__ __forceinline__ double expm1_series(double r)
     return fma(r2, p, r);
 }
 
-// expm1 for m outside {-1, 0} (rare; out of line, not evaluated
+// expm1 for m outside [-2, 1] (rare; out of line, not evaluated
 // speculatively): r -= k ln2_lo/256, S = Th em + Tl, (2^m Th - 1) + 2^m S,
 // and (Th + S) 2^(m-1023) 2^1023 where 2^m overflows
 static __device__ __noinline__ double expm1_far(double r, double dk, int j, int m)
@@ -312,7 +314,7 @@ __device__ __forceinline__ double series_expm1(double w)
     // w - k ln2_hi/256, exact (the constant negated, not k: no separate
     // negation of k on the FP64 pipe)
     const double r = fma(dk, -(ln2_hi / 256.0), wc);
-    // m in {-1, 0}: e^w - 1 = A em + B, A = e^(k ln2_hi/256) and B = A - 1
+    // m in [-2, 1]: e^w - 1 = A em + B, A = e^(k ln2_hi/256) and B = A - 1
     // rounded, from the table, in one fma
     const unsigned mr = (unsigned)(m - F64_EXP_M0);
     if (mr < (unsigned)F64_EXP_NM) {
