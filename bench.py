@@ -65,14 +65,14 @@ BYTES_PER_STEP = {"fp64": 57.0, "mixed": 29.0}
 # holds only for the kernel sources it was taken from (the hash beside it,
 # kernel_src_hash); otherwise the bench reports it as null.
 MIXED_SRC = "d0b109deb9ab3b6a"   # mixed kernel at the capture (unchanged since)
-FP64_SRC = "3eef6c2fd9945972"    # FP64 kernel at its capture
-TRAFFIC = {"fp64": {"src": FP64_SRC, "value": 5 * (313.220352e6 + 305.719808e6)},
+FP64_SRC = "90bd096129eeb0ed"    # FP64 kernel at its capture
+TRAFFIC = {"fp64": {"src": FP64_SRC, "value": 5 * (312.961792e6 + 306.072064e6)},
            "mixed": {"src": MIXED_SRC, "value": 5 * (43.280128e6 + 287.389184e6)}}
 # From the same capture: the FP64 pipe's busy fraction in the FP64 kernel
 # (sm__pipe_fp64_cycles_active, % of peak sustained active), the executed
 # counterpart of the algorithmic fraction (which charges every axis's exit
 # time while the kernel evaluates the exact one of about 1.1 axes a step).
-FP64_PIPE_ACTIVE = {"src": FP64_SRC, "value": 0.7945}
+FP64_PIPE_ACTIVE = {"src": FP64_SRC, "value": 0.7851}
 # Warp-instructions per cell-step of the mixed kernel in the same capture
 # (smsp__inst_executed.sum / cell-steps on 2e5 particles, static schedule,
 # 256 threads: the tuned launch): the mixed kernel is issue-bound, and its
@@ -82,7 +82,7 @@ MIXED_INST_PER_STEP = {"src": MIXED_SRC, "value": 1154103429.0 / 54832447.0}
 ISSUE_PEAK_TINST = 152 * 4 * 2.07e9 / 1e12
 # L2 read bytes per cell-step in the same capture (lts__t_sectors_srcunit_tex_op_read
 # x 32 B / cell-steps): the record gather, cell sizes, output times.
-L2_READ_PER_STEP = {"fp64": {"src": FP64_SRC, "value": 253926022.0 * 32 / 54832426.0},
+L2_READ_PER_STEP = {"fp64": {"src": FP64_SRC, "value": 254077659.0 * 32 / 54832426.0},
                     "mixed": {"src": MIXED_SRC, "value": 61315161.0 * 32 / 54832447.0}}
 
 

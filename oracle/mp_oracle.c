@@ -35,7 +35,7 @@
  *   t_a = ln(1 + z) / A and p + vp (e^{A t} - 1) / A, with 1/A formed once
  *   per cell and multiplied, v1 + A p and the motion's last product and sum
  *   as single fused multiply-adds (C99 fma), d / vp as d times a
- *   Newton-refined reciprocal (orc_div), and log1p / expm1 evaluated by
+ *   refined reciprocal (orc_div), and log1p / expm1 evaluated by
  *   fixed table-driven steps (Tang's method: P. T. P. Tang, "Table-driven
  *   implementation of the exponential function in IEEE floating-point
  *   arithmetic", ACM TOMS 15(2), 1989, and "Table-driven implementation of
@@ -317,17 +317,20 @@ double orc_expm1(double w)
     return fma(t, S, fma(t, Th, -1.0));
 }
 
-/* d / v as d times a reciprocal: the IEEE single-precision reciprocal of
- * the truncated v, then two Newton steps y = y + y (1 - v y), each one fma
- * pair (1 / v within about half an ulp, the quotient within about one);
- * |v| outside [2^-120, 2^121), 0, infinity and NaN divide in IEEE double */
+/* d / v as d times a reciprocal: the IEEE single-precision reciprocal y0
+ * of the truncated v, then one third-order step y = y0 + y0 (e + e^2) with
+ * e = 1 - v y0 in one fma (rounded by less than 2^-75): the truncated
+ * series of 1/v = y0 / (1 - e) leaves e^3 < 2^-67 and the
+ * roundings (1 / v within about half an ulp, the quotient within about
+ * one); |v| outside [2^-120, 2^121), 0, infinity and NaN divide in IEEE
+ * double */
 double orc_div(double d, double v)
 {
     int e = (int)((orc_bits(v) >> 52) & 0x7ff) - 1023;
     if (e < -120 || e > 120) return d / v;
     double y = (double)(1.0f / orc_f32_trunc(v));
-    y = fma(y, fma(-v, y, 1.0), y);
-    y = fma(y, fma(-v, y, 1.0), y);
+    double e0 = fma(-v, y, 1.0);
+    y = fma(y, fma(e0, e0, e0), y);
     return d * y;
 }
 

@@ -150,11 +150,13 @@ __device__ __forceinline__ double f2d_normal(float f)
                                 ((long long)(fb & 0x7fffffu) << 29));
 }
 
-// d / v as d times 1 / v: the IEEE FP32 reciprocal of the truncated v
-// (relative error below 1.8e-7) and two Newton steps y += y (1 - v y)
-// (each squares the error, then one rounding), so 1 / v within about half
-// an ulp and the quotient within about one.  |v| outside [2^-120, 2^121)
-// (and 0, infinity, NaN) takes the IEEE division.
+// d / v as d times 1 / v: the IEEE FP32 reciprocal y0 of the truncated v
+// (relative error below 1.8e-7), then one third-order step
+// y = y0 + y0 (e + e^2) with e = 1 - v y0 in one fma (rounded by less
+// than 2^-75), which leaves e^3 < 2^-67 and the roundings, so 1 / v
+// within about half an ulp and the quotient within about one (three fmas
+// where two Newton steps take four).  |v| outside [2^-120, 2^121) (and 0,
+// infinity, NaN) takes the IEEE division.
 static __device__ __noinline__ double div_ieee(double a, double b) { return a / b; }
 
 __device__ __forceinline__ double f64_div(double d, double v)
@@ -162,9 +164,9 @@ __device__ __forceinline__ double f64_div(double d, double v)
     const int e = (int)((bits(v) >> 52) & 0x7ff) - 1023;
     if (e < -120 || e > 120) return div_ieee(d, v);
     const double y0 = f2d_normal(__frcp_rn(f32_trunc(v)));   // |1 / v| in (2^-121, 2^120]: normal
-    const double y1 = fma(y0, fma(-v, y0, 1.0), y0);
-    const double y2 = fma(y1, fma(-v, y1, 1.0), y1);
-    return d * y2;
+    const double e0 = fma(-v, y0, 1.0);
+    const double y1 = fma(y0, fma(e0, e0, e0), y0);
+    return d * y1;
 }
 
 // ---------------------------------------------------------------------------

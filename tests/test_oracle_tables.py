@@ -227,7 +227,7 @@ def test_expm1_within_two_ulp_for_every_j():
 
 def test_quotient_within_one_ulp():
     """The mirror quotient d / v (the single-precision IEEE reciprocal of the
-    truncated v, two Newton steps, one product) is within one ulp of the
+    truncated v, one third-order step, one product) is within one ulp of the
     correctly rounded quotient over the range of v it serves, exact where
     1 / v is a power of two, and outside that range (|v| < 2^-120 or
     >= 2^121, zero, infinity, NaN) it is the IEEE division."""
