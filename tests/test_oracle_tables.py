@@ -10,7 +10,9 @@ tables the FP64 kernels carry), from outside both:
 * the exponential's reduction, with k rounded in FP32 from the truncated
   argument, keeps |r| below the bound its series is sized for;
 * the oracle's log1p and expm1 stay within 1 and 2 ulp of the correctly
-  rounded result (mpmath) for arguments in every bucket and every j.
+  rounded result (mpmath) for arguments in every bucket and every j;
+* the mirror quotient's reciprocal is correctly rounded on a sample and
+  the quotient within one ulp of the IEEE one.
 """
 import math
 import os
@@ -223,6 +225,19 @@ def test_expm1_within_two_ulp_for_every_j():
     for w in (709.5, 709.78, 709.782):
         assert O.expm1(w) == float(mpmath.expm1(mpmath.mpf(w)))
     assert O.expm1(709.8) == math.inf and O.expm1(1e300) == math.inf and O.expm1(-1e300) == -1.0
+
+
+def test_reciprocal_correctly_rounded():
+    """With d = 1 the mirror quotient is its refined reciprocal alone:
+    y0 + y0 (e + e^2) rounded once, within 2^-67 of 1 / v before that
+    rounding, so it is the correctly rounded 1 / v except within 2^-15 ulp
+    of a rounding midpoint (none in this sample); a step without the e^2
+    term (2^-46 off) or with a wrong sign fails at once."""
+    rng = np.random.default_rng(4)
+    n = 20000
+    v = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-120, 121, n)) * rng.choice([-1.0, 1.0], n)
+    y = np.array([O.div(1.0, float(b)) for b in v])
+    assert np.array_equal(y, 1.0 / v)
 
 
 def test_quotient_within_one_ulp():
